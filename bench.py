@@ -1,0 +1,346 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 SCLaP partitioner on the batched workload.
+
+Workload (default): 512 independent graphs of uneven size partitioned in one
+batched call: half R-MAT (scale uniform in 10..16, edge factor 8,
+a,b,c,d = 0.57,0.19,0.19,0.05), half 2D random geometric graphs (n
+log-uniform in 1k..64k), k uniform in {2,4,8,16}, eps = 0.03, seed 0.  A
+step = one full multilevel partition of every graph (coarsening, initial
+partitioning, uncoarsening, repair, cut), inputs already resident in HBM
+(~1 GB of CSR, larger than L2, so no flush is needed between steps).
+
+Prints one JSON line.  value = partitions/s of the whole job (all ranks).
+Extra keys: sclap_edges_per_s (arcs swept by LP / step time),
+plain_partitions_per_s (the same graphs, one call each, equal cuts checked),
+roofline (LP propose sweep vs the measured HBM copy peak), cpu_baseline (the
+oracle's round-synchronous variant on the host), e2e (host buffers through
+the C ABI, copies included), clocks, gpu_launches.
+
+--impl reference times the CPU oracle instead (the reference arm).
+Multi-GPU (torchrun): replicas only -- each rank partitions its own batch
+(different graph seeds); no data-path collective.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import graphgen as gg  # noqa: E402
+
+# Algorithmic bytes of the LP propose sweep.  Per arc: col (4) + edge weight
+# (4) + label gather (4).  Per node: sub-round list entry (4), row_ptr pair
+# (16), slot id (4), own label (4), node weight (4), proposal target (4) and
+# admission key (8) written.
+ARC_BYTES = 12
+NODE_BYTES = 44
+BUCKETS = ["lanes4", "lanes8", "lanes16", "lanes32", "warp_smem", "cta_smem", "cta_global"]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--count", type=int, default=512)
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload(count, seed):
+    procs = min(16, os.cpu_count() or 1)
+    return gg.batch_workload(count, seed, processes=procs)
+
+
+def config_dict(count, ws):
+    return {
+        "workload": f"batched-{count}: half R-MAT scale U[10,16] ef 8 (0.57,0.19,0.19,0.05), "
+                    "half 2D RGG n logU[1k,64k] r=0.55*sqrt(ln n/n); k U{2,4,8,16}; eps 0.03; "
+                    "unit int32 weights; seed 0",
+        "graphs_per_rank": count,
+        "ranks": ws,
+        "l2": "inputs ~1 GB per batch, larger than L2 (no flush)",
+        "params": "l=10 LP rounds coarse/refine, f=18, coarsen to max(1000,60k), 16 IP trials, "
+                  "8 colour classes",
+    }
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for r in rows for j in range(4) if r[5 + j] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def traffic_for(kernel_src):
+    """dram bytes per propose launch from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        d = json.load(open(path))
+    except ValueError:
+        return None
+    h = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+    if d.get("lp_cu_sha256_16") != h:
+        return None
+    return d.get("bytes_per_arc"), d.get("note")
+
+
+def oracle_rate(graphs, seconds, steps=None):
+    """Round-synchronous oracle on the host: partitions graphs in order until
+    `seconds` of CPU work (at least one graph).  Returns (partitions/s, n)."""
+    import oracle as O
+    t0 = time.perf_counter()
+    done = 0
+    for g, k, eps in graphs:
+        O.partition(g, k, eps, seed=0, variant=O.SYNC)
+        done += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    return done / (time.perf_counter() - t0), done
+
+
+def reference_arm(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    graphs = workload(args.count, 0)
+    import oracle as O
+    O.build()
+    # one step = the first 16 graphs of the batch (a bounded sample)
+    sample = graphs[:16]
+    for _ in range(args.warmup):
+        for g, k, eps in sample[:2]:
+            O.partition(g, k, eps, seed=0)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for g, k, eps in sample:
+            O.partition(g, k, eps, seed=0)
+    dt = time.perf_counter() - t0
+    value = args.steps * len(sample) / dt
+    line = {
+        "impl": "reference", "metric": "partitions/s", "value": value, "unit": "partitions/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": config_dict(args.count, 1),
+        "cpu_baseline": {"value": value, "unit": "partitions/s", "cores": 1, "kind": "oracle",
+                         "sample": f"first {len(sample)} graphs of the batch per step, "
+                                   "round-synchronous oracle, single thread"},
+        "e2e": {"value": value, "unit": "partitions/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+    ws, rank, local = dist_env()
+    graphs = workload(args.count, rank)          # each rank its own batch
+
+    import torch
+    import paper_1402_3281_gb300 as P
+    P.load()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    items = [dict(row_ptr=t(g.row_ptr), col=t(g.col), k=k, eps=eps, seed=0)
+             for g, k, eps in graphs]
+    arcs_in = sum(g.arcs for g, _, _ in graphs)
+    torch.cuda.synchronize()
+
+    ref = None
+    for _ in range(args.warmup):
+        ref = P.sclap_partition_batch(items, device=True)
+    torch.cuda.synchronize()
+    ref_cuts = [r.cut for r in ref]
+
+    sampler = ClockSampler(local)
+    P.sclap_profile_reset()
+    P.sclap_profile_enable(True)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    e0.record(stream)
+    last = None
+    for _ in range(args.steps):
+        last = P.sclap_partition_batch(items, device=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    P.sclap_profile_enable(False)
+    prof = P.sclap_profile_read()
+    elapsed_ms = e0.elapsed_time(e1)
+    if ws > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([elapsed_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(tt.item())
+    deterministic = [r.cut for r in last] == ref_cuts
+    balanced = all(r.status == 0 for r in last)
+
+    parts = args.steps * len(graphs) * ws
+    value = parts / (elapsed_ms / 1000.0)
+    swept = sum(prof["propose_arcs"])
+    prop_ms = sum(prof["propose_ms"])
+    prop_bytes = ARC_BYTES * swept + NODE_BYTES * sum(prof["propose_nodes"])
+    peaks = {}
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        peaks = json.load(open(pk))
+    peak = peaks.get("hbm_gbs", 6800.0)
+    achieved = prop_bytes / (prop_ms / 1000.0) / 1e9 if prop_ms > 0 else 0.0
+    tr = traffic_for(os.path.join(ROOT, "paper_1402_3281_gb300", "csrc", "lp.cu"))
+    nl = sum(prof["propose_launches"])
+    roofline = {
+        "kernel": "LP propose sweep (k_propose_*, all degree buckets)",
+        "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+        "frac": achieved / peak, "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+        "traffic": (tr[0] * swept / nl if tr and tr[0] else None) if nl else None,
+        "bytes_per_launch": prop_bytes / nl if nl else None,
+        "avg_launch_ms": prop_ms / nl if nl else None,
+        "launches": nl,
+        "share_of_step": prop_ms / elapsed_ms if elapsed_ms else None,
+        "per_bucket": {BUCKETS[b]: {"ms": prof["propose_ms"][b], "launches": prof["propose_launches"][b],
+                                    "nodes": prof["propose_nodes"][b], "arcs": prof["propose_arcs"][b]}
+                       for b in range(7)},
+    }
+
+    line = {
+        "metric": "partitions/s", "value": value, "unit": "partitions/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic", "config": config_dict(len(graphs), ws),
+        "sclap_edges_per_s": swept / (elapsed_ms / 1000.0) * (ws if ws > 1 else 1),
+        "input_edges_per_s": arcs_in / 2 * args.steps * ws / (elapsed_ms / 1000.0),
+        "deterministic": deterministic, "balanced": balanced,
+        "roofline": roofline, "clocks": clocks,
+        "gpu_launches": prof["kernel_launches"],
+    }
+
+    if rank == 0 and not args.no_plain:
+        # the same graphs, one call each (the plain form), and equal cuts
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        plain = [P.sclap_partition_device(it["row_ptr"], it["col"], k=it["k"], eps=it["eps"],
+                                          seed=0) for it in items]
+        torch.cuda.synchronize()
+        pt = time.perf_counter() - t0
+        line["plain_partitions_per_s"] = len(items) / pt
+        line["batched_vs_plain"] = value / ws / (len(items) / pt)
+        line["equal_cut"] = [p.cut for p in plain] == ref_cuts
+
+    if not args.no_e2e:
+        host_items = [dict(row_ptr=g.row_ptr, col=g.col, k=k, eps=eps, seed=0)
+                      for g, k, eps in graphs]
+        h2d = sum(g.row_ptr.nbytes + g.col.nbytes for g, _, _ in graphs)
+        d2h = sum(4 * g.n for g, _, _ in graphs)
+        barrier()
+        t0 = time.perf_counter()
+        e2e_steps = max(1, min(2, args.steps))
+        for _ in range(e2e_steps):
+            hres = P.sclap_partition_batch(host_items, device=False)
+        torch.cuda.synchronize()
+        et = time.perf_counter() - t0
+        if ws > 1:
+            import torch.distributed as dist
+            tt = torch.tensor([et], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            et = float(tt.item())
+        line["e2e"] = {"value": e2e_steps * len(graphs) * ws / et, "unit": "partitions/s",
+                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                       "equal_cut": [r.cut for r in hres] == ref_cuts}
+
+    if rank == 0 and ws == 1:
+        rate, done = oracle_rate(graphs, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": rate, "unit": "partitions/s", "cores": 1,
+                                "kind": "oracle",
+                                "sample": f"first {done} graphs of the batch in order "
+                                          f"(~{args.cpu_seconds:.0f} s), round-synchronous "
+                                          "oracle, single thread"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

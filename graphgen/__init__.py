@@ -217,23 +217,36 @@ def random_weights(g: Graph, seed: int, max_node_w: int = 4, max_edge_w: int = 8
                  name=g.name + f"-w{seed}", meta=dict(g.meta))
 
 
-def batch_workload(count: int = 512, seed: int = 0):
-    """The batched workload: ``count`` independent graphs of uneven size,
-    half R-MAT (scale uniform in 10..16, edge factor 8, a,b,c,d =
-    0.57,0.19,0.19,0.05) and half 2D RGG (n log-uniform in 1k..64k), each
-    with k drawn uniformly from {2,4,8,16} and eps=0.03.
+def batch_params(i: int, count: int = 512, seed: int = 0):
+    """Parameters of graph ``i`` of the batched workload: even i -> R-MAT with
+    scale uniform in 10..16 (edge factor 8), odd i -> 2D RGG with n
+    log-uniform in 1k..64k; k uniform in {2,4,8,16}; eps = 0.03."""
+    rng = np.random.default_rng(np.random.SeedSequence([0x42415443, count, seed, i]))
+    k = int(rng.choice([2, 4, 8, 16]))
+    if i % 2 == 0:
+        return dict(kind="rmat", scale=int(rng.integers(10, 17)), k=k, eps=0.03,
+                    gseed=1000 * seed + i)
+    n = int(round(math.exp(rng.uniform(math.log(1000), math.log(65536)))))
+    return dict(kind="rgg", n=n, k=k, eps=0.03, gseed=1000 * seed + i)
 
-    Returns a list of (Graph, k, eps).
-    """
-    rng = np.random.default_rng(np.random.SeedSequence([0x42415443, count, seed]))
-    out = []
-    for i in range(count):
-        k = int(rng.choice([2, 4, 8, 16]))
-        if i % 2 == 0:
-            scale = int(rng.integers(10, 17))
-            g = rmat(scale, 8, seed=1000 * seed + i)
-        else:
-            n = int(round(math.exp(rng.uniform(math.log(1000), math.log(65536)))))
-            g = rgg2d(n, seed=1000 * seed + i)
-        out.append((g, k, 0.03))
-    return out
+
+def batch_graph(i: int, count: int = 512, seed: int = 0):
+    """Graph ``i`` of the batched workload as (Graph, k, eps)."""
+    p = batch_params(i, count, seed)
+    if p["kind"] == "rmat":
+        g = rmat(p["scale"], 8, seed=p["gseed"])
+    else:
+        g = rgg2d(p["n"], seed=p["gseed"])
+    return g, p["k"], p["eps"]
+
+
+def batch_workload(count: int = 512, seed: int = 0, processes: int = 0):
+    """The batched workload: ``count`` independent graphs of uneven size
+    (see batch_params).  Returns a list of (Graph, k, eps).  With
+    processes > 1 the graphs are generated by a spawn-started process pool
+    (results do not depend on it)."""
+    if processes and processes > 1:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(processes) as pool:
+            return pool.starmap(batch_graph, [(i, count, seed) for i in range(count)])
+    return [batch_graph(i, count, seed) for i in range(count)]

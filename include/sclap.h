@@ -1,0 +1,214 @@
+/*
+ * sclap.h -- C ABI of the GB300 (sm_103a) multilevel size-constrained label
+ * propagation (SCLaP) graph partitioner.
+ *
+ * Method: Meyerhenke, Sanders, Schulz, "Partitioning Complex Networks via
+ * Size-constrained Clustering".  The problem (Sec. 2.1): given an undirected
+ * graph G = (V, E, c, w) with node weights c and edge weights w, find blocks
+ * V_0..V_{k-1} partitioning V with c(V_i) <= Lmax for every i that minimise
+ * the cut sum_{i<j} w(E_ij).  Here Lmax = floor((1+eps) * ceil(c(V)/k)), the
+ * paper's unweighted form of the balance constraint applied to c(V).
+ * The multilevel scheme (Sec. 1 Fig. 1, Sec. 3) coarsens by size-constrained
+ * LP clustering (cluster bound U = max(max_v c(v), floor(Lmax/f)), Sec. 3.1)
+ * and cluster contraction, partitions the coarsest graph, then projects and
+ * refines each level with LP local search under Lmax (Sec. 3.1) using active
+ * nodes (Sec. 4).  Every step runs in CUDA kernels on the current device.
+ *
+ * Determinism: the result is a pure function of (graph, k, eps, seed, cfg).
+ * It equals the round-synchronous variant of the CPU oracle bit for bit and
+ * does not depend on which other graphs share a batch.
+ *
+ * Graph format (all entry points):
+ *   n        number of nodes, 1 <= n < 2^31
+ *   row_ptr  int64[n+1], row_ptr[0] = 0, non-decreasing; m = row_ptr[n] arcs
+ *   col      int32[m], neighbour ids in [0, n); the graph must be symmetric
+ *            (every arc (u,v) has its twin (v,u) with the same weight) and
+ *            contain no self-loops.  Row order is free.
+ *   node_w   int32[n], positive, sum < 2^31; NULL means unit weights
+ *   edge_w   int32[m], positive; NULL means unit weights
+ * Symmetry is the caller's contract and is not checked; everything else is,
+ * before any kernel reads the graph.
+ *
+ * Ownership: the caller owns every buffer passed in; the library copies what
+ * it needs and keeps no pointer after a call returns.  Working memory comes
+ * from the CUDA stream-ordered allocator of the current device.
+ *
+ * Errors: every function returns SCLAP_OK (0) or a negative SCLAP_E* code;
+ * sclap_error_string() describes it.  No exception crosses the ABI.  Device
+ * waits are bounded; a bounded wait that runs out reports SCLAP_ETIMEOUT.
+ */
+#ifndef SCLAP_H
+#define SCLAP_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  SCLAP_OK = 0,
+  SCLAP_EINVAL = -1,      /* bad argument (k < 1, k > n, eps < 0, NULL pointer, ...) */
+  SCLAP_ECSR = -2,        /* malformed CSR: row_ptr, col range, self-loop, weights   */
+  SCLAP_ENOMEM = -3,      /* device allocation failed                                */
+  SCLAP_ECUDA = -4,       /* a CUDA call failed                                      */
+  SCLAP_EOVERFLOW = -5,   /* a coarse edge weight or c(V) does not fit in int32      */
+  SCLAP_EINFEASIBLE = -6, /* blocks stay above Lmax after repair (outputs written)   */
+  SCLAP_ETIMEOUT = -7,    /* a bounded device-side wait ran out                      */
+  SCLAP_EINTERNAL = -8    /* internal consistency check failed                       */
+};
+
+/* Tunables.  Defaults (sclap_default_config): the paper's parameters (Sec. 5):
+ * l = 10 LP rounds per level in coarsening and uncoarsening, f = 18; plus
+ * coarsening down to max(1000, 60k) nodes, 16 initial-partitioning trials,
+ * 8 colour classes per synchronous round, 64 repair rounds, 64 levels. */
+typedef struct sclap_config {
+  int32_t lp_rounds_coarse;
+  int32_t lp_rounds_refine;
+  int32_t f;
+  int32_t coarse_min_nodes;
+  int32_t ip_trials;
+  int32_t sub_rounds;
+  int32_t repair_rounds;
+  int32_t max_levels;
+} sclap_config;
+
+/* Per-call statistics (optional output). */
+typedef struct sclap_stats {
+  int32_t levels;              /* graphs in the hierarchy, input included   */
+  int64_t level_n[64];
+  int64_t level_m[64];         /* arcs per level                            */
+  int32_t cluster_rounds[64];  /* LP rounds run clustering level l          */
+  int32_t refine_rounds[64];   /* LP rounds run refining level l            */
+  int32_t ip_best_trial;
+  int64_t ip_cut;
+  int64_t Lmax, U;
+  int64_t lp_arcs;             /* arcs scanned by LP sweeps (all levels)    */
+} sclap_stats;
+
+void sclap_default_config(sclap_config* cfg);
+const char* sclap_error_string(int code);
+/* Message of the last error raised on the calling thread ("" after success). */
+const char* sclap_last_error(void);
+
+/* Partition one graph held in HOST memory (Sec. 2.1 problem statement).
+ * block_out: caller-owned int32[n], receives block ids in [0, k).
+ * cut_out: receives the edge cut.  max_block_weight_out, stats: nullable.
+ * cfg: nullable (defaults).  Synchronous: returns when results are written.
+ * Returns SCLAP_EINFEASIBLE (with outputs written) if balance could not be
+ * reached, which needs node weights above the eps slack. */
+int sclap_partition(int64_t n, const int64_t* row_ptr, const int32_t* col,
+                    const int32_t* node_w, const int32_t* edge_w, int32_t k, double eps,
+                    uint64_t seed, const sclap_config* cfg, int32_t* block_out,
+                    int64_t* cut_out, int64_t* max_block_weight_out, sclap_stats* stats);
+
+/* Same, with every array in DEVICE memory (block_out too) and the work
+ * ordered on `stream` (a cudaStream_t; NULL = legacy default stream).  The
+ * call synchronises the stream before returning (level sizes are read back
+ * between levels). */
+int sclap_partition_device(int64_t n, const int64_t* row_ptr, const int32_t* col,
+                           const int32_t* node_w, const int32_t* edge_w, int32_t k,
+                           double eps, uint64_t seed, const sclap_config* cfg,
+                           int32_t* block_out, int64_t* cut_out,
+                           int64_t* max_block_weight_out, sclap_stats* stats, void* stream);
+
+/* One graph of a batch.  Inputs as above; block_out caller-owned int32[n];
+ * cut, max_block_weight and status are written by the call. */
+typedef struct sclap_graph {
+  int64_t n;
+  const int64_t* row_ptr;
+  const int32_t* col;
+  const int32_t* node_w;
+  const int32_t* edge_w;
+  int32_t k;
+  double eps;
+  uint64_t seed;
+  int32_t* block_out;
+  int64_t cut;
+  int64_t max_block_weight;
+  int32_t status;
+} sclap_graph;
+
+/* Partition `count` independent graphs together: every kernel launch covers
+ * all graphs still active at that level, so small graphs share the GPU.
+ * Each graph's result equals what sclap_partition returns for it alone.
+ * device_ptrs = 0: arrays are in host memory; 1: in device memory.
+ * Returns SCLAP_OK if every graph succeeded, else the first graph error
+ * (per-graph codes in graphs[i].status). */
+int sclap_partition_batch(int32_t count, sclap_graph* graphs, const sclap_config* cfg,
+                          int32_t device_ptrs, void* stream);
+
+/* ---- Step-level entry points (device pointers, stream-ordered, synchronous
+ * on return).  They run exactly the kernels the partitioner uses, on one
+ * graph, so each step can be checked on its own. ---- */
+
+/* One synchronous LP round (Sec. 3.1) over all colour classes.
+ * mode 0 = clustering (labels are node ids, W has n entries),
+ * mode 1 = local search (labels are blocks 0..nlabels-1, W has nlabels).
+ * label (int32[n]) and W (int64[nlabels]) are updated in place.
+ * active_cur: uint8[n] or NULL (all active); active_next: uint8[n] or NULL,
+ * receives 1 for each neighbour of a moved node.  moved_out: host int64. */
+int sclap_lp_round(int32_t mode, int64_t n, const int64_t* row_ptr, const int32_t* col,
+                   const int32_t* node_w, const int32_t* edge_w, int32_t* label, int64_t* W,
+                   int64_t nlabels, int64_t bound, uint64_t rkey, int32_t sub_rounds,
+                   const uint8_t* active_cur, uint8_t* active_next, int64_t* moved_out,
+                   void* stream);
+
+/* Size-constrained clustering of one level (Sec. 3.1): label_out int32[n]
+ * (node id of each cluster's original representative); rounds_out: host. */
+int sclap_cluster(int64_t n, const int64_t* row_ptr, const int32_t* col, const int32_t* node_w,
+                  const int32_t* edge_w, int64_t U, uint64_t seed, int32_t level,
+                  const sclap_config* cfg, int32_t* label_out, int32_t* rounds_out,
+                  void* stream);
+
+/* Cluster contraction (Sec. 3.1).  Coarse id = rank of the cluster label.
+ * Outputs sized by the fine graph: cmap int32[n], cnode_w int32[n],
+ * crow_ptr int64[n+1], ccol int32[m], cedge_w int32[m]; nc_out, mc_out on
+ * the host.  Coarse rows are in no particular order. */
+int sclap_contract(int64_t n, const int64_t* row_ptr, const int32_t* col,
+                   const int32_t* node_w, const int32_t* edge_w, const int32_t* label,
+                   int32_t* cmap, int64_t* nc_out, int32_t* cnode_w, int64_t* crow_ptr,
+                   int32_t* ccol, int32_t* cedge_w, int64_t* mc_out, void* stream);
+
+/* Initial partitioning of a (coarsest) graph: cfg->ip_trials trials of
+ * greedy growing plus LP local search, best by (overload, cut, trial).
+ * block_out int32[n]; cut_out, best_trial_out on the host. */
+int sclap_initial_partition(int64_t n, const int64_t* row_ptr, const int32_t* col,
+                            const int32_t* node_w, const int32_t* edge_w, int32_t k,
+                            int64_t Lmax, int64_t avg, uint64_t seed, int32_t level,
+                            const sclap_config* cfg, int32_t* block_out, int64_t* cut_out,
+                            int32_t* best_trial_out, void* stream);
+
+/* LP local search on one level (Sec. 3.1 last paragraph; active nodes,
+ * Sec. 4).  block int32[n] in/out; phase selects the hash domain
+ * (2 = refinement, 5 = initial-partitioning refinement). */
+int sclap_refine(int64_t n, const int64_t* row_ptr, const int32_t* col, const int32_t* node_w,
+                 const int32_t* edge_w, int32_t k, int64_t Lmax, uint64_t seed, int32_t phase,
+                 int32_t level, const sclap_config* cfg, int32_t* block, int32_t* rounds_out,
+                 void* stream);
+
+/* Edge cut sum_{i<j} w(E_ij) (Sec. 2.1) of block (int32[n]); cut_out host. */
+int sclap_cut(int64_t n, const int64_t* row_ptr, const int32_t* col, const int32_t* edge_w,
+              const int32_t* block, int64_t* cut_out, void* stream);
+
+/* ---- Instrumentation (no counterpart in the paper).  Process-wide
+ * counters read by the benchmark: every kernel launch is counted; with
+ * profiling enabled, each launch of the LP propose sweep is bracketed by CUDA
+ * events on its stream and its nodes/arcs are tallied per degree bucket
+ * (0..3: 4/8/16/32 lanes per node, 4: warp + shared table, 5: CTA + shared
+ * table, 6: CTA + global table).  Times are device milliseconds. ---- */
+typedef struct sclap_profile {
+  int64_t kernel_launches;
+  int64_t propose_launches[7];
+  double propose_ms[7];
+  int64_t propose_nodes[7];
+  int64_t propose_arcs[7];
+} sclap_profile;
+void sclap_profile_enable(int on);
+void sclap_profile_reset(void);
+void sclap_profile_read(sclap_profile* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,378 @@
+// common.cuh -- shared definitions of the sm_103a SCLaP library: the
+// counter-based hash, the segmented ("batched") level description, launch
+// helpers and small warp/block primitives.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <cstdio>
+#include <mutex>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/sclap.h"
+
+namespace sclap {
+
+// ---------------------------------------------------------------------------
+// Errors.  Host code throws sclap::Error; the C ABI converts it to a code.
+// ---------------------------------------------------------------------------
+struct Error : std::runtime_error {
+  int code;
+  Error(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+#define SCLAP_CUDA(call)                                                                   \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      throw ::sclap::Error(e_ == cudaErrorMemoryAllocation ? SCLAP_ENOMEM : SCLAP_ECUDA,   \
+                           std::string(#call) + ": " + cudaGetErrorString(e_));            \
+  } while (0)
+
+#define SCLAP_LAUNCH_CHECK() SCLAP_CUDA(cudaGetLastError())
+
+// Process-wide instrumentation (see sclap_profile in sclap.h).
+struct ProfileState {
+  std::atomic<int64_t> launches{0};
+  std::atomic<bool> enabled{false};
+  std::mutex mu;
+  double ms[7] = {};
+  int64_t nlaunch[7] = {}, nodes[7] = {}, arcs[7] = {};
+};
+ProfileState& profile();
+#define SCLAP_NOTE_LAUNCH() \
+  ::sclap::profile().launches.fetch_add(1, std::memory_order_relaxed)
+
+// Device error word bits (set by kernels, read by the host after a phase).
+enum : int32_t {
+  DERR_HASH_FULL = 1,     // open-addressing table ran out of slots
+  DERR_W_OVERFLOW = 2,    // coarse edge weight above INT32_MAX
+  DERR_BAD_CSR = 4,       // validation
+  DERR_INTERNAL = 8,
+};
+
+// ---------------------------------------------------------------------------
+// SplitMix64 output function (Steele, Lea, Flood, OOPSLA 2014) and the keyed
+// chain used for every random choice.  All hashes take graph-local ids so a
+// graph's result does not depend on its position in a batch.
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+__host__ __device__ __forceinline__ uint64_t hkey(uint64_t seed, uint64_t phase, uint64_t level,
+                                                  uint64_t round) {
+  return mix64(mix64(mix64(mix64(seed) ^ phase) ^ level) ^ round);
+}
+
+enum Phase : int32_t {
+  PH_CLUSTER = 1, PH_REFINE = 2, PH_TRIAL = 3, PH_GGG = 4, PH_IPREF = 5, PH_REPAIR = 6
+};
+enum Mode : int32_t { MODE_CLUSTER = 0, MODE_REFINE = 1, MODE_REPAIR = 2 };
+
+// Degree buckets of the LP sweep.  0..3: a group of 4/8/16/32 lanes per node,
+// labels aggregated with warp match; 4: one warp per node with a shared-memory
+// hash; 5: one CTA per node, shared-memory hash; 6: one CTA per node, hash in
+// global scratch.
+constexpr int NB = 7;
+constexpr int WARP_HASH_MAXDEG = 512;      // table 1024 slots per warp
+constexpr int WARP_HASH_SLOTS = 1024;
+constexpr int CTA_HASH_MAXDEG = 4096;      // table 8192 slots per CTA
+constexpr int CTA_HASH_SLOTS = 8192;
+
+__host__ __device__ __forceinline__ int bucket_of(int64_t deg, bool overloaded) {
+  if (!overloaded) {
+    if (deg <= 4) return 0;
+    if (deg <= 8) return 1;
+    if (deg <= 16) return 2;
+    if (deg <= 32) return 3;
+  }
+  if (deg <= WARP_HASH_MAXDEG) return 4;
+  if (deg <= CTA_HASH_MAXDEG) return 5;
+  return 6;
+}
+
+// ---------------------------------------------------------------------------
+// A level: one CSR holding the graphs of all slots back to back (node ids are
+// global, node range of slot s = [noff[s], noff[s+1])).
+// ---------------------------------------------------------------------------
+struct LevelView {
+  int64_t N = 0, M = 0;
+  const int64_t* row_ptr = nullptr;
+  const int32_t* col = nullptr;
+  const int32_t* ew = nullptr;
+  const int32_t* nw = nullptr;
+  const int32_t* gid = nullptr;   // slot of each node
+};
+
+// Per-slot parameters of an LP run (device arrays of `nslots` entries).
+struct SlotParams {
+  int32_t nslots = 0;
+  const int64_t* noff = nullptr;    // [nslots+1]
+  const int64_t* loff = nullptr;    // label offset: local label = label - loff
+  const int64_t* bound = nullptr;   // U (clustering) or Lmax (local search)
+  const uint64_t* seed = nullptr;   // seed key fed to hkey
+  const int32_t* level = nullptr;   // level id fed to hkey
+  const int32_t* nlab = nullptr;    // labels of the slot (k in local search)
+  int32_t* done = nullptr;          // 1: slot takes no part in further rounds
+  int64_t* moved = nullptr;         // moves of the current round
+  uint64_t* rkey = nullptr;         // key of the current round
+  int32_t* rounds = nullptr;        // rounds run
+};
+
+// ---------------------------------------------------------------------------
+// Small helpers.
+// ---------------------------------------------------------------------------
+inline int num_sms() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  return sms;
+}
+
+inline unsigned grid_for(int64_t items, int per_block, int64_t cap) {
+  int64_t g = (items + per_block - 1) / per_block;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return (unsigned)g;
+}
+
+__device__ __forceinline__ unsigned long long* ull(int64_t* p) {
+  return reinterpret_cast<unsigned long long*>(p);
+}
+
+// Candidate order of the move rule: stronger connection first, then smaller
+// tie hash, then smaller local label.  conn < 0 marks "no candidate".
+struct Cand {
+  int64_t conn;
+  uint64_t h;
+  int32_t C;  // local label
+};
+__device__ __forceinline__ bool cand_better(const Cand& a, const Cand& b) {
+  if (a.conn != b.conn) return a.conn > b.conn;
+  if (a.h != b.h) return a.h < b.h;
+  return a.C < b.C;
+}
+__device__ __forceinline__ Cand shfl_xor_cand(const Cand& c, int off, int width = 32) {
+  Cand o;
+  o.conn = __shfl_xor_sync(0xffffffffu, (long long)c.conn, off, width);
+  o.h = __shfl_xor_sync(0xffffffffu, (unsigned long long)c.h, off, width);
+  o.C = __shfl_xor_sync(0xffffffffu, c.C, off, width);
+  return o;
+}
+__device__ __forceinline__ Cand warp_best(Cand c, int width = 32) {
+  for (int off = width / 2; off > 0; off >>= 1) {
+    Cand o = shfl_xor_cand(c, off, width);
+    if (cand_better(o, c)) c = o;
+  }
+  return c;
+}
+__device__ __forceinline__ long long warp_max_ll(long long x, int width = 32) {
+  for (int off = width / 2; off > 0; off >>= 1) {
+    long long o = __shfl_xor_sync(0xffffffffu, x, off, width);
+    x = o > x ? o : x;
+  }
+  return x;
+}
+__device__ __forceinline__ long long warp_sum_ll(long long x) {
+  for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+  return x;
+}
+
+// Sum of positive int32 values over the lanes of `mask` as a 64-bit number,
+// from two 32-bit warp reductions of the 16-bit halves.
+__device__ __forceinline__ int64_t match_sum(unsigned mask, int32_t w) {
+  unsigned lo = __reduce_add_sync(mask, (unsigned)w & 0xffffu);
+  unsigned hi = __reduce_add_sync(mask, (unsigned)w >> 16);
+  return ((int64_t)hi << 16) + (int64_t)lo;
+}
+
+// Admission key: smaller key = admitted first.  High half: larger gain first
+// (gain clamped to int32); low half: smaller priority hash first.
+__device__ __forceinline__ uint64_t admission_key(int64_t gain, uint32_t prio) {
+  int64_t g = gain > INT32_MAX ? INT32_MAX : (gain < INT32_MIN ? INT32_MIN : gain);
+  uint32_t hi = (uint32_t)((int64_t)INT32_MAX - g);
+  return ((uint64_t)hi << 32) | prio;
+}
+
+__host__ __device__ __forceinline__ int64_t max64(int64_t a, int64_t b) { return a > b ? a : b; }
+__host__ __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
+
+__host__ __device__ __forceinline__ int ceil_log2(int64_t x) {
+  int l = 0;
+  while (((int64_t)1 << l) < x) ++l;
+  return l;
+}
+
+// Open-addressing table slot for key C (multiplicative hashing).
+__device__ __forceinline__ uint32_t table_slot(int32_t C, int logcap) {
+  return logcap == 0 ? 0u : (((uint32_t)C * 0x9E3779B1u) >> (32 - logcap));
+}
+
+// ---------------------------------------------------------------------------
+// Device buffers from the stream-ordered allocator.
+// ---------------------------------------------------------------------------
+template <class T>
+struct DevBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  cudaStream_t s = nullptr;
+  DevBuf() = default;
+  DevBuf(size_t count, cudaStream_t st) { alloc(count, st); }
+  void alloc(size_t count, cudaStream_t st) {
+    release();
+    s = st;
+    n = count;
+    if (count) SCLAP_CUDA(cudaMallocAsync((void**)&p, count * sizeof(T), st));
+  }
+  void release() {
+    if (p) cudaFreeAsync(p, s);
+    p = nullptr;
+    n = 0;
+  }
+  void zero() {
+    if (n) SCLAP_CUDA(cudaMemsetAsync(p, 0, n * sizeof(T), s));
+  }
+  void fill_bytes(int v) {
+    if (n) SCLAP_CUDA(cudaMemsetAsync(p, v, n * sizeof(T), s));
+  }
+  void upload(const T* h, size_t count) {
+    if (count) SCLAP_CUDA(cudaMemcpyAsync(p, h, count * sizeof(T), cudaMemcpyHostToDevice, s));
+  }
+  void upload(const std::vector<T>& v) { upload(v.data(), v.size()); }
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  DevBuf(DevBuf&& o) noexcept { *this = std::move(o); }
+  DevBuf& operator=(DevBuf&& o) noexcept {
+    if (this != &o) {
+      release();
+      p = o.p; n = o.n; s = o.s;
+      o.p = nullptr; o.n = 0;
+    }
+    return *this;
+  }
+  ~DevBuf() { release(); }
+};
+
+// ---------------------------------------------------------------------------
+// Entry points of the kernel files (host side).
+// ---------------------------------------------------------------------------
+// scan.cu: out[0..n] = exclusive prefix sums of in[0..n) (out[n] = total).
+void scan_excl_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, cudaStream_t s);
+void scan_excl_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t s);
+void scan_excl_u8_to_i64(const uint8_t* in, int64_t* out, int64_t n, cudaStream_t s);
+// largest row length (atomicMax into *out, which the caller zeroes)
+void level_max_degree(const int64_t* row_ptr, int64_t N, int64_t* out, cudaStream_t s);
+// slot id of every node from node offsets
+void fill_gid(const int64_t* noff, int32_t nslots, int32_t* gid, int64_t N, cudaStream_t s);
+
+// lp.cu
+struct LPBuffers;
+struct LPRun {
+  int mode = MODE_CLUSTER;
+  int phase = PH_CLUSTER;
+  int rounds = 10;
+  int sub_rounds = 8;
+  bool stop_rule = true;       // 5% rule (not in repair)
+  bool use_active = false;     // local search: active nodes
+  bool raw_key = false;        // slot seed is used as the round key itself
+};
+// Runs `run.rounds` synchronous LP rounds on `lv` for every slot not marked
+// done; label/W are updated in place.  Returns the number of arcs scanned.
+int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, int64_t* W,
+               int64_t Wsize, const LPRun& run, int32_t* d_err, cudaStream_t s,
+               const uint8_t* active_init = nullptr, uint8_t* active_next_out = nullptr);
+void lp_round_begin_host_keys(const SlotParams& sp, int phase, int r, int mode,
+                              const int64_t* W, cudaStream_t s);
+
+// contract.cu -- cluster contraction (Sec. 3.1) of every slot of a level.
+struct ContractWork {
+  DevBuf<int32_t> flag;        // [N] label used
+  DevBuf<int64_t> cid;         // [N+1] exclusive scan of flag: rank of a label
+  std::vector<int64_t> cid_at; // cid at each slot's first node [nslots+1]
+};
+struct CoarseLevel {
+  int64_t N = 0, M = 0;
+  DevBuf<int64_t> row_ptr;
+  DevBuf<int32_t> col, ew, nw, gid;
+  DevBuf<int64_t> noff_d;
+  std::vector<int64_t> noff;   // [nslots+1]
+  std::vector<int64_t> aoff;   // arc offset of each slot [nslots+1]
+  LevelView view() const {
+    LevelView v;
+    v.N = N; v.M = M; v.row_ptr = row_ptr.p; v.col = col.p; v.ew = ew.p; v.nw = nw.p;
+    v.gid = gid.p;
+    return v;
+  }
+};
+// Step 1: ranks the used labels; nc_slot[s] = coarse nodes of slot s.
+void contract_rank(const LevelView& lv, const std::vector<int64_t>& noff, const int32_t* label,
+                   ContractWork& w, std::vector<int64_t>& nc_slot, cudaStream_t s);
+// Step 2: builds the coarse graph of the slots with keep[s] != 0 (the other
+// slots get no coarse nodes and cmap = -1).  cmap: [N] fine -> coarse id.
+void contract_build(const LevelView& lv, const std::vector<int64_t>& noff, const int32_t* label,
+                    const ContractWork& w, const std::vector<uint8_t>& keep, int32_t* cmap,
+                    CoarseLevel& out, int32_t* d_err, cudaStream_t s);
+
+// ip.cu -- initial partitioning of the coarsest graphs (all trials of all
+// graphs in one batch), cut, projection.
+struct CopyTask {              // copy one graph segment (NULL weights -> unit)
+  const int64_t* row_ptr;
+  const int32_t* col;
+  const int32_t* ew;
+  const int32_t* nw;
+  int64_t src_n0, src_a0, n, m, dst_n0, dst_a0;
+};
+void ip_replicate(const std::vector<CopyTask>& tasks, int64_t* row_ptr, int32_t* col,
+                  int32_t* ew, int32_t* nw, int64_t M_total, cudaStream_t s);
+struct GGGArgs {
+  const int64_t* row_ptr;
+  const int32_t* col;
+  const int32_t* ew;
+  const int32_t* nw;
+  const int64_t* noff;     // trial slot node offsets
+  const int64_t* boff;     // trial slot block offsets
+  const int32_t* nlab;     // k per trial slot
+  const int64_t* avg;      // ceil(c(V)/k) per trial slot
+  const uint64_t* tkey;    // trial key per slot
+  const int32_t* level;    // coarsest level index per slot
+  int32_t* label;          // out: global block ids
+  int64_t* W;              // out: block weights
+  int64_t* conn;           // scratch [N]
+  int32_t* step;           // scratch [N]
+  int64_t* wfA;            // scratch [sum k]
+  int32_t* wforder;        // scratch [sum k]
+  int32_t nslots;
+};
+void ggg_trials(const GGGArgs& a, cudaStream_t s);
+// cut2[slot] += twice the cut of each slot (arcs counted from both ends).
+void slot_cut(const LevelView& lv, const int32_t* label, int64_t* cut2, cudaStream_t s);
+struct SelectTask {            // choose the best trial of one graph, copy it out
+  int32_t* dst_blk;            // level array of the graph's coarsest level
+  int64_t dst_n0, n;
+  int64_t slot0;               // first trial slot of the graph
+  int32_t trials, k;
+  int64_t Lmax, g_boff;        // graph's block offset in the refinement block space
+  int32_t g;
+};
+// best[g], ipcut[g] on the device; block weights copied to Wg[g_boff..].
+void ip_select_copy(const std::vector<SelectTask>& tasks, const int64_t* cut2,
+                    const int64_t* ip_W, const int64_t* ip_noff, const int64_t* ip_boff,
+                    const int32_t* ip_label, int64_t* Wg, int32_t* best, int64_t* ipcut,
+                    cudaStream_t s);
+// fine_blk[v] = coarse_blk[cmap[v]] where cmap[v] >= 0.
+void project(const int32_t* cmap, const int32_t* coarse_blk, int32_t* fine_blk, int64_t N,
+             cudaStream_t s);
+// Block weights of every slot from scratch: W[label[v]] += nw[v].
+void block_weights(const int32_t* label, const int32_t* nw, int64_t N, int64_t* W, cudaStream_t s);
+
+}  // namespace sclap

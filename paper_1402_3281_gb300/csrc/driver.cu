@@ -1,0 +1,1039 @@
+// driver.cu -- the multilevel scheme (Sec. 1 Fig. 1, Sec. 3) over a batch of
+// graphs, and the C ABI declared in include/sclap.h.
+//
+// All graphs of a call live in one segmented level (slot g = graph g), so
+// every kernel launch of a level covers every graph still at that level.
+// Coarsening: SCLaP clustering (bound U) + contraction while a graph has more
+// than max(coarse_min_nodes, 60k) nodes and a contraction removes >= 5% of
+// them.  Initial partitioning: all trials of all graphs in one batch.
+// Uncoarsening: projection + LP local search (bound Lmax, active nodes) level
+// by level; a final repair pass on the input level if a block is still
+// above Lmax.  The host only reads level sizes back between levels.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+
+#include "common.cuh"
+
+namespace sclap {
+namespace {
+
+thread_local std::string g_last_error;
+
+void init_pool() {
+  static bool done = false;
+  if (done) return;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  done = true;
+}
+
+sclap_config resolve_cfg(const sclap_config* c) {
+  sclap_config r;
+  sclap_default_config(&r);
+  if (c) r = *c;
+  if (r.lp_rounds_coarse < 0 || r.lp_rounds_refine < 0 || r.f < 1 || r.coarse_min_nodes < 1 ||
+      r.ip_trials < 1 || r.sub_rounds < 1 || r.sub_rounds > 64 || r.repair_rounds < 0 ||
+      r.max_levels < 1)
+    throw Error(SCLAP_EINVAL, "invalid sclap_config");
+  return r;
+}
+
+// ------------------------------------------------------------- validation
+__global__ void k_validate(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                           const int32_t* __restrict__ nw, const int32_t* __restrict__ ew,
+                           int64_t n, int64_t m, int32_t* err, unsigned long long* cV,
+                           int32_t* maxc) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t0 == 0 && (row_ptr[0] != 0 || row_ptr[n] != m)) atomicOr(err, DERR_BAD_CSR);
+  unsigned long long wsum = 0;
+  int32_t wmax = 0;
+  for (int64_t v = t0; v < n; v += stride) {
+    const int64_t rs = row_ptr[v], re = row_ptr[v + 1];
+    if (rs < 0 || rs > re || re > m) { atomicOr(err, DERR_BAD_CSR); continue; }
+    const int32_t w = nw ? nw[v] : 1;
+    if (w <= 0) atomicOr(err, DERR_BAD_CSR);
+    wsum += (unsigned long long)(w > 0 ? w : 0);
+    wmax = max(wmax, w);
+    for (int64_t e = rs; e < re; ++e) {
+      const int32_t c = col[e];
+      if (c < 0 || c >= n || c == v) { atomicOr(err, DERR_BAD_CSR); break; }
+      if (ew && ew[e] <= 0) { atomicOr(err, DERR_BAD_CSR); break; }
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
+    wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(cV, wsum);
+    atomicMax(maxc, wmax);
+  }
+}
+
+__global__ void k_iota(int32_t* label, int64_t N) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N;
+       v += (int64_t)gridDim.x * blockDim.x)
+    label[v] = (int32_t)v;
+}
+
+__global__ void k_w_from_nw(const int32_t* nw, int64_t N, int64_t* W) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N;
+       v += (int64_t)gridDim.x * blockDim.x)
+    W[v] = nw[v];
+}
+
+__global__ void k_check_range(const int32_t* __restrict__ a, int64_t n, int64_t lo, int64_t hi,
+                              int32_t* err) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x)
+    if (a[v] < lo || a[v] >= hi) atomicOr(err, DERR_BAD_CSR);
+}
+
+struct OutTask {
+  int32_t* out;
+  int64_t n0, n, boff;
+};
+__global__ void k_write_out(const OutTask* __restrict__ t, const int32_t* __restrict__ blk) {
+  const OutTask o = t[blockIdx.y];
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < o.n;
+       v += (int64_t)gridDim.x * blockDim.x)
+    o.out[v] = (int32_t)(blk[o.n0 + v] - o.boff);
+}
+
+// ------------------------------------------------------------- slot arrays
+struct Slots {
+  DevBuf<int64_t> loff, bound, moved;
+  DevBuf<uint64_t> seed, rkey;
+  DevBuf<int32_t> level, nlab, done, rounds;
+  SlotParams sp;
+  Slots(cudaStream_t s, int n, const int64_t* noff_d, const std::vector<int64_t>& h_loff,
+        const std::vector<int64_t>& h_bound, const std::vector<uint64_t>& h_seed,
+        const std::vector<int32_t>& h_level, const std::vector<int32_t>& h_nlab,
+        const std::vector<int32_t>& h_done)
+      : loff(n, s), bound(n, s), moved(n, s), seed(n, s), rkey(n, s), level(n, s), nlab(n, s),
+        done(n, s), rounds(n, s) {
+    loff.upload(h_loff); bound.upload(h_bound); seed.upload(h_seed); level.upload(h_level);
+    nlab.upload(h_nlab); done.upload(h_done); rounds.zero(); moved.zero();
+    sp.nslots = n; sp.noff = noff_d; sp.loff = loff.p; sp.bound = bound.p; sp.seed = seed.p;
+    sp.level = level.p; sp.nlab = nlab.p; sp.done = done.p; sp.moved = moved.p; sp.rkey = rkey.p;
+    sp.rounds = rounds.p;
+  }
+  std::vector<int32_t> host_rounds(cudaStream_t s) {
+    std::vector<int32_t> r(sp.nslots);
+    SCLAP_CUDA(cudaMemcpyAsync(r.data(), rounds.p, r.size() * sizeof(int32_t),
+                               cudaMemcpyDeviceToHost, s));
+    SCLAP_CUDA(cudaStreamSynchronize(s));
+    return r;
+  }
+};
+
+// A batched level with owned storage.
+struct Level {
+  int64_t N = 0, M = 0;
+  DevBuf<int64_t> row_ptr, noff_d;
+  DevBuf<int32_t> col, ew, nw, gid, cmap, blk;
+  std::vector<int64_t> noff, aoff;
+  LevelView view() const {
+    LevelView v;
+    v.N = N; v.M = M; v.row_ptr = row_ptr.p; v.col = col.p; v.ew = ew.p; v.nw = nw.p;
+    v.gid = gid.p;
+    return v;
+  }
+};
+
+// One input graph, arrays already in device memory.
+struct GIn {
+  int64_t n = 0, m = 0;
+  const int64_t* row_ptr = nullptr;
+  const int32_t* col = nullptr;
+  const int32_t* nw = nullptr;
+  const int32_t* ew = nullptr;
+  int32_t k = 2;
+  double eps = 0.03;
+  uint64_t seed = 0;
+};
+
+struct GOut {
+  int32_t status = SCLAP_OK;
+  int64_t cut = 0, maxbw = 0;
+  sclap_stats st{};
+};
+
+// Lmax = floor((1+eps) * ceil(cV/k)); U = max(max c(v), floor(Lmax/f)).
+void bounds(int64_t cV, int64_t maxc, int32_t k, double eps, int32_t f, int64_t* Lmax,
+            int64_t* U) {
+  const int64_t avg = (cV + k - 1) / k;
+  const int64_t L = (int64_t)std::floor((1.0 + eps) * (double)avg);
+  *Lmax = L;
+  *U = std::max<int64_t>(maxc, L / f);
+}
+
+void check_err(int32_t* d_err, cudaStream_t s) {
+  int32_t e = 0;
+  SCLAP_CUDA(cudaMemcpyAsync(&e, d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  SCLAP_CUDA(cudaStreamSynchronize(s));
+  if (e & DERR_W_OVERFLOW) throw Error(SCLAP_EOVERFLOW, "coarse edge weight above INT32_MAX");
+  if (e & DERR_HASH_FULL) throw Error(SCLAP_EINTERNAL, "hash table full");
+  if (e & DERR_BAD_CSR) throw Error(SCLAP_ECSR, "malformed CSR");
+  if (e) throw Error(SCLAP_EINTERNAL, "device error word set");
+}
+
+// Raises SCLAP_EINVAL unless every a[v] lies in [lo, hi).
+void check_range(const int32_t* a, int64_t n, int64_t lo, int64_t hi, cudaStream_t s,
+                 const char* what) {
+  DevBuf<int32_t> err(1, s);
+  err.zero();
+  k_check_range<<<grid_for(n, 256, (int64_t)num_sms() * 8), 256, 0, s>>>(a, n, lo, hi, err.p); SCLAP_NOTE_LAUNCH();
+  SCLAP_LAUNCH_CHECK();
+  int32_t e = 0;
+  SCLAP_CUDA(cudaMemcpyAsync(&e, err.p, 4, cudaMemcpyDeviceToHost, s));
+  SCLAP_CUDA(cudaStreamSynchronize(s));
+  if (e) throw Error(SCLAP_EINVAL, std::string(what) + " out of range");
+}
+
+// Validates one device-resident graph; returns c(V) and max c(v).
+void validate(const GIn& g, cudaStream_t s, int64_t* cV, int64_t* maxc) {
+  DevBuf<int32_t> err(1, s), mx(1, s);
+  DevBuf<unsigned long long> sum(1, s);
+  err.zero(); mx.zero(); sum.zero();
+  k_validate<<<grid_for(g.n, 256, (int64_t)num_sms() * 8), 256, 0, s>>>(
+      g.row_ptr, g.col, g.nw, g.ew, g.n, g.m, err.p, sum.p, mx.p); SCLAP_NOTE_LAUNCH();
+  SCLAP_LAUNCH_CHECK();
+  int32_t e = 0, m = 0;
+  unsigned long long w = 0;
+  SCLAP_CUDA(cudaMemcpyAsync(&e, err.p, 4, cudaMemcpyDeviceToHost, s));
+  SCLAP_CUDA(cudaMemcpyAsync(&m, mx.p, 4, cudaMemcpyDeviceToHost, s));
+  SCLAP_CUDA(cudaMemcpyAsync(&w, sum.p, 8, cudaMemcpyDeviceToHost, s));
+  SCLAP_CUDA(cudaStreamSynchronize(s));
+  if (e) throw Error(SCLAP_ECSR, "malformed CSR (row_ptr, column range, self-loop or weight)");
+  if (w >= (1ull << 31)) throw Error(SCLAP_EOVERFLOW, "sum of node weights must be < 2^31");
+  *cV = (int64_t)w;
+  *maxc = m;
+}
+
+// Builds the level holding the graphs `gs` back to back.
+void build_level0(const std::vector<GIn>& gs, Level& L, cudaStream_t s) {
+  const int B = (int)gs.size();
+  L.noff.assign(B + 1, 0);
+  L.aoff.assign(B + 1, 0);
+  for (int i = 0; i < B; ++i) {
+    L.noff[i + 1] = L.noff[i] + gs[i].n;
+    L.aoff[i + 1] = L.aoff[i] + gs[i].m;
+  }
+  L.N = L.noff[B];
+  L.M = L.aoff[B];
+  if (L.N >= ((int64_t)1 << 31)) throw Error(SCLAP_EINVAL, "total node count must be < 2^31");
+  L.row_ptr.alloc(L.N + 1, s);
+  L.col.alloc(std::max<int64_t>(L.M, 1), s);
+  L.ew.alloc(std::max<int64_t>(L.M, 1), s);
+  L.nw.alloc(std::max<int64_t>(L.N, 1), s);
+  std::vector<CopyTask> tasks(B);
+  for (int i = 0; i < B; ++i)
+    tasks[i] = CopyTask{gs[i].row_ptr, gs[i].col, gs[i].ew, gs[i].nw, 0, 0, gs[i].n, gs[i].m,
+                        L.noff[i], L.aoff[i]};
+  ip_replicate(tasks, L.row_ptr.p, L.col.p, L.ew.p, L.nw.p, L.M, s);
+  L.noff_d.alloc(B + 1, s);
+  L.noff_d.upload(L.noff);
+  L.gid.alloc(std::max<int64_t>(L.N, 1), s);
+  fill_gid(L.noff_d.p, B, L.gid.p, L.N, s);
+}
+
+struct GState {
+  int32_t k;
+  uint64_t seed;
+  int64_t cV, Lmax, U, avg, T;
+  int32_t q = 0;
+  int64_t boff = 0;
+  std::vector<int64_t> n_at, m_at;
+  std::vector<int32_t> crounds, rrounds;
+};
+
+
+
+// ---------------------------------------------------------------------------
+// Initial partitioning of a set of coarsest graphs: every graph gets
+// cfg.ip_trials trials (greedy growing + water-filling + LP local search),
+// all in one trial batch; the best trial of each graph is copied into its
+// level's block array and its block weights into Wg.
+// ---------------------------------------------------------------------------
+struct IPIn {
+  const Level* Q;      // level holding the graph
+  int g;               // slot of the graph in Q
+  int32_t k;
+  int64_t Lmax, avg;
+  uint64_t seed;
+  int32_t q;           // level index (hash input)
+  int64_t boff;        // graph's offset in the block space of Wg
+  int32_t* dst_blk;    // block array of Q
+};
+
+void run_ip(const std::vector<IPIn>& in, const sclap_config& cfg, int64_t* Wg,
+            std::vector<int32_t>& best, std::vector<int64_t>& ipcut, int64_t* lp_arcs,
+            int32_t* d_err, cudaStream_t s) {
+  const int B = (int)in.size();
+  const int T = cfg.ip_trials;
+  const int S = B * T;
+  std::vector<int64_t> noff(S + 1, 0), aoff(S + 1, 0), boff(S + 1, 0);
+  std::vector<CopyTask> tasks;
+  tasks.reserve(S);
+  for (int g = 0; g < B; ++g) {
+    const Level& Q = *in[g].Q;
+    const int x = in[g].g;
+    const int64_t n = Q.noff[x + 1] - Q.noff[x], m = Q.aoff[x + 1] - Q.aoff[x];
+    for (int t = 0; t < T; ++t) {
+      const int i = g * T + t;
+      noff[i + 1] = noff[i] + n;
+      aoff[i + 1] = aoff[i] + m;
+      boff[i + 1] = boff[i] + in[g].k;
+      tasks.push_back(CopyTask{Q.row_ptr.p, Q.col.p, Q.ew.p, Q.nw.p, Q.noff[x], Q.aoff[x], n, m,
+                               noff[i], aoff[i]});
+    }
+  }
+  Level ip;
+  ip.N = noff[S];
+  ip.M = aoff[S];
+  if (ip.N >= ((int64_t)1 << 31)) throw Error(SCLAP_EINVAL, "trial batch too large");
+  ip.row_ptr.alloc(ip.N + 1, s);
+  ip.col.alloc(std::max<int64_t>(ip.M, 1), s);
+  ip.ew.alloc(std::max<int64_t>(ip.M, 1), s);
+  ip.nw.alloc(std::max<int64_t>(ip.N, 1), s);
+  ip_replicate(tasks, ip.row_ptr.p, ip.col.p, ip.ew.p, ip.nw.p, ip.M, s);
+  ip.noff = noff;
+  ip.aoff = aoff;
+  ip.noff_d.alloc(S + 1, s);
+  ip.noff_d.upload(noff);
+  ip.gid.alloc(std::max<int64_t>(ip.N, 1), s);
+  fill_gid(ip.noff_d.p, S, ip.gid.p, ip.N, s);
+
+  const int64_t K = boff[S];
+  DevBuf<int32_t> label(std::max<int64_t>(ip.N, 1), s), step(std::max<int64_t>(ip.N, 1), s);
+  DevBuf<int64_t> W(std::max<int64_t>(K, 1), s), conn(std::max<int64_t>(ip.N, 1), s);
+  DevBuf<int64_t> wfA(std::max<int64_t>(K, 1), s), d_boff(S + 1, s), d_avg(S, s);
+  DevBuf<int32_t> wforder(std::max<int64_t>(K, 1), s);
+  std::vector<int64_t> h_avg(S), h_bound(S);
+  std::vector<uint64_t> h_tkey(S);
+  std::vector<int32_t> h_level(S), h_nlab(S), h_done(S, 0);
+  for (int g = 0; g < B; ++g)
+    for (int t = 0; t < T; ++t) {
+      const int i = g * T + t;
+      h_avg[i] = in[g].avg;
+      h_bound[i] = in[g].Lmax;
+      h_tkey[i] = hkey(in[g].seed, PH_TRIAL, (uint64_t)in[g].q, (uint64_t)t);
+      h_level[i] = in[g].q;
+      h_nlab[i] = in[g].k;
+    }
+  d_boff.upload(boff);
+  d_avg.upload(h_avg);
+  std::vector<int64_t> h_loff(boff.begin(), boff.end() - 1);
+  Slots sl(s, S, ip.noff_d.p, h_loff, h_bound, h_tkey, h_level, h_nlab, h_done);
+
+  GGGArgs ga{};
+  ga.row_ptr = ip.row_ptr.p; ga.col = ip.col.p; ga.ew = ip.ew.p; ga.nw = ip.nw.p;
+  ga.noff = ip.noff_d.p; ga.boff = d_boff.p; ga.nlab = sl.nlab.p; ga.avg = d_avg.p;
+  ga.tkey = sl.seed.p; ga.level = sl.level.p; ga.label = label.p; ga.W = W.p;
+  ga.conn = conn.p; ga.step = step.p; ga.wfA = wfA.p; ga.wforder = wforder.p;
+  ga.nslots = S;
+  ggg_trials(ga, s);
+
+  LPRun run;
+  run.mode = MODE_REFINE;
+  run.phase = PH_IPREF;
+  run.rounds = cfg.lp_rounds_refine;
+  run.sub_rounds = cfg.sub_rounds;
+  run.use_active = true;
+  *lp_arcs += lp_run(ip.view(), sl.sp, label.p, W.p, K, run, d_err, s);
+
+  DevBuf<int64_t> cut2(S, s);
+  cut2.zero();
+  slot_cut(ip.view(), label.p, cut2.p, s);
+  std::vector<SelectTask> sel(B);
+  for (int g = 0; g < B; ++g) {
+    const Level& Q = *in[g].Q;
+    const int x = in[g].g;
+    sel[g] = SelectTask{in[g].dst_blk, Q.noff[x], Q.noff[x + 1] - Q.noff[x], (int64_t)g * T, T,
+                        in[g].k, in[g].Lmax, in[g].boff, g};
+  }
+  DevBuf<int32_t> d_best(B, s);
+  DevBuf<int64_t> d_cut(B, s);
+  ip_select_copy(sel, cut2.p, W.p, ip.noff_d.p, d_boff.p, label.p, Wg, d_best.p, d_cut.p, s);
+  best.assign(B, 0);
+  ipcut.assign(B, 0);
+  SCLAP_CUDA(cudaMemcpyAsync(best.data(), d_best.p, B * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  SCLAP_CUDA(cudaMemcpyAsync(ipcut.data(), d_cut.p, B * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  SCLAP_CUDA(cudaStreamSynchronize(s));
+}
+
+// ---------------------------------------------------------------------------
+// The multilevel partitioner over a batch of validated graphs.
+// ---------------------------------------------------------------------------
+void run_batch(const std::vector<GIn>& gs, const std::vector<int64_t>& cV,
+               const std::vector<int64_t>& maxc, const sclap_config& cfg,
+               const std::vector<int32_t*>& outs, std::vector<GOut>& res, cudaStream_t s) {
+  const int B = (int)gs.size();
+  res.assign(B, GOut{});
+  std::vector<GState> st(B);
+  int64_t Ktot = 0;
+  for (int g = 0; g < B; ++g) {
+    GState& x = st[g];
+    x.k = gs[g].k;
+    x.seed = gs[g].seed;
+    x.cV = cV[g];
+    bounds(cV[g], maxc[g], x.k, gs[g].eps, cfg.f, &x.Lmax, &x.U);
+    x.avg = (cV[g] + x.k - 1) / x.k;
+    x.T = std::max<int64_t>(cfg.coarse_min_nodes, 60 * (int64_t)x.k);
+    x.boff = Ktot;
+    Ktot += x.k;
+    x.n_at.push_back(gs[g].n);
+    x.m_at.push_back(gs[g].m);
+  }
+  DevBuf<int32_t> d_err(1, s);
+  d_err.zero();
+  int64_t lp_arcs = 0;
+  const int sms = num_sms();
+
+  std::vector<std::unique_ptr<Level>> lv;
+  lv.emplace_back(new Level());
+  build_level0(gs, *lv[0], s);
+
+  // ---------------- coarsening
+  std::vector<char> coarsening(B, 0);
+  for (int g = 0; g < B; ++g) coarsening[g] = (gs[g].n > st[g].T && 1 < cfg.max_levels) ? 1 : 0;
+  for (int L = 0;; ++L) {
+    bool any = false;
+    for (int g = 0; g < B; ++g) any = any || coarsening[g];
+    if (!any) break;
+    Level& cur = *lv[L];
+    const LevelView v = cur.view();
+    std::vector<int64_t> h_bound(B);
+    std::vector<uint64_t> h_seed(B);
+    std::vector<int32_t> h_level(B, L), h_nlab(B, 0), h_done(B);
+    for (int g = 0; g < B; ++g) {
+      h_bound[g] = st[g].U;
+      h_seed[g] = st[g].seed;
+      h_done[g] = coarsening[g] ? 0 : 1;
+    }
+    std::vector<int64_t> h_loff(cur.noff.begin(), cur.noff.end() - 1);
+    Slots sl(s, B, cur.noff_d.p, h_loff, h_bound, h_seed, h_level, h_nlab, h_done);
+    DevBuf<int32_t> label(std::max<int64_t>(v.N, 1), s);
+    DevBuf<int64_t> W(std::max<int64_t>(v.N, 1), s);
+    k_iota<<<grid_for(v.N, 256, (int64_t)sms * 16), 256, 0, s>>>(label.p, v.N); SCLAP_NOTE_LAUNCH();
+    k_w_from_nw<<<grid_for(v.N, 256, (int64_t)sms * 16), 256, 0, s>>>(v.nw, v.N, W.p); SCLAP_NOTE_LAUNCH();
+    SCLAP_LAUNCH_CHECK();
+    LPRun run;
+    run.mode = MODE_CLUSTER;
+    run.phase = PH_CLUSTER;
+    run.rounds = cfg.lp_rounds_coarse;
+    run.sub_rounds = cfg.sub_rounds;
+    lp_arcs += lp_run(v, sl.sp, label.p, W.p, v.N, run, d_err.p, s);
+    const std::vector<int32_t> rr = sl.host_rounds(s);
+    for (int g = 0; g < B; ++g)
+      if (coarsening[g]) st[g].crounds.push_back(rr[g]);
+    ContractWork cw;
+    std::vector<int64_t> nc;
+    contract_rank(v, cur.noff, label.p, cw, nc, s);
+    std::vector<uint8_t> keep(B, 0);
+    bool anykeep = false;
+    for (int g = 0; g < B; ++g) {
+      if (!coarsening[g]) continue;
+      const int64_t n = cur.noff[g + 1] - cur.noff[g];
+      if (20 * (n - nc[g]) < n) {
+        coarsening[g] = 0;   // shrink below 5%: this level stays the coarsest
+      } else {
+        keep[g] = 1;
+        anykeep = true;
+      }
+    }
+    if (!anykeep) break;
+    cur.cmap.alloc(std::max<int64_t>(v.N, 1), s);
+    CoarseLevel co;
+    contract_build(v, cur.noff, label.p, cw, keep, cur.cmap.p, co, d_err.p, s);
+    std::unique_ptr<Level> nx(new Level());
+    nx->N = co.N;
+    nx->M = co.M;
+    nx->row_ptr = std::move(co.row_ptr);
+    nx->col = std::move(co.col);
+    nx->ew = std::move(co.ew);
+    nx->nw = std::move(co.nw);
+    nx->gid = std::move(co.gid);
+    nx->noff_d = std::move(co.noff_d);
+    nx->noff = co.noff;
+    nx->aoff = co.aoff;
+    for (int g = 0; g < B; ++g) {
+      if (!keep[g]) continue;
+      st[g].q = L + 1;
+      const int64_t n = nx->noff[g + 1] - nx->noff[g];
+      st[g].n_at.push_back(n);
+      st[g].m_at.push_back(nx->aoff[g + 1] - nx->aoff[g]);
+      coarsening[g] = (n > st[g].T && L + 2 < cfg.max_levels) ? 1 : 0;
+    }
+    lv.push_back(std::move(nx));
+  }
+  check_err(d_err.p, s);
+  const int nlev = (int)lv.size();
+  for (int L = 0; L < nlev; ++L) lv[L]->blk.alloc(std::max<int64_t>(lv[L]->N, 1), s);
+
+  // ---------------- initial partitioning
+  DevBuf<int64_t> Wg(std::max<int64_t>(Ktot, 1), s);
+  {
+    std::vector<IPIn> in(B);
+    for (int g = 0; g < B; ++g) {
+      const Level* Q = lv[st[g].q].get();
+      in[g] = IPIn{Q, g, st[g].k, st[g].Lmax, st[g].avg, st[g].seed, st[g].q, st[g].boff,
+                   Q->blk.p};
+    }
+    std::vector<int32_t> best;
+    std::vector<int64_t> ipcut;
+    run_ip(in, cfg, Wg.p, best, ipcut, &lp_arcs, d_err.p, s);
+    for (int g = 0; g < B; ++g) {
+      res[g].st.ip_best_trial = best[g];
+      res[g].st.ip_cut = ipcut[g];
+    }
+  }
+
+  // ---------------- uncoarsening: project, then LP local search
+  std::vector<int64_t> h_Lmax(B), h_boff(B);
+  std::vector<uint64_t> h_seed(B);
+  std::vector<int32_t> h_k(B);
+  for (int g = 0; g < B; ++g) {
+    h_Lmax[g] = st[g].Lmax;
+    h_boff[g] = st[g].boff;
+    h_seed[g] = st[g].seed;
+    h_k[g] = st[g].k;
+    st[g].rrounds.assign(st[g].q + 1, 0);
+  }
+  for (int L = nlev - 2; L >= 0; --L) {
+    Level& F = *lv[L];
+    project(F.cmap.p, lv[L + 1]->blk.p, F.blk.p, F.N, s);
+    lv[L + 1].reset();
+    std::vector<int32_t> h_level(B, L), h_done(B);
+    bool any = false;
+    for (int g = 0; g < B; ++g) {
+      h_done[g] = st[g].q > L ? 0 : 1;
+      any = any || !h_done[g];
+    }
+    if (!any) continue;
+    Slots sl(s, B, F.noff_d.p, h_boff, h_Lmax, h_seed, h_level, h_k, h_done);
+    LPRun run;
+    run.mode = MODE_REFINE;
+    run.phase = PH_REFINE;
+    run.rounds = cfg.lp_rounds_refine;
+    run.sub_rounds = cfg.sub_rounds;
+    run.use_active = true;
+    lp_arcs += lp_run(F.view(), sl.sp, F.blk.p, Wg.p, Ktot, run, d_err.p, s);
+    const std::vector<int32_t> rr = sl.host_rounds(s);
+    for (int g = 0; g < B; ++g)
+      if (st[g].q > L) st[g].rrounds[L] = rr[g];
+  }
+
+  // ---------------- balance repair on the input level
+  Level& F0 = *lv[0];
+  if (cfg.repair_rounds > 0) {
+    std::vector<int32_t> h_level(B, 0), h_done(B, 0);
+    Slots sl(s, B, F0.noff_d.p, h_boff, h_Lmax, h_seed, h_level, h_k, h_done);
+    LPRun run;
+    run.mode = MODE_REPAIR;
+    run.phase = PH_REPAIR;
+    run.rounds = cfg.repair_rounds;
+    run.sub_rounds = cfg.sub_rounds;
+    run.stop_rule = false;
+    lp_arcs += lp_run(F0.view(), sl.sp, F0.blk.p, Wg.p, Ktot, run, d_err.p, s);
+  }
+  check_err(d_err.p, s);
+
+  // ---------------- cut, outputs
+  DevBuf<int64_t> cut2(B, s);
+  cut2.zero();
+  slot_cut(F0.view(), F0.blk.p, cut2.p, s);
+  std::vector<OutTask> ot(B);
+  int64_t mx = 1;
+  for (int g = 0; g < B; ++g) {
+    ot[g] = OutTask{outs[g], F0.noff[g], gs[g].n, st[g].boff};
+    mx = std::max(mx, gs[g].n);
+  }
+  DevBuf<OutTask> d_ot(B, s);
+  d_ot.upload(ot);
+  for (int b0 = 0; b0 < B; b0 += 65535) {
+    dim3 grid(grid_for(mx, 256, 256), (unsigned)std::min(65535, B - b0));
+    k_write_out<<<grid, 256, 0, s>>>(d_ot.p + b0, F0.blk.p); SCLAP_NOTE_LAUNCH();
+  }
+  SCLAP_LAUNCH_CHECK();
+  std::vector<int64_t> h_cut2(B), h_W(Ktot);
+  SCLAP_CUDA(cudaMemcpyAsync(h_cut2.data(), cut2.p, B * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  SCLAP_CUDA(cudaMemcpyAsync(h_W.data(), Wg.p, Ktot * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  SCLAP_CUDA(cudaStreamSynchronize(s));
+  for (int g = 0; g < B; ++g) {
+    GOut& o = res[g];
+    o.cut = h_cut2[g] / 2;
+    int64_t m = 0;
+    for (int b = 0; b < st[g].k; ++b) m = std::max(m, h_W[st[g].boff + b]);
+    o.maxbw = m;
+    o.status = m <= st[g].Lmax ? SCLAP_OK : SCLAP_EINFEASIBLE;
+    sclap_stats& x = o.st;
+    x.levels = st[g].q + 1;
+    for (int l = 0; l <= st[g].q && l < 64; ++l) {
+      x.level_n[l] = st[g].n_at[l];
+      x.level_m[l] = st[g].m_at[l];
+      x.refine_rounds[l] = l < (int)st[g].rrounds.size() ? st[g].rrounds[l] : 0;
+    }
+    for (size_t l = 0; l < st[g].crounds.size() && l < 64; ++l) x.cluster_rounds[l] = st[g].crounds[l];
+    x.Lmax = st[g].Lmax;
+    x.U = st[g].U;
+    x.lp_arcs = lp_arcs;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Helpers for the C ABI.
+// ---------------------------------------------------------------------------
+template <class F>
+int guarded(F&& f) {
+  try {
+    init_pool();
+    f();
+    g_last_error.clear();
+    return SCLAP_OK;
+  } catch (const Error& e) {
+    g_last_error = e.what();
+    return e.code;
+  } catch (const std::exception& e) {
+    g_last_error = e.what();
+    return SCLAP_EINTERNAL;
+  } catch (...) {
+    g_last_error = "unknown exception";
+    return SCLAP_EINTERNAL;
+  }
+}
+
+void check_args(int64_t n, const void* row_ptr, const void* col, int32_t k, double eps,
+                const void* out) {
+  if (n < 1 || n >= ((int64_t)1 << 31)) throw Error(SCLAP_EINVAL, "n must be in [1, 2^31)");
+  if (!row_ptr || !out) throw Error(SCLAP_EINVAL, "NULL array");
+  (void)col;   // may be NULL when the graph has no arcs (checked once m is known)
+  if (k < 1 || (int64_t)k > n) throw Error(SCLAP_EINVAL, "k must be in [1, n]");
+  if (!(eps >= 0.0) || !std::isfinite(eps)) throw Error(SCLAP_EINVAL, "eps must be >= 0");
+}
+
+int64_t device_arcs(const int64_t* row_ptr, int64_t n, cudaStream_t s) {
+  int64_t m = 0;
+  SCLAP_CUDA(cudaMemcpyAsync(&m, row_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  SCLAP_CUDA(cudaStreamSynchronize(s));
+  if (m < 0 || m >= ((int64_t)1 << 40)) throw Error(SCLAP_ECSR, "row_ptr[n] out of range");
+  return m;
+}
+
+void check_col(const void* col, int64_t m) {
+  if (m > 0 && !col) throw Error(SCLAP_EINVAL, "NULL col with arcs present");
+}
+
+// Owned device copy of a host graph.
+struct HostUpload {
+  DevBuf<int64_t> rp;
+  DevBuf<int32_t> col, nw, ew;
+  GIn g;
+  HostUpload(int64_t n, const int64_t* row_ptr, const int32_t* c, const int32_t* node_w,
+             const int32_t* edge_w, cudaStream_t s) {
+    const int64_t m = row_ptr[n];
+    if (m < 0) throw Error(SCLAP_ECSR, "row_ptr[n] < 0");
+    check_col(c, m);
+    rp.alloc(n + 1, s);
+    rp.upload(row_ptr, n + 1);
+    col.alloc(std::max<int64_t>(m, 1), s);
+    col.upload(c, m);
+    if (node_w) { nw.alloc(n, s); nw.upload(node_w, n); }
+    if (edge_w) { ew.alloc(std::max<int64_t>(m, 1), s); ew.upload(edge_w, m); }
+    g.n = n; g.m = m; g.row_ptr = rp.p; g.col = col.p;
+    g.nw = node_w ? nw.p : nullptr;
+    g.ew = edge_w ? ew.p : nullptr;
+  }
+};
+
+// A one-slot level holding a copy of a device graph (step entry points).
+void single_level(const GIn& g, Level& L, cudaStream_t s) {
+  std::vector<GIn> v{g};
+  build_level0(v, L, s);
+}
+
+void fill_stats(sclap_stats* dst, const GOut& o) {
+  if (dst) *dst = o.st;
+}
+
+}  // namespace
+}  // namespace sclap
+
+using namespace sclap;
+
+extern "C" {
+
+void sclap_default_config(sclap_config* c) {
+  if (!c) return;
+  c->lp_rounds_coarse = 10;
+  c->lp_rounds_refine = 10;
+  c->f = 18;
+  c->coarse_min_nodes = 1000;
+  c->ip_trials = 16;
+  c->sub_rounds = 8;
+  c->repair_rounds = 64;
+  c->max_levels = 64;
+}
+
+const char* sclap_error_string(int code) {
+  switch (code) {
+    case SCLAP_OK: return "ok";
+    case SCLAP_EINVAL: return "invalid argument";
+    case SCLAP_ECSR: return "malformed CSR input";
+    case SCLAP_ENOMEM: return "device out of memory";
+    case SCLAP_ECUDA: return "CUDA error";
+    case SCLAP_EOVERFLOW: return "integer weight overflow";
+    case SCLAP_EINFEASIBLE: return "balance constraint could not be met";
+    case SCLAP_ETIMEOUT: return "bounded device wait timed out";
+    case SCLAP_EINTERNAL: return "internal error";
+    default: return "unknown error code";
+  }
+}
+
+const char* sclap_last_error(void) { return g_last_error.c_str(); }
+
+int sclap_partition(int64_t n, const int64_t* row_ptr, const int32_t* col, const int32_t* node_w,
+                    const int32_t* edge_w, int32_t k, double eps, uint64_t seed,
+                    const sclap_config* cfg, int32_t* block_out, int64_t* cut_out,
+                    int64_t* max_block_weight_out, sclap_stats* stats) {
+  int status = SCLAP_OK;
+  int rc = guarded([&] {
+    check_args(n, row_ptr, col, k, eps, block_out);
+    const sclap_config c = resolve_cfg(cfg);
+    cudaStream_t s = 0;
+    HostUpload up(n, row_ptr, col, node_w, edge_w, s);
+    up.g.k = k; up.g.eps = eps; up.g.seed = seed;
+    int64_t cV, maxc;
+    validate(up.g, s, &cV, &maxc);
+    DevBuf<int32_t> out(n, s);
+    std::vector<GOut> res;
+    run_batch({up.g}, {cV}, {maxc}, c, {out.p}, res, s);
+    SCLAP_CUDA(cudaMemcpyAsync(block_out, out.p, n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    SCLAP_CUDA(cudaStreamSynchronize(s));
+    if (cut_out) *cut_out = res[0].cut;
+    if (max_block_weight_out) *max_block_weight_out = res[0].maxbw;
+    fill_stats(stats, res[0]);
+    status = res[0].status;
+  });
+  return rc != SCLAP_OK ? rc : status;
+}
+
+int sclap_partition_device(int64_t n, const int64_t* row_ptr, const int32_t* col,
+                           const int32_t* node_w, const int32_t* edge_w, int32_t k, double eps,
+                           uint64_t seed, const sclap_config* cfg, int32_t* block_out,
+                           int64_t* cut_out, int64_t* max_block_weight_out, sclap_stats* stats,
+                           void* stream) {
+  int status = SCLAP_OK;
+  int rc = guarded([&] {
+    check_args(n, row_ptr, col, k, eps, block_out);
+    const sclap_config c = resolve_cfg(cfg);
+    cudaStream_t s = (cudaStream_t)stream;
+    GIn g;
+    g.n = n; g.m = device_arcs(row_ptr, n, s); g.row_ptr = row_ptr; g.col = col;
+    g.nw = node_w; g.ew = edge_w; g.k = k; g.eps = eps; g.seed = seed;
+    check_col(g.col, g.m);
+    int64_t cV, maxc;
+    validate(g, s, &cV, &maxc);
+    std::vector<GOut> res;
+    run_batch({g}, {cV}, {maxc}, c, {block_out}, res, s);
+    SCLAP_CUDA(cudaStreamSynchronize(s));
+    if (cut_out) *cut_out = res[0].cut;
+    if (max_block_weight_out) *max_block_weight_out = res[0].maxbw;
+    fill_stats(stats, res[0]);
+    status = res[0].status;
+  });
+  return rc != SCLAP_OK ? rc : status;
+}
+
+int sclap_partition_batch(int32_t count, sclap_graph* graphs, const sclap_config* cfg,
+                          int32_t device_ptrs, void* stream) {
+  int first_err = SCLAP_OK;
+  int rc = guarded([&] {
+    if (count < 0 || (count > 0 && !graphs)) throw Error(SCLAP_EINVAL, "bad batch");
+    const sclap_config c = resolve_cfg(cfg);
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<std::unique_ptr<HostUpload>> ups;
+    std::vector<GIn> gs;
+    std::vector<int64_t> cV, maxc;
+    std::vector<int> idx;
+    std::vector<std::unique_ptr<DevBuf<int32_t>>> outbufs;
+    std::vector<int32_t*> outs;
+    for (int i = 0; i < count; ++i) {
+      sclap_graph& G = graphs[i];
+      G.status = guarded([&] {
+        check_args(G.n, G.row_ptr, G.col, G.k, G.eps, G.block_out);
+        GIn g;
+        if (device_ptrs) {
+          g.n = G.n; g.m = device_arcs(G.row_ptr, G.n, s); g.row_ptr = G.row_ptr;
+          g.col = G.col; g.nw = G.node_w; g.ew = G.edge_w;
+        } else {
+          ups.emplace_back(new HostUpload(G.n, G.row_ptr, G.col, G.node_w, G.edge_w, s));
+          g = ups.back()->g;
+        }
+        g.k = G.k; g.eps = G.eps; g.seed = G.seed;
+        check_col(g.col, g.m);
+        int64_t a, b;
+        validate(g, s, &a, &b);
+        gs.push_back(g);
+        cV.push_back(a);
+        maxc.push_back(b);
+        idx.push_back(i);
+        if (device_ptrs) {
+          outs.push_back(G.block_out);
+        } else {
+          outbufs.emplace_back(new DevBuf<int32_t>(G.n, s));
+          outs.push_back(outbufs.back()->p);
+        }
+      });
+      if (G.status != SCLAP_OK && first_err == SCLAP_OK) first_err = G.status;
+    }
+    if (gs.empty()) return;
+    std::vector<GOut> res;
+    run_batch(gs, cV, maxc, c, outs, res, s);
+    for (size_t j = 0; j < gs.size(); ++j) {
+      sclap_graph& G = graphs[idx[j]];
+      if (!device_ptrs)
+        SCLAP_CUDA(cudaMemcpyAsync(G.block_out, outs[j], G.n * sizeof(int32_t),
+                                   cudaMemcpyDeviceToHost, s));
+      G.cut = res[j].cut;
+      G.max_block_weight = res[j].maxbw;
+      G.status = res[j].status;
+      if (G.status != SCLAP_OK && first_err == SCLAP_OK) first_err = G.status;
+    }
+    SCLAP_CUDA(cudaStreamSynchronize(s));
+  });
+  return rc != SCLAP_OK ? rc : first_err;
+}
+
+int sclap_lp_round(int32_t mode, int64_t n, const int64_t* row_ptr, const int32_t* col,
+                   const int32_t* node_w, const int32_t* edge_w, int32_t* label, int64_t* W,
+                   int64_t nlabels, int64_t bound, uint64_t rkey, int32_t sub_rounds,
+                   const uint8_t* active_cur, uint8_t* active_next, int64_t* moved_out,
+                   void* stream) {
+  return guarded([&] {
+    if (mode != 0 && mode != 1) throw Error(SCLAP_EINVAL, "mode must be 0 or 1");
+    if (n < 1 || !row_ptr || !col || !label || !W || nlabels < 1 || sub_rounds < 1 ||
+        sub_rounds > 64)
+      throw Error(SCLAP_EINVAL, "bad argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    GIn g;
+    g.n = n; g.m = device_arcs(row_ptr, n, s); g.row_ptr = row_ptr; g.col = col; g.nw = node_w;
+    g.ew = edge_w;
+    check_col(g.col, g.m);
+    int64_t cV, maxc;
+    validate(g, s, &cV, &maxc);
+    if (mode == 0 && nlabels < n) throw Error(SCLAP_EINVAL, "clustering needs nlabels >= n");
+    check_range(label, n, 0, nlabels, s, "label");
+    Level L;
+    single_level(g, L, s);
+    Slots sl(s, 1, L.noff_d.p, {0}, {bound}, {rkey}, {0}, {(int32_t)nlabels}, {0});
+    LPRun run;
+    run.mode = mode == 0 ? MODE_CLUSTER : MODE_REFINE;
+    run.rounds = 1;
+    run.sub_rounds = sub_rounds;
+    run.stop_rule = false;
+    run.raw_key = true;
+    DevBuf<int32_t> d_err(1, s);
+    d_err.zero();
+    lp_run(L.view(), sl.sp, label, W, nlabels, run, d_err.p, s, active_cur, active_next);
+    check_err(d_err.p, s);
+    int64_t mv = 0;
+    SCLAP_CUDA(cudaMemcpyAsync(&mv, sl.moved.p, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    SCLAP_CUDA(cudaStreamSynchronize(s));
+    if (moved_out) *moved_out = mv;
+  });
+}
+
+int sclap_cluster(int64_t n, const int64_t* row_ptr, const int32_t* col, const int32_t* node_w,
+                  const int32_t* edge_w, int64_t U, uint64_t seed, int32_t level,
+                  const sclap_config* cfg, int32_t* label_out, int32_t* rounds_out,
+                  void* stream) {
+  return guarded([&] {
+    if (n < 1 || !row_ptr || !col || !label_out) throw Error(SCLAP_EINVAL, "bad argument");
+    const sclap_config c = resolve_cfg(cfg);
+    cudaStream_t s = (cudaStream_t)stream;
+    GIn g;
+    g.n = n; g.m = device_arcs(row_ptr, n, s); g.row_ptr = row_ptr; g.col = col; g.nw = node_w;
+    g.ew = edge_w;
+    check_col(g.col, g.m);
+    int64_t cV, maxc;
+    validate(g, s, &cV, &maxc);
+    Level L;
+    single_level(g, L, s);
+    Slots sl(s, 1, L.noff_d.p, {0}, {U}, {seed}, {level}, {0}, {0});
+    DevBuf<int64_t> W(n, s);
+    k_iota<<<grid_for(n, 256, (int64_t)num_sms() * 16), 256, 0, s>>>(label_out, n); SCLAP_NOTE_LAUNCH();
+    k_w_from_nw<<<grid_for(n, 256, (int64_t)num_sms() * 16), 256, 0, s>>>(L.nw.p, n, W.p); SCLAP_NOTE_LAUNCH();
+    LPRun run;
+    run.mode = MODE_CLUSTER;
+    run.phase = PH_CLUSTER;
+    run.rounds = c.lp_rounds_coarse;
+    run.sub_rounds = c.sub_rounds;
+    DevBuf<int32_t> d_err(1, s);
+    d_err.zero();
+    lp_run(L.view(), sl.sp, label_out, W.p, n, run, d_err.p, s);
+    check_err(d_err.p, s);
+    if (rounds_out) *rounds_out = sl.host_rounds(s)[0];
+  });
+}
+
+int sclap_contract(int64_t n, const int64_t* row_ptr, const int32_t* col, const int32_t* node_w,
+                   const int32_t* edge_w, const int32_t* label, int32_t* cmap, int64_t* nc_out,
+                   int32_t* cnode_w, int64_t* crow_ptr, int32_t* ccol, int32_t* cedge_w,
+                   int64_t* mc_out, void* stream) {
+  return guarded([&] {
+    if (n < 1 || !row_ptr || !col || !label || !cmap || !cnode_w || !crow_ptr || !ccol ||
+        !cedge_w)
+      throw Error(SCLAP_EINVAL, "bad argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    GIn g;
+    g.n = n; g.m = device_arcs(row_ptr, n, s); g.row_ptr = row_ptr; g.col = col; g.nw = node_w;
+    g.ew = edge_w;
+    check_col(g.col, g.m);
+    int64_t cV, maxc;
+    validate(g, s, &cV, &maxc);
+    check_range(label, n, 0, n, s, "label");
+    Level L;
+    single_level(g, L, s);
+    ContractWork w;
+    std::vector<int64_t> nc;
+    contract_rank(L.view(), L.noff, label, w, nc, s);
+    CoarseLevel co;
+    DevBuf<int32_t> d_err(1, s);
+    d_err.zero();
+    contract_build(L.view(), L.noff, label, w, {1}, cmap, co, d_err.p, s);
+    check_err(d_err.p, s);
+    SCLAP_CUDA(cudaMemcpyAsync(cnode_w, co.nw.p, co.N * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    SCLAP_CUDA(cudaMemcpyAsync(crow_ptr, co.row_ptr.p, (co.N + 1) * sizeof(int64_t),
+                               cudaMemcpyDeviceToDevice, s));
+    if (co.M > 0) {
+      SCLAP_CUDA(cudaMemcpyAsync(ccol, co.col.p, co.M * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+      SCLAP_CUDA(cudaMemcpyAsync(cedge_w, co.ew.p, co.M * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    }
+    SCLAP_CUDA(cudaStreamSynchronize(s));
+    if (nc_out) *nc_out = co.N;
+    if (mc_out) *mc_out = co.M;
+  });
+}
+
+int sclap_initial_partition(int64_t n, const int64_t* row_ptr, const int32_t* col,
+                            const int32_t* node_w, const int32_t* edge_w, int32_t k,
+                            int64_t Lmax, int64_t avg, uint64_t seed, int32_t level,
+                            const sclap_config* cfg, int32_t* block_out, int64_t* cut_out,
+                            int32_t* best_trial_out, void* stream) {
+  return guarded([&] {
+    if (n < 1 || !row_ptr || !col || !block_out || k < 1 || k > n)
+      throw Error(SCLAP_EINVAL, "bad argument");
+    const sclap_config c = resolve_cfg(cfg);
+    cudaStream_t s = (cudaStream_t)stream;
+    GIn g;
+    g.n = n; g.m = device_arcs(row_ptr, n, s); g.row_ptr = row_ptr; g.col = col; g.nw = node_w;
+    g.ew = edge_w;
+    check_col(g.col, g.m);
+    int64_t cV, maxc;
+    validate(g, s, &cV, &maxc);
+    Level L;
+    single_level(g, L, s);
+    DevBuf<int64_t> Wg(k, s);
+    DevBuf<int32_t> d_err(1, s);
+    d_err.zero();
+    std::vector<IPIn> in{IPIn{&L, 0, k, Lmax, avg, seed, level, 0, block_out}};
+    std::vector<int32_t> best;
+    std::vector<int64_t> ipcut;
+    int64_t arcs = 0;
+    run_ip(in, c, Wg.p, best, ipcut, &arcs, d_err.p, s);
+    check_err(d_err.p, s);
+    if (cut_out) *cut_out = ipcut[0];
+    if (best_trial_out) *best_trial_out = best[0];
+  });
+}
+
+int sclap_refine(int64_t n, const int64_t* row_ptr, const int32_t* col, const int32_t* node_w,
+                 const int32_t* edge_w, int32_t k, int64_t Lmax, uint64_t seed, int32_t phase,
+                 int32_t level, const sclap_config* cfg, int32_t* block, int32_t* rounds_out,
+                 void* stream) {
+  return guarded([&] {
+    if (n < 1 || !row_ptr || !col || !block || k < 1) throw Error(SCLAP_EINVAL, "bad argument");
+    const sclap_config c = resolve_cfg(cfg);
+    cudaStream_t s = (cudaStream_t)stream;
+    GIn g;
+    g.n = n; g.m = device_arcs(row_ptr, n, s); g.row_ptr = row_ptr; g.col = col; g.nw = node_w;
+    g.ew = edge_w;
+    check_col(g.col, g.m);
+    int64_t cV, maxc;
+    validate(g, s, &cV, &maxc);
+    check_range(block, n, 0, k, s, "block");
+    Level L;
+    single_level(g, L, s);
+    DevBuf<int64_t> W(k, s);
+    W.zero();
+    block_weights(block, L.nw.p, n, W.p, s);
+    Slots sl(s, 1, L.noff_d.p, {0}, {Lmax}, {seed}, {level}, {k}, {0});
+    LPRun run;
+    run.mode = MODE_REFINE;
+    run.phase = phase;
+    run.rounds = c.lp_rounds_refine;
+    run.sub_rounds = c.sub_rounds;
+    run.use_active = true;
+    DevBuf<int32_t> d_err(1, s);
+    d_err.zero();
+    lp_run(L.view(), sl.sp, block, W.p, k, run, d_err.p, s);
+    check_err(d_err.p, s);
+    if (rounds_out) *rounds_out = sl.host_rounds(s)[0];
+  });
+}
+
+int sclap_cut(int64_t n, const int64_t* row_ptr, const int32_t* col, const int32_t* edge_w,
+              const int32_t* block, int64_t* cut_out, void* stream) {
+  return guarded([&] {
+    if (n < 1 || !row_ptr || !col || !block) throw Error(SCLAP_EINVAL, "bad argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    GIn g;
+    g.n = n; g.m = device_arcs(row_ptr, n, s); g.row_ptr = row_ptr; g.col = col; g.ew = edge_w;
+    check_col(g.col, g.m);
+    int64_t cV, maxc;
+    validate(g, s, &cV, &maxc);
+    Level L;
+    single_level(g, L, s);
+    DevBuf<int64_t> cut2(1, s);
+    cut2.zero();
+    slot_cut(L.view(), block, cut2.p, s);
+    int64_t c2 = 0;
+    SCLAP_CUDA(cudaMemcpyAsync(&c2, cut2.p, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    SCLAP_CUDA(cudaStreamSynchronize(s));
+    if (cut_out) *cut_out = c2 / 2;
+  });
+}
+
+void sclap_profile_enable(int on) { profile().enabled.store(on != 0); }
+
+void sclap_profile_reset(void) {
+  ProfileState& P = profile();
+  std::lock_guard<std::mutex> lk(P.mu);
+  P.launches.store(0);
+  for (int b = 0; b < 7; ++b) { P.ms[b] = 0; P.nlaunch[b] = 0; P.nodes[b] = 0; P.arcs[b] = 0; }
+}
+
+void sclap_profile_read(sclap_profile* out) {
+  if (!out) return;
+  ProfileState& P = profile();
+  std::lock_guard<std::mutex> lk(P.mu);
+  out->kernel_launches = P.launches.load();
+  for (int b = 0; b < 7; ++b) {
+    out->propose_launches[b] = P.nlaunch[b];
+    out->propose_ms[b] = P.ms[b];
+    out->propose_nodes[b] = P.nodes[b];
+    out->propose_arcs[b] = P.arcs[b];
+  }
+}
+
+}  // extern "C"

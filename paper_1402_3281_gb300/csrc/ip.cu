@@ -1,0 +1,363 @@
+// ip.cu -- initial partitioning of the coarsest graphs, cut, projection.
+//
+// The paper partitions the coarsest graph with KaHIP's recursive bisection,
+// which it does not specify.  Here every graph gets `trials` independent
+// trials, all graphs' trials forming one batch: greedy graph growing (one CTA
+// per trial: block j starts at a hashed seed and absorbs the unassigned
+// nodes connected to it, in node-id order, while it stays <= ceil(c(V)/k)),
+// water-filling of the leftovers, then LP local search (the lp.cu kernels on
+// the whole trial batch).  The best trial by (overload, cut, trial) is kept.
+#include "common.cuh"
+
+namespace sclap {
+namespace {
+
+constexpr int GNT = 512;
+
+__global__ void k_replicate(const CopyTask* __restrict__ tasks, int64_t* __restrict__ row_ptr,
+                            int32_t* __restrict__ col, int32_t* __restrict__ ew,
+                            int32_t* __restrict__ nw) {
+  const CopyTask t = tasks[blockIdx.y];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < t.n; v += stride) {
+    row_ptr[t.dst_n0 + v] = t.dst_a0 + (t.row_ptr[t.src_n0 + v] - t.src_a0);
+    nw[t.dst_n0 + v] = t.nw ? t.nw[t.src_n0 + v] : 1;
+  }
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < t.m; e += stride) {
+    col[t.dst_a0 + e] = (int32_t)(t.col[t.src_a0 + e] - t.src_n0 + t.dst_n0);
+    ew[t.dst_a0 + e] = t.ew ? t.ew[t.src_a0 + e] : 1;
+  }
+}
+
+// Block-wide inclusive scan of an int64 (all GNT threads call it).
+__device__ int64_t block_incl_scan(int64_t x, int64_t* sh, int64_t* total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int o = 1; o < 32; o <<= 1) {
+    int64_t y = __shfl_up_sync(0xffffffffu, (long long)x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sh[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    int64_t v = lane < GNT / 32 ? sh[lane] : 0;
+    int64_t vi = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      int64_t y = __shfl_up_sync(0xffffffffu, (long long)vi, o);
+      if (lane >= o) vi += y;
+    }
+    if (lane < GNT / 32) sh[lane] = vi - v;
+    if (lane == 31) sh[32] = vi;
+  }
+  __syncthreads();
+  x += sh[wid];
+  *total = sh[32];
+  __syncthreads();
+  return x;
+}
+
+__device__ int64_t block_sum(int64_t x, int64_t* sh) {
+  int64_t tot;
+  block_incl_scan(x, sh, &tot);
+  return tot;
+}
+
+__global__ void __launch_bounds__(GNT) k_ggg(GGGArgs a) {
+  __shared__ int64_t sh[33];
+  __shared__ uint64_t shh[GNT / 32];
+  __shared__ int32_t shv[GNT / 32];
+  __shared__ int64_t Wj_sh, accw_sh;
+  __shared__ int32_t nstep_sh, seed_sh;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  for (int32_t s = blockIdx.x; s < a.nslots; s += gridDim.x) {
+    const int64_t base = a.noff[s], n = a.noff[s + 1] - base;
+    const int32_t k = a.nlab[s];
+    const int64_t bo = a.boff[s], avg = a.avg[s];
+    const uint64_t tkey = a.tkey[s];
+    const int32_t lvl = a.level[s];
+    for (int64_t v = tid; v < n; v += GNT) a.label[base + v] = -1;
+    for (int32_t b = tid; b < k; b += GNT) a.W[bo + b] = 0;
+    __syncthreads();
+    for (int32_t j = 0; j < k; ++j) {
+      // seed: unassigned non-isolated node with the smallest hash
+      const uint64_t skey = hkey(tkey, PH_GGG, (uint64_t)lvl, (uint64_t)j);
+      uint64_t bh = ~0ull;
+      int32_t bv = -1;
+      for (int64_t v = tid; v < n; v += GNT) {
+        const int64_t gv = base + v;
+        if (a.label[gv] >= 0 || a.row_ptr[gv + 1] == a.row_ptr[gv]) continue;
+        const uint64_t h = mix64(skey ^ (uint64_t)v);
+        if (bv < 0 || h < bh) { bh = h; bv = (int32_t)v; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        uint64_t oh = __shfl_xor_sync(0xffffffffu, (unsigned long long)bh, o);
+        int32_t ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        if (ov >= 0 && (bv < 0 || oh < bh || (oh == bh && ov < bv))) { bh = oh; bv = ov; }
+      }
+      if (lane == 0) { shh[wid] = bh; shv[wid] = bv; }
+      __syncthreads();
+      if (tid == 0) {
+        uint64_t h = ~0ull;
+        int32_t v = -1;
+        for (int w = 0; w < GNT / 32; ++w)
+          if (shv[w] >= 0 && (v < 0 || shh[w] < h || (shh[w] == h && shv[w] < v))) {
+            h = shh[w]; v = shv[w];
+          }
+        seed_sh = v;
+      }
+      __syncthreads();
+      const int32_t seed = seed_sh;
+      if (seed < 0) break;
+      for (int64_t v = tid; v < n; v += GNT) a.conn[base + v] = 0;
+      __syncthreads();
+      if (tid == 0) {
+        a.label[base + seed] = (int32_t)(bo + j);
+        a.step[base] = (int32_t)(base + seed);
+        nstep_sh = 1;
+        Wj_sh = a.nw[base + seed];
+      }
+      __syncthreads();
+      while (true) {
+        // connections of unassigned nodes to the block grow with each step
+        const int32_t nstep = nstep_sh;
+        for (int32_t q = wid; q < nstep; q += GNT / 32) {
+          const int32_t u = a.step[base + q];
+          for (int64_t e = a.row_ptr[u] + lane; e < a.row_ptr[u + 1]; e += 32) {
+            const int32_t x = a.col[e];
+            if (a.label[x] < 0) atomicAdd(ull(&a.conn[x]), (unsigned long long)a.ew[e]);
+          }
+        }
+        __syncthreads();
+        const int64_t Wj = Wj_sh;
+        if (Wj >= avg) break;
+        if (tid == 0) accw_sh = 0;
+        // connected unassigned nodes in id order, longest prefix that fits
+        int64_t carry_w = 0;
+        int32_t carry_c = 0;
+        for (int64_t v0 = 0; v0 < n; v0 += GNT) {
+          const int64_t v = v0 + tid;
+          bool cand = false;
+          int64_t wt = 0;
+          if (v < n) {
+            const int64_t gv = base + v;
+            cand = a.label[gv] < 0 && a.conn[gv] > 0;
+            wt = cand ? a.nw[gv] : 0;
+          }
+          int64_t tw;
+          const int64_t iw = block_incl_scan(wt, sh, &tw);
+          const bool adm = cand && (Wj + carry_w + iw <= avg);
+          int64_t tc;
+          const int64_t ic = block_incl_scan(adm ? 1 : 0, sh, &tc);
+          if (adm) {
+            a.step[base + carry_c + ic - 1] = (int32_t)(base + v);
+            atomicAdd(ull(&accw_sh), (unsigned long long)wt);
+          }
+          carry_w += tw;
+          carry_c += (int32_t)tc;
+          if (Wj + carry_w > avg) break;   // no later candidate can fit
+        }
+        __syncthreads();
+        if (tid == 0) {
+          nstep_sh = carry_c;
+          Wj_sh = Wj + accw_sh;
+        }
+        __syncthreads();
+        const int32_t ns2 = nstep_sh;
+        if (ns2 == 0) break;
+        for (int32_t q = tid; q < ns2; q += GNT) a.label[a.step[base + q]] = (int32_t)(bo + j);
+        __syncthreads();
+      }
+      if (tid == 0) a.W[bo + j] = Wj_sh;
+      __syncthreads();
+    }
+    // water-filling of the nodes left unassigned
+    int64_t r = 0;
+    for (int64_t v = tid; v < n; v += GNT)
+      if (a.label[base + v] < 0) r += a.nw[base + v];
+    const int64_t R = block_sum(r, sh);
+    if (R > 0) {
+      if (tid == 0) {
+        int64_t lo = a.W[bo], hi = a.W[bo];
+        for (int32_t b = 1; b < k; ++b) { lo = min(lo, a.W[bo + b]); hi = max(hi, a.W[bo + b]); }
+        hi += R;
+        while (lo < hi) {
+          const int64_t mid = lo + (hi - lo) / 2;
+          int64_t f = 0;
+          for (int32_t b = 0; b < k; ++b) f += max64(0, mid - a.W[bo + b]);
+          if (f >= R) hi = mid; else lo = mid + 1;
+        }
+        const int64_t L = lo;
+        for (int32_t j = 0; j < k; ++j) {       // insertion sort by (W, id)
+          int32_t b = j;
+          int32_t p = j;
+          while (p > 0) {
+            const int32_t q = a.wforder[bo + p - 1];
+            if (a.W[bo + q] > a.W[bo + b] || (a.W[bo + q] == a.W[bo + b] && q > b)) {
+              a.wforder[bo + p] = q;
+              --p;
+            } else {
+              break;
+            }
+          }
+          a.wforder[bo + p] = b;
+        }
+        int64_t acc = 0;
+        for (int32_t j = 0; j < k; ++j) {
+          a.wfA[bo + j] = acc;
+          acc += max64(0, L - a.W[bo + a.wforder[bo + j]]);
+        }
+      }
+      __syncthreads();
+      int64_t carry = 0;
+      for (int64_t v0 = 0; v0 < n; v0 += GNT) {
+        const int64_t v = v0 + tid;
+        const bool left = v < n && a.label[base + v] < 0;
+        const int64_t wt = left ? a.nw[base + v] : 0;
+        int64_t tw;
+        const int64_t iw = block_incl_scan(wt, sh, &tw);
+        if (left) {
+          const int64_t p = carry + iw - wt;
+          int32_t lo = 0, hi = k - 1;               // last j with A[j] <= p
+          while (lo < hi) {
+            const int32_t mid = (lo + hi + 1) >> 1;
+            if (a.wfA[bo + mid] <= p) lo = mid; else hi = mid - 1;
+          }
+          const int32_t b = a.wforder[bo + lo];
+          a.label[base + v] = (int32_t)(bo + b);
+          atomicAdd(ull(&a.W[bo + b]), (unsigned long long)wt);
+        }
+        carry += tw;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_slot_cut(const int64_t* __restrict__ row_ptr,
+                                                  const int32_t* __restrict__ col,
+                                                  const int32_t* __restrict__ ew,
+                                                  const int32_t* __restrict__ gid,
+                                                  const int32_t* __restrict__ label, int64_t N,
+                                                  int64_t* __restrict__ cut2) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t v = warp; v < N; v += nwarps) {
+    const int32_t lv = label[v];
+    long long sum = 0;
+    for (int64_t e = row_ptr[v] + lane; e < row_ptr[v + 1]; e += 32)
+      if (label[col[e]] != lv) sum += ew[e];
+    sum = warp_sum_ll(sum);
+    if (lane == 0 && sum) atomicAdd(ull(&cut2[gid[v]]), (unsigned long long)sum);
+  }
+}
+
+__global__ void k_select_copy(const SelectTask* __restrict__ tasks, const int64_t* __restrict__ cut2,
+                              const int64_t* __restrict__ ip_W, const int64_t* __restrict__ ip_noff,
+                              const int64_t* __restrict__ ip_boff,
+                              const int32_t* __restrict__ ip_label, int64_t* __restrict__ Wg,
+                              int32_t* __restrict__ best, int64_t* __restrict__ ipcut) {
+  const SelectTask t = tasks[blockIdx.x];
+  __shared__ int32_t bt_sh;
+  if (threadIdx.x == 0) {
+    int64_t bo = -1, bc = -1;
+    int32_t bt = -1;
+    for (int32_t tr = 0; tr < t.trials; ++tr) {
+      const int64_t slot = t.slot0 + tr;
+      int64_t mx = 0;
+      for (int32_t b = 0; b < t.k; ++b) mx = max(mx, ip_W[ip_boff[slot] + b]);
+      const int64_t ov = max64(0, mx - t.Lmax);
+      const int64_t c = cut2[slot] / 2;
+      if (bt < 0 || ov < bo || (ov == bo && c < bc)) { bo = ov; bc = c; bt = tr; }
+    }
+    bt_sh = bt;
+    best[t.g] = bt;
+    ipcut[t.g] = bc;
+  }
+  __syncthreads();
+  const int64_t slot = t.slot0 + bt_sh;
+  const int64_t src = ip_noff[slot], sbo = ip_boff[slot];
+  for (int64_t v = threadIdx.x; v < t.n; v += blockDim.x)
+    t.dst_blk[t.dst_n0 + v] = (int32_t)(t.g_boff + (ip_label[src + v] - sbo));
+  for (int32_t b = threadIdx.x; b < t.k; b += blockDim.x) Wg[t.g_boff + b] = ip_W[sbo + b];
+}
+
+__global__ void k_project(const int32_t* __restrict__ cmap, const int32_t* __restrict__ cblk,
+                          int32_t* __restrict__ fblk, int64_t N) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t c = cmap[v];
+    if (c >= 0) fblk[v] = cblk[c];
+  }
+}
+
+__global__ void k_block_weights(const int32_t* __restrict__ label, const int32_t* __restrict__ nw,
+                                int64_t N, int64_t* __restrict__ W) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N;
+       v += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(ull(&W[label[v]]), (unsigned long long)nw[v]);
+}
+
+}  // namespace
+
+void ip_replicate(const std::vector<CopyTask>& tasks, int64_t* row_ptr, int32_t* col,
+                  int32_t* ew, int32_t* nw, int64_t M_total, cudaStream_t s) {
+  if (tasks.empty()) return;
+  DevBuf<CopyTask> d(tasks.size(), s);
+  d.upload(tasks);
+  int64_t mx = 1;
+  for (const auto& t : tasks) mx = std::max(mx, std::max(t.n, t.m));
+  for (size_t t0 = 0; t0 < tasks.size(); t0 += 65535) {
+    const unsigned ny = (unsigned)std::min<size_t>(65535, tasks.size() - t0);
+    dim3 grid(grid_for(mx, 256, 64), ny);
+    k_replicate<<<grid, 256, 0, s>>>(d.p + t0, row_ptr, col, ew, nw); SCLAP_NOTE_LAUNCH();
+  }
+  int64_t endv = M_total;
+  int64_t Ntot = 0;
+  for (const auto& t : tasks) Ntot = std::max(Ntot, t.dst_n0 + t.n);
+  SCLAP_CUDA(cudaMemcpyAsync(row_ptr + Ntot, &endv, sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  SCLAP_CUDA(cudaStreamSynchronize(s));   // endv lives on the host stack
+  SCLAP_LAUNCH_CHECK();
+}
+
+void ggg_trials(const GGGArgs& a, cudaStream_t s) {
+  if (a.nslots <= 0) return;
+  k_ggg<<<(unsigned)std::min<int64_t>(a.nslots, (int64_t)num_sms() * 8), GNT, 0, s>>>(a); SCLAP_NOTE_LAUNCH();
+  SCLAP_LAUNCH_CHECK();
+}
+
+void slot_cut(const LevelView& lv, const int32_t* label, int64_t* cut2, cudaStream_t s) {
+  if (lv.N <= 0) return;
+  k_slot_cut<<<grid_for(lv.N, 8, (int64_t)num_sms() * 16), 256, 0, s>>>(
+      lv.row_ptr, lv.col, lv.ew, lv.gid, label, lv.N, cut2); SCLAP_NOTE_LAUNCH();
+  SCLAP_LAUNCH_CHECK();
+}
+
+void ip_select_copy(const std::vector<SelectTask>& tasks, const int64_t* cut2,
+                    const int64_t* ip_W, const int64_t* ip_noff, const int64_t* ip_boff,
+                    const int32_t* ip_label, int64_t* Wg, int32_t* best, int64_t* ipcut,
+                    cudaStream_t s) {
+  if (tasks.empty()) return;
+  DevBuf<SelectTask> d(tasks.size(), s);
+  d.upload(tasks);
+  k_select_copy<<<(unsigned)tasks.size(), 256, 0, s>>>(d.p, cut2, ip_W, ip_noff, ip_boff,
+                                                       ip_label, Wg, best, ipcut); SCLAP_NOTE_LAUNCH();
+  SCLAP_LAUNCH_CHECK();
+  SCLAP_CUDA(cudaStreamSynchronize(s));   // the task array is freed on return
+}
+
+void project(const int32_t* cmap, const int32_t* coarse_blk, int32_t* fine_blk, int64_t N,
+             cudaStream_t s) {
+  if (N <= 0) return;
+  k_project<<<grid_for(N, 256, (int64_t)num_sms() * 16), 256, 0, s>>>(cmap, coarse_blk,
+                                                                      fine_blk, N); SCLAP_NOTE_LAUNCH();
+  SCLAP_LAUNCH_CHECK();
+}
+
+void block_weights(const int32_t* label, const int32_t* nw, int64_t N, int64_t* W,
+                   cudaStream_t s) {
+  if (N <= 0) return;
+  k_block_weights<<<grid_for(N, 256, (int64_t)num_sms() * 16), 256, 0, s>>>(label, nw, N, W); SCLAP_NOTE_LAUNCH();
+  SCLAP_LAUNCH_CHECK();
+}
+
+}  // namespace sclap

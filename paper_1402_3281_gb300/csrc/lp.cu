@@ -1,0 +1,851 @@
+// lp.cu -- one synchronous round of size-constrained label propagation
+// (Sec. 3.1), as clustering (bound U) or local search (bound Lmax, active
+// nodes, Sec. 4), over every slot of a batched level at once.
+//
+// A round splits the participating nodes into S colour classes by a per-node
+// hash; each class is a sub-round:
+//   propose  every node computes its connection to each neighbouring label
+//            (degree-bucketed: lane groups + warp match for small degrees,
+//            shared-memory hashes per warp or CTA, a global-memory hash for
+//            hubs) and proposes the strongest eligible label;
+//   resolve  a target whose proposals all fit admits them all; otherwise the
+//            proposals into it form a segment and one CTA admits the longest
+//            prefix in (gain desc, priority asc, node asc) order that fits;
+//   source   (local search) forced moves out of an overloaded block are capped
+//            at the block's excess the same way;
+//   apply    labels and label weights are updated with integer atomics
+//            (order-free, hence deterministic) and moved nodes activate their
+//            neighbours.
+#include "common.cuh"
+
+namespace sclap {
+namespace {
+
+struct LPArgs {
+  // level
+  const int64_t* row_ptr;
+  const int32_t* col;
+  const int32_t* ew;
+  const int32_t* nw;
+  const int32_t* gid;
+  // slots
+  const int64_t* noff;
+  const int64_t* loff;
+  const int64_t* bound;
+  uint64_t* rkey;
+  const int32_t* nlab;
+  int32_t* done;
+  int64_t* moved;
+  int32_t* rounds;
+  // state
+  int32_t* label;
+  int64_t* W;
+  int64_t* in_w;
+  int32_t mode;
+  int32_t S;
+  // sub-round lists and proposals
+  int32_t* list;
+  int32_t* prop_t;
+  uint64_t* prop_key;
+  int8_t* adm;
+  int8_t* stage;
+  int32_t* grp;
+  // overflow segments
+  int32_t* ovf_cnt;
+  int32_t* ovf_fill;
+  int64_t* ovf_base;
+  int64_t* ctr;          // [0] entry cursor, [1] segment count
+  int32_t* seg_g;
+  int64_t* seg_base;
+  int32_t* seg_cnt;
+  int64_t* seg_thr;
+  uint64_t* ent_key;
+  int32_t* ent_v;
+  int32_t* ent_w;
+  int32_t* ent_i;
+  // bucketing
+  int32_t* bcnt;
+  int32_t* bfill;
+  int64_t* boff;
+  int64_t* arcs;         // arcs scanned (statistics)
+  int64_t* karcs;        // arcs per (colour, bucket) key
+  // active nodes
+  const uint8_t* act_cur;
+  uint8_t* act_next;
+  int32_t* err;
+};
+
+struct NodeCtx {
+  int32_t v, slot, own, cv;
+  int64_t bound, loff, rs, re;
+  uint64_t hv;
+};
+
+__device__ __forceinline__ NodeCtx load_node(const LPArgs& a, int32_t v) {
+  NodeCtx c;
+  c.v = v;
+  c.slot = a.gid[v];
+  c.own = a.label[v];
+  c.cv = a.nw[v];
+  c.bound = a.bound[c.slot];
+  c.loff = a.loff[c.slot];
+  c.rs = a.row_ptr[v];
+  c.re = a.row_ptr[v + 1];
+  c.hv = mix64(a.rkey[c.slot] ^ (uint64_t)(v - a.noff[c.slot]));
+  return c;
+}
+
+__device__ __forceinline__ Cand make_cand(const NodeCtx& c, int32_t C, int64_t conn) {
+  const int32_t Cl = (int32_t)(C - c.loff);
+  return Cand{conn, mix64(c.hv ^ (uint64_t)(uint32_t)Cl), Cl};
+}
+
+__device__ __forceinline__ void write_prop(const LPArgs& a, int64_t i, const NodeCtx& c,
+                                           const Cand& best, int64_t own_conn, bool overloaded) {
+  const bool move = best.conn >= 0 && (overloaded || best.conn > own_conn);
+  if (move) {
+    const int32_t t = (int32_t)(c.loff + best.C);
+    a.prop_t[i] = t;
+    a.prop_key[i] = admission_key(best.conn - own_conn, (uint32_t)c.hv);
+    atomicAdd(ull(&a.in_w[t]), (unsigned long long)c.cv);
+  } else {
+    a.prop_t[i] = -1;
+  }
+}
+
+// ------------------------------------------------------------- round control
+__global__ void k_round_begin(LPArgs a, int32_t nslots, int32_t phase, int32_t r,
+                              const uint64_t* seed, const int32_t* level, int32_t raw_key) {
+  for (int32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < nslots;
+       s += gridDim.x * blockDim.x) {
+    if (a.done[s]) continue;
+    if (a.mode == MODE_REPAIR) {
+      int64_t mx = 0;
+      const int64_t lo = a.loff[s];
+      for (int32_t b = 0; b < a.nlab[s]; ++b) mx = max(mx, a.W[lo + b]);
+      if (mx <= a.bound[s]) { a.done[s] = 1; continue; }
+    }
+    a.rkey[s] = raw_key ? seed[s] : hkey(seed[s], (uint64_t)phase, (uint64_t)level[s], (uint64_t)r);
+    a.moved[s] = 0;
+  }
+}
+
+__global__ void k_round_end(LPArgs a, int32_t nslots, int32_t stop_rule) {
+  for (int32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < nslots;
+       s += gridDim.x * blockDim.x) {
+    if (a.done[s]) continue;
+    a.rounds[s] += 1;
+    const int64_t n = a.noff[s + 1] - a.noff[s];
+    if (stop_rule && 20 * a.moved[s] < n) a.done[s] = 1;
+  }
+}
+
+// ------------------------------------------------------------- bucketing
+// PASS 0 counts nodes per (colour, bucket); PASS 1 scatters them.
+template <int PASS>
+__global__ void __launch_bounds__(256) k_bucket(LPArgs a, int64_t N) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t base = w0 * 32; base < N; base += nw * 32) {
+    const int64_t v = base + lane;
+    int key = -1;
+    int64_t deg = 0;
+    if (v < N) {
+      const int32_t s = a.gid[v];
+      if (!a.done[s]) {
+        deg = a.row_ptr[v + 1] - a.row_ptr[v];
+        bool take, ov = false;
+        if (a.mode == MODE_CLUSTER) {
+          take = deg > 0 && (a.act_cur == nullptr || a.act_cur[v]);
+        } else {
+          ov = a.W[a.label[v]] > a.bound[s];
+          if (a.mode == MODE_REPAIR) take = ov;
+          else take = (a.act_cur == nullptr || a.act_cur[v]) && (deg > 0 || ov);
+        }
+        if (take) {
+          const uint64_t hv = mix64(a.rkey[s] ^ (uint64_t)(v - a.noff[s]));
+          const int sub = (int)((uint32_t)(hv >> 32) % (uint32_t)a.S);
+          key = sub * NB + bucket_of(deg, ov);
+        }
+      }
+    }
+    const unsigned mm = __match_any_sync(0xffffffffu, key);
+    const int leader = __ffs(mm) - 1;
+    if (PASS == 0) {
+      long long dsum = warp_sum_ll(key >= 0 ? deg : 0);
+      const int64_t ksum = match_sum(mm, key >= 0 ? (int32_t)deg : 0);
+      if (key >= 0 && lane == leader) {
+        atomicAdd(&a.bcnt[key], __popc(mm));
+        atomicAdd(ull(&a.karcs[key]), (unsigned long long)ksum);
+      }
+      if (lane == 0 && dsum) atomicAdd(ull(a.arcs), (unsigned long long)dsum);
+    } else {
+      int base_pos = 0;
+      if (key >= 0 && lane == leader) base_pos = atomicAdd(&a.bfill[key], __popc(mm));
+      base_pos = __shfl_sync(0xffffffffu, base_pos, leader);
+      if (key >= 0) {
+        const int rank = __popc(mm & ((1u << lane) - 1));
+        a.list[a.boff[key] + base_pos + rank] = (int32_t)v;
+      }
+    }
+  }
+}
+
+__global__ void k_bucket_offsets(LPArgs a, int nkeys) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    int64_t s = 0;
+    for (int j = 0; j < nkeys; ++j) {
+      a.boff[j] = s;
+      s += a.bcnt[j];
+      a.bfill[j] = 0;
+    }
+    a.boff[nkeys] = s;
+  }
+}
+
+// ------------------------------------------------------------- propose
+// Degrees <= G: one group of G lanes per node, one arc per lane; equal labels
+// are merged with a warp match and their weights summed.
+template <int G>
+__global__ void __launch_bounds__(256) k_propose_small(LPArgs a, int64_t lbeg, int64_t cnt) {
+  constexpr int GPW = 32 / G;
+  const int lane = threadIdx.x & 31, gw = lane / G, gl = lane % G;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t t0 = warp * GPW; t0 < cnt; t0 += nwarps * GPW) {
+    const int64_t li = t0 + gw;
+    const bool has = li < cnt;
+    const int64_t i = lbeg + li;
+    NodeCtx c{};
+    int32_t C = -1, w = 0;
+    bool valid = false;
+    if (has) {
+      c = load_node(a, a.list[i]);
+      if (gl < c.re - c.rs) {
+        valid = true;
+        const int32_t u = a.col[c.rs + gl];
+        w = a.ew[c.rs + gl];
+        C = a.label[u];
+      }
+    }
+    const uint64_t mk = ((uint64_t)gw << 32) | (uint32_t)C;
+    const unsigned mm = __match_any_sync(0xffffffffu, mk);
+    const int64_t conn = match_sum(mm, w);
+    const bool leader = lane == __ffs(mm) - 1;
+    long long oc = (valid && leader && C == c.own) ? conn : 0;
+    oc = warp_max_ll(oc, G);
+    Cand cd{-1, 0, 0};
+    if (valid && leader && C != c.own && a.W[C] + c.cv <= c.bound) cd = make_cand(c, C, conn);
+    cd = warp_best(cd, G);
+    if (has && gl == 0) write_prop(a, i, c, cd, oc, false);
+  }
+}
+
+// Open-addressing accumulation (linear probing, bounded).
+__device__ __forceinline__ void table_add(int32_t* keys, unsigned long long* vals, int logcap,
+                                          int32_t C, int64_t w, int32_t* err) {
+  const uint32_t mask = (1u << logcap) - 1;
+  uint32_t s = table_slot(C, logcap);
+  for (uint32_t p = 0; p <= mask; ++p) {
+    const int32_t k = atomicCAS(&keys[s], -1, C);
+    if (k == -1 || k == C) {
+      atomicAdd(&vals[s], (unsigned long long)w);
+      return;
+    }
+    s = (s + 1) & mask;
+  }
+  atomicOr(err, DERR_HASH_FULL);
+}
+
+__device__ __forceinline__ int64_t table_get(const int32_t* keys, const unsigned long long* vals,
+                                             int logcap, int32_t C) {
+  const uint32_t mask = (1u << logcap) - 1;
+  uint32_t s = table_slot(C, logcap);
+  for (uint32_t p = 0; p <= mask; ++p) {
+    const int32_t k = keys[s];
+    if (k == C) return (int64_t)vals[s];
+    if (k == -1) return 0;
+    s = (s + 1) & mask;
+  }
+  return 0;
+}
+
+// Adds the arcs [rs, re) of a node into the table; the whole warp calls it
+// with the same range (lanes stride over the arcs; equal labels within one
+// stride are pre-merged by a warp match).
+__device__ __forceinline__ void accumulate_arcs(const LPArgs& a, int64_t rs, int64_t re,
+                                                int first_lane, int lanes, int32_t* keys,
+                                                unsigned long long* vals, int logcap) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t e0 = rs; e0 < re; e0 += lanes) {
+    const int64_t e = e0 + first_lane + lane;
+    const bool valid = e < re;
+    int32_t C = -1, w = 0;
+    if (valid) {
+      w = a.ew[e];
+      C = a.label[a.col[e]];
+    }
+    const unsigned mm = __match_any_sync(0xffffffffu, C);
+    const int64_t sum = match_sum(mm, w);
+    if (valid && lane == __ffs(mm) - 1) table_add(keys, vals, logcap, C, sum, a.err);
+  }
+}
+
+// Degrees in (32, 512], and small-degree nodes of overloaded blocks: one warp
+// per node, a 1024-slot table per warp in shared memory.
+__global__ void __launch_bounds__(256) k_propose_warp(LPArgs a, int64_t lbeg, int64_t cnt) {
+  extern __shared__ unsigned long long smem_u64[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  unsigned long long* vals = smem_u64 + wib * WARP_HASH_SLOTS;
+  int32_t* keys = reinterpret_cast<int32_t*>(smem_u64 + 8 * WARP_HASH_SLOTS) + wib * WARP_HASH_SLOTS;
+  for (int j = lane; j < WARP_HASH_SLOTS; j += 32) { keys[j] = -1; vals[j] = 0; }
+  __syncwarp();
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t li = warp; li < cnt; li += nwarps) {
+    const int64_t i = lbeg + li;
+    const NodeCtx c = load_node(a, a.list[i]);
+    const int64_t deg = c.re - c.rs;
+    const int logcap = ceil_log2(max64(2 * deg, 32));
+    const int cap = 1 << logcap;
+    accumulate_arcs(a, c.rs, c.re, 0, 32, keys, vals, logcap);
+    __syncwarp();
+    const bool ov = a.mode != MODE_CLUSTER && a.W[c.own] > c.bound;
+    long long oc = 0;
+    Cand cd{-1, 0, 0};
+    for (int j = lane; j < cap; j += 32) {
+      const int32_t K = keys[j];
+      if (K == -1) continue;
+      const int64_t conn = (int64_t)vals[j];
+      if (K == c.own) oc = conn;
+      else if (!ov && a.W[K] + c.cv <= c.bound) {
+        Cand x = make_cand(c, K, conn);
+        if (cd.conn < 0 || cand_better(x, cd)) cd = x;
+      }
+    }
+    if (ov) {
+      const int32_t nl = a.nlab[c.slot];
+      for (int32_t b = lane; b < nl; b += 32) {
+        const int32_t C = (int32_t)(c.loff + b);
+        if (C == c.own || a.W[C] + c.cv > c.bound) continue;
+        Cand x = make_cand(c, C, table_get(keys, vals, logcap, C));
+        if (cd.conn < 0 || cand_better(x, cd)) cd = x;
+      }
+    }
+    __syncwarp();
+    for (int j = lane; j < cap; j += 32) { keys[j] = -1; vals[j] = 0; }
+    oc = warp_max_ll(oc);
+    cd = warp_best(cd);
+    __syncwarp();
+    if (lane == 0) write_prop(a, i, c, cd, oc, ov);
+  }
+}
+
+template <int NT>
+__device__ void block_reduce(long long& oc, Cand& cd, long long* sh_oc, Cand* sh_cd) {
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  oc = warp_max_ll(oc);
+  cd = warp_best(cd);
+  if (lane == 0) { sh_oc[wib] = oc; sh_cd[wib] = cd; }
+  __syncthreads();
+  if (wib == 0) {
+    oc = lane < NT / 32 ? sh_oc[lane] : 0;
+    cd = lane < NT / 32 ? sh_cd[lane] : Cand{-1, 0, 0};
+    oc = warp_max_ll(oc);
+    cd = warp_best(cd);
+  }
+}
+
+// Degrees above 512: one CTA per node; the table lives in shared memory
+// (degree <= 4096) or in a per-CTA region of global scratch (hubs).
+template <bool GLOBAL>
+__global__ void __launch_bounds__(512) k_propose_cta(LPArgs a, int64_t lbeg, int64_t cnt,
+                                                     int32_t* gkeys, unsigned long long* gvals,
+                                                     int64_t gcap) {
+  constexpr int NT = 512;
+  extern __shared__ unsigned long long smem_u64[];
+  __shared__ long long sh_oc[NT / 32];
+  __shared__ Cand sh_cd[NT / 32];
+  const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
+  unsigned long long* vals;
+  int32_t* keys;
+  if (GLOBAL) {
+    vals = gvals + (int64_t)blockIdx.x * gcap;
+    keys = gkeys + (int64_t)blockIdx.x * gcap;
+  } else {
+    vals = smem_u64;
+    keys = reinterpret_cast<int32_t*>(smem_u64 + CTA_HASH_SLOTS);
+    for (int j = tid; j < CTA_HASH_SLOTS; j += NT) { keys[j] = -1; vals[j] = 0; }
+    __syncthreads();
+  }
+  for (int64_t li = blockIdx.x; li < cnt; li += gridDim.x) {
+    const int64_t i = lbeg + li;
+    const NodeCtx c = load_node(a, a.list[i]);
+    const int64_t deg = c.re - c.rs;
+    const int logcap = ceil_log2(max64(2 * deg, 32));
+    const int64_t cap = (int64_t)1 << logcap;
+    accumulate_arcs(a, c.rs, c.re, wib * 32, NT, keys, vals, logcap);
+    __syncthreads();
+    const bool ov = a.mode != MODE_CLUSTER && a.W[c.own] > c.bound;
+    long long oc = 0;
+    Cand cd{-1, 0, 0};
+    for (int64_t j = tid; j < cap; j += NT) {
+      const int32_t K = keys[j];
+      if (K == -1) continue;
+      const int64_t conn = (int64_t)vals[j];
+      if (K == c.own) oc = conn;
+      else if (!ov && a.W[K] + c.cv <= c.bound) {
+        Cand x = make_cand(c, K, conn);
+        if (cd.conn < 0 || cand_better(x, cd)) cd = x;
+      }
+    }
+    if (ov) {
+      const int32_t nl = a.nlab[c.slot];
+      for (int32_t b = tid; b < nl; b += NT) {
+        const int32_t C = (int32_t)(c.loff + b);
+        if (C == c.own || a.W[C] + c.cv > c.bound) continue;
+        Cand x = make_cand(c, C, table_get(keys, vals, logcap, C));
+        if (cd.conn < 0 || cand_better(x, cd)) cd = x;
+      }
+    }
+    __syncthreads();
+    for (int64_t j = tid; j < cap; j += NT) { keys[j] = -1; vals[j] = 0; }
+    block_reduce<NT>(oc, cd, sh_oc, sh_cd);
+    if (tid == 0) write_prop(a, i, c, cd, oc, ov);
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------- admission
+__global__ void k_resolve(LPArgs a, int64_t lbeg, int64_t cnt) {
+  for (int64_t li = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; li < cnt;
+       li += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = lbeg + li;
+    const int32_t t = a.prop_t[i];
+    a.stage[i] = 0;
+    if (t < 0) { a.adm[i] = 0; continue; }
+    const int32_t s = a.gid[a.list[i]];
+    if (a.W[t] + a.in_w[t] <= a.bound[s]) {
+      a.adm[i] = 1;
+    } else {
+      a.adm[i] = 0;
+      a.grp[i] = t;
+      const int c = atomicAdd(&a.ovf_cnt[t], 1);
+      a.stage[i] = c == 0 ? 2 : 1;
+    }
+  }
+}
+
+// Forced moves out of overloaded blocks (local search), grouped by source.
+__global__ void k_forced(LPArgs a, int64_t lbeg, int64_t cnt) {
+  for (int64_t li = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; li < cnt;
+       li += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = lbeg + li;
+    a.stage[i] = 0;
+    if (a.adm[i] != 1) continue;
+    const int32_t v = a.list[i];
+    const int32_t own = a.label[v];
+    if (a.W[own] > a.bound[a.gid[v]]) {
+      a.grp[i] = own;
+      const int c = atomicAdd(&a.ovf_cnt[own], 1);
+      a.stage[i] = c == 0 ? 2 : 1;
+    }
+  }
+}
+
+// One leader per group allocates the group's segment.  thr: target side,
+// admit while the inclusive prefix <= bound - W[t]; source side, admit while
+// the exclusive prefix <= W[src] - bound - 1.
+__global__ void k_ovf_alloc(LPArgs a, int64_t lbeg, int64_t cnt, int32_t source) {
+  for (int64_t li = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; li < cnt;
+       li += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = lbeg + li;
+    if (a.stage[i] != 2) continue;
+    const int32_t g = a.grp[i];
+    const int32_t n = a.ovf_cnt[g];
+    const int64_t base = (int64_t)atomicAdd(ull(&a.ctr[0]), (unsigned long long)n);
+    a.ovf_base[g] = base;
+    const int64_t seg = (int64_t)atomicAdd(ull(&a.ctr[1]), 1ull);
+    const int64_t bound = a.bound[a.gid[a.list[i]]];
+    a.seg_g[seg] = g;
+    a.seg_base[seg] = base;
+    a.seg_cnt[seg] = n;
+    a.seg_thr[seg] = source ? (a.W[g] - bound - 1) : (bound - a.W[g]);
+  }
+}
+
+__global__ void k_ovf_scatter(LPArgs a, int64_t lbeg, int64_t cnt) {
+  for (int64_t li = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; li < cnt;
+       li += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = lbeg + li;
+    if (a.stage[i] == 0) continue;
+    const int32_t g = a.grp[i];
+    const int64_t pos = a.ovf_base[g] + atomicAdd(&a.ovf_fill[g], 1);
+    const int32_t v = a.list[i];
+    a.ent_key[pos] = a.prop_key[i];
+    a.ent_v[pos] = v;
+    a.ent_w[pos] = a.nw[v];
+    a.ent_i[pos] = (int32_t)(i);
+  }
+}
+
+constexpr int SEL_NT = 256;
+constexpr int SEL_SMALL = 1024;
+
+__device__ __forceinline__ bool key_less(uint64_t k1, int32_t v1, uint64_t k2, int32_t v2) {
+  return k1 < k2 || (k1 == k2 && v1 < v2);
+}
+__device__ __forceinline__ uint32_t digit_of(uint64_t k, int32_t v, int p) {
+  return p < 8 ? (uint32_t)(k >> (56 - 8 * p)) & 0xffu
+               : ((uint32_t)v >> (24 - 8 * (p - 8))) & 0xffu;
+}
+__device__ __forceinline__ bool prefix_match(uint64_t k, int32_t v, uint64_t PK, uint32_t PV,
+                                             int p) {
+  if (p == 0) return true;
+  if (p <= 8) return (k >> (64 - 8 * p)) == (PK >> (64 - 8 * p));
+  if (k != PK) return false;
+  const int b = 8 * (p - 8);
+  return ((uint32_t)v >> (32 - b)) == (PV >> (32 - b));
+}
+
+// Admission inside one overflowing group: entries ordered by (key, node);
+// target side admits while the inclusive prefix weight <= thr, source side
+// while the exclusive prefix weight <= thr.  Small groups compare all
+// pairs in shared memory; large ones locate the boundary entry by an MSD
+// radix select over the 96-bit (key, node) order with weight histograms.
+__global__ void __launch_bounds__(SEL_NT) k_ovf_select(LPArgs a, int32_t source) {
+  __shared__ uint64_t sk[SEL_SMALL];
+  __shared__ int32_t sv[SEL_SMALL];
+  __shared__ int32_t sw[SEL_SMALL];
+  __shared__ unsigned long long hist[256];
+  __shared__ uint64_t PK;
+  __shared__ uint32_t PV;
+  __shared__ long long acc_sh;
+  __shared__ int found_sh;
+  const int tid = threadIdx.x;
+  const int64_t nseg = a.ctr[1];
+  for (int64_t sg = blockIdx.x; sg < nseg; sg += gridDim.x) {
+    const int64_t base = a.seg_base[sg];
+    const int32_t n = a.seg_cnt[sg];
+    const int64_t thr = a.seg_thr[sg];
+    if (n <= SEL_SMALL) {
+      for (int j = tid; j < n; j += SEL_NT) {
+        sk[j] = a.ent_key[base + j];
+        sv[j] = a.ent_v[base + j];
+        sw[j] = a.ent_w[base + j];
+      }
+      __syncthreads();
+      for (int j = tid; j < n; j += SEL_NT) {
+        int64_t excl = 0;
+        const uint64_t kj = sk[j];
+        const int32_t vj = sv[j];
+        for (int l = 0; l < n; ++l)
+          if (key_less(sk[l], sv[l], kj, vj)) excl += sw[l];
+        const bool ok = source ? (excl <= thr) : (excl + sw[j] <= thr);
+        a.adm[a.ent_i[base + j]] = ok ? 1 : 0;
+      }
+      __syncthreads();
+    } else {
+      if (tid == 0) { PK = 0; PV = 0; acc_sh = 0; found_sh = 1; }
+      __syncthreads();
+      for (int p = 0; p < 12; ++p) {
+        for (int j = tid; j < 256; j += SEL_NT) hist[j] = 0;
+        __syncthreads();
+        const uint64_t pk = PK;
+        const uint32_t pv = PV;
+        for (int64_t j = tid; j < n; j += SEL_NT) {
+          const uint64_t k = a.ent_key[base + j];
+          const int32_t v = a.ent_v[base + j];
+          if (prefix_match(k, v, pk, pv, p))
+            atomicAdd(&hist[digit_of(k, v, p)], (unsigned long long)a.ent_w[base + j]);
+        }
+        __syncthreads();
+        if (tid == 0) {
+          long long acc = acc_sh;
+          int x = -1;
+          for (int d = 0; d < 256; ++d) {
+            if (acc + (long long)hist[d] > thr) { x = d; break; }
+            acc += (long long)hist[d];
+          }
+          if (x < 0) {
+            found_sh = 0;   // every remaining entry fits
+          } else {
+            acc_sh = acc;
+            if (p < 8) PK |= (uint64_t)x << (56 - 8 * p);
+            else PV |= (uint32_t)x << (24 - 8 * (p - 8));
+          }
+        }
+        __syncthreads();
+        if (!found_sh) break;
+      }
+      const int found = found_sh;
+      const uint64_t pk = PK;
+      const int32_t pv = (int32_t)PV;
+      for (int64_t j = tid; j < n; j += SEL_NT) {
+        const uint64_t k = a.ent_key[base + j];
+        const int32_t v = a.ent_v[base + j];
+        bool ok;
+        if (!found) ok = true;
+        else if (source) ok = key_less(k, v, pk, pv) || (k == pk && v == pv);
+        else ok = key_less(k, v, pk, pv);
+        a.adm[a.ent_i[base + j]] = ok ? 1 : 0;
+      }
+      __syncthreads();
+    }
+    if (tid == 0) {
+      const int32_t g = a.seg_g[sg];
+      a.ovf_cnt[g] = 0;
+      a.ovf_fill[g] = 0;
+    }
+  }
+}
+
+// ------------------------------------------------------------- apply
+__global__ void __launch_bounds__(256) k_apply(LPArgs a, int64_t lbeg, int64_t cnt) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t b0 = w0 * 32; b0 < cnt; b0 += nw * 32) {
+    const int64_t li = b0 + lane;
+    int32_t slot = -1;
+    if (li < cnt) {
+      const int64_t i = lbeg + li;
+      const int32_t t = a.prop_t[i];
+      if (t >= 0) {
+        a.in_w[t] = 0;
+        if (a.adm[i]) {
+          const int32_t v = a.list[i];
+          const int32_t own = a.label[v];
+          const int64_t cv = a.nw[v];
+          a.label[v] = t;
+          atomicAdd(ull(&a.W[t]), (unsigned long long)cv);
+          atomicAdd(ull(&a.W[own]), (unsigned long long)(-cv));
+          slot = a.gid[v];
+          if (a.act_next)
+            for (int64_t e = a.row_ptr[v]; e < a.row_ptr[v + 1]; ++e) a.act_next[a.col[e]] = 1;
+        }
+      }
+    }
+    const unsigned mm = __match_any_sync(0xffffffffu, slot);
+    if (slot >= 0 && lane == __ffs(mm) - 1)
+      atomicAdd(ull(&a.moved[slot]), (unsigned long long)__popc(mm));
+  }
+}
+
+// Reused CUDA events for the profiling brackets.
+std::mutex g_event_mu;
+std::vector<cudaEvent_t> g_events;
+cudaEvent_t event_from_pool() {
+  std::lock_guard<std::mutex> lk(g_event_mu);
+  if (!g_events.empty()) {
+    cudaEvent_t e = g_events.back();
+    g_events.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  SCLAP_CUDA(cudaEventCreate(&e));
+  return e;
+}
+void event_to_pool(cudaEvent_t e) {
+  std::lock_guard<std::mutex> lk(g_event_mu);
+  g_events.push_back(e);
+}
+
+}  // namespace
+
+ProfileState& profile() {
+  static ProfileState p;
+  return p;
+}
+
+// ---------------------------------------------------------------------------
+// Host driver of the rounds.
+// ---------------------------------------------------------------------------
+int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, int64_t* W,
+               int64_t Wsize, const LPRun& run, int32_t* d_err, cudaStream_t s,
+               const uint8_t* active_init, uint8_t* active_next_out) {
+  const int64_t N = lv.N;
+  if (N == 0 || run.rounds <= 0) return 0;
+  const int S = run.sub_rounds;
+  const int nkeys = S * NB;
+  const int sms = num_sms();
+
+  DevBuf<int64_t> in_w((size_t)Wsize, s), ovf_base((size_t)Wsize, s);
+  DevBuf<int32_t> ovf_cnt((size_t)Wsize, s), ovf_fill((size_t)Wsize, s);
+  in_w.zero(); ovf_cnt.zero(); ovf_fill.zero();
+  DevBuf<int32_t> list(N, s), prop_t(N, s), grp(N, s), seg_g(N, s), seg_cnt(N, s);
+  DevBuf<uint64_t> prop_key(N, s), ent_key(N, s);
+  DevBuf<int8_t> adm(N, s), stage(N, s);
+  DevBuf<int64_t> seg_base(N, s), seg_thr(N, s);
+  DevBuf<int32_t> ent_v(N, s), ent_w(N, s), ent_i(N, s);
+  DevBuf<int64_t> ctr(2, s);
+  DevBuf<int32_t> bcnt(nkeys, s), bfill(nkeys, s);
+  DevBuf<int64_t> boff(nkeys + 1, s), arcs(1, s), karcs(nkeys, s);
+  bfill.zero(); arcs.zero();
+
+  const bool track_active = run.use_active || active_init != nullptr || active_next_out != nullptr;
+  DevBuf<uint8_t> act_a, act_b;
+  if (track_active) {
+    act_a.alloc(N, s);
+    act_b.alloc(N, s);
+    if (active_init) SCLAP_CUDA(cudaMemcpyAsync(act_a.p, active_init, N, cudaMemcpyDeviceToDevice, s));
+    else act_a.fill_bytes(1);
+    act_b.zero();
+  }
+
+  // Global hash scratch for hub nodes: one region per CTA, sized for the
+  // largest degree of the level.
+  int64_t maxdeg = 0;
+  int64_t gcap = 0;
+  DevBuf<int32_t> gkeys;
+  DevBuf<unsigned long long> gvals;
+  int gblocks = 0;
+
+  LPArgs a{};
+  a.row_ptr = lv.row_ptr; a.col = lv.col; a.ew = lv.ew; a.nw = lv.nw; a.gid = lv.gid;
+  a.noff = sp.noff; a.loff = sp.loff; a.bound = sp.bound; a.rkey = sp.rkey; a.nlab = sp.nlab;
+  a.done = sp.done; a.moved = sp.moved; a.rounds = sp.rounds;
+  a.label = label; a.W = W; a.in_w = in_w.p; a.mode = run.mode; a.S = S;
+  a.list = list.p; a.prop_t = prop_t.p; a.prop_key = prop_key.p; a.adm = adm.p; a.stage = stage.p;
+  a.grp = grp.p; a.ovf_cnt = ovf_cnt.p; a.ovf_fill = ovf_fill.p; a.ovf_base = ovf_base.p;
+  a.ctr = ctr.p; a.seg_g = seg_g.p; a.seg_base = seg_base.p; a.seg_cnt = seg_cnt.p;
+  a.seg_thr = seg_thr.p; a.ent_key = ent_key.p; a.ent_v = ent_v.p; a.ent_w = ent_w.p;
+  a.ent_i = ent_i.p; a.bcnt = bcnt.p; a.bfill = bfill.p; a.boff = boff.p; a.arcs = arcs.p;
+  a.karcs = karcs.p;
+  a.err = d_err;
+
+  std::vector<int64_t> hoff(nkeys + 1), hkarcs(nkeys);
+  const bool prof = profile().enabled.load();
+  struct Timed { int bucket; cudaEvent_t a, b; };
+  std::vector<Timed> timed;
+  int64_t pn[NB] = {}, pa[NB] = {};
+  const unsigned small_grid = (unsigned)(sms * 8);
+  const size_t warp_smem = 8 * WARP_HASH_SLOTS * (sizeof(unsigned long long) + sizeof(int32_t));
+  const size_t cta_smem = CTA_HASH_SLOTS * (sizeof(unsigned long long) + sizeof(int32_t));
+  static bool attrs_set = false;
+  if (!attrs_set) {
+    SCLAP_CUDA(cudaFuncSetAttribute(k_propose_warp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)warp_smem));
+    SCLAP_CUDA(cudaFuncSetAttribute(k_propose_cta<false>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cta_smem));
+    attrs_set = true;
+  }
+
+  for (int r = 0; r < run.rounds; ++r) {
+    a.act_cur = track_active ? act_a.p : nullptr;
+    a.act_next = track_active ? act_b.p : nullptr;
+    k_round_begin<<<grid_for(sp.nslots, 128, 1024), 128, 0, s>>>(a, sp.nslots, run.phase, r,
+                                                                  sp.seed, sp.level,
+                                                                  run.raw_key ? 1 : 0); SCLAP_NOTE_LAUNCH();
+    bcnt.zero();
+    karcs.zero();
+    const unsigned bgrid = grid_for(N, 256, (int64_t)sms * 16);
+    k_bucket<0><<<bgrid, 256, 0, s>>>(a, N); SCLAP_NOTE_LAUNCH();
+    k_bucket_offsets<<<1, 32, 0, s>>>(a, nkeys); SCLAP_NOTE_LAUNCH();
+    k_bucket<1><<<bgrid, 256, 0, s>>>(a, N); SCLAP_NOTE_LAUNCH();
+    SCLAP_LAUNCH_CHECK();
+    SCLAP_CUDA(cudaMemcpyAsync(hoff.data(), boff.p, (nkeys + 1) * sizeof(int64_t),
+                               cudaMemcpyDeviceToHost, s));
+    if (prof)
+      SCLAP_CUDA(cudaMemcpyAsync(hkarcs.data(), karcs.p, nkeys * sizeof(int64_t),
+                                 cudaMemcpyDeviceToHost, s));
+    SCLAP_CUDA(cudaStreamSynchronize(s));
+    if (hoff[nkeys] == 0) {
+      k_round_end<<<grid_for(sp.nslots, 128, 1024), 128, 0, s>>>(a, sp.nslots,
+                                                                  run.stop_rule ? 1 : 0); SCLAP_NOTE_LAUNCH();
+      break;
+    }
+    // global hash scratch for the hub bucket, sized on first need
+    int64_t nhub = 0;
+    for (int sub = 0; sub < S; ++sub) nhub += hoff[sub * NB + 6 + 1] - hoff[sub * NB + 6];
+    if (nhub > 0 && gcap == 0) {
+      // largest degree of the level, read once
+      DevBuf<int64_t> dmax(1, s);
+      dmax.zero();
+      level_max_degree(lv.row_ptr, N, dmax.p, s);
+      SCLAP_CUDA(cudaMemcpyAsync(&maxdeg, dmax.p, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+      SCLAP_CUDA(cudaStreamSynchronize(s));
+      gcap = (int64_t)1 << ceil_log2(std::max<int64_t>(2 * maxdeg, 32));
+      gblocks = std::max(1, std::min(sms * 2, (int)std::min<int64_t>(nhub * 4, 1 << 20)));
+      gkeys.alloc((size_t)(gblocks * gcap), s);
+      gvals.alloc((size_t)(gblocks * gcap), s);
+      gkeys.fill_bytes(0xff);
+      gvals.zero();
+    }
+    for (int sub = 0; sub < S; ++sub) {
+      const int64_t lbeg = hoff[sub * NB], lend = hoff[(sub + 1) * NB];
+      const int64_t cnt = lend - lbeg;
+      if (cnt == 0) continue;
+      for (int b = 0; b < NB; ++b) {
+        const int64_t bb = hoff[sub * NB + b], bc = hoff[sub * NB + b + 1] - bb;
+        if (bc == 0) continue;
+        Timed tm{b, nullptr, nullptr};
+        if (prof) {
+          tm.a = event_from_pool();
+          tm.b = event_from_pool();
+          SCLAP_CUDA(cudaEventRecord(tm.a, s));
+          pn[b] += bc;
+          pa[b] += hkarcs[sub * NB + b];
+        }
+        switch (b) {
+          case 0: k_propose_small<4><<<grid_for(bc, 64, small_grid), 256, 0, s>>>(a, bb, bc); SCLAP_NOTE_LAUNCH(); break;
+          case 1: k_propose_small<8><<<grid_for(bc, 32, small_grid), 256, 0, s>>>(a, bb, bc); SCLAP_NOTE_LAUNCH(); break;
+          case 2: k_propose_small<16><<<grid_for(bc, 16, small_grid), 256, 0, s>>>(a, bb, bc); SCLAP_NOTE_LAUNCH(); break;
+          case 3: k_propose_small<32><<<grid_for(bc, 8, small_grid), 256, 0, s>>>(a, bb, bc); SCLAP_NOTE_LAUNCH(); break;
+          case 4: k_propose_warp<<<grid_for(bc, 8, (int64_t)sms * 2), 256, warp_smem, s>>>(a, bb, bc); SCLAP_NOTE_LAUNCH(); break;
+          case 5: k_propose_cta<false><<<grid_for(bc, 1, (int64_t)sms * 2), 512, cta_smem, s>>>(
+                      a, bb, bc, nullptr, nullptr, 0); SCLAP_NOTE_LAUNCH(); break;
+          default: k_propose_cta<true><<<(unsigned)std::min<int64_t>(bc, gblocks), 512, 0, s>>>(
+                      a, bb, bc, gkeys.p, gvals.p, gcap); SCLAP_NOTE_LAUNCH(); break;
+        }
+        if (prof) {
+          SCLAP_CUDA(cudaEventRecord(tm.b, s));
+          timed.push_back(tm);
+        }
+      }
+      const unsigned lg = grid_for(cnt, 256, (int64_t)sms * 16);
+      k_resolve<<<lg, 256, 0, s>>>(a, lbeg, cnt); SCLAP_NOTE_LAUNCH();
+      ctr.zero();
+      k_ovf_alloc<<<lg, 256, 0, s>>>(a, lbeg, cnt, 0); SCLAP_NOTE_LAUNCH();
+      k_ovf_scatter<<<lg, 256, 0, s>>>(a, lbeg, cnt); SCLAP_NOTE_LAUNCH();
+      k_ovf_select<<<(unsigned)(sms * 4), SEL_NT, 0, s>>>(a, 0); SCLAP_NOTE_LAUNCH();
+      if (run.mode != MODE_CLUSTER) {
+        k_forced<<<lg, 256, 0, s>>>(a, lbeg, cnt); SCLAP_NOTE_LAUNCH();
+        ctr.zero();
+        k_ovf_alloc<<<lg, 256, 0, s>>>(a, lbeg, cnt, 1); SCLAP_NOTE_LAUNCH();
+        k_ovf_scatter<<<lg, 256, 0, s>>>(a, lbeg, cnt); SCLAP_NOTE_LAUNCH();
+        k_ovf_select<<<(unsigned)(sms * 4), SEL_NT, 0, s>>>(a, 1); SCLAP_NOTE_LAUNCH();
+      }
+      k_apply<<<lg, 256, 0, s>>>(a, lbeg, cnt); SCLAP_NOTE_LAUNCH();
+      SCLAP_LAUNCH_CHECK();
+    }
+    k_round_end<<<grid_for(sp.nslots, 128, 1024), 128, 0, s>>>(a, sp.nslots,
+                                                                run.stop_rule ? 1 : 0); SCLAP_NOTE_LAUNCH();
+    SCLAP_LAUNCH_CHECK();
+    if (track_active && r + 1 < run.rounds) {
+      std::swap(act_a, act_b);
+      act_b.zero();
+    }
+  }
+  if (active_next_out && track_active)
+    SCLAP_CUDA(cudaMemcpyAsync(active_next_out, act_b.p, N, cudaMemcpyDeviceToDevice, s));
+  int64_t h_arcs = 0;
+  SCLAP_CUDA(cudaMemcpyAsync(&h_arcs, arcs.p, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  SCLAP_CUDA(cudaStreamSynchronize(s));
+  if (prof) {
+    ProfileState& P = profile();
+    std::lock_guard<std::mutex> lk(P.mu);
+    for (const Timed& t : timed) {
+      float ms = 0.f;
+      SCLAP_CUDA(cudaEventElapsedTime(&ms, t.a, t.b));
+      P.ms[t.bucket] += ms;
+      P.nlaunch[t.bucket] += 1;
+    }
+    for (int b = 0; b < NB; ++b) { P.nodes[b] += pn[b]; P.arcs[b] += pa[b]; }
+    for (const Timed& t : timed) { event_to_pool(t.a); event_to_pool(t.b); }
+  }
+  return h_arcs;
+}
+
+}  // namespace sclap

@@ -1,0 +1,342 @@
+"""Python binding of the C ABI in include/sclap.h (ctypes).
+
+Argument marshalling only: every step runs in libsclap.so's CUDA kernels.
+Host arrays are numpy arrays; device arrays are CUDA torch tensors.  Loading
+fails loudly if the library has not been built (there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsclap.so")
+
+OK, EINVAL, ECSR, ENOMEM, ECUDA, EOVERFLOW, EINFEASIBLE, ETIMEOUT, EINTERNAL = (
+    0, -1, -2, -3, -4, -5, -6, -7, -8)
+MODE_CLUSTER, MODE_REFINE = 0, 1
+PH_REFINE, PH_IPREF = 2, 5
+
+SYMBOLS = (
+    "sclap_default_config", "sclap_error_string", "sclap_last_error", "sclap_partition",
+    "sclap_partition_device", "sclap_partition_batch", "sclap_lp_round", "sclap_cluster",
+    "sclap_contract", "sclap_initial_partition", "sclap_refine", "sclap_cut",
+    "sclap_profile_enable", "sclap_profile_reset", "sclap_profile_read",
+)
+
+
+class SclapError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        msg = _lib().sclap_error_string(code).decode()
+        detail = _lib().sclap_last_error().decode()
+        super().__init__(f"{where}: {msg} ({code}){': ' + detail if detail else ''}")
+        self.code = code
+
+
+class Config(C.Structure):
+    _fields_ = [(n, C.c_int32) for n in (
+        "lp_rounds_coarse", "lp_rounds_refine", "f", "coarse_min_nodes", "ip_trials",
+        "sub_rounds", "repair_rounds", "max_levels")]
+
+
+class Stats(C.Structure):
+    _fields_ = [("levels", C.c_int32), ("level_n", C.c_int64 * 64), ("level_m", C.c_int64 * 64),
+                ("cluster_rounds", C.c_int32 * 64), ("refine_rounds", C.c_int32 * 64),
+                ("ip_best_trial", C.c_int32), ("ip_cut", C.c_int64), ("Lmax", C.c_int64),
+                ("U", C.c_int64), ("lp_arcs", C.c_int64)]
+
+    def to_dict(self) -> dict:
+        L = self.levels
+        return dict(levels=L, level_n=list(self.level_n[:L]), level_m=list(self.level_m[:L]),
+                    cluster_rounds=list(self.cluster_rounds[:L]),
+                    refine_rounds=list(self.refine_rounds[:L]),
+                    ip_best_trial=self.ip_best_trial, ip_cut=self.ip_cut, Lmax=self.Lmax,
+                    U=self.U, lp_arcs=self.lp_arcs)
+
+
+class Profile(C.Structure):
+    _fields_ = [("kernel_launches", C.c_int64), ("propose_launches", C.c_int64 * 7),
+                ("propose_ms", C.c_double * 7), ("propose_nodes", C.c_int64 * 7),
+                ("propose_arcs", C.c_int64 * 7)]
+
+    def to_dict(self) -> dict:
+        return dict(kernel_launches=self.kernel_launches,
+                    propose_launches=list(self.propose_launches),
+                    propose_ms=list(self.propose_ms), propose_nodes=list(self.propose_nodes),
+                    propose_arcs=list(self.propose_arcs))
+
+
+class GraphDesc(C.Structure):
+    _fields_ = [("n", C.c_int64), ("row_ptr", C.c_void_p), ("col", C.c_void_p),
+                ("node_w", C.c_void_p), ("edge_w", C.c_void_p), ("k", C.c_int32),
+                ("eps", C.c_double), ("seed", C.c_uint64), ("block_out", C.c_void_p),
+                ("cut", C.c_int64), ("max_block_weight", C.c_int64), ("status", C.c_int32)]
+
+
+_handle = None
+
+
+def _lib():
+    global _handle
+    if _handle is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"{LIB_PATH} is missing: build it with `python -m paper_1402_3281_gb300.build` "
+                "(the partitioner has no CPU fallback)")
+        h = C.CDLL(LIB_PATH)
+        p, i32, i64, u64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64, C.c_double
+        sig = {
+            "sclap_default_config": (None, [p]),
+            "sclap_error_string": (C.c_char_p, [C.c_int]),
+            "sclap_last_error": (C.c_char_p, []),
+            "sclap_partition": (C.c_int, [i64, p, p, p, p, i32, dbl, u64, p, p, p, p, p]),
+            "sclap_partition_device": (C.c_int, [i64, p, p, p, p, i32, dbl, u64, p, p, p, p, p, p]),
+            "sclap_partition_batch": (C.c_int, [i32, p, p, i32, p]),
+            "sclap_lp_round": (C.c_int, [i32, i64, p, p, p, p, p, p, i64, i64, u64, i32, p, p, p, p]),
+            "sclap_cluster": (C.c_int, [i64, p, p, p, p, i64, u64, i32, p, p, p, p]),
+            "sclap_contract": (C.c_int, [i64, p, p, p, p, p, p, p, p, p, p, p, p, p]),
+            "sclap_initial_partition": (C.c_int, [i64, p, p, p, p, i32, i64, i64, u64, i32, p, p,
+                                                  p, p, p]),
+            "sclap_refine": (C.c_int, [i64, p, p, p, p, i32, i64, u64, i32, i32, p, p, p, p]),
+            "sclap_cut": (C.c_int, [i64, p, p, p, p, p, p]),
+            "sclap_profile_enable": (None, [C.c_int]),
+            "sclap_profile_reset": (None, []),
+            "sclap_profile_read": (None, [p]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(h, name)
+            f.restype = res
+            f.argtypes = args
+        _handle = h
+    return _handle
+
+
+def load():
+    """Loads libsclap.so (raises if it is missing)."""
+    return _lib()
+
+
+def sclap_profile_enable(on: bool = True) -> None:
+    _lib().sclap_profile_enable(1 if on else 0)
+
+
+def sclap_profile_reset() -> None:
+    _lib().sclap_profile_reset()
+
+
+def sclap_profile_read() -> dict:
+    p = Profile()
+    _lib().sclap_profile_read(C.byref(p))
+    return p.to_dict()
+
+
+def default_config(**overrides) -> Config:
+    c = Config()
+    _lib().sclap_default_config(C.byref(c))
+    for k, v in overrides.items():
+        setattr(c, k, int(v))
+    return c
+
+
+def _check(rc: int, where: str, allow=(OK,)):
+    if rc not in allow:
+        raise SclapError(rc, where)
+    return rc
+
+
+def _np(a, dtype):
+    return None if a is None else np.ascontiguousarray(a, dtype=dtype)
+
+
+def _hp(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _dp(t):
+    """Device pointer of a CUDA tensor (or None)."""
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+@dataclass
+class Result:
+    block: object          # numpy array (host API) or torch tensor (device API)
+    cut: int
+    max_block_weight: int
+    status: int
+    stats: Optional[dict] = None
+
+
+# --------------------------------------------------------------- whole partitioner
+def sclap_partition(row_ptr, col, node_w=None, edge_w=None, k=2, eps=0.03, seed=0,
+                    cfg: Optional[Config] = None) -> Result:
+    """Host arrays in, host block ids out (sclap_partition)."""
+    rp = _np(row_ptr, np.int64)
+    cl = _np(col, np.int32)
+    nw = _np(node_w, np.int32)
+    ew = _np(edge_w, np.int32)
+    n = rp.size - 1
+    blk = np.empty(n, np.int32)
+    cut, mb = C.c_int64(), C.c_int64()
+    st = Stats()
+    rc = _lib().sclap_partition(n, _hp(rp), _hp(cl), _hp(nw), _hp(ew), int(k), float(eps),
+                                int(seed) & (2**64 - 1), C.byref(cfg) if cfg else None,
+                                _hp(blk), C.byref(cut), C.byref(mb), C.byref(st))
+    _check(rc, "sclap_partition", allow=(OK, EINFEASIBLE))
+    return Result(blk, cut.value, mb.value, rc, st.to_dict())
+
+
+def sclap_partition_device(row_ptr, col, node_w=None, edge_w=None, k=2, eps=0.03, seed=0,
+                           cfg: Optional[Config] = None, block_out=None, stream=None) -> Result:
+    """CUDA tensors in, CUDA tensor of block ids out (sclap_partition_device)."""
+    import torch
+    n = row_ptr.numel() - 1
+    if block_out is None:
+        block_out = torch.empty(n, dtype=torch.int32, device=row_ptr.device)
+    cut, mb = C.c_int64(), C.c_int64()
+    st = Stats()
+    rc = _lib().sclap_partition_device(n, _dp(row_ptr), _dp(col), _dp(node_w), _dp(edge_w),
+                                       int(k), float(eps), int(seed) & (2**64 - 1),
+                                       C.byref(cfg) if cfg else None, _dp(block_out),
+                                       C.byref(cut), C.byref(mb), C.byref(st), _stream(stream))
+    _check(rc, "sclap_partition_device", allow=(OK, EINFEASIBLE))
+    return Result(block_out, cut.value, mb.value, rc, st.to_dict())
+
+
+def sclap_partition_batch(graphs: Sequence[dict], cfg: Optional[Config] = None,
+                          device: bool = False, stream=None):
+    """Partitions many graphs in one call (sclap_partition_batch).
+
+    Each entry: dict(row_ptr, col, node_w=None, edge_w=None, k, eps, seed); numpy
+    arrays when device=False, CUDA tensors when device=True.  Returns a list
+    of Result (block ids as numpy arrays or CUDA tensors).
+    """
+    descs = (GraphDesc * len(graphs))()
+    keep = []
+    outs = []
+    for i, g in enumerate(graphs):
+        d = descs[i]
+        if device:
+            import torch
+            rp, cl = g["row_ptr"], g["col"]
+            out = torch.empty(rp.numel() - 1, dtype=torch.int32, device=rp.device)
+            d.n = rp.numel() - 1
+            d.row_ptr, d.col = _dp(rp).value, _dp(cl).value
+            d.node_w = _dp(g.get("node_w")).value if g.get("node_w") is not None else None
+            d.edge_w = _dp(g.get("edge_w")).value if g.get("edge_w") is not None else None
+            d.block_out = _dp(out).value
+            keep.append((rp, cl, g.get("node_w"), g.get("edge_w")))
+        else:
+            rp, cl = _np(g["row_ptr"], np.int64), _np(g["col"], np.int32)
+            nw, ew = _np(g.get("node_w"), np.int32), _np(g.get("edge_w"), np.int32)
+            out = np.empty(rp.size - 1, np.int32)
+            d.n = rp.size - 1
+            d.row_ptr, d.col = _hp(rp).value, _hp(cl).value
+            d.node_w = _hp(nw).value if nw is not None else None
+            d.edge_w = _hp(ew).value if ew is not None else None
+            d.block_out = _hp(out).value
+            keep.append((rp, cl, nw, ew))
+        d.k = int(g.get("k", 2))
+        d.eps = float(g.get("eps", 0.03))
+        d.seed = int(g.get("seed", 0)) & (2**64 - 1)
+        outs.append(out)
+    rc = _lib().sclap_partition_batch(len(graphs), C.cast(descs, C.c_void_p),
+                                      C.byref(cfg) if cfg else None, 1 if device else 0,
+                                      _stream(stream) if device else None)
+    res = [Result(outs[i], descs[i].cut, descs[i].max_block_weight, descs[i].status)
+           for i in range(len(graphs))]
+    _check(rc, "sclap_partition_batch", allow=(OK, EINFEASIBLE))
+    return res
+
+
+# --------------------------------------------------------------- step entry points
+def sclap_lp_round(mode, row_ptr, col, node_w, edge_w, label, W, bound, rkey, sub_rounds,
+                   active_cur=None, active_next=None, stream=None) -> int:
+    moved = C.c_int64()
+    n = row_ptr.numel() - 1
+    rc = _lib().sclap_lp_round(int(mode), n, _dp(row_ptr), _dp(col), _dp(node_w), _dp(edge_w),
+                               _dp(label), _dp(W), W.numel(), int(bound),
+                               int(rkey) & (2**64 - 1), int(sub_rounds), _dp(active_cur),
+                               _dp(active_next), C.byref(moved), _stream(stream))
+    _check(rc, "sclap_lp_round")
+    return moved.value
+
+
+def sclap_cluster(row_ptr, col, node_w, edge_w, U, seed, level=0, cfg=None, stream=None):
+    import torch
+    n = row_ptr.numel() - 1
+    label = torch.empty(n, dtype=torch.int32, device=row_ptr.device)
+    rounds = C.c_int32()
+    rc = _lib().sclap_cluster(n, _dp(row_ptr), _dp(col), _dp(node_w), _dp(edge_w), int(U),
+                              int(seed) & (2**64 - 1), int(level), C.byref(cfg) if cfg else None,
+                              _dp(label), C.byref(rounds), _stream(stream))
+    _check(rc, "sclap_cluster")
+    return label, rounds.value
+
+
+def sclap_contract(row_ptr, col, node_w, edge_w, label, stream=None):
+    """Returns (cmap, row_ptr, col, node_w, edge_w) of the coarse graph (CUDA)."""
+    import torch
+    n = row_ptr.numel() - 1
+    m = col.numel()
+    dev = row_ptr.device
+    cmap = torch.empty(n, dtype=torch.int32, device=dev)
+    cnw = torch.empty(n, dtype=torch.int32, device=dev)
+    crp = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    ccol = torch.empty(max(m, 1), dtype=torch.int32, device=dev)
+    cew = torch.empty(max(m, 1), dtype=torch.int32, device=dev)
+    nc, mc = C.c_int64(), C.c_int64()
+    rc = _lib().sclap_contract(n, _dp(row_ptr), _dp(col), _dp(node_w), _dp(edge_w), _dp(label),
+                               _dp(cmap), C.byref(nc), _dp(cnw), _dp(crp), _dp(ccol), _dp(cew),
+                               C.byref(mc), _stream(stream))
+    _check(rc, "sclap_contract")
+    a, b = nc.value, mc.value
+    return cmap, crp[:a + 1], ccol[:b], cnw[:a], cew[:b]
+
+
+def sclap_initial_partition(row_ptr, col, node_w, edge_w, k, Lmax, avg, seed, level=0,
+                            cfg=None, stream=None):
+    import torch
+    n = row_ptr.numel() - 1
+    blk = torch.empty(n, dtype=torch.int32, device=row_ptr.device)
+    cut, best = C.c_int64(), C.c_int32()
+    rc = _lib().sclap_initial_partition(n, _dp(row_ptr), _dp(col), _dp(node_w), _dp(edge_w),
+                                        int(k), int(Lmax), int(avg), int(seed) & (2**64 - 1),
+                                        int(level), C.byref(cfg) if cfg else None, _dp(blk),
+                                        C.byref(cut), C.byref(best), _stream(stream))
+    _check(rc, "sclap_initial_partition")
+    return blk, cut.value, best.value
+
+
+def sclap_refine(row_ptr, col, node_w, edge_w, k, Lmax, block, seed, phase=PH_REFINE, level=0,
+                 cfg=None, stream=None) -> int:
+    rounds = C.c_int32()
+    n = row_ptr.numel() - 1
+    rc = _lib().sclap_refine(n, _dp(row_ptr), _dp(col), _dp(node_w), _dp(edge_w), int(k),
+                             int(Lmax), int(seed) & (2**64 - 1), int(phase), int(level),
+                             C.byref(cfg) if cfg else None, _dp(block), C.byref(rounds),
+                             _stream(stream))
+    _check(rc, "sclap_refine")
+    return rounds.value
+
+
+def sclap_cut(row_ptr, col, edge_w, block, stream=None) -> int:
+    cut = C.c_int64()
+    n = row_ptr.numel() - 1
+    rc = _lib().sclap_cut(n, _dp(row_ptr), _dp(col), _dp(edge_w), _dp(block), C.byref(cut),
+                          _stream(stream))
+    _check(rc, "sclap_cut")
+    return cut.value

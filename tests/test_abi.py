@@ -1,0 +1,64 @@
+"""CPU checks of the C ABI boundary: the library builds for sm_103a, loads
+without a GPU, and exports every function that include/sclap.h declares.
+No compute call is made here."""
+import ctypes
+import os
+import re
+import shutil
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "sclap.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(sclap_[a-z_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    from paper_1402_3281_gb300 import build as B
+    if shutil.which("nvcc") or os.path.exists("/usr/local/cuda/bin/nvcc"):
+        return B.build()
+    if not os.path.exists(B.SO):
+        pytest.skip("nvcc not available and library not built")
+    return B.SO
+
+
+def test_header_declares_the_documented_entry_points():
+    names = declared_functions()
+    for n in ("sclap_partition", "sclap_partition_device", "sclap_partition_batch",
+              "sclap_lp_round", "sclap_cluster", "sclap_contract", "sclap_initial_partition",
+              "sclap_refine", "sclap_cut", "sclap_default_config", "sclap_error_string"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib_path):
+    lib = ctypes.CDLL(lib_path)
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_binding_covers_every_declared_symbol():
+    from paper_1402_3281_gb300 import sclap
+    assert sorted(sclap.SYMBOLS) == declared_functions()
+
+
+def test_default_config_and_error_strings(lib_path):
+    from paper_1402_3281_gb300 import sclap
+    c = sclap.default_config()
+    assert (c.lp_rounds_coarse, c.lp_rounds_refine, c.f, c.sub_rounds) == (10, 10, 18, 8)
+    lib = sclap.load()
+    assert lib.sclap_error_string(0) == b"ok"
+    assert b"CSR" in lib.sclap_error_string(-2)
+
+
+def test_oracle_and_library_defaults_agree(lib_path):
+    import oracle as O
+    from paper_1402_3281_gb300 import sclap
+    a, b = O.config(), sclap.default_config()
+    for f, _ in O.Config._fields_:
+        assert getattr(a, f) == getattr(b, f), f

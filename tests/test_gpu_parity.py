@@ -1,0 +1,299 @@
+"""GPU parity: every step of the CUDA path, called through the C ABI, equals the
+CPU oracle's round-synchronous variant bit for bit (labels, weights, coarse
+graphs, blocks, cuts).  Inputs are seeded synthetic graphs spanning every
+degree bucket of the LP sweep (lane groups, warp / CTA shared-memory tables,
+global-memory tables for hubs) and both admission paths (all-pairs and radix
+select).
+"""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - CPU machines
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_1402_3281_gb300 as P  # noqa: E402
+
+DEV = torch.device("cuda:0")
+
+
+def dt(a, dtype=None):
+    a = np.ascontiguousarray(a if dtype is None else np.asarray(a, dtype=dtype))
+    return torch.from_numpy(a).to(DEV)
+
+
+def dg(g):
+    return dt(g.row_ptr), dt(g.col), dt(g.node_w), dt(g.edge_w)
+
+
+def hub_graph(seed=0):
+    """R-MAT plus a star whose centre has degree 9000 (global-table bucket)."""
+    base = gg.rmat(12, 8, seed)
+    n = base.n
+    src = np.repeat(np.arange(n), np.diff(base.row_ptr))
+    keep = src < base.col
+    s = np.concatenate([src[keep], np.zeros(9000, np.int64)])
+    d = np.concatenate([base.col[keep], np.arange(n, n + 9000)])
+    s = np.concatenate([s, np.arange(n, n + 9000)])
+    d = np.concatenate([d, np.repeat(np.arange(1, 100), 91)[:9000]])
+    return gg.from_edges(n + 9000, s, d, name="hub")
+
+
+GRAPHS = {
+    "rmat12": lambda: gg.rmat(12, 8, 1),
+    "rmat16": lambda: gg.rmat(16, 8, 0),
+    "rgg": lambda: gg.rgg2d(5000, 2),
+    "weighted": lambda: gg.random_weights(gg.rmat(11, 8, 4), 7, max_node_w=5, max_edge_w=9),
+    "star": lambda: gg.star(3000),
+    "hub": lambda: hub_graph(2),
+}
+
+
+@pytest.fixture(scope="module", params=sorted(GRAPHS))
+def graph(request):
+    return GRAPHS[request.param]()
+
+
+# ------------------------------------------------------------------ one round
+@pytest.mark.parametrize("S", [1, 3, 8])
+def test_cluster_round_bit_exact(graph, S):
+    rng = np.random.default_rng(S)
+    g = graph
+    label = np.arange(g.n, dtype=np.int32)
+    if S == 3:  # start from a partial clustering so some clusters are near the bound
+        label = (np.arange(g.n) // 3).astype(np.int32)
+    W = np.bincount(label, weights=g.node_w, minlength=g.n).astype(np.int64)
+    U = int(W.max()) + int(rng.integers(2, 40))
+    rkey = int(rng.integers(1, 2**62))
+    ol, oW, om, on = O.lp_round(g, O.MODE_CLUSTER, label, W, U, rkey, S, want_next=True)
+    rp, col, nw, ew = dg(g)
+    tl, tW = dt(label), dt(W)
+    an = torch.zeros(g.n, dtype=torch.uint8, device=DEV)
+    moved = P.sclap_lp_round(0, rp, col, nw, ew, tl, tW, U, rkey, S, active_next=an)
+    assert moved == om
+    assert np.array_equal(tl.cpu().numpy(), ol)
+    assert np.array_equal(tW.cpu().numpy(), oW)
+    assert np.array_equal(an.cpu().numpy(), on)
+
+
+@pytest.mark.parametrize("k", [2, 7, 64])
+def test_refine_round_bit_exact(graph, k):
+    rng = np.random.default_rng(k)
+    g = graph
+    label = rng.integers(0, k, g.n).astype(np.int32)
+    if k == 7:  # overload block 0 so forced moves and the source cap run
+        label[rng.random(g.n) < 0.3] = 0
+    W = np.bincount(label, weights=g.node_w, minlength=k).astype(np.int64)
+    Lmax = O.bounds(int(g.node_w.sum()), int(g.node_w.max()), k, 0.03)[0]
+    active = (rng.random(g.n) < 0.7).astype(np.uint8)
+    rkey = int(rng.integers(1, 2**62))
+    ol, oW, om, on = O.lp_round(g, O.MODE_REFINE, label, W, Lmax, rkey, 8, active_cur=active,
+                                want_next=True)
+    rp, col, nw, ew = dg(g)
+    tl, tW = dt(label), dt(W)
+    an = torch.zeros(g.n, dtype=torch.uint8, device=DEV)
+    moved = P.sclap_lp_round(1, rp, col, nw, ew, tl, tW, Lmax, rkey, 8, active_cur=dt(active),
+                             active_next=an)
+    assert moved == om
+    assert np.array_equal(tl.cpu().numpy(), ol)
+    assert np.array_equal(tW.cpu().numpy(), oW)
+    assert np.array_equal(an.cpu().numpy(), on)
+
+
+def test_large_overflow_segment_uses_radix_select():
+    # Every leaf of a 5000-leaf star proposes the centre's cluster: one
+    # segment far above the all-pairs limit.
+    g = gg.star(5000)
+    label = np.arange(g.n, dtype=np.int32)
+    W = np.ones(g.n, np.int64)
+    for U, S in [(17, 1), (1500, 1), (2600, 2)]:
+        ol, oW, om, _ = O.lp_round(g, O.MODE_CLUSTER, label, W, U, 77, S)
+        rp, col, nw, ew = dg(g)
+        tl, tW = dt(label), dt(W)
+        moved = P.sclap_lp_round(0, rp, col, nw, ew, tl, tW, U, 77, S)
+        assert moved == om
+        assert np.array_equal(tl.cpu().numpy(), ol)
+        assert np.array_equal(tW.cpu().numpy(), oW)
+
+
+# ------------------------------------------------------------------ level steps
+def test_cluster_level_bit_exact(graph):
+    g = graph
+    Lmax, U = O.bounds(int(g.node_w.sum()), int(g.node_w.max()), 2, 0.03)
+    ol, orounds = O.cluster(g, U, seed=11, level=2)
+    tl, rounds = P.sclap_cluster(*dg(g), U, 11, 2)
+    assert rounds == orounds
+    assert np.array_equal(tl.cpu().numpy(), ol)
+
+
+def _canon(rp, col, w):
+    n = rp.size - 1
+    src = np.repeat(np.arange(n), np.diff(rp))
+    o = np.lexsort((col, src))
+    return src[o], col[o], w[o]
+
+
+def test_contract_bit_exact(graph):
+    g = graph
+    U = 25
+    lab, _ = O.cluster(g, U, seed=3)
+    for label in (lab, np.arange(g.n, dtype=np.int32),
+                  np.random.default_rng(1).integers(0, max(1, g.n // 50), g.n).astype(np.int32)):
+        c = O.contract(g, label)
+        cmap, crp, ccol, cnw, cew = P.sclap_contract(*dg(g), dt(label))
+        assert np.array_equal(cmap.cpu().numpy(), c.cmap)
+        assert np.array_equal(cnw.cpu().numpy(), c.node_w)
+        assert np.array_equal(crp.cpu().numpy(), c.row_ptr)
+        a = _canon(crp.cpu().numpy(), ccol.cpu().numpy(), cew.cpu().numpy())
+        b = _canon(c.row_ptr, c.col, c.edge_w)
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("k", [2, 5, 16])
+def test_initial_partition_bit_exact(k):
+    for g in (gg.rgg2d(1500, 3), gg.random_weights(gg.rmat(10, 8, 2), 3), gg.path(300)):
+        cV = int(g.node_w.sum())
+        Lmax, _ = O.bounds(cV, int(g.node_w.max()), k, 0.03)
+        avg = -(-cV // k)
+        cfg_o = O.config(ip_trials=6)
+        ob, ocut, obest = O.initial_partition(g, k, Lmax, avg, seed=9, level=3, cfg=cfg_o)
+        cfg = P.default_config(ip_trials=6)
+        tb, cut, best = P.sclap_initial_partition(*dg(g), k, Lmax, avg, 9, 3, cfg=cfg)
+        assert (cut, best) == (ocut, obest)
+        assert np.array_equal(tb.cpu().numpy(), ob)
+
+
+def test_ggg_single_trial_bit_exact():
+    # one trial with no LP afterwards: the growing + water-filling step alone
+    g = gg.random_weights(gg.rgg2d(2000, 5), 2)
+    k = 6
+    cV = int(g.node_w.sum())
+    avg = -(-cV // k)
+    Lmax = 10**9   # no local search moves can happen... (bound irrelevant, rounds = 0)
+    cfg_o = O.config(ip_trials=1, lp_rounds_refine=0)
+    ob, ocut, _ = O.initial_partition(g, k, Lmax, avg, seed=5, level=0, cfg=cfg_o)
+    tkey = O.hkey(5, O.PH_TRIAL, 0, 0)
+    gb, gW = O.ggg(g, k, avg, tkey, 0)
+    assert np.array_equal(ob, gb)
+    tb, cut, _ = P.sclap_initial_partition(*dg(g), k, Lmax, avg, 5, 0,
+                                           cfg=P.default_config(ip_trials=1, lp_rounds_refine=0))
+    assert cut == ocut
+    assert np.array_equal(tb.cpu().numpy(), ob)
+
+
+def test_refine_level_bit_exact(graph):
+    g = graph
+    k = 4
+    rng = np.random.default_rng(5)
+    blk = rng.integers(0, k, g.n).astype(np.int32)
+    Lmax = O.bounds(int(g.node_w.sum()), int(g.node_w.max()), k, 0.03)[0]
+    ob, orounds = O.refine(g, k, Lmax, blk, seed=21, phase=O.PH_REFINE, level=1)
+    tb = dt(blk)
+    rounds = P.sclap_refine(*dg(g), k, Lmax, tb, 21, O.PH_REFINE, 1)
+    assert rounds == orounds
+    assert np.array_equal(tb.cpu().numpy(), ob)
+
+
+def test_cut_matches_oracle(graph):
+    g = graph
+    rng = np.random.default_rng(0)
+    for k in (2, 9):
+        b = rng.integers(0, k, g.n).astype(np.int32)
+        rp, col, nw, ew = dg(g)
+        assert P.sclap_cut(rp, col, ew, dt(b)) == O.cut(g, b)
+
+
+# ------------------------------------------------------------------ end to end
+E2E = [
+    ("rmat16", 2), ("rmat16", 8), ("rmat12", 4), ("rgg", 2), ("rgg", 16), ("weighted", 3),
+    ("star", 2), ("hub", 4),
+]
+
+
+@pytest.mark.parametrize("name,k", E2E)
+def test_partition_bit_exact(name, k):
+    g = GRAPHS[name]()
+    ref = O.partition(g, k, 0.03, seed=0)
+    res = P.sclap_partition_device(*dg(g), k=k, eps=0.03, seed=0)
+    assert res.status == ref.status
+    assert res.cut == ref.cut
+    assert np.array_equal(res.block.cpu().numpy(), ref.block)
+    assert res.max_block_weight == ref.max_block_weight
+    st = res.stats
+    assert st["levels"] == ref.stats.levels
+    assert st["level_n"] == list(ref.stats.level_n[:ref.stats.levels])
+
+
+def test_partition_host_api_and_seeds():
+    g = gg.rmat(14, 8, 3)
+    for seed in (0, 1, 2):
+        ref = O.partition(g, 4, 0.05, seed=seed)
+        res = P.sclap_partition(g.row_ptr, g.col, None, None, k=4, eps=0.05, seed=seed)
+        assert res.cut == ref.cut and np.array_equal(res.block, ref.block)
+
+
+@pytest.mark.parametrize("case", ["k1", "no_edges", "path", "tiny", "clique_ring", "eps0"])
+def test_partition_edge_cases(case):
+    if case == "k1":
+        g, k, eps = gg.rmat(10, 8, 0), 1, 0.03
+    elif case == "no_edges":
+        g, k, eps = gg.from_edges(3000, [], []), 4, 0.03
+    elif case == "path":
+        g, k, eps = gg.path(5000), 2, 0.03
+    elif case == "tiny":
+        g, k, eps = gg.path(3), 3, 0.0
+    elif case == "clique_ring":
+        g, k, eps = gg.clique_ring(16, 50), 16, 0.03
+    else:
+        g, k, eps = gg.rgg2d(4000, 1), 8, 0.0
+    ref = O.partition(g, k, eps, seed=4)
+    res = P.sclap_partition_device(*dg(g), k=k, eps=eps, seed=4)
+    assert (res.status, res.cut) == (ref.status, ref.cut)
+    assert np.array_equal(res.block.cpu().numpy(), ref.block)
+
+
+def test_batch_equals_each_graph_alone():
+    graphs = [(gg.rmat(10 + i % 4, 8, i), [2, 4, 8, 16][i % 4]) for i in range(6)]
+    graphs += [(gg.rgg2d(1000 + 700 * i, i), [2, 4, 8, 16][(i + 1) % 4]) for i in range(6)]
+    graphs.append((gg.random_weights(gg.rmat(11, 8, 9), 1), 5))
+    items = [dict(row_ptr=g.row_ptr, col=g.col, node_w=g.node_w, edge_w=g.edge_w, k=k, eps=0.03,
+                  seed=i) for i, (g, k) in enumerate(graphs)]
+    res = P.sclap_partition_batch(items)
+    dres = P.sclap_partition_batch(
+        [dict(row_ptr=dt(g.row_ptr), col=dt(g.col), node_w=dt(g.node_w), edge_w=dt(g.edge_w),
+              k=k, eps=0.03, seed=i) for i, (g, k) in enumerate(graphs)], device=True)
+    for i, (g, k) in enumerate(graphs):
+        ref = O.partition(g, k, 0.03, seed=i)
+        assert res[i].cut == ref.cut and np.array_equal(res[i].block, ref.block), i
+        assert dres[i].cut == ref.cut
+        assert np.array_equal(dres[i].block.cpu().numpy(), ref.block), i
+
+
+def test_invalid_inputs_are_rejected():
+    g = gg.rmat(8, 8, 0)
+    bad = g.col.copy()
+    bad[5] = g.n + 3                       # column out of range
+    with pytest.raises(P.SclapError) as e:
+        P.sclap_partition(g.row_ptr, bad, k=2)
+    assert e.value.code == -2
+    loop = g.col.copy()
+    loop[g.row_ptr[7]] = 7 if g.row_ptr[8] > g.row_ptr[7] else loop[0]   # self-loop
+    if g.row_ptr[8] > g.row_ptr[7]:
+        with pytest.raises(P.SclapError):
+            P.sclap_partition(g.row_ptr, loop, k=2)
+    with pytest.raises(P.SclapError) as e:
+        P.sclap_partition(g.row_ptr, g.col, k=g.n + 1)
+    assert e.value.code == -1
+    nw = np.ones(g.n, np.int32)
+    nw[3] = 0                              # non-positive weight
+    with pytest.raises(P.SclapError):
+        P.sclap_partition(g.row_ptr, g.col, node_w=nw, k=2)
+    # a failing call leaves the library usable
+    ok = P.sclap_partition(g.row_ptr, g.col, k=2)
+    assert ok.status == 0
