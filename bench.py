@@ -45,7 +45,7 @@ import graphgen as gg  # noqa: E402
 # admission key (8) written.
 ARC_BYTES = 12
 NODE_BYTES = 44
-BUCKETS = ["lanes4", "lanes8", "lanes16", "lanes32", "warp_smem", "cta_smem", "cta_global"]
+FAMILIES = ["lane_groups", "warp_smem", "cta_smem", "cta_global"]
 
 
 def parse():
@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--timeline", action="store_true",
+                    help="after the timed steps, run one step with per-kernel timeline "
+                         "events and print the table to stderr")
     return ap.parse_args()
 
 
@@ -253,6 +256,17 @@ def main():
         tt = torch.tensor([elapsed_ms], device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         elapsed_ms = float(tt.item())
+    if args.timeline:
+        P.sclap_profile_dump()
+        P.sclap_profile_timeline(True)
+        P.sclap_partition_batch(items, device=True)
+        torch.cuda.synchronize()
+        P.sclap_profile_timeline(False)
+        tl = P.sclap_profile_dump()
+        tot = sum(v[1] for v in tl.values())
+        print(f"timeline of one step: {tot:.2f} ms", file=sys.stderr)
+        for name, (cnt, ms) in sorted(tl.items(), key=lambda x: -x[1][1]):
+            print(f"  {name:28s} {cnt:7d} {ms:10.3f} ms {100 * ms / tot:6.1f}%", file=sys.stderr)
     deterministic = [r.cut for r in last] == ref_cuts
     balanced = all(r.status == 0 for r in last)
 
@@ -278,9 +292,9 @@ def main():
         "avg_launch_ms": prop_ms / nl if nl else None,
         "launches": nl,
         "share_of_step": prop_ms / elapsed_ms if elapsed_ms else None,
-        "per_bucket": {BUCKETS[b]: {"ms": prof["propose_ms"][b], "launches": prof["propose_launches"][b],
-                                    "nodes": prof["propose_nodes"][b], "arcs": prof["propose_arcs"][b]}
-                       for b in range(7)},
+        "per_family": {FAMILIES[b]: {"ms": prof["propose_ms"][b], "launches": prof["propose_launches"][b],
+                                     "nodes": prof["propose_nodes"][b], "arcs": prof["propose_arcs"][b]}
+                       for b in range(4)},
     }
 
     line = {

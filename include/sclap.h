@@ -194,19 +194,28 @@ int sclap_cut(int64_t n, const int64_t* row_ptr, const int32_t* col, const int32
 /* ---- Instrumentation (no counterpart in the paper).  Process-wide
  * counters read by the benchmark: every kernel launch is counted; with
  * profiling enabled, each launch of the LP propose sweep is bracketed by CUDA
- * events on its stream and its nodes/arcs are tallied per degree bucket
- * (0..3: 4/8/16/32 lanes per node, 4: warp + shared table, 5: CTA + shared
- * table, 6: CTA + global table).  Times are device milliseconds. ---- */
+ * events on its stream and its nodes/arcs are tallied per kernel family
+ * (0: lane groups of 4/8/16/32 per node, degree <= 32; 1: one warp per node
+ * with a shared table, degree <= 512; 2: one CTA per node, shared table,
+ * degree <= 4096; 3: one CTA per node, global table).  Times are device
+ * milliseconds. ---- */
 typedef struct sclap_profile {
   int64_t kernel_launches;
-  int64_t propose_launches[7];
-  double propose_ms[7];
-  int64_t propose_nodes[7];
-  int64_t propose_arcs[7];
+  int64_t propose_launches[4];
+  double propose_ms[4];
+  int64_t propose_nodes[4];
+  int64_t propose_arcs[4];
 } sclap_profile;
 void sclap_profile_enable(int on);
 void sclap_profile_reset(void);
 void sclap_profile_read(sclap_profile* out);
+/* Timeline mode: an event after every kernel launch and after every host
+ * wait; sclap_profile_dump writes "name launches total_ms" lines (time since
+ * the previous mark of the same call: device time plus any idle gap) into
+ * buf (cap bytes, NUL-terminated), clears the timeline and returns the length
+ * the full text needs. */
+void sclap_profile_timeline(int on);
+int64_t sclap_profile_dump(char* buf, int64_t cap);
 
 #ifdef __cplusplus
 }

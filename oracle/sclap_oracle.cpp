@@ -522,25 +522,50 @@ void block_weights(const G& g, int32_t k, const int32_t* block, int64_t* W) {
 
 // Initial partitioning: `ip_trials` seeded trials of growing + LP local
 // search; the trial with the smallest (overload, cut, trial index) is kept.
+// Nodes without neighbours cannot affect a cut and never move in LP, so the
+// trials run on the induced subgraph of the other nodes (ids renumbered in
+// order); the isolated nodes are water-filled into the best trial's blocks.
 int initial_partition(int variant, const G& g, int32_t k, int64_t Lmax, int64_t avg,
                       uint64_t seed, int32_t level, const orc_config& cfg, int32_t* block_out,
                       int64_t* cut_out, int32_t* best_out) {
-  vector<int32_t> lab((size_t)g.n);
-  vector<int64_t> W((size_t)k);
-  int64_t bo = -1, bc = -1;
-  int32_t bt = -1;
-  for (int32_t t = 0; t < cfg.ip_trials; ++t) {
-    uint64_t tkey = hkey(seed, ORC_PH_TRIAL, (uint64_t)level, (uint64_t)t);
-    ggg(g, k, avg, tkey, level, lab.data(), W.data());
-    refine_level(variant, g, k, Lmax, tkey, ORC_PH_IPREF, level, cfg, lab.data(), W.data(),
-                 nullptr);
-    int64_t ov = std::max<int64_t>(0, max_weight(W.data(), k) - Lmax);
-    int64_t c = cut_of(g, lab.data());
-    if (bt < 0 || ov < bo || (ov == bo && c < bc)) {
-      bo = ov; bc = c; bt = t;
-      std::copy(lab.begin(), lab.end(), block_out);
+  vector<int32_t> rank((size_t)g.n, -1);
+  OG ga;
+  for (int64_t v = 0; v < g.n; ++v)
+    if (g.deg(v) > 0) rank[v] = (int32_t)ga.n++;
+  ga.xadj.assign((size_t)ga.n + 1, 0);
+  ga.nw.resize((size_t)ga.n);
+  for (int64_t v = 0; v < g.n; ++v) {
+    if (rank[v] < 0) continue;
+    ga.nw[rank[v]] = g.nw[v];
+    for (int64_t e = g.xadj[v]; e < g.xadj[v + 1]; ++e) {
+      ga.adj.push_back(rank[g.adj[e]]);
+      ga.ew.push_back(g.ew[e]);
+    }
+    ga.xadj[rank[v] + 1] = (int64_t)ga.adj.size();
+  }
+  const G gA = ga.view();
+  vector<int32_t> lab((size_t)gA.n), best_lab((size_t)gA.n);
+  vector<int64_t> W((size_t)k), best_W((size_t)k, 0);
+  int64_t bo = -1, bc = 0;
+  int32_t bt = 0;
+  if (gA.n > 0) {
+    bt = -1;
+    for (int32_t t = 0; t < cfg.ip_trials; ++t) {
+      uint64_t tkey = hkey(seed, ORC_PH_TRIAL, (uint64_t)level, (uint64_t)t);
+      ggg(gA, k, avg, tkey, level, lab.data(), W.data());
+      refine_level(variant, gA, k, Lmax, tkey, ORC_PH_IPREF, level, cfg, lab.data(), W.data(),
+                   nullptr);
+      int64_t ov = std::max<int64_t>(0, max_weight(W.data(), k) - Lmax);
+      int64_t c = cut_of(gA, lab.data());
+      if (bt < 0 || ov < bo || (ov == bo && c < bc)) {
+        bo = ov; bc = c; bt = t;
+        best_lab = lab;
+        best_W = W;
+      }
     }
   }
+  for (int64_t v = 0; v < g.n; ++v) block_out[v] = rank[v] >= 0 ? best_lab[rank[v]] : -1;
+  waterfill(g, k, block_out, best_W.data());
   if (cut_out) *cut_out = bc;
   if (best_out) *best_out = bt;
   return ORC_OK;

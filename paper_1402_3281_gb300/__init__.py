@@ -6,6 +6,7 @@ include/sclap.h); `sclap` is its ctypes binding.
 from .sclap import (  # noqa: F401
     Config, Result, SclapError, default_config, load, sclap_cluster, sclap_contract, sclap_cut,
     sclap_initial_partition, sclap_lp_round, sclap_partition, sclap_partition_batch,
-    sclap_partition_device, sclap_profile_enable, sclap_profile_read, sclap_profile_reset,
+    sclap_partition_device, sclap_profile_dump, sclap_profile_enable, sclap_profile_read,
+    sclap_profile_reset, sclap_profile_timeline,
     sclap_refine,
 )

@@ -38,13 +38,32 @@ struct Error : std::runtime_error {
 struct ProfileState {
   std::atomic<int64_t> launches{0};
   std::atomic<bool> enabled{false};
+  std::atomic<bool> timeline{false};
   std::mutex mu;
-  double ms[7] = {};
-  int64_t nlaunch[7] = {}, nodes[7] = {}, arcs[7] = {};
+  double ms[4] = {};
+  int64_t nlaunch[4] = {}, nodes[4] = {}, arcs[4] = {};
+  // timeline mode: an event after every launch; the time from the previous
+  // event of the same call to this one is charged to the kernel (device time
+  // plus any idle gap before it)
+  std::vector<std::pair<const char*, cudaEvent_t>> marks;
 };
 ProfileState& profile();
-#define SCLAP_NOTE_LAUNCH() \
-  ::sclap::profile().launches.fetch_add(1, std::memory_order_relaxed)
+void timeline_mark(const char* name, cudaStream_t s);
+std::string timeline_dump();
+// cudaStreamSynchronize that also marks the timeline ("host": the copy and
+// round trip that preceded the wait).
+inline void stream_sync(cudaStream_t s) {
+  SCLAP_CUDA(cudaStreamSynchronize(s));
+  if (profile().timeline.load(std::memory_order_relaxed)) timeline_mark("host", s);
+}
+cudaEvent_t event_from_pool();
+void event_to_pool(cudaEvent_t e);
+#define SCLAP_NOTE_LAUNCH(name)                                               \
+  do {                                                                        \
+    ::sclap::profile().launches.fetch_add(1, std::memory_order_relaxed);      \
+    if (::sclap::profile().timeline.load(std::memory_order_relaxed))          \
+      ::sclap::timeline_mark(name, s);                                        \
+  } while (0)
 
 // Device error word bits (set by kernels, read by the host after a phase).
 enum : int32_t {
@@ -76,10 +95,12 @@ enum Phase : int32_t {
 enum Mode : int32_t { MODE_CLUSTER = 0, MODE_REFINE = 1, MODE_REPAIR = 2 };
 
 // Degree buckets of the LP sweep.  0..3: a group of 4/8/16/32 lanes per node,
-// labels aggregated with warp match; 4: one warp per node with a shared-memory
-// hash; 5: one CTA per node, shared-memory hash; 6: one CTA per node, hash in
-// global scratch.
-constexpr int NB = 7;
+// labels aggregated with warp match; 4, 5: one warp per node with a
+// shared-memory table of 256 / 1024 slots; 6: one CTA per node, shared-memory
+// table; 7: one CTA per node, table in global scratch.
+constexpr int NB = 8;
+constexpr int WARP_SMALL_MAXDEG = 128;     // table 256 slots per warp
+constexpr int WARP_SMALL_SLOTS = 256;
 constexpr int WARP_HASH_MAXDEG = 512;      // table 1024 slots per warp
 constexpr int WARP_HASH_SLOTS = 1024;
 constexpr int CTA_HASH_MAXDEG = 4096;      // table 8192 slots per CTA
@@ -92,9 +113,10 @@ __host__ __device__ __forceinline__ int bucket_of(int64_t deg, bool overloaded) 
     if (deg <= 16) return 2;
     if (deg <= 32) return 3;
   }
-  if (deg <= WARP_HASH_MAXDEG) return 4;
-  if (deg <= CTA_HASH_MAXDEG) return 5;
-  return 6;
+  if (deg <= WARP_SMALL_MAXDEG) return 4;
+  if (deg <= WARP_HASH_MAXDEG) return 5;
+  if (deg <= CTA_HASH_MAXDEG) return 6;
+  return 7;
 }
 
 // ---------------------------------------------------------------------------
@@ -270,6 +292,8 @@ struct DevBuf {
 void scan_excl_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, cudaStream_t s);
 void scan_excl_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t s);
 void scan_excl_u8_to_i64(const uint8_t* in, int64_t* out, int64_t n, cudaStream_t s);
+// out[i] = number of keys[0..i) that are >= 0 (occupied hash slots).
+void scan_excl_occupied(const int32_t* keys, int64_t* out, int64_t n, cudaStream_t s);
 // largest row length (atomicMax into *out, which the caller zeroes)
 void level_max_degree(const int64_t* row_ptr, int64_t N, int64_t* out, cudaStream_t s);
 // slot id of every node from node offsets
@@ -331,9 +355,17 @@ struct CopyTask {              // copy one graph segment (NULL weights -> unit)
   const int32_t* ew;
   const int32_t* nw;
   int64_t src_n0, src_a0, n, m, dst_n0, dst_a0;
+  // optional renumbering: rank[v] - rbase is the new id of a node with
+  // neighbours (rank = exclusive scan of "has neighbours"); isolated nodes
+  // are dropped.  NULL: plain copy.
+  const int64_t* rank;
+  int64_t rbase;
 };
+// Copies graph segments; row_ptr[N_total] = M_total.  N_total_override < 0:
+// the end of the last plain task.
 void ip_replicate(const std::vector<CopyTask>& tasks, int64_t* row_ptr, int32_t* col,
-                  int32_t* ew, int32_t* nw, int64_t M_total, cudaStream_t s);
+                  int32_t* ew, int32_t* nw, int64_t M_total, cudaStream_t s,
+                  int64_t N_total_override = -1);
 struct GGGArgs {
   const int64_t* row_ptr;
   const int32_t* col;
@@ -363,7 +395,24 @@ struct SelectTask {            // choose the best trial of one graph, copy it ou
   int32_t trials, k;
   int64_t Lmax, g_boff;        // graph's block offset in the refinement block space
   int32_t g;
+  const int64_t* rank;         // renumbering of the trial graphs (see CopyTask)
+  int64_t rbase;
 };
+// Water-filling of the isolated nodes (dst_blk < 0) of one graph into its
+// lightest blocks, in node order; iso_prefix is the exclusive scan of the
+// isolated nodes' weights over the level.
+struct FillTask {
+  int32_t* blk;
+  const int32_t* nw;
+  const int64_t* iso_prefix;
+  int64_t n0, n, g_boff;
+  int32_t k;
+};
+void waterfill_isolated(const std::vector<FillTask>& tasks, int64_t* Wg, int64_t Ktot,
+                        cudaStream_t s);
+// flags[v] = 1 if v has neighbours; iso_w[v] = nw[v] if it has none, else 0.
+void isolated_flags(const int64_t* row_ptr, const int32_t* nw, int64_t N, uint8_t* flags,
+                    int32_t* iso_w, cudaStream_t s);
 // best[g], ipcut[g] on the device; block weights copied to Wg[g_boff..].
 void ip_select_copy(const std::vector<SelectTask>& tasks, const int64_t* cut2,
                     const int64_t* ip_W, const int64_t* ip_noff, const int64_t* ip_boff,

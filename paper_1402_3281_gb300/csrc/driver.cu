@@ -46,35 +46,75 @@ sclap_config resolve_cfg(const sclap_config* c) {
 }
 
 // ------------------------------------------------------------- validation
-__global__ void k_validate(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
-                           const int32_t* __restrict__ nw, const int32_t* __restrict__ ew,
-                           int64_t n, int64_t m, int32_t* err, unsigned long long* cV,
-                           int32_t* maxc) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t0 == 0 && (row_ptr[0] != 0 || row_ptr[n] != m)) atomicOr(err, DERR_BAD_CSR);
-  unsigned long long wsum = 0;
-  int32_t wmax = 0;
-  for (int64_t v = t0; v < n; v += stride) {
-    const int64_t rs = row_ptr[v], re = row_ptr[v + 1];
-    if (rs < 0 || rs > re || re > m) { atomicOr(err, DERR_BAD_CSR); continue; }
-    const int32_t w = nw ? nw[v] : 1;
-    if (w <= 0) atomicOr(err, DERR_BAD_CSR);
-    wsum += (unsigned long long)(w > 0 ? w : 0);
-    wmax = max(wmax, w);
-    for (int64_t e = rs; e < re; ++e) {
-      const int32_t c = col[e];
-      if (c < 0 || c >= n || c == v) { atomicOr(err, DERR_BAD_CSR); break; }
-      if (ew && ew[e] <= 0) { atomicOr(err, DERR_BAD_CSR); break; }
+// Checks a batched level as built from the inputs (one warp per 32 nodes,
+// arcs flattened across lanes): row offsets non-decreasing and inside the
+// slot's arc range, neighbours inside the slot, no self-loops, positive
+// weights.  Per-slot error flags, c(V) and max c(v).  Arcs are read only
+// inside ranges already checked, so malformed input cannot send a read out
+// of the level's arrays.
+__global__ void __launch_bounds__(256) k_validate_level(
+    const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+    const int32_t* __restrict__ ew, const int32_t* __restrict__ nw,
+    const int64_t* __restrict__ noff, const int64_t* __restrict__ aoff, int32_t nslots,
+    int64_t N, int32_t* gerr, unsigned long long* cV, int32_t* maxc) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t base = w0 * 32; base < N; base += nwarps * 32) {
+    const int64_t v = base + lane;
+    int32_t s = -1;
+    int64_t rs = 0, d = 0;
+    bool bad = false;
+    int32_t w = 0;
+    if (v < N) {
+      int32_t lo = 0, hi = nslots - 1;
+      while (lo < hi) {
+        const int32_t mid = (lo + hi + 1) >> 1;
+        if (noff[mid] <= v) lo = mid; else hi = mid - 1;
+      }
+      s = lo;
+      rs = row_ptr[v];
+      const int64_t re = row_ptr[v + 1];
+      if (rs > re || rs < aoff[s] || re > aoff[s + 1]) bad = true;
+      if (v == noff[s] && rs != aoff[s]) bad = true;
+      if (v == noff[s + 1] - 1 && re != aoff[s + 1]) bad = true;
+      w = nw[v];
+      if (w <= 0) bad = true;
+      d = bad ? 0 : re - rs;
     }
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
-    wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
-  }
-  if ((threadIdx.x & 31) == 0) {
-    atomicAdd(cV, wsum);
-    atomicMax(maxc, wmax);
+    // per-slot sums of node weights (lanes of one slot merged)
+    const unsigned mm = __match_any_sync(0xffffffffu, s);
+    const int64_t wsum = match_sum(mm, w > 0 ? w : 0);
+    const int wmax = __reduce_max_sync(mm, w > 0 ? w : 0);
+    if (s >= 0 && lane == __ffs(mm) - 1) {
+      atomicAdd(&cV[s], (unsigned long long)wsum);
+      atomicMax(&maxc[s], wmax);
+    }
+    long long incl = d;
+    for (int o = 1; o < 32; o <<= 1) {
+      long long y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const long long excl = incl - d;
+    const long long total = __shfl_sync(0xffffffffu, incl, 31);
+    for (long long x0 = 0; x0 < total; x0 += 32) {
+      const long long x = x0 + lane;
+      int L = 0;
+      for (int step = 16; step > 0; step >>= 1) {
+        long long y = __shfl_sync(0xffffffffu, incl, L + step - 1);
+        if (y <= x) L += step;
+      }
+      const long long rsL = __shfl_sync(0xffffffffu, (long long)rs, L);
+      const long long exL = __shfl_sync(0xffffffffu, excl, L);
+      const int32_t sL = __shfl_sync(0xffffffffu, s, L);
+      if (x < total) {
+        const int64_t e = rsL + (x - exL);
+        const int64_t src = base + L;
+        const int32_t c = col[e];
+        if (c < noff[sL] || c >= noff[sL + 1] || c == src || ew[e] <= 0) atomicOr(&gerr[sL], 1);
+      }
+    }
+    if (bad && s >= 0) atomicOr(&gerr[s], 1);
   }
 }
 
@@ -95,6 +135,12 @@ __global__ void k_check_range(const int32_t* __restrict__ a, int64_t n, int64_t 
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
        v += (int64_t)gridDim.x * blockDim.x)
     if (a[v] < lo || a[v] >= hi) atomicOr(err, DERR_BAD_CSR);
+}
+
+__global__ void k_gather_at(const int64_t* __restrict__ src, const int64_t* __restrict__ idx, int n,
+                            int64_t* __restrict__ dst) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    dst[i] = src[idx[i]];
 }
 
 struct OutTask {
@@ -130,7 +176,7 @@ struct Slots {
     std::vector<int32_t> r(sp.nslots);
     SCLAP_CUDA(cudaMemcpyAsync(r.data(), rounds.p, r.size() * sizeof(int32_t),
                                cudaMemcpyDeviceToHost, s));
-    SCLAP_CUDA(cudaStreamSynchronize(s));
+    stream_sync(s);
     return r;
   }
 };
@@ -179,7 +225,7 @@ void bounds(int64_t cV, int64_t maxc, int32_t k, double eps, int32_t f, int64_t*
 void check_err(int32_t* d_err, cudaStream_t s) {
   int32_t e = 0;
   SCLAP_CUDA(cudaMemcpyAsync(&e, d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-  SCLAP_CUDA(cudaStreamSynchronize(s));
+  stream_sync(s);
   if (e & DERR_W_OVERFLOW) throw Error(SCLAP_EOVERFLOW, "coarse edge weight above INT32_MAX");
   if (e & DERR_HASH_FULL) throw Error(SCLAP_EINTERNAL, "hash table full");
   if (e & DERR_BAD_CSR) throw Error(SCLAP_ECSR, "malformed CSR");
@@ -191,32 +237,60 @@ void check_range(const int32_t* a, int64_t n, int64_t lo, int64_t hi, cudaStream
                  const char* what) {
   DevBuf<int32_t> err(1, s);
   err.zero();
-  k_check_range<<<grid_for(n, 256, (int64_t)num_sms() * 8), 256, 0, s>>>(a, n, lo, hi, err.p); SCLAP_NOTE_LAUNCH();
+  k_check_range<<<grid_for(n, 256, (int64_t)num_sms() * 8), 256, 0, s>>>(a, n, lo, hi, err.p); SCLAP_NOTE_LAUNCH("k_check_range");
   SCLAP_LAUNCH_CHECK();
   int32_t e = 0;
   SCLAP_CUDA(cudaMemcpyAsync(&e, err.p, 4, cudaMemcpyDeviceToHost, s));
-  SCLAP_CUDA(cudaStreamSynchronize(s));
+  stream_sync(s);
   if (e) throw Error(SCLAP_EINVAL, std::string(what) + " out of range");
 }
 
-// Validates one device-resident graph; returns c(V) and max c(v).
-void validate(const GIn& g, cudaStream_t s, int64_t* cV, int64_t* maxc) {
-  DevBuf<int32_t> err(1, s), mx(1, s);
-  DevBuf<unsigned long long> sum(1, s);
+void build_level0(const std::vector<GIn>& gs, struct Level& L, cudaStream_t s);
+
+// Validates the batched level L (built by build_level0 from `B` inputs):
+// per-graph status (SCLAP_OK, SCLAP_ECSR or SCLAP_EOVERFLOW), c(V), max c(v).
+void validate_level(const Level& L, int B, std::vector<int32_t>& status,
+                    std::vector<int64_t>& cV, std::vector<int64_t>& maxc, cudaStream_t s) {
+  DevBuf<int32_t> err(B, s), mx(B, s);
+  DevBuf<unsigned long long> sum(B, s);
+  DevBuf<int64_t> d_aoff(B + 1, s);
   err.zero(); mx.zero(); sum.zero();
-  k_validate<<<grid_for(g.n, 256, (int64_t)num_sms() * 8), 256, 0, s>>>(
-      g.row_ptr, g.col, g.nw, g.ew, g.n, g.m, err.p, sum.p, mx.p); SCLAP_NOTE_LAUNCH();
-  SCLAP_LAUNCH_CHECK();
-  int32_t e = 0, m = 0;
-  unsigned long long w = 0;
-  SCLAP_CUDA(cudaMemcpyAsync(&e, err.p, 4, cudaMemcpyDeviceToHost, s));
-  SCLAP_CUDA(cudaMemcpyAsync(&m, mx.p, 4, cudaMemcpyDeviceToHost, s));
-  SCLAP_CUDA(cudaMemcpyAsync(&w, sum.p, 8, cudaMemcpyDeviceToHost, s));
-  SCLAP_CUDA(cudaStreamSynchronize(s));
-  if (e) throw Error(SCLAP_ECSR, "malformed CSR (row_ptr, column range, self-loop or weight)");
-  if (w >= (1ull << 31)) throw Error(SCLAP_EOVERFLOW, "sum of node weights must be < 2^31");
-  *cV = (int64_t)w;
-  *maxc = m;
+  d_aoff.upload(L.aoff);
+  if (L.N > 0) {
+    k_validate_level<<<grid_for(L.N, 256, (int64_t)num_sms() * 16), 256, 0, s>>>(
+        L.row_ptr.p, L.col.p, L.ew.p, L.nw.p, L.noff_d.p, d_aoff.p, B, L.N, err.p, sum.p, mx.p); SCLAP_NOTE_LAUNCH("k_validate_level");
+    SCLAP_LAUNCH_CHECK();
+  }
+  std::vector<int32_t> e(B), m(B);
+  std::vector<unsigned long long> w(B);
+  SCLAP_CUDA(cudaMemcpyAsync(e.data(), err.p, B * 4, cudaMemcpyDeviceToHost, s));
+  SCLAP_CUDA(cudaMemcpyAsync(m.data(), mx.p, B * 4, cudaMemcpyDeviceToHost, s));
+  SCLAP_CUDA(cudaMemcpyAsync(w.data(), sum.p, B * 8, cudaMemcpyDeviceToHost, s));
+  stream_sync(s);
+  status.assign(B, SCLAP_OK);
+  cV.assign(B, 0);
+  maxc.assign(B, 0);
+  for (int g = 0; g < B; ++g) {
+    if (e[g]) status[g] = SCLAP_ECSR;
+    else if (w[g] >= (1ull << 31)) status[g] = SCLAP_EOVERFLOW;
+    cV[g] = (int64_t)w[g];
+    maxc[g] = m[g];
+  }
+}
+
+// Validates one device-resident graph (step entry points); returns c(V) and
+// max c(v) or throws.
+void validate(const GIn& g, cudaStream_t s, int64_t* cV, int64_t* maxc) {
+  Level L;
+  build_level0({g}, L, s);
+  std::vector<int32_t> st;
+  std::vector<int64_t> a, b;
+  validate_level(L, 1, st, a, b, s);
+  if (st[0] == SCLAP_ECSR)
+    throw Error(SCLAP_ECSR, "malformed CSR (row_ptr, column range, self-loop or weight)");
+  if (st[0] == SCLAP_EOVERFLOW) throw Error(SCLAP_EOVERFLOW, "sum of node weights must be < 2^31");
+  *cV = a[0];
+  *maxc = b[0];
 }
 
 // Builds the level holding the graphs `gs` back to back.
@@ -238,7 +312,7 @@ void build_level0(const std::vector<GIn>& gs, Level& L, cudaStream_t s) {
   std::vector<CopyTask> tasks(B);
   for (int i = 0; i < B; ++i)
     tasks[i] = CopyTask{gs[i].row_ptr, gs[i].col, gs[i].ew, gs[i].nw, 0, 0, gs[i].n, gs[i].m,
-                        L.noff[i], L.aoff[i]};
+                        L.noff[i], L.aoff[i], nullptr, 0};
   ip_replicate(tasks, L.row_ptr.p, L.col.p, L.ew.p, L.nw.p, L.M, s);
   L.noff_d.alloc(B + 1, s);
   L.noff_d.upload(L.noff);
@@ -281,20 +355,52 @@ void run_ip(const std::vector<IPIn>& in, const sclap_config& cfg, int64_t* Wg,
   const int B = (int)in.size();
   const int T = cfg.ip_trials;
   const int S = B * T;
+  // Trials run on the nodes that have neighbours: per level holding coarsest
+  // graphs, rank them (scan of "has neighbours") and keep the isolated
+  // nodes' weight prefix for the water-filling afterwards.
+  struct LevelAux {
+    DevBuf<int64_t> rank, iso_prefix;
+    std::vector<int64_t> rank_at;
+  };
+  std::vector<std::pair<const Level*, std::unique_ptr<LevelAux>>> aux;
+  auto aux_of = [&](const Level* Q) -> LevelAux& {
+    for (auto& p : aux)
+      if (p.first == Q) return *p.second;
+    std::unique_ptr<LevelAux> x(new LevelAux());
+    const int ns = (int)Q->noff.size() - 1;
+    DevBuf<uint8_t> flags(std::max<int64_t>(Q->N, 1), s);
+    DevBuf<int32_t> iso(std::max<int64_t>(Q->N, 1), s);
+    isolated_flags(Q->row_ptr.p, Q->nw.p, Q->N, flags.p, iso.p, s);
+    x->rank.alloc(Q->N + 1, s);
+    x->iso_prefix.alloc(Q->N + 1, s);
+    scan_excl_u8_to_i64(flags.p, x->rank.p, Q->N, s);
+    scan_excl_i32_to_i64(iso.p, x->iso_prefix.p, Q->N, s);
+    x->rank_at.assign(ns + 1, 0);
+    DevBuf<int64_t> got(ns + 1, s);
+    k_gather_at<<<grid_for(ns + 1, 128, 64), 128, 0, s>>>(x->rank.p, Q->noff_d.p, ns + 1, got.p); SCLAP_NOTE_LAUNCH("k_gather_at");
+    SCLAP_LAUNCH_CHECK();
+    SCLAP_CUDA(cudaMemcpyAsync(x->rank_at.data(), got.p, (ns + 1) * sizeof(int64_t),
+                               cudaMemcpyDeviceToHost, s));
+    stream_sync(s);
+    aux.emplace_back(Q, std::move(x));
+    return *aux.back().second;
+  };
   std::vector<int64_t> noff(S + 1, 0), aoff(S + 1, 0), boff(S + 1, 0);
   std::vector<CopyTask> tasks;
   tasks.reserve(S);
   for (int g = 0; g < B; ++g) {
     const Level& Q = *in[g].Q;
+    LevelAux& X = aux_of(&Q);
     const int x = in[g].g;
     const int64_t n = Q.noff[x + 1] - Q.noff[x], m = Q.aoff[x + 1] - Q.aoff[x];
+    const int64_t nA = X.rank_at[x + 1] - X.rank_at[x];
     for (int t = 0; t < T; ++t) {
       const int i = g * T + t;
-      noff[i + 1] = noff[i] + n;
+      noff[i + 1] = noff[i] + nA;
       aoff[i + 1] = aoff[i] + m;
       boff[i + 1] = boff[i] + in[g].k;
       tasks.push_back(CopyTask{Q.row_ptr.p, Q.col.p, Q.ew.p, Q.nw.p, Q.noff[x], Q.aoff[x], n, m,
-                               noff[i], aoff[i]});
+                               noff[i], aoff[i], X.rank.p, X.rank_at[x]});
     }
   }
   Level ip;
@@ -305,7 +411,7 @@ void run_ip(const std::vector<IPIn>& in, const sclap_config& cfg, int64_t* Wg,
   ip.col.alloc(std::max<int64_t>(ip.M, 1), s);
   ip.ew.alloc(std::max<int64_t>(ip.M, 1), s);
   ip.nw.alloc(std::max<int64_t>(ip.N, 1), s);
-  ip_replicate(tasks, ip.row_ptr.p, ip.col.p, ip.ew.p, ip.nw.p, ip.M, s);
+  ip_replicate(tasks, ip.row_ptr.p, ip.col.p, ip.ew.p, ip.nw.p, ip.M, s, ip.N);
   ip.noff = noff;
   ip.aoff = aoff;
   ip.noff_d.alloc(S + 1, s);
@@ -358,25 +464,81 @@ void run_ip(const std::vector<IPIn>& in, const sclap_config& cfg, int64_t* Wg,
   for (int g = 0; g < B; ++g) {
     const Level& Q = *in[g].Q;
     const int x = in[g].g;
+    LevelAux& X = aux_of(&Q);
     sel[g] = SelectTask{in[g].dst_blk, Q.noff[x], Q.noff[x + 1] - Q.noff[x], (int64_t)g * T, T,
-                        in[g].k, in[g].Lmax, in[g].boff, g};
+                        in[g].k, in[g].Lmax, in[g].boff, g, X.rank.p, X.rank_at[x]};
   }
   DevBuf<int32_t> d_best(B, s);
   DevBuf<int64_t> d_cut(B, s);
   ip_select_copy(sel, cut2.p, W.p, ip.noff_d.p, d_boff.p, label.p, Wg, d_best.p, d_cut.p, s);
+  std::vector<FillTask> fill(B);
+  int64_t Kmax = 0;
+  for (int g = 0; g < B; ++g) {
+    const Level& Q = *in[g].Q;
+    LevelAux& X = aux_of(&Q);
+    const int x = in[g].g;
+    fill[g] = FillTask{in[g].dst_blk, Q.nw.p, X.iso_prefix.p, Q.noff[x], Q.noff[x + 1] - Q.noff[x],
+                       in[g].boff, in[g].k};
+    Kmax = std::max(Kmax, in[g].boff + in[g].k);
+  }
+  waterfill_isolated(fill, Wg, Kmax, s);
   best.assign(B, 0);
   ipcut.assign(B, 0);
   SCLAP_CUDA(cudaMemcpyAsync(best.data(), d_best.p, B * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   SCLAP_CUDA(cudaMemcpyAsync(ipcut.data(), d_cut.p, B * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-  SCLAP_CUDA(cudaStreamSynchronize(s));
+  stream_sync(s);
 }
 
 // ---------------------------------------------------------------------------
 // The multilevel partitioner over a batch of validated graphs.
 // ---------------------------------------------------------------------------
-void run_batch(const std::vector<GIn>& gs, const std::vector<int64_t>& cV,
-               const std::vector<int64_t>& maxc, const sclap_config& cfg,
-               const std::vector<int32_t*>& outs, std::vector<GOut>& res, cudaStream_t s) {
+void run_valid_batch(const std::vector<GIn>& gs, const std::vector<int64_t>& cV,
+                     const std::vector<int64_t>& maxc, const sclap_config& cfg,
+                     const std::vector<int32_t*>& outs, std::vector<GOut>& res,
+                     std::unique_ptr<Level> level0, cudaStream_t s);
+
+// Validates the inputs on the device and partitions the valid ones together;
+// invalid graphs get their error in res[g].status.
+void run_batch(const std::vector<GIn>& gs_in, const sclap_config& cfg,
+               const std::vector<int32_t*>& outs_in, std::vector<GOut>& res, cudaStream_t s) {
+  const int B = (int)gs_in.size();
+  res.assign(B, GOut{});
+  if (profile().timeline.load()) timeline_mark("<call>", s);
+  std::unique_ptr<Level> L0(new Level());
+  build_level0(gs_in, *L0, s);
+  std::vector<int32_t> status;
+  std::vector<int64_t> cV, maxc;
+  validate_level(*L0, B, status, cV, maxc, s);
+  std::vector<int> ok;
+  for (int g = 0; g < B; ++g) {
+    if (status[g] == SCLAP_OK) ok.push_back(g);
+    else res[g].status = status[g];
+  }
+  if ((int)ok.size() == B) {
+    run_valid_batch(gs_in, cV, maxc, cfg, outs_in, res, std::move(L0), s);
+    return;
+  }
+  if (ok.empty()) return;
+  std::vector<GIn> gs;
+  std::vector<int64_t> c2, m2;
+  std::vector<int32_t*> outs;
+  for (int g : ok) {
+    gs.push_back(gs_in[g]);
+    c2.push_back(cV[g]);
+    m2.push_back(maxc[g]);
+    outs.push_back(outs_in[g]);
+  }
+  L0.reset(new Level());
+  build_level0(gs, *L0, s);
+  std::vector<GOut> r2;
+  run_valid_batch(gs, c2, m2, cfg, outs, r2, std::move(L0), s);
+  for (size_t j = 0; j < ok.size(); ++j) res[ok[j]] = r2[j];
+}
+
+void run_valid_batch(const std::vector<GIn>& gs, const std::vector<int64_t>& cV,
+                     const std::vector<int64_t>& maxc, const sclap_config& cfg,
+                     const std::vector<int32_t*>& outs, std::vector<GOut>& res,
+                     std::unique_ptr<Level> level0, cudaStream_t s) {
   const int B = (int)gs.size();
   res.assign(B, GOut{});
   std::vector<GState> st(B);
@@ -400,8 +562,7 @@ void run_batch(const std::vector<GIn>& gs, const std::vector<int64_t>& cV,
   const int sms = num_sms();
 
   std::vector<std::unique_ptr<Level>> lv;
-  lv.emplace_back(new Level());
-  build_level0(gs, *lv[0], s);
+  lv.push_back(std::move(level0));
 
   // ---------------- coarsening
   std::vector<char> coarsening(B, 0);
@@ -424,8 +585,8 @@ void run_batch(const std::vector<GIn>& gs, const std::vector<int64_t>& cV,
     Slots sl(s, B, cur.noff_d.p, h_loff, h_bound, h_seed, h_level, h_nlab, h_done);
     DevBuf<int32_t> label(std::max<int64_t>(v.N, 1), s);
     DevBuf<int64_t> W(std::max<int64_t>(v.N, 1), s);
-    k_iota<<<grid_for(v.N, 256, (int64_t)sms * 16), 256, 0, s>>>(label.p, v.N); SCLAP_NOTE_LAUNCH();
-    k_w_from_nw<<<grid_for(v.N, 256, (int64_t)sms * 16), 256, 0, s>>>(v.nw, v.N, W.p); SCLAP_NOTE_LAUNCH();
+    k_iota<<<grid_for(v.N, 256, (int64_t)sms * 16), 256, 0, s>>>(label.p, v.N); SCLAP_NOTE_LAUNCH("k_iota");
+    k_w_from_nw<<<grid_for(v.N, 256, (int64_t)sms * 16), 256, 0, s>>>(v.nw, v.N, W.p); SCLAP_NOTE_LAUNCH("k_w_from_nw");
     SCLAP_LAUNCH_CHECK();
     LPRun run;
     run.mode = MODE_CLUSTER;
@@ -562,13 +723,13 @@ void run_batch(const std::vector<GIn>& gs, const std::vector<int64_t>& cV,
   d_ot.upload(ot);
   for (int b0 = 0; b0 < B; b0 += 65535) {
     dim3 grid(grid_for(mx, 256, 256), (unsigned)std::min(65535, B - b0));
-    k_write_out<<<grid, 256, 0, s>>>(d_ot.p + b0, F0.blk.p); SCLAP_NOTE_LAUNCH();
+    k_write_out<<<grid, 256, 0, s>>>(d_ot.p + b0, F0.blk.p); SCLAP_NOTE_LAUNCH("k_write_out");
   }
   SCLAP_LAUNCH_CHECK();
   std::vector<int64_t> h_cut2(B), h_W(Ktot);
   SCLAP_CUDA(cudaMemcpyAsync(h_cut2.data(), cut2.p, B * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   SCLAP_CUDA(cudaMemcpyAsync(h_W.data(), Wg.p, Ktot * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-  SCLAP_CUDA(cudaStreamSynchronize(s));
+  stream_sync(s);
   for (int g = 0; g < B; ++g) {
     GOut& o = res[g];
     o.cut = h_cut2[g] / 2;
@@ -624,7 +785,7 @@ void check_args(int64_t n, const void* row_ptr, const void* col, int32_t k, doub
 int64_t device_arcs(const int64_t* row_ptr, int64_t n, cudaStream_t s) {
   int64_t m = 0;
   SCLAP_CUDA(cudaMemcpyAsync(&m, row_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-  SCLAP_CUDA(cudaStreamSynchronize(s));
+  stream_sync(s);
   if (m < 0 || m >= ((int64_t)1 << 40)) throw Error(SCLAP_ECSR, "row_ptr[n] out of range");
   return m;
 }
@@ -712,13 +873,13 @@ int sclap_partition(int64_t n, const int64_t* row_ptr, const int32_t* col, const
     cudaStream_t s = 0;
     HostUpload up(n, row_ptr, col, node_w, edge_w, s);
     up.g.k = k; up.g.eps = eps; up.g.seed = seed;
-    int64_t cV, maxc;
-    validate(up.g, s, &cV, &maxc);
     DevBuf<int32_t> out(n, s);
     std::vector<GOut> res;
-    run_batch({up.g}, {cV}, {maxc}, c, {out.p}, res, s);
+    run_batch({up.g}, c, {out.p}, res, s);
+    if (res[0].status != SCLAP_OK && res[0].status != SCLAP_EINFEASIBLE)
+      throw Error(res[0].status, "invalid input graph");
     SCLAP_CUDA(cudaMemcpyAsync(block_out, out.p, n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    SCLAP_CUDA(cudaStreamSynchronize(s));
+    stream_sync(s);
     if (cut_out) *cut_out = res[0].cut;
     if (max_block_weight_out) *max_block_weight_out = res[0].maxbw;
     fill_stats(stats, res[0]);
@@ -741,11 +902,11 @@ int sclap_partition_device(int64_t n, const int64_t* row_ptr, const int32_t* col
     g.n = n; g.m = device_arcs(row_ptr, n, s); g.row_ptr = row_ptr; g.col = col;
     g.nw = node_w; g.ew = edge_w; g.k = k; g.eps = eps; g.seed = seed;
     check_col(g.col, g.m);
-    int64_t cV, maxc;
-    validate(g, s, &cV, &maxc);
     std::vector<GOut> res;
-    run_batch({g}, {cV}, {maxc}, c, {block_out}, res, s);
-    SCLAP_CUDA(cudaStreamSynchronize(s));
+    run_batch({g}, c, {block_out}, res, s);
+    if (res[0].status != SCLAP_OK && res[0].status != SCLAP_EINFEASIBLE)
+      throw Error(res[0].status, "invalid input graph");
+    stream_sync(s);
     if (cut_out) *cut_out = res[0].cut;
     if (max_block_weight_out) *max_block_weight_out = res[0].maxbw;
     fill_stats(stats, res[0]);
@@ -781,11 +942,7 @@ int sclap_partition_batch(int32_t count, sclap_graph* graphs, const sclap_config
         }
         g.k = G.k; g.eps = G.eps; g.seed = G.seed;
         check_col(g.col, g.m);
-        int64_t a, b;
-        validate(g, s, &a, &b);
         gs.push_back(g);
-        cV.push_back(a);
-        maxc.push_back(b);
         idx.push_back(i);
         if (device_ptrs) {
           outs.push_back(G.block_out);
@@ -798,7 +955,7 @@ int sclap_partition_batch(int32_t count, sclap_graph* graphs, const sclap_config
     }
     if (gs.empty()) return;
     std::vector<GOut> res;
-    run_batch(gs, cV, maxc, c, outs, res, s);
+    run_batch(gs, c, outs, res, s);
     for (size_t j = 0; j < gs.size(); ++j) {
       sclap_graph& G = graphs[idx[j]];
       if (!device_ptrs)
@@ -807,9 +964,10 @@ int sclap_partition_batch(int32_t count, sclap_graph* graphs, const sclap_config
       G.cut = res[j].cut;
       G.max_block_weight = res[j].maxbw;
       G.status = res[j].status;
+      if (G.status != SCLAP_OK && G.status != SCLAP_EINFEASIBLE) continue;
       if (G.status != SCLAP_OK && first_err == SCLAP_OK) first_err = G.status;
     }
-    SCLAP_CUDA(cudaStreamSynchronize(s));
+    stream_sync(s);
   });
   return rc != SCLAP_OK ? rc : first_err;
 }
@@ -848,7 +1006,7 @@ int sclap_lp_round(int32_t mode, int64_t n, const int64_t* row_ptr, const int32_
     check_err(d_err.p, s);
     int64_t mv = 0;
     SCLAP_CUDA(cudaMemcpyAsync(&mv, sl.moved.p, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    SCLAP_CUDA(cudaStreamSynchronize(s));
+    stream_sync(s);
     if (moved_out) *moved_out = mv;
   });
 }
@@ -871,8 +1029,8 @@ int sclap_cluster(int64_t n, const int64_t* row_ptr, const int32_t* col, const i
     single_level(g, L, s);
     Slots sl(s, 1, L.noff_d.p, {0}, {U}, {seed}, {level}, {0}, {0});
     DevBuf<int64_t> W(n, s);
-    k_iota<<<grid_for(n, 256, (int64_t)num_sms() * 16), 256, 0, s>>>(label_out, n); SCLAP_NOTE_LAUNCH();
-    k_w_from_nw<<<grid_for(n, 256, (int64_t)num_sms() * 16), 256, 0, s>>>(L.nw.p, n, W.p); SCLAP_NOTE_LAUNCH();
+    k_iota<<<grid_for(n, 256, (int64_t)num_sms() * 16), 256, 0, s>>>(label_out, n); SCLAP_NOTE_LAUNCH("k_iota");
+    k_w_from_nw<<<grid_for(n, 256, (int64_t)num_sms() * 16), 256, 0, s>>>(L.nw.p, n, W.p); SCLAP_NOTE_LAUNCH("k_w_from_nw");
     LPRun run;
     run.mode = MODE_CLUSTER;
     run.phase = PH_CLUSTER;
@@ -919,7 +1077,7 @@ int sclap_contract(int64_t n, const int64_t* row_ptr, const int32_t* col, const 
       SCLAP_CUDA(cudaMemcpyAsync(ccol, co.col.p, co.M * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
       SCLAP_CUDA(cudaMemcpyAsync(cedge_w, co.ew.p, co.M * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
     }
-    SCLAP_CUDA(cudaStreamSynchronize(s));
+    stream_sync(s);
     if (nc_out) *nc_out = co.N;
     if (mc_out) *mc_out = co.M;
   });
@@ -1009,18 +1167,30 @@ int sclap_cut(int64_t n, const int64_t* row_ptr, const int32_t* col, const int32
     slot_cut(L.view(), block, cut2.p, s);
     int64_t c2 = 0;
     SCLAP_CUDA(cudaMemcpyAsync(&c2, cut2.p, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    SCLAP_CUDA(cudaStreamSynchronize(s));
+    stream_sync(s);
     if (cut_out) *cut_out = c2 / 2;
   });
 }
 
 void sclap_profile_enable(int on) { profile().enabled.store(on != 0); }
 
+void sclap_profile_timeline(int on) { profile().timeline.store(on != 0); }
+
+int64_t sclap_profile_dump(char* buf, int64_t cap) {
+  const std::string t = timeline_dump();
+  if (buf && cap > 0) {
+    const int64_t n = std::min<int64_t>(cap - 1, (int64_t)t.size());
+    std::memcpy(buf, t.data(), (size_t)n);
+    buf[n] = 0;
+  }
+  return (int64_t)t.size() + 1;
+}
+
 void sclap_profile_reset(void) {
   ProfileState& P = profile();
   std::lock_guard<std::mutex> lk(P.mu);
   P.launches.store(0);
-  for (int b = 0; b < 7; ++b) { P.ms[b] = 0; P.nlaunch[b] = 0; P.nodes[b] = 0; P.arcs[b] = 0; }
+  for (int b = 0; b < 4; ++b) { P.ms[b] = 0; P.nlaunch[b] = 0; P.nodes[b] = 0; P.arcs[b] = 0; }
 }
 
 void sclap_profile_read(sclap_profile* out) {
@@ -1028,7 +1198,7 @@ void sclap_profile_read(sclap_profile* out) {
   ProfileState& P = profile();
   std::lock_guard<std::mutex> lk(P.mu);
   out->kernel_launches = P.launches.load();
-  for (int b = 0; b < 7; ++b) {
+  for (int b = 0; b < 4; ++b) {
     out->propose_launches[b] = P.nlaunch[b];
     out->propose_ms[b] = P.ms[b];
     out->propose_nodes[b] = P.nodes[b];

@@ -20,11 +20,19 @@ __global__ void k_replicate(const CopyTask* __restrict__ tasks, int64_t* __restr
   const CopyTask t = tasks[blockIdx.y];
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < t.n; v += stride) {
-    row_ptr[t.dst_n0 + v] = t.dst_a0 + (t.row_ptr[t.src_n0 + v] - t.src_a0);
-    nw[t.dst_n0 + v] = t.nw ? t.nw[t.src_n0 + v] : 1;
+    int64_t d = v;
+    if (t.rank) {
+      const int64_t r0 = t.rank[t.src_n0 + v];
+      if (t.rank[t.src_n0 + v + 1] == r0) continue;   // isolated: dropped
+      d = r0 - t.rbase;
+    }
+    row_ptr[t.dst_n0 + d] = t.dst_a0 + (t.row_ptr[t.src_n0 + v] - t.src_a0);
+    nw[t.dst_n0 + d] = t.nw ? t.nw[t.src_n0 + v] : 1;
   }
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < t.m; e += stride) {
-    col[t.dst_a0 + e] = (int32_t)(t.col[t.src_a0 + e] - t.src_n0 + t.dst_n0);
+    const int64_t u = t.col[t.src_a0 + e];
+    const int64_t du = t.rank ? t.rank[u] - t.rbase : u - t.src_n0;
+    col[t.dst_a0 + e] = (int32_t)(du + t.dst_n0);
     ew[t.dst_a0 + e] = t.ew ? t.ew[t.src_a0 + e] : 1;
   }
 }
@@ -276,8 +284,15 @@ __global__ void k_select_copy(const SelectTask* __restrict__ tasks, const int64_
   __syncthreads();
   const int64_t slot = t.slot0 + bt_sh;
   const int64_t src = ip_noff[slot], sbo = ip_boff[slot];
-  for (int64_t v = threadIdx.x; v < t.n; v += blockDim.x)
-    t.dst_blk[t.dst_n0 + v] = (int32_t)(t.g_boff + (ip_label[src + v] - sbo));
+  for (int64_t v = threadIdx.x; v < t.n; v += blockDim.x) {
+    int64_t d = v;
+    if (t.rank) {
+      const int64_t r0 = t.rank[t.dst_n0 + v];
+      if (t.rank[t.dst_n0 + v + 1] == r0) { t.dst_blk[t.dst_n0 + v] = -1; continue; }
+      d = r0 - t.rbase;
+    }
+    t.dst_blk[t.dst_n0 + v] = (int32_t)(t.g_boff + (ip_label[src + d] - sbo));
+  }
   for (int32_t b = threadIdx.x; b < t.k; b += blockDim.x) Wg[t.g_boff + b] = ip_W[sbo + b];
 }
 
@@ -297,10 +312,102 @@ __global__ void k_block_weights(const int32_t* __restrict__ label, const int32_t
     atomicAdd(ull(&W[label[v]]), (unsigned long long)nw[v]);
 }
 
+__global__ void k_isolated(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ nw,
+                           int64_t N, uint8_t* __restrict__ flags, int32_t* __restrict__ iso_w) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    const bool has = row_ptr[v + 1] > row_ptr[v];
+    flags[v] = has ? 1 : 0;
+    iso_w[v] = has ? 0 : nw[v];
+  }
+}
+
+// One thread per graph: fill level L (smallest L with sum_b max(0, L - W_b)
+// >= R), blocks ordered by (weight, id), and the start of each block's
+// stretch of free capacity below L.
+__global__ void k_wf_setup(const FillTask* __restrict__ tasks, int ntasks, const int64_t* Wg,
+                           int32_t* order, int64_t* A) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ntasks) return;
+  const FillTask t = tasks[i];
+  const int64_t R = t.iso_prefix[t.n0 + t.n] - t.iso_prefix[t.n0];
+  if (R == 0) return;
+  const int64_t* W = Wg + t.g_boff;
+  int64_t lo = W[0], hi = W[0];
+  for (int32_t b = 1; b < t.k; ++b) { lo = min(lo, W[b]); hi = max(hi, W[b]); }
+  hi += R;
+  while (lo < hi) {
+    const int64_t mid = lo + (hi - lo) / 2;
+    int64_t f = 0;
+    for (int32_t b = 0; b < t.k; ++b) f += max64(0, mid - W[b]);
+    if (f >= R) hi = mid; else lo = mid + 1;
+  }
+  int32_t* ord = order + t.g_boff;
+  for (int32_t j = 0; j < t.k; ++j) {
+    int32_t p = j;
+    while (p > 0) {
+      const int32_t q = ord[p - 1];
+      if (W[q] > W[j] || (W[q] == W[j] && q > j)) { ord[p] = q; --p; } else break;
+    }
+    ord[p] = j;
+  }
+  int64_t acc = 0;
+  for (int32_t j = 0; j < t.k; ++j) {
+    A[t.g_boff + j] = acc;
+    acc += max64(0, lo - W[ord[j]]);
+  }
+}
+
+__global__ void k_wf_assign(const FillTask* __restrict__ tasks, int64_t* Wg,
+                            const int32_t* __restrict__ order, const int64_t* __restrict__ A) {
+  const FillTask t = tasks[blockIdx.y];
+  const int64_t base = t.iso_prefix[t.n0];
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < t.n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    if (t.blk[t.n0 + v] >= 0) continue;
+    const int64_t p = t.iso_prefix[t.n0 + v] - base;
+    int32_t lo = 0, hi = t.k - 1;   // last j with A[j] <= p
+    while (lo < hi) {
+      const int32_t mid = (lo + hi + 1) >> 1;
+      if (A[t.g_boff + mid] <= p) lo = mid; else hi = mid - 1;
+    }
+    const int32_t b = order[t.g_boff + lo];
+    t.blk[t.n0 + v] = (int32_t)(t.g_boff + b);
+    atomicAdd(ull(&Wg[t.g_boff + b]), (unsigned long long)t.nw[t.n0 + v]);
+  }
+}
+
 }  // namespace
 
+void isolated_flags(const int64_t* row_ptr, const int32_t* nw, int64_t N, uint8_t* flags,
+                    int32_t* iso_w, cudaStream_t s) {
+  if (N <= 0) return;
+  k_isolated<<<grid_for(N, 256, (int64_t)num_sms() * 16), 256, 0, s>>>(row_ptr, nw, N, flags, iso_w); SCLAP_NOTE_LAUNCH("k_isolated");
+  SCLAP_LAUNCH_CHECK();
+}
+
+void waterfill_isolated(const std::vector<FillTask>& tasks, int64_t* Wg, int64_t Ktot,
+                        cudaStream_t s) {
+  if (tasks.empty()) return;
+  DevBuf<FillTask> d(tasks.size(), s);
+  d.upload(tasks);
+  DevBuf<int32_t> order(std::max<int64_t>(Ktot, 1), s);
+  DevBuf<int64_t> A(std::max<int64_t>(Ktot, 1), s);
+  const int nt = (int)tasks.size();
+  k_wf_setup<<<(nt + 127) / 128, 128, 0, s>>>(d.p, nt, Wg, order.p, A.p); SCLAP_NOTE_LAUNCH("k_wf_setup");
+  int64_t mx = 1;
+  for (const auto& t : tasks) mx = std::max(mx, t.n);
+  for (int t0 = 0; t0 < nt; t0 += 65535) {
+    dim3 grid(grid_for(mx, 256, 64), (unsigned)std::min(65535, nt - t0));
+    k_wf_assign<<<grid, 256, 0, s>>>(d.p + t0, Wg, order.p, A.p); SCLAP_NOTE_LAUNCH("k_wf_assign");
+  }
+  SCLAP_LAUNCH_CHECK();
+  stream_sync(s);   // task array freed on return
+}
+
 void ip_replicate(const std::vector<CopyTask>& tasks, int64_t* row_ptr, int32_t* col,
-                  int32_t* ew, int32_t* nw, int64_t M_total, cudaStream_t s) {
+                  int32_t* ew, int32_t* nw, int64_t M_total, cudaStream_t s,
+                  int64_t N_total_override) {
   if (tasks.empty()) return;
   DevBuf<CopyTask> d(tasks.size(), s);
   d.upload(tasks);
@@ -309,26 +416,30 @@ void ip_replicate(const std::vector<CopyTask>& tasks, int64_t* row_ptr, int32_t*
   for (size_t t0 = 0; t0 < tasks.size(); t0 += 65535) {
     const unsigned ny = (unsigned)std::min<size_t>(65535, tasks.size() - t0);
     dim3 grid(grid_for(mx, 256, 64), ny);
-    k_replicate<<<grid, 256, 0, s>>>(d.p + t0, row_ptr, col, ew, nw); SCLAP_NOTE_LAUNCH();
+    k_replicate<<<grid, 256, 0, s>>>(d.p + t0, row_ptr, col, ew, nw); SCLAP_NOTE_LAUNCH("k_replicate");
   }
   int64_t endv = M_total;
   int64_t Ntot = 0;
-  for (const auto& t : tasks) Ntot = std::max(Ntot, t.dst_n0 + t.n);
+  for (const auto& t : tasks) {
+    const int64_t nd = t.rank ? 0 : t.n;   // renumbered tasks: caller passes dst end below
+    Ntot = std::max(Ntot, t.dst_n0 + nd);
+  }
+  if (N_total_override >= 0) Ntot = N_total_override;
   SCLAP_CUDA(cudaMemcpyAsync(row_ptr + Ntot, &endv, sizeof(int64_t), cudaMemcpyHostToDevice, s));
-  SCLAP_CUDA(cudaStreamSynchronize(s));   // endv lives on the host stack
+  stream_sync(s);   // endv lives on the host stack
   SCLAP_LAUNCH_CHECK();
 }
 
 void ggg_trials(const GGGArgs& a, cudaStream_t s) {
   if (a.nslots <= 0) return;
-  k_ggg<<<(unsigned)std::min<int64_t>(a.nslots, (int64_t)num_sms() * 8), GNT, 0, s>>>(a); SCLAP_NOTE_LAUNCH();
+  k_ggg<<<(unsigned)std::min<int64_t>(a.nslots, (int64_t)num_sms() * 8), GNT, 0, s>>>(a); SCLAP_NOTE_LAUNCH("k_ggg");
   SCLAP_LAUNCH_CHECK();
 }
 
 void slot_cut(const LevelView& lv, const int32_t* label, int64_t* cut2, cudaStream_t s) {
   if (lv.N <= 0) return;
   k_slot_cut<<<grid_for(lv.N, 8, (int64_t)num_sms() * 16), 256, 0, s>>>(
-      lv.row_ptr, lv.col, lv.ew, lv.gid, label, lv.N, cut2); SCLAP_NOTE_LAUNCH();
+      lv.row_ptr, lv.col, lv.ew, lv.gid, label, lv.N, cut2); SCLAP_NOTE_LAUNCH("k_slot_cut");
   SCLAP_LAUNCH_CHECK();
 }
 
@@ -340,23 +451,23 @@ void ip_select_copy(const std::vector<SelectTask>& tasks, const int64_t* cut2,
   DevBuf<SelectTask> d(tasks.size(), s);
   d.upload(tasks);
   k_select_copy<<<(unsigned)tasks.size(), 256, 0, s>>>(d.p, cut2, ip_W, ip_noff, ip_boff,
-                                                       ip_label, Wg, best, ipcut); SCLAP_NOTE_LAUNCH();
+                                                       ip_label, Wg, best, ipcut); SCLAP_NOTE_LAUNCH("k_select_copy");
   SCLAP_LAUNCH_CHECK();
-  SCLAP_CUDA(cudaStreamSynchronize(s));   // the task array is freed on return
+  stream_sync(s);   // the task array is freed on return
 }
 
 void project(const int32_t* cmap, const int32_t* coarse_blk, int32_t* fine_blk, int64_t N,
              cudaStream_t s) {
   if (N <= 0) return;
   k_project<<<grid_for(N, 256, (int64_t)num_sms() * 16), 256, 0, s>>>(cmap, coarse_blk,
-                                                                      fine_blk, N); SCLAP_NOTE_LAUNCH();
+                                                                      fine_blk, N); SCLAP_NOTE_LAUNCH("k_project");
   SCLAP_LAUNCH_CHECK();
 }
 
 void block_weights(const int32_t* label, const int32_t* nw, int64_t N, int64_t* W,
                    cudaStream_t s) {
   if (N <= 0) return;
-  k_block_weights<<<grid_for(N, 256, (int64_t)num_sms() * 16), 256, 0, s>>>(label, nw, N, W); SCLAP_NOTE_LAUNCH();
+  k_block_weights<<<grid_for(N, 256, (int64_t)num_sms() * 16), 256, 0, s>>>(label, nw, N, W); SCLAP_NOTE_LAUNCH("k_block_weights");
   SCLAP_LAUNCH_CHECK();
 }
 

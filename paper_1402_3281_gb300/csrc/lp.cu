@@ -69,6 +69,8 @@ struct LPArgs {
   int64_t* boff;
   int64_t* arcs;         // arcs scanned (statistics)
   int64_t* karcs;        // arcs per (colour, bucket) key
+  int32_t* flags;        // [0]: a listed node sits in an overloaded block
+  int16_t* nkey;         // bucket key of each node this round (-1: not listed)
   // active nodes
   const uint8_t* act_cur;
   uint8_t* act_next;
@@ -141,54 +143,94 @@ __global__ void k_round_end(LPArgs a, int32_t nslots, int32_t stop_rule) {
 }
 
 // ------------------------------------------------------------- bucketing
-// PASS 0 counts nodes per (colour, bucket); PASS 1 scatters them.
-template <int PASS>
-__global__ void __launch_bounds__(256) k_bucket(LPArgs a, int64_t N) {
-  const int lane = threadIdx.x & 31;
-  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t base = w0 * 32; base < N; base += nw * 32) {
-    const int64_t v = base + lane;
-    int key = -1;
+// Pass 0 decides each node's (colour, bucket) key, stores it and counts per
+// key; pass 1 scatters the listed nodes into their key's range.  Both passes
+// aggregate per key in shared memory and touch the global counters once per
+// key per block (same-address global atomics serialise in L2).
+constexpr int BK_NT = 256;
+constexpr int BK_PER = 8;                    // nodes per thread
+constexpr int BK_TILE = BK_NT * BK_PER;      // nodes per block
+constexpr int MAX_KEYS = 64 * NB;
+
+__device__ __forceinline__ int node_key(const LPArgs& a, int64_t v, int64_t* deg_out,
+                                        bool* ov_out) {
+  const int32_t s = a.gid[v];
+  if (a.done[s]) return -1;
+  const int64_t deg = a.row_ptr[v + 1] - a.row_ptr[v];
+  bool take, ov = false;
+  if (a.mode == MODE_CLUSTER) {
+    take = deg > 0 && (a.act_cur == nullptr || a.act_cur[v]);
+  } else {
+    ov = a.W[a.label[v]] > a.bound[s];
+    if (a.mode == MODE_REPAIR) take = ov;
+    else take = (a.act_cur == nullptr || a.act_cur[v]) && (deg > 0 || ov);
+  }
+  if (!take) return -1;
+  const uint64_t hv = mix64(a.rkey[s] ^ (uint64_t)(v - a.noff[s]));
+  const int sub = (int)((uint32_t)(hv >> 32) % (uint32_t)a.S);
+  *deg_out = deg;
+  *ov_out = ov;
+  return sub * NB + bucket_of(deg, ov);
+}
+
+__global__ void __launch_bounds__(BK_NT) k_bucket_count(LPArgs a, int64_t N) {
+  __shared__ int sh_cnt[MAX_KEYS];
+  __shared__ unsigned long long sh_arcs[MAX_KEYS];
+  __shared__ int sh_ov;
+  const int nkeys = a.S * NB;
+  for (int j = threadIdx.x; j < nkeys; j += BK_NT) { sh_cnt[j] = 0; sh_arcs[j] = 0; }
+  if (threadIdx.x == 0) sh_ov = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * BK_TILE;
+  bool any_ov = false;
+#pragma unroll
+  for (int j = 0; j < BK_PER; ++j) {
+    const int64_t v = base + (int64_t)j * BK_NT + threadIdx.x;
+    if (v >= N) break;
     int64_t deg = 0;
-    if (v < N) {
-      const int32_t s = a.gid[v];
-      if (!a.done[s]) {
-        deg = a.row_ptr[v + 1] - a.row_ptr[v];
-        bool take, ov = false;
-        if (a.mode == MODE_CLUSTER) {
-          take = deg > 0 && (a.act_cur == nullptr || a.act_cur[v]);
-        } else {
-          ov = a.W[a.label[v]] > a.bound[s];
-          if (a.mode == MODE_REPAIR) take = ov;
-          else take = (a.act_cur == nullptr || a.act_cur[v]) && (deg > 0 || ov);
-        }
-        if (take) {
-          const uint64_t hv = mix64(a.rkey[s] ^ (uint64_t)(v - a.noff[s]));
-          const int sub = (int)((uint32_t)(hv >> 32) % (uint32_t)a.S);
-          key = sub * NB + bucket_of(deg, ov);
-        }
-      }
+    bool ov = false;
+    const int key = node_key(a, v, &deg, &ov);
+    a.nkey[v] = (int16_t)key;
+    if (key >= 0) {
+      atomicAdd(&sh_cnt[key], 1);
+      atomicAdd(&sh_arcs[key], (unsigned long long)deg);
+      any_ov = any_ov || ov;
     }
-    const unsigned mm = __match_any_sync(0xffffffffu, key);
-    const int leader = __ffs(mm) - 1;
-    if (PASS == 0) {
-      long long dsum = warp_sum_ll(key >= 0 ? deg : 0);
-      const int64_t ksum = match_sum(mm, key >= 0 ? (int32_t)deg : 0);
-      if (key >= 0 && lane == leader) {
-        atomicAdd(&a.bcnt[key], __popc(mm));
-        atomicAdd(ull(&a.karcs[key]), (unsigned long long)ksum);
-      }
-      if (lane == 0 && dsum) atomicAdd(ull(a.arcs), (unsigned long long)dsum);
-    } else {
-      int base_pos = 0;
-      if (key >= 0 && lane == leader) base_pos = atomicAdd(&a.bfill[key], __popc(mm));
-      base_pos = __shfl_sync(0xffffffffu, base_pos, leader);
-      if (key >= 0) {
-        const int rank = __popc(mm & ((1u << lane) - 1));
-        a.list[a.boff[key] + base_pos + rank] = (int32_t)v;
-      }
+  }
+  if (any_ov) sh_ov = 1;
+  __syncthreads();
+  for (int j = threadIdx.x; j < nkeys; j += BK_NT) {
+    if (sh_cnt[j]) {
+      atomicAdd(&a.bcnt[j], sh_cnt[j]);
+      atomicAdd(ull(&a.karcs[j]), sh_arcs[j]);
     }
+  }
+  if (threadIdx.x == 0 && sh_ov) atomicOr(&a.flags[0], 1);
+}
+
+__global__ void __launch_bounds__(BK_NT) k_bucket_scatter(LPArgs a, int64_t N) {
+  __shared__ int sh_cnt[MAX_KEYS];
+  __shared__ int sh_base[MAX_KEYS];
+  const int nkeys = a.S * NB;
+  for (int j = threadIdx.x; j < nkeys; j += BK_NT) sh_cnt[j] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * BK_TILE;
+  int key[BK_PER], rank[BK_PER];
+#pragma unroll
+  for (int j = 0; j < BK_PER; ++j) {
+    const int64_t v = base + (int64_t)j * BK_NT + threadIdx.x;
+    key[j] = v < N ? a.nkey[v] : -1;
+    rank[j] = key[j] >= 0 ? atomicAdd(&sh_cnt[key[j]], 1) : 0;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < nkeys; j += BK_NT)
+    sh_base[j] = sh_cnt[j] ? (int)atomicAdd(&a.bfill[j], sh_cnt[j]) : 0;
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < BK_PER; ++j) {
+    if (key[j] < 0) continue;
+    const int64_t v = base + (int64_t)j * BK_NT + threadIdx.x;
+    a.list[a.boff[key[j]] + sh_base[key[j]] + rank[j]] = (int32_t)v;
   }
 }
 
@@ -208,11 +250,12 @@ __global__ void k_bucket_offsets(LPArgs a, int nkeys) {
 // Degrees <= G: one group of G lanes per node, one arc per lane; equal labels
 // are merged with a warp match and their weights summed.
 template <int G>
-__global__ void __launch_bounds__(256) k_propose_small(LPArgs a, int64_t lbeg, int64_t cnt) {
+__device__ __forceinline__ void propose_small(const LPArgs& a, int64_t lbeg, int64_t cnt,
+                                              int64_t blk, int64_t nblk) {
   constexpr int GPW = 32 / G;
   const int lane = threadIdx.x & 31, gw = lane / G, gl = lane % G;
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t warp = (blk * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = (nblk * blockDim.x) >> 5;
   for (int64_t t0 = warp * GPW; t0 < cnt; t0 += nwarps * GPW) {
     const int64_t li = t0 + gw;
     const bool has = li < cnt;
@@ -240,6 +283,20 @@ __global__ void __launch_bounds__(256) k_propose_small(LPArgs a, int64_t lbeg, i
     cd = warp_best(cd, G);
     if (has && gl == 0) write_prop(a, i, c, cd, oc, false);
   }
+}
+
+// The four lane-group buckets of one sub-round in one launch: block ranges
+// [bs[j], bs[j+1]) serve bucket j.
+struct SmallLaunch {
+  int64_t beg[4], cnt[4];
+  int32_t bs[5];
+};
+__global__ void __launch_bounds__(256) k_propose_small(LPArgs a, SmallLaunch L) {
+  const int32_t b = blockIdx.x;
+  if (b < L.bs[1]) propose_small<4>(a, L.beg[0], L.cnt[0], b - L.bs[0], L.bs[1] - L.bs[0]);
+  else if (b < L.bs[2]) propose_small<8>(a, L.beg[1], L.cnt[1], b - L.bs[1], L.bs[2] - L.bs[1]);
+  else if (b < L.bs[3]) propose_small<16>(a, L.beg[2], L.cnt[2], b - L.bs[2], L.bs[3] - L.bs[2]);
+  else propose_small<32>(a, L.beg[3], L.cnt[3], b - L.bs[3], L.bs[4] - L.bs[3]);
 }
 
 // Open-addressing accumulation (linear probing, bounded).
@@ -292,53 +349,23 @@ __device__ __forceinline__ void accumulate_arcs(const LPArgs& a, int64_t rs, int
   }
 }
 
-// Degrees in (32, 512], and small-degree nodes of overloaded blocks: one warp
-// per node, a 1024-slot table per warp in shared memory.
-__global__ void __launch_bounds__(256) k_propose_warp(LPArgs a, int64_t lbeg, int64_t cnt) {
-  extern __shared__ unsigned long long smem_u64[];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  unsigned long long* vals = smem_u64 + wib * WARP_HASH_SLOTS;
-  int32_t* keys = reinterpret_cast<int32_t*>(smem_u64 + 8 * WARP_HASH_SLOTS) + wib * WARP_HASH_SLOTS;
-  for (int j = lane; j < WARP_HASH_SLOTS; j += 32) { keys[j] = -1; vals[j] = 0; }
-  __syncwarp();
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t li = warp; li < cnt; li += nwarps) {
-    const int64_t i = lbeg + li;
-    const NodeCtx c = load_node(a, a.list[i]);
-    const int64_t deg = c.re - c.rs;
-    const int logcap = ceil_log2(max64(2 * deg, 32));
-    const int cap = 1 << logcap;
-    accumulate_arcs(a, c.rs, c.re, 0, 32, keys, vals, logcap);
-    __syncwarp();
-    const bool ov = a.mode != MODE_CLUSTER && a.W[c.own] > c.bound;
-    long long oc = 0;
-    Cand cd{-1, 0, 0};
-    for (int j = lane; j < cap; j += 32) {
-      const int32_t K = keys[j];
-      if (K == -1) continue;
-      const int64_t conn = (int64_t)vals[j];
-      if (K == c.own) oc = conn;
-      else if (!ov && a.W[K] + c.cv <= c.bound) {
-        Cand x = make_cand(c, K, conn);
-        if (cd.conn < 0 || cand_better(x, cd)) cd = x;
-      }
+// Direct accumulation for local search: labels are block ids, so the
+// connection of block b (local id) sits at vals[b]; no probing.
+__device__ __forceinline__ void accumulate_direct(const LPArgs& a, int64_t rs, int64_t re,
+                                                  int first_lane, int lanes, int64_t loff,
+                                                  unsigned long long* vals) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t e0 = rs; e0 < re; e0 += lanes) {
+    const int64_t e = e0 + first_lane + lane;
+    const bool valid = e < re;
+    int32_t b = -1, w = 0;
+    if (valid) {
+      w = a.ew[e];
+      b = (int32_t)(a.label[a.col[e]] - loff);
     }
-    if (ov) {
-      const int32_t nl = a.nlab[c.slot];
-      for (int32_t b = lane; b < nl; b += 32) {
-        const int32_t C = (int32_t)(c.loff + b);
-        if (C == c.own || a.W[C] + c.cv > c.bound) continue;
-        Cand x = make_cand(c, C, table_get(keys, vals, logcap, C));
-        if (cd.conn < 0 || cand_better(x, cd)) cd = x;
-      }
-    }
-    __syncwarp();
-    for (int j = lane; j < cap; j += 32) { keys[j] = -1; vals[j] = 0; }
-    oc = warp_max_ll(oc);
-    cd = warp_best(cd);
-    __syncwarp();
-    if (lane == 0) write_prop(a, i, c, cd, oc, ov);
+    const unsigned mm = __match_any_sync(0xffffffffu, b);
+    const int64_t sum = match_sum(mm, w);
+    if (valid && lane == __ffs(mm) - 1) atomicAdd(&vals[b], (unsigned long long)sum);
   }
 }
 
@@ -357,60 +384,82 @@ __device__ void block_reduce(long long& oc, Cand& cd, long long* sh_oc, Cand* sh
   }
 }
 
-// Degrees above 512: one CTA per node; the table lives in shared memory
-// (degree <= 4096) or in a per-CTA region of global scratch (hubs).
-template <bool GLOBAL>
-__global__ void __launch_bounds__(512) k_propose_cta(LPArgs a, int64_t lbeg, int64_t cnt,
-                                                     int32_t* gkeys, unsigned long long* gvals,
-                                                     int64_t gcap) {
-  constexpr int NT = 512;
+// Degrees above 32 (and nodes of overloaded blocks): one CTA of NT threads
+// per node with a SLOTS-slot table in shared memory, or (GLOBAL, hubs) a
+// per-CTA region of global scratch.  Clustering keys the table by label
+// (open addressing); local search with k no larger than the table indexes
+// it by block id directly.
+template <int NT, int SLOTS, bool GLOBAL>
+__global__ void __launch_bounds__(NT) k_propose_cta(LPArgs a, int64_t lbeg, int64_t cnt,
+                                                    int32_t* gkeys, unsigned long long* gvals,
+                                                    int64_t gcap) {
   extern __shared__ unsigned long long smem_u64[];
   __shared__ long long sh_oc[NT / 32];
   __shared__ Cand sh_cd[NT / 32];
-  const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
+  const int tid = threadIdx.x, wib = tid >> 5;
   unsigned long long* vals;
   int32_t* keys;
+  int64_t tcap;
   if (GLOBAL) {
     vals = gvals + (int64_t)blockIdx.x * gcap;
     keys = gkeys + (int64_t)blockIdx.x * gcap;
+    tcap = gcap;
   } else {
     vals = smem_u64;
-    keys = reinterpret_cast<int32_t*>(smem_u64 + CTA_HASH_SLOTS);
-    for (int j = tid; j < CTA_HASH_SLOTS; j += NT) { keys[j] = -1; vals[j] = 0; }
+    keys = reinterpret_cast<int32_t*>(smem_u64 + SLOTS);
+    tcap = SLOTS;
+    for (int j = tid; j < SLOTS; j += NT) { keys[j] = -1; vals[j] = 0; }
     __syncthreads();
   }
   for (int64_t li = blockIdx.x; li < cnt; li += gridDim.x) {
     const int64_t i = lbeg + li;
     const NodeCtx c = load_node(a, a.list[i]);
-    const int64_t deg = c.re - c.rs;
-    const int logcap = ceil_log2(max64(2 * deg, 32));
-    const int64_t cap = (int64_t)1 << logcap;
-    accumulate_arcs(a, c.rs, c.re, wib * 32, NT, keys, vals, logcap);
-    __syncthreads();
     const bool ov = a.mode != MODE_CLUSTER && a.W[c.own] > c.bound;
     long long oc = 0;
     Cand cd{-1, 0, 0};
-    for (int64_t j = tid; j < cap; j += NT) {
-      const int32_t K = keys[j];
-      if (K == -1) continue;
-      const int64_t conn = (int64_t)vals[j];
-      if (K == c.own) oc = conn;
-      else if (!ov && a.W[K] + c.cv <= c.bound) {
-        Cand x = make_cand(c, K, conn);
-        if (cd.conn < 0 || cand_better(x, cd)) cd = x;
-      }
-    }
-    if (ov) {
-      const int32_t nl = a.nlab[c.slot];
+    const int32_t nl = a.mode != MODE_CLUSTER ? a.nlab[c.slot] : 0;
+    if (a.mode != MODE_CLUSTER && nl <= tcap) {
+      accumulate_direct(a, c.rs, c.re, wib * 32, NT, c.loff, vals);
+      __syncthreads();
+      const int32_t own_l = (int32_t)(c.own - c.loff);
       for (int32_t b = tid; b < nl; b += NT) {
+        const int64_t conn = (int64_t)vals[b];
+        if (b == own_l) { oc = conn; continue; }
+        if (conn == 0 && !ov) continue;
         const int32_t C = (int32_t)(c.loff + b);
-        if (C == c.own || a.W[C] + c.cv > c.bound) continue;
-        Cand x = make_cand(c, C, table_get(keys, vals, logcap, C));
+        if (a.W[C] + c.cv > c.bound) continue;
+        Cand x = make_cand(c, C, conn);
         if (cd.conn < 0 || cand_better(x, cd)) cd = x;
       }
+      __syncthreads();
+      for (int32_t b = tid; b < nl; b += NT) vals[b] = 0;
+    } else {
+      const int64_t deg = c.re - c.rs;
+      const int logcap = ceil_log2(max64(2 * deg, 32));
+      const int64_t cap = (int64_t)1 << logcap;
+      accumulate_arcs(a, c.rs, c.re, wib * 32, NT, keys, vals, logcap);
+      __syncthreads();
+      for (int64_t j = tid; j < cap; j += NT) {
+        const int32_t K = keys[j];
+        if (K == -1) continue;
+        const int64_t conn = (int64_t)vals[j];
+        if (K == c.own) oc = conn;
+        else if (!ov && a.W[K] + c.cv <= c.bound) {
+          Cand x = make_cand(c, K, conn);
+          if (cd.conn < 0 || cand_better(x, cd)) cd = x;
+        }
+      }
+      if (ov) {
+        for (int32_t b = tid; b < nl; b += NT) {
+          const int32_t C = (int32_t)(c.loff + b);
+          if (C == c.own || a.W[C] + c.cv > c.bound) continue;
+          Cand x = make_cand(c, C, table_get(keys, vals, logcap, C));
+          if (cd.conn < 0 || cand_better(x, cd)) cd = x;
+        }
+      }
+      __syncthreads();
+      for (int64_t j = tid; j < cap; j += NT) { keys[j] = -1; vals[j] = 0; }
     }
-    __syncthreads();
-    for (int64_t j = tid; j < cap; j += NT) { keys[j] = -1; vals[j] = 0; }
     block_reduce<NT>(oc, cd, sh_oc, sh_cd);
     if (tid == 0) write_prop(a, i, c, cd, oc, ov);
     __syncthreads();
@@ -491,7 +540,7 @@ __global__ void k_ovf_scatter(LPArgs a, int64_t lbeg, int64_t cnt) {
 }
 
 constexpr int SEL_NT = 256;
-constexpr int SEL_SMALL = 1024;
+constexpr int SEL_SMALL = 64;     // all-pairs ranking up to this many entries
 
 __device__ __forceinline__ bool key_less(uint64_t k1, int32_t v1, uint64_t k2, int32_t v2) {
   return k1 < k2 || (k1 == k2 && v1 < v2);
@@ -511,18 +560,49 @@ __device__ __forceinline__ bool prefix_match(uint64_t k, int32_t v, uint64_t PK,
 
 // Admission inside one overflowing group: entries ordered by (key, node);
 // target side admits while the inclusive prefix weight <= thr, source side
-// while the exclusive prefix weight <= thr.  Small groups compare all
-// pairs in shared memory; large ones locate the boundary entry by an MSD
-// radix select over the 96-bit (key, node) order with weight histograms.
+// while the exclusive prefix weight <= thr.  Groups of <= 64 entries rank
+// all pairs in shared memory.  Larger ones locate the boundary entry (the
+// first whose inclusive prefix exceeds thr) by an MSD radix select over the
+// 96-bit (key, node) order: the bytes shared by the smallest and largest
+// entry are skipped, each pass histograms the weights of the entries still
+// matching the chosen prefix, and once <= 64 candidates remain they are
+// ranked in shared memory.
+__device__ __forceinline__ void select_rank_small(const LPArgs& a, int n, int64_t thr,
+                                                  int64_t acc, uint64_t* sk, int32_t* sv,
+                                                  int32_t* sw, int32_t* si, bool write_adm,
+                                                  int32_t source, uint64_t* bk, int32_t* bv,
+                                                  int* bfound) {
+  // excl/incl prefix of every staged entry; write admissions directly, or
+  // report the boundary entry (smallest with acc + incl > thr).
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    int64_t excl = acc;
+    const uint64_t kj = sk[j];
+    const int32_t vj = sv[j];
+    for (int l = 0; l < n; ++l)
+      if (key_less(sk[l], sv[l], kj, vj)) excl += sw[l];
+    if (write_adm) {
+      const bool ok = source ? (excl <= thr) : (excl + sw[j] <= thr);
+      a.adm[si[j]] = ok ? 1 : 0;
+    } else if (excl + sw[j] > thr && excl <= thr) {
+      *bk = kj;      // the unique entry whose inclusive prefix first exceeds thr
+      *bv = vj;
+      *bfound = 1;
+    }
+  }
+}
+
 __global__ void __launch_bounds__(SEL_NT) k_ovf_select(LPArgs a, int32_t source) {
   __shared__ uint64_t sk[SEL_SMALL];
   __shared__ int32_t sv[SEL_SMALL];
   __shared__ int32_t sw[SEL_SMALL];
+  __shared__ int32_t si[SEL_SMALL];
   __shared__ unsigned long long hist[256];
-  __shared__ uint64_t PK;
+  __shared__ unsigned int hcnt[256];
+  __shared__ uint64_t PK, kmin_sh, kmax_sh, BK;
   __shared__ uint32_t PV;
+  __shared__ int32_t vmin_sh, vmax_sh, BV;
   __shared__ long long acc_sh;
-  __shared__ int found_sh;
+  __shared__ int found_sh, ncand_sh, bfound_sh, done_sh;
   const int tid = threadIdx.x;
   const int64_t nseg = a.ctr[1];
   for (int64_t sg = blockIdx.x; sg < nseg; sg += gridDim.x) {
@@ -534,31 +614,64 @@ __global__ void __launch_bounds__(SEL_NT) k_ovf_select(LPArgs a, int32_t source)
         sk[j] = a.ent_key[base + j];
         sv[j] = a.ent_v[base + j];
         sw[j] = a.ent_w[base + j];
+        si[j] = a.ent_i[base + j];
       }
       __syncthreads();
-      for (int j = tid; j < n; j += SEL_NT) {
-        int64_t excl = 0;
-        const uint64_t kj = sk[j];
-        const int32_t vj = sv[j];
-        for (int l = 0; l < n; ++l)
-          if (key_less(sk[l], sv[l], kj, vj)) excl += sw[l];
-        const bool ok = source ? (excl <= thr) : (excl + sw[j] <= thr);
-        a.adm[a.ent_i[base + j]] = ok ? 1 : 0;
-      }
+      select_rank_small(a, n, thr, 0, sk, sv, sw, si, true, source, nullptr, nullptr, nullptr);
       __syncthreads();
     } else {
-      if (tid == 0) { PK = 0; PV = 0; acc_sh = 0; found_sh = 1; }
+      // smallest and largest (key, node): their shared leading bytes are skipped
+      if (tid == 0) { kmin_sh = ~0ull; kmax_sh = 0; vmin_sh = INT32_MAX; vmax_sh = -1; }
       __syncthreads();
-      for (int p = 0; p < 12; ++p) {
-        for (int j = tid; j < 256; j += SEL_NT) hist[j] = 0;
+      uint64_t lmin = ~0ull, lmax = 0;
+      for (int64_t j = tid; j < n; j += SEL_NT) {
+        const uint64_t k = a.ent_key[base + j];
+        lmin = k < lmin ? k : lmin;
+        lmax = k > lmax ? k : lmax;
+      }
+      atomicMin(reinterpret_cast<unsigned long long*>(&kmin_sh), lmin);
+      atomicMax(reinterpret_cast<unsigned long long*>(&kmax_sh), lmax);
+      __syncthreads();
+      const uint64_t kmin = kmin_sh, kmax = kmax_sh;
+      int p0 = 0;
+      while (p0 < 8 && digit_of(kmin, 0, p0) == digit_of(kmax, 0, p0)) ++p0;
+      if (p0 == 8) {
+        int32_t l1 = INT32_MAX, l2 = -1;
+        for (int64_t j = tid; j < n; j += SEL_NT) {
+          const int32_t v = a.ent_v[base + j];
+          l1 = v < l1 ? v : l1;
+          l2 = v > l2 ? v : l2;
+        }
+        atomicMin(&vmin_sh, l1);
+        atomicMax(&vmax_sh, l2);
+        __syncthreads();
+        while (p0 < 12 && digit_of(0, vmin_sh, p0) == digit_of(0, vmax_sh, p0)) ++p0;
+      }
+      if (tid == 0) {
+        PK = p0 >= 8 ? kmin : (p0 == 0 ? 0ull : (kmin >> (64 - 8 * p0)) << (64 - 8 * p0));
+        const int pv = p0 > 8 ? p0 - 8 : 0;
+        PV = pv == 0 ? 0u : (((uint32_t)vmin_sh >> (32 - 8 * pv)) << (32 - 8 * pv));
+        acc_sh = 0;
+        found_sh = 1;
+        done_sh = 0;
+        ncand_sh = 0;
+        bfound_sh = 0;
+      }
+      __syncthreads();
+      int p = p0;
+      for (; p < 12; ++p) {
+        for (int j = tid; j < 256; j += SEL_NT) { hist[j] = 0; hcnt[j] = 0; }
         __syncthreads();
         const uint64_t pk = PK;
         const uint32_t pv = PV;
         for (int64_t j = tid; j < n; j += SEL_NT) {
           const uint64_t k = a.ent_key[base + j];
           const int32_t v = a.ent_v[base + j];
-          if (prefix_match(k, v, pk, pv, p))
-            atomicAdd(&hist[digit_of(k, v, p)], (unsigned long long)a.ent_w[base + j]);
+          if (prefix_match(k, v, pk, pv, p)) {
+            const uint32_t d = digit_of(k, v, p);
+            atomicAdd(&hist[d], (unsigned long long)a.ent_w[base + j]);
+            atomicAdd(&hcnt[d], 1u);
+          }
         }
         __syncthreads();
         if (tid == 0) {
@@ -574,10 +687,32 @@ __global__ void __launch_bounds__(SEL_NT) k_ovf_select(LPArgs a, int32_t source)
             acc_sh = acc;
             if (p < 8) PK |= (uint64_t)x << (56 - 8 * p);
             else PV |= (uint32_t)x << (24 - 8 * (p - 8));
+            if (hcnt[x] <= SEL_SMALL) done_sh = 1;
           }
         }
         __syncthreads();
-        if (!found_sh) break;
+        if (!found_sh || done_sh) break;
+      }
+      if (found_sh && done_sh && p < 11) {
+        // stage the few candidates sharing the chosen prefix; rank them
+        const uint64_t pk = PK;
+        const uint32_t pv = PV;
+        for (int64_t j = tid; j < n; j += SEL_NT) {
+          const uint64_t k = a.ent_key[base + j];
+          const int32_t v = a.ent_v[base + j];
+          if (prefix_match(k, v, pk, pv, p + 1)) {
+            const int q = atomicAdd(&ncand_sh, 1);
+            sk[q] = k;
+            sv[q] = v;
+            sw[q] = a.ent_w[base + j];
+          }
+        }
+        __syncthreads();
+        select_rank_small(a, ncand_sh, thr, acc_sh, sk, sv, sw, si, false, source, &BK, &BV,
+                          &bfound_sh);
+        __syncthreads();
+        if (tid == 0 && bfound_sh) { PK = BK; PV = (uint32_t)BV; }
+        __syncthreads();
       }
       const int found = found_sh;
       const uint64_t pk = PK;
@@ -602,36 +737,67 @@ __global__ void __launch_bounds__(SEL_NT) k_ovf_select(LPArgs a, int32_t source)
 }
 
 // ------------------------------------------------------------- apply
+// Admitted moves update labels and weights; moved nodes activate their
+// neighbours (small rows by their own lane, larger rows by the whole warp).
 __global__ void __launch_bounds__(256) k_apply(LPArgs a, int64_t lbeg, int64_t cnt) {
+  __shared__ int sh_slot;
+  __shared__ unsigned long long sh_moved;
   const int lane = threadIdx.x & 31;
   const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  if (threadIdx.x == 0) {
+    const int64_t li0 = (int64_t)blockIdx.x * blockDim.x;
+    sh_slot = li0 < cnt ? a.gid[a.list[lbeg + li0]] : -1;
+    sh_moved = 0;
+  }
+  __syncthreads();
   for (int64_t b0 = w0 * 32; b0 < cnt; b0 += nw * 32) {
     const int64_t li = b0 + lane;
-    int32_t slot = -1;
+    int32_t slot = -1, v = -1;
+    int64_t rs = 0, re = 0;
     if (li < cnt) {
       const int64_t i = lbeg + li;
       const int32_t t = a.prop_t[i];
       if (t >= 0) {
         a.in_w[t] = 0;
         if (a.adm[i]) {
-          const int32_t v = a.list[i];
+          v = a.list[i];
           const int32_t own = a.label[v];
           const int64_t cv = a.nw[v];
           a.label[v] = t;
           atomicAdd(ull(&a.W[t]), (unsigned long long)cv);
           atomicAdd(ull(&a.W[own]), (unsigned long long)(-cv));
           slot = a.gid[v];
-          if (a.act_next)
-            for (int64_t e = a.row_ptr[v]; e < a.row_ptr[v + 1]; ++e) a.act_next[a.col[e]] = 1;
+          if (a.act_next) {
+            rs = a.row_ptr[v];
+            re = a.row_ptr[v + 1];
+            if (re - rs <= 8) {
+              for (int64_t e = rs; e < re; ++e) a.act_next[a.col[e]] = 1;
+              re = rs;
+            }
+          }
         }
       }
     }
+    unsigned big = __ballot_sync(0xffffffffu, re > rs);
+    while (big) {
+      const int src = __ffs(big) - 1;
+      big &= big - 1;
+      const int64_t s0 = __shfl_sync(0xffffffffu, (long long)rs, src);
+      const int64_t s1 = __shfl_sync(0xffffffffu, (long long)re, src);
+      for (int64_t e = s0 + lane; e < s1; e += 32) a.act_next[a.col[e]] = 1;
+    }
     const unsigned mm = __match_any_sync(0xffffffffu, slot);
-    if (slot >= 0 && lane == __ffs(mm) - 1)
-      atomicAdd(ull(&a.moved[slot]), (unsigned long long)__popc(mm));
+    if (slot >= 0 && lane == __ffs(mm) - 1) {
+      if (slot == sh_slot) atomicAdd(&sh_moved, (unsigned long long)__popc(mm));
+      else atomicAdd(ull(&a.moved[slot]), (unsigned long long)__popc(mm));
+    }
   }
+  __syncthreads();
+  if (threadIdx.x == 0 && sh_moved) atomicAdd(ull(&a.moved[sh_slot]), sh_moved);
 }
+
+}  // namespace
 
 // Reused CUDA events for the profiling brackets.
 std::mutex g_event_mu;
@@ -652,11 +818,50 @@ void event_to_pool(cudaEvent_t e) {
   g_events.push_back(e);
 }
 
-}  // namespace
-
 ProfileState& profile() {
   static ProfileState p;
   return p;
+}
+
+void timeline_mark(const char* name, cudaStream_t s) {
+  cudaEvent_t e = event_from_pool();
+  cudaEventRecord(e, s);
+  ProfileState& P = profile();
+  std::lock_guard<std::mutex> lk(P.mu);
+  P.marks.emplace_back(name, e);
+}
+
+// Aggregates the timeline into "name count total_ms" lines (marks named
+// "<call>" open a new segment and are not charged).
+std::string timeline_dump() {
+  ProfileState& P = profile();
+  std::lock_guard<std::mutex> lk(P.mu);
+  std::vector<std::string> names;
+  std::vector<double> tot;
+  std::vector<int64_t> cnt;
+  cudaEvent_t prev = nullptr;
+  for (auto& m : P.marks) {
+    cudaEventSynchronize(m.second);
+    if (prev && std::string(m.first) != "<call>") {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, prev, m.second);
+      size_t j = 0;
+      while (j < names.size() && names[j] != m.first) ++j;
+      if (j == names.size()) { names.push_back(m.first); tot.push_back(0); cnt.push_back(0); }
+      tot[j] += ms;
+      cnt[j] += 1;
+    }
+    prev = m.second;
+  }
+  std::string out;
+  char buf[256];
+  for (size_t j = 0; j < names.size(); ++j) {
+    snprintf(buf, sizeof(buf), "%s %lld %.6f\n", names[j].c_str(), (long long)cnt[j], tot[j]);
+    out += buf;
+  }
+  for (auto& m : P.marks) event_to_pool(m.second);
+  P.marks.clear();
+  return out;
 }
 
 // ---------------------------------------------------------------------------
@@ -682,6 +887,8 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, int64_
   DevBuf<int64_t> ctr(2, s);
   DevBuf<int32_t> bcnt(nkeys, s), bfill(nkeys, s);
   DevBuf<int64_t> boff(nkeys + 1, s), arcs(1, s), karcs(nkeys, s);
+  DevBuf<int32_t> flags(1, s);
+  DevBuf<int16_t> nkey(N, s);
   bfill.zero(); arcs.zero();
 
   const bool track_active = run.use_active || active_init != nullptr || active_next_out != nullptr;
@@ -713,22 +920,26 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, int64_
   a.seg_thr = seg_thr.p; a.ent_key = ent_key.p; a.ent_v = ent_v.p; a.ent_w = ent_w.p;
   a.ent_i = ent_i.p; a.bcnt = bcnt.p; a.bfill = bfill.p; a.boff = boff.p; a.arcs = arcs.p;
   a.karcs = karcs.p;
+  a.flags = flags.p;
+  a.nkey = nkey.p;
   a.err = d_err;
 
   std::vector<int64_t> hoff(nkeys + 1), hkarcs(nkeys);
   const bool prof = profile().enabled.load();
-  struct Timed { int bucket; cudaEvent_t a, b; };
+  struct Timed { int family; cudaEvent_t a, b; };
   std::vector<Timed> timed;
-  int64_t pn[NB] = {}, pa[NB] = {};
+  int64_t pn[4] = {}, pa[4] = {};
+  int32_t hflags = 0;
+  int64_t arcs_total = 0;
   const unsigned small_grid = (unsigned)(sms * 8);
-  const size_t warp_smem = 8 * WARP_HASH_SLOTS * (sizeof(unsigned long long) + sizeof(int32_t));
-  const size_t cta_smem = CTA_HASH_SLOTS * (sizeof(unsigned long long) + sizeof(int32_t));
+  constexpr size_t SLOT_BYTES = sizeof(unsigned long long) + sizeof(int32_t);
+  const size_t smem4 = WARP_SMALL_SLOTS * SLOT_BYTES;   // 64 threads, 256 slots
+  const size_t smem5 = WARP_HASH_SLOTS * SLOT_BYTES;    // 128 threads, 1024 slots
+  const size_t smem6 = CTA_HASH_SLOTS * SLOT_BYTES;     // 512 threads, 8192 slots
   static bool attrs_set = false;
   if (!attrs_set) {
-    SCLAP_CUDA(cudaFuncSetAttribute(k_propose_warp, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)warp_smem));
-    SCLAP_CUDA(cudaFuncSetAttribute(k_propose_cta<false>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cta_smem));
+    SCLAP_CUDA(cudaFuncSetAttribute(k_propose_cta<512, CTA_HASH_SLOTS, false>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem6));
     attrs_set = true;
   }
 
@@ -737,35 +948,37 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, int64_
     a.act_next = track_active ? act_b.p : nullptr;
     k_round_begin<<<grid_for(sp.nslots, 128, 1024), 128, 0, s>>>(a, sp.nslots, run.phase, r,
                                                                   sp.seed, sp.level,
-                                                                  run.raw_key ? 1 : 0); SCLAP_NOTE_LAUNCH();
+                                                                  run.raw_key ? 1 : 0); SCLAP_NOTE_LAUNCH("k_round_begin");
     bcnt.zero();
     karcs.zero();
-    const unsigned bgrid = grid_for(N, 256, (int64_t)sms * 16);
-    k_bucket<0><<<bgrid, 256, 0, s>>>(a, N); SCLAP_NOTE_LAUNCH();
-    k_bucket_offsets<<<1, 32, 0, s>>>(a, nkeys); SCLAP_NOTE_LAUNCH();
-    k_bucket<1><<<bgrid, 256, 0, s>>>(a, N); SCLAP_NOTE_LAUNCH();
+    flags.zero();
+    const unsigned bgrid = (unsigned)((N + BK_TILE - 1) / BK_TILE);
+    k_bucket_count<<<bgrid, BK_NT, 0, s>>>(a, N); SCLAP_NOTE_LAUNCH("k_bucket_count");
+    k_bucket_offsets<<<1, 32, 0, s>>>(a, nkeys); SCLAP_NOTE_LAUNCH("k_bucket_offsets");
+    k_bucket_scatter<<<bgrid, BK_NT, 0, s>>>(a, N); SCLAP_NOTE_LAUNCH("k_bucket_scatter");
     SCLAP_LAUNCH_CHECK();
     SCLAP_CUDA(cudaMemcpyAsync(hoff.data(), boff.p, (nkeys + 1) * sizeof(int64_t),
                                cudaMemcpyDeviceToHost, s));
-    if (prof)
-      SCLAP_CUDA(cudaMemcpyAsync(hkarcs.data(), karcs.p, nkeys * sizeof(int64_t),
-                                 cudaMemcpyDeviceToHost, s));
-    SCLAP_CUDA(cudaStreamSynchronize(s));
+    SCLAP_CUDA(cudaMemcpyAsync(hkarcs.data(), karcs.p, nkeys * sizeof(int64_t),
+                               cudaMemcpyDeviceToHost, s));
+    SCLAP_CUDA(cudaMemcpyAsync(&hflags, flags.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    stream_sync(s);
+    for (int j = 0; j < nkeys; ++j) arcs_total += hkarcs[j];
     if (hoff[nkeys] == 0) {
       k_round_end<<<grid_for(sp.nslots, 128, 1024), 128, 0, s>>>(a, sp.nslots,
-                                                                  run.stop_rule ? 1 : 0); SCLAP_NOTE_LAUNCH();
+                                                                  run.stop_rule ? 1 : 0); SCLAP_NOTE_LAUNCH("k_round_end");
       break;
     }
     // global hash scratch for the hub bucket, sized on first need
     int64_t nhub = 0;
-    for (int sub = 0; sub < S; ++sub) nhub += hoff[sub * NB + 6 + 1] - hoff[sub * NB + 6];
+    for (int sub = 0; sub < S; ++sub) nhub += hoff[sub * NB + 7 + 1] - hoff[sub * NB + 7];
     if (nhub > 0 && gcap == 0) {
       // largest degree of the level, read once
       DevBuf<int64_t> dmax(1, s);
       dmax.zero();
       level_max_degree(lv.row_ptr, N, dmax.p, s);
       SCLAP_CUDA(cudaMemcpyAsync(&maxdeg, dmax.p, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-      SCLAP_CUDA(cudaStreamSynchronize(s));
+      stream_sync(s);
       gcap = (int64_t)1 << ceil_log2(std::max<int64_t>(2 * maxdeg, 32));
       gblocks = std::max(1, std::min(sms * 2, (int)std::min<int64_t>(nhub * 4, 1 << 20)));
       gkeys.alloc((size_t)(gblocks * gcap), s);
@@ -777,27 +990,58 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, int64_
       const int64_t lbeg = hoff[sub * NB], lend = hoff[(sub + 1) * NB];
       const int64_t cnt = lend - lbeg;
       if (cnt == 0) continue;
-      for (int b = 0; b < NB; ++b) {
+      // family 0: the four lane-group buckets in one launch
+      {
+        SmallLaunch L{};
+        int32_t nb = 0;
+        const int per_block[4] = {64, 32, 16, 8};
+        int64_t nodes = 0, arcs_f = 0;
+        for (int b = 0; b < 4; ++b) {
+          L.beg[b] = hoff[sub * NB + b];
+          L.cnt[b] = hoff[sub * NB + b + 1] - L.beg[b];
+          L.bs[b] = nb;
+          if (L.cnt[b] > 0) nb += (int32_t)grid_for(L.cnt[b], per_block[b], small_grid);
+          nodes += L.cnt[b];
+          if (prof) arcs_f += hkarcs[sub * NB + b];
+        }
+        L.bs[4] = nb;
+        if (nb > 0) {
+          Timed tm{0, nullptr, nullptr};
+          if (prof) {
+            tm.a = event_from_pool();
+            tm.b = event_from_pool();
+            SCLAP_CUDA(cudaEventRecord(tm.a, s));
+            pn[0] += nodes;
+            pa[0] += arcs_f;
+          }
+          k_propose_small<<<nb, 256, 0, s>>>(a, L); SCLAP_NOTE_LAUNCH("k_propose_small");
+          if (prof) {
+            SCLAP_CUDA(cudaEventRecord(tm.b, s));
+            timed.push_back(tm);
+          }
+        }
+      }
+      for (int b = 4; b < NB; ++b) {
         const int64_t bb = hoff[sub * NB + b], bc = hoff[sub * NB + b + 1] - bb;
         if (bc == 0) continue;
-        Timed tm{b, nullptr, nullptr};
+        const int fam = b <= 5 ? 1 : b - 4;
+        Timed tm{fam, nullptr, nullptr};
         if (prof) {
           tm.a = event_from_pool();
           tm.b = event_from_pool();
           SCLAP_CUDA(cudaEventRecord(tm.a, s));
-          pn[b] += bc;
-          pa[b] += hkarcs[sub * NB + b];
+          pn[fam] += bc;
+          pa[fam] += hkarcs[sub * NB + b];
         }
         switch (b) {
-          case 0: k_propose_small<4><<<grid_for(bc, 64, small_grid), 256, 0, s>>>(a, bb, bc); SCLAP_NOTE_LAUNCH(); break;
-          case 1: k_propose_small<8><<<grid_for(bc, 32, small_grid), 256, 0, s>>>(a, bb, bc); SCLAP_NOTE_LAUNCH(); break;
-          case 2: k_propose_small<16><<<grid_for(bc, 16, small_grid), 256, 0, s>>>(a, bb, bc); SCLAP_NOTE_LAUNCH(); break;
-          case 3: k_propose_small<32><<<grid_for(bc, 8, small_grid), 256, 0, s>>>(a, bb, bc); SCLAP_NOTE_LAUNCH(); break;
-          case 4: k_propose_warp<<<grid_for(bc, 8, (int64_t)sms * 2), 256, warp_smem, s>>>(a, bb, bc); SCLAP_NOTE_LAUNCH(); break;
-          case 5: k_propose_cta<false><<<grid_for(bc, 1, (int64_t)sms * 2), 512, cta_smem, s>>>(
-                      a, bb, bc, nullptr, nullptr, 0); SCLAP_NOTE_LAUNCH(); break;
-          default: k_propose_cta<true><<<(unsigned)std::min<int64_t>(bc, gblocks), 512, 0, s>>>(
-                      a, bb, bc, gkeys.p, gvals.p, gcap); SCLAP_NOTE_LAUNCH(); break;
+          case 4: k_propose_cta<64, WARP_SMALL_SLOTS, false><<<grid_for(bc, 1, (int64_t)sms * 32), 64, smem4, s>>>(
+                      a, bb, bc, nullptr, nullptr, 0); SCLAP_NOTE_LAUNCH("k_propose_cta64"); break;
+          case 5: k_propose_cta<128, WARP_HASH_SLOTS, false><<<grid_for(bc, 1, (int64_t)sms * 16), 128, smem5, s>>>(
+                      a, bb, bc, nullptr, nullptr, 0); SCLAP_NOTE_LAUNCH("k_propose_cta128"); break;
+          case 6: k_propose_cta<512, CTA_HASH_SLOTS, false><<<grid_for(bc, 1, (int64_t)sms * 2), 512, smem6, s>>>(
+                      a, bb, bc, nullptr, nullptr, 0); SCLAP_NOTE_LAUNCH("k_propose_cta512"); break;
+          default: k_propose_cta<512, 1, true><<<(unsigned)std::min<int64_t>(bc, gblocks), 512, 0, s>>>(
+                      a, bb, bc, gkeys.p, gvals.p, gcap); SCLAP_NOTE_LAUNCH("k_propose_cta_global"); break;
         }
         if (prof) {
           SCLAP_CUDA(cudaEventRecord(tm.b, s));
@@ -805,23 +1049,23 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, int64_
         }
       }
       const unsigned lg = grid_for(cnt, 256, (int64_t)sms * 16);
-      k_resolve<<<lg, 256, 0, s>>>(a, lbeg, cnt); SCLAP_NOTE_LAUNCH();
+      k_resolve<<<lg, 256, 0, s>>>(a, lbeg, cnt); SCLAP_NOTE_LAUNCH("k_resolve");
       ctr.zero();
-      k_ovf_alloc<<<lg, 256, 0, s>>>(a, lbeg, cnt, 0); SCLAP_NOTE_LAUNCH();
-      k_ovf_scatter<<<lg, 256, 0, s>>>(a, lbeg, cnt); SCLAP_NOTE_LAUNCH();
-      k_ovf_select<<<(unsigned)(sms * 4), SEL_NT, 0, s>>>(a, 0); SCLAP_NOTE_LAUNCH();
-      if (run.mode != MODE_CLUSTER) {
-        k_forced<<<lg, 256, 0, s>>>(a, lbeg, cnt); SCLAP_NOTE_LAUNCH();
+      k_ovf_alloc<<<lg, 256, 0, s>>>(a, lbeg, cnt, 0); SCLAP_NOTE_LAUNCH("k_ovf_alloc");
+      k_ovf_scatter<<<lg, 256, 0, s>>>(a, lbeg, cnt); SCLAP_NOTE_LAUNCH("k_ovf_scatter");
+      k_ovf_select<<<(unsigned)(sms * 4), SEL_NT, 0, s>>>(a, 0); SCLAP_NOTE_LAUNCH("k_ovf_select");
+      if (run.mode != MODE_CLUSTER && hflags) {
+        k_forced<<<lg, 256, 0, s>>>(a, lbeg, cnt); SCLAP_NOTE_LAUNCH("k_forced");
         ctr.zero();
-        k_ovf_alloc<<<lg, 256, 0, s>>>(a, lbeg, cnt, 1); SCLAP_NOTE_LAUNCH();
-        k_ovf_scatter<<<lg, 256, 0, s>>>(a, lbeg, cnt); SCLAP_NOTE_LAUNCH();
-        k_ovf_select<<<(unsigned)(sms * 4), SEL_NT, 0, s>>>(a, 1); SCLAP_NOTE_LAUNCH();
+        k_ovf_alloc<<<lg, 256, 0, s>>>(a, lbeg, cnt, 1); SCLAP_NOTE_LAUNCH("k_ovf_alloc");
+        k_ovf_scatter<<<lg, 256, 0, s>>>(a, lbeg, cnt); SCLAP_NOTE_LAUNCH("k_ovf_scatter");
+        k_ovf_select<<<(unsigned)(sms * 4), SEL_NT, 0, s>>>(a, 1); SCLAP_NOTE_LAUNCH("k_ovf_select");
       }
-      k_apply<<<lg, 256, 0, s>>>(a, lbeg, cnt); SCLAP_NOTE_LAUNCH();
+      k_apply<<<lg, 256, 0, s>>>(a, lbeg, cnt); SCLAP_NOTE_LAUNCH("k_apply");
       SCLAP_LAUNCH_CHECK();
     }
     k_round_end<<<grid_for(sp.nslots, 128, 1024), 128, 0, s>>>(a, sp.nslots,
-                                                                run.stop_rule ? 1 : 0); SCLAP_NOTE_LAUNCH();
+                                                                run.stop_rule ? 1 : 0); SCLAP_NOTE_LAUNCH("k_round_end");
     SCLAP_LAUNCH_CHECK();
     if (track_active && r + 1 < run.rounds) {
       std::swap(act_a, act_b);
@@ -830,19 +1074,18 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, int64_
   }
   if (active_next_out && track_active)
     SCLAP_CUDA(cudaMemcpyAsync(active_next_out, act_b.p, N, cudaMemcpyDeviceToDevice, s));
-  int64_t h_arcs = 0;
-  SCLAP_CUDA(cudaMemcpyAsync(&h_arcs, arcs.p, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-  SCLAP_CUDA(cudaStreamSynchronize(s));
+  stream_sync(s);
+  const int64_t h_arcs = arcs_total;
   if (prof) {
     ProfileState& P = profile();
     std::lock_guard<std::mutex> lk(P.mu);
     for (const Timed& t : timed) {
       float ms = 0.f;
       SCLAP_CUDA(cudaEventElapsedTime(&ms, t.a, t.b));
-      P.ms[t.bucket] += ms;
-      P.nlaunch[t.bucket] += 1;
+      P.ms[t.family] += ms;
+      P.nlaunch[t.family] += 1;
     }
-    for (int b = 0; b < NB; ++b) { P.nodes[b] += pn[b]; P.arcs[b] += pa[b]; }
+    for (int b = 0; b < 4; ++b) { P.nodes[b] += pn[b]; P.arcs[b] += pa[b]; }
     for (const Timed& t : timed) { event_to_pool(t.a); event_to_pool(t.b); }
   }
   return h_arcs;

@@ -36,7 +36,17 @@ __device__ T block_excl_scan(T x, T* sh, T* total) {
   return res;
 }
 
-template <class Tin, class Tout>
+// Input transforms: plain value, or 1 for a non-negative int32 (an occupied
+// hash slot), else 0.
+struct Plain {
+  template <class T>
+  __device__ __forceinline__ T operator()(T x) const { return x; }
+};
+struct Occupied {
+  __device__ __forceinline__ int64_t operator()(int32_t x) const { return x >= 0 ? 1 : 0; }
+};
+
+template <class Tin, class Tout, class F = Plain>
 __global__ void __launch_bounds__(SB) k_reduce(const Tin* __restrict__ in, int64_t n,
                                                Tout* __restrict__ part) {
   __shared__ Tout sh[33];
@@ -45,7 +55,7 @@ __global__ void __launch_bounds__(SB) k_reduce(const Tin* __restrict__ in, int64
 #pragma unroll
   for (int j = 0; j < SI; ++j) {
     int64_t i = base + (int64_t)j * SB + threadIdx.x;
-    if (i < n) s += (Tout)in[i];
+    if (i < n) s += (Tout)F()(in[i]);
   }
   Tout tot;
   block_excl_scan<Tout>(s, sh, &tot);
@@ -67,7 +77,7 @@ __global__ void __launch_bounds__(SB) k_scan_part(Tout* part, int64_t nb, Tout* 
   if (threadIdx.x == 0) *total_out = carry;
 }
 
-template <class Tin, class Tout>
+template <class Tin, class Tout, class F = Plain>
 __global__ void __launch_bounds__(SB) k_scan_add(const Tin* __restrict__ in, int64_t n,
                                                  const Tout* __restrict__ part,
                                                  Tout* __restrict__ out) {
@@ -78,7 +88,7 @@ __global__ void __launch_bounds__(SB) k_scan_add(const Tin* __restrict__ in, int
 #pragma unroll
   for (int j = 0; j < SI; ++j) {
     int64_t i = base + j;
-    v[j] = i < n ? (Tout)in[i] : Tout(0);
+    v[j] = i < n ? (Tout)F()(in[i]) : Tout(0);
     s += v[j];
   }
   Tout tot;
@@ -91,7 +101,7 @@ __global__ void __launch_bounds__(SB) k_scan_add(const Tin* __restrict__ in, int
   }
 }
 
-template <class Tin, class Tout>
+template <class Tin, class Tout, class F = Plain>
 void scan_excl(const Tin* in, Tout* out, int64_t n, cudaStream_t s) {
   if (n <= 0) {
     SCLAP_CUDA(cudaMemsetAsync(out, 0, sizeof(Tout), s));
@@ -99,9 +109,9 @@ void scan_excl(const Tin* in, Tout* out, int64_t n, cudaStream_t s) {
   }
   const int64_t nb = (n + TILE - 1) / TILE;
   DevBuf<Tout> part((size_t)nb, s);
-  k_reduce<Tin, Tout><<<(unsigned)nb, SB, 0, s>>>(in, n, part.p); SCLAP_NOTE_LAUNCH();
-  k_scan_part<Tout><<<1, SB, 0, s>>>(part.p, nb, out + n); SCLAP_NOTE_LAUNCH();
-  k_scan_add<Tin, Tout><<<(unsigned)nb, SB, 0, s>>>(in, n, part.p, out); SCLAP_NOTE_LAUNCH();
+  k_reduce<Tin, Tout, F><<<(unsigned)nb, SB, 0, s>>>(in, n, part.p); SCLAP_NOTE_LAUNCH("k_scan_reduce");
+  k_scan_part<Tout><<<1, SB, 0, s>>>(part.p, nb, out + n); SCLAP_NOTE_LAUNCH("k_scan_part");
+  k_scan_add<Tin, Tout, F><<<(unsigned)nb, SB, 0, s>>>(in, n, part.p, out); SCLAP_NOTE_LAUNCH("k_scan_add");
   SCLAP_LAUNCH_CHECK();
 }
 
@@ -138,7 +148,7 @@ __global__ void k_max_degree(const int64_t* __restrict__ row_ptr, int64_t N,
 void level_max_degree(const int64_t* row_ptr, int64_t N, int64_t* out, cudaStream_t s) {
   if (N <= 0) return;
   k_max_degree<<<grid_for(N, 256, (int64_t)num_sms() * 8), 256, 0, s>>>(
-      row_ptr, N, reinterpret_cast<unsigned long long*>(out)); SCLAP_NOTE_LAUNCH();
+      row_ptr, N, reinterpret_cast<unsigned long long*>(out)); SCLAP_NOTE_LAUNCH("k_max_degree");
   SCLAP_LAUNCH_CHECK();
 }
 
@@ -151,10 +161,13 @@ void scan_excl_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t s) {
 void scan_excl_u8_to_i64(const uint8_t* in, int64_t* out, int64_t n, cudaStream_t s) {
   scan_excl<uint8_t, int64_t>(in, out, n, s);
 }
+void scan_excl_occupied(const int32_t* keys, int64_t* out, int64_t n, cudaStream_t s) {
+  scan_excl<int32_t, int64_t, Occupied>(keys, out, n, s);
+}
 
 void fill_gid(const int64_t* noff, int32_t nslots, int32_t* gid, int64_t N, cudaStream_t s) {
   if (N <= 0) return;
-  k_fill_gid<<<grid_for(N, 256, (int64_t)num_sms() * 32), 256, 0, s>>>(noff, nslots, gid, N); SCLAP_NOTE_LAUNCH();
+  k_fill_gid<<<grid_for(N, 256, (int64_t)num_sms() * 32), 256, 0, s>>>(noff, nslots, gid, N); SCLAP_NOTE_LAUNCH("k_fill_gid");
   SCLAP_LAUNCH_CHECK();
 }
 

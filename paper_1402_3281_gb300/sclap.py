@@ -26,6 +26,7 @@ SYMBOLS = (
     "sclap_partition_device", "sclap_partition_batch", "sclap_lp_round", "sclap_cluster",
     "sclap_contract", "sclap_initial_partition", "sclap_refine", "sclap_cut",
     "sclap_profile_enable", "sclap_profile_reset", "sclap_profile_read",
+    "sclap_profile_timeline", "sclap_profile_dump",
 )
 
 
@@ -59,9 +60,9 @@ class Stats(C.Structure):
 
 
 class Profile(C.Structure):
-    _fields_ = [("kernel_launches", C.c_int64), ("propose_launches", C.c_int64 * 7),
-                ("propose_ms", C.c_double * 7), ("propose_nodes", C.c_int64 * 7),
-                ("propose_arcs", C.c_int64 * 7)]
+    _fields_ = [("kernel_launches", C.c_int64), ("propose_launches", C.c_int64 * 4),
+                ("propose_ms", C.c_double * 4), ("propose_nodes", C.c_int64 * 4),
+                ("propose_arcs", C.c_int64 * 4)]
 
     def to_dict(self) -> dict:
         return dict(kernel_launches=self.kernel_launches,
@@ -106,6 +107,8 @@ def _lib():
             "sclap_profile_enable": (None, [C.c_int]),
             "sclap_profile_reset": (None, []),
             "sclap_profile_read": (None, [p]),
+            "sclap_profile_timeline": (None, [C.c_int]),
+            "sclap_profile_dump": (C.c_int64, [p, C.c_int64]),
         }
         for name, (res, args) in sig.items():
             f = getattr(h, name)
@@ -132,6 +135,21 @@ def sclap_profile_read() -> dict:
     p = Profile()
     _lib().sclap_profile_read(C.byref(p))
     return p.to_dict()
+
+
+def sclap_profile_timeline(on: bool = True) -> None:
+    _lib().sclap_profile_timeline(1 if on else 0)
+
+
+def sclap_profile_dump() -> dict:
+    """{kernel name: (launches, total ms)} since the last dump."""
+    buf = C.create_string_buffer(1 << 20)
+    _lib().sclap_profile_dump(buf, len(buf))
+    out = {}
+    for line in buf.value.decode().splitlines():
+        name, cnt, ms = line.rsplit(" ", 2)
+        out[name] = (int(cnt), float(ms))
+    return out
 
 
 def default_config(**overrides) -> Config:
