@@ -45,7 +45,7 @@ import graphgen as gg  # noqa: E402
 # admission key (8) written.
 ARC_BYTES = 12
 NODE_BYTES = 44
-FAMILIES = ["lane_groups", "warp_smem", "cta_smem", "cta_global"]
+FAMILIES = ["lane_groups", "cta64_128", "cta256_512", "cta_global"]
 
 
 def parse():
@@ -273,7 +273,7 @@ def main():
     parts = args.steps * len(graphs) * ws
     value = parts / (elapsed_ms / 1000.0)
     swept = sum(prof["propose_arcs"])
-    prop_ms = sum(prof["propose_ms"])
+    prop_ms = prof["sweep_ms"]
     prop_bytes = ARC_BYTES * swept + NODE_BYTES * sum(prof["propose_nodes"])
     peaks = {}
     pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -282,9 +282,11 @@ def main():
     peak = peaks.get("hbm_gbs", 6800.0)
     achieved = prop_bytes / (prop_ms / 1000.0) / 1e9 if prop_ms > 0 else 0.0
     tr = traffic_for(os.path.join(ROOT, "paper_1402_3281_gb300", "csrc", "lp.cu"))
-    nl = sum(prof["propose_launches"])
+    nl = prof["sweeps"]
     roofline = {
-        "kernel": "LP propose sweep (k_propose_*, all degree buckets)",
+        "kernel": "LP propose sweep of a sub-round (k_propose_small + k_propose_cta*, the "
+                  "degree-bucket launches of one colour class, run concurrently); one "
+                  "'launch' = one such phase, timed fork to join with CUDA events",
         "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
         "frac": achieved / peak, "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
         "traffic": (tr[0] * swept / nl if tr and tr[0] else None) if nl else None,

@@ -195,16 +195,19 @@ int sclap_cut(int64_t n, const int64_t* row_ptr, const int32_t* col, const int32
  * counters read by the benchmark: every kernel launch is counted; with
  * profiling enabled, each launch of the LP propose sweep is bracketed by CUDA
  * events on its stream and its nodes/arcs are tallied per kernel family
- * (0: lane groups of 4/8/16/32 per node, degree <= 32; 1: one warp per node
- * with a shared table, degree <= 512; 2: one CTA per node, shared table,
- * degree <= 4096; 3: one CTA per node, global table).  Times are device
- * milliseconds. ---- */
+ * (0: lane groups of 4/8/16/32 per node, degree <= 32; 1: CTAs of 64/128
+ * threads per node with shared tables, degree <= 512; 2: CTAs of 256/512
+ * threads, degree <= 8192; 3: one CTA per node with a global table).  Times
+ * are device milliseconds. ---- */
 typedef struct sclap_profile {
   int64_t kernel_launches;
   int64_t propose_launches[4];
-  double propose_ms[4];
+  double propose_ms[4];        /* per launch, events on its own stream      */
   int64_t propose_nodes[4];
   int64_t propose_arcs[4];
+  double sweep_ms;             /* propose phases: the families of a sub-round
+                                  run concurrently; first launch to last     */
+  int64_t sweeps;
 } sclap_profile;
 void sclap_profile_enable(int on);
 void sclap_profile_reset(void);

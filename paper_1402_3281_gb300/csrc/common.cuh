@@ -42,6 +42,8 @@ struct ProfileState {
   std::mutex mu;
   double ms[4] = {};
   int64_t nlaunch[4] = {}, nodes[4] = {}, arcs[4] = {};
+  double sweep_ms = 0;       // propose phases, fork to join (concurrent launches)
+  int64_t sweeps = 0;
   // timeline mode: an event after every launch; the time from the previous
   // event of the same call to this one is charged to the kernel (device time
   // plus any idle gap before it)
@@ -57,6 +59,7 @@ inline void stream_sync(cudaStream_t s) {
   if (profile().timeline.load(std::memory_order_relaxed)) timeline_mark("host", s);
 }
 cudaEvent_t event_from_pool();
+cudaStream_t side_stream(int i);
 void event_to_pool(cudaEvent_t e);
 #define SCLAP_NOTE_LAUNCH(name)                                               \
   do {                                                                        \
@@ -95,16 +98,14 @@ enum Phase : int32_t {
 enum Mode : int32_t { MODE_CLUSTER = 0, MODE_REFINE = 1, MODE_REPAIR = 2 };
 
 // Degree buckets of the LP sweep.  0..3: a group of 4/8/16/32 lanes per node,
-// labels aggregated with warp match; 4, 5: one warp per node with a
-// shared-memory table of 256 / 1024 slots; 6: one CTA per node, shared-memory
-// table; 7: one CTA per node, table in global scratch.
-constexpr int NB = 8;
-constexpr int WARP_SMALL_MAXDEG = 128;     // table 256 slots per warp
-constexpr int WARP_SMALL_SLOTS = 256;
-constexpr int WARP_HASH_MAXDEG = 512;      // table 1024 slots per warp
-constexpr int WARP_HASH_SLOTS = 1024;
-constexpr int CTA_HASH_MAXDEG = 4096;      // table 8192 slots per CTA
-constexpr int CTA_HASH_SLOTS = 8192;
+// labels aggregated with warp match; 4..7: one CTA of 64/128/256/512 threads
+// per node with a shared-memory table of 256/1024/4096/16384 slots; 8: one
+// CTA per node, table in global scratch (hubs).
+constexpr int NB = 9;
+constexpr int B4_MAXDEG = 128, B4_SLOTS = 256;
+constexpr int B5_MAXDEG = 512, B5_SLOTS = 1024;
+constexpr int B6_MAXDEG = 2048, B6_SLOTS = 4096;
+constexpr int B7_MAXDEG = 8192, B7_SLOTS = 16384;
 
 __host__ __device__ __forceinline__ int bucket_of(int64_t deg, bool overloaded) {
   if (!overloaded) {
@@ -113,11 +114,17 @@ __host__ __device__ __forceinline__ int bucket_of(int64_t deg, bool overloaded) 
     if (deg <= 16) return 2;
     if (deg <= 32) return 3;
   }
-  if (deg <= WARP_SMALL_MAXDEG) return 4;
-  if (deg <= WARP_HASH_MAXDEG) return 5;
-  if (deg <= CTA_HASH_MAXDEG) return 6;
-  return 7;
+  if (deg <= B4_MAXDEG) return 4;
+  if (deg <= B5_MAXDEG) return 5;
+  if (deg <= B6_MAXDEG) return 6;
+  if (deg <= B7_MAXDEG) return 7;
+  return 8;
 }
+
+// Weight of a cluster or block.  Node weights are validated to sum below
+// 2^31, so every label weight fits in 32 bits; sums with a node weight are
+// formed in 64 bits.
+using wgt_t = int32_t;
 
 // ---------------------------------------------------------------------------
 // A level: one CSR holding the graphs of all slots back to back (node ids are
@@ -312,11 +319,11 @@ struct LPRun {
 };
 // Runs `run.rounds` synchronous LP rounds on `lv` for every slot not marked
 // done; label/W are updated in place.  Returns the number of arcs scanned.
-int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, int64_t* W,
+int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, wgt_t* W,
                int64_t Wsize, const LPRun& run, int32_t* d_err, cudaStream_t s,
                const uint8_t* active_init = nullptr, uint8_t* active_next_out = nullptr);
 void lp_round_begin_host_keys(const SlotParams& sp, int phase, int r, int mode,
-                              const int64_t* W, cudaStream_t s);
+                              const wgt_t* W, cudaStream_t s);
 
 // contract.cu -- cluster contraction (Sec. 3.1) of every slot of a level.
 struct ContractWork {
@@ -378,7 +385,7 @@ struct GGGArgs {
   const uint64_t* tkey;    // trial key per slot
   const int32_t* level;    // coarsest level index per slot
   int32_t* label;          // out: global block ids
-  int64_t* W;              // out: block weights
+  wgt_t* W;                // out: block weights
   int64_t* conn;           // scratch [N]
   int32_t* step;           // scratch [N]
   int64_t* wfA;            // scratch [sum k]
@@ -408,20 +415,20 @@ struct FillTask {
   int64_t n0, n, g_boff;
   int32_t k;
 };
-void waterfill_isolated(const std::vector<FillTask>& tasks, int64_t* Wg, int64_t Ktot,
+void waterfill_isolated(const std::vector<FillTask>& tasks, wgt_t* Wg, int64_t Ktot,
                         cudaStream_t s);
 // flags[v] = 1 if v has neighbours; iso_w[v] = nw[v] if it has none, else 0.
 void isolated_flags(const int64_t* row_ptr, const int32_t* nw, int64_t N, uint8_t* flags,
                     int32_t* iso_w, cudaStream_t s);
 // best[g], ipcut[g] on the device; block weights copied to Wg[g_boff..].
 void ip_select_copy(const std::vector<SelectTask>& tasks, const int64_t* cut2,
-                    const int64_t* ip_W, const int64_t* ip_noff, const int64_t* ip_boff,
-                    const int32_t* ip_label, int64_t* Wg, int32_t* best, int64_t* ipcut,
+                    const wgt_t* ip_W, const int64_t* ip_noff, const int64_t* ip_boff,
+                    const int32_t* ip_label, wgt_t* Wg, int32_t* best, int64_t* ipcut,
                     cudaStream_t s);
 // fine_blk[v] = coarse_blk[cmap[v]] where cmap[v] >= 0.
 void project(const int32_t* cmap, const int32_t* coarse_blk, int32_t* fine_blk, int64_t N,
              cudaStream_t s);
 // Block weights of every slot from scratch: W[label[v]] += nw[v].
-void block_weights(const int32_t* label, const int32_t* nw, int64_t N, int64_t* W, cudaStream_t s);
+void block_weights(const int32_t* label, const int32_t* nw, int64_t N, wgt_t* W, cudaStream_t s);
 
 }  // namespace sclap

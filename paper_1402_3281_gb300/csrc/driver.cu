@@ -124,7 +124,7 @@ __global__ void k_iota(int32_t* label, int64_t N) {
     label[v] = (int32_t)v;
 }
 
-__global__ void k_w_from_nw(const int32_t* nw, int64_t N, int64_t* W) {
+__global__ void k_w_from_nw(const int32_t* nw, int64_t N, wgt_t* W) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N;
        v += (int64_t)gridDim.x * blockDim.x)
     W[v] = nw[v];
@@ -141,6 +141,21 @@ __global__ void k_gather_at(const int64_t* __restrict__ src, const int64_t* __re
                             int64_t* __restrict__ dst) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
     dst[i] = src[idx[i]];
+}
+
+__global__ void k_narrow(const int64_t* __restrict__ in, int64_t n, wgt_t* __restrict__ out,
+                         int32_t* err) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t x = in[i];
+    if (x < INT32_MIN || x > INT32_MAX) atomicOr(err, DERR_BAD_CSR);
+    out[i] = (wgt_t)x;
+  }
+}
+__global__ void k_widen(const wgt_t* __restrict__ in, int64_t n, int64_t* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = in[i];
 }
 
 struct OutTask {
@@ -349,7 +364,7 @@ struct IPIn {
   int32_t* dst_blk;    // block array of Q
 };
 
-void run_ip(const std::vector<IPIn>& in, const sclap_config& cfg, int64_t* Wg,
+void run_ip(const std::vector<IPIn>& in, const sclap_config& cfg, wgt_t* Wg,
             std::vector<int32_t>& best, std::vector<int64_t>& ipcut, int64_t* lp_arcs,
             int32_t* d_err, cudaStream_t s) {
   const int B = (int)in.size();
@@ -421,7 +436,8 @@ void run_ip(const std::vector<IPIn>& in, const sclap_config& cfg, int64_t* Wg,
 
   const int64_t K = boff[S];
   DevBuf<int32_t> label(std::max<int64_t>(ip.N, 1), s), step(std::max<int64_t>(ip.N, 1), s);
-  DevBuf<int64_t> W(std::max<int64_t>(K, 1), s), conn(std::max<int64_t>(ip.N, 1), s);
+  DevBuf<wgt_t> W(std::max<int64_t>(K, 1), s);
+  DevBuf<int64_t> conn(std::max<int64_t>(ip.N, 1), s);
   DevBuf<int64_t> wfA(std::max<int64_t>(K, 1), s), d_boff(S + 1, s), d_avg(S, s);
   DevBuf<int32_t> wforder(std::max<int64_t>(K, 1), s);
   std::vector<int64_t> h_avg(S), h_bound(S);
@@ -584,7 +600,7 @@ void run_valid_batch(const std::vector<GIn>& gs, const std::vector<int64_t>& cV,
     std::vector<int64_t> h_loff(cur.noff.begin(), cur.noff.end() - 1);
     Slots sl(s, B, cur.noff_d.p, h_loff, h_bound, h_seed, h_level, h_nlab, h_done);
     DevBuf<int32_t> label(std::max<int64_t>(v.N, 1), s);
-    DevBuf<int64_t> W(std::max<int64_t>(v.N, 1), s);
+    DevBuf<wgt_t> W(std::max<int64_t>(v.N, 1), s);
     k_iota<<<grid_for(v.N, 256, (int64_t)sms * 16), 256, 0, s>>>(label.p, v.N); SCLAP_NOTE_LAUNCH("k_iota");
     k_w_from_nw<<<grid_for(v.N, 256, (int64_t)sms * 16), 256, 0, s>>>(v.nw, v.N, W.p); SCLAP_NOTE_LAUNCH("k_w_from_nw");
     SCLAP_LAUNCH_CHECK();
@@ -642,7 +658,7 @@ void run_valid_batch(const std::vector<GIn>& gs, const std::vector<int64_t>& cV,
   for (int L = 0; L < nlev; ++L) lv[L]->blk.alloc(std::max<int64_t>(lv[L]->N, 1), s);
 
   // ---------------- initial partitioning
-  DevBuf<int64_t> Wg(std::max<int64_t>(Ktot, 1), s);
+  DevBuf<wgt_t> Wg(std::max<int64_t>(Ktot, 1), s);
   {
     std::vector<IPIn> in(B);
     for (int g = 0; g < B; ++g) {
@@ -726,15 +742,16 @@ void run_valid_batch(const std::vector<GIn>& gs, const std::vector<int64_t>& cV,
     k_write_out<<<grid, 256, 0, s>>>(d_ot.p + b0, F0.blk.p); SCLAP_NOTE_LAUNCH("k_write_out");
   }
   SCLAP_LAUNCH_CHECK();
-  std::vector<int64_t> h_cut2(B), h_W(Ktot);
+  std::vector<int64_t> h_cut2(B);
+  std::vector<wgt_t> h_W(Ktot);
   SCLAP_CUDA(cudaMemcpyAsync(h_cut2.data(), cut2.p, B * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-  SCLAP_CUDA(cudaMemcpyAsync(h_W.data(), Wg.p, Ktot * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  SCLAP_CUDA(cudaMemcpyAsync(h_W.data(), Wg.p, Ktot * sizeof(wgt_t), cudaMemcpyDeviceToHost, s));
   stream_sync(s);
   for (int g = 0; g < B; ++g) {
     GOut& o = res[g];
     o.cut = h_cut2[g] / 2;
     int64_t m = 0;
-    for (int b = 0; b < st[g].k; ++b) m = std::max(m, h_W[st[g].boff + b]);
+    for (int b = 0; b < st[g].k; ++b) m = std::max<int64_t>(m, h_W[st[g].boff + b]);
     o.maxbw = m;
     o.status = m <= st[g].Lmax ? SCLAP_OK : SCLAP_EINFEASIBLE;
     sclap_stats& x = o.st;
@@ -787,6 +804,28 @@ int64_t device_arcs(const int64_t* row_ptr, int64_t n, cudaStream_t s) {
   SCLAP_CUDA(cudaMemcpyAsync(&m, row_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   stream_sync(s);
   if (m < 0 || m >= ((int64_t)1 << 40)) throw Error(SCLAP_ECSR, "row_ptr[n] out of range");
+  return m;
+}
+
+__global__ void k_read_ends(const int64_t* const* __restrict__ ends, int n, int64_t* __restrict__ out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    out[i] = *ends[i];
+}
+
+// row_ptr[n] of many device graphs with one launch and one copy.
+std::vector<int64_t> device_arcs_many(const std::vector<const int64_t*>& ends, cudaStream_t s) {
+  const int n = (int)ends.size();
+  std::vector<int64_t> m(n, 0);
+  if (n == 0) return m;
+  DevBuf<const int64_t*> d(n, s);
+  d.upload(ends);
+  DevBuf<int64_t> out(n, s);
+  k_read_ends<<<grid_for(n, 128, 64), 128, 0, s>>>(d.p, n, out.p); SCLAP_NOTE_LAUNCH("k_read_ends");
+  SCLAP_LAUNCH_CHECK();
+  SCLAP_CUDA(cudaMemcpyAsync(m.data(), out.p, n * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  stream_sync(s);
+  for (int64_t x : m)
+    if (x < 0 || x >= ((int64_t)1 << 40)) throw Error(SCLAP_ECSR, "row_ptr[n] out of range");
   return m;
 }
 
@@ -928,13 +967,27 @@ int sclap_partition_batch(int32_t count, sclap_graph* graphs, const sclap_config
     std::vector<int> idx;
     std::vector<std::unique_ptr<DevBuf<int32_t>>> outbufs;
     std::vector<int32_t*> outs;
+    std::vector<int64_t> dev_m(count, 0);
+    if (device_ptrs) {
+      std::vector<const int64_t*> ends;
+      std::vector<int> who;
+      for (int i = 0; i < count; ++i) {
+        const sclap_graph& G = graphs[i];
+        if (G.row_ptr && G.n >= 1 && G.n < ((int64_t)1 << 31)) {
+          ends.push_back(G.row_ptr + G.n);
+          who.push_back(i);
+        }
+      }
+      const std::vector<int64_t> m = device_arcs_many(ends, s);
+      for (size_t j = 0; j < who.size(); ++j) dev_m[who[j]] = m[j];
+    }
     for (int i = 0; i < count; ++i) {
       sclap_graph& G = graphs[i];
       G.status = guarded([&] {
         check_args(G.n, G.row_ptr, G.col, G.k, G.eps, G.block_out);
         GIn g;
         if (device_ptrs) {
-          g.n = G.n; g.m = device_arcs(G.row_ptr, G.n, s); g.row_ptr = G.row_ptr;
+          g.n = G.n; g.m = dev_m[i]; g.row_ptr = G.row_ptr;
           g.col = G.col; g.nw = G.node_w; g.ew = G.edge_w;
         } else {
           ups.emplace_back(new HostUpload(G.n, G.row_ptr, G.col, G.node_w, G.edge_w, s));
@@ -1002,7 +1055,11 @@ int sclap_lp_round(int32_t mode, int64_t n, const int64_t* row_ptr, const int32_
     run.raw_key = true;
     DevBuf<int32_t> d_err(1, s);
     d_err.zero();
-    lp_run(L.view(), sl.sp, label, W, nlabels, run, d_err.p, s, active_cur, active_next);
+    DevBuf<wgt_t> W32(nlabels, s);
+    k_narrow<<<grid_for(nlabels, 256, 1024), 256, 0, s>>>(W, nlabels, W32.p, d_err.p); SCLAP_NOTE_LAUNCH("k_narrow");
+    check_err(d_err.p, s);
+    lp_run(L.view(), sl.sp, label, W32.p, nlabels, run, d_err.p, s, active_cur, active_next);
+    k_widen<<<grid_for(nlabels, 256, 1024), 256, 0, s>>>(W32.p, nlabels, W); SCLAP_NOTE_LAUNCH("k_widen");
     check_err(d_err.p, s);
     int64_t mv = 0;
     SCLAP_CUDA(cudaMemcpyAsync(&mv, sl.moved.p, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -1028,7 +1085,7 @@ int sclap_cluster(int64_t n, const int64_t* row_ptr, const int32_t* col, const i
     Level L;
     single_level(g, L, s);
     Slots sl(s, 1, L.noff_d.p, {0}, {U}, {seed}, {level}, {0}, {0});
-    DevBuf<int64_t> W(n, s);
+    DevBuf<wgt_t> W(n, s);
     k_iota<<<grid_for(n, 256, (int64_t)num_sms() * 16), 256, 0, s>>>(label_out, n); SCLAP_NOTE_LAUNCH("k_iota");
     k_w_from_nw<<<grid_for(n, 256, (int64_t)num_sms() * 16), 256, 0, s>>>(L.nw.p, n, W.p); SCLAP_NOTE_LAUNCH("k_w_from_nw");
     LPRun run;
@@ -1101,7 +1158,7 @@ int sclap_initial_partition(int64_t n, const int64_t* row_ptr, const int32_t* co
     validate(g, s, &cV, &maxc);
     Level L;
     single_level(g, L, s);
-    DevBuf<int64_t> Wg(k, s);
+    DevBuf<wgt_t> Wg(k, s);
     DevBuf<int32_t> d_err(1, s);
     d_err.zero();
     std::vector<IPIn> in{IPIn{&L, 0, k, Lmax, avg, seed, level, 0, block_out}};
@@ -1132,7 +1189,7 @@ int sclap_refine(int64_t n, const int64_t* row_ptr, const int32_t* col, const in
     check_range(block, n, 0, k, s, "block");
     Level L;
     single_level(g, L, s);
-    DevBuf<int64_t> W(k, s);
+    DevBuf<wgt_t> W(k, s);
     W.zero();
     block_weights(block, L.nw.p, n, W.p, s);
     Slots sl(s, 1, L.noff_d.p, {0}, {Lmax}, {seed}, {level}, {k}, {0});
@@ -1191,6 +1248,8 @@ void sclap_profile_reset(void) {
   std::lock_guard<std::mutex> lk(P.mu);
   P.launches.store(0);
   for (int b = 0; b < 4; ++b) { P.ms[b] = 0; P.nlaunch[b] = 0; P.nodes[b] = 0; P.arcs[b] = 0; }
+  P.sweep_ms = 0;
+  P.sweeps = 0;
 }
 
 void sclap_profile_read(sclap_profile* out) {
@@ -1204,6 +1263,8 @@ void sclap_profile_read(sclap_profile* out) {
     out->propose_nodes[b] = P.nodes[b];
     out->propose_arcs[b] = P.arcs[b];
   }
+  out->sweep_ms = P.sweep_ms;
+  out->sweeps = P.sweeps;
 }
 
 }  // extern "C"

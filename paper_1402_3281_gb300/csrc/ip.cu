@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(GNT) k_ggg(GGGArgs a) {
         for (int32_t q = tid; q < ns2; q += GNT) a.label[a.step[base + q]] = (int32_t)(bo + j);
         __syncthreads();
       }
-      if (tid == 0) a.W[bo + j] = Wj_sh;
+      if (tid == 0) a.W[bo + j] = (wgt_t)Wj_sh;
       __syncthreads();
     }
     // water-filling of the nodes left unassigned
@@ -185,12 +185,15 @@ __global__ void __launch_bounds__(GNT) k_ggg(GGGArgs a) {
     if (R > 0) {
       if (tid == 0) {
         int64_t lo = a.W[bo], hi = a.W[bo];
-        for (int32_t b = 1; b < k; ++b) { lo = min(lo, a.W[bo + b]); hi = max(hi, a.W[bo + b]); }
+        for (int32_t b = 1; b < k; ++b) {
+          lo = min64(lo, (int64_t)a.W[bo + b]);
+          hi = max64(hi, (int64_t)a.W[bo + b]);
+        }
         hi += R;
         while (lo < hi) {
           const int64_t mid = lo + (hi - lo) / 2;
           int64_t f = 0;
-          for (int32_t b = 0; b < k; ++b) f += max64(0, mid - a.W[bo + b]);
+          for (int32_t b = 0; b < k; ++b) f += max64(0, mid - (int64_t)a.W[bo + b]);
           if (f >= R) hi = mid; else lo = mid + 1;
         }
         const int64_t L = lo;
@@ -211,7 +214,7 @@ __global__ void __launch_bounds__(GNT) k_ggg(GGGArgs a) {
         int64_t acc = 0;
         for (int32_t j = 0; j < k; ++j) {
           a.wfA[bo + j] = acc;
-          acc += max64(0, L - a.W[bo + a.wforder[bo + j]]);
+          acc += max64(0, L - (int64_t)a.W[bo + a.wforder[bo + j]]);
         }
       }
       __syncthreads();
@@ -231,7 +234,7 @@ __global__ void __launch_bounds__(GNT) k_ggg(GGGArgs a) {
           }
           const int32_t b = a.wforder[bo + lo];
           a.label[base + v] = (int32_t)(bo + b);
-          atomicAdd(ull(&a.W[bo + b]), (unsigned long long)wt);
+          atomicAdd(&a.W[bo + b], (wgt_t)wt);
         }
         carry += tw;
       }
@@ -240,29 +243,75 @@ __global__ void __launch_bounds__(GNT) k_ggg(GGGArgs a) {
   }
 }
 
+// Twice the cut of every slot: 32 nodes per warp, their arcs spread over
+// the lanes; per-slot sums merged within the warp before the atomic.
 __global__ void __launch_bounds__(256) k_slot_cut(const int64_t* __restrict__ row_ptr,
                                                   const int32_t* __restrict__ col,
                                                   const int32_t* __restrict__ ew,
                                                   const int32_t* __restrict__ gid,
                                                   const int32_t* __restrict__ label, int64_t N,
                                                   int64_t* __restrict__ cut2) {
+  __shared__ int sh_slot;
+  __shared__ unsigned long long sh_sum;
   const int lane = threadIdx.x & 31;
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t v = warp; v < N; v += nwarps) {
-    const int32_t lv = label[v];
-    long long sum = 0;
-    for (int64_t e = row_ptr[v] + lane; e < row_ptr[v + 1]; e += 32)
-      if (label[col[e]] != lv) sum += ew[e];
-    sum = warp_sum_ll(sum);
-    if (lane == 0 && sum) atomicAdd(ull(&cut2[gid[v]]), (unsigned long long)sum);
+  if (threadIdx.x == 0) {
+    const int64_t v0 = (int64_t)blockIdx.x * blockDim.x;
+    sh_slot = v0 < N ? gid[v0] : -1;
+    sh_sum = 0;
   }
+  __syncthreads();
+  for (int64_t base = w0 * 32; base < N; base += nwarps * 32) {
+    const int64_t v = base + lane;
+    int64_t rs = 0, d = 0;
+    int32_t lv = 0, s = -1;
+    if (v < N) {
+      rs = row_ptr[v];
+      d = row_ptr[v + 1] - rs;
+      lv = label[v];
+      s = gid[v];
+    }
+    long long incl = d;
+    for (int o = 1; o < 32; o <<= 1) {
+      long long y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const long long excl = incl - d;
+    const long long total = __shfl_sync(0xffffffffu, incl, 31);
+    for (long long x0 = 0; x0 < total; x0 += 32) {
+      const long long x = x0 + lane;
+      int L = 0;
+      for (int step = 16; step > 0; step >>= 1) {
+        long long y = __shfl_sync(0xffffffffu, incl, L + step - 1);
+        if (y <= x) L += step;
+      }
+      const long long rsL = __shfl_sync(0xffffffffu, (long long)rs, L);
+      const long long exL = __shfl_sync(0xffffffffu, excl, L);
+      const int32_t lvL = __shfl_sync(0xffffffffu, lv, L);
+      const int32_t sL = __shfl_sync(0xffffffffu, s, L);
+      int32_t w = 0;
+      if (x < total) {
+        const int64_t e = rsL + (x - exL);
+        if (label[col[e]] != lvL) w = ew[e];
+      }
+      const int32_t key = w > 0 ? sL : -1;
+      const unsigned mm = __match_any_sync(0xffffffffu, key);
+      const int64_t sum = match_sum(mm, w);
+      if (key >= 0 && lane == __ffs(mm) - 1) {
+        if (sL == sh_slot) atomicAdd(&sh_sum, (unsigned long long)sum);
+        else atomicAdd(ull(&cut2[sL]), (unsigned long long)sum);
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && sh_sum) atomicAdd(ull(&cut2[sh_slot]), sh_sum);
 }
 
 __global__ void k_select_copy(const SelectTask* __restrict__ tasks, const int64_t* __restrict__ cut2,
-                              const int64_t* __restrict__ ip_W, const int64_t* __restrict__ ip_noff,
+                              const wgt_t* __restrict__ ip_W, const int64_t* __restrict__ ip_noff,
                               const int64_t* __restrict__ ip_boff,
-                              const int32_t* __restrict__ ip_label, int64_t* __restrict__ Wg,
+                              const int32_t* __restrict__ ip_label, wgt_t* __restrict__ Wg,
                               int32_t* __restrict__ best, int64_t* __restrict__ ipcut) {
   const SelectTask t = tasks[blockIdx.x];
   __shared__ int32_t bt_sh;
@@ -272,7 +321,7 @@ __global__ void k_select_copy(const SelectTask* __restrict__ tasks, const int64_
     for (int32_t tr = 0; tr < t.trials; ++tr) {
       const int64_t slot = t.slot0 + tr;
       int64_t mx = 0;
-      for (int32_t b = 0; b < t.k; ++b) mx = max(mx, ip_W[ip_boff[slot] + b]);
+      for (int32_t b = 0; b < t.k; ++b) mx = max64(mx, (int64_t)ip_W[ip_boff[slot] + b]);
       const int64_t ov = max64(0, mx - t.Lmax);
       const int64_t c = cut2[slot] / 2;
       if (bt < 0 || ov < bo || (ov == bo && c < bc)) { bo = ov; bc = c; bt = tr; }
@@ -306,10 +355,10 @@ __global__ void k_project(const int32_t* __restrict__ cmap, const int32_t* __res
 }
 
 __global__ void k_block_weights(const int32_t* __restrict__ label, const int32_t* __restrict__ nw,
-                                int64_t N, int64_t* __restrict__ W) {
+                                int64_t N, wgt_t* __restrict__ W) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N;
        v += (int64_t)gridDim.x * blockDim.x)
-    atomicAdd(ull(&W[label[v]]), (unsigned long long)nw[v]);
+    atomicAdd(&W[label[v]], (wgt_t)nw[v]);
 }
 
 __global__ void k_isolated(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ nw,
@@ -325,21 +374,21 @@ __global__ void k_isolated(const int64_t* __restrict__ row_ptr, const int32_t* _
 // One thread per graph: fill level L (smallest L with sum_b max(0, L - W_b)
 // >= R), blocks ordered by (weight, id), and the start of each block's
 // stretch of free capacity below L.
-__global__ void k_wf_setup(const FillTask* __restrict__ tasks, int ntasks, const int64_t* Wg,
+__global__ void k_wf_setup(const FillTask* __restrict__ tasks, int ntasks, const wgt_t* Wg,
                            int32_t* order, int64_t* A) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= ntasks) return;
   const FillTask t = tasks[i];
   const int64_t R = t.iso_prefix[t.n0 + t.n] - t.iso_prefix[t.n0];
   if (R == 0) return;
-  const int64_t* W = Wg + t.g_boff;
+  const wgt_t* W = Wg + t.g_boff;
   int64_t lo = W[0], hi = W[0];
-  for (int32_t b = 1; b < t.k; ++b) { lo = min(lo, W[b]); hi = max(hi, W[b]); }
+  for (int32_t b = 1; b < t.k; ++b) { lo = min64(lo, (int64_t)W[b]); hi = max64(hi, (int64_t)W[b]); }
   hi += R;
   while (lo < hi) {
     const int64_t mid = lo + (hi - lo) / 2;
     int64_t f = 0;
-    for (int32_t b = 0; b < t.k; ++b) f += max64(0, mid - W[b]);
+    for (int32_t b = 0; b < t.k; ++b) f += max64(0, mid - (int64_t)W[b]);
     if (f >= R) hi = mid; else lo = mid + 1;
   }
   int32_t* ord = order + t.g_boff;
@@ -354,11 +403,11 @@ __global__ void k_wf_setup(const FillTask* __restrict__ tasks, int ntasks, const
   int64_t acc = 0;
   for (int32_t j = 0; j < t.k; ++j) {
     A[t.g_boff + j] = acc;
-    acc += max64(0, lo - W[ord[j]]);
+    acc += max64(0, lo - (int64_t)W[ord[j]]);
   }
 }
 
-__global__ void k_wf_assign(const FillTask* __restrict__ tasks, int64_t* Wg,
+__global__ void k_wf_assign(const FillTask* __restrict__ tasks, wgt_t* Wg,
                             const int32_t* __restrict__ order, const int64_t* __restrict__ A) {
   const FillTask t = tasks[blockIdx.y];
   const int64_t base = t.iso_prefix[t.n0];
@@ -373,7 +422,7 @@ __global__ void k_wf_assign(const FillTask* __restrict__ tasks, int64_t* Wg,
     }
     const int32_t b = order[t.g_boff + lo];
     t.blk[t.n0 + v] = (int32_t)(t.g_boff + b);
-    atomicAdd(ull(&Wg[t.g_boff + b]), (unsigned long long)t.nw[t.n0 + v]);
+    atomicAdd(&Wg[t.g_boff + b], (wgt_t)t.nw[t.n0 + v]);
   }
 }
 
@@ -386,7 +435,7 @@ void isolated_flags(const int64_t* row_ptr, const int32_t* nw, int64_t N, uint8_
   SCLAP_LAUNCH_CHECK();
 }
 
-void waterfill_isolated(const std::vector<FillTask>& tasks, int64_t* Wg, int64_t Ktot,
+void waterfill_isolated(const std::vector<FillTask>& tasks, wgt_t* Wg, int64_t Ktot,
                         cudaStream_t s) {
   if (tasks.empty()) return;
   DevBuf<FillTask> d(tasks.size(), s);
@@ -438,14 +487,14 @@ void ggg_trials(const GGGArgs& a, cudaStream_t s) {
 
 void slot_cut(const LevelView& lv, const int32_t* label, int64_t* cut2, cudaStream_t s) {
   if (lv.N <= 0) return;
-  k_slot_cut<<<grid_for(lv.N, 8, (int64_t)num_sms() * 16), 256, 0, s>>>(
+  k_slot_cut<<<grid_for(lv.N, 256, (int64_t)num_sms() * 16), 256, 0, s>>>(
       lv.row_ptr, lv.col, lv.ew, lv.gid, label, lv.N, cut2); SCLAP_NOTE_LAUNCH("k_slot_cut");
   SCLAP_LAUNCH_CHECK();
 }
 
 void ip_select_copy(const std::vector<SelectTask>& tasks, const int64_t* cut2,
-                    const int64_t* ip_W, const int64_t* ip_noff, const int64_t* ip_boff,
-                    const int32_t* ip_label, int64_t* Wg, int32_t* best, int64_t* ipcut,
+                    const wgt_t* ip_W, const int64_t* ip_noff, const int64_t* ip_boff,
+                    const int32_t* ip_label, wgt_t* Wg, int32_t* best, int64_t* ipcut,
                     cudaStream_t s) {
   if (tasks.empty()) return;
   DevBuf<SelectTask> d(tasks.size(), s);
@@ -464,7 +513,7 @@ void project(const int32_t* cmap, const int32_t* coarse_blk, int32_t* fine_blk, 
   SCLAP_LAUNCH_CHECK();
 }
 
-void block_weights(const int32_t* label, const int32_t* nw, int64_t N, int64_t* W,
+void block_weights(const int32_t* label, const int32_t* nw, int64_t N, wgt_t* W,
                    cudaStream_t s) {
   if (N <= 0) return;
   k_block_weights<<<grid_for(N, 256, (int64_t)num_sms() * 16), 256, 0, s>>>(label, nw, N, W); SCLAP_NOTE_LAUNCH("k_block_weights");

@@ -39,12 +39,14 @@ struct LPArgs {
   int32_t* rounds;
   // state
   int32_t* label;
-  int64_t* W;
+  wgt_t* W;
   int64_t* in_w;
   int32_t mode;
   int32_t S;
-  // sub-round lists and proposals
-  int32_t* list;
+  // sub-round lists: for each listed node {v, own label, weight, slot} and
+  // {row start, degree}, written by the bucketing pass
+  int4* rec;
+  longlong2* rec2;
   int32_t* prop_t;
   uint64_t* prop_key;
   int8_t* adm;
@@ -83,17 +85,19 @@ struct NodeCtx {
   uint64_t hv;
 };
 
-__device__ __forceinline__ NodeCtx load_node(const LPArgs& a, int32_t v) {
+__device__ __forceinline__ NodeCtx load_node(const LPArgs& a, int64_t i) {
+  const int4 r = a.rec[i];
+  const longlong2 r2 = a.rec2[i];
   NodeCtx c;
-  c.v = v;
-  c.slot = a.gid[v];
-  c.own = a.label[v];
-  c.cv = a.nw[v];
+  c.v = r.x;
+  c.own = r.y;
+  c.cv = r.z;
+  c.slot = r.w;
+  c.rs = r2.x;
+  c.re = r2.x + r2.y;
   c.bound = a.bound[c.slot];
   c.loff = a.loff[c.slot];
-  c.rs = a.row_ptr[v];
-  c.re = a.row_ptr[v + 1];
-  c.hv = mix64(a.rkey[c.slot] ^ (uint64_t)(v - a.noff[c.slot]));
+  c.hv = mix64(a.rkey[c.slot] ^ (uint64_t)(c.v - a.noff[c.slot]));
   return c;
 }
 
@@ -124,7 +128,7 @@ __global__ void k_round_begin(LPArgs a, int32_t nslots, int32_t phase, int32_t r
     if (a.mode == MODE_REPAIR) {
       int64_t mx = 0;
       const int64_t lo = a.loff[s];
-      for (int32_t b = 0; b < a.nlab[s]; ++b) mx = max(mx, a.W[lo + b]);
+      for (int32_t b = 0; b < a.nlab[s]; ++b) mx = max64(mx, (int64_t)a.W[lo + b]);
       if (mx <= a.bound[s]) { a.done[s] = 1; continue; }
     }
     a.rkey[s] = raw_key ? seed[s] : hkey(seed[s], (uint64_t)phase, (uint64_t)level[s], (uint64_t)r);
@@ -230,7 +234,10 @@ __global__ void __launch_bounds__(BK_NT) k_bucket_scatter(LPArgs a, int64_t N) {
   for (int j = 0; j < BK_PER; ++j) {
     if (key[j] < 0) continue;
     const int64_t v = base + (int64_t)j * BK_NT + threadIdx.x;
-    a.list[a.boff[key[j]] + sh_base[key[j]] + rank[j]] = (int32_t)v;
+    const int64_t pos = a.boff[key[j]] + sh_base[key[j]] + rank[j];
+    const int64_t rs = a.row_ptr[v];
+    a.rec[pos] = make_int4((int32_t)v, a.label[v], a.nw[v], a.gid[v]);
+    a.rec2[pos] = make_longlong2(rs, a.row_ptr[v + 1] - rs);
   }
 }
 
@@ -264,7 +271,7 @@ __device__ __forceinline__ void propose_small(const LPArgs& a, int64_t lbeg, int
     int32_t C = -1, w = 0;
     bool valid = false;
     if (has) {
-      c = load_node(a, a.list[i]);
+      c = load_node(a, i);
       if (gl < c.re - c.rs) {
         valid = true;
         const int32_t u = a.col[c.rs + gl];
@@ -279,22 +286,66 @@ __device__ __forceinline__ void propose_small(const LPArgs& a, int64_t lbeg, int
     long long oc = (valid && leader && C == c.own) ? conn : 0;
     oc = warp_max_ll(oc, G);
     Cand cd{-1, 0, 0};
-    if (valid && leader && C != c.own && a.W[C] + c.cv <= c.bound) cd = make_cand(c, C, conn);
+    if (valid && leader && C != c.own && (int64_t)a.W[C] + c.cv <= c.bound) cd = make_cand(c, C, conn);
     cd = warp_best(cd, G);
     if (has && gl == 0) write_prop(a, i, c, cd, oc, false);
   }
 }
 
-// The four lane-group buckets of one sub-round in one launch: block ranges
-// [bs[j], bs[j+1]) serve bucket j.
+// Degrees <= MAXD (4 or 8): one thread per node.  The row sits in registers
+// (unrolled, predicated loads); equal labels are merged by an O(d^2)
+// comparison and the best candidate is chosen without cross-lane traffic.
+template <int MAXD>
+__device__ __forceinline__ void propose_thread(const LPArgs& a, int64_t lbeg, int64_t cnt,
+                                               int64_t blk, int64_t nblk) {
+  for (int64_t li = blk * blockDim.x + threadIdx.x; li < cnt; li += nblk * blockDim.x) {
+    const int64_t i = lbeg + li;
+    const NodeCtx c = load_node(a, i);
+    const int deg = (int)(c.re - c.rs);
+    int32_t C[MAXD], w[MAXD];
+#pragma unroll
+    for (int j = 0; j < MAXD; ++j) {
+      C[j] = -1;
+      w[j] = 0;
+      if (j < deg) {
+        w[j] = a.ew[c.rs + j];
+        C[j] = a.label[a.col[c.rs + j]];
+      }
+    }
+    long long oc = 0;
+    Cand best{-1, 0, 0};
+#pragma unroll
+    for (int j = 0; j < MAXD; ++j) {
+      if (C[j] < 0) continue;
+      bool first = true;
+      int64_t conn = w[j];
+#pragma unroll
+      for (int l = 0; l < MAXD; ++l) {
+        if (l == j || C[l] != C[j]) continue;
+        if (l < j) first = false;
+        conn += w[l];
+      }
+      if (!first) continue;
+      if (C[j] == c.own) { oc = conn; continue; }
+      if ((int64_t)a.W[C[j]] + c.cv > c.bound) continue;
+      const Cand x = make_cand(c, C[j], conn);
+      if (best.conn < 0 || cand_better(x, best)) best = x;
+    }
+    write_prop(a, i, c, best, oc, false);
+  }
+}
+
+// The four small-degree buckets of one sub-round in one launch: block ranges
+// [bs[j], bs[j+1]) serve bucket j (one thread per node for degree <= 8,
+// lane groups of 16 / 32 above).
 struct SmallLaunch {
   int64_t beg[4], cnt[4];
   int32_t bs[5];
 };
 __global__ void __launch_bounds__(256) k_propose_small(LPArgs a, SmallLaunch L) {
   const int32_t b = blockIdx.x;
-  if (b < L.bs[1]) propose_small<4>(a, L.beg[0], L.cnt[0], b - L.bs[0], L.bs[1] - L.bs[0]);
-  else if (b < L.bs[2]) propose_small<8>(a, L.beg[1], L.cnt[1], b - L.bs[1], L.bs[2] - L.bs[1]);
+  if (b < L.bs[1]) propose_thread<4>(a, L.beg[0], L.cnt[0], b - L.bs[0], L.bs[1] - L.bs[0]);
+  else if (b < L.bs[2]) propose_thread<8>(a, L.beg[1], L.cnt[1], b - L.bs[1], L.bs[2] - L.bs[1]);
   else if (b < L.bs[3]) propose_small<16>(a, L.beg[2], L.cnt[2], b - L.bs[2], L.bs[3] - L.bs[2]);
   else propose_small<32>(a, L.beg[3], L.cnt[3], b - L.bs[3], L.bs[4] - L.bs[3]);
 }
@@ -413,7 +464,7 @@ __global__ void __launch_bounds__(NT) k_propose_cta(LPArgs a, int64_t lbeg, int6
   }
   for (int64_t li = blockIdx.x; li < cnt; li += gridDim.x) {
     const int64_t i = lbeg + li;
-    const NodeCtx c = load_node(a, a.list[i]);
+    const NodeCtx c = load_node(a, i);
     const bool ov = a.mode != MODE_CLUSTER && a.W[c.own] > c.bound;
     long long oc = 0;
     Cand cd{-1, 0, 0};
@@ -427,7 +478,7 @@ __global__ void __launch_bounds__(NT) k_propose_cta(LPArgs a, int64_t lbeg, int6
         if (b == own_l) { oc = conn; continue; }
         if (conn == 0 && !ov) continue;
         const int32_t C = (int32_t)(c.loff + b);
-        if (a.W[C] + c.cv > c.bound) continue;
+        if ((int64_t)a.W[C] + c.cv > c.bound) continue;
         Cand x = make_cand(c, C, conn);
         if (cd.conn < 0 || cand_better(x, cd)) cd = x;
       }
@@ -444,7 +495,7 @@ __global__ void __launch_bounds__(NT) k_propose_cta(LPArgs a, int64_t lbeg, int6
         if (K == -1) continue;
         const int64_t conn = (int64_t)vals[j];
         if (K == c.own) oc = conn;
-        else if (!ov && a.W[K] + c.cv <= c.bound) {
+        else if (!ov && (int64_t)a.W[K] + c.cv <= c.bound) {
           Cand x = make_cand(c, K, conn);
           if (cd.conn < 0 || cand_better(x, cd)) cd = x;
         }
@@ -452,7 +503,7 @@ __global__ void __launch_bounds__(NT) k_propose_cta(LPArgs a, int64_t lbeg, int6
       if (ov) {
         for (int32_t b = tid; b < nl; b += NT) {
           const int32_t C = (int32_t)(c.loff + b);
-          if (C == c.own || a.W[C] + c.cv > c.bound) continue;
+          if (C == c.own || (int64_t)a.W[C] + c.cv > c.bound) continue;
           Cand x = make_cand(c, C, table_get(keys, vals, logcap, C));
           if (cd.conn < 0 || cand_better(x, cd)) cd = x;
         }
@@ -474,8 +525,8 @@ __global__ void k_resolve(LPArgs a, int64_t lbeg, int64_t cnt) {
     const int32_t t = a.prop_t[i];
     a.stage[i] = 0;
     if (t < 0) { a.adm[i] = 0; continue; }
-    const int32_t s = a.gid[a.list[i]];
-    if (a.W[t] + a.in_w[t] <= a.bound[s]) {
+    const int32_t s = a.rec[i].w;
+    if ((int64_t)a.W[t] + a.in_w[t] <= a.bound[s]) {
       a.adm[i] = 1;
     } else {
       a.adm[i] = 0;
@@ -493,9 +544,9 @@ __global__ void k_forced(LPArgs a, int64_t lbeg, int64_t cnt) {
     const int64_t i = lbeg + li;
     a.stage[i] = 0;
     if (a.adm[i] != 1) continue;
-    const int32_t v = a.list[i];
-    const int32_t own = a.label[v];
-    if (a.W[own] > a.bound[a.gid[v]]) {
+    const int4 r = a.rec[i];
+    const int32_t own = r.y;
+    if (a.W[own] > a.bound[r.w]) {
       a.grp[i] = own;
       const int c = atomicAdd(&a.ovf_cnt[own], 1);
       a.stage[i] = c == 0 ? 2 : 1;
@@ -516,11 +567,11 @@ __global__ void k_ovf_alloc(LPArgs a, int64_t lbeg, int64_t cnt, int32_t source)
     const int64_t base = (int64_t)atomicAdd(ull(&a.ctr[0]), (unsigned long long)n);
     a.ovf_base[g] = base;
     const int64_t seg = (int64_t)atomicAdd(ull(&a.ctr[1]), 1ull);
-    const int64_t bound = a.bound[a.gid[a.list[i]]];
+    const int64_t bound = a.bound[a.rec[i].w];
     a.seg_g[seg] = g;
     a.seg_base[seg] = base;
     a.seg_cnt[seg] = n;
-    a.seg_thr[seg] = source ? (a.W[g] - bound - 1) : (bound - a.W[g]);
+    a.seg_thr[seg] = source ? ((int64_t)a.W[g] - bound - 1) : (bound - (int64_t)a.W[g]);
   }
 }
 
@@ -531,10 +582,10 @@ __global__ void k_ovf_scatter(LPArgs a, int64_t lbeg, int64_t cnt) {
     if (a.stage[i] == 0) continue;
     const int32_t g = a.grp[i];
     const int64_t pos = a.ovf_base[g] + atomicAdd(&a.ovf_fill[g], 1);
-    const int32_t v = a.list[i];
+    const int4 r = a.rec[i];
     a.ent_key[pos] = a.prop_key[i];
-    a.ent_v[pos] = v;
-    a.ent_w[pos] = a.nw[v];
+    a.ent_v[pos] = r.x;
+    a.ent_w[pos] = r.z;
     a.ent_i[pos] = (int32_t)(i);
   }
 }
@@ -740,41 +791,36 @@ __global__ void __launch_bounds__(SEL_NT) k_ovf_select(LPArgs a, int32_t source)
 // Admitted moves update labels and weights; moved nodes activate their
 // neighbours (small rows by their own lane, larger rows by the whole warp).
 __global__ void __launch_bounds__(256) k_apply(LPArgs a, int64_t lbeg, int64_t cnt) {
-  __shared__ int sh_slot;
-  __shared__ unsigned long long sh_moved;
   const int lane = threadIdx.x & 31;
   const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  if (threadIdx.x == 0) {
-    const int64_t li0 = (int64_t)blockIdx.x * blockDim.x;
-    sh_slot = li0 < cnt ? a.gid[a.list[lbeg + li0]] : -1;
-    sh_moved = 0;
-  }
-  __syncthreads();
+  int32_t run_slot = -1;           // moves counted in registers per slot run
+  unsigned long long run_cnt = 0;
   for (int64_t b0 = w0 * 32; b0 < cnt; b0 += nw * 32) {
     const int64_t li = b0 + lane;
-    int32_t slot = -1, v = -1;
+    int32_t slot = -1;
     int64_t rs = 0, re = 0;
     if (li < cnt) {
       const int64_t i = lbeg + li;
       const int32_t t = a.prop_t[i];
+      const int8_t ad = a.adm[i];
       if (t >= 0) {
         a.in_w[t] = 0;
-        if (a.adm[i]) {
-          v = a.list[i];
-          const int32_t own = a.label[v];
-          const int64_t cv = a.nw[v];
-          a.label[v] = t;
-          atomicAdd(ull(&a.W[t]), (unsigned long long)cv);
-          atomicAdd(ull(&a.W[own]), (unsigned long long)(-cv));
-          slot = a.gid[v];
+        if (ad) {
+          const int4 r = a.rec[i];
+          const int32_t v = r.x, own = r.y, cv = r.z;
+          slot = r.w;
           if (a.act_next) {
-            rs = a.row_ptr[v];
-            re = a.row_ptr[v + 1];
-            if (re - rs <= 8) {
-              for (int64_t e = rs; e < re; ++e) a.act_next[a.col[e]] = 1;
-              re = rs;
-            }
+            const longlong2 r2 = a.rec2[i];
+            rs = r2.x;
+            re = r2.x + r2.y;
+          }
+          a.label[v] = t;
+          atomicAdd(&a.W[t], (wgt_t)cv);
+          atomicSub(&a.W[own], (wgt_t)cv);
+          if (re - rs <= 8) {
+            for (int64_t e = rs; e < re; ++e) a.act_next[a.col[e]] = 1;
+            re = rs;
           }
         }
       }
@@ -789,15 +835,51 @@ __global__ void __launch_bounds__(256) k_apply(LPArgs a, int64_t lbeg, int64_t c
     }
     const unsigned mm = __match_any_sync(0xffffffffu, slot);
     if (slot >= 0 && lane == __ffs(mm) - 1) {
-      if (slot == sh_slot) atomicAdd(&sh_moved, (unsigned long long)__popc(mm));
-      else atomicAdd(ull(&a.moved[slot]), (unsigned long long)__popc(mm));
+      if (slot == run_slot) {
+        run_cnt += __popc(mm);
+      } else {
+        if (run_cnt) atomicAdd(ull(&a.moved[run_slot]), run_cnt);
+        run_slot = slot;
+        run_cnt = __popc(mm);
+      }
     }
   }
-  __syncthreads();
-  if (threadIdx.x == 0 && sh_moved) atomicAdd(ull(&a.moved[sh_slot]), sh_moved);
+  if (run_cnt) atomicAdd(ull(&a.moved[run_slot]), run_cnt);
 }
 
 }  // namespace
+
+// Side streams for concurrent launches (created once, non-blocking).
+cudaStream_t side_stream(int i) {
+  static std::mutex mu;
+  static std::vector<cudaStream_t> pool;
+  std::lock_guard<std::mutex> lk(mu);
+  while ((int)pool.size() <= i) {
+    cudaStream_t st;
+    SCLAP_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    pool.push_back(st);
+  }
+  return pool[i];
+}
+
+// Reused events without timing, for stream fork/join only.
+std::mutex g_sync_ev_mu;
+std::vector<cudaEvent_t> g_sync_events;
+cudaEvent_t sync_event_get() {
+  std::lock_guard<std::mutex> lk(g_sync_ev_mu);
+  if (!g_sync_events.empty()) {
+    cudaEvent_t e = g_sync_events.back();
+    g_sync_events.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  SCLAP_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  return e;
+}
+void sync_event_put(cudaEvent_t e) {
+  std::lock_guard<std::mutex> lk(g_sync_ev_mu);
+  g_sync_events.push_back(e);
+}
 
 // Reused CUDA events for the profiling brackets.
 std::mutex g_event_mu;
@@ -867,7 +949,7 @@ std::string timeline_dump() {
 // ---------------------------------------------------------------------------
 // Host driver of the rounds.
 // ---------------------------------------------------------------------------
-int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, int64_t* W,
+int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, wgt_t* W,
                int64_t Wsize, const LPRun& run, int32_t* d_err, cudaStream_t s,
                const uint8_t* active_init, uint8_t* active_next_out) {
   const int64_t N = lv.N;
@@ -879,7 +961,9 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, int64_
   DevBuf<int64_t> in_w((size_t)Wsize, s), ovf_base((size_t)Wsize, s);
   DevBuf<int32_t> ovf_cnt((size_t)Wsize, s), ovf_fill((size_t)Wsize, s);
   in_w.zero(); ovf_cnt.zero(); ovf_fill.zero();
-  DevBuf<int32_t> list(N, s), prop_t(N, s), grp(N, s), seg_g(N, s), seg_cnt(N, s);
+  DevBuf<int4> rec(N, s);
+  DevBuf<longlong2> rec2(N, s);
+  DevBuf<int32_t> prop_t(N, s), grp(N, s), seg_g(N, s), seg_cnt(N, s);
   DevBuf<uint64_t> prop_key(N, s), ent_key(N, s);
   DevBuf<int8_t> adm(N, s), stage(N, s);
   DevBuf<int64_t> seg_base(N, s), seg_thr(N, s);
@@ -914,7 +998,7 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, int64_
   a.noff = sp.noff; a.loff = sp.loff; a.bound = sp.bound; a.rkey = sp.rkey; a.nlab = sp.nlab;
   a.done = sp.done; a.moved = sp.moved; a.rounds = sp.rounds;
   a.label = label; a.W = W; a.in_w = in_w.p; a.mode = run.mode; a.S = S;
-  a.list = list.p; a.prop_t = prop_t.p; a.prop_key = prop_key.p; a.adm = adm.p; a.stage = stage.p;
+  a.rec = rec.p; a.rec2 = rec2.p; a.prop_t = prop_t.p; a.prop_key = prop_key.p; a.adm = adm.p; a.stage = stage.p;
   a.grp = grp.p; a.ovf_cnt = ovf_cnt.p; a.ovf_fill = ovf_fill.p; a.ovf_base = ovf_base.p;
   a.ctr = ctr.p; a.seg_g = seg_g.p; a.seg_base = seg_base.p; a.seg_cnt = seg_cnt.p;
   a.seg_thr = seg_thr.p; a.ent_key = ent_key.p; a.ent_v = ent_v.p; a.ent_w = ent_w.p;
@@ -933,13 +1017,16 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, int64_
   int64_t arcs_total = 0;
   const unsigned small_grid = (unsigned)(sms * 8);
   constexpr size_t SLOT_BYTES = sizeof(unsigned long long) + sizeof(int32_t);
-  const size_t smem4 = WARP_SMALL_SLOTS * SLOT_BYTES;   // 64 threads, 256 slots
-  const size_t smem5 = WARP_HASH_SLOTS * SLOT_BYTES;    // 128 threads, 1024 slots
-  const size_t smem6 = CTA_HASH_SLOTS * SLOT_BYTES;     // 512 threads, 8192 slots
+  const size_t smem4 = B4_SLOTS * SLOT_BYTES;
+  const size_t smem5 = B5_SLOTS * SLOT_BYTES;
+  const size_t smem6 = B6_SLOTS * SLOT_BYTES;
+  const size_t smem7 = B7_SLOTS * SLOT_BYTES;
   static bool attrs_set = false;
   if (!attrs_set) {
-    SCLAP_CUDA(cudaFuncSetAttribute(k_propose_cta<512, CTA_HASH_SLOTS, false>,
+    SCLAP_CUDA(cudaFuncSetAttribute(k_propose_cta<256, B6_SLOTS, false>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem6));
+    SCLAP_CUDA(cudaFuncSetAttribute(k_propose_cta<512, B7_SLOTS, false>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem7));
     attrs_set = true;
   }
 
@@ -971,7 +1058,7 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, int64_
     }
     // global hash scratch for the hub bucket, sized on first need
     int64_t nhub = 0;
-    for (int sub = 0; sub < S; ++sub) nhub += hoff[sub * NB + 7 + 1] - hoff[sub * NB + 7];
+    for (int sub = 0; sub < S; ++sub) nhub += hoff[sub * NB + 8 + 1] - hoff[sub * NB + 8];
     if (nhub > 0 && gcap == 0) {
       // largest degree of the level, read once
       DevBuf<int64_t> dmax(1, s);
@@ -990,11 +1077,35 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, int64_
       const int64_t lbeg = hoff[sub * NB], lend = hoff[(sub + 1) * NB];
       const int64_t cnt = lend - lbeg;
       if (cnt == 0) continue;
-      // family 0: the four lane-group buckets in one launch
+      // The propose launches of a sub-round are independent of one another:
+      // they run on side streams joined back by events, so latency-bound
+      // launches overlap (serial when the timeline profiler is on).
+      const bool fork = !profile().timeline.load(std::memory_order_relaxed);
+      Timed phase{-1, nullptr, nullptr};
+      if (prof) {
+        phase.a = event_from_pool();
+        phase.b = event_from_pool();
+        SCLAP_CUDA(cudaEventRecord(phase.a, s));
+      }
+      cudaEvent_t ev_fork = nullptr;
+      if (fork) {
+        ev_fork = sync_event_get();
+        SCLAP_CUDA(cudaEventRecord(ev_fork, s));
+      }
+      int nside = 0;
+      cudaStream_t joined[NB];
+      auto lane = [&]() -> cudaStream_t {
+        if (!fork) return s;
+        cudaStream_t ss = side_stream(nside);
+        SCLAP_CUDA(cudaStreamWaitEvent(ss, ev_fork, 0));
+        joined[nside++] = ss;
+        return ss;
+      };
+      // family 0: the four small-degree buckets in one launch
       {
         SmallLaunch L{};
         int32_t nb = 0;
-        const int per_block[4] = {64, 32, 16, 8};
+        const int per_block[4] = {256, 256, 16, 8};
         int64_t nodes = 0, arcs_f = 0;
         for (int b = 0; b < 4; ++b) {
           L.beg[b] = hoff[sub * NB + b];
@@ -1006,6 +1117,7 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, int64_
         }
         L.bs[4] = nb;
         if (nb > 0) {
+          cudaStream_t s = lane();
           Timed tm{0, nullptr, nullptr};
           if (prof) {
             tm.a = event_from_pool();
@@ -1024,7 +1136,8 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, int64_
       for (int b = 4; b < NB; ++b) {
         const int64_t bb = hoff[sub * NB + b], bc = hoff[sub * NB + b + 1] - bb;
         if (bc == 0) continue;
-        const int fam = b <= 5 ? 1 : b - 4;
+        cudaStream_t s = lane();
+        const int fam = b <= 5 ? 1 : (b <= 7 ? 2 : 3);
         Timed tm{fam, nullptr, nullptr};
         if (prof) {
           tm.a = event_from_pool();
@@ -1034,11 +1147,13 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, int64_
           pa[fam] += hkarcs[sub * NB + b];
         }
         switch (b) {
-          case 4: k_propose_cta<64, WARP_SMALL_SLOTS, false><<<grid_for(bc, 1, (int64_t)sms * 32), 64, smem4, s>>>(
+          case 4: k_propose_cta<64, B4_SLOTS, false><<<grid_for(bc, 1, (int64_t)sms * 32), 64, smem4, s>>>(
                       a, bb, bc, nullptr, nullptr, 0); SCLAP_NOTE_LAUNCH("k_propose_cta64"); break;
-          case 5: k_propose_cta<128, WARP_HASH_SLOTS, false><<<grid_for(bc, 1, (int64_t)sms * 16), 128, smem5, s>>>(
+          case 5: k_propose_cta<128, B5_SLOTS, false><<<grid_for(bc, 1, (int64_t)sms * 16), 128, smem5, s>>>(
                       a, bb, bc, nullptr, nullptr, 0); SCLAP_NOTE_LAUNCH("k_propose_cta128"); break;
-          case 6: k_propose_cta<512, CTA_HASH_SLOTS, false><<<grid_for(bc, 1, (int64_t)sms * 2), 512, smem6, s>>>(
+          case 6: k_propose_cta<256, B6_SLOTS, false><<<grid_for(bc, 1, (int64_t)sms * 4), 256, smem6, s>>>(
+                      a, bb, bc, nullptr, nullptr, 0); SCLAP_NOTE_LAUNCH("k_propose_cta256"); break;
+          case 7: k_propose_cta<512, B7_SLOTS, false><<<grid_for(bc, 1, (int64_t)sms * 1), 512, smem7, s>>>(
                       a, bb, bc, nullptr, nullptr, 0); SCLAP_NOTE_LAUNCH("k_propose_cta512"); break;
           default: k_propose_cta<512, 1, true><<<(unsigned)std::min<int64_t>(bc, gblocks), 512, 0, s>>>(
                       a, bb, bc, gkeys.p, gvals.p, gcap); SCLAP_NOTE_LAUNCH("k_propose_cta_global"); break;
@@ -1047,6 +1162,19 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, int64_
           SCLAP_CUDA(cudaEventRecord(tm.b, s));
           timed.push_back(tm);
         }
+      }
+      if (fork) {
+        for (int j = 0; j < nside; ++j) {
+          cudaEvent_t ej = sync_event_get();
+          SCLAP_CUDA(cudaEventRecord(ej, joined[j]));
+          SCLAP_CUDA(cudaStreamWaitEvent(s, ej, 0));
+          sync_event_put(ej);
+        }
+        sync_event_put(ev_fork);
+      }
+      if (prof) {
+        SCLAP_CUDA(cudaEventRecord(phase.b, s));
+        timed.push_back(phase);
       }
       const unsigned lg = grid_for(cnt, 256, (int64_t)sms * 16);
       k_resolve<<<lg, 256, 0, s>>>(a, lbeg, cnt); SCLAP_NOTE_LAUNCH("k_resolve");
@@ -1082,6 +1210,11 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, int64_
     for (const Timed& t : timed) {
       float ms = 0.f;
       SCLAP_CUDA(cudaEventElapsedTime(&ms, t.a, t.b));
+      if (t.family < 0) {
+        P.sweep_ms += ms;
+        P.sweeps += 1;
+        continue;
+      }
       P.ms[t.family] += ms;
       P.nlaunch[t.family] += 1;
     }
