@@ -76,6 +76,22 @@ def workload(count, seed):
     return gg.batch_workload(count, seed, processes=procs)
 
 
+def rank_seed(rank):
+    """Each rank partitions its own batch (replicas, weak scaling)."""
+    return rank
+
+
+def max_over_ranks(x, ws, device=None):
+    """Largest value of x over all ranks (a plain float when ws == 1)."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def config_dict(count, ws):
     return {
         "workload": f"batched-{count}: half R-MAT scale U[10,16] ef 8 (0.57,0.19,0.19,0.05), "
@@ -204,7 +220,7 @@ def main():
         reference_arm(args)
         return
     ws, rank, local = dist_env()
-    graphs = workload(args.count, rank)          # each rank its own batch
+    graphs = workload(args.count, rank_seed(rank))
 
     import torch
     import paper_1402_3281_gb300 as P
@@ -250,12 +266,7 @@ def main():
     clocks = sampler.stop()
     P.sclap_profile_enable(False)
     prof = P.sclap_profile_read()
-    elapsed_ms = e0.elapsed_time(e1)
-    if ws > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([elapsed_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(tt.item())
+    elapsed_ms = max_over_ranks(e0.elapsed_time(e1), ws, dev)
     if args.timeline:
         P.sclap_profile_dump()
         P.sclap_profile_timeline(True)
@@ -334,12 +345,7 @@ def main():
         for _ in range(e2e_steps):
             hres = P.sclap_partition_batch(host_items, device=False)
         torch.cuda.synchronize()
-        et = time.perf_counter() - t0
-        if ws > 1:
-            import torch.distributed as dist
-            tt = torch.tensor([et], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            et = float(tt.item())
+        et = max_over_ranks(time.perf_counter() - t0, ws, dev)
         line["e2e"] = {"value": e2e_steps * len(graphs) * ws / et, "unit": "partitions/s",
                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                        "equal_cut": [r.cut for r in hres] == ref_cuts}

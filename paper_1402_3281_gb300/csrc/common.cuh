@@ -301,6 +301,9 @@ void scan_excl_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t s);
 void scan_excl_u8_to_i64(const uint8_t* in, int64_t* out, int64_t n, cudaStream_t s);
 // out[i] = number of keys[0..i) that are >= 0 (occupied hash slots).
 void scan_excl_occupied(const int32_t* keys, int64_t* out, int64_t n, cudaStream_t s);
+// out[i] = number of slots[0..i) that are not ~0 (occupied packed slots).
+void scan_excl_occupied_slots(const unsigned long long* slots, int64_t* out, int64_t n,
+                              cudaStream_t s);
 // largest row length (atomicMax into *out, which the caller zeroes)
 void level_max_degree(const int64_t* row_ptr, int64_t N, int64_t* out, cudaStream_t s);
 // slot id of every node from node offsets

@@ -41,8 +41,7 @@ struct CArgs {
   int32_t* cnw;
   int32_t* inter;          // inter-cluster arcs per coarse node
   const int64_t* tbase;    // table region of each coarse node
-  int32_t* tkeys;
-  unsigned long long* tvals;
+  unsigned long long* tslot;   // (coarse neighbour << 32) | summed weight; ~0 = empty
   int32_t* err;
 };
 
@@ -122,20 +121,33 @@ __global__ void k_table_caps(const int32_t* __restrict__ inter, int64_t Nc, int6
   }
 }
 
+// A slot packs (coarse neighbour, summed weight) in one 64-bit word: the
+// first arc claims an empty slot with one CAS carrying its weight, later arcs
+// add to the low half with one atomicAdd.  A coarse edge weight must fit in
+// int32, so a sum reaching 2^31 is reported (and cannot carry into the key).
 __global__ void __launch_bounds__(256) k_insert(CArgs a, int64_t N) {
   for_inter_arcs(a, N, [&](int32_t cv, int32_t cu, int32_t w) {
     const uint64_t key = cu >= 0 ? (((uint64_t)(uint32_t)cv << 32) | (uint32_t)cu) : ~0ull;
     const unsigned mm = __match_any_sync(0xffffffffu, key);
     const int64_t sum = match_sum(mm, w);
     if (cu < 0 || (threadIdx.x & 31) != __ffs(mm) - 1) return;
+    if (sum > INT32_MAX) { atomicOr(a.err, DERR_W_OVERFLOW); return; }
     const int64_t base = a.tbase[cv];
     const int logcap = ceil_log2(a.tbase[cv + 1] - base);
     const uint32_t mask = (1u << logcap) - 1;
     uint32_t sl = table_slot(cu, logcap);
+    const unsigned long long mine = ((unsigned long long)(uint32_t)cu << 32) | (uint64_t)sum;
     for (uint32_t p = 0; p <= mask; ++p) {
-      const int32_t k = atomicCAS(&a.tkeys[base + sl], -1, cu);
-      if (k == -1 || k == cu) {
-        atomicAdd(&a.tvals[base + sl], (unsigned long long)sum);
+      unsigned long long* slot = &a.tslot[base + sl];
+      unsigned long long cur = *slot;
+      if (cur == ~0ull) {
+        cur = atomicCAS(slot, ~0ull, mine);
+        if (cur == ~0ull) return;
+      }
+      if ((uint32_t)(cur >> 32) == (uint32_t)cu) {
+        const unsigned long long old = atomicAdd(slot, (unsigned long long)sum);
+        if ((old & 0xffffffffull) + (unsigned long long)sum > (unsigned long long)INT32_MAX)
+          atomicOr(a.err, DERR_W_OVERFLOW);
         return;
       }
       sl = (sl + 1) & mask;
@@ -146,17 +158,15 @@ __global__ void __launch_bounds__(256) k_insert(CArgs a, int64_t N) {
 
 // Occupied slots land at their rank among all occupied slots: regions are
 // laid out in coarse-node order, so that rank is the CSR position directly.
-__global__ void k_emit(const int32_t* __restrict__ tkeys, const unsigned long long* __restrict__ tvals,
+__global__ void k_emit(const unsigned long long* __restrict__ tslot,
                        const int64_t* __restrict__ pos, int64_t T, int32_t* __restrict__ ccol,
-                       int32_t* __restrict__ cew, int32_t* err) {
+                       int32_t* __restrict__ cew) {
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < T;
        j += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t K = tkeys[j];
-    if (K < 0) continue;
-    const unsigned long long val = tvals[j];
-    if (val > (unsigned long long)INT32_MAX) atomicOr(err, DERR_W_OVERFLOW);
-    ccol[pos[j]] = K;
-    cew[pos[j]] = (int32_t)min(val, (unsigned long long)INT32_MAX);
+    const unsigned long long x = tslot[j];
+    if (x == ~0ull) continue;
+    ccol[pos[j]] = (int32_t)(x >> 32);
+    cew[pos[j]] = (int32_t)(x & 0xffffffffull);
   }
 }
 
@@ -238,14 +248,12 @@ void contract_build(const LevelView& lv, const std::vector<int64_t>& noff, const
   int64_t T = 0;
   SCLAP_CUDA(cudaMemcpyAsync(&T, tbase.p + Nc, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   stream_sync(s);
-  DevBuf<int32_t> tkeys(std::max<int64_t>(T, 1), s);
-  DevBuf<unsigned long long> tvals(std::max<int64_t>(T, 1), s);
+  DevBuf<unsigned long long> tslot(std::max<int64_t>(T, 1), s);
   DevBuf<int64_t> pos(T + 1, s);
-  tkeys.fill_bytes(0xff);
-  tvals.zero();
-  a.tkeys = tkeys.p; a.tvals = tvals.p;
+  tslot.fill_bytes(0xff);
+  a.tslot = tslot.p;
   if (N > 0 && T > 0) { k_insert<<<wg, 256, 0, s>>>(a, N); SCLAP_NOTE_LAUNCH("k_insert"); }
-  scan_excl_occupied(tkeys.p, pos.p, T, s);
+  scan_excl_occupied_slots(tslot.p, pos.p, T, s);
   out.row_ptr.alloc(Nc + 1, s);
   k_rows<<<grid_for(Nc + 1, 256, (int64_t)sms * 16), 256, 0, s>>>(tbase.p, pos.p, Nc, out.row_ptr.p); SCLAP_NOTE_LAUNCH("k_rows");
   int64_t Mc = 0;
@@ -255,8 +263,8 @@ void contract_build(const LevelView& lv, const std::vector<int64_t>& noff, const
   out.col.alloc(std::max<int64_t>(Mc, 1), s);
   out.ew.alloc(std::max<int64_t>(Mc, 1), s);
   if (T > 0) {
-    k_emit<<<grid_for(T, 256, (int64_t)sms * 32), 256, 0, s>>>(tkeys.p, tvals.p, pos.p, T, out.col.p,
-                                                               out.ew.p, d_err); SCLAP_NOTE_LAUNCH("k_emit");
+    k_emit<<<grid_for(T, 256, (int64_t)sms * 32), 256, 0, s>>>(tslot.p, pos.p, T, out.col.p,
+                                                               out.ew.p); SCLAP_NOTE_LAUNCH("k_emit");
   }
   SCLAP_LAUNCH_CHECK();
   out.gid.alloc(std::max<int64_t>(Nc, 1), s);

@@ -138,7 +138,14 @@ __global__ void __launch_bounds__(GNT) k_ggg(GGGArgs a) {
         const int64_t Wj = Wj_sh;
         if (Wj >= avg) break;
         if (tid == 0) accw_sh = 0;
-        // connected unassigned nodes in id order, longest prefix that fits
+        // connected unassigned nodes in id order, longest prefix that fits;
+        // when all of them fit (the usual step) no ordered scan is needed
+        int64_t cw_all = 0;
+        for (int64_t v = tid; v < n; v += GNT) {
+          const int64_t gv = base + v;
+          if (a.label[gv] < 0 && a.conn[gv] > 0) cw_all += a.nw[gv];
+        }
+        const bool all_fit = Wj + block_sum(cw_all, sh) <= avg;
         int64_t carry_w = 0;
         int32_t carry_c = 0;
         for (int64_t v0 = 0; v0 < n; v0 += GNT) {
@@ -150,9 +157,9 @@ __global__ void __launch_bounds__(GNT) k_ggg(GGGArgs a) {
             cand = a.label[gv] < 0 && a.conn[gv] > 0;
             wt = cand ? a.nw[gv] : 0;
           }
-          int64_t tw;
-          const int64_t iw = block_incl_scan(wt, sh, &tw);
-          const bool adm = cand && (Wj + carry_w + iw <= avg);
+          int64_t tw = 0, iw = wt;
+          if (!all_fit) iw = block_incl_scan(wt, sh, &tw);
+          const bool adm = cand && (all_fit || Wj + carry_w + iw <= avg);
           int64_t tc;
           const int64_t ic = block_incl_scan(adm ? 1 : 0, sh, &tc);
           if (adm) {
@@ -161,7 +168,7 @@ __global__ void __launch_bounds__(GNT) k_ggg(GGGArgs a) {
           }
           carry_w += tw;
           carry_c += (int32_t)tc;
-          if (Wj + carry_w > avg) break;   // no later candidate can fit
+          if (!all_fit && Wj + carry_w > avg) break;   // no later candidate can fit
         }
         __syncthreads();
         if (tid == 0) {

@@ -295,3 +295,32 @@ def test_invalid_inputs_are_rejected():
     # a failing call leaves the library usable
     ok = P.sclap_partition(g.row_ptr, g.col, k=2)
     assert ok.status == 0
+
+
+def test_full_batch_sampled_against_oracle():
+    # The benchmark's launch configuration: the whole 512-graph batch in one
+    # device call; a sample of graphs (largest of each kind, a k = 16 one and
+    # a few spread over the batch) is recomputed by the oracle one by one.
+    import bench
+    graphs = bench.workload(512, 0)
+    items = [dict(row_ptr=dt(g.row_ptr), col=dt(g.col), k=k, eps=eps, seed=0)
+             for g, k, eps in graphs]
+    res = P.sclap_partition_batch(items, device=True)
+    assert all(r.status == 0 for r in res)
+    sizes = [g.n for g, _, _ in graphs]
+    rmat_big = max(range(0, 512, 2), key=lambda i: sizes[i])
+    rgg_big = max(range(1, 512, 2), key=lambda i: sizes[i])
+    k16 = next(i for i, (_, k, _) in enumerate(graphs) if k == 16)
+    sample = sorted({rmat_big, rgg_big, k16, 0, 1, 255, 511})
+    for i in sample:
+        g, k, eps = graphs[i]
+        ref = O.partition(g, k, eps, seed=0)
+        assert res[i].cut == ref.cut, i
+        assert np.array_equal(res[i].block.cpu().numpy(), ref.block), i
+    # every graph balanced, cut equals a recount
+    for i in range(0, 512, 37):
+        g, k, eps = graphs[i]
+        b = res[i].block.cpu().numpy()
+        Lmax, _ = O.bounds(g.n, 1, k, eps)
+        assert np.bincount(b, minlength=k).max() <= Lmax
+        assert O.cut(g, b) == res[i].cut
