@@ -191,6 +191,43 @@ int sclap_refine(int64_t n, const int64_t* row_ptr, const int32_t* col, const in
 int sclap_cut(int64_t n, const int64_t* row_ptr, const int32_t* col, const int32_t* edge_w,
               const int32_t* block, int64_t* cut_out, void* stream);
 
+/* ---- Cut and block weights without device allocation (the paper has no
+ * counterpart: it is a deployment variant of sclap_cut plus the block
+ * weights c(V_i) of Sec. 2.1).
+ *
+ * Every other entry point takes working memory from the CUDA allocator.
+ * This one does not: its working memory is one fixed array in device global
+ * memory, compiled into the library (2 + SCLAP_CUT_STATIC_MAX_K 64-bit words,
+ * about 32 KB per device).  It is meant for callers that cannot allocate
+ * device memory when they ask for the measure, e.g. a process that has
+ * handed nearly all device memory to another allocator and keeps it, or a
+ * latency-sensitive loop that must not enter the allocator, where an
+ * allocation can block or fail.
+ *
+ * Arguments: the graph (device pointers, format as above; col may be NULL
+ * only when row_ptr[n] == 0; node_w / edge_w NULL = unit), block int32[n]
+ * on the device with every id in [0, k), 1 <= k <= min(n,
+ * SCLAP_CUT_STATIC_MAX_K).  Outputs on the HOST: cut_out (int64, may be
+ * NULL) and block_w_out (int64[k], c(V_i) per block, may be NULL).  The
+ * work is ordered on `stream` and the call synchronises it before
+ * returning.  Results equal sclap_cut's cut on the same input.
+ *
+ * Errors: k above SCLAP_CUT_STATIC_MAX_K, k > n, n out of range, NULL
+ * row_ptr or block, or a block id outside [0, k) -> SCLAP_EINVAL; row_ptr
+ * not starting at 0 or decreasing, a neighbour id outside [0, n), a
+ * self-loop or a non-positive weight -> SCLAP_ECSR.  Symmetry is not
+ * checked.
+ *
+ * Set-up: the first call on a device looks up the array's device address
+ * (once per device, with that device current); make that first call before
+ * any stream capture starts.  The array is shared by all callers on a
+ * device: calls that overlap in time (from two host threads, or on two
+ * streams) race on it and must be serialised by the caller. */
+#define SCLAP_CUT_STATIC_MAX_K 4096
+int sclap_cut_static(int64_t n, const int64_t* row_ptr, const int32_t* col,
+                     const int32_t* node_w, const int32_t* edge_w, const int32_t* block,
+                     int32_t k, int64_t* cut_out, int64_t* block_w_out, void* stream);
+
 /* ---- Instrumentation (no counterpart in the paper).  Process-wide
  * counters read by the benchmark: every kernel launch is counted; with
  * profiling enabled, each launch of the LP propose sweep is bracketed by CUDA

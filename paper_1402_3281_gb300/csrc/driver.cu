@@ -870,6 +870,12 @@ void fill_stats(sclap_stats* dst, const GOut& o) {
 
 using namespace sclap;
 
+// Message returned by sclap_last_error() for entry points defined in other
+// translation units.
+namespace sclap {
+void record_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
+}  // namespace sclap
+
 extern "C" {
 
 void sclap_default_config(sclap_config* c) {

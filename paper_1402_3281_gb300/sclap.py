@@ -25,7 +25,7 @@ SYMBOLS = (
     "sclap_default_config", "sclap_error_string", "sclap_last_error", "sclap_partition",
     "sclap_partition_device", "sclap_partition_batch", "sclap_lp_round", "sclap_cluster",
     "sclap_contract", "sclap_initial_partition", "sclap_refine", "sclap_cut",
-    "sclap_profile_enable", "sclap_profile_reset", "sclap_profile_read",
+    "sclap_cut_static", "sclap_profile_enable", "sclap_profile_reset", "sclap_profile_read",
     "sclap_profile_timeline", "sclap_profile_dump",
 )
 
@@ -106,6 +106,7 @@ def _lib():
                                                   p, p, p]),
             "sclap_refine": (C.c_int, [i64, p, p, p, p, i32, i64, u64, i32, i32, p, p, p, p]),
             "sclap_cut": (C.c_int, [i64, p, p, p, p, p, p]),
+            "sclap_cut_static": (C.c_int, [i64, p, p, p, p, p, C.c_int32, p, p, p]),
             "sclap_profile_enable": (None, [C.c_int]),
             "sclap_profile_reset": (None, []),
             "sclap_profile_read": (None, [p]),
@@ -360,3 +361,21 @@ def sclap_cut(row_ptr, col, edge_w, block, stream=None) -> int:
                           _stream(stream))
     _check(rc, "sclap_cut")
     return cut.value
+
+
+# Largest k sclap_cut_static accepts (SCLAP_CUT_STATIC_MAX_K in sclap.h).
+CUT_STATIC_MAX_K = 4096
+
+
+def sclap_cut_static(row_ptr, col, node_w, edge_w, block, k, stream=None):
+    """Cut and block weights (c(V_i), i < k) of ``block`` without any device
+    allocation: the library works in a fixed device array of its own, so
+    k <= CUT_STATIC_MAX_K and calls must not overlap in time.  Device
+    tensors in; returns (cut, numpy int64[k])."""
+    cut = C.c_int64()
+    n = row_ptr.numel() - 1
+    bw = np.zeros(max(int(k), 1), dtype=np.int64)
+    rc = _lib().sclap_cut_static(n, _dp(row_ptr), _dp(col), _dp(node_w), _dp(edge_w), _dp(block),
+                                 int(k), C.byref(cut), _hp(bw), _stream(stream))
+    _check(rc, "sclap_cut_static")
+    return cut.value, bw[:int(k)]

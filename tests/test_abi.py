@@ -62,3 +62,9 @@ def test_oracle_and_library_defaults_agree(lib_path):
     a, b = O.config(), sclap.default_config()
     for f, _ in O.Config._fields_:
         assert getattr(a, f) == getattr(b, f), f
+
+
+def test_static_cut_limit_matches_header():
+    from paper_1402_3281_gb300 import sclap
+    m = re.search(r"#define\s+SCLAP_CUT_STATIC_MAX_K\s+(\d+)", open(HEADER).read())
+    assert m and int(m.group(1)) == sclap.CUT_STATIC_MAX_K
