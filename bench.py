@@ -14,7 +14,8 @@ Extra keys: sclap_edges_per_s (arcs swept by LP / step time),
 plain_partitions_per_s (the same graphs, one call each, equal cuts checked),
 roofline (LP propose sweep vs the measured HBM copy peak), cpu_baseline (the
 oracle's round-synchronous variant on the host), e2e (host buffers through
-the C ABI, copies included), clocks, gpu_launches.
+the C ABI, copies included), serving (p50/p99 latency of Poisson request
+streams through the server), clocks, gpu_launches.
 
 --impl reference times the CPU oracle instead (the reference arm).
 Multi-GPU (torchrun): replicas only -- each rank partitions its own batch
@@ -57,6 +58,7 @@ def parse():
     ap.add_argument("--count", type=int, default=512)
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--timeline", action="store_true",
                     help="after the timed steps, run one step with per-kernel timeline "
@@ -214,6 +216,45 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
+def serve_stream(P, graphs, lam, count, ref_cuts, seed=0):
+    """Open-loop Poisson stream through the server: ``count`` requests (the
+    batch's graphs in order, cycling) with exponential gaps of mean 1/lam s,
+    submitted on time by one thread while the main thread collects results
+    in order.  Latency = submit to completion, measured by the server."""
+    import threading
+    rng = np.random.default_rng(np.random.SeedSequence([0x53525645, seed, count]))
+    gaps = rng.exponential(1.0 / lam, size=count)
+    ids = [None] * count
+    ready = [threading.Event() for _ in range(count)]
+    with P.Server() as srv:
+        def feeder():
+            t_next = time.perf_counter()
+            for i in range(count):
+                t_next += gaps[i]
+                d = t_next - time.perf_counter()
+                if d > 0:
+                    time.sleep(d)
+                g, k, eps = graphs[i % len(graphs)]
+                ids[i] = srv.submit(g.row_ptr, g.col, None, None, k, eps, 0)
+                ready[i].set()
+        th = threading.Thread(target=feeder)
+        t0 = time.perf_counter()
+        th.start()
+        lat, same = [], True
+        for i in range(count):
+            ready[i].wait()
+            r = srv.poll(ids[i], -1)
+            lat.append(r.latency_ms)
+            same &= r.cut == ref_cuts[i % len(graphs)]
+        t1 = time.perf_counter()
+        th.join()
+    lat.sort()
+    q = lambda f: lat[min(len(lat) - 1, int(f * len(lat)))]
+    return {"lambda_per_s": lam, "requests": count, "p50_ms": q(0.50), "p99_ms": q(0.99),
+            "partitions_per_s": count / (t1 - t0), "offered_per_s": count / float(gaps.sum()),
+            "equal_cut": bool(same)}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -349,6 +390,15 @@ def main():
         line["e2e"] = {"value": e2e_steps * len(graphs) * ws / et, "unit": "partitions/s",
                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                        "equal_cut": [r.cut for r in hres] == ref_cuts}
+
+    if rank == 0 and not args.no_serve:
+        runs = [serve_stream(P, graphs, lam, cnt, ref_cuts)
+                for lam, cnt in ((50, 100), (500, len(graphs)), (2000, len(graphs)))]
+        line["serving"] = {
+            "workload": "open-loop Poisson stream of this batch's graphs (in order), "
+                        "host arrays, sclap_server_* with default options (2 workers, "
+                        "120 GiB admission budget, batches up to 512)",
+            "runs": runs}
 
     if rank == 0 and ws == 1:
         rate, done = oracle_rate(graphs, args.cpu_seconds)

@@ -55,7 +55,8 @@ enum {
   SCLAP_EOVERFLOW = -5,   /* a coarse edge weight or c(V) does not fit in int32      */
   SCLAP_EINFEASIBLE = -6, /* blocks stay above Lmax after repair (outputs written)   */
   SCLAP_ETIMEOUT = -7,    /* a bounded device-side wait ran out                      */
-  SCLAP_EINTERNAL = -8    /* internal consistency check failed                       */
+  SCLAP_EINTERNAL = -8,   /* internal consistency check failed                       */
+  SCLAP_PENDING = 1       /* sclap_server_poll: the request has not finished yet     */
 };
 
 /* Tunables.  Defaults (sclap_default_config): the paper's parameters (Sec. 5):
@@ -190,6 +191,58 @@ int sclap_refine(int64_t n, const int64_t* row_ptr, const int32_t* col, const in
 /* Edge cut sum_{i<j} w(E_ij) (Sec. 2.1) of block (int32[n]); cut_out host. */
 int sclap_cut(int64_t n, const int64_t* row_ptr, const int32_t* col, const int32_t* edge_w,
               const int32_t* block, int64_t* cut_out, void* stream);
+
+/* ---- Serving (no counterpart in the paper, which partitions one graph per
+ * run).  A server owns worker threads, each with its own CUDA stream on the
+ * device that was current at creation.  Requests are copied in by
+ * sclap_server_submit and queued in arrival order; a free worker takes the
+ * longest run of queued requests from the front whose estimated device
+ * memory fits in what the budget has left (a request alone is always
+ * admitted when nothing else runs) and partitions them as one batch, as
+ * sclap_partition_batch does.  Requests that arrive while a batch is on the
+ * GPU go into the next batch a worker starts, which overlaps on the device
+ * with those still running.  Each result is bit-identical to what
+ * sclap_partition returns for the same request alone.
+ *
+ * Threads: submit and poll may be called from any threads at once; each
+ * request id must be polled by one thread at a time; no other call may be in
+ * progress on the server when sclap_server_destroy is called. ---- */
+typedef struct sclap_server sclap_server;
+
+typedef struct sclap_server_options {
+  int64_t device_budget_bytes; /* admission budget; 0 = 120 GiB                   */
+  int32_t workers;             /* batches in flight at once (0 = 2, at most 16)   */
+  int32_t max_batch;           /* requests per batch (0 = 512)                    */
+  int64_t linger_us;           /* wait for a partial batch to fill (0 = none)     */
+} sclap_server_options;
+
+/* cfg NULL = defaults; opts NULL = all defaults.  *out receives the server. */
+int sclap_server_create(const sclap_config* cfg, const sclap_server_options* opts,
+                        sclap_server** out);
+
+/* Queue one partition request.  Arrays in HOST memory, format as above; the
+ * server copies them before returning.  *request_id receives the request's
+ * id.  Argument errors (and a request whose estimated device memory exceeds
+ * the whole budget, SCLAP_ENOMEM) are returned here; errors found on the
+ * device (malformed CSR, weight overflow, ...) are returned by the poll. */
+int sclap_server_submit(sclap_server* srv, int64_t n, const int64_t* row_ptr, const int32_t* col,
+                        const int32_t* node_w, const int32_t* edge_w, int32_t k, double eps,
+                        uint64_t seed, int64_t* request_id);
+
+/* Result of a request.  timeout_ms: 0 = do not wait, < 0 = wait until done,
+ * > 0 = wait at most that long.  Returns SCLAP_PENDING if the request has
+ * not finished; otherwise its status (SCLAP_OK, or an error code), writes
+ * the outputs (block_out host int32[n]; cut, max block weight; each may be
+ * NULL) when the status is SCLAP_OK or SCLAP_EINFEASIBLE, writes the time
+ * from submit to completion in milliseconds, and releases the request (its
+ * id is then unknown: SCLAP_EINVAL). */
+int sclap_server_poll(sclap_server* srv, int64_t request_id, int32_t timeout_ms,
+                      int32_t* block_out, int64_t* cut_out, int64_t* max_block_weight_out,
+                      double* latency_ms_out);
+
+/* Stops the workers after their current batches, drops queued requests and
+ * frees the server. */
+int sclap_server_destroy(sclap_server* srv);
 
 /* ---- Cut and block weights without device allocation (the paper has no
  * counterpart: it is a deployment variant of sclap_cut plus the block

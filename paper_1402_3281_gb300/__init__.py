@@ -4,8 +4,8 @@ The compute path is libsclap.so (hand-written CUDA behind the C ABI in
 include/sclap.h); `sclap` is its ctypes binding.
 """
 from .sclap import (  # noqa: F401
-    CUT_STATIC_MAX_K, ECSR, ECUDA, EINFEASIBLE, EINTERNAL, EINVAL, ENOMEM, EOVERFLOW, ETIMEOUT, OK,
-    Config, Result, SclapError, default_config, load, sclap_cluster, sclap_contract, sclap_cut,
+    CUT_STATIC_MAX_K, PENDING, ECSR, ECUDA, EINFEASIBLE, EINTERNAL, EINVAL, ENOMEM, EOVERFLOW, ETIMEOUT, OK,
+    Config, Result, SclapError, Server, Served, default_config, load, sclap_cluster, sclap_contract, sclap_cut,
     sclap_cut_static,
     sclap_initial_partition, sclap_lp_round, sclap_partition, sclap_partition_batch,
     sclap_partition_device, sclap_profile_dump, sclap_profile_enable, sclap_profile_read,

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 SO = os.path.join(HERE, "libsclap.so")
-SOURCES = ["scan.cu", "lp.cu", "contract.cu", "ip.cu", "driver.cu", "noalloc.cu"]
+SOURCES = ["scan.cu", "lp.cu", "contract.cu", "ip.cu", "driver.cu", "noalloc.cu", "server.cu"]
 HEADERS = [os.path.join(CSRC, "common.cuh"), os.path.join(ROOT, "include", "sclap.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC"]

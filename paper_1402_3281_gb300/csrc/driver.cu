@@ -22,16 +22,16 @@ namespace {
 thread_local std::string g_last_error;
 
 void init_pool() {
-  static bool done = false;
-  if (done) return;
-  int dev = 0;
-  cudaGetDevice(&dev);
-  cudaMemPool_t pool;
-  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
-    uint64_t thr = UINT64_MAX;
-    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
-  }
-  done = true;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      uint64_t thr = UINT64_MAX;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+  });
 }
 
 sclap_config resolve_cfg(const sclap_config* c) {
@@ -901,6 +901,7 @@ const char* sclap_error_string(int code) {
     case SCLAP_EINFEASIBLE: return "balance constraint could not be met";
     case SCLAP_ETIMEOUT: return "bounded device wait timed out";
     case SCLAP_EINTERNAL: return "internal error";
+    case SCLAP_PENDING: return "request pending";
     default: return "unknown error code";
   }
 }

@@ -849,11 +849,12 @@ __global__ void __launch_bounds__(256) k_apply(LPArgs a, int64_t lbeg, int64_t c
 
 }  // namespace
 
-// Side streams for concurrent launches (created once, non-blocking).
+// Side streams for concurrent launches (non-blocking, created on first use
+// and kept).  Each host thread has its own, so callers running partitions
+// from several threads at once (the server's workers) do not serialise on
+// one another's side streams.
 cudaStream_t side_stream(int i) {
-  static std::mutex mu;
-  static std::vector<cudaStream_t> pool;
-  std::lock_guard<std::mutex> lk(mu);
+  thread_local std::vector<cudaStream_t> pool;
   while ((int)pool.size() <= i) {
     cudaStream_t st;
     SCLAP_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
@@ -1021,14 +1022,13 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, wgt_t*
   const size_t smem5 = B5_SLOTS * SLOT_BYTES;
   const size_t smem6 = B6_SLOTS * SLOT_BYTES;
   const size_t smem7 = B7_SLOTS * SLOT_BYTES;
-  static bool attrs_set = false;
-  if (!attrs_set) {
+  static std::once_flag attrs_once;
+  std::call_once(attrs_once, [&] {
     SCLAP_CUDA(cudaFuncSetAttribute(k_propose_cta<256, B6_SLOTS, false>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem6));
     SCLAP_CUDA(cudaFuncSetAttribute(k_propose_cta<512, B7_SLOTS, false>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem7));
-    attrs_set = true;
-  }
+  });
 
   for (int r = 0; r < run.rounds; ++r) {
     a.act_cur = track_active ? act_a.p : nullptr;

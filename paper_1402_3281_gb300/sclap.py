@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libsclap.so")
 
 OK, EINVAL, ECSR, ENOMEM, ECUDA, EOVERFLOW, EINFEASIBLE, ETIMEOUT, EINTERNAL = (
     0, -1, -2, -3, -4, -5, -6, -7, -8)
+PENDING = 1
 MODE_CLUSTER, MODE_REFINE = 0, 1
 PH_REFINE, PH_IPREF = 2, 5
 
@@ -25,7 +26,8 @@ SYMBOLS = (
     "sclap_default_config", "sclap_error_string", "sclap_last_error", "sclap_partition",
     "sclap_partition_device", "sclap_partition_batch", "sclap_lp_round", "sclap_cluster",
     "sclap_contract", "sclap_initial_partition", "sclap_refine", "sclap_cut",
-    "sclap_cut_static", "sclap_profile_enable", "sclap_profile_reset", "sclap_profile_read",
+    "sclap_cut_static", "sclap_server_create", "sclap_server_submit", "sclap_server_poll",
+    "sclap_server_destroy", "sclap_profile_enable", "sclap_profile_reset", "sclap_profile_read",
     "sclap_profile_timeline", "sclap_profile_dump",
 )
 
@@ -73,6 +75,11 @@ class Profile(C.Structure):
                     sweeps=self.sweeps)
 
 
+class ServerOptions(C.Structure):
+    _fields_ = [("device_budget_bytes", C.c_int64), ("workers", C.c_int32),
+                ("max_batch", C.c_int32), ("linger_us", C.c_int64)]
+
+
 class GraphDesc(C.Structure):
     _fields_ = [("n", C.c_int64), ("row_ptr", C.c_void_p), ("col", C.c_void_p),
                 ("node_w", C.c_void_p), ("edge_w", C.c_void_p), ("k", C.c_int32),
@@ -107,6 +114,10 @@ def _lib():
             "sclap_refine": (C.c_int, [i64, p, p, p, p, i32, i64, u64, i32, i32, p, p, p, p]),
             "sclap_cut": (C.c_int, [i64, p, p, p, p, p, p]),
             "sclap_cut_static": (C.c_int, [i64, p, p, p, p, p, C.c_int32, p, p, p]),
+            "sclap_server_create": (C.c_int, [p, p, p]),
+            "sclap_server_submit": (C.c_int, [p, i64, p, p, p, p, i32, dbl, u64, p]),
+            "sclap_server_poll": (C.c_int, [p, i64, i32, p, p, p, p]),
+            "sclap_server_destroy": (C.c_int, [p]),
             "sclap_profile_enable": (None, [C.c_int]),
             "sclap_profile_reset": (None, []),
             "sclap_profile_read": (None, [p]),
@@ -379,3 +390,73 @@ def sclap_cut_static(row_ptr, col, node_w, edge_w, block, k, stream=None):
                                  int(k), C.byref(cut), _hp(bw), _stream(stream))
     _check(rc, "sclap_cut_static")
     return cut.value, bw[:int(k)]
+
+
+@dataclass
+class Served:
+    """Result of one served request."""
+    block: np.ndarray
+    cut: int
+    max_block_weight: int
+    status: int
+    latency_ms: float
+
+
+class Server:
+    """Continuous-batching partition server (sclap_server_*).  Requests are
+    host arrays; results come back through poll()."""
+
+    def __init__(self, cfg: Optional[Config] = None, device_budget_bytes: int = 0,
+                 workers: int = 0, max_batch: int = 0, linger_us: int = 0):
+        opts = ServerOptions(int(device_budget_bytes), int(workers), int(max_batch),
+                             int(linger_us))
+        h = C.c_void_p()
+        rc = _lib().sclap_server_create(C.byref(cfg) if cfg else None, C.byref(opts),
+                                        C.byref(h))
+        _check(rc, "sclap_server_create")
+        self._h = h
+        self._n = {}
+
+    def submit(self, row_ptr, col, node_w=None, edge_w=None, k=2, eps=0.03, seed=0) -> int:
+        rp = _np(row_ptr, np.int64)
+        cl = _np(col, np.int32)
+        nw = _np(node_w, np.int32)
+        ew = _np(edge_w, np.int32)
+        rid = C.c_int64()
+        rc = _lib().sclap_server_submit(self._h, rp.size - 1, _hp(rp), _hp(cl), _hp(nw), _hp(ew),
+                                        int(k), float(eps), int(seed) & (2**64 - 1),
+                                        C.byref(rid))
+        _check(rc, "sclap_server_submit")
+        self._n[rid.value] = rp.size - 1
+        return rid.value
+
+    def poll(self, request_id: int, timeout_ms: int = -1) -> Optional[Served]:
+        """The request's result, or None while it is pending.  Raises
+        SclapError for a failed request (and for an unknown id)."""
+        n = self._n.get(request_id, 1)
+        blk = np.empty(max(n, 1), np.int32)
+        cut, mb, lat = C.c_int64(), C.c_int64(), C.c_double()
+        rc = _lib().sclap_server_poll(self._h, int(request_id), int(timeout_ms), _hp(blk),
+                                      C.byref(cut), C.byref(mb), C.byref(lat))
+        if rc == PENDING:
+            return None
+        self._n.pop(request_id, None)
+        _check(rc, "sclap_server_poll", allow=(OK, EINFEASIBLE))
+        return Served(blk[:n], cut.value, mb.value, rc, lat.value)
+
+    def close(self):
+        if self._h:
+            _lib().sclap_server_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):  # pragma: no cover - interpreter shutdown order
+        try:
+            self.close()
+        except Exception:
+            pass
