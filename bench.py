@@ -46,7 +46,7 @@ import graphgen as gg  # noqa: E402
 # admission key (8) written.
 ARC_BYTES = 12
 NODE_BYTES = 44
-FAMILIES = ["lane_groups", "cta64_128", "cta256_512", "cta_global"]
+FAMILIES = ["thread_deg_le16", "warp_deg_le128_cta128", "cta256_512", "cta_global"]
 
 
 def parse():
@@ -336,9 +336,10 @@ def main():
     tr = traffic_for(os.path.join(ROOT, "paper_1402_3281_gb300", "csrc", "lp.cu"))
     nl = prof["sweeps"]
     roofline = {
-        "kernel": "LP propose sweep of a sub-round (k_propose_small + k_propose_cta*, the "
-                  "degree-bucket launches of one colour class, run concurrently); one "
-                  "'launch' = one such phase, timed fork to join with CUDA events",
+        "kernel": "LP propose sweep of a sub-round (k_propose_small, k_propose_warp, "
+                  "k_propose_blk*: the degree-bucket launches of one colour class, run "
+                  "concurrently); one 'launch' = one such phase, timed fork to join with "
+                  "CUDA events",
         "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
         "frac": achieved / peak, "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
         "traffic": (tr[0] * swept / nl if tr and tr[0] else None) if nl else None,

@@ -285,10 +285,10 @@ int sclap_cut_static(int64_t n, const int64_t* row_ptr, const int32_t* col,
  * counters read by the benchmark: every kernel launch is counted; with
  * profiling enabled, each launch of the LP propose sweep is bracketed by CUDA
  * events on its stream and its nodes/arcs are tallied per kernel family
- * (0: lane groups of 4/8/16/32 per node, degree <= 32; 1: CTAs of 64/128
- * threads per node with shared tables, degree <= 512; 2: CTAs of 256/512
- * threads, degree <= 8192; 3: one CTA per node with a global table).  Times
- * are device milliseconds. ---- */
+ * (0: one thread per node, degree <= 16; 1: one warp per node, degree
+ * 17..128, and CTAs of 128 threads per node, degree <= 512; 2: CTAs of
+ * 256/512 threads, degree <= 8192; 3: one CTA per node with a global table).
+ * Times are device milliseconds. ---- */
 typedef struct sclap_profile {
   int64_t kernel_launches;
   int64_t propose_launches[4];

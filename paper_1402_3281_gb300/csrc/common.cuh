@@ -185,10 +185,18 @@ struct Cand {
   uint64_t h;
   int32_t C;  // local label
 };
+// Evaluated with bitwise logic on predicates (no short-circuit), so it
+// compiles to compares and selects rather than branches.
 __device__ __forceinline__ bool cand_better(const Cand& a, const Cand& b) {
-  if (a.conn != b.conn) return a.conn > b.conn;
-  if (a.h != b.h) return a.h < b.h;
-  return a.C < b.C;
+  const bool gt = a.conn > b.conn, eq = a.conn == b.conn;
+  return gt | (eq & ((a.h < b.h) | ((a.h == b.h) & (a.C < b.C))));
+}
+__device__ __forceinline__ Cand cand_pick(bool take, const Cand& x, const Cand& c) {
+  Cand r;
+  r.conn = take ? x.conn : c.conn;
+  r.h = take ? x.h : c.h;
+  r.C = take ? x.C : c.C;
+  return r;
 }
 __device__ __forceinline__ Cand shfl_xor_cand(const Cand& c, int off, int width = 32) {
   Cand o;
@@ -198,13 +206,15 @@ __device__ __forceinline__ Cand shfl_xor_cand(const Cand& c, int off, int width 
   return o;
 }
 __device__ __forceinline__ Cand warp_best(Cand c, int width = 32) {
+#pragma unroll
   for (int off = width / 2; off > 0; off >>= 1) {
-    Cand o = shfl_xor_cand(c, off, width);
-    if (cand_better(o, c)) c = o;
+    const Cand o = shfl_xor_cand(c, off, width);
+    c = cand_pick(cand_better(o, c), o, c);
   }
   return c;
 }
 __device__ __forceinline__ long long warp_max_ll(long long x, int width = 32) {
+#pragma unroll
   for (int off = width / 2; off > 0; off >>= 1) {
     long long o = __shfl_xor_sync(0xffffffffu, x, off, width);
     x = o > x ? o : x;

@@ -127,11 +127,8 @@ __global__ void k_table_caps(const int32_t* __restrict__ inter, int64_t Nc, int6
 // int32, so a sum reaching 2^31 is reported (and cannot carry into the key).
 __global__ void __launch_bounds__(256) k_insert(CArgs a, int64_t N) {
   for_inter_arcs(a, N, [&](int32_t cv, int32_t cu, int32_t w) {
-    const uint64_t key = cu >= 0 ? (((uint64_t)(uint32_t)cv << 32) | (uint32_t)cu) : ~0ull;
-    const unsigned mm = __match_any_sync(0xffffffffu, key);
-    const int64_t sum = match_sum(mm, w);
-    if (cu < 0 || (threadIdx.x & 31) != __ffs(mm) - 1) return;
-    if (sum > INT32_MAX) { atomicOr(a.err, DERR_W_OVERFLOW); return; }
+    if (cu < 0) return;
+    const int64_t sum = w;
     const int64_t base = a.tbase[cv];
     const int logcap = ceil_log2(a.tbase[cv + 1] - base);
     const uint32_t mask = (1u << logcap) - 1;

@@ -254,47 +254,57 @@ __global__ void k_bucket_offsets(LPArgs a, int nkeys) {
 }
 
 // ------------------------------------------------------------- propose
-// Degrees <= G: one group of G lanes per node, one arc per lane; equal labels
-// are merged with a warp match and their weights summed.
-template <int G>
-__device__ __forceinline__ void propose_small(const LPArgs& a, int64_t lbeg, int64_t cnt,
-                                              int64_t blk, int64_t nblk) {
-  constexpr int GPW = 32 / G;
-  const int lane = threadIdx.x & 31, gw = lane / G, gl = lane % G;
-  const int64_t warp = (blk * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = (nblk * blockDim.x) >> 5;
-  for (int64_t t0 = warp * GPW; t0 < cnt; t0 += nwarps * GPW) {
-    const int64_t li = t0 + gw;
-    const bool has = li < cnt;
-    const int64_t i = lbeg + li;
-    NodeCtx c{};
-    int32_t C = -1, w = 0;
-    bool valid = false;
-    if (has) {
-      c = load_node(a, i);
-      if (gl < c.re - c.rs) {
-        valid = true;
-        const int32_t u = a.col[c.rs + gl];
-        w = a.ew[c.rs + gl];
-        C = a.label[u];
+// Degrees <= MAXD (4, 8 or 16): one thread per node, the whole row in
+// registers.  The row's (label, weight) pairs are sorted by label with a
+// bitonic network (compile-time indices, so the arrays stay in registers);
+// equal labels then form runs, the run sums are the connections, and the
+// last entry of each run is that label's candidate.  No cross-lane
+// operation is involved, and apart from the loop every step is predicated
+// loads, compares and selects.  Unused entries carry label INT32_MAX and
+// sort to the end.  When the row's total weight exceeds int32 (heavy coarse
+// edges) the run sums are kept in 64 bits.
+template <int MAXD, typename SumT>
+__device__ __forceinline__ void sorted_row_best(const LPArgs& a, const NodeCtx& c, int32_t (&C)[MAXD],
+                                                int32_t (&w)[MAXD], long long& oc, Cand& best) {
+#pragma unroll
+  for (int k = 2; k <= MAXD; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+#pragma unroll
+      for (int i = 0; i < MAXD; ++i) {
+        const int l = i ^ j;
+        if (l > i) {
+          const bool up = (i & k) == 0;
+          const bool sw = up ? (C[i] > C[l]) : (C[i] < C[l]);
+          const int32_t c0 = sw ? C[l] : C[i], c1 = sw ? C[i] : C[l];
+          const int32_t w0 = sw ? w[l] : w[i], w1 = sw ? w[i] : w[l];
+          C[i] = c0; C[l] = c1; w[i] = w0; w[l] = w1;
+        }
       }
     }
-    const uint64_t mk = ((uint64_t)gw << 32) | (uint32_t)C;
-    const unsigned mm = __match_any_sync(0xffffffffu, mk);
-    const int64_t conn = match_sum(mm, w);
-    const bool leader = lane == __ffs(mm) - 1;
-    long long oc = (valid && leader && C == c.own) ? conn : 0;
-    oc = warp_max_ll(oc, G);
-    Cand cd{-1, 0, 0};
-    if (valid && leader && C != c.own && (int64_t)a.W[C] + c.cv <= c.bound) cd = make_cand(c, C, conn);
-    cd = warp_best(cd, G);
-    if (has && gl == 0) write_prop(a, i, c, cd, oc, false);
+  }
+  SumT run[MAXD];
+  bool end[MAXD];
+#pragma unroll
+  for (int j = 0; j < MAXD; ++j) {
+    const SumT prev = j > 0 ? run[j - 1] : (SumT)0;
+    run[j] = (j > 0 && C[j] == C[j - 1]) ? prev + (SumT)w[j] : (SumT)w[j];
+    end[j] = C[j] != INT32_MAX && (j == MAXD - 1 || C[j] != C[j + 1]);
+  }
+  int32_t Wl[MAXD];
+#pragma unroll
+  for (int j = 0; j < MAXD; ++j) Wl[j] = end[j] & (C[j] != c.own) ? a.W[C[j]] : 0;
+#pragma unroll
+  for (int j = 0; j < MAXD; ++j) {
+    const bool own = end[j] & (C[j] == c.own);
+    oc = own ? (long long)run[j] : oc;
+    const bool elig = end[j] & (C[j] != c.own) & ((int64_t)Wl[j] + c.cv <= c.bound);
+    const int32_t Cl = (int32_t)(C[j] - c.loff);
+    const Cand x{(int64_t)run[j], mix64(c.hv ^ (uint64_t)(uint32_t)Cl), Cl};
+    best = cand_pick(elig & cand_better(x, best), x, best);
   }
 }
 
-// Degrees <= MAXD (4 or 8): one thread per node.  The row sits in registers
-// (unrolled, predicated loads); equal labels are merged by an O(d^2)
-// comparison and the best candidate is chosen without cross-lane traffic.
 template <int MAXD>
 __device__ __forceinline__ void propose_thread(const LPArgs& a, int64_t lbeg, int64_t cnt,
                                                int64_t blk, int64_t nblk) {
@@ -303,51 +313,36 @@ __device__ __forceinline__ void propose_thread(const LPArgs& a, int64_t lbeg, in
     const NodeCtx c = load_node(a, i);
     const int deg = (int)(c.re - c.rs);
     int32_t C[MAXD], w[MAXD];
+    int64_t total = 0;
 #pragma unroll
     for (int j = 0; j < MAXD; ++j) {
-      C[j] = -1;
-      w[j] = 0;
-      if (j < deg) {
-        w[j] = a.ew[c.rs + j];
-        C[j] = a.label[a.col[c.rs + j]];
-      }
+      const bool in = j < deg;
+      w[j] = in ? a.ew[c.rs + j] : 0;
+      C[j] = in ? a.col[c.rs + j] : -1;
+      total += w[j];
     }
+#pragma unroll
+    for (int j = 0; j < MAXD; ++j) C[j] = C[j] >= 0 ? a.label[C[j]] : INT32_MAX;
     long long oc = 0;
     Cand best{-1, 0, 0};
-#pragma unroll
-    for (int j = 0; j < MAXD; ++j) {
-      if (C[j] < 0) continue;
-      bool first = true;
-      int64_t conn = w[j];
-#pragma unroll
-      for (int l = 0; l < MAXD; ++l) {
-        if (l == j || C[l] != C[j]) continue;
-        if (l < j) first = false;
-        conn += w[l];
-      }
-      if (!first) continue;
-      if (C[j] == c.own) { oc = conn; continue; }
-      if ((int64_t)a.W[C[j]] + c.cv > c.bound) continue;
-      const Cand x = make_cand(c, C[j], conn);
-      if (best.conn < 0 || cand_better(x, best)) best = x;
-    }
+    if (total <= INT32_MAX) sorted_row_best<MAXD, int32_t>(a, c, C, w, oc, best);
+    else sorted_row_best<MAXD, int64_t>(a, c, C, w, oc, best);
     write_prop(a, i, c, best, oc, false);
   }
 }
 
-// The four small-degree buckets of one sub-round in one launch: block ranges
-// [bs[j], bs[j+1]) serve bucket j (one thread per node for degree <= 8,
-// lane groups of 16 / 32 above).
+// The small-degree buckets of one sub-round in one launch: block ranges
+// [bs[j], bs[j+1]) serve bucket j (degree <= 4, <= 8, <= 16), one thread per
+// node.
 struct SmallLaunch {
-  int64_t beg[4], cnt[4];
-  int32_t bs[5];
+  int64_t beg[3], cnt[3];
+  int32_t bs[4];
 };
-__global__ void __launch_bounds__(256) k_propose_small(LPArgs a, SmallLaunch L) {
+__global__ void __launch_bounds__(256, 4) k_propose_small(LPArgs a, SmallLaunch L) {
   const int32_t b = blockIdx.x;
   if (b < L.bs[1]) propose_thread<4>(a, L.beg[0], L.cnt[0], b - L.bs[0], L.bs[1] - L.bs[0]);
   else if (b < L.bs[2]) propose_thread<8>(a, L.beg[1], L.cnt[1], b - L.bs[1], L.bs[2] - L.bs[1]);
-  else if (b < L.bs[3]) propose_small<16>(a, L.beg[2], L.cnt[2], b - L.bs[2], L.bs[3] - L.bs[2]);
-  else propose_small<32>(a, L.beg[3], L.cnt[3], b - L.bs[3], L.bs[4] - L.bs[3]);
+  else propose_thread<16>(a, L.beg[2], L.cnt[2], b - L.bs[2], L.bs[3] - L.bs[2]);
 }
 
 // Open-addressing accumulation (linear probing, bounded).
@@ -380,8 +375,7 @@ __device__ __forceinline__ int64_t table_get(const int32_t* keys, const unsigned
 }
 
 // Adds the arcs [rs, re) of a node into the table; the whole warp calls it
-// with the same range (lanes stride over the arcs; equal labels within one
-// stride are pre-merged by a warp match).
+// with the same range (lanes stride over the arcs, one atomic per arc).
 __device__ __forceinline__ void accumulate_arcs(const LPArgs& a, int64_t rs, int64_t re,
                                                 int first_lane, int lanes, int32_t* keys,
                                                 unsigned long long* vals, int logcap) {
@@ -394,9 +388,7 @@ __device__ __forceinline__ void accumulate_arcs(const LPArgs& a, int64_t rs, int
       w = a.ew[e];
       C = a.label[a.col[e]];
     }
-    const unsigned mm = __match_any_sync(0xffffffffu, C);
-    const int64_t sum = match_sum(mm, w);
-    if (valid && lane == __ffs(mm) - 1) table_add(keys, vals, logcap, C, sum, a.err);
+    if (valid) table_add(keys, vals, logcap, C, w, a.err);
   }
 }
 
@@ -414,9 +406,7 @@ __device__ __forceinline__ void accumulate_direct(const LPArgs& a, int64_t rs, i
       w = a.ew[e];
       b = (int32_t)(a.label[a.col[e]] - loff);
     }
-    const unsigned mm = __match_any_sync(0xffffffffu, b);
-    const int64_t sum = match_sum(mm, w);
-    if (valid && lane == __ffs(mm) - 1) atomicAdd(&vals[b], (unsigned long long)sum);
+    if (valid) atomicAdd(&vals[b], (unsigned long long)w);
   }
 }
 
@@ -513,6 +503,256 @@ __global__ void __launch_bounds__(NT) k_propose_cta(LPArgs a, int64_t lbeg, int6
     }
     block_reduce<NT>(oc, cd, sh_oc, sh_cd);
     if (tid == 0) write_prop(a, i, c, cd, oc, ov);
+    __syncthreads();
+  }
+}
+
+// Degrees 17..128 (and nodes of overloaded blocks up to that degree): one
+// warp per node, eight warps per CTA, each with a private WCAP-slot table in
+// shared memory, so no CTA barrier is needed between nodes.  The row (at most
+// four arcs per lane) is loaded up front and its labels gathered together;
+// every arc is then added to its label's slot by shared-memory atomics (no
+// warp-level pre-merge: reductions over per-label lane masks serialise per
+// distinct label).  The lane that created a key evaluates it and later
+// clears its slot, so the work per node follows the degree, not the table
+// size.
+constexpr int WARP_MAXDEG = B4_MAXDEG;
+constexpr int WCAP = 2 * WARP_MAXDEG;        // at most half full
+constexpr int WLOG = 8;                      // log2(WCAP)
+constexpr int WPC = 8;                       // warps per CTA
+static_assert((1 << WLOG) == WCAP, "WCAP must be 2^WLOG");
+
+__global__ void __launch_bounds__(WPC * 32) k_propose_warp(LPArgs a, int64_t lbeg, int64_t cnt) {
+  __shared__ unsigned long long sh_vals[WPC][WCAP];
+  __shared__ int32_t sh_keys[WPC][WCAP];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  unsigned long long* vals = sh_vals[wib];
+  int32_t* keys = sh_keys[wib];
+  for (int j = lane; j < WCAP; j += 32) { keys[j] = -1; vals[j] = 0; }
+  __syncwarp();
+  const int64_t nwarps = (int64_t)gridDim.x * WPC;
+  for (int64_t li = (int64_t)blockIdx.x * WPC + wib; li < cnt; li += nwarps) {
+    const int64_t i = lbeg + li;
+    const NodeCtx c = load_node(a, i);
+    const bool ov = a.mode != MODE_CLUSTER && a.W[c.own] > c.bound;
+    const int32_t nl = a.mode != MODE_CLUSTER ? a.nlab[c.slot] : 0;
+    const bool direct = a.mode != MODE_CLUSTER && nl <= WCAP;
+    const int deg = (int)(c.re - c.rs);
+    int32_t C[4], w[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const bool in = t * 32 + lane < deg;
+      const int64_t e = c.rs + t * 32 + lane;
+      w[t] = in ? a.ew[e] : 0;
+      C[t] = in ? a.col[e] : -1;
+    }
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+      if (C[t] >= 0) C[t] = a.label[C[t]];
+    // keys: local block id (direct) or label (hashed)
+    int slot[4] = {0, 0, 0, 0};
+    unsigned created = 0;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      if (t * 32 >= deg) break;
+      const int32_t key = C[t] < 0 ? -1 : (direct ? (int32_t)(C[t] - c.loff) : C[t]);
+      if (key < 0) continue;
+      if (direct) {
+        atomicAdd(&vals[key], (unsigned long long)w[t]);
+      } else {
+        uint32_t s = table_slot(key, WLOG);
+        for (int p = 0; p < WCAP; ++p) {
+          const int32_t prev = atomicCAS(&keys[s], -1, key);
+          if (prev == -1 || prev == key) {
+            if (prev == -1) { created |= 1u << t; slot[t] = (int)s; }
+            atomicAdd(&vals[s], (unsigned long long)w[t]);
+            break;
+          }
+          s = (s + 1) & (WCAP - 1);
+          if (p == WCAP - 1) atomicOr(a.err, DERR_HASH_FULL);
+        }
+      }
+    }
+    __syncwarp();
+    long long oc = 0;
+    bool has_oc = false;
+    Cand cd{-1, 0, 0};
+    if (direct) {
+      const int32_t own_l = (int32_t)(c.own - c.loff);
+      for (int32_t b = lane; b < nl; b += 32) {
+        const int64_t conn = (int64_t)vals[b];
+        if (b == own_l) { oc = conn; has_oc = true; continue; }
+        if (conn == 0 && !ov) continue;
+        const int32_t Cb = (int32_t)(c.loff + b);
+        if ((int64_t)a.W[Cb] + c.cv > c.bound) continue;
+        const Cand x = make_cand(c, Cb, conn);
+        if (cd.conn < 0 || cand_better(x, cd)) cd = x;
+      }
+      __syncwarp();
+      for (int32_t b = lane; b < nl; b += 32) vals[b] = 0;
+    } else {
+      int32_t Wk[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+        Wk[t] = ((created >> t) & 1u) && C[t] != c.own && !ov ? a.W[C[t]] : 0;
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        if (!((created >> t) & 1u)) continue;
+        const int64_t conn = (int64_t)vals[slot[t]];
+        if (C[t] == c.own) { oc = conn; has_oc = true; continue; }
+        if (ov || (int64_t)Wk[t] + c.cv > c.bound) continue;
+        const Cand x = make_cand(c, C[t], conn);
+        if (cd.conn < 0 || cand_better(x, cd)) cd = x;
+      }
+      if (ov) {
+        // an overloaded node may move to any block that fits, connected or not
+        for (int32_t b = lane; b < nl; b += 32) {
+          const int32_t Cb = (int32_t)(c.loff + b);
+          if (Cb == c.own || (int64_t)a.W[Cb] + c.cv > c.bound) continue;
+          const Cand x = make_cand(c, Cb, table_get(keys, vals, WLOG, Cb));
+          if (cd.conn < 0 || cand_better(x, cd)) cd = x;
+        }
+      }
+      __syncwarp();
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+        if ((created >> t) & 1u) { keys[slot[t]] = -1; vals[slot[t]] = 0; }
+    }
+    const unsigned om = __ballot_sync(0xffffffffu, has_oc);
+    oc = om ? __shfl_sync(0xffffffffu, oc, __ffs(om) - 1) : 0;
+    cd = warp_best(cd);
+    if (lane == 0) write_prop(a, i, c, cd, oc, ov);
+    __syncwarp();
+  }
+}
+
+// Degrees 129..8192 (buckets 5-7): one CTA of NT threads per node, a
+// SLOTS-slot table in dynamic shared memory (keys, sums) plus a list of the
+// slots created for the current node.  The row is read four strides at a
+// time (loads first, then label gathers, then inserts), candidates are the
+// created slots only, and only those slots are cleared afterwards.
+template <int SLOTS>
+constexpr size_t blk_smem_bytes() {
+  return (size_t)SLOTS * (sizeof(unsigned long long) + sizeof(int32_t)) +
+         (size_t)(SLOTS / 2) * sizeof(int32_t);
+}
+
+template <int NT, int SLOTS>
+__global__ void __launch_bounds__(NT) k_propose_blk(LPArgs a, int64_t lbeg, int64_t cnt) {
+  extern __shared__ unsigned long long smem_u64[];
+  __shared__ long long sh_oc[NT / 32];
+  __shared__ Cand sh_cd[NT / 32];
+  __shared__ int sh_nc;
+  unsigned long long* vals = smem_u64;
+  int32_t* keys = reinterpret_cast<int32_t*>(smem_u64 + SLOTS);
+  int32_t* clist = keys + SLOTS;
+  const int tid = threadIdx.x, lane = tid & 31;
+  for (int j = tid; j < SLOTS; j += NT) { keys[j] = -1; vals[j] = 0; }
+  if (tid == 0) sh_nc = 0;
+  __syncthreads();
+  for (int64_t li = blockIdx.x; li < cnt; li += gridDim.x) {
+    const int64_t i = lbeg + li;
+    const NodeCtx c = load_node(a, i);
+    const bool ov = a.mode != MODE_CLUSTER && a.W[c.own] > c.bound;
+    const int32_t nl = a.mode != MODE_CLUSTER ? a.nlab[c.slot] : 0;
+    const bool direct = a.mode != MODE_CLUSTER && nl <= SLOTS;
+    const int64_t deg = c.re - c.rs;
+    const int logcap = ceil_log2(max64(2 * deg, 32));
+    const uint32_t mask = (1u << logcap) - 1;
+    for (int64_t e0 = c.rs; e0 < c.re; e0 += 4 * NT) {
+      int32_t C[4], w[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t e = e0 + (int64_t)u * NT + tid;
+        const bool in = e < c.re;
+        w[u] = in ? a.ew[e] : 0;
+        C[u] = in ? a.col[e] : -1;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (C[u] >= 0) C[u] = a.label[C[u]];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (e0 + (int64_t)u * NT >= c.re) break;
+        const int32_t key = C[u] < 0 ? -1 : (direct ? (int32_t)(C[u] - c.loff) : C[u]);
+        const int64_t sum = w[u];
+        bool cr = false;
+        uint32_t s = 0;
+        if (key >= 0) {
+          if (direct) {
+            atomicAdd(&vals[key], (unsigned long long)sum);
+          } else {
+            s = table_slot(key, logcap);
+            for (uint32_t p = 0; p <= mask; ++p) {
+              const int32_t prev = atomicCAS(&keys[s], -1, key);
+              if (prev == -1 || prev == key) {
+                cr = prev == -1;
+                atomicAdd(&vals[s], (unsigned long long)sum);
+                break;
+              }
+              s = (s + 1) & mask;
+              if (p == mask) atomicOr(a.err, DERR_HASH_FULL);
+            }
+          }
+        }
+        // one list reservation per warp for the slots it created
+        const unsigned cm = __ballot_sync(0xffffffffu, cr);
+        if (cm) {
+          const int first = __ffs(cm) - 1;
+          int base = 0;
+          if (lane == first) base = atomicAdd(&sh_nc, __popc(cm));
+          base = __shfl_sync(0xffffffffu, base, first);
+          if (cr) clist[base + __popc(cm & ((1u << lane) - 1))] = (int32_t)s;
+        }
+      }
+    }
+    __syncthreads();
+    long long oc = 0;
+    Cand cd{-1, 0, 0};
+    if (direct) {
+      const int32_t own_l = (int32_t)(c.own - c.loff);
+      for (int32_t b = tid; b < nl; b += NT) {
+        const int64_t conn = (int64_t)vals[b];
+        if (b == own_l) { oc = conn; continue; }
+        if (conn == 0 && !ov) continue;
+        const int32_t Cb = (int32_t)(c.loff + b);
+        if ((int64_t)a.W[Cb] + c.cv > c.bound) continue;
+        Cand x = make_cand(c, Cb, conn);
+        if (cd.conn < 0 || cand_better(x, cd)) cd = x;
+      }
+      __syncthreads();
+      for (int32_t b = tid; b < nl; b += NT) vals[b] = 0;
+    } else {
+      const int nc = sh_nc;
+      for (int j = tid; j < nc; j += NT) {
+        const int32_t s = clist[j];
+        const int32_t K = keys[s];
+        const int64_t conn = (int64_t)vals[s];
+        if (K == c.own) { oc = conn; continue; }
+        if (ov || (int64_t)a.W[K] + c.cv > c.bound) continue;
+        Cand x = make_cand(c, K, conn);
+        if (cd.conn < 0 || cand_better(x, cd)) cd = x;
+      }
+      if (ov) {
+        for (int32_t b = tid; b < nl; b += NT) {
+          const int32_t Cb = (int32_t)(c.loff + b);
+          if (Cb == c.own || (int64_t)a.W[Cb] + c.cv > c.bound) continue;
+          Cand x = make_cand(c, Cb, table_get(keys, vals, logcap, Cb));
+          if (cd.conn < 0 || cand_better(x, cd)) cd = x;
+        }
+      }
+      __syncthreads();
+      for (int j = tid; j < nc; j += NT) {
+        const int32_t s = clist[j];
+        keys[s] = -1;
+        vals[s] = 0;
+      }
+    }
+    block_reduce<NT>(oc, cd, sh_oc, sh_cd);
+    if (tid == 0) {
+      write_prop(a, i, c, cd, oc, ov);
+      sh_nc = 0;
+    }
     __syncthreads();
   }
 }
@@ -1017,16 +1257,14 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, wgt_t*
   int32_t hflags = 0;
   int64_t arcs_total = 0;
   const unsigned small_grid = (unsigned)(sms * 8);
-  constexpr size_t SLOT_BYTES = sizeof(unsigned long long) + sizeof(int32_t);
-  const size_t smem4 = B4_SLOTS * SLOT_BYTES;
-  const size_t smem5 = B5_SLOTS * SLOT_BYTES;
-  const size_t smem6 = B6_SLOTS * SLOT_BYTES;
-  const size_t smem7 = B7_SLOTS * SLOT_BYTES;
+  constexpr size_t smem5 = blk_smem_bytes<B5_SLOTS>();
+  constexpr size_t smem6 = blk_smem_bytes<B6_SLOTS>();
+  constexpr size_t smem7 = blk_smem_bytes<B7_SLOTS>();
   static std::once_flag attrs_once;
   std::call_once(attrs_once, [&] {
-    SCLAP_CUDA(cudaFuncSetAttribute(k_propose_cta<256, B6_SLOTS, false>,
+    SCLAP_CUDA(cudaFuncSetAttribute(k_propose_blk<256, B6_SLOTS>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem6));
-    SCLAP_CUDA(cudaFuncSetAttribute(k_propose_cta<512, B7_SLOTS, false>,
+    SCLAP_CUDA(cudaFuncSetAttribute(k_propose_blk<512, B7_SLOTS>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem7));
   });
 
@@ -1101,21 +1339,21 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, wgt_t*
         joined[nside++] = ss;
         return ss;
       };
-      // family 0: the four small-degree buckets in one launch
+      // family 0: degrees <= 16, one thread per node, three buckets in one
+      // launch
       {
         SmallLaunch L{};
         int32_t nb = 0;
-        const int per_block[4] = {256, 256, 16, 8};
         int64_t nodes = 0, arcs_f = 0;
-        for (int b = 0; b < 4; ++b) {
+        for (int b = 0; b < 3; ++b) {
           L.beg[b] = hoff[sub * NB + b];
           L.cnt[b] = hoff[sub * NB + b + 1] - L.beg[b];
           L.bs[b] = nb;
-          if (L.cnt[b] > 0) nb += (int32_t)grid_for(L.cnt[b], per_block[b], small_grid);
+          if (L.cnt[b] > 0) nb += (int32_t)grid_for(L.cnt[b], 256, small_grid);
           nodes += L.cnt[b];
           if (prof) arcs_f += hkarcs[sub * NB + b];
         }
-        L.bs[4] = nb;
+        L.bs[3] = nb;
         if (nb > 0) {
           cudaStream_t s = lane();
           Timed tm{0, nullptr, nullptr};
@@ -1133,28 +1371,34 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, wgt_t*
           }
         }
       }
-      for (int b = 4; b < NB; ++b) {
-        const int64_t bb = hoff[sub * NB + b], bc = hoff[sub * NB + b + 1] - bb;
+      // families 1-3: buckets 3 and 4 (degrees 17..128, adjacent in the list)
+      // share the warp-per-node launch; buckets 5.. get one launch each
+      for (int b = 3; b < NB; ++b) {
+        const int64_t bb = hoff[sub * NB + b];
+        const int bend = b == 3 ? 5 : b + 1;
+        const int64_t bc = hoff[sub * NB + bend] - bb;
+        const int bcase = b;
+        if (b == 3) b = 4;
         if (bc == 0) continue;
         cudaStream_t s = lane();
-        const int fam = b <= 5 ? 1 : (b <= 7 ? 2 : 3);
+        const int fam = bcase <= 5 ? 1 : (bcase <= 7 ? 2 : 3);
         Timed tm{fam, nullptr, nullptr};
         if (prof) {
           tm.a = event_from_pool();
           tm.b = event_from_pool();
           SCLAP_CUDA(cudaEventRecord(tm.a, s));
           pn[fam] += bc;
-          pa[fam] += hkarcs[sub * NB + b];
+          for (int q = bcase; q < bend; ++q) pa[fam] += hkarcs[sub * NB + q];
         }
-        switch (b) {
-          case 4: k_propose_cta<64, B4_SLOTS, false><<<grid_for(bc, 1, (int64_t)sms * 32), 64, smem4, s>>>(
-                      a, bb, bc, nullptr, nullptr, 0); SCLAP_NOTE_LAUNCH("k_propose_cta64"); break;
-          case 5: k_propose_cta<128, B5_SLOTS, false><<<grid_for(bc, 1, (int64_t)sms * 16), 128, smem5, s>>>(
-                      a, bb, bc, nullptr, nullptr, 0); SCLAP_NOTE_LAUNCH("k_propose_cta128"); break;
-          case 6: k_propose_cta<256, B6_SLOTS, false><<<grid_for(bc, 1, (int64_t)sms * 4), 256, smem6, s>>>(
-                      a, bb, bc, nullptr, nullptr, 0); SCLAP_NOTE_LAUNCH("k_propose_cta256"); break;
-          case 7: k_propose_cta<512, B7_SLOTS, false><<<grid_for(bc, 1, (int64_t)sms * 1), 512, smem7, s>>>(
-                      a, bb, bc, nullptr, nullptr, 0); SCLAP_NOTE_LAUNCH("k_propose_cta512"); break;
+        switch (bcase) {
+          case 3: k_propose_warp<<<grid_for(bc, WPC, (int64_t)sms * 8), WPC * 32, 0, s>>>(
+                      a, bb, bc); SCLAP_NOTE_LAUNCH("k_propose_warp"); break;
+          case 5: k_propose_blk<128, B5_SLOTS><<<grid_for(bc, 1, (int64_t)sms * 16), 128, smem5, s>>>(
+                      a, bb, bc); SCLAP_NOTE_LAUNCH("k_propose_blk128"); break;
+          case 6: k_propose_blk<256, B6_SLOTS><<<grid_for(bc, 1, (int64_t)sms * 4), 256, smem6, s>>>(
+                      a, bb, bc); SCLAP_NOTE_LAUNCH("k_propose_blk256"); break;
+          case 7: k_propose_blk<512, B7_SLOTS><<<grid_for(bc, 1, (int64_t)sms * 1), 512, smem7, s>>>(
+                      a, bb, bc); SCLAP_NOTE_LAUNCH("k_propose_blk512"); break;
           default: k_propose_cta<512, 1, true><<<(unsigned)std::min<int64_t>(bc, gblocks), 512, 0, s>>>(
                       a, bb, bc, gkeys.p, gvals.p, gcap); SCLAP_NOTE_LAUNCH("k_propose_cta_global"); break;
         }
