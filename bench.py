@@ -60,6 +60,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--phases", action="store_true",
+                    help="print per-sub-round propose/admission times grouped by run kind "
+                         "and round (stderr)")
     ap.add_argument("--timeline", action="store_true",
                     help="after the timed steps, run one step with per-kernel timeline "
                          "events and print the table to stderr")
@@ -216,6 +219,27 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
+KINDS = {1: "cluster", 2: "refine", 3: "ip-trial", 5: "ip-refine", 6: "repair"}
+
+
+def print_phases(ph, steps):
+    """Per-step totals of the sub-round records, by run kind and round."""
+    if ph.size == 0:
+        return
+    print(f"sub-rounds per step: {len(ph) / steps:.0f}", file=sys.stderr)
+    print(f"{'kind':10s} {'round':>5s} {'subs':>5s} {'nodes':>11s} {'arcs':>12s} "
+          f"{'sweep_ms':>9s} {'adm_ms':>8s} {'GB/s':>7s}", file=sys.stderr)
+    keys = sorted({(int(r[0]), int(r[1])) for r in ph})
+    for kind, rnd in keys + [(k, -1) for k in sorted({int(r[0]) for r in ph})]:
+        m = (ph[:, 0] == kind) & ((ph[:, 1] == rnd) | (rnd < 0))
+        q = ph[m]
+        nodes, arcs = q[:, 3].sum() / steps, q[:, 4].sum() / steps
+        sw, ad = q[:, 5].sum() / steps, q[:, 6].sum() / steps
+        gbs = (ARC_BYTES * arcs + NODE_BYTES * nodes) / (sw / 1e3) / 1e9 if sw else 0.0
+        print(f"{KINDS.get(kind, kind):10s} {'all' if rnd < 0 else rnd:>5} {len(q) / steps:5.0f} "
+              f"{nodes:11.0f} {arcs:12.0f} {sw:9.3f} {ad:8.3f} {gbs:7.0f}", file=sys.stderr)
+
+
 def serve_stream(P, graphs, lam, count, ref_cuts, seed=0):
     """Open-loop Poisson stream through the server: ``count`` requests (the
     batch's graphs in order, cycling) with exponential gaps of mean 1/lam s,
@@ -289,9 +313,10 @@ def main():
     torch.cuda.synchronize()
     ref_cuts = [r.cut for r in ref]
 
+    # timed steps: no event instrumentation inside (only the launch counter)
     sampler = ClockSampler(local)
+    P.sclap_profile_enable(False)
     P.sclap_profile_reset()
-    P.sclap_profile_enable(True)
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
@@ -305,9 +330,24 @@ def main():
     torch.cuda.synchronize()
     barrier()
     clocks = sampler.stop()
+    launches = P.sclap_profile_read()["kernel_launches"]
+    elapsed_ms = max_over_ranks(e0.elapsed_time(e1), ws, dev)
+    # the same steps again with CUDA events around every propose phase (the
+    # roofline's time base) and launch
+    P.sclap_profile_reset()
+    P.sclap_profile_enable(True)
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    p0.record(stream)
+    for _ in range(args.steps):
+        P.sclap_partition_batch(items, device=True)
+    p1.record(stream)
+    torch.cuda.synchronize()
     P.sclap_profile_enable(False)
     prof = P.sclap_profile_read()
-    elapsed_ms = max_over_ranks(e0.elapsed_time(e1), ws, dev)
+    prof_ms = p0.elapsed_time(p1)
+    if args.phases:
+        print_phases(P.sclap_profile_phases(), args.steps)
     if args.timeline:
         P.sclap_profile_dump()
         P.sclap_profile_timeline(True)
@@ -346,7 +386,8 @@ def main():
         "bytes_per_launch": prop_bytes / nl if nl else None,
         "avg_launch_ms": prop_ms / nl if nl else None,
         "launches": nl,
-        "share_of_step": prop_ms / elapsed_ms if elapsed_ms else None,
+        "share_of_step": prop_ms / prof_ms if prof_ms else None,
+        "profiled_ms_per_step": prof_ms / args.steps,
         "per_family": {FAMILIES[b]: {"ms": prof["propose_ms"][b], "launches": prof["propose_launches"][b],
                                      "nodes": prof["propose_nodes"][b], "arcs": prof["propose_arcs"][b]}
                        for b in range(4)},
@@ -361,7 +402,7 @@ def main():
         "input_edges_per_s": arcs_in / 2 * args.steps * ws / (elapsed_ms / 1000.0),
         "deterministic": deterministic, "balanced": balanced,
         "roofline": roofline, "clocks": clocks,
-        "gpu_launches": prof["kernel_launches"],
+        "gpu_launches": launches,
     }
 
     if rank == 0 and not args.no_plain:

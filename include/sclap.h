@@ -302,6 +302,13 @@ typedef struct sclap_profile {
 void sclap_profile_enable(int on);
 void sclap_profile_reset(void);
 void sclap_profile_read(sclap_profile* out);
+/* One record per LP sub-round run while profiling was enabled, 7 doubles
+ * each: run kind (1 clustering, 2 refinement, 3 initial-partitioning trial,
+ * 5 trial refinement, 6 repair), round, colour class, listed nodes, their
+ * arcs, propose-phase milliseconds (fork to join), admission milliseconds
+ * (join to the end of apply).  Writes at most `cap` records to `out` (may be
+ * NULL) and returns the number recorded since the last reset. */
+int64_t sclap_profile_phases(double* out, int64_t cap);
 /* Timeline mode: an event after every kernel launch and after every host
  * wait; sclap_profile_dump writes "name launches total_ms" lines (time since
  * the previous mark of the same call: device time plus any idle gap) into

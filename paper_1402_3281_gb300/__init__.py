@@ -8,7 +8,7 @@ from .sclap import (  # noqa: F401
     Config, Result, SclapError, Server, Served, default_config, load, sclap_cluster, sclap_contract, sclap_cut,
     sclap_cut_static,
     sclap_initial_partition, sclap_lp_round, sclap_partition, sclap_partition_batch,
-    sclap_partition_device, sclap_profile_dump, sclap_profile_enable, sclap_profile_read,
+    sclap_partition_device, sclap_profile_dump, sclap_profile_enable, sclap_profile_phases, sclap_profile_read,
     sclap_profile_reset, sclap_profile_timeline,
     sclap_refine,
 )

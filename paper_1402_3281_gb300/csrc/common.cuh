@@ -44,6 +44,9 @@ struct ProfileState {
   int64_t nlaunch[4] = {}, nodes[4] = {}, arcs[4] = {};
   double sweep_ms = 0;       // propose phases, fork to join (concurrent launches)
   int64_t sweeps = 0;
+  // per sub-round: run kind, round, colour class, nodes, arcs, propose ms,
+  // admission ms (7 values each)
+  std::vector<double> phases;
   // timeline mode: an event after every launch; the time from the previous
   // event of the same call to this one is charged to the kernel (device time
   // plus any idle gap before it)

@@ -1257,6 +1257,18 @@ void sclap_profile_reset(void) {
   for (int b = 0; b < 4; ++b) { P.ms[b] = 0; P.nlaunch[b] = 0; P.nodes[b] = 0; P.arcs[b] = 0; }
   P.sweep_ms = 0;
   P.sweeps = 0;
+  P.phases.clear();
+}
+
+int64_t sclap_profile_phases(double* out, int64_t cap) {
+  ProfileState& P = profile();
+  std::lock_guard<std::mutex> lk(P.mu);
+  const int64_t n = (int64_t)P.phases.size() / 7;
+  if (out && cap > 0) {
+    const int64_t m = std::min(n, cap);
+    std::memcpy(out, P.phases.data(), (size_t)(m * 7) * sizeof(double));
+  }
+  return n;
 }
 
 void sclap_profile_read(sclap_profile* out) {

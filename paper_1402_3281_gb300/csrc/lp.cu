@@ -894,23 +894,56 @@ __global__ void __launch_bounds__(SEL_NT) k_ovf_select(LPArgs a, int32_t source)
   __shared__ int32_t vmin_sh, vmax_sh, BV;
   __shared__ long long acc_sh;
   __shared__ int found_sh, ncand_sh, bfound_sh, done_sh;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31;
   const int64_t nseg = a.ctr[1];
+  // Phase 1: groups of <= 64 entries, one warp each (entries lane and
+  // lane + 32 in registers, every pair ranked through shuffles).
+  {
+    const int64_t nw = (int64_t)gridDim.x * (SEL_NT / 32);
+    for (int64_t sg = (int64_t)blockIdx.x * (SEL_NT / 32) + (tid >> 5); sg < nseg; sg += nw) {
+      const int32_t n = a.seg_cnt[sg];
+      if (n > SEL_SMALL) continue;
+      const int64_t base = a.seg_base[sg];
+      const int64_t thr = a.seg_thr[sg];
+      const bool h0 = lane < n, h1 = lane + 32 < n;
+      const uint64_t k0 = h0 ? a.ent_key[base + lane] : ~0ull;
+      const int32_t v0 = h0 ? a.ent_v[base + lane] : INT32_MAX;
+      const int32_t w0 = h0 ? a.ent_w[base + lane] : 0;
+      const uint64_t k1 = h1 ? a.ent_key[base + lane + 32] : ~0ull;
+      const int32_t v1 = h1 ? a.ent_v[base + lane + 32] : INT32_MAX;
+      const int32_t w1 = h1 ? a.ent_w[base + lane + 32] : 0;
+      int64_t e0 = 0, e1 = 0;
+      const int n0 = n < 32 ? n : 32;
+      for (int l = 0; l < n0; ++l) {
+        const uint64_t kl = __shfl_sync(0xffffffffu, k0, l);
+        const int32_t vl = __shfl_sync(0xffffffffu, v0, l);
+        const int32_t wl = __shfl_sync(0xffffffffu, w0, l);
+        e0 += key_less(kl, vl, k0, v0) ? wl : 0;
+        e1 += key_less(kl, vl, k1, v1) ? wl : 0;
+      }
+      for (int l = 32; l < n; ++l) {
+        const uint64_t kl = __shfl_sync(0xffffffffu, k1, l - 32);
+        const int32_t vl = __shfl_sync(0xffffffffu, v1, l - 32);
+        const int32_t wl = __shfl_sync(0xffffffffu, w1, l - 32);
+        e0 += key_less(kl, vl, k0, v0) ? wl : 0;
+        e1 += key_less(kl, vl, k1, v1) ? wl : 0;
+      }
+      if (h0) a.adm[a.ent_i[base + lane]] = (source ? e0 <= thr : e0 + w0 <= thr) ? 1 : 0;
+      if (h1) a.adm[a.ent_i[base + lane + 32]] = (source ? e1 <= thr : e1 + w1 <= thr) ? 1 : 0;
+      if (lane == 0) {
+        const int32_t g = a.seg_g[sg];
+        a.ovf_cnt[g] = 0;
+        a.ovf_fill[g] = 0;
+      }
+    }
+  }
+  // Phase 2: larger groups, one CTA each.
   for (int64_t sg = blockIdx.x; sg < nseg; sg += gridDim.x) {
     const int64_t base = a.seg_base[sg];
     const int32_t n = a.seg_cnt[sg];
     const int64_t thr = a.seg_thr[sg];
-    if (n <= SEL_SMALL) {
-      for (int j = tid; j < n; j += SEL_NT) {
-        sk[j] = a.ent_key[base + j];
-        sv[j] = a.ent_v[base + j];
-        sw[j] = a.ent_w[base + j];
-        si[j] = a.ent_i[base + j];
-      }
-      __syncthreads();
-      select_rank_small(a, n, thr, 0, sk, sv, sw, si, true, source, nullptr, nullptr, nullptr);
-      __syncthreads();
-    } else {
+    if (n <= SEL_SMALL) continue;
+    {
       // smallest and largest (key, node): their shared leading bytes are skipped
       if (tid == 0) { kmin_sh = ~0ull; kmax_sh = 0; vmin_sh = INT32_MAX; vmax_sh = -1; }
       __syncthreads();
@@ -965,17 +998,33 @@ __global__ void __launch_bounds__(SEL_NT) k_ovf_select(LPArgs a, int32_t source)
           }
         }
         __syncthreads();
-        if (tid == 0) {
-          long long acc = acc_sh;
-          int x = -1;
-          for (int d = 0; d < 256; ++d) {
-            if (acc + (long long)hist[d] > thr) { x = d; break; }
-            acc += (long long)hist[d];
+        if (tid < 32) {
+          // first digit whose bin takes the running weight past thr: each
+          // lane owns 8 consecutive bins, a warp scan gives its offset
+          long long loc[8], sum = 0;
+#pragma unroll
+          for (int q = 0; q < 8; ++q) { loc[q] = (long long)hist[tid * 8 + q]; sum += loc[q]; }
+          long long incl = sum;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const long long y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (tid >= o) incl += y;
           }
-          if (x < 0) {
-            found_sh = 0;   // every remaining entry fits
-          } else {
-            acc_sh = acc;
+          long long run = acc_sh + incl - sum;
+          int xq = -1;
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            if (xq < 0) {
+              if (run + loc[q] > thr) xq = q;
+              else run += loc[q];
+            }
+          }
+          const unsigned fm = __ballot_sync(0xffffffffu, xq >= 0);
+          if (fm == 0) {
+            if (tid == 0) found_sh = 0;   // every remaining entry fits
+          } else if (tid == __ffs(fm) - 1) {
+            const int x = tid * 8 + xq;
+            acc_sh = run;
             if (p < 8) PK |= (uint64_t)x << (56 - 8 * p);
             else PV |= (uint32_t)x << (24 - 8 * (p - 8));
             if (hcnt[x] <= SEL_SMALL) done_sh = 1;
@@ -1030,7 +1079,32 @@ __global__ void __launch_bounds__(SEL_NT) k_ovf_select(LPArgs a, int32_t source)
 // ------------------------------------------------------------- apply
 // Admitted moves update labels and weights; moved nodes activate their
 // neighbours (small rows by their own lane, larger rows by the whole warp).
+// Label-weight changes are first summed per CTA in a small shared hash
+// (label -> delta; a label that finds no slot within a few probes goes to
+// global memory directly), then flushed with one atomic per label: moves in
+// local search concentrate on a handful of blocks, whose global counters
+// would otherwise take one atomic per moved node each.
+constexpr int APPLY_SLOTS = 1024;
+__device__ __forceinline__ void apply_delta(int32_t* hk, int32_t* hv, wgt_t* W, int32_t L,
+                                            int32_t d) {
+  uint32_t s = table_slot(L, 10);
+#pragma unroll 1
+  for (int p = 0; p < 8; ++p) {
+    const int32_t prev = atomicCAS(&hk[s], -1, L);
+    if (prev == -1 || prev == L) {
+      atomicAdd(&hv[s], d);
+      return;
+    }
+    s = (s + 1) & (APPLY_SLOTS - 1);
+  }
+  atomicAdd(&W[L], (wgt_t)d);
+}
+
 __global__ void __launch_bounds__(256) k_apply(LPArgs a, int64_t lbeg, int64_t cnt) {
+  __shared__ int32_t hk[APPLY_SLOTS];
+  __shared__ int32_t hv[APPLY_SLOTS];
+  for (int j = threadIdx.x; j < APPLY_SLOTS; j += blockDim.x) { hk[j] = -1; hv[j] = 0; }
+  __syncthreads();
   const int lane = threadIdx.x & 31;
   const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -1056,8 +1130,8 @@ __global__ void __launch_bounds__(256) k_apply(LPArgs a, int64_t lbeg, int64_t c
             re = r2.x + r2.y;
           }
           a.label[v] = t;
-          atomicAdd(&a.W[t], (wgt_t)cv);
-          atomicSub(&a.W[own], (wgt_t)cv);
+          apply_delta(hk, hv, a.W, t, cv);
+          apply_delta(hk, hv, a.W, own, -cv);
           if (re - rs <= 8) {
             for (int64_t e = rs; e < re; ++e) a.act_next[a.col[e]] = 1;
             re = rs;
@@ -1085,6 +1159,9 @@ __global__ void __launch_bounds__(256) k_apply(LPArgs a, int64_t lbeg, int64_t c
     }
   }
   if (run_cnt) atomicAdd(ull(&a.moved[run_slot]), run_cnt);
+  __syncthreads();
+  for (int j = threadIdx.x; j < APPLY_SLOTS; j += blockDim.x)
+    if (hk[j] >= 0 && hv[j] != 0) atomicAdd(&a.W[hk[j]], (wgt_t)hv[j]);
 }
 
 }  // namespace
@@ -1253,6 +1330,10 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, wgt_t*
   const bool prof = profile().enabled.load();
   struct Timed { int family; cudaEvent_t a, b; };
   std::vector<Timed> timed;
+  // per sub-round record: kind of run, round, colour class, nodes, arcs and
+  // events at fork, join (end of the propose phase) and after apply
+  struct PhaseRec { int32_t ph, r, sub; int64_t nodes, arcs; cudaEvent_t a, b, c; };
+  std::vector<PhaseRec> precs;
   int64_t pn[4] = {}, pa[4] = {};
   int32_t hflags = 0;
   int64_t arcs_total = 0;
@@ -1419,6 +1500,10 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, wgt_t*
       if (prof) {
         SCLAP_CUDA(cudaEventRecord(phase.b, s));
         timed.push_back(phase);
+        int64_t sub_arcs = 0;
+        for (int q = 0; q < NB; ++q) sub_arcs += hkarcs[sub * NB + q];
+        precs.push_back(PhaseRec{run.phase, r, sub, cnt, sub_arcs, phase.a, phase.b,
+                                 event_from_pool()});
       }
       const unsigned lg = grid_for(cnt, 256, (int64_t)sms * 16);
       k_resolve<<<lg, 256, 0, s>>>(a, lbeg, cnt); SCLAP_NOTE_LAUNCH("k_resolve");
@@ -1435,6 +1520,7 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, wgt_t*
       }
       k_apply<<<lg, 256, 0, s>>>(a, lbeg, cnt); SCLAP_NOTE_LAUNCH("k_apply");
       SCLAP_LAUNCH_CHECK();
+      if (prof) SCLAP_CUDA(cudaEventRecord(precs.back().c, s));
     }
     k_round_end<<<grid_for(sp.nslots, 128, 1024), 128, 0, s>>>(a, sp.nslots,
                                                                 run.stop_rule ? 1 : 0); SCLAP_NOTE_LAUNCH("k_round_end");
@@ -1463,6 +1549,15 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, wgt_t*
       P.nlaunch[t.family] += 1;
     }
     for (int b = 0; b < 4; ++b) { P.nodes[b] += pn[b]; P.arcs[b] += pa[b]; }
+    for (const PhaseRec& q : precs) {
+      float sw = 0.f, ad = 0.f;
+      SCLAP_CUDA(cudaEventElapsedTime(&sw, q.a, q.b));
+      SCLAP_CUDA(cudaEventElapsedTime(&ad, q.b, q.c));
+      const double rec[7] = {(double)q.ph, (double)q.r, (double)q.sub, (double)q.nodes,
+                             (double)q.arcs, (double)sw, (double)ad};
+      P.phases.insert(P.phases.end(), rec, rec + 7);
+      event_to_pool(q.c);
+    }
     for (const Timed& t : timed) { event_to_pool(t.a); event_to_pool(t.b); }
   }
   return h_arcs;

@@ -28,7 +28,7 @@ SYMBOLS = (
     "sclap_contract", "sclap_initial_partition", "sclap_refine", "sclap_cut",
     "sclap_cut_static", "sclap_server_create", "sclap_server_submit", "sclap_server_poll",
     "sclap_server_destroy", "sclap_profile_enable", "sclap_profile_reset", "sclap_profile_read",
-    "sclap_profile_timeline", "sclap_profile_dump",
+    "sclap_profile_timeline", "sclap_profile_dump", "sclap_profile_phases",
 )
 
 
@@ -123,6 +123,7 @@ def _lib():
             "sclap_profile_read": (None, [p]),
             "sclap_profile_timeline": (None, [C.c_int]),
             "sclap_profile_dump": (C.c_int64, [p, C.c_int64]),
+            "sclap_profile_phases": (C.c_int64, [p, C.c_int64]),
         }
         for name, (res, args) in sig.items():
             f = getattr(h, name)
@@ -460,3 +461,12 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def sclap_profile_phases() -> np.ndarray:
+    """Per-sub-round records since the last reset, shape (count, 7): run kind,
+    round, colour class, nodes, arcs, propose ms, admission ms."""
+    n = _lib().sclap_profile_phases(None, 0)
+    out = np.zeros((max(n, 1), 7), dtype=np.float64)
+    m = _lib().sclap_profile_phases(out.ctypes.data_as(C.c_void_p), n)
+    return out[:min(n, m)]
