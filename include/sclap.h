@@ -62,7 +62,14 @@ enum {
 /* Tunables.  Defaults (sclap_default_config): the paper's parameters (Sec. 5):
  * l = 10 LP rounds per level in coarsening and uncoarsening, f = 18; plus
  * coarsening down to max(1000, 60k) nodes, 16 initial-partitioning trials,
- * 8 colour classes per synchronous round, 64 repair rounds, 64 levels. */
+ * 8 colour classes per synchronous round, 64 repair rounds, 64 levels, and
+ * clustering without active nodes.
+ * cluster_active = 1 turns on active nodes during coarsening (Sec. 4 "Active
+ * Nodes", configuration A of Table 2): after the first round a clustering
+ * round visits only nodes with a neighbour that changed its cluster in the
+ * round before.  (Configuration R, a random node order, is what the
+ * synchronous rounds do already: nodes are split into colour classes by a
+ * per-round hash.) */
 typedef struct sclap_config {
   int32_t lp_rounds_coarse;
   int32_t lp_rounds_refine;
@@ -72,6 +79,7 @@ typedef struct sclap_config {
   int32_t sub_rounds;
   int32_t repair_rounds;
   int32_t max_levels;
+  int32_t cluster_active;
 } sclap_config;
 
 /* Per-call statistics (optional output). */

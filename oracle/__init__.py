@@ -36,7 +36,8 @@ def build(force: bool = False) -> str:
 class Config(C.Structure):
     _fields_ = [(name, C.c_int32) for name in (
         "lp_rounds_coarse", "lp_rounds_refine", "f", "coarse_min_nodes",
-        "ip_trials", "sub_rounds", "repair_rounds", "max_levels")]
+        "ip_trials", "sub_rounds", "repair_rounds", "max_levels", "cluster_active",
+        "random_order")]
 
 
 class Stats(C.Structure):

@@ -277,12 +277,27 @@ vector<int32_t> degree_order(const G& g, uint64_t rkey) {
   return order;
 }
 
+// Random node order (configuration R of Table 2): the hash order alone.
+vector<int32_t> hashed_order(const G& g, uint64_t rkey) {
+  vector<std::pair<uint64_t, int32_t>> keyed((size_t)g.n);
+  for (int64_t v = 0; v < g.n; ++v) keyed[v] = std::make_pair(node_hash(rkey, v), (int32_t)v);
+  std::sort(keyed.begin(), keyed.end());
+  vector<int32_t> order((size_t)g.n);
+  for (int64_t i = 0; i < g.n; ++i) order[i] = keyed[i].second;
+  return order;
+}
+
 // One sequential clustering round (Sec. 3.1): visit every node once, move it
-// immediately to its strongest eligible cluster.
+// immediately to its strongest eligible cluster.  With active flags (Sec. 4,
+// "Active Nodes"), nodes not flagged in active_cur are skipped and the
+// neighbours of every moved node are flagged in active_next.
 int64_t seq_cluster_round(const G& g, int32_t* label, int64_t* W, int64_t bound, uint64_t rkey,
-                          Conn& conn) {
+                          Conn& conn, bool random_order, const uint8_t* active_cur,
+                          uint8_t* active_next) {
   int64_t moved = 0;
-  for (int32_t v : degree_order(g, rkey)) {
+  const vector<int32_t> order = random_order ? hashed_order(g, rkey) : degree_order(g, rkey);
+  for (int32_t v : order) {
+    if (active_cur && !active_cur[v]) continue;
     uint64_t hv = node_hash(rkey, v);
     conn.build(g, label, v);
     int32_t t;
@@ -292,6 +307,8 @@ int64_t seq_cluster_round(const G& g, int32_t* label, int64_t* W, int64_t bound,
       W[label[v]] -= g.nw[v];
       label[v] = t;
       ++moved;
+      if (active_next)
+        for (int64_t e = g.xadj[v]; e < g.xadj[v + 1]; ++e) active_next[g.adj[e]] = 1;
     }
   }
   conn.clear();
@@ -307,13 +324,23 @@ int cluster_level(int variant, const G& g, int64_t U, uint64_t seed, int32_t lev
   for (int64_t v = 0; v < g.n; ++v) { label[v] = (int32_t)v; W[v] = g.nw[v]; }
   Conn conn(g.n);
   int32_t rounds = 0;
+  // active nodes (Sec. 4): every node is active in the first round; a node
+  // is active in a later round iff a neighbour changed its cluster in the
+  // round before
+  const bool act = cfg.cluster_active != 0;
+  vector<uint8_t> cur(act ? (size_t)g.n : 0, 1), nxt(act ? (size_t)g.n : 0, 0);
   for (int32_t r = 0; r < cfg.lp_rounds_coarse; ++r) {
     uint64_t rkey = hkey(seed, ORC_PH_CLUSTER, (uint64_t)level, (uint64_t)r);
     int64_t moved = variant == ORC_SYNC
         ? sync_round(ORC_MODE_CLUSTER, g, label, W.data(), g.n, U, rkey, cfg.sub_rounds,
-                     nullptr, nullptr)
-        : seq_cluster_round(g, label, W.data(), U, rkey, conn);
+                     act ? cur.data() : nullptr, act ? nxt.data() : nullptr)
+        : seq_cluster_round(g, label, W.data(), U, rkey, conn, cfg.random_order != 0,
+                            act ? cur.data() : nullptr, act ? nxt.data() : nullptr);
     ++rounds;
+    if (act) {
+      cur.swap(nxt);
+      std::fill(nxt.begin(), nxt.end(), 0);
+    }
     if (20 * moved < g.n) break;
   }
   if (rounds_out) *rounds_out = rounds;
@@ -612,6 +639,8 @@ void orc_default_config(orc_config* cfg) {
   cfg->sub_rounds = 8;
   cfg->repair_rounds = 64;
   cfg->max_levels = 64;
+  cfg->cluster_active = 0;
+  cfg->random_order = 0;
 }
 
 uint64_t orc_mix64(uint64_t x) { return mix64(x); }

@@ -51,6 +51,13 @@ typedef struct orc_config {
   int32_t sub_rounds;       /* colour classes per synchronous round                */
   int32_t repair_rounds;    /* cap on final balance-repair rounds                  */
   int32_t max_levels;       /* cap on hierarchy depth                              */
+  int32_t cluster_active;   /* 1: active nodes during coarsening (Sec. 4 "Active
+                               Nodes", configuration A of Table 2): after the first
+                               round, only nodes next to a node that changed its
+                               cluster in the previous round are visited            */
+  int32_t random_order;     /* sequential variant only, 1: visit nodes in hashed
+                               random order instead of increasing degree
+                               (configuration R of Table 2)                         */
 } orc_config;
 
 typedef struct orc_stats {

@@ -40,7 +40,7 @@ sclap_config resolve_cfg(const sclap_config* c) {
   if (c) r = *c;
   if (r.lp_rounds_coarse < 0 || r.lp_rounds_refine < 0 || r.f < 1 || r.coarse_min_nodes < 1 ||
       r.ip_trials < 1 || r.sub_rounds < 1 || r.sub_rounds > 64 || r.repair_rounds < 0 ||
-      r.max_levels < 1)
+      r.max_levels < 1 || r.cluster_active < 0 || r.cluster_active > 1)
     throw Error(SCLAP_EINVAL, "invalid sclap_config");
   return r;
 }
@@ -609,6 +609,7 @@ void run_valid_batch(const std::vector<GIn>& gs, const std::vector<int64_t>& cV,
     run.phase = PH_CLUSTER;
     run.rounds = cfg.lp_rounds_coarse;
     run.sub_rounds = cfg.sub_rounds;
+    run.use_active = cfg.cluster_active != 0;
     lp_arcs += lp_run(v, sl.sp, label.p, W.p, v.N, run, d_err.p, s);
     const std::vector<int32_t> rr = sl.host_rounds(s);
     for (int g = 0; g < B; ++g)
@@ -888,6 +889,7 @@ void sclap_default_config(sclap_config* c) {
   c->sub_rounds = 8;
   c->repair_rounds = 64;
   c->max_levels = 64;
+  c->cluster_active = 0;
 }
 
 const char* sclap_error_string(int code) {
@@ -1100,6 +1102,7 @@ int sclap_cluster(int64_t n, const int64_t* row_ptr, const int32_t* col, const i
     run.phase = PH_CLUSTER;
     run.rounds = c.lp_rounds_coarse;
     run.sub_rounds = c.sub_rounds;
+    run.use_active = c.cluster_active != 0;
     DevBuf<int32_t> d_err(1, s);
     d_err.zero();
     lp_run(L.view(), sl.sp, label_out, W.p, n, run, d_err.p, s);

@@ -60,8 +60,13 @@ def test_oracle_and_library_defaults_agree(lib_path):
     import oracle as O
     from paper_1402_3281_gb300 import sclap
     a, b = O.config(), sclap.default_config()
+    lib_fields = {f for f, _ in sclap.Config._fields_}
     for f, _ in O.Config._fields_:
+        if f == "random_order":      # sequential variant only: not in the GPU config
+            assert f not in lib_fields
+            continue
         assert getattr(a, f) == getattr(b, f), f
+    assert lib_fields <= {f for f, _ in O.Config._fields_}
 
 
 def test_static_cut_limit_matches_header():

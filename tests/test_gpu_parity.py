@@ -131,6 +131,16 @@ def test_cluster_level_bit_exact(graph):
     assert np.array_equal(tl.cpu().numpy(), ol)
 
 
+def test_cluster_level_active_nodes_bit_exact(graph):
+    """Active nodes during coarsening (configuration A)."""
+    g = graph
+    Lmax, U = O.bounds(int(g.node_w.sum()), int(g.node_w.max()), 2, 0.03)
+    ol, orounds = O.cluster(g, U, seed=5, level=1, cfg=O.config(cluster_active=1))
+    tl, rounds = P.sclap_cluster(*dg(g), U, 5, 1, cfg=P.default_config(cluster_active=1))
+    assert rounds == orounds
+    assert np.array_equal(tl.cpu().numpy(), ol)
+
+
 def _canon(rp, col, w):
     n = rp.size - 1
     src = np.repeat(np.arange(n), np.diff(rp))
@@ -226,6 +236,17 @@ def test_partition_bit_exact(name, k):
     st = res.stats
     assert st["levels"] == ref.stats.levels
     assert st["level_n"] == list(ref.stats.level_n[:ref.stats.levels])
+
+
+@pytest.mark.parametrize("name", ["rmat16", "rgg", "weighted"])
+def test_partition_active_coarsening_bit_exact(name):
+    g = GRAPHS[name]()
+    ref = O.partition(g, 8, 0.03, seed=2, cfg=O.config(cluster_active=1))
+    res = P.sclap_partition_device(*dg(g), k=8, eps=0.03, seed=2,
+                                   cfg=P.default_config(cluster_active=1))
+    assert (res.status, res.cut) == (ref.status, ref.cut)
+    assert np.array_equal(res.block.cpu().numpy(), ref.block)
+    assert res.stats["level_n"] == list(ref.stats.level_n[:ref.stats.levels])
 
 
 def test_partition_host_api_and_seeds():

@@ -408,3 +408,61 @@ def test_sync_mean_cut_within_5_percent_of_sequential():
     seq = np.mean([O.partition(g, 2, 0.03, s, variant=O.SEQ).cut for s in range(5)])
     syn = np.mean([O.partition(g, 2, 0.03, s, variant=O.SYNC).cut for s in range(5)])
     assert syn <= 1.05 * seq
+
+
+# ---------------------------------------------------------------- active nodes
+# Active nodes during coarsening (Sec. 4 "Active Nodes"; configuration A of
+# Table 2): in the first round every node is active, afterwards a node is
+# active iff one of its neighbours changed its cluster in the previous round.
+
+@pytest.mark.parametrize("variant", [O.SYNC, O.SEQ])
+def test_active_coarsening_single_round_equals_plain(variant):
+    g = gg.rmat(11, 8, 5)
+    one = dict(lp_rounds_coarse=1)
+    a, _ = O.cluster(g, 40, 3, variant=variant, cfg=O.config(cluster_active=1, **one))
+    b, _ = O.cluster(g, 40, 3, variant=variant, cfg=O.config(cluster_active=0, **one))
+    assert np.array_equal(a, b)
+
+
+def test_active_coarsening_follows_the_definition():
+    """orc_cluster with active nodes equals rounds driven from Python, where
+    each round's active set is recomputed from the definition: the
+    neighbours of the nodes whose label changed in the round before."""
+    g = gg.rgg2d(1500, 7)
+    U, seed, level = 25, 11, 2
+    src = np.repeat(np.arange(g.n), np.diff(g.row_ptr))
+    label = np.arange(g.n, dtype=np.int32)
+    W = g.node_w.astype(np.int64)
+    active = np.ones(g.n, dtype=np.uint8)
+    for R in range(1, 6):
+        rkey = O.hkey(seed, O.PH_CLUSTER, level, R - 1)
+        new, W, moved, _ = O.lp_round(g, O.MODE_CLUSTER, label, W, U, rkey, 8, active_cur=active)
+        changed = new != label
+        active = np.zeros(g.n, dtype=np.uint8)
+        active[g.col[changed[src]]] = 1
+        label = new
+        got, rounds = O.cluster(g, U, seed, level=level,
+                                cfg=O.config(cluster_active=1, lp_rounds_coarse=R))
+        if rounds < R:          # stopped early by the 5% rule: nothing more to compare
+            break
+        assert np.array_equal(got, label), R
+
+
+@pytest.mark.parametrize("variant", [O.SYNC, O.SEQ])
+def test_active_coarsening_respects_U(variant):
+    g = gg.random_weights(gg.rmat(12, 8, 2), 4, max_node_w=5)
+    U = 60
+    lab, _ = O.cluster(g, U, 1, variant=variant, cfg=O.config(cluster_active=1))
+    assert np.bincount(lab, weights=g.node_w, minlength=g.n).max() <= U
+
+
+@pytest.mark.parametrize("active", [0, 1])
+def test_random_order_recovers_cliques(active):
+    """Configuration R (random node order, sequential variant): cliques joined
+    by single edges are still found exactly when U equals the clique size."""
+    k, s = 6, 7
+    g = gg.clique_ring(k, s)
+    lab, _ = O.cluster(g, s, 4, variant=O.SEQ,
+                       cfg=O.config(random_order=1, cluster_active=active))
+    groups = {tuple(np.flatnonzero(lab == c)) for c in np.unique(lab)}
+    assert groups == {tuple(range(q * s, (q + 1) * s)) for q in range(k)}
