@@ -179,6 +179,25 @@ int sclap_contract(int64_t n, const int64_t* row_ptr, const int32_t* col,
                    int32_t* cmap, int64_t* nc_out, int32_t* cnode_w, int64_t* crow_ptr,
                    int32_t* ccol, int32_t* cedge_w, int64_t* mc_out, void* stream);
 
+/* Clustering hierarchy without a partitioning target (Sec. 3.1 clustering
+ * and contraction, repeated as in the coarsening phase; usable on its own
+ * for size-constrained community-style coarsening).  Clusters the graph
+ * with bound U (cluster weight <= U; nodes heavier than U stay alone), level
+ * l hashing with level l; contracts; repeats while the current graph has
+ * more than stop_nodes nodes, the hierarchy has fewer than cfg->max_levels
+ * graphs, and the contraction removes at least 5% of the nodes (a
+ * contraction that removes less is discarded).  Device: comm_out int32[n]
+ * receives, for every input node, its node in the last graph (the
+ * community id, in [0, level_n_out[levels])).  Host: *levels_out the number
+ * of contractions kept; level_n_out (cap entries, may be NULL) the node
+ * counts, input first.  Uses cfg->lp_rounds_coarse, sub_rounds,
+ * cluster_active and max_levels. */
+int sclap_cluster_hierarchy(int64_t n, const int64_t* row_ptr, const int32_t* col,
+                            const int32_t* node_w, const int32_t* edge_w, int64_t U,
+                            int64_t stop_nodes, uint64_t seed, const sclap_config* cfg,
+                            int32_t* comm_out, int32_t* levels_out, int64_t* level_n_out,
+                            int32_t cap, void* stream);
+
 /* Initial partitioning of a (coarsest) graph: cfg->ip_trials trials of
  * greedy growing plus LP local search, best by (overload, cut, trial).
  * block_out int32[n]; cut_out, best_trial_out on the host. */

@@ -65,6 +65,8 @@ def lib():
             "orc_lp_round": (C.c_int, [i32, i64, p, p, p, p, p, p, i64, i64, u64, i32, p, p, p]),
             "orc_cluster": (C.c_int, [i32, i64, p, p, p, p, i64, u64, i32, p, p, p]),
             "orc_contract": (C.c_int, [i64, p, p, p, p, p, p, p, p, p, p, p, p]),
+            "orc_cluster_hierarchy": (C.c_int, [i32, i64, p, p, p, p, i64, i64, u64, p, p, p,
+                                                p, i32]),
             "orc_ggg": (C.c_int, [i64, p, p, p, p, i32, i64, u64, i32, p, p]),
             "orc_initial_partition": (C.c_int, [i32, i64, p, p, p, p, i32, i64, i64, u64, i32,
                                                 p, p, p, p]),
@@ -143,6 +145,23 @@ def cluster(g, U, seed, level=0, variant=SYNC, cfg=None):
     if rc:
         raise RuntimeError(f"orc_cluster rc={rc}")
     return label, rounds.value
+
+
+def cluster_hierarchy(g, U, stop_nodes, seed, variant=SYNC, cfg=None):
+    """Clustering hierarchy without k: (community of each input node,
+    contractions kept, node counts per level, input first)."""
+    rp, col, nw, ew = _graph_arrays(g)
+    comm = np.empty(g.n, dtype=np.int32)
+    levels = C.c_int32()
+    cap = 65
+    level_n = np.zeros(cap, dtype=np.int64)
+    cfg = cfg or config()
+    rc = lib().orc_cluster_hierarchy(variant, g.n, _p(rp), _p(col), _p(nw), _p(ew), int(U),
+                                     int(stop_nodes), seed & (2**64 - 1), C.byref(cfg),
+                                     _p(comm), C.byref(levels), _p(level_n), cap)
+    if rc:
+        raise RuntimeError(f"orc_cluster_hierarchy rc={rc}")
+    return comm, levels.value, [int(x) for x in level_n[:levels.value + 1]]
 
 
 @dataclass

@@ -672,6 +672,40 @@ int orc_cluster(int32_t variant, int64_t n, const int64_t* xadj, const int32_t* 
   return cluster_level(variant, g, U, seed, level, c, label_out, rounds_out);
 }
 
+int orc_cluster_hierarchy(int32_t variant, int64_t n, const int64_t* xadj, const int32_t* adj,
+                          const int32_t* nw, const int32_t* ew, int64_t U, int64_t stop_nodes,
+                          uint64_t seed, const orc_config* cfg, int32_t* comm_out,
+                          int32_t* levels_out, int64_t* level_n_out, int32_t cap) {
+  if (n < 1 || U < 1 || !comm_out) return ORC_EINVAL;
+  orc_config c;
+  if (cfg) c = *cfg; else orc_default_config(&c);
+  for (int64_t v = 0; v < n; ++v) comm_out[v] = (int32_t)v;
+  OG cur;
+  cur.n = n;
+  cur.xadj.assign(xadj, xadj + n + 1);
+  cur.adj.assign(adj, adj + xadj[n]);
+  cur.nw.assign(nw, nw + n);
+  cur.ew.assign(ew, ew + xadj[n]);
+  int32_t levels = 0;
+  if (level_n_out && cap > 0) level_n_out[0] = n;
+  while (cur.n > stop_nodes && levels + 1 < c.max_levels) {
+    const G g = cur.view();
+    vector<int32_t> label((size_t)g.n);
+    cluster_level(variant, g, U, seed, levels, c, label.data(), nullptr);
+    vector<int32_t> cmap;
+    OG coarse;
+    const int rc = contract(g, label.data(), cmap, coarse);
+    if (rc != ORC_OK) return rc;
+    if (20 * (g.n - coarse.n) < g.n) break;      // shrink below 5%: discarded
+    for (int64_t v = 0; v < n; ++v) comm_out[v] = cmap[comm_out[v]];
+    cur = std::move(coarse);
+    ++levels;
+    if (level_n_out && levels < cap) level_n_out[levels] = cur.n;
+  }
+  if (levels_out) *levels_out = levels;
+  return ORC_OK;
+}
+
 int orc_contract(int64_t n, const int64_t* xadj, const int32_t* adj, const int32_t* nw,
                  const int32_t* ew, const int32_t* label, int32_t* cmap_out, int64_t* nc_out,
                  int32_t* cnw_out, int64_t* cxadj_out, int32_t* cadj_out, int32_t* cew_out,

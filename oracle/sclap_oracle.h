@@ -103,6 +103,20 @@ int orc_cluster(int32_t variant, int64_t n, const int64_t* xadj, const int32_t* 
                 int32_t level, const orc_config* cfg, int32_t* label_out,
                 int32_t* rounds_out);
 
+/* Clustering hierarchy without a partitioning target (Sec. 3.1 clustering
+ * and contraction, repeated as in the coarsening phase of Sec. 3): cluster
+ * the current graph with bound U (level l uses hash level l), contract, and
+ * repeat while the current graph has more than stop_nodes nodes, the
+ * hierarchy has fewer than cfg->max_levels graphs, and the contraction
+ * removes at least 5% of the nodes (a contraction removing less is
+ * discarded).  comm_out[v] (n entries) receives the node of the last graph
+ * that input node v belongs to; *levels_out the number of contractions
+ * kept; level_n_out[0..min(levels, cap-1)] the node counts, input first. */
+int orc_cluster_hierarchy(int32_t variant, int64_t n, const int64_t* xadj, const int32_t* adj,
+                          const int32_t* nw, const int32_t* ew, int64_t U, int64_t stop_nodes,
+                          uint64_t seed, const orc_config* cfg, int32_t* comm_out,
+                          int32_t* levels_out, int64_t* level_n_out, int32_t cap);
+
 /* Cluster contraction (Sec. 3.1): coarse id = rank of the cluster label;
  * outputs sized by the fine graph (n, n+1, m entries). */
 int orc_contract(int64_t n, const int64_t* xadj, const int32_t* adj, const int32_t* nw,

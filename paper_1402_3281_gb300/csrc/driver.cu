@@ -124,6 +124,15 @@ __global__ void k_iota(int32_t* label, int64_t N) {
     label[v] = (int32_t)v;
 }
 
+// comm[v] <- cmap[comm[v]]: one more contraction composed into the
+// input-node-to-coarse-node map.
+__global__ void k_compose(int32_t* __restrict__ comm, const int32_t* __restrict__ cmap,
+                          int64_t n) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x)
+    comm[v] = cmap[comm[v]];
+}
+
 __global__ void k_w_from_nw(const int32_t* nw, int64_t N, wgt_t* W) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N;
        v += (int64_t)gridDim.x * blockDim.x)
@@ -1108,6 +1117,73 @@ int sclap_cluster(int64_t n, const int64_t* row_ptr, const int32_t* col, const i
     lp_run(L.view(), sl.sp, label_out, W.p, n, run, d_err.p, s);
     check_err(d_err.p, s);
     if (rounds_out) *rounds_out = sl.host_rounds(s)[0];
+  });
+}
+
+int sclap_cluster_hierarchy(int64_t n, const int64_t* row_ptr, const int32_t* col,
+                            const int32_t* node_w, const int32_t* edge_w, int64_t U,
+                            int64_t stop_nodes, uint64_t seed, const sclap_config* cfg,
+                            int32_t* comm_out, int32_t* levels_out, int64_t* level_n_out,
+                            int32_t cap, void* stream) {
+  return guarded([&] {
+    if (n < 1 || n >= ((int64_t)1 << 31) || !row_ptr || !comm_out || U < 1)
+      throw Error(SCLAP_EINVAL, "bad argument");
+    const sclap_config c = resolve_cfg(cfg);
+    cudaStream_t s = (cudaStream_t)stream;
+    GIn g;
+    g.n = n; g.m = device_arcs(row_ptr, n, s); g.row_ptr = row_ptr; g.col = col; g.nw = node_w;
+    g.ew = edge_w;
+    check_col(g.col, g.m);
+    int64_t cV, maxc;
+    validate(g, s, &cV, &maxc);
+    const int sms = num_sms();
+    std::unique_ptr<Level> cur(new Level());
+    single_level(g, *cur, s);
+    k_iota<<<grid_for(n, 256, (int64_t)sms * 16), 256, 0, s>>>(comm_out, n); SCLAP_NOTE_LAUNCH("k_iota");
+    int32_t levels = 0;
+    if (level_n_out && cap > 0) level_n_out[0] = n;
+    DevBuf<int32_t> d_err(1, s);
+    d_err.zero();
+    while (cur->N > stop_nodes && levels + 1 < c.max_levels) {
+      const LevelView v = cur->view();
+      Slots sl(s, 1, cur->noff_d.p, {0}, {U}, {seed}, {levels}, {0}, {0});
+      DevBuf<int32_t> label(v.N, s);
+      DevBuf<wgt_t> W(v.N, s);
+      k_iota<<<grid_for(v.N, 256, (int64_t)sms * 16), 256, 0, s>>>(label.p, v.N); SCLAP_NOTE_LAUNCH("k_iota");
+      k_w_from_nw<<<grid_for(v.N, 256, (int64_t)sms * 16), 256, 0, s>>>(v.nw, v.N, W.p); SCLAP_NOTE_LAUNCH("k_w_from_nw");
+      LPRun run;
+      run.mode = MODE_CLUSTER;
+      run.phase = PH_CLUSTER;
+      run.rounds = c.lp_rounds_coarse;
+      run.sub_rounds = c.sub_rounds;
+      run.use_active = c.cluster_active != 0;
+      lp_run(v, sl.sp, label.p, W.p, v.N, run, d_err.p, s);
+      ContractWork cw;
+      std::vector<int64_t> nc;
+      contract_rank(v, cur->noff, label.p, cw, nc, s);
+      if (20 * (v.N - nc[0]) < v.N) break;          // shrink below 5%: discarded
+      cur->cmap.alloc(v.N, s);
+      CoarseLevel co;
+      contract_build(v, cur->noff, label.p, cw, {1}, cur->cmap.p, co, d_err.p, s);
+      k_compose<<<grid_for(n, 256, (int64_t)sms * 16), 256, 0, s>>>(comm_out, cur->cmap.p, n); SCLAP_NOTE_LAUNCH("k_compose");
+      std::unique_ptr<Level> nx(new Level());
+      nx->N = co.N;
+      nx->M = co.M;
+      nx->row_ptr = std::move(co.row_ptr);
+      nx->col = std::move(co.col);
+      nx->ew = std::move(co.ew);
+      nx->nw = std::move(co.nw);
+      nx->gid = std::move(co.gid);
+      nx->noff_d = std::move(co.noff_d);
+      nx->noff = co.noff;
+      nx->aoff = co.aoff;
+      cur = std::move(nx);
+      ++levels;
+      if (level_n_out && levels < cap) level_n_out[levels] = cur->N;
+    }
+    check_err(d_err.p, s);
+    stream_sync(s);
+    if (levels_out) *levels_out = levels;
   });
 }
 

@@ -25,7 +25,7 @@ PH_REFINE, PH_IPREF = 2, 5
 SYMBOLS = (
     "sclap_default_config", "sclap_error_string", "sclap_last_error", "sclap_partition",
     "sclap_partition_device", "sclap_partition_batch", "sclap_lp_round", "sclap_cluster",
-    "sclap_contract", "sclap_initial_partition", "sclap_refine", "sclap_cut",
+    "sclap_contract", "sclap_cluster_hierarchy", "sclap_initial_partition", "sclap_refine", "sclap_cut",
     "sclap_cut_static", "sclap_server_create", "sclap_server_submit", "sclap_server_poll",
     "sclap_server_destroy", "sclap_profile_enable", "sclap_profile_reset", "sclap_profile_read",
     "sclap_profile_timeline", "sclap_profile_dump", "sclap_profile_phases",
@@ -109,6 +109,8 @@ def _lib():
             "sclap_lp_round": (C.c_int, [i32, i64, p, p, p, p, p, p, i64, i64, u64, i32, p, p, p, p]),
             "sclap_cluster": (C.c_int, [i64, p, p, p, p, i64, u64, i32, p, p, p, p]),
             "sclap_contract": (C.c_int, [i64, p, p, p, p, p, p, p, p, p, p, p, p, p]),
+            "sclap_cluster_hierarchy": (C.c_int, [i64, p, p, p, p, i64, i64, u64, p, p, p, p,
+                                                  i32, p]),
             "sclap_initial_partition": (C.c_int, [i64, p, p, p, p, i32, i64, i64, u64, i32, p, p,
                                                   p, p, p]),
             "sclap_refine": (C.c_int, [i64, p, p, p, p, i32, i64, u64, i32, i32, p, p, p, p]),
@@ -318,6 +320,25 @@ def sclap_cluster(row_ptr, col, node_w, edge_w, U, seed, level=0, cfg=None, stre
                               _dp(label), C.byref(rounds), _stream(stream))
     _check(rc, "sclap_cluster")
     return label, rounds.value
+
+
+def sclap_cluster_hierarchy(row_ptr, col, node_w, edge_w, U, stop_nodes, seed, cfg=None,
+                            stream=None):
+    """Clustering hierarchy without k (device tensors in): returns (community
+    of each input node as a CUDA tensor, contractions kept, node counts per
+    level, input first)."""
+    import torch
+    n = row_ptr.numel() - 1
+    comm = torch.empty(n, dtype=torch.int32, device=row_ptr.device)
+    levels = C.c_int32()
+    cap = 65
+    level_n = np.zeros(cap, dtype=np.int64)
+    rc = _lib().sclap_cluster_hierarchy(n, _dp(row_ptr), _dp(col), _dp(node_w), _dp(edge_w),
+                                        int(U), int(stop_nodes), int(seed) & (2**64 - 1),
+                                        C.byref(cfg) if cfg else None, _dp(comm),
+                                        C.byref(levels), _hp(level_n), cap, _stream(stream))
+    _check(rc, "sclap_cluster_hierarchy")
+    return comm, levels.value, [int(x) for x in level_n[:levels.value + 1]]
 
 
 def sclap_contract(row_ptr, col, node_w, edge_w, label, stream=None):

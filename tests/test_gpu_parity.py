@@ -141,6 +141,30 @@ def test_cluster_level_active_nodes_bit_exact(graph):
     assert np.array_equal(tl.cpu().numpy(), ol)
 
 
+@pytest.mark.parametrize("U,stop,active", [(30, 100, 0), (400, 1, 0), (60, 1, 1)])
+def test_cluster_hierarchy_bit_exact(graph, U, stop, active):
+    """Clustering-only hierarchy (no k): communities and level sizes."""
+    g = graph
+    oc, olev, osz = O.cluster_hierarchy(g, U, stop, 13, cfg=O.config(cluster_active=active))
+    tc, tlev, tsz = P.sclap_cluster_hierarchy(*dg(g), U, stop, 13,
+                                              cfg=P.default_config(cluster_active=active))
+    assert (tlev, tsz) == (olev, osz)
+    assert np.array_equal(tc.cpu().numpy(), oc)
+
+
+def test_cluster_hierarchy_edge_cases():
+    g = gg.clique_ring(20, 8)
+    tc, tlev, tsz = P.sclap_cluster_hierarchy(*dg(g), 8, 1, 2)
+    oc, olev, osz = O.cluster_hierarchy(g, 8, 1, 2)
+    assert (tlev, tsz) == (olev, osz) == (1, [160, 20])
+    assert np.array_equal(tc.cpu().numpy(), oc)
+    g = gg.from_edges(500, [], [])                   # no edges: nothing to merge
+    tc, tlev, _ = P.sclap_cluster_hierarchy(*dg(g), 10, 1, 0)
+    assert tlev == 0 and np.array_equal(tc.cpu().numpy(), np.arange(500))
+    with pytest.raises(P.SclapError):                # U must be >= 1
+        P.sclap_cluster_hierarchy(*dg(g), 0, 1, 0)
+
+
 def _canon(rp, col, w):
     n = rp.size - 1
     src = np.repeat(np.arange(n), np.diff(rp))

@@ -466,3 +466,56 @@ def test_random_order_recovers_cliques(active):
                        cfg=O.config(random_order=1, cluster_active=active))
     groups = {tuple(np.flatnonzero(lab == c)) for c in np.unique(lab)}
     assert groups == {tuple(range(q * s, (q + 1) * s)) for q in range(k)}
+
+
+# ------------------------------------------------------ clustering hierarchy
+# Clustering without a partitioning target (Sec. 3.1 clustering and
+# contraction, repeated as in the coarsening phase).
+
+def _hierarchy_by_hand(g, U, stop, seed, cfg):
+    """The repetition written out: cluster, contract, keep the contraction
+    only if it removes >= 5% of the nodes, compose the maps."""
+    comm = np.arange(g.n)
+    sizes = [g.n]
+    cur, level = g, 0
+    while cur.n > stop and level + 1 < cfg.max_levels:
+        lab, _ = O.cluster(cur, U, seed, level=level, cfg=cfg)
+        c = O.contract(cur, lab)
+        if 20 * (cur.n - c.n) < cur.n:
+            break
+        comm = c.cmap[comm]
+        cur = gg.Graph(c.row_ptr, c.col, c.node_w, c.edge_w)
+        level += 1
+        sizes.append(cur.n)
+    return comm, level, sizes
+
+
+@pytest.mark.parametrize("maker", [lambda: gg.rmat(12, 8, 3), lambda: gg.rgg2d(3000, 2),
+                                   lambda: gg.random_weights(gg.rmat(11, 8, 1), 2)])
+def test_cluster_hierarchy_is_repeated_cluster_and_contract(maker):
+    g = maker()
+    cfg = O.config()
+    for U, stop in ((30, 100), (200, 1)):
+        comm, levels, sizes = O.cluster_hierarchy(g, U, stop, 9, cfg=cfg)
+        ref = _hierarchy_by_hand(g, U, stop, 9, cfg)
+        assert levels == ref[1] and sizes == ref[2]
+        assert np.array_equal(comm, ref[0])
+        # every community is a coarse node: at most U in weight
+        assert np.bincount(comm, weights=g.node_w).max() <= U
+
+
+def test_cluster_hierarchy_special_cases():
+    g = gg.rmat(10, 8, 2)
+    comm, levels, sizes = O.cluster_hierarchy(g, 1, 1, 0)      # U = 1: nothing merges
+    assert levels == 0 and sizes == [g.n] and np.array_equal(comm, np.arange(g.n))
+    comm, levels, _ = O.cluster_hierarchy(g, 50, g.n, 0)       # already small enough
+    assert levels == 0 and np.array_equal(comm, np.arange(g.n))
+    # cliques of size s joined in a ring, U = s: one contraction finds the
+    # cliques, after which no cluster can grow and the hierarchy stops
+    k, s = 12, 9
+    g = gg.clique_ring(k, s)
+    comm, levels, sizes = O.cluster_hierarchy(g, s, 1, 5)
+    assert levels == 1 and sizes == [k * s, k]
+    for q in range(k):
+        assert len(set(comm[q * s:(q + 1) * s])) == 1
+    assert len(set(comm)) == k
