@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--graph-rounds", action="store_true",
+                    help="run each level's LP rounds as one CUDA graph (device-side loop)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--phases", action="store_true",
                     help="print per-sub-round propose/admission times grouped by run kind "
@@ -307,9 +309,10 @@ def main():
     arcs_in = sum(g.arcs for g, _, _ in graphs)
     torch.cuda.synchronize()
 
+    cfg = P.default_config(graph_rounds=1 if args.graph_rounds else 0)
     ref = None
     for _ in range(args.warmup):
-        ref = P.sclap_partition_batch(items, device=True)
+        ref = P.sclap_partition_batch(items, cfg=cfg, device=True)
     torch.cuda.synchronize()
     ref_cuts = [r.cut for r in ref]
 
@@ -325,7 +328,7 @@ def main():
     e0.record(stream)
     last = None
     for _ in range(args.steps):
-        last = P.sclap_partition_batch(items, device=True)
+        last = P.sclap_partition_batch(items, cfg=cfg, device=True)
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -340,7 +343,7 @@ def main():
     torch.cuda.synchronize()
     p0.record(stream)
     for _ in range(args.steps):
-        P.sclap_partition_batch(items, device=True)
+        P.sclap_partition_batch(items, cfg=cfg, device=True)
     p1.record(stream)
     torch.cuda.synchronize()
     P.sclap_profile_enable(False)
@@ -393,11 +396,13 @@ def main():
                        for b in range(4)},
     }
 
+    conf = config_dict(len(graphs), ws)
+    conf["lp_rounds_driver"] = "cuda-graph (WHILE node per level)" if args.graph_rounds else "host"
     line = {
         "metric": "partitions/s", "value": value, "unit": "partitions/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
-        "data": "synthetic", "config": config_dict(len(graphs), ws),
+        "data": "synthetic", "config": conf,
         "sclap_edges_per_s": swept / (elapsed_ms / 1000.0) * (ws if ws > 1 else 1),
         "input_edges_per_s": arcs_in / 2 * args.steps * ws / (elapsed_ms / 1000.0),
         "deterministic": deterministic, "balanced": balanced,

@@ -64,6 +64,12 @@ enum {
  * coarsening down to max(1000, 60k) nodes, 16 initial-partitioning trials,
  * 8 colour classes per synchronous round, 64 repair rounds, 64 levels, and
  * clustering without active nodes.
+ * graph_rounds = 1 runs each level's LP rounds as one CUDA graph: a
+ * conditional WHILE node around one round, whose condition the device sets
+ * at the end of the round, so the host neither waits nor decides between
+ * rounds (it then launches every bucket's kernel; empty ones exit at once).
+ * 0 (default) drives the rounds from the host, which reads the bucket sizes
+ * once per round and skips empty launches.  Results are identical.
  * cluster_active = 1 turns on active nodes during coarsening (Sec. 4 "Active
  * Nodes", configuration A of Table 2): after the first round a clustering
  * round visits only nodes with a neighbour that changed its cluster in the
@@ -80,6 +86,7 @@ typedef struct sclap_config {
   int32_t repair_rounds;
   int32_t max_levels;
   int32_t cluster_active;
+  int32_t graph_rounds;
 } sclap_config;
 
 /* Per-call statistics (optional output). */

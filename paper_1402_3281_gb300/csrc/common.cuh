@@ -317,7 +317,10 @@ void scan_excl_occupied(const int32_t* keys, int64_t* out, int64_t n, cudaStream
 void scan_excl_occupied_slots(const unsigned long long* slots, int64_t* out, int64_t n,
                               cudaStream_t s);
 // largest row length (atomicMax into *out, which the caller zeroes)
-void level_max_degree(const int64_t* row_ptr, int64_t N, int64_t* out, cudaStream_t s);
+// out[0] = largest degree of the level, out[1] = nodes with degree > thr
+// (out zeroed by the caller).
+void level_degree_stats(const int64_t* row_ptr, int64_t N, int64_t thr, int64_t* out,
+                        cudaStream_t s);
 // slot id of every node from node offsets
 void fill_gid(const int64_t* noff, int32_t nslots, int32_t* gid, int64_t N, cudaStream_t s);
 
@@ -331,6 +334,7 @@ struct LPRun {
   bool stop_rule = true;       // 5% rule (not in repair)
   bool use_active = false;     // local search: active nodes
   bool raw_key = false;        // slot seed is used as the round key itself
+  bool graph = false;          // run the rounds as one CUDA graph (WHILE node)
 };
 // Runs `run.rounds` synchronous LP rounds on `lv` for every slot not marked
 // done; label/W are updated in place.  Returns the number of arcs scanned.

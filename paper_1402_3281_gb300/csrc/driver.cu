@@ -40,7 +40,8 @@ sclap_config resolve_cfg(const sclap_config* c) {
   if (c) r = *c;
   if (r.lp_rounds_coarse < 0 || r.lp_rounds_refine < 0 || r.f < 1 || r.coarse_min_nodes < 1 ||
       r.ip_trials < 1 || r.sub_rounds < 1 || r.sub_rounds > 64 || r.repair_rounds < 0 ||
-      r.max_levels < 1 || r.cluster_active < 0 || r.cluster_active > 1)
+      r.max_levels < 1 || r.cluster_active < 0 || r.cluster_active > 1 || r.graph_rounds < 0 ||
+      r.graph_rounds > 1)
     throw Error(SCLAP_EINVAL, "invalid sclap_config");
   return r;
 }
@@ -479,6 +480,7 @@ void run_ip(const std::vector<IPIn>& in, const sclap_config& cfg, wgt_t* Wg,
   run.phase = PH_IPREF;
   run.rounds = cfg.lp_rounds_refine;
   run.sub_rounds = cfg.sub_rounds;
+  run.graph = cfg.graph_rounds != 0;
   run.use_active = true;
   *lp_arcs += lp_run(ip.view(), sl.sp, label.p, W.p, K, run, d_err, s);
 
@@ -618,6 +620,7 @@ void run_valid_batch(const std::vector<GIn>& gs, const std::vector<int64_t>& cV,
     run.phase = PH_CLUSTER;
     run.rounds = cfg.lp_rounds_coarse;
     run.sub_rounds = cfg.sub_rounds;
+    run.graph = cfg.graph_rounds != 0;
     run.use_active = cfg.cluster_active != 0;
     lp_arcs += lp_run(v, sl.sp, label.p, W.p, v.N, run, d_err.p, s);
     const std::vector<int32_t> rr = sl.host_rounds(s);
@@ -713,6 +716,7 @@ void run_valid_batch(const std::vector<GIn>& gs, const std::vector<int64_t>& cV,
     run.phase = PH_REFINE;
     run.rounds = cfg.lp_rounds_refine;
     run.sub_rounds = cfg.sub_rounds;
+    run.graph = cfg.graph_rounds != 0;
     run.use_active = true;
     lp_arcs += lp_run(F.view(), sl.sp, F.blk.p, Wg.p, Ktot, run, d_err.p, s);
     const std::vector<int32_t> rr = sl.host_rounds(s);
@@ -730,6 +734,7 @@ void run_valid_batch(const std::vector<GIn>& gs, const std::vector<int64_t>& cV,
     run.phase = PH_REPAIR;
     run.rounds = cfg.repair_rounds;
     run.sub_rounds = cfg.sub_rounds;
+    run.graph = cfg.graph_rounds != 0;
     run.stop_rule = false;
     lp_arcs += lp_run(F0.view(), sl.sp, F0.blk.p, Wg.p, Ktot, run, d_err.p, s);
   }
@@ -899,6 +904,7 @@ void sclap_default_config(sclap_config* c) {
   c->repair_rounds = 64;
   c->max_levels = 64;
   c->cluster_active = 0;
+  c->graph_rounds = 0;
 }
 
 const char* sclap_error_string(int code) {
@@ -1111,6 +1117,7 @@ int sclap_cluster(int64_t n, const int64_t* row_ptr, const int32_t* col, const i
     run.phase = PH_CLUSTER;
     run.rounds = c.lp_rounds_coarse;
     run.sub_rounds = c.sub_rounds;
+    run.graph = c.graph_rounds != 0;
     run.use_active = c.cluster_active != 0;
     DevBuf<int32_t> d_err(1, s);
     d_err.zero();
@@ -1156,6 +1163,7 @@ int sclap_cluster_hierarchy(int64_t n, const int64_t* row_ptr, const int32_t* co
       run.phase = PH_CLUSTER;
       run.rounds = c.lp_rounds_coarse;
       run.sub_rounds = c.sub_rounds;
+      run.graph = c.graph_rounds != 0;
       run.use_active = c.cluster_active != 0;
       lp_run(v, sl.sp, label.p, W.p, v.N, run, d_err.p, s);
       ContractWork cw;
@@ -1284,6 +1292,7 @@ int sclap_refine(int64_t n, const int64_t* row_ptr, const int32_t* col, const in
     run.phase = phase;
     run.rounds = c.lp_rounds_refine;
     run.sub_rounds = c.sub_rounds;
+    run.graph = c.graph_rounds != 0;
     run.use_active = true;
     DevBuf<int32_t> d_err(1, s);
     d_err.zero();

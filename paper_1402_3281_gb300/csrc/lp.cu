@@ -73,11 +73,32 @@ struct LPArgs {
   int64_t* karcs;        // arcs per (colour, bucket) key
   int32_t* flags;        // [0]: a listed node sits in an overloaded block
   int16_t* nkey;         // bucket key of each node this round (-1: not listed)
-  // active nodes
-  const uint8_t* act_cur;
-  uint8_t* act_next;
+  // active nodes: act[r & 1] holds round r's flags, act[(r + 1) & 1] the
+  // next round's (both NULL when all nodes are always active)
+  uint8_t* act[2];
+  // round state on the device, so that a level's rounds need no host
+  // decision: the round index, slots still running after k_round_end, and
+  // the limits of the run
+  int32_t* rnd;
+  int32_t* live;
+  int32_t rounds_max;
+  int32_t stop_rule;
   int32_t* err;
 };
+
+__device__ __forceinline__ const uint8_t* act_cur(const LPArgs& a) {
+  return a.act[0] ? a.act[a.rnd[0] & 1] : nullptr;
+}
+__device__ __forceinline__ uint8_t* act_next(const LPArgs& a) {
+  return a.act[0] ? a.act[(a.rnd[0] + 1) & 1] : nullptr;
+}
+// Node range [beg, beg + cnt) of buckets [b0, b1) of colour class `sub`,
+// read on the device from the bucketing offsets.
+__device__ __forceinline__ void sub_range(const LPArgs& a, int sub, int b0, int b1,
+                                          int64_t* beg, int64_t* cnt) {
+  *beg = a.boff[sub * NB + b0];
+  *cnt = a.boff[sub * NB + b1] - *beg;
+}
 
 struct NodeCtx {
   int32_t v, slot, own, cv;
@@ -120,8 +141,10 @@ __device__ __forceinline__ void write_prop(const LPArgs& a, int64_t i, const Nod
 }
 
 // ------------------------------------------------------------- round control
-__global__ void k_round_begin(LPArgs a, int32_t nslots, int32_t phase, int32_t r,
+__global__ void k_round_begin(LPArgs a, int32_t nslots, int32_t phase,
                               const uint64_t* seed, const int32_t* level, int32_t raw_key) {
+  const int32_t r = a.rnd[0];
+  if (blockIdx.x == 0 && threadIdx.x == 0) a.live[0] = 0;
   for (int32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < nslots;
        s += gridDim.x * blockDim.x) {
     if (a.done[s]) continue;
@@ -136,14 +159,29 @@ __global__ void k_round_begin(LPArgs a, int32_t nslots, int32_t phase, int32_t r
   }
 }
 
-__global__ void k_round_end(LPArgs a, int32_t nslots, int32_t stop_rule) {
+__global__ void k_round_end(LPArgs a, int32_t nslots) {
+  int live = 0;
   for (int32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < nslots;
        s += gridDim.x * blockDim.x) {
     if (a.done[s]) continue;
     a.rounds[s] += 1;
     const int64_t n = a.noff[s + 1] - a.noff[s];
-    if (stop_rule && 20 * a.moved[s] < n) a.done[s] = 1;
+    if (a.stop_rule && 20 * a.moved[s] < n) a.done[s] = 1;
+    else ++live;
   }
+  if (live) atomicAdd(a.live, live);
+}
+
+// Decides whether the run goes on: another round is allowed, the round just
+// finished listed some node, and some slot is still running.  Advances the
+// round index and, inside a graph, sets the loop's condition.
+__global__ void k_round_cond(LPArgs a, int32_t nkeys, cudaGraphConditionalHandle h,
+                             int32_t use_handle, int32_t* cont) {
+  const int32_t r = a.rnd[0];
+  const bool more = r + 1 < a.rounds_max && a.boff[nkeys] > 0 && a.live[0] > 0;
+  a.rnd[0] = r + 1;
+  cont[0] = more ? 1 : 0;
+  if (use_handle) cudaGraphSetConditional(h, more ? 1u : 0u);
 }
 
 // ------------------------------------------------------------- bucketing
@@ -156,18 +194,18 @@ constexpr int BK_PER = 8;                    // nodes per thread
 constexpr int BK_TILE = BK_NT * BK_PER;      // nodes per block
 constexpr int MAX_KEYS = 64 * NB;
 
-__device__ __forceinline__ int node_key(const LPArgs& a, int64_t v, int64_t* deg_out,
-                                        bool* ov_out) {
+__device__ __forceinline__ int node_key(const LPArgs& a, const uint8_t* ac, int64_t v,
+                                        int64_t* deg_out, bool* ov_out) {
   const int32_t s = a.gid[v];
   if (a.done[s]) return -1;
   const int64_t deg = a.row_ptr[v + 1] - a.row_ptr[v];
   bool take, ov = false;
   if (a.mode == MODE_CLUSTER) {
-    take = deg > 0 && (a.act_cur == nullptr || a.act_cur[v]);
+    take = deg > 0 && (ac == nullptr || ac[v]);
   } else {
     ov = a.W[a.label[v]] > a.bound[s];
     if (a.mode == MODE_REPAIR) take = ov;
-    else take = (a.act_cur == nullptr || a.act_cur[v]) && (deg > 0 || ov);
+    else take = (ac == nullptr || ac[v]) && (deg > 0 || ov);
   }
   if (!take) return -1;
   const uint64_t hv = mix64(a.rkey[s] ^ (uint64_t)(v - a.noff[s]));
@@ -187,13 +225,16 @@ __global__ void __launch_bounds__(BK_NT) k_bucket_count(LPArgs a, int64_t N) {
   __syncthreads();
   const int64_t base = (int64_t)blockIdx.x * BK_TILE;
   bool any_ov = false;
+  const uint8_t* ac = act_cur(a);
+  uint8_t* an = act_next(a);
 #pragma unroll
   for (int j = 0; j < BK_PER; ++j) {
     const int64_t v = base + (int64_t)j * BK_NT + threadIdx.x;
     if (v >= N) break;
+    if (an) an[v] = 0;                 // next round's flags start cleared
     int64_t deg = 0;
     bool ov = false;
-    const int key = node_key(a, v, &deg, &ov);
+    const int key = node_key(a, ac, v, &deg, &ov);
     a.nkey[v] = (int16_t)key;
     if (key >= 0) {
       atomicAdd(&sh_cnt[key], 1);
@@ -243,13 +284,15 @@ __global__ void __launch_bounds__(BK_NT) k_bucket_scatter(LPArgs a, int64_t N) {
 
 __global__ void k_bucket_offsets(LPArgs a, int nkeys) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
-    int64_t s = 0;
+    int64_t s = 0, arcs = 0;
     for (int j = 0; j < nkeys; ++j) {
       a.boff[j] = s;
       s += a.bcnt[j];
       a.bfill[j] = 0;
+      arcs += a.karcs[j];
     }
     a.boff[nkeys] = s;
+    a.arcs[0] += arcs;
   }
 }
 
@@ -334,15 +377,39 @@ __device__ __forceinline__ void propose_thread(const LPArgs& a, int64_t lbeg, in
 // The small-degree buckets of one sub-round in one launch: block ranges
 // [bs[j], bs[j+1]) serve bucket j (degree <= 4, <= 8, <= 16), one thread per
 // node.
-struct SmallLaunch {
-  int64_t beg[3], cnt[3];
-  int32_t bs[4];
-};
-__global__ void __launch_bounds__(256, 4) k_propose_small(LPArgs a, SmallLaunch L) {
-  const int32_t b = blockIdx.x;
-  if (b < L.bs[1]) propose_thread<4>(a, L.beg[0], L.cnt[0], b - L.bs[0], L.bs[1] - L.bs[0]);
-  else if (b < L.bs[2]) propose_thread<8>(a, L.beg[1], L.cnt[1], b - L.bs[1], L.bs[2] - L.bs[1]);
-  else propose_thread<16>(a, L.beg[2], L.cnt[2], b - L.bs[2], L.bs[3] - L.bs[2]);
+// The grid is split among the three buckets in proportion to the blocks each
+// needs (256 nodes per block), every non-empty bucket getting at least one;
+// every block computes the same split from the device offsets.
+__global__ void __launch_bounds__(256, 4) k_propose_small(LPArgs a, int32_t sub) {
+  const int64_t* bo = a.boff + sub * NB;
+  int64_t c[3], need[3], tot = 0;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    c[j] = bo[j + 1] - bo[j];
+    need[j] = (c[j] + 255) / 256;
+    tot += need[j];
+  }
+  if (tot == 0) return;
+  const int64_t G = gridDim.x;
+  int64_t g[3];
+  if (tot <= G) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) g[j] = need[j];
+  } else {
+    int64_t used = 0;
+    int last = 0;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      g[j] = c[j] ? max64(1, G * need[j] / tot) : 0;
+      used += g[j];
+      if (c[j]) last = j;
+    }
+    g[last] += G - used;
+  }
+  const int64_t b = blockIdx.x;
+  if (b < g[0]) propose_thread<4>(a, bo[0], c[0], b, g[0]);
+  else if (b < g[0] + g[1]) propose_thread<8>(a, bo[1], c[1], b - g[0], g[1]);
+  else if (b < g[0] + g[1] + g[2]) propose_thread<16>(a, bo[2], c[2], b - g[0] - g[1], g[2]);
 }
 
 // Open-addressing accumulation (linear probing, bounded).
@@ -431,9 +498,12 @@ __device__ void block_reduce(long long& oc, Cand& cd, long long* sh_oc, Cand* sh
 // (open addressing); local search with k no larger than the table indexes
 // it by block id directly.
 template <int NT, int SLOTS, bool GLOBAL>
-__global__ void __launch_bounds__(NT) k_propose_cta(LPArgs a, int64_t lbeg, int64_t cnt,
+__global__ void __launch_bounds__(NT) k_propose_cta(LPArgs a, int32_t sub, int32_t bucket,
                                                     int32_t* gkeys, unsigned long long* gvals,
                                                     int64_t gcap) {
+  int64_t lbeg, cnt;
+  sub_range(a, sub, bucket, bucket + 1, &lbeg, &cnt);
+  if (cnt == 0) return;
   extern __shared__ unsigned long long smem_u64[];
   __shared__ long long sh_oc[NT / 32];
   __shared__ Cand sh_cd[NT / 32];
@@ -522,7 +592,10 @@ constexpr int WLOG = 8;                      // log2(WCAP)
 constexpr int WPC = 8;                       // warps per CTA
 static_assert((1 << WLOG) == WCAP, "WCAP must be 2^WLOG");
 
-__global__ void __launch_bounds__(WPC * 32) k_propose_warp(LPArgs a, int64_t lbeg, int64_t cnt) {
+__global__ void __launch_bounds__(WPC * 32) k_propose_warp(LPArgs a, int32_t sub) {
+  int64_t lbeg, cnt;
+  sub_range(a, sub, 3, 5, &lbeg, &cnt);     // buckets 3 and 4 are adjacent
+  if (cnt == 0) return;
   __shared__ unsigned long long sh_vals[WPC][WCAP];
   __shared__ int32_t sh_keys[WPC][WCAP];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -638,7 +711,10 @@ constexpr size_t blk_smem_bytes() {
 }
 
 template <int NT, int SLOTS>
-__global__ void __launch_bounds__(NT) k_propose_blk(LPArgs a, int64_t lbeg, int64_t cnt) {
+__global__ void __launch_bounds__(NT) k_propose_blk(LPArgs a, int32_t sub, int32_t bucket) {
+  int64_t lbeg, cnt;
+  sub_range(a, sub, bucket, bucket + 1, &lbeg, &cnt);
+  if (cnt == 0) return;
   extern __shared__ unsigned long long smem_u64[];
   __shared__ long long sh_oc[NT / 32];
   __shared__ Cand sh_cd[NT / 32];
@@ -758,7 +834,9 @@ __global__ void __launch_bounds__(NT) k_propose_blk(LPArgs a, int64_t lbeg, int6
 }
 
 // ------------------------------------------------------------- admission
-__global__ void k_resolve(LPArgs a, int64_t lbeg, int64_t cnt) {
+__global__ void k_resolve(LPArgs a, int32_t sub) {
+  int64_t lbeg, cnt;
+  sub_range(a, sub, 0, NB, &lbeg, &cnt);
   for (int64_t li = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; li < cnt;
        li += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = lbeg + li;
@@ -778,7 +856,10 @@ __global__ void k_resolve(LPArgs a, int64_t lbeg, int64_t cnt) {
 }
 
 // Forced moves out of overloaded blocks (local search), grouped by source.
-__global__ void k_forced(LPArgs a, int64_t lbeg, int64_t cnt) {
+__global__ void k_forced(LPArgs a, int32_t sub) {
+  if (a.flags[0] == 0) return;              // no listed node in an overloaded block
+  int64_t lbeg, cnt;
+  sub_range(a, sub, 0, NB, &lbeg, &cnt);
   for (int64_t li = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; li < cnt;
        li += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = lbeg + li;
@@ -797,7 +878,10 @@ __global__ void k_forced(LPArgs a, int64_t lbeg, int64_t cnt) {
 // One leader per group allocates the group's segment.  thr: target side,
 // admit while the inclusive prefix <= bound - W[t]; source side, admit while
 // the exclusive prefix <= W[src] - bound - 1.
-__global__ void k_ovf_alloc(LPArgs a, int64_t lbeg, int64_t cnt, int32_t source) {
+__global__ void k_ovf_alloc(LPArgs a, int32_t sub, int32_t source) {
+  if (source && a.flags[0] == 0) return;    // source side idle this round
+  int64_t lbeg, cnt;
+  sub_range(a, sub, 0, NB, &lbeg, &cnt);
   for (int64_t li = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; li < cnt;
        li += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = lbeg + li;
@@ -815,7 +899,10 @@ __global__ void k_ovf_alloc(LPArgs a, int64_t lbeg, int64_t cnt, int32_t source)
   }
 }
 
-__global__ void k_ovf_scatter(LPArgs a, int64_t lbeg, int64_t cnt) {
+__global__ void k_ovf_scatter(LPArgs a, int32_t sub, int32_t source) {
+  if (source && a.flags[0] == 0) return;
+  int64_t lbeg, cnt;
+  sub_range(a, sub, 0, NB, &lbeg, &cnt);
   for (int64_t li = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; li < cnt;
        li += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = lbeg + li;
@@ -1100,7 +1187,10 @@ __device__ __forceinline__ void apply_delta(int32_t* hk, int32_t* hv, wgt_t* W, 
   atomicAdd(&W[L], (wgt_t)d);
 }
 
-__global__ void __launch_bounds__(256) k_apply(LPArgs a, int64_t lbeg, int64_t cnt) {
+__global__ void __launch_bounds__(256) k_apply(LPArgs a, int32_t sub) {
+  int64_t lbeg, cnt;
+  sub_range(a, sub, 0, NB, &lbeg, &cnt);
+  uint8_t* const an = act_next(a);
   __shared__ int32_t hk[APPLY_SLOTS];
   __shared__ int32_t hv[APPLY_SLOTS];
   for (int j = threadIdx.x; j < APPLY_SLOTS; j += blockDim.x) { hk[j] = -1; hv[j] = 0; }
@@ -1124,7 +1214,7 @@ __global__ void __launch_bounds__(256) k_apply(LPArgs a, int64_t lbeg, int64_t c
           const int4 r = a.rec[i];
           const int32_t v = r.x, own = r.y, cv = r.z;
           slot = r.w;
-          if (a.act_next) {
+          if (an) {
             const longlong2 r2 = a.rec2[i];
             rs = r2.x;
             re = r2.x + r2.y;
@@ -1133,7 +1223,7 @@ __global__ void __launch_bounds__(256) k_apply(LPArgs a, int64_t lbeg, int64_t c
           apply_delta(hk, hv, a.W, t, cv);
           apply_delta(hk, hv, a.W, own, -cv);
           if (re - rs <= 8) {
-            for (int64_t e = rs; e < re; ++e) a.act_next[a.col[e]] = 1;
+            for (int64_t e = rs; e < re; ++e) an[a.col[e]] = 1;
             re = rs;
           }
         }
@@ -1145,7 +1235,7 @@ __global__ void __launch_bounds__(256) k_apply(LPArgs a, int64_t lbeg, int64_t c
       big &= big - 1;
       const int64_t s0 = __shfl_sync(0xffffffffu, (long long)rs, src);
       const int64_t s1 = __shfl_sync(0xffffffffu, (long long)re, src);
-      for (int64_t e = s0 + lane; e < s1; e += 32) a.act_next[a.col[e]] = 1;
+      for (int64_t e = s0 + lane; e < s1; e += 32) an[a.col[e]] = 1;
     }
     const unsigned mm = __match_any_sync(0xffffffffu, slot);
     if (slot >= 0 && lane == __ffs(mm) - 1) {
@@ -1165,6 +1255,13 @@ __global__ void __launch_bounds__(256) k_apply(LPArgs a, int64_t lbeg, int64_t c
 }
 
 }  // namespace
+
+// Stream on which this thread captures graphs (non-blocking, created once).
+cudaStream_t capture_stream() {
+  thread_local cudaStream_t cs = nullptr;
+  if (!cs) SCLAP_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  return cs;
+}
 
 // Side streams for concurrent launches (non-blocking, created on first use
 // and kept).  Each host thread has its own, so callers running partitions
@@ -1305,7 +1402,6 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, wgt_t*
 
   // Global hash scratch for hub nodes: one region per CTA, sized for the
   // largest degree of the level.
-  int64_t maxdeg = 0;
   int64_t gcap = 0;
   DevBuf<int32_t> gkeys;
   DevBuf<unsigned long long> gvals;
@@ -1326,18 +1422,38 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, wgt_t*
   a.nkey = nkey.p;
   a.err = d_err;
 
-  std::vector<int64_t> hoff(nkeys + 1), hkarcs(nkeys);
-  const bool prof = profile().enabled.load();
-  struct Timed { int family; cudaEvent_t a, b; };
-  std::vector<Timed> timed;
-  // per sub-round record: kind of run, round, colour class, nodes, arcs and
-  // events at fork, join (end of the propose phase) and after apply
-  struct PhaseRec { int32_t ph, r, sub; int64_t nodes, arcs; cudaEvent_t a, b, c; };
-  std::vector<PhaseRec> precs;
-  int64_t pn[4] = {}, pa[4] = {};
-  int32_t hflags = 0;
-  int64_t arcs_total = 0;
-  const unsigned small_grid = (unsigned)(sms * 8);
+  // ---- round-invariant setup ---------------------------------------------
+  DevBuf<int32_t> rstate(3, s);        // round index, live slots, continue flag
+  rstate.zero();
+  a.rnd = rstate.p;
+  a.live = rstate.p + 1;
+  int32_t* const d_cont = rstate.p + 2;
+  a.rounds_max = run.rounds;
+  a.stop_rule = run.stop_rule ? 1 : 0;
+  a.act[0] = track_active ? act_a.p : nullptr;
+  a.act[1] = track_active ? act_b.p : nullptr;
+
+  // The level's degrees decide which propose launches can ever have work
+  // (and size the hub tables): one read-back per run, none per round.
+  DevBuf<int64_t> dstat(2, s);
+  dstat.zero();
+  level_degree_stats(lv.row_ptr, N, B7_MAXDEG, dstat.p, s);
+  int64_t hstat[2] = {0, 0};
+  SCLAP_CUDA(cudaMemcpyAsync(hstat, dstat.p, sizeof(hstat), cudaMemcpyDeviceToHost, s));
+  stream_sync(s);
+  const int64_t maxdeg = hstat[0], nhubs = hstat[1];
+  const bool refine = run.mode != MODE_CLUSTER;
+  const bool need[NB] = {true, true, true, refine || maxdeg > 16, false,
+                         maxdeg > B4_MAXDEG, maxdeg > B5_MAXDEG, maxdeg > B6_MAXDEG,
+                         maxdeg > B7_MAXDEG};
+  if (need[8]) {
+    gcap = (int64_t)1 << ceil_log2(std::max<int64_t>(2 * maxdeg, 32));
+    gblocks = (int)std::max<int64_t>(1, std::min<int64_t>(sms * 2, nhubs));
+    gkeys.alloc((size_t)(gblocks * gcap), s);
+    gvals.alloc((size_t)(gblocks * gcap), s);
+    gkeys.fill_bytes(0xff);
+    gvals.zero();
+  }
   constexpr size_t smem5 = blk_smem_bytes<B5_SLOTS>();
   constexpr size_t smem6 = blk_smem_bytes<B6_SLOTS>();
   constexpr size_t smem7 = blk_smem_bytes<B7_SLOTS>();
@@ -1348,192 +1464,256 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, wgt_t*
     SCLAP_CUDA(cudaFuncSetAttribute(k_propose_blk<512, B7_SLOTS>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem7));
   });
+  // fixed launch shapes: kernels read their node ranges on the device and
+  // grid-stride over them
+  const unsigned nsl_grid = grid_for(sp.nslots, 128, 1024);
+  const unsigned bgrid = (unsigned)((N + BK_TILE - 1) / BK_TILE);
+  const unsigned grid_small = (unsigned)(sms * 8), grid_warp = (unsigned)(sms * 8);
+  const unsigned grid_b5 = (unsigned)(sms * 16), grid_b6 = (unsigned)(sms * 4);
+  const unsigned grid_b7 = (unsigned)sms, grid_adm_max = (unsigned)(sms * 16);
+  const unsigned grid_sel = (unsigned)(sms * 4);
+  const int32_t raw = run.raw_key ? 1 : 0;
 
-  for (int r = 0; r < run.rounds; ++r) {
-    a.act_cur = track_active ? act_a.p : nullptr;
-    a.act_next = track_active ? act_b.p : nullptr;
-    k_round_begin<<<grid_for(sp.nslots, 128, 1024), 128, 0, s>>>(a, sp.nslots, run.phase, r,
-                                                                  sp.seed, sp.level,
-                                                                  run.raw_key ? 1 : 0); SCLAP_NOTE_LAUNCH("k_round_begin");
-    bcnt.zero();
-    karcs.zero();
-    flags.zero();
-    const unsigned bgrid = (unsigned)((N + BK_TILE - 1) / BK_TILE);
+  // ---- one round, as launches on s (shared by both drivers) ----------------
+  // (every operation of a round goes to the stream passed in: the caller's
+  // stream when driven directly, the capture stream when building the graph)
+  auto head = [&](cudaStream_t s) {
+    k_round_begin<<<nsl_grid, 128, 0, s>>>(a, sp.nslots, run.phase, sp.seed, sp.level, raw); SCLAP_NOTE_LAUNCH("k_round_begin");
+    SCLAP_CUDA(cudaMemsetAsync(bcnt.p, 0, nkeys * sizeof(int32_t), s));
+    SCLAP_CUDA(cudaMemsetAsync(karcs.p, 0, nkeys * sizeof(int64_t), s));
+    SCLAP_CUDA(cudaMemsetAsync(flags.p, 0, sizeof(int32_t), s));
     k_bucket_count<<<bgrid, BK_NT, 0, s>>>(a, N); SCLAP_NOTE_LAUNCH("k_bucket_count");
     k_bucket_offsets<<<1, 32, 0, s>>>(a, nkeys); SCLAP_NOTE_LAUNCH("k_bucket_offsets");
     k_bucket_scatter<<<bgrid, BK_NT, 0, s>>>(a, N); SCLAP_NOTE_LAUNCH("k_bucket_scatter");
     SCLAP_LAUNCH_CHECK();
-    SCLAP_CUDA(cudaMemcpyAsync(hoff.data(), boff.p, (nkeys + 1) * sizeof(int64_t),
-                               cudaMemcpyDeviceToHost, s));
-    SCLAP_CUDA(cudaMemcpyAsync(hkarcs.data(), karcs.p, nkeys * sizeof(int64_t),
-                               cudaMemcpyDeviceToHost, s));
-    SCLAP_CUDA(cudaMemcpyAsync(&hflags, flags.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    stream_sync(s);
-    for (int j = 0; j < nkeys; ++j) arcs_total += hkarcs[j];
-    if (hoff[nkeys] == 0) {
-      k_round_end<<<grid_for(sp.nslots, 128, 1024), 128, 0, s>>>(a, sp.nslots,
-                                                                  run.stop_rule ? 1 : 0); SCLAP_NOTE_LAUNCH("k_round_end");
-      break;
+  };
+  // Per-launch profiling of the direct driver (host offsets known).
+  struct Timed { int family; cudaEvent_t a, b; };
+  std::vector<Timed> timed;
+  int64_t pn[4] = {}, pa[4] = {};
+  std::vector<int64_t> hoff(nkeys + 1), hkarcs(nkeys);
+  const bool prof = profile().enabled.load();
+  const bool timeline = profile().timeline.load(std::memory_order_relaxed);
+  // The propose launches of a colour class are independent of one another:
+  // they run on side streams joined back by events, so latency-bound
+  // launches overlap (serial when the timeline profiler is on).  With host
+  // offsets (direct driver) empty launches are skipped and, when profiling,
+  // each launch is timed and its nodes and arcs tallied by family.
+  auto propose = [&](cudaStream_t s, int sub, bool fork, const int64_t* ho) {
+    cudaEvent_t ev_fork = nullptr;
+    if (fork) {
+      ev_fork = sync_event_get();
+      SCLAP_CUDA(cudaEventRecord(ev_fork, s));
     }
-    // global hash scratch for the hub bucket, sized on first need
-    int64_t nhub = 0;
-    for (int sub = 0; sub < S; ++sub) nhub += hoff[sub * NB + 8 + 1] - hoff[sub * NB + 8];
-    if (nhub > 0 && gcap == 0) {
-      // largest degree of the level, read once
-      DevBuf<int64_t> dmax(1, s);
-      dmax.zero();
-      level_max_degree(lv.row_ptr, N, dmax.p, s);
-      SCLAP_CUDA(cudaMemcpyAsync(&maxdeg, dmax.p, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-      stream_sync(s);
-      gcap = (int64_t)1 << ceil_log2(std::max<int64_t>(2 * maxdeg, 32));
-      gblocks = std::max(1, std::min(sms * 2, (int)std::min<int64_t>(nhub * 4, 1 << 20)));
-      gkeys.alloc((size_t)(gblocks * gcap), s);
-      gvals.alloc((size_t)(gblocks * gcap), s);
-      gkeys.fill_bytes(0xff);
-      gvals.zero();
+    int nside = 0;
+    cudaStream_t joined[NB];
+    auto lane = [&]() -> cudaStream_t {
+      if (!fork) return s;
+      cudaStream_t ss = side_stream(nside);
+      SCLAP_CUDA(cudaStreamWaitEvent(ss, ev_fork, 0));
+      joined[nside++] = ss;
+      return ss;
+    };
+    // buckets [b0, b1) of this colour class in one launch of family fam
+    auto launch = [&](int b0, int b1, int fam, auto&& fn) {
+      if (ho && ho[sub * NB + b1] == ho[sub * NB + b0]) return;
+      cudaStream_t ls = lane();
+      Timed tm{fam, nullptr, nullptr};
+      if (prof && ho) {
+        tm.a = event_from_pool();
+        tm.b = event_from_pool();
+        SCLAP_CUDA(cudaEventRecord(tm.a, ls));
+        pn[fam] += ho[sub * NB + b1] - ho[sub * NB + b0];
+        for (int q = b0; q < b1; ++q) pa[fam] += hkarcs[sub * NB + q];
+      }
+      fn(ls);
+      if (prof && ho) {
+        SCLAP_CUDA(cudaEventRecord(tm.b, ls));
+        timed.push_back(tm);
+      }
+    };
+    // grid of a launch over buckets [b0, b1): sized from the host counts
+    // when known, else the fixed maximum (kernels grid-stride either way)
+    auto grid = [&](int b0, int b1, int per, unsigned cap) -> unsigned {
+      if (!ho) return cap;
+      if (b0 == 0) {                  // one block per 256 nodes of each bucket
+        int64_t nb = 0;
+        for (int q = 0; q < 3; ++q) nb += (ho[sub * NB + q + 1] - ho[sub * NB + q] + 255) / 256;
+        return (unsigned)std::max<int64_t>(1, std::min<int64_t>(nb, cap));
+      }
+      return grid_for(ho[sub * NB + b1] - ho[sub * NB + b0], per, cap);
+    };
+    // family 0 first: it holds most nodes, and the first launch gets the SMs
+    launch(0, 3, 0, [&](cudaStream_t ls) {
+      k_propose_small<<<grid(0, 3, 256, grid_small), 256, 0, ls>>>(a, sub); SCLAP_NOTE_LAUNCH("k_propose_small");
+    });
+    if (need[3]) launch(3, 5, 1, [&](cudaStream_t ls) {
+      k_propose_warp<<<grid(3, 5, WPC, grid_warp), WPC * 32, 0, ls>>>(a, sub); SCLAP_NOTE_LAUNCH("k_propose_warp");
+    });
+    if (need[5]) launch(5, 6, 1, [&](cudaStream_t ls) {
+      k_propose_blk<128, B5_SLOTS><<<grid(5, 6, 1, grid_b5), 128, smem5, ls>>>(a, sub, 5); SCLAP_NOTE_LAUNCH("k_propose_blk128");
+    });
+    if (need[6]) launch(6, 7, 2, [&](cudaStream_t ls) {
+      k_propose_blk<256, B6_SLOTS><<<grid(6, 7, 1, grid_b6), 256, smem6, ls>>>(a, sub, 6); SCLAP_NOTE_LAUNCH("k_propose_blk256");
+    });
+    if (need[7]) launch(7, 8, 2, [&](cudaStream_t ls) {
+      k_propose_blk<512, B7_SLOTS><<<grid(7, 8, 1, grid_b7), 512, smem7, ls>>>(a, sub, 7); SCLAP_NOTE_LAUNCH("k_propose_blk512");
+    });
+    if (need[8]) launch(8, 9, 3, [&](cudaStream_t ls) {
+      k_propose_cta<512, 1, true><<<(unsigned)gblocks, 512, 0, ls>>>(a, sub, 8, gkeys.p, gvals.p, gcap); SCLAP_NOTE_LAUNCH("k_propose_cta_global");
+    });
+    if (fork) {
+      for (int j = 0; j < nside; ++j) {
+        cudaEvent_t ej = sync_event_get();
+        SCLAP_CUDA(cudaEventRecord(ej, joined[j]));
+        SCLAP_CUDA(cudaStreamWaitEvent(s, ej, 0));
+        sync_event_put(ej);
+      }
+      sync_event_put(ev_fork);
     }
-    for (int sub = 0; sub < S; ++sub) {
-      const int64_t lbeg = hoff[sub * NB], lend = hoff[(sub + 1) * NB];
-      const int64_t cnt = lend - lbeg;
-      if (cnt == 0) continue;
-      // The propose launches of a sub-round are independent of one another:
-      // they run on side streams joined back by events, so latency-bound
-      // launches overlap (serial when the timeline profiler is on).
-      const bool fork = !profile().timeline.load(std::memory_order_relaxed);
-      Timed phase{-1, nullptr, nullptr};
-      if (prof) {
-        phase.a = event_from_pool();
-        phase.b = event_from_pool();
-        SCLAP_CUDA(cudaEventRecord(phase.a, s));
-      }
-      cudaEvent_t ev_fork = nullptr;
-      if (fork) {
-        ev_fork = sync_event_get();
-        SCLAP_CUDA(cudaEventRecord(ev_fork, s));
-      }
-      int nside = 0;
-      cudaStream_t joined[NB];
-      auto lane = [&]() -> cudaStream_t {
-        if (!fork) return s;
-        cudaStream_t ss = side_stream(nside);
-        SCLAP_CUDA(cudaStreamWaitEvent(ss, ev_fork, 0));
-        joined[nside++] = ss;
-        return ss;
-      };
-      // family 0: degrees <= 16, one thread per node, three buckets in one
-      // launch
-      {
-        SmallLaunch L{};
-        int32_t nb = 0;
-        int64_t nodes = 0, arcs_f = 0;
-        for (int b = 0; b < 3; ++b) {
-          L.beg[b] = hoff[sub * NB + b];
-          L.cnt[b] = hoff[sub * NB + b + 1] - L.beg[b];
-          L.bs[b] = nb;
-          if (L.cnt[b] > 0) nb += (int32_t)grid_for(L.cnt[b], 256, small_grid);
-          nodes += L.cnt[b];
-          if (prof) arcs_f += hkarcs[sub * NB + b];
-        }
-        L.bs[3] = nb;
-        if (nb > 0) {
-          cudaStream_t s = lane();
-          Timed tm{0, nullptr, nullptr};
-          if (prof) {
-            tm.a = event_from_pool();
-            tm.b = event_from_pool();
-            SCLAP_CUDA(cudaEventRecord(tm.a, s));
-            pn[0] += nodes;
-            pa[0] += arcs_f;
-          }
-          k_propose_small<<<nb, 256, 0, s>>>(a, L); SCLAP_NOTE_LAUNCH("k_propose_small");
-          if (prof) {
-            SCLAP_CUDA(cudaEventRecord(tm.b, s));
-            timed.push_back(tm);
-          }
-        }
-      }
-      // families 1-3: buckets 3 and 4 (degrees 17..128, adjacent in the list)
-      // share the warp-per-node launch; buckets 5.. get one launch each
-      for (int b = 3; b < NB; ++b) {
-        const int64_t bb = hoff[sub * NB + b];
-        const int bend = b == 3 ? 5 : b + 1;
-        const int64_t bc = hoff[sub * NB + bend] - bb;
-        const int bcase = b;
-        if (b == 3) b = 4;
-        if (bc == 0) continue;
-        cudaStream_t s = lane();
-        const int fam = bcase <= 5 ? 1 : (bcase <= 7 ? 2 : 3);
-        Timed tm{fam, nullptr, nullptr};
-        if (prof) {
-          tm.a = event_from_pool();
-          tm.b = event_from_pool();
-          SCLAP_CUDA(cudaEventRecord(tm.a, s));
-          pn[fam] += bc;
-          for (int q = bcase; q < bend; ++q) pa[fam] += hkarcs[sub * NB + q];
-        }
-        switch (bcase) {
-          case 3: k_propose_warp<<<grid_for(bc, WPC, (int64_t)sms * 8), WPC * 32, 0, s>>>(
-                      a, bb, bc); SCLAP_NOTE_LAUNCH("k_propose_warp"); break;
-          case 5: k_propose_blk<128, B5_SLOTS><<<grid_for(bc, 1, (int64_t)sms * 16), 128, smem5, s>>>(
-                      a, bb, bc); SCLAP_NOTE_LAUNCH("k_propose_blk128"); break;
-          case 6: k_propose_blk<256, B6_SLOTS><<<grid_for(bc, 1, (int64_t)sms * 4), 256, smem6, s>>>(
-                      a, bb, bc); SCLAP_NOTE_LAUNCH("k_propose_blk256"); break;
-          case 7: k_propose_blk<512, B7_SLOTS><<<grid_for(bc, 1, (int64_t)sms * 1), 512, smem7, s>>>(
-                      a, bb, bc); SCLAP_NOTE_LAUNCH("k_propose_blk512"); break;
-          default: k_propose_cta<512, 1, true><<<(unsigned)std::min<int64_t>(bc, gblocks), 512, 0, s>>>(
-                      a, bb, bc, gkeys.p, gvals.p, gcap); SCLAP_NOTE_LAUNCH("k_propose_cta_global"); break;
-        }
-        if (prof) {
-          SCLAP_CUDA(cudaEventRecord(tm.b, s));
-          timed.push_back(tm);
-        }
-      }
-      if (fork) {
-        for (int j = 0; j < nside; ++j) {
-          cudaEvent_t ej = sync_event_get();
-          SCLAP_CUDA(cudaEventRecord(ej, joined[j]));
-          SCLAP_CUDA(cudaStreamWaitEvent(s, ej, 0));
-          sync_event_put(ej);
-        }
-        sync_event_put(ev_fork);
-      }
-      if (prof) {
-        SCLAP_CUDA(cudaEventRecord(phase.b, s));
-        timed.push_back(phase);
-        int64_t sub_arcs = 0;
-        for (int q = 0; q < NB; ++q) sub_arcs += hkarcs[sub * NB + q];
-        precs.push_back(PhaseRec{run.phase, r, sub, cnt, sub_arcs, phase.a, phase.b,
-                                 event_from_pool()});
-      }
-      const unsigned lg = grid_for(cnt, 256, (int64_t)sms * 16);
-      k_resolve<<<lg, 256, 0, s>>>(a, lbeg, cnt); SCLAP_NOTE_LAUNCH("k_resolve");
-      ctr.zero();
-      k_ovf_alloc<<<lg, 256, 0, s>>>(a, lbeg, cnt, 0); SCLAP_NOTE_LAUNCH("k_ovf_alloc");
-      k_ovf_scatter<<<lg, 256, 0, s>>>(a, lbeg, cnt); SCLAP_NOTE_LAUNCH("k_ovf_scatter");
-      k_ovf_select<<<(unsigned)(sms * 4), SEL_NT, 0, s>>>(a, 0); SCLAP_NOTE_LAUNCH("k_ovf_select");
-      if (run.mode != MODE_CLUSTER && hflags) {
-        k_forced<<<lg, 256, 0, s>>>(a, lbeg, cnt); SCLAP_NOTE_LAUNCH("k_forced");
-        ctr.zero();
-        k_ovf_alloc<<<lg, 256, 0, s>>>(a, lbeg, cnt, 1); SCLAP_NOTE_LAUNCH("k_ovf_alloc");
-        k_ovf_scatter<<<lg, 256, 0, s>>>(a, lbeg, cnt); SCLAP_NOTE_LAUNCH("k_ovf_scatter");
-        k_ovf_select<<<(unsigned)(sms * 4), SEL_NT, 0, s>>>(a, 1); SCLAP_NOTE_LAUNCH("k_ovf_select");
-      }
-      k_apply<<<lg, 256, 0, s>>>(a, lbeg, cnt); SCLAP_NOTE_LAUNCH("k_apply");
-      SCLAP_LAUNCH_CHECK();
-      if (prof) SCLAP_CUDA(cudaEventRecord(precs.back().c, s));
-    }
-    k_round_end<<<grid_for(sp.nslots, 128, 1024), 128, 0, s>>>(a, sp.nslots,
-                                                                run.stop_rule ? 1 : 0); SCLAP_NOTE_LAUNCH("k_round_end");
     SCLAP_LAUNCH_CHECK();
-    if (track_active && r + 1 < run.rounds) {
-      std::swap(act_a, act_b);
-      act_b.zero();
+  };
+  // Admission and application of colour class `sub`; the source-side chain
+  // (local search) is skipped by the host when it knows no listed node sits
+  // in an overloaded block, else its kernels check that on the device.
+  auto admit = [&](cudaStream_t s, int sub, bool source_chain, int64_t cnt) {
+    const unsigned grid_adm = cnt < 0 ? grid_adm_max : grid_for(cnt, 256, grid_adm_max);
+    k_resolve<<<grid_adm, 256, 0, s>>>(a, sub); SCLAP_NOTE_LAUNCH("k_resolve");
+    SCLAP_CUDA(cudaMemsetAsync(ctr.p, 0, 2 * sizeof(int64_t), s));
+    k_ovf_alloc<<<grid_adm, 256, 0, s>>>(a, sub, 0); SCLAP_NOTE_LAUNCH("k_ovf_alloc");
+    k_ovf_scatter<<<grid_adm, 256, 0, s>>>(a, sub, 0); SCLAP_NOTE_LAUNCH("k_ovf_scatter");
+    k_ovf_select<<<grid_sel, SEL_NT, 0, s>>>(a, 0); SCLAP_NOTE_LAUNCH("k_ovf_select");
+    if (source_chain) {
+      k_forced<<<grid_adm, 256, 0, s>>>(a, sub); SCLAP_NOTE_LAUNCH("k_forced");
+      SCLAP_CUDA(cudaMemsetAsync(ctr.p, 0, 2 * sizeof(int64_t), s));
+      k_ovf_alloc<<<grid_adm, 256, 0, s>>>(a, sub, 1); SCLAP_NOTE_LAUNCH("k_ovf_alloc");
+      k_ovf_scatter<<<grid_adm, 256, 0, s>>>(a, sub, 1); SCLAP_NOTE_LAUNCH("k_ovf_scatter");
+      k_ovf_select<<<grid_sel, SEL_NT, 0, s>>>(a, 1); SCLAP_NOTE_LAUNCH("k_ovf_select");
+    }
+    k_apply<<<grid_adm, 256, 0, s>>>(a, sub); SCLAP_NOTE_LAUNCH("k_apply");
+    SCLAP_LAUNCH_CHECK();
+  };
+  auto tail = [&](cudaStream_t s, cudaGraphConditionalHandle h, bool in_graph) {
+    k_round_end<<<nsl_grid, 128, 0, s>>>(a, sp.nslots); SCLAP_NOTE_LAUNCH("k_round_end");
+    k_round_cond<<<1, 1, 0, s>>>(a, nkeys, h, in_graph ? 1 : 0, d_cont); SCLAP_NOTE_LAUNCH("k_round_cond");
+    SCLAP_LAUNCH_CHECK();
+  };
+
+  // per sub-round record (direct driver, profiling): kind of run, round,
+  // colour class, nodes, arcs and events at fork, join (end of the propose
+  // phase) and after apply
+  struct PhaseRec { int32_t ph, r, sub; int64_t nodes, arcs; cudaEvent_t a, b, c; };
+  std::vector<PhaseRec> precs;
+
+  if (run.graph && !prof && !timeline) {
+    // ---- graph driver: the whole round loop is one CUDA graph, a WHILE
+    // node around one round whose condition k_round_cond sets on the device
+    // streams and events the capture will use are created beforehand (no
+    // object creation while the stream is capturing)
+    for (int j = 0; j < NB; ++j) (void)side_stream(j);
+    (void)capture_stream();
+    {
+      cudaEvent_t warm[NB + 1];
+      for (int j = 0; j <= NB; ++j) warm[j] = sync_event_get();
+      for (int j = 0; j <= NB; ++j) sync_event_put(warm[j]);
+    }
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ex = nullptr;
+    SCLAP_CUDA(cudaGraphCreate(&g, 0));
+    const int64_t launches0 = profile().launches.load();
+    try {
+      cudaGraphConditionalHandle h;
+      SCLAP_CUDA(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+      cudaGraphNodeParams cp = {};
+      cp.type = cudaGraphNodeTypeConditional;
+      cp.conditional.handle = h;
+      cp.conditional.type = cudaGraphCondTypeWhile;
+      cp.conditional.size = 1;
+      cudaGraphNode_t wnode;
+      SCLAP_CUDA(cudaGraphAddNode(&wnode, g, nullptr, nullptr, 0, &cp));
+      cudaGraph_t body = cp.conditional.phGraph_out[0];
+      // the caller's stream may be the legacy default stream, which cannot
+      // capture: the body is captured on a stream of this thread
+      cudaStream_t cs = capture_stream();
+      SCLAP_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0,
+                                               cudaStreamCaptureModeThreadLocal));
+      try {
+        head(cs);
+        for (int sub = 0; sub < S; ++sub) {
+          propose(cs, sub, true, nullptr);
+          admit(cs, sub, refine, -1);
+        }
+        tail(cs, h, true);
+      } catch (...) {
+        cudaGraph_t junk = nullptr;
+        cudaStreamEndCapture(cs, &junk);
+        throw;
+      }
+      cudaGraph_t captured = nullptr;
+      SCLAP_CUDA(cudaStreamEndCapture(cs, &captured));
+      SCLAP_CUDA(cudaGraphInstantiate(&ex, g, 0));
+      SCLAP_CUDA(cudaGraphLaunch(ex, s));
+    } catch (...) {
+      if (ex) cudaGraphExecDestroy(ex);
+      cudaGraphDestroy(g);
+      throw;
+    }
+    // the capture counted one round's launches; the graph ran them per round
+    int32_t hr = 0;
+    SCLAP_CUDA(cudaMemcpyAsync(&hr, a.rnd, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    stream_sync(s);
+    cudaGraphExecDestroy(ex);
+    cudaGraphDestroy(g);
+    const int64_t per_round = profile().launches.load() - launches0;
+    if (hr > 1) profile().launches.fetch_add(per_round * (hr - 1));
+  } else {
+    // ---- direct driver: one round at a time; the host reads the bucket
+    // offsets after bucketing (one wait per round), skips empty launches and
+    // colour classes, and stops at the first round that lists no node
+    for (int r = 0; r < run.rounds; ++r) {
+      head(s);
+      int32_t hflags = 0;
+      SCLAP_CUDA(cudaMemcpyAsync(hoff.data(), boff.p, (nkeys + 1) * sizeof(int64_t),
+                                 cudaMemcpyDeviceToHost, s));
+      SCLAP_CUDA(cudaMemcpyAsync(hkarcs.data(), karcs.p, nkeys * sizeof(int64_t),
+                                 cudaMemcpyDeviceToHost, s));
+      SCLAP_CUDA(cudaMemcpyAsync(&hflags, flags.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      stream_sync(s);
+      if (hoff[nkeys] == 0) {
+        tail(s, 0, false);
+        break;
+      }
+      for (int sub = 0; sub < S; ++sub) {
+        const int64_t cnt = hoff[(sub + 1) * NB] - hoff[sub * NB];
+        if (cnt == 0) continue;
+        Timed phase{-1, nullptr, nullptr};
+        if (prof) {
+          phase.a = event_from_pool();
+          phase.b = event_from_pool();
+          SCLAP_CUDA(cudaEventRecord(phase.a, s));
+        }
+        propose(s, sub, !timeline, hoff.data());
+        if (prof) {
+          SCLAP_CUDA(cudaEventRecord(phase.b, s));
+          timed.push_back(phase);
+          int64_t sub_arcs = 0;
+          for (int q = 0; q < NB; ++q) sub_arcs += hkarcs[sub * NB + q];
+          precs.push_back(PhaseRec{run.phase, r, sub, cnt, sub_arcs, phase.a, phase.b,
+                                   event_from_pool()});
+        }
+        admit(s, sub, refine && hflags != 0, cnt);
+        if (prof) SCLAP_CUDA(cudaEventRecord(precs.back().c, s));
+      }
+      tail(s, 0, false);
     }
   }
-  if (active_next_out && track_active)
-    SCLAP_CUDA(cudaMemcpyAsync(active_next_out, act_b.p, N, cudaMemcpyDeviceToDevice, s));
+  int32_t hr = 0;
+  int64_t h_arcs = 0;
+  SCLAP_CUDA(cudaMemcpyAsync(&hr, a.rnd, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  SCLAP_CUDA(cudaMemcpyAsync(&h_arcs, arcs.p, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   stream_sync(s);
-  const int64_t h_arcs = arcs_total;
+  if (active_next_out && track_active)
+    SCLAP_CUDA(cudaMemcpyAsync(active_next_out, a.act[hr & 1], N, cudaMemcpyDeviceToDevice, s));
   if (prof) {
     ProfileState& P = profile();
     std::lock_guard<std::mutex> lk(P.mu);

@@ -133,27 +133,35 @@ __global__ void k_fill_gid(const int64_t* __restrict__ noff, int32_t nslots,
   }
 }
 
-__global__ void k_max_degree(const int64_t* __restrict__ row_ptr, int64_t N,
-                             unsigned long long* out) {
-  unsigned long long m = 0;
+// Largest degree of a level (out[0]) and the number of nodes whose degree
+// exceeds thr (out[1]).
+__global__ void k_degree_stats(const int64_t* __restrict__ row_ptr, int64_t N, int64_t thr,
+                               unsigned long long* out) {
+  unsigned long long m = 0, c = 0;
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N;
        v += (int64_t)gridDim.x * blockDim.x) {
-    unsigned long long d = (unsigned long long)(row_ptr[v + 1] - row_ptr[v]);
-    m = d > m ? d : m;
+    const int64_t d = row_ptr[v + 1] - row_ptr[v];
+    m = (unsigned long long)d > m ? (unsigned long long)d : m;
+    c += d > thr ? 1ull : 0ull;
   }
   for (int o = 16; o > 0; o >>= 1) {
-    unsigned long long y = __shfl_xor_sync(0xffffffffu, m, o);
+    const unsigned long long y = __shfl_xor_sync(0xffffffffu, m, o);
     m = y > m ? y : m;
+    c += __shfl_xor_sync(0xffffffffu, c, o);
   }
-  if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
+  if ((threadIdx.x & 31) == 0) {
+    if (m) atomicMax(&out[0], m);
+    if (c) atomicAdd(&out[1], c);
+  }
 }
 
 }  // namespace
 
-void level_max_degree(const int64_t* row_ptr, int64_t N, int64_t* out, cudaStream_t s) {
+void level_degree_stats(const int64_t* row_ptr, int64_t N, int64_t thr, int64_t* out,
+                        cudaStream_t s) {
   if (N <= 0) return;
-  k_max_degree<<<grid_for(N, 256, (int64_t)num_sms() * 8), 256, 0, s>>>(
-      row_ptr, N, reinterpret_cast<unsigned long long*>(out)); SCLAP_NOTE_LAUNCH("k_max_degree");
+  k_degree_stats<<<grid_for(N, 256, (int64_t)num_sms() * 8), 256, 0, s>>>(
+      row_ptr, N, thr, reinterpret_cast<unsigned long long*>(out)); SCLAP_NOTE_LAUNCH("k_degree_stats");
   SCLAP_LAUNCH_CHECK();
 }
 

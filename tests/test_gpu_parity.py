@@ -273,6 +273,31 @@ def test_partition_active_coarsening_bit_exact(name):
     assert res.stats["level_n"] == list(ref.stats.level_n[:ref.stats.levels])
 
 
+@pytest.mark.parametrize("name,k", [("rmat16", 2), ("rgg", 8), ("weighted", 5), ("hub", 4)])
+def test_partition_graph_driver_bit_exact(name, k):
+    """The rounds run as one CUDA graph (device-side loop condition) give the
+    same partition as the host-driven rounds and the oracle."""
+    g = GRAPHS[name]()
+    ref = O.partition(g, k, 0.03, seed=1)
+    res = P.sclap_partition_device(*dg(g), k=k, eps=0.03, seed=1,
+                                   cfg=P.default_config(graph_rounds=1))
+    assert (res.status, res.cut) == (ref.status, ref.cut)
+    assert np.array_equal(res.block.cpu().numpy(), ref.block)
+    assert res.stats["cluster_rounds"] == list(ref.stats.cluster_rounds[:len(res.stats["cluster_rounds"])])
+
+
+def test_batch_graph_driver_equals_host_driver():
+    graphs = [(gg.rmat(10 + i % 5, 8, 40 + i), [2, 4, 8, 16][i % 4]) for i in range(8)]
+    graphs += [(gg.rgg2d(1500 + 900 * i, 60 + i), [2, 4, 8, 16][(i + 2) % 4]) for i in range(8)]
+    items = [dict(row_ptr=dt(g.row_ptr), col=dt(g.col), k=k, eps=0.03, seed=i)
+             for i, (g, k) in enumerate(graphs)]
+    a = P.sclap_partition_batch(items, device=True)
+    b = P.sclap_partition_batch(items, device=True, cfg=P.default_config(graph_rounds=1))
+    for x, y in zip(a, b):
+        assert (x.status, x.cut) == (y.status, y.cut)
+        assert np.array_equal(x.block.cpu().numpy(), y.block.cpu().numpy())
+
+
 def test_partition_host_api_and_seeds():
     g = gg.rmat(14, 8, 3)
     for seed in (0, 1, 2):
