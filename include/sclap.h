@@ -70,6 +70,13 @@ enum {
  * rounds (it then launches every bucket's kernel; empty ones exit at once).
  * 0 (default) drives the rounds from the host, which reads the bucket sizes
  * once per round and skips empty launches.  Results are identical.
+ * ensemble = 1 turns on ensemble clusterings during coarsening (Sec. 4
+ * "Ensemble Clusterings", configuration E): every level computes l
+ * clusterings (the first with the run's seed, clustering j >= 1 with the key
+ * hkey(seed, 7, level, j)) and contracts their overlay, in which two nodes
+ * share a cluster iff every clustering puts them together.  l =
+ * ensemble_size if > 0, else the paper's rule (Sec. 5): 18 for k < 16, 7 for
+ * k = 16..32, 3 above.
  * cluster_active = 1 turns on active nodes during coarsening (Sec. 4 "Active
  * Nodes", configuration A of Table 2): after the first round a clustering
  * round visits only nodes with a neighbour that changed its cluster in the
@@ -87,6 +94,8 @@ typedef struct sclap_config {
   int32_t max_levels;
   int32_t cluster_active;
   int32_t graph_rounds;
+  int32_t ensemble;
+  int32_t ensemble_size;
 } sclap_config;
 
 /* Per-call statistics (optional output). */

@@ -19,7 +19,7 @@ _SRC = [os.path.join(_HERE, "sclap_oracle.cpp")]
 
 SYNC, SEQ = 0, 1
 MODE_CLUSTER, MODE_REFINE = 0, 1
-PH_CLUSTER, PH_REFINE, PH_TRIAL, PH_GGG, PH_IPREF, PH_REPAIR = 1, 2, 3, 4, 5, 6
+PH_CLUSTER, PH_REFINE, PH_TRIAL, PH_GGG, PH_IPREF, PH_REPAIR, PH_ENSEMBLE = 1, 2, 3, 4, 5, 6, 7
 OK, EINVAL, EOVERFLOW, EINFEASIBLE = 0, -1, -2, -3
 
 
@@ -37,7 +37,7 @@ class Config(C.Structure):
     _fields_ = [(name, C.c_int32) for name in (
         "lp_rounds_coarse", "lp_rounds_refine", "f", "coarse_min_nodes",
         "ip_trials", "sub_rounds", "repair_rounds", "max_levels", "cluster_active",
-        "random_order")]
+        "random_order", "ensemble", "ensemble_size")]
 
 
 class Stats(C.Structure):
@@ -67,6 +67,7 @@ def lib():
             "orc_contract": (C.c_int, [i64, p, p, p, p, p, p, p, p, p, p, p, p]),
             "orc_cluster_hierarchy": (C.c_int, [i32, i64, p, p, p, p, i64, i64, u64, p, p, p,
                                                 p, i32]),
+            "orc_overlay": (C.c_int, [i64, p, p, p]),
             "orc_ggg": (C.c_int, [i64, p, p, p, p, i32, i64, u64, i32, p, p]),
             "orc_initial_partition": (C.c_int, [i32, i64, p, p, p, p, i32, i64, i64, u64, i32,
                                                 p, p, p, p]),
@@ -145,6 +146,17 @@ def cluster(g, U, seed, level=0, variant=SYNC, cfg=None):
     if rc:
         raise RuntimeError(f"orc_cluster rc={rc}")
     return label, rounds.value
+
+
+def overlay(a, b):
+    """Overlay of two clusterings, ids numbered by first occurrence."""
+    a = np.ascontiguousarray(a, dtype=np.int32)
+    b = np.ascontiguousarray(b, dtype=np.int32)
+    out = np.empty(a.size, dtype=np.int32)
+    rc = lib().orc_overlay(a.size, _p(a), _p(b), _p(out))
+    if rc:
+        raise RuntimeError(f"orc_overlay rc={rc}")
+    return out
 
 
 def cluster_hierarchy(g, U, stop_nodes, seed, variant=SYNC, cfg=None):

@@ -10,6 +10,7 @@
 #include "sclap_oracle.h"
 
 #include <algorithm>
+#include <map>
 #include <climits>
 #include <cmath>
 #include <cstring>
@@ -347,6 +348,43 @@ int cluster_level(int variant, const G& g, int64_t U, uint64_t seed, int32_t lev
   return ORC_OK;
 }
 
+// Overlay of two clusterings (Sec. 4, "Ensemble Clusterings"): the pair
+// (a[v], b[v]) names v's overlay cluster; pairs are numbered by their first
+// occurrence in node order.
+void overlay(int64_t n, const int32_t* a, const int32_t* b, int32_t* out) {
+  std::map<std::pair<int32_t, int32_t>, int32_t> H;
+  int32_t c = 0;
+  for (int64_t v = 0; v < n; ++v) {
+    const auto key = std::make_pair(a[v], b[v]);
+    auto it = H.find(key);
+    if (it == H.end()) it = H.emplace(key, c++).first;
+    out[v] = it->second;
+  }
+}
+
+// Number of clusterings of an ensemble (Sec. 5).
+int32_t ensemble_size_for(int32_t k, const orc_config& cfg) {
+  if (cfg.ensemble_size > 0) return cfg.ensemble_size;
+  return k < 16 ? 18 : (k <= 32 ? 7 : 3);
+}
+
+// Clustering of one coarsening level: plain, or the overlay of an ensemble
+// of clusterings (clustering 0 uses the run's seed, clustering j >= 1 the
+// key hkey(seed, ENSEMBLE, level, j)).  rounds_out: clustering 0's rounds.
+void coarsen_clustering(int variant, const G& g, int64_t U, uint64_t seed, int32_t level,
+                        int32_t k, const orc_config& cfg, int32_t* label, int32_t* rounds_out) {
+  cluster_level(variant, g, U, seed, level, cfg, label, rounds_out);
+  if (!cfg.ensemble) return;
+  const int32_t ell = ensemble_size_for(k, cfg);
+  vector<int32_t> C((size_t)g.n), O((size_t)g.n);
+  for (int32_t j = 1; j < ell; ++j) {
+    const uint64_t sj = hkey(seed, ORC_PH_ENSEMBLE, (uint64_t)level, (uint64_t)j);
+    cluster_level(variant, g, U, sj, level, cfg, C.data(), nullptr);
+    overlay(g.n, label, C.data(), O.data());
+    std::copy(O.begin(), O.end(), label);
+  }
+}
+
 // Cluster contraction (Sec. 3.1): each cluster becomes one node whose weight
 // is the sum of its members; two coarse nodes are adjacent iff their clusters
 // are, with the summed weight of the edges between them.  Coarse ids follow
@@ -641,6 +679,8 @@ void orc_default_config(orc_config* cfg) {
   cfg->max_levels = 64;
   cfg->cluster_active = 0;
   cfg->random_order = 0;
+  cfg->ensemble = 0;
+  cfg->ensemble_size = 0;
 }
 
 uint64_t orc_mix64(uint64_t x) { return mix64(x); }
@@ -670,6 +710,12 @@ int orc_cluster(int32_t variant, int64_t n, const int64_t* xadj, const int32_t* 
   if (cfg) c = *cfg; else orc_default_config(&c);
   G g{n, xadj, adj, nw, ew};
   return cluster_level(variant, g, U, seed, level, c, label_out, rounds_out);
+}
+
+int orc_overlay(int64_t n, const int32_t* a, const int32_t* b, int32_t* out) {
+  if (n < 0 || (n > 0 && (!a || !b || !out))) return ORC_EINVAL;
+  overlay(n, a, b, out);
+  return ORC_OK;
 }
 
 int orc_cluster_hierarchy(int32_t variant, int64_t n, const int64_t* xadj, const int32_t* adj,
@@ -812,7 +858,7 @@ int orc_partition(int32_t variant, int64_t n, const int64_t* xadj, const int32_t
     if (g.n <= T || (int64_t)coarse.size() + 1 >= cfg.max_levels) break;
     vector<int32_t> label((size_t)g.n);
     int32_t r = 0;
-    cluster_level(variant, g, U, seed, (int32_t)coarse.size(), cfg, label.data(), &r);
+    coarsen_clustering(variant, g, U, seed, (int32_t)coarse.size(), k, cfg, label.data(), &r);
     vector<int32_t> cmap;
     OG c;
     rc = contract(g, label.data(), cmap, c);

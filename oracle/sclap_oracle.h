@@ -38,7 +38,7 @@ enum { ORC_MODE_CLUSTER = 0, ORC_MODE_REFINE = 1 };
 /* Hash-domain tags for the counter-based generator (one per phase). */
 enum {
   ORC_PH_CLUSTER = 1, ORC_PH_REFINE = 2, ORC_PH_TRIAL = 3,
-  ORC_PH_GGG = 4, ORC_PH_IPREF = 5, ORC_PH_REPAIR = 6
+  ORC_PH_GGG = 4, ORC_PH_IPREF = 5, ORC_PH_REPAIR = 6, ORC_PH_ENSEMBLE = 7
 };
 enum { ORC_OK = 0, ORC_EINVAL = -1, ORC_EOVERFLOW = -2, ORC_EINFEASIBLE = -3 };
 
@@ -58,6 +58,11 @@ typedef struct orc_config {
   int32_t random_order;     /* sequential variant only, 1: visit nodes in hashed
                                random order instead of increasing degree
                                (configuration R of Table 2)                         */
+  int32_t ensemble;         /* 1: ensemble clusterings during coarsening (Sec. 4
+                               "Ensemble Clusterings", configuration E): each level
+                               contracts the overlay of l clusterings             */
+  int32_t ensemble_size;    /* l; 0 = the paper's rule (Sec. 5): 18 if k < 16, 7 if
+                               k is 16 or 32, 3 if k > 32                           */
 } orc_config;
 
 typedef struct orc_stats {
@@ -112,6 +117,12 @@ int orc_cluster(int32_t variant, int64_t n, const int64_t* xadj, const int32_t* 
  * discarded).  comm_out[v] (n entries) receives the node of the last graph
  * that input node v belongs to; *levels_out the number of contractions
  * kept; level_n_out[0..min(levels, cap-1)] the node counts, input first. */
+/* Overlay of two clusterings (Sec. 4 "Ensemble Clusterings"): two nodes
+ * share an overlay cluster iff they share a cluster in a and in b.  Overlay
+ * ids are numbered 0, 1, ... in the order the (a[v], b[v]) pairs first occur
+ * for v = 0..n-1 (the paper's hash-map construction). */
+int orc_overlay(int64_t n, const int32_t* a, const int32_t* b, int32_t* out);
+
 int orc_cluster_hierarchy(int32_t variant, int64_t n, const int64_t* xadj, const int32_t* adj,
                           const int32_t* nw, const int32_t* ew, int64_t U, int64_t stop_nodes,
                           uint64_t seed, const orc_config* cfg, int32_t* comm_out,

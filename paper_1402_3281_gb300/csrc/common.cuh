@@ -96,7 +96,8 @@ __host__ __device__ __forceinline__ uint64_t hkey(uint64_t seed, uint64_t phase,
 }
 
 enum Phase : int32_t {
-  PH_CLUSTER = 1, PH_REFINE = 2, PH_TRIAL = 3, PH_GGG = 4, PH_IPREF = 5, PH_REPAIR = 6
+  PH_CLUSTER = 1, PH_REFINE = 2, PH_TRIAL = 3, PH_GGG = 4, PH_IPREF = 5, PH_REPAIR = 6,
+  PH_ENSEMBLE = 7
 };
 enum Mode : int32_t { MODE_CLUSTER = 0, MODE_REFINE = 1, MODE_REPAIR = 2 };
 
@@ -365,6 +366,13 @@ struct CoarseLevel {
   }
 };
 // Step 1: ranks the used labels; nc_slot[s] = coarse nodes of slot s.
+// Overlay of two clusterings of a batched level (ensemble clusterings): for
+// every node of a slot with part[slot] != 0, O[v] becomes the smallest node
+// id sharing both its O and its C label; other slots keep O.  Errors (table
+// overflow) are or-ed into err.
+void overlay_labels(const LevelView& lv, const int32_t* part, int32_t* O, const int32_t* C,
+                    int32_t* err, cudaStream_t s);
+
 void contract_rank(const LevelView& lv, const std::vector<int64_t>& noff, const int32_t* label,
                    ContractWork& w, std::vector<int64_t>& nc_slot, cudaStream_t s);
 // Step 2: builds the coarse graph of the slots with keep[s] != 0 (the other

@@ -175,6 +175,57 @@ __global__ void k_rows(const int64_t* __restrict__ tbase, const int64_t* __restr
     crow[c] = pos[tbase[c]];
 }
 
+// Overlay (ensemble clusterings): the pair (O[v], C[v]) keys an open-
+// addressing table whose entry keeps the smallest node id with that pair.
+// Labels are node ids < 2^31, so a key never equals the empty marker ~0.
+__device__ __forceinline__ uint64_t pair_key(int32_t o, int32_t c) {
+  return ((uint64_t)(uint32_t)o << 32) | (uint32_t)c;
+}
+
+__global__ void k_overlay_insert(const int32_t* __restrict__ gid, const int32_t* __restrict__ part,
+                                 const int32_t* __restrict__ O, const int32_t* __restrict__ C,
+                                 int64_t N, unsigned long long* keys, int32_t* rep, int logcap,
+                                 int32_t* err) {
+  const uint64_t mask = ((uint64_t)1 << logcap) - 1;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    if (!part[gid[v]]) continue;
+    const unsigned long long key = pair_key(O[v], C[v]);
+    uint64_t s = mix64(key) & mask;
+    bool placed = false;
+    for (uint64_t p = 0; p <= mask; ++p) {
+      unsigned long long cur = keys[s];
+      if (cur == ~0ull) cur = atomicCAS(&keys[s], ~0ull, key);
+      if (cur == ~0ull || cur == key) {
+        atomicMin(&rep[s], (int32_t)v);
+        placed = true;
+        break;
+      }
+      s = (s + 1) & mask;
+    }
+    if (!placed) atomicOr(err, DERR_HASH_FULL);
+  }
+}
+
+__global__ void k_overlay_apply(const int32_t* __restrict__ gid, const int32_t* __restrict__ part,
+                                int32_t* O, const int32_t* __restrict__ C, int64_t N,
+                                const unsigned long long* __restrict__ keys,
+                                const int32_t* __restrict__ rep, int logcap) {
+  const uint64_t mask = ((uint64_t)1 << logcap) - 1;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    if (!part[gid[v]]) continue;
+    const unsigned long long key = pair_key(O[v], C[v]);
+    uint64_t s = mix64(key) & mask;
+    for (uint64_t p = 0; p <= mask; ++p) {
+      const unsigned long long cur = keys[s];
+      if (cur == key) { O[v] = rep[s]; break; }
+      if (cur == ~0ull) break;          // cannot happen after the insert pass
+      s = (s + 1) & mask;
+    }
+  }
+}
+
 }  // namespace
 
 void contract_rank(const LevelView& lv, const std::vector<int64_t>& noff, const int32_t* label,
@@ -273,6 +324,21 @@ void contract_build(const LevelView& lv, const std::vector<int64_t>& noff, const
   SCLAP_CUDA(cudaMemcpyAsync(out.aoff.data(), ga.p, (ns + 1) * sizeof(int64_t),
                              cudaMemcpyDeviceToHost, s));
   stream_sync(s);
+}
+
+void overlay_labels(const LevelView& lv, const int32_t* part, int32_t* O, const int32_t* C,
+                    int32_t* err, cudaStream_t s) {
+  if (lv.N == 0) return;
+  const int logcap = ceil_log2(std::max<int64_t>(2 * lv.N, 64));
+  const int64_t cap = (int64_t)1 << logcap;
+  DevBuf<unsigned long long> keys(cap, s);
+  DevBuf<int32_t> rep(cap, s);
+  keys.fill_bytes(0xff);
+  rep.fill_bytes(0x7f);                    // 0x7f7f7f7f: above every node id
+  const unsigned g = grid_for(lv.N, 256, (int64_t)num_sms() * 16);
+  k_overlay_insert<<<g, 256, 0, s>>>(lv.gid, part, O, C, lv.N, keys.p, rep.p, logcap, err); SCLAP_NOTE_LAUNCH("k_overlay_insert");
+  k_overlay_apply<<<g, 256, 0, s>>>(lv.gid, part, O, C, lv.N, keys.p, rep.p, logcap); SCLAP_NOTE_LAUNCH("k_overlay_apply");
+  SCLAP_LAUNCH_CHECK();
 }
 
 }  // namespace sclap

@@ -34,6 +34,12 @@ void init_pool() {
   });
 }
 
+// Clusterings per ensemble (Sec. 5): 18 for k < 16, 7 for k = 16..32, 3 above.
+int32_t ensemble_size_for(int32_t k, const sclap_config& c) {
+  if (c.ensemble_size > 0) return c.ensemble_size;
+  return k < 16 ? 18 : (k <= 32 ? 7 : 3);
+}
+
 sclap_config resolve_cfg(const sclap_config* c) {
   sclap_config r;
   sclap_default_config(&r);
@@ -41,7 +47,7 @@ sclap_config resolve_cfg(const sclap_config* c) {
   if (r.lp_rounds_coarse < 0 || r.lp_rounds_refine < 0 || r.f < 1 || r.coarse_min_nodes < 1 ||
       r.ip_trials < 1 || r.sub_rounds < 1 || r.sub_rounds > 64 || r.repair_rounds < 0 ||
       r.max_levels < 1 || r.cluster_active < 0 || r.cluster_active > 1 || r.graph_rounds < 0 ||
-      r.graph_rounds > 1)
+      r.graph_rounds > 1 || r.ensemble < 0 || r.ensemble > 1 || r.ensemble_size < 0)
     throw Error(SCLAP_EINVAL, "invalid sclap_config");
   return r;
 }
@@ -626,6 +632,35 @@ void run_valid_batch(const std::vector<GIn>& gs, const std::vector<int64_t>& cV,
     const std::vector<int32_t> rr = sl.host_rounds(s);
     for (int g = 0; g < B; ++g)
       if (coarsening[g]) st[g].crounds.push_back(rr[g]);
+    if (cfg.ensemble) {
+      // ensemble clusterings: clustering j >= 1 of every slot whose ensemble
+      // is that large, overlaid onto the labels so far
+      std::vector<int32_t> ell(B, 1);
+      int32_t ell_max = 1;
+      for (int g = 0; g < B; ++g)
+        if (coarsening[g]) {
+          ell[g] = ensemble_size_for(st[g].k, cfg);
+          ell_max = std::max(ell_max, ell[g]);
+        }
+      if (ell_max > 1) {
+        DevBuf<int32_t> C(std::max<int64_t>(v.N, 1), s), part(B, s);
+        for (int32_t j = 1; j < ell_max; ++j) {
+          std::vector<uint64_t> sj(B);
+          std::vector<int32_t> dj(B), pj(B);
+          for (int g = 0; g < B; ++g) {
+            pj[g] = coarsening[g] && j < ell[g] ? 1 : 0;
+            dj[g] = pj[g] ? 0 : 1;
+            sj[g] = hkey(st[g].seed, PH_ENSEMBLE, (uint64_t)L, (uint64_t)j);
+          }
+          Slots slj(s, B, cur.noff_d.p, h_loff, h_bound, sj, h_level, h_nlab, dj);
+          k_iota<<<grid_for(v.N, 256, (int64_t)sms * 16), 256, 0, s>>>(C.p, v.N); SCLAP_NOTE_LAUNCH("k_iota");
+          k_w_from_nw<<<grid_for(v.N, 256, (int64_t)sms * 16), 256, 0, s>>>(v.nw, v.N, W.p); SCLAP_NOTE_LAUNCH("k_w_from_nw");
+          lp_arcs += lp_run(v, slj.sp, C.p, W.p, v.N, run, d_err.p, s);
+          part.upload(pj);
+          overlay_labels(v, part.p, label.p, C.p, d_err.p, s);
+        }
+      }
+    }
     ContractWork cw;
     std::vector<int64_t> nc;
     contract_rank(v, cur.noff, label.p, cw, nc, s);
@@ -905,6 +940,8 @@ void sclap_default_config(sclap_config* c) {
   c->max_levels = 64;
   c->cluster_active = 0;
   c->graph_rounds = 0;
+  c->ensemble = 0;
+  c->ensemble_size = 0;
 }
 
 const char* sclap_error_string(int code) {

@@ -298,6 +298,31 @@ def test_batch_graph_driver_equals_host_driver():
         assert np.array_equal(x.block.cpu().numpy(), y.block.cpu().numpy())
 
 
+@pytest.mark.parametrize("name,k,size", [("rmat12", 2, 0), ("rgg", 4, 0), ("weighted", 16, 0),
+                                         ("rmat16", 8, 3), ("hub", 64, 0)])
+def test_partition_ensemble_bit_exact(name, k, size):
+    """Ensemble clusterings during coarsening (configuration E)."""
+    g = GRAPHS[name]()
+    ref = O.partition(g, k, 0.03, seed=6, cfg=O.config(ensemble=1, ensemble_size=size))
+    res = P.sclap_partition_device(*dg(g), k=k, eps=0.03, seed=6,
+                                   cfg=P.default_config(ensemble=1, ensemble_size=size))
+    assert (res.status, res.cut) == (ref.status, ref.cut)
+    assert np.array_equal(res.block.cpu().numpy(), ref.block)
+    assert res.stats["level_n"] == list(ref.stats.level_n[:ref.stats.levels])
+
+
+def test_batch_ensemble_mixed_sizes_equals_oracle():
+    """Slots of one batch run ensembles of different sizes (l = 18, 7, 3)."""
+    graphs = [(gg.rmat(11, 8, 70 + i), [2, 16, 64][i % 3]) for i in range(6)]
+    items = [dict(row_ptr=dt(g.row_ptr), col=dt(g.col), k=k, eps=0.03, seed=i)
+             for i, (g, k) in enumerate(graphs)]
+    out = P.sclap_partition_batch(items, device=True, cfg=P.default_config(ensemble=1))
+    for i, ((g, k), r) in enumerate(zip(graphs, out)):
+        ref = O.partition(g, k, 0.03, seed=i, cfg=O.config(ensemble=1))
+        assert (r.status, r.cut) == (ref.status, ref.cut)
+        assert np.array_equal(r.block.cpu().numpy(), ref.block)
+
+
 def test_partition_host_api_and_seeds():
     g = gg.rmat(14, 8, 3)
     for seed in (0, 1, 2):

@@ -519,3 +519,50 @@ def test_cluster_hierarchy_special_cases():
     for q in range(k):
         assert len(set(comm[q * s:(q + 1) * s])) == 1
     assert len(set(comm)) == k
+
+
+# ----------------------------------------------------- ensemble clusterings
+# Sec. 4 "Ensemble Clusterings" (configuration E): the overlay puts two nodes
+# together iff every input clustering does; each coarsening level contracts
+# the overlay of l clusterings (Sec. 5: l = 18 / 7 / 3 by k).
+
+def test_overlay_is_the_intersection_brute_force():
+    rng = np.random.default_rng(3)
+    for n, ka, kb in [(12, 3, 4), (30, 5, 2), (25, 25, 1)]:
+        a = rng.integers(0, ka, n).astype(np.int32) * 7 + 100     # arbitrary ids
+        b = rng.integers(0, kb, n).astype(np.int32) * 3
+        o = O.overlay(a, b)
+        for u in range(n):
+            for v in range(n):
+                assert (o[u] == o[v]) == (a[u] == a[v] and b[u] == b[v])
+        # numbered 0, 1, ... by first occurrence in node order
+        firsts = [o[v] for v in range(n) if o[v] not in set(o[:v])]
+        assert firsts == list(range(len(firsts)))
+
+
+def test_overlay_of_ensemble_refines_each_clustering_and_keeps_U():
+    g = gg.rmat(11, 8, 6)
+    U = 40
+    labs = [O.cluster(g, U, seed=100 + j)[0] for j in range(4)]
+    o = labs[0]
+    for lab in labs[1:]:
+        o = O.overlay(o, lab)
+    assert len(np.unique(o)) >= max(len(np.unique(l)) for l in labs)
+    assert np.bincount(o, weights=g.node_w).max() <= U
+
+
+@pytest.mark.parametrize("variant", [O.SYNC, O.SEQ])
+def test_ensemble_of_one_is_plain_coarsening(variant):
+    g = gg.rmat(13, 8, 2)
+    a = O.partition(g, 4, 0.03, seed=3, variant=variant, cfg=O.config(ensemble=1, ensemble_size=1))
+    b = O.partition(g, 4, 0.03, seed=3, variant=variant)
+    assert a.cut == b.cut and np.array_equal(a.block, b.block)
+
+
+@pytest.mark.parametrize("k", [2, 16, 64])
+def test_ensemble_partition_is_balanced_and_counted(k):
+    g = gg.rgg2d(6000, 4)
+    r = O.partition(g, k, 0.03, seed=1, cfg=O.config(ensemble=1, ensemble_size=3))
+    Lmax, _ = O.bounds(int(g.node_w.sum()), int(g.node_w.max()), k, 0.03)
+    assert np.bincount(r.block, minlength=k).max() <= Lmax
+    assert r.cut == O.cut(g, r.block)
