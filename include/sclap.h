@@ -77,6 +77,12 @@ enum {
  * share a cluster iff every clustering puts them together.  l =
  * ensemble_size if > 0, else the paper's rule (Sec. 5): 18 for k < 16, 7 for
  * k = 16..32, 3 above.
+ * vcycles = number of multilevel cycles (Sec. 4 "Iterated Multilevel
+ * Algorithms", App. A; configuration V uses 3, Sec. 5); default 1.  Every
+ * cycle after the first coarsens with clusterings that stay inside the
+ * blocks of the current partition (so no cut edge is contracted), starts
+ * from that partition on its coarsest graph, refines every level on the way
+ * back and repairs balance; cycle c uses hkey(seed, 8, c, 0) as its seed.
  * cluster_active = 1 turns on active nodes during coarsening (Sec. 4 "Active
  * Nodes", configuration A of Table 2): after the first round a clustering
  * round visits only nodes with a neighbour that changed its cluster in the
@@ -96,6 +102,7 @@ typedef struct sclap_config {
   int32_t graph_rounds;
   int32_t ensemble;
   int32_t ensemble_size;
+  int32_t vcycles;
 } sclap_config;
 
 /* Per-call statistics (optional output). */

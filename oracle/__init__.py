@@ -19,7 +19,8 @@ _SRC = [os.path.join(_HERE, "sclap_oracle.cpp")]
 
 SYNC, SEQ = 0, 1
 MODE_CLUSTER, MODE_REFINE = 0, 1
-PH_CLUSTER, PH_REFINE, PH_TRIAL, PH_GGG, PH_IPREF, PH_REPAIR, PH_ENSEMBLE = 1, 2, 3, 4, 5, 6, 7
+PH_CLUSTER, PH_REFINE, PH_TRIAL, PH_GGG, PH_IPREF, PH_REPAIR, PH_ENSEMBLE, PH_VCYCLE = (
+    1, 2, 3, 4, 5, 6, 7, 8)
 OK, EINVAL, EOVERFLOW, EINFEASIBLE = 0, -1, -2, -3
 
 
@@ -37,7 +38,7 @@ class Config(C.Structure):
     _fields_ = [(name, C.c_int32) for name in (
         "lp_rounds_coarse", "lp_rounds_refine", "f", "coarse_min_nodes",
         "ip_trials", "sub_rounds", "repair_rounds", "max_levels", "cluster_active",
-        "random_order", "ensemble", "ensemble_size")]
+        "random_order", "ensemble", "ensemble_size", "vcycles")]
 
 
 class Stats(C.Structure):
@@ -68,6 +69,8 @@ def lib():
             "orc_cluster_hierarchy": (C.c_int, [i32, i64, p, p, p, p, i64, i64, u64, p, p, p,
                                                 p, i32]),
             "orc_overlay": (C.c_int, [i64, p, p, p]),
+            "orc_cluster_in_blocks": (C.c_int, [i32, i64, p, p, p, p, i64, u64, i32, p, p, p,
+                                                p]),
             "orc_ggg": (C.c_int, [i64, p, p, p, p, i32, i64, u64, i32, p, p]),
             "orc_initial_partition": (C.c_int, [i32, i64, p, p, p, p, i32, i64, i64, u64, i32,
                                                 p, p, p, p]),
@@ -145,6 +148,20 @@ def cluster(g, U, seed, level=0, variant=SYNC, cfg=None):
                            C.byref(cfg), _p(label), C.byref(rounds))
     if rc:
         raise RuntimeError(f"orc_cluster rc={rc}")
+    return label, rounds.value
+
+
+def cluster_in_blocks(g, U, seed, blk, level=0, variant=SYNC, cfg=None):
+    """Clustering in which every cluster lies inside one block of blk."""
+    rp, col, nw, ew = _graph_arrays(g)
+    blk = np.ascontiguousarray(blk, dtype=np.int32)
+    label = np.empty(g.n, dtype=np.int32)
+    rounds = C.c_int32()
+    cfg = cfg or config()
+    rc = lib().orc_cluster_in_blocks(variant, g.n, _p(rp), _p(col), _p(nw), _p(ew), U, seed,
+                                     level, C.byref(cfg), _p(blk), _p(label), C.byref(rounds))
+    if rc:
+        raise RuntimeError(f"orc_cluster_in_blocks rc={rc}")
     return label, rounds.value
 
 

@@ -53,6 +53,9 @@ struct G {
   const int32_t* adj;
   const int32_t* nw;
   const int32_t* ew;
+  // V-cycles (App. A): block of every node in the partition a clustering
+  // must respect (a cluster may only gather nodes of one block), or null
+  const int32_t* rblk = nullptr;
   int64_t deg(int64_t v) const { return xadj[v + 1] - xadj[v]; }
 };
 
@@ -113,7 +116,8 @@ struct Conn {
 // Returns true with (t, gain) when v should move.
 // ---------------------------------------------------------------------------
 bool choose(int mode, const Conn& conn, int32_t own, int64_t cv, const int64_t* W,
-            int64_t nlabels, int64_t bound, uint64_t hv, int32_t* t_out, int64_t* gain_out) {
+            int64_t nlabels, int64_t bound, uint64_t hv, int32_t* t_out, int64_t* gain_out,
+            const int32_t* rblk = nullptr, int32_t v = 0) {
   const int64_t own_conn = conn.get(own);
   const bool overloaded = (mode == ORC_MODE_REFINE) && W[own] > bound;
   bool have = false;
@@ -123,6 +127,9 @@ bool choose(int mode, const Conn& conn, int32_t own, int64_t cv, const int64_t* 
   auto consider = [&](int32_t C, int64_t c) {
     if (C == own) return;
     if (W[C] + cv > bound) return;
+    // a clustering that respects a partition joins only clusters of v's block
+    // (labels are node ids while clustering, so rblk[C] is the cluster's block)
+    if (rblk && rblk[C] != rblk[v]) return;
     uint64_t h = cand_hash(hv, C);
     if (!have || c > bc || (c == bc && (h < bh || (h == bh && C < bC)))) {
       have = true; bc = c; bh = h; bC = C;
@@ -180,7 +187,8 @@ int64_t sync_subround(int mode, const G& g, int32_t* label, int64_t* W, int64_t 
     conn.build(g, label, v);
     int32_t t;
     int64_t gain;
-    if (choose(mode, conn, label[v], g.nw[v], W, nlabels, bound, hv, &t, &gain))
+    if (choose(mode, conn, label[v], g.nw[v], W, nlabels, bound, hv, &t, &gain,
+               mode == ORC_MODE_CLUSTER ? g.rblk : nullptr, v))
       props.push_back(Prop{v, t, label[v], (int64_t)g.nw[v], gain, (uint32_t)hv});
   }
   conn.clear();
@@ -303,7 +311,8 @@ int64_t seq_cluster_round(const G& g, int32_t* label, int64_t* W, int64_t bound,
     conn.build(g, label, v);
     int32_t t;
     int64_t gain;
-    if (choose(ORC_MODE_CLUSTER, conn, label[v], g.nw[v], W, g.n, bound, hv, &t, &gain)) {
+    if (choose(ORC_MODE_CLUSTER, conn, label[v], g.nw[v], W, g.n, bound, hv, &t, &gain,
+               g.rblk, v)) {
       W[t] += g.nw[v];
       W[label[v]] -= g.nw[v];
       label[v] = t;
@@ -681,6 +690,7 @@ void orc_default_config(orc_config* cfg) {
   cfg->random_order = 0;
   cfg->ensemble = 0;
   cfg->ensemble_size = 0;
+  cfg->vcycles = 1;
 }
 
 uint64_t orc_mix64(uint64_t x) { return mix64(x); }
@@ -709,6 +719,18 @@ int orc_cluster(int32_t variant, int64_t n, const int64_t* xadj, const int32_t* 
   orc_config c;
   if (cfg) c = *cfg; else orc_default_config(&c);
   G g{n, xadj, adj, nw, ew};
+  return cluster_level(variant, g, U, seed, level, c, label_out, rounds_out);
+}
+
+int orc_cluster_in_blocks(int32_t variant, int64_t n, const int64_t* xadj, const int32_t* adj,
+                          const int32_t* nw, const int32_t* ew, int64_t U, uint64_t seed,
+                          int32_t level, const orc_config* cfg, const int32_t* blk,
+                          int32_t* label_out, int32_t* rounds_out) {
+  if (n < 1 || !blk || !label_out) return ORC_EINVAL;
+  orc_config c;
+  if (cfg) c = *cfg; else orc_default_config(&c);
+  G g{n, xadj, adj, nw, ew};
+  g.rblk = blk;
   return cluster_level(variant, g, U, seed, level, c, label_out, rounds_out);
 }
 
@@ -900,6 +922,52 @@ int orc_partition(int32_t variant, int64_t n, const int64_t* xadj, const int32_t
   }
   int32_t rr = 0;
   rc = repair(g0, k, Lmax, seed, cfg, blk.data(), W.data(), &rr);
+  // Iterated V-cycles (Sec. 4 "Iterated Multilevel Algorithms", App. A):
+  // coarsen again with clusterings that respect the current partition (cut
+  // edges are never contracted), start from that partition on the coarsest
+  // graph, refine every level on the way back, repair.  Cycle c uses the key
+  // hkey(seed, VCYCLE, c, 0) in place of the seed.
+  for (int32_t cyc = 1; cyc < std::max(1, cfg.vcycles) && rc != ORC_EINVAL; ++cyc) {
+    const uint64_t sc = hkey(seed, ORC_PH_VCYCLE, (uint64_t)cyc, 0);
+    vector<OG> vco;                        // vco[l-1] is level l of this cycle
+    vector<vector<int32_t>> vmaps, vblk;   // vblk[l]: the partition on level l
+    vblk.push_back(blk);
+    auto vgraph = [&](size_t l) {
+      G g = l == 0 ? g0 : vco[l - 1].view();
+      g.rblk = vblk[l].data();
+      return g;
+    };
+    while (true) {
+      G g = vgraph(vco.size());
+      if (g.n <= T || (int64_t)vco.size() + 1 >= cfg.max_levels) break;
+      vector<int32_t> label((size_t)g.n);
+      coarsen_clustering(variant, g, U, sc, (int32_t)vco.size(), k, cfg, label.data(), nullptr);
+      vector<int32_t> cmap;
+      OG c;
+      rc = contract(g, label.data(), cmap, c);
+      if (rc != ORC_OK) return rc;
+      if (20 * (g.n - c.n) < g.n) break;
+      vector<int32_t> cb((size_t)c.n, 0);
+      for (int64_t v = 0; v < g.n; ++v) cb[cmap[v]] = vblk.back()[v];
+      vmaps.push_back(std::move(cmap));
+      vco.push_back(std::move(c));
+      vblk.push_back(std::move(cb));
+    }
+    const int32_t q2 = (int32_t)vco.size();
+    vector<int32_t> cur = vblk[q2];
+    for (int32_t l = q2; l >= 0; --l) {
+      G g = vgraph(l);
+      g.rblk = nullptr;
+      if (l < q2) {
+        vector<int32_t> fine((size_t)g.n);
+        for (int64_t v = 0; v < g.n; ++v) fine[v] = cur[vmaps[l][v]];
+        cur.swap(fine);
+      }
+      refine_level(variant, g, k, Lmax, sc, ORC_PH_REFINE, l, cfg, cur.data(), W.data(), nullptr);
+    }
+    blk.swap(cur);
+    rc = repair(g0, k, Lmax, sc, cfg, blk.data(), W.data(), &rr);
+  }
   std::copy(blk.begin(), blk.end(), block_out);
   if (cut_out) *cut_out = cut_of(g0, block_out);
   if (maxbw_out) *maxbw_out = max_weight(W.data(), k);

@@ -38,7 +38,7 @@ enum { ORC_MODE_CLUSTER = 0, ORC_MODE_REFINE = 1 };
 /* Hash-domain tags for the counter-based generator (one per phase). */
 enum {
   ORC_PH_CLUSTER = 1, ORC_PH_REFINE = 2, ORC_PH_TRIAL = 3,
-  ORC_PH_GGG = 4, ORC_PH_IPREF = 5, ORC_PH_REPAIR = 6, ORC_PH_ENSEMBLE = 7
+  ORC_PH_GGG = 4, ORC_PH_IPREF = 5, ORC_PH_REPAIR = 6, ORC_PH_ENSEMBLE = 7, ORC_PH_VCYCLE = 8
 };
 enum { ORC_OK = 0, ORC_EINVAL = -1, ORC_EOVERFLOW = -2, ORC_EINFEASIBLE = -3 };
 
@@ -63,6 +63,9 @@ typedef struct orc_config {
                                contracts the overlay of l clusterings             */
   int32_t ensemble_size;    /* l; 0 = the paper's rule (Sec. 5): 18 if k < 16, 7 if
                                k is 16 or 32, 3 if k > 32                           */
+  int32_t vcycles;          /* multilevel cycles (Sec. 4 "Iterated Multilevel
+                               Algorithms", App. A; configuration V, Sec. 5: 3);
+                               1 = one plain multilevel run                         */
 } orc_config;
 
 typedef struct orc_stats {
@@ -117,6 +120,14 @@ int orc_cluster(int32_t variant, int64_t n, const int64_t* xadj, const int32_t* 
  * discarded).  comm_out[v] (n entries) receives the node of the last graph
  * that input node v belongs to; *levels_out the number of contractions
  * kept; level_n_out[0..min(levels, cap-1)] the node counts, input first. */
+/* Size-constrained clustering that respects a partition (App. A): as
+ * orc_cluster, but a node may only join clusters inside its own block blk[v]
+ * (blk: n entries), so every cluster lies inside one block. */
+int orc_cluster_in_blocks(int32_t variant, int64_t n, const int64_t* xadj, const int32_t* adj,
+                          const int32_t* nw, const int32_t* ew, int64_t U, uint64_t seed,
+                          int32_t level, const orc_config* cfg, const int32_t* blk,
+                          int32_t* label_out, int32_t* rounds_out);
+
 /* Overlay of two clusterings (Sec. 4 "Ensemble Clusterings"): two nodes
  * share an overlay cluster iff they share a cluster in a and in b.  Overlay
  * ids are numbered 0, 1, ... in the order the (a[v], b[v]) pairs first occur

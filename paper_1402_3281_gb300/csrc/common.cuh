@@ -97,7 +97,7 @@ __host__ __device__ __forceinline__ uint64_t hkey(uint64_t seed, uint64_t phase,
 
 enum Phase : int32_t {
   PH_CLUSTER = 1, PH_REFINE = 2, PH_TRIAL = 3, PH_GGG = 4, PH_IPREF = 5, PH_REPAIR = 6,
-  PH_ENSEMBLE = 7
+  PH_ENSEMBLE = 7, PH_VCYCLE = 8
 };
 enum Mode : int32_t { MODE_CLUSTER = 0, MODE_REFINE = 1, MODE_REPAIR = 2 };
 
@@ -336,6 +336,7 @@ struct LPRun {
   bool use_active = false;     // local search: active nodes
   bool raw_key = false;        // slot seed is used as the round key itself
   bool graph = false;          // run the rounds as one CUDA graph (WHILE node)
+  const int32_t* rblk = nullptr;  // clustering: respect this partition (V-cycles)
 };
 // Runs `run.rounds` synchronous LP rounds on `lv` for every slot not marked
 // done; label/W are updated in place.  Returns the number of arcs scanned.
@@ -453,6 +454,10 @@ void ip_select_copy(const std::vector<SelectTask>& tasks, const int64_t* cut2,
                     const int32_t* ip_label, wgt_t* Wg, int32_t* best, int64_t* ipcut,
                     cudaStream_t s);
 // fine_blk[v] = coarse_blk[cmap[v]] where cmap[v] >= 0.
+// V-cycles: coarse_blk[cmap[v]] = fine_blk[v] for every fine node with
+// cmap[v] >= 0 (all members of a coarse node share one block).
+void lift_blocks(const int32_t* cmap, const int32_t* fine_blk, int32_t* coarse_blk, int64_t N,
+                 cudaStream_t s);
 void project(const int32_t* cmap, const int32_t* coarse_blk, int32_t* fine_blk, int64_t N,
              cudaStream_t s);
 // Block weights of every slot from scratch: W[label[v]] += nw[v].

@@ -47,7 +47,8 @@ sclap_config resolve_cfg(const sclap_config* c) {
   if (r.lp_rounds_coarse < 0 || r.lp_rounds_refine < 0 || r.f < 1 || r.coarse_min_nodes < 1 ||
       r.ip_trials < 1 || r.sub_rounds < 1 || r.sub_rounds > 64 || r.repair_rounds < 0 ||
       r.max_levels < 1 || r.cluster_active < 0 || r.cluster_active > 1 || r.graph_rounds < 0 ||
-      r.graph_rounds > 1 || r.ensemble < 0 || r.ensemble > 1 || r.ensemble_size < 0)
+      r.graph_rounds > 1 || r.ensemble < 0 || r.ensemble > 1 || r.ensemble_size < 0 ||
+      r.vcycles < 0)
     throw Error(SCLAP_EINVAL, "invalid sclap_config");
   return r;
 }
@@ -597,111 +598,135 @@ void run_valid_batch(const std::vector<GIn>& gs, const std::vector<int64_t>& cV,
   std::vector<std::unique_ptr<Level>> lv;
   lv.push_back(std::move(level0));
 
-  // ---------------- coarsening
-  std::vector<char> coarsening(B, 0);
-  for (int g = 0; g < B; ++g) coarsening[g] = (gs[g].n > st[g].T && 1 < cfg.max_levels) ? 1 : 0;
-  for (int L = 0;; ++L) {
-    bool any = false;
-    for (int g = 0; g < B; ++g) any = any || coarsening[g];
-    if (!any) break;
-    Level& cur = *lv[L];
-    const LevelView v = cur.view();
-    std::vector<int64_t> h_bound(B);
-    std::vector<uint64_t> h_seed(B);
-    std::vector<int32_t> h_level(B, L), h_nlab(B, 0), h_done(B);
-    for (int g = 0; g < B; ++g) {
-      h_bound[g] = st[g].U;
-      h_seed[g] = st[g].seed;
-      h_done[g] = coarsening[g] ? 0 : 1;
-    }
-    std::vector<int64_t> h_loff(cur.noff.begin(), cur.noff.end() - 1);
-    Slots sl(s, B, cur.noff_d.p, h_loff, h_bound, h_seed, h_level, h_nlab, h_done);
-    DevBuf<int32_t> label(std::max<int64_t>(v.N, 1), s);
-    DevBuf<wgt_t> W(std::max<int64_t>(v.N, 1), s);
-    k_iota<<<grid_for(v.N, 256, (int64_t)sms * 16), 256, 0, s>>>(label.p, v.N); SCLAP_NOTE_LAUNCH("k_iota");
-    k_w_from_nw<<<grid_for(v.N, 256, (int64_t)sms * 16), 256, 0, s>>>(v.nw, v.N, W.p); SCLAP_NOTE_LAUNCH("k_w_from_nw");
-    SCLAP_LAUNCH_CHECK();
-    LPRun run;
-    run.mode = MODE_CLUSTER;
-    run.phase = PH_CLUSTER;
-    run.rounds = cfg.lp_rounds_coarse;
-    run.sub_rounds = cfg.sub_rounds;
-    run.graph = cfg.graph_rounds != 0;
-    run.use_active = cfg.cluster_active != 0;
-    lp_arcs += lp_run(v, sl.sp, label.p, W.p, v.N, run, d_err.p, s);
-    const std::vector<int32_t> rr = sl.host_rounds(s);
+  // ---------------- coarsening (as a stage: later V-cycles run it again)
+  // Builds the hierarchy above lv[0] (the only level when called).  seeds:
+  // per-slot keys of the clusterings; respect: clusterings stay inside the
+  // blocks of lv[L]->blk (V-cycles), coarse levels get the projected blocks;
+  // record: fill the statistics.  q[g] receives slot g's coarsest level.
+  auto coarsen = [&](const std::vector<uint64_t>& seeds, bool respect, bool record,
+                     std::vector<int32_t>& q) {
+    q.assign(B, 0);
+    std::vector<char> coarsening(B, 0);
     for (int g = 0; g < B; ++g)
-      if (coarsening[g]) st[g].crounds.push_back(rr[g]);
-    if (cfg.ensemble) {
-      // ensemble clusterings: clustering j >= 1 of every slot whose ensemble
-      // is that large, overlaid onto the labels so far
-      std::vector<int32_t> ell(B, 1);
-      int32_t ell_max = 1;
-      for (int g = 0; g < B; ++g)
-        if (coarsening[g]) {
-          ell[g] = ensemble_size_for(st[g].k, cfg);
-          ell_max = std::max(ell_max, ell[g]);
-        }
-      if (ell_max > 1) {
-        DevBuf<int32_t> C(std::max<int64_t>(v.N, 1), s), part(B, s);
-        for (int32_t j = 1; j < ell_max; ++j) {
-          std::vector<uint64_t> sj(B);
-          std::vector<int32_t> dj(B), pj(B);
-          for (int g = 0; g < B; ++g) {
-            pj[g] = coarsening[g] && j < ell[g] ? 1 : 0;
-            dj[g] = pj[g] ? 0 : 1;
-            sj[g] = hkey(st[g].seed, PH_ENSEMBLE, (uint64_t)L, (uint64_t)j);
+      coarsening[g] = (gs[g].n > st[g].T && 1 < cfg.max_levels) ? 1 : 0;
+    for (int L = 0;; ++L) {
+      bool any = false;
+      for (int g = 0; g < B; ++g) any = any || coarsening[g];
+      if (!any) break;
+      Level& cur = *lv[L];
+      const LevelView v = cur.view();
+      std::vector<int64_t> h_bound(B);
+      std::vector<int32_t> h_level(B, L), h_nlab(B, 0), h_done(B);
+      for (int g = 0; g < B; ++g) {
+        h_bound[g] = st[g].U;
+        h_done[g] = coarsening[g] ? 0 : 1;
+      }
+      std::vector<int64_t> h_loff(cur.noff.begin(), cur.noff.end() - 1);
+      Slots sl(s, B, cur.noff_d.p, h_loff, h_bound, seeds, h_level, h_nlab, h_done);
+      DevBuf<int32_t> label(std::max<int64_t>(v.N, 1), s);
+      DevBuf<wgt_t> W(std::max<int64_t>(v.N, 1), s);
+      k_iota<<<grid_for(v.N, 256, (int64_t)sms * 16), 256, 0, s>>>(label.p, v.N); SCLAP_NOTE_LAUNCH("k_iota");
+      k_w_from_nw<<<grid_for(v.N, 256, (int64_t)sms * 16), 256, 0, s>>>(v.nw, v.N, W.p); SCLAP_NOTE_LAUNCH("k_w_from_nw");
+      SCLAP_LAUNCH_CHECK();
+      LPRun run;
+      run.mode = MODE_CLUSTER;
+      run.phase = PH_CLUSTER;
+      run.rounds = cfg.lp_rounds_coarse;
+      run.sub_rounds = cfg.sub_rounds;
+      run.graph = cfg.graph_rounds != 0;
+      run.use_active = cfg.cluster_active != 0;
+      run.rblk = respect ? cur.blk.p : nullptr;
+      lp_arcs += lp_run(v, sl.sp, label.p, W.p, v.N, run, d_err.p, s);
+      const std::vector<int32_t> rr = sl.host_rounds(s);
+      if (record)
+        for (int g = 0; g < B; ++g)
+          if (coarsening[g]) st[g].crounds.push_back(rr[g]);
+      if (cfg.ensemble) {
+        // ensemble clusterings: clustering j >= 1 of every slot whose ensemble
+        // is that large, overlaid onto the labels so far
+        std::vector<int32_t> ell(B, 1);
+        int32_t ell_max = 1;
+        for (int g = 0; g < B; ++g)
+          if (coarsening[g]) {
+            ell[g] = ensemble_size_for(st[g].k, cfg);
+            ell_max = std::max(ell_max, ell[g]);
           }
-          Slots slj(s, B, cur.noff_d.p, h_loff, h_bound, sj, h_level, h_nlab, dj);
-          k_iota<<<grid_for(v.N, 256, (int64_t)sms * 16), 256, 0, s>>>(C.p, v.N); SCLAP_NOTE_LAUNCH("k_iota");
-          k_w_from_nw<<<grid_for(v.N, 256, (int64_t)sms * 16), 256, 0, s>>>(v.nw, v.N, W.p); SCLAP_NOTE_LAUNCH("k_w_from_nw");
-          lp_arcs += lp_run(v, slj.sp, C.p, W.p, v.N, run, d_err.p, s);
-          part.upload(pj);
-          overlay_labels(v, part.p, label.p, C.p, d_err.p, s);
+        if (ell_max > 1) {
+          DevBuf<int32_t> C(std::max<int64_t>(v.N, 1), s), part(B, s);
+          for (int32_t j = 1; j < ell_max; ++j) {
+            std::vector<uint64_t> sj(B);
+            std::vector<int32_t> dj(B), pj(B);
+            for (int g = 0; g < B; ++g) {
+              pj[g] = coarsening[g] && j < ell[g] ? 1 : 0;
+              dj[g] = pj[g] ? 0 : 1;
+              sj[g] = hkey(seeds[g], PH_ENSEMBLE, (uint64_t)L, (uint64_t)j);
+            }
+            Slots slj(s, B, cur.noff_d.p, h_loff, h_bound, sj, h_level, h_nlab, dj);
+            k_iota<<<grid_for(v.N, 256, (int64_t)sms * 16), 256, 0, s>>>(C.p, v.N); SCLAP_NOTE_LAUNCH("k_iota");
+            k_w_from_nw<<<grid_for(v.N, 256, (int64_t)sms * 16), 256, 0, s>>>(v.nw, v.N, W.p); SCLAP_NOTE_LAUNCH("k_w_from_nw");
+            lp_arcs += lp_run(v, slj.sp, C.p, W.p, v.N, run, d_err.p, s);
+            part.upload(pj);
+            overlay_labels(v, part.p, label.p, C.p, d_err.p, s);
+          }
         }
       }
-    }
-    ContractWork cw;
-    std::vector<int64_t> nc;
-    contract_rank(v, cur.noff, label.p, cw, nc, s);
-    std::vector<uint8_t> keep(B, 0);
-    bool anykeep = false;
-    for (int g = 0; g < B; ++g) {
-      if (!coarsening[g]) continue;
-      const int64_t n = cur.noff[g + 1] - cur.noff[g];
-      if (20 * (n - nc[g]) < n) {
-        coarsening[g] = 0;   // shrink below 5%: this level stays the coarsest
-      } else {
-        keep[g] = 1;
-        anykeep = true;
+      ContractWork cw;
+      std::vector<int64_t> nc;
+      contract_rank(v, cur.noff, label.p, cw, nc, s);
+      std::vector<uint8_t> keep(B, 0);
+      bool anykeep = false;
+      for (int g = 0; g < B; ++g) {
+        if (!coarsening[g]) continue;
+        const int64_t n = cur.noff[g + 1] - cur.noff[g];
+        if (20 * (n - nc[g]) < n) {
+          coarsening[g] = 0;   // shrink below 5%: this level stays the coarsest
+        } else {
+          keep[g] = 1;
+          anykeep = true;
+        }
       }
+      if (!anykeep) break;
+      cur.cmap.alloc(std::max<int64_t>(v.N, 1), s);
+      CoarseLevel co;
+      contract_build(v, cur.noff, label.p, cw, keep, cur.cmap.p, co, d_err.p, s);
+      std::unique_ptr<Level> nx(new Level());
+      nx->N = co.N;
+      nx->M = co.M;
+      nx->row_ptr = std::move(co.row_ptr);
+      nx->col = std::move(co.col);
+      nx->ew = std::move(co.ew);
+      nx->nw = std::move(co.nw);
+      nx->gid = std::move(co.gid);
+      nx->noff_d = std::move(co.noff_d);
+      nx->noff = co.noff;
+      nx->aoff = co.aoff;
+      if (respect) {
+        // the partition moves up with the clusters (all members share a block)
+        nx->blk.alloc(std::max<int64_t>(nx->N, 1), s);
+        lift_blocks(cur.cmap.p, cur.blk.p, nx->blk.p, v.N, s);
+      }
+      for (int g = 0; g < B; ++g) {
+        if (!keep[g]) continue;
+        q[g] = L + 1;
+        const int64_t n = nx->noff[g + 1] - nx->noff[g];
+        if (record) {
+          st[g].n_at.push_back(n);
+          st[g].m_at.push_back(nx->aoff[g + 1] - nx->aoff[g]);
+        }
+        coarsening[g] = (n > st[g].T && L + 2 < cfg.max_levels) ? 1 : 0;
+      }
+      lv.push_back(std::move(nx));
     }
-    if (!anykeep) break;
-    cur.cmap.alloc(std::max<int64_t>(v.N, 1), s);
-    CoarseLevel co;
-    contract_build(v, cur.noff, label.p, cw, keep, cur.cmap.p, co, d_err.p, s);
-    std::unique_ptr<Level> nx(new Level());
-    nx->N = co.N;
-    nx->M = co.M;
-    nx->row_ptr = std::move(co.row_ptr);
-    nx->col = std::move(co.col);
-    nx->ew = std::move(co.ew);
-    nx->nw = std::move(co.nw);
-    nx->gid = std::move(co.gid);
-    nx->noff_d = std::move(co.noff_d);
-    nx->noff = co.noff;
-    nx->aoff = co.aoff;
-    for (int g = 0; g < B; ++g) {
-      if (!keep[g]) continue;
-      st[g].q = L + 1;
-      const int64_t n = nx->noff[g + 1] - nx->noff[g];
-      st[g].n_at.push_back(n);
-      st[g].m_at.push_back(nx->aoff[g + 1] - nx->aoff[g]);
-      coarsening[g] = (n > st[g].T && L + 2 < cfg.max_levels) ? 1 : 0;
-    }
-    lv.push_back(std::move(nx));
+    check_err(d_err.p, s);
+  };
+
+  std::vector<uint64_t> seed0(B);
+  for (int g = 0; g < B; ++g) seed0[g] = st[g].seed;
+  {
+    std::vector<int32_t> q;
+    coarsen(seed0, false, true, q);
+    for (int g = 0; g < B; ++g) st[g].q = q[g];
   }
-  check_err(d_err.p, s);
   const int nlev = (int)lv.size();
   for (int L = 0; L < nlev; ++L) lv[L]->blk.alloc(std::max<int64_t>(lv[L]->N, 1), s);
 
@@ -723,47 +748,58 @@ void run_valid_batch(const std::vector<GIn>& gs, const std::vector<int64_t>& cV,
     }
   }
 
-  // ---------------- uncoarsening: project, then LP local search
+  // ---------------- uncoarsening: project, then LP local search (a stage)
   std::vector<int64_t> h_Lmax(B), h_boff(B);
-  std::vector<uint64_t> h_seed(B);
   std::vector<int32_t> h_k(B);
   for (int g = 0; g < B; ++g) {
     h_Lmax[g] = st[g].Lmax;
     h_boff[g] = st[g].boff;
-    h_seed[g] = st[g].seed;
     h_k[g] = st[g].k;
     st[g].rrounds.assign(st[g].q + 1, 0);
   }
-  for (int L = nlev - 2; L >= 0; --L) {
-    Level& F = *lv[L];
-    project(F.cmap.p, lv[L + 1]->blk.p, F.blk.p, F.N, s);
-    lv[L + 1].reset();
-    std::vector<int32_t> h_level(B, L), h_done(B);
-    bool any = false;
-    for (int g = 0; g < B; ++g) {
-      h_done[g] = st[g].q > L ? 0 : 1;
-      any = any || !h_done[g];
+  // From the top of lv down to the input level: project, then refine every
+  // slot whose hierarchy reaches that level (below its coarsest level, and
+  // at it too when refine_top: the partition there was projected up, not
+  // computed by initial partitioning).
+  auto uncoarsen = [&](const std::vector<uint64_t>& seeds, const std::vector<int32_t>& q,
+                       bool refine_top, bool record) {
+    const int top = (int)lv.size() - 1;
+    for (int L = refine_top ? top : top - 1; L >= 0; --L) {
+      Level& F = *lv[L];
+      if (L < top) {
+        project(F.cmap.p, lv[L + 1]->blk.p, F.blk.p, F.N, s);
+        lv[L + 1].reset();
+      }
+      std::vector<int32_t> h_level(B, L), h_done(B);
+      bool any = false;
+      for (int g = 0; g < B; ++g) {
+        h_done[g] = (refine_top ? q[g] >= L : q[g] > L) ? 0 : 1;
+        any = any || !h_done[g];
+      }
+      if (!any) continue;
+      Slots sl(s, B, F.noff_d.p, h_boff, h_Lmax, seeds, h_level, h_k, h_done);
+      LPRun run;
+      run.mode = MODE_REFINE;
+      run.phase = PH_REFINE;
+      run.rounds = cfg.lp_rounds_refine;
+      run.sub_rounds = cfg.sub_rounds;
+      run.graph = cfg.graph_rounds != 0;
+      run.use_active = true;
+      lp_arcs += lp_run(F.view(), sl.sp, F.blk.p, Wg.p, Ktot, run, d_err.p, s);
+      if (record) {
+        const std::vector<int32_t> rr = sl.host_rounds(s);
+        for (int g = 0; g < B; ++g)
+          if (q[g] > L) st[g].rrounds[L] = rr[g];
+      }
     }
-    if (!any) continue;
-    Slots sl(s, B, F.noff_d.p, h_boff, h_Lmax, h_seed, h_level, h_k, h_done);
-    LPRun run;
-    run.mode = MODE_REFINE;
-    run.phase = PH_REFINE;
-    run.rounds = cfg.lp_rounds_refine;
-    run.sub_rounds = cfg.sub_rounds;
-    run.graph = cfg.graph_rounds != 0;
-    run.use_active = true;
-    lp_arcs += lp_run(F.view(), sl.sp, F.blk.p, Wg.p, Ktot, run, d_err.p, s);
-    const std::vector<int32_t> rr = sl.host_rounds(s);
-    for (int g = 0; g < B; ++g)
-      if (st[g].q > L) st[g].rrounds[L] = rr[g];
-  }
-
-  // ---------------- balance repair on the input level
-  Level& F0 = *lv[0];
-  if (cfg.repair_rounds > 0) {
+    lv.resize(1);
+  };
+  // ---------------- balance repair on the input level (a stage)
+  auto repair = [&](const std::vector<uint64_t>& seeds) {
+    Level& F0 = *lv[0];
+    if (cfg.repair_rounds <= 0) return;
     std::vector<int32_t> h_level(B, 0), h_done(B, 0);
-    Slots sl(s, B, F0.noff_d.p, h_boff, h_Lmax, h_seed, h_level, h_k, h_done);
+    Slots sl(s, B, F0.noff_d.p, h_boff, h_Lmax, seeds, h_level, h_k, h_done);
     LPRun run;
     run.mode = MODE_REPAIR;
     run.phase = PH_REPAIR;
@@ -772,8 +808,30 @@ void run_valid_batch(const std::vector<GIn>& gs, const std::vector<int64_t>& cV,
     run.graph = cfg.graph_rounds != 0;
     run.stop_rule = false;
     lp_arcs += lp_run(F0.view(), sl.sp, F0.blk.p, Wg.p, Ktot, run, d_err.p, s);
+  };
+  {
+    std::vector<int32_t> q(B);
+    for (int g = 0; g < B; ++g) q[g] = st[g].q;
+    uncoarsen(seed0, q, false, true);
   }
+  repair(seed0);
   check_err(d_err.p, s);
+
+  // ---------------- iterated V-cycles (Sec. 4 "Iterated Multilevel
+  // Algorithms", App. A): coarsen again with clusterings inside the blocks
+  // of the current partition (cut edges are never contracted), start from
+  // that partition on the coarsest level, refine every level on the way back,
+  // repair.  Cycle c uses hkey(seed, VCYCLE, c, 0) in place of the seed.
+  for (int32_t cyc = 1; cyc < std::max(1, cfg.vcycles); ++cyc) {
+    std::vector<uint64_t> sc(B);
+    for (int g = 0; g < B; ++g) sc[g] = hkey(st[g].seed, PH_VCYCLE, (uint64_t)cyc, 0);
+    std::vector<int32_t> q;
+    coarsen(sc, true, false, q);
+    uncoarsen(sc, q, true, false);
+    repair(sc);
+    check_err(d_err.p, s);
+  }
+  Level& F0 = *lv[0];
 
   // ---------------- cut, outputs
   DevBuf<int64_t> cut2(B, s);
@@ -942,6 +1000,7 @@ void sclap_default_config(sclap_config* c) {
   c->graph_rounds = 0;
   c->ensemble = 0;
   c->ensemble_size = 0;
+  c->vcycles = 1;
 }
 
 const char* sclap_error_string(int code) {

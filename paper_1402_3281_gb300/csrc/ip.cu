@@ -361,6 +361,15 @@ __global__ void k_project(const int32_t* __restrict__ cmap, const int32_t* __res
   }
 }
 
+__global__ void k_lift_blocks(const int32_t* __restrict__ cmap, const int32_t* __restrict__ fblk,
+                              int32_t* __restrict__ cblk, int64_t N) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t c = cmap[v];
+    if (c >= 0) cblk[c] = fblk[v];
+  }
+}
+
 __global__ void k_block_weights(const int32_t* __restrict__ label, const int32_t* __restrict__ nw,
                                 int64_t N, wgt_t* __restrict__ W) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N;
@@ -517,6 +526,14 @@ void project(const int32_t* cmap, const int32_t* coarse_blk, int32_t* fine_blk, 
   if (N <= 0) return;
   k_project<<<grid_for(N, 256, (int64_t)num_sms() * 16), 256, 0, s>>>(cmap, coarse_blk,
                                                                       fine_blk, N); SCLAP_NOTE_LAUNCH("k_project");
+  SCLAP_LAUNCH_CHECK();
+}
+
+void lift_blocks(const int32_t* cmap, const int32_t* fine_blk, int32_t* coarse_blk, int64_t N,
+                 cudaStream_t s) {
+  if (N <= 0) return;
+  k_lift_blocks<<<grid_for(N, 256, (int64_t)num_sms() * 16), 256, 0, s>>>(cmap, fine_blk,
+                                                                          coarse_blk, N); SCLAP_NOTE_LAUNCH("k_lift_blocks");
   SCLAP_LAUNCH_CHECK();
 }
 

@@ -83,6 +83,9 @@ struct LPArgs {
   int32_t* live;
   int32_t rounds_max;
   int32_t stop_rule;
+  // V-cycles: block of every node in a partition the clustering must respect
+  // (a node joins only clusters of its own block), or NULL
+  const int32_t* rblk;
   int32_t* err;
 };
 
@@ -101,7 +104,7 @@ __device__ __forceinline__ void sub_range(const LPArgs& a, int sub, int b0, int 
 }
 
 struct NodeCtx {
-  int32_t v, slot, own, cv;
+  int32_t v, slot, own, cv, vb;
   int64_t bound, loff, rs, re;
   uint64_t hv;
 };
@@ -119,7 +122,16 @@ __device__ __forceinline__ NodeCtx load_node(const LPArgs& a, int64_t i) {
   c.bound = a.bound[c.slot];
   c.loff = a.loff[c.slot];
   c.hv = mix64(a.rkey[c.slot] ^ (uint64_t)(c.v - a.noff[c.slot]));
+  c.vb = a.rblk ? a.rblk[c.v] : 0;
   return c;
+}
+
+// Block of cluster C when clustering must respect a partition (labels are
+// node ids while clustering, so it is the block of node C); vb otherwise, so
+// the comparison passes.  Loaded only for candidates still in question.
+__device__ __forceinline__ int32_t cand_block(const LPArgs& a, const NodeCtx& c, bool need,
+                                              int32_t C) {
+  return a.rblk && need ? a.rblk[C] : c.vb;
 }
 
 __device__ __forceinline__ Cand make_cand(const NodeCtx& c, int32_t C, int64_t conn) {
@@ -334,14 +346,19 @@ __device__ __forceinline__ void sorted_row_best(const LPArgs& a, const NodeCtx& 
     run[j] = (j > 0 && C[j] == C[j - 1]) ? prev + (SumT)w[j] : (SumT)w[j];
     end[j] = C[j] != INT32_MAX && (j == MAXD - 1 || C[j] != C[j + 1]);
   }
-  int32_t Wl[MAXD];
+  int32_t Wl[MAXD], Bl[MAXD];
 #pragma unroll
-  for (int j = 0; j < MAXD; ++j) Wl[j] = end[j] & (C[j] != c.own) ? a.W[C[j]] : 0;
+  for (int j = 0; j < MAXD; ++j) {
+    const bool q = end[j] & (C[j] != c.own);
+    Wl[j] = q ? a.W[C[j]] : 0;
+    Bl[j] = cand_block(a, c, q, C[j]);
+  }
 #pragma unroll
   for (int j = 0; j < MAXD; ++j) {
     const bool own = end[j] & (C[j] == c.own);
     oc = own ? (long long)run[j] : oc;
-    const bool elig = end[j] & (C[j] != c.own) & ((int64_t)Wl[j] + c.cv <= c.bound);
+    const bool elig = end[j] & (C[j] != c.own) & ((int64_t)Wl[j] + c.cv <= c.bound) &
+                      (Bl[j] == c.vb);
     const int32_t Cl = (int32_t)(C[j] - c.loff);
     const Cand x{(int64_t)run[j], mix64(c.hv ^ (uint64_t)(uint32_t)Cl), Cl};
     best = cand_pick(elig & cand_better(x, best), x, best);
@@ -555,7 +572,7 @@ __global__ void __launch_bounds__(NT) k_propose_cta(LPArgs a, int32_t sub, int32
         if (K == -1) continue;
         const int64_t conn = (int64_t)vals[j];
         if (K == c.own) oc = conn;
-        else if (!ov && (int64_t)a.W[K] + c.cv <= c.bound) {
+        else if (!ov && (int64_t)a.W[K] + c.cv <= c.bound && cand_block(a, c, true, K) == c.vb) {
           Cand x = make_cand(c, K, conn);
           if (cd.conn < 0 || cand_better(x, cd)) cd = x;
         }
@@ -664,16 +681,19 @@ __global__ void __launch_bounds__(WPC * 32) k_propose_warp(LPArgs a, int32_t sub
       __syncwarp();
       for (int32_t b = lane; b < nl; b += 32) vals[b] = 0;
     } else {
-      int32_t Wk[4];
+      int32_t Wk[4], Bk[4];
 #pragma unroll
-      for (int t = 0; t < 4; ++t)
-        Wk[t] = ((created >> t) & 1u) && C[t] != c.own && !ov ? a.W[C[t]] : 0;
+      for (int t = 0; t < 4; ++t) {
+        const bool q = ((created >> t) & 1u) && C[t] != c.own && !ov;
+        Wk[t] = q ? a.W[C[t]] : 0;
+        Bk[t] = cand_block(a, c, q, C[t]);
+      }
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
         if (!((created >> t) & 1u)) continue;
         const int64_t conn = (int64_t)vals[slot[t]];
         if (C[t] == c.own) { oc = conn; has_oc = true; continue; }
-        if (ov || (int64_t)Wk[t] + c.cv > c.bound) continue;
+        if (ov || (int64_t)Wk[t] + c.cv > c.bound || Bk[t] != c.vb) continue;
         const Cand x = make_cand(c, C[t], conn);
         if (cd.conn < 0 || cand_better(x, cd)) cd = x;
       }
@@ -806,6 +826,7 @@ __global__ void __launch_bounds__(NT) k_propose_blk(LPArgs a, int32_t sub, int32
         const int64_t conn = (int64_t)vals[s];
         if (K == c.own) { oc = conn; continue; }
         if (ov || (int64_t)a.W[K] + c.cv > c.bound) continue;
+        if (cand_block(a, c, true, K) != c.vb) continue;
         Cand x = make_cand(c, K, conn);
         if (cd.conn < 0 || cand_better(x, cd)) cd = x;
       }
@@ -1430,6 +1451,7 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, wgt_t*
   int32_t* const d_cont = rstate.p + 2;
   a.rounds_max = run.rounds;
   a.stop_rule = run.stop_rule ? 1 : 0;
+  a.rblk = run.mode == MODE_CLUSTER ? run.rblk : nullptr;
   a.act[0] = track_active ? act_a.p : nullptr;
   a.act[1] = track_active ? act_b.p : nullptr;
 

@@ -44,7 +44,7 @@ class Config(C.Structure):
     _fields_ = [(n, C.c_int32) for n in (
         "lp_rounds_coarse", "lp_rounds_refine", "f", "coarse_min_nodes", "ip_trials",
         "sub_rounds", "repair_rounds", "max_levels", "cluster_active", "graph_rounds",
-        "ensemble", "ensemble_size")]
+        "ensemble", "ensemble_size", "vcycles")]
 
 
 class Stats(C.Structure):

@@ -323,6 +323,31 @@ def test_batch_ensemble_mixed_sizes_equals_oracle():
         assert np.array_equal(r.block.cpu().numpy(), ref.block)
 
 
+@pytest.mark.parametrize("name,k,extra", [("rmat16", 2, {}), ("rgg", 8, {}), ("weighted", 5, {}),
+                                          ("hub", 16, {}), ("rmat12", 4, {"ensemble": 1}),
+                                          ("rgg", 3, {"cluster_active": 1})])
+def test_partition_vcycles_bit_exact(name, k, extra):
+    """Iterated V-cycles (configuration V, 3 cycles), alone and combined."""
+    g = GRAPHS[name]()
+    ref = O.partition(g, k, 0.03, seed=8, cfg=O.config(vcycles=3, **extra))
+    res = P.sclap_partition_device(*dg(g), k=k, eps=0.03, seed=8,
+                                   cfg=P.default_config(vcycles=3, **extra))
+    assert (res.status, res.cut) == (ref.status, ref.cut)
+    assert np.array_equal(res.block.cpu().numpy(), ref.block)
+
+
+def test_batch_vcycles_equals_oracle():
+    graphs = [(gg.rmat(10 + i % 4, 8, 90 + i), [2, 4, 8, 16][i % 4]) for i in range(5)]
+    graphs += [(gg.rgg2d(1200 + 800 * i, 95 + i), [2, 4, 8][i % 3]) for i in range(4)]
+    items = [dict(row_ptr=dt(g.row_ptr), col=dt(g.col), k=k, eps=0.03, seed=i)
+             for i, (g, k) in enumerate(graphs)]
+    out = P.sclap_partition_batch(items, device=True, cfg=P.default_config(vcycles=3))
+    for i, ((g, k), r) in enumerate(zip(graphs, out)):
+        ref = O.partition(g, k, 0.03, seed=i, cfg=O.config(vcycles=3))
+        assert (r.status, r.cut) == (ref.status, ref.cut)
+        assert np.array_equal(r.block.cpu().numpy(), ref.block)
+
+
 def test_partition_host_api_and_seeds():
     g = gg.rmat(14, 8, 3)
     for seed in (0, 1, 2):

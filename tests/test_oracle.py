@@ -566,3 +566,61 @@ def test_ensemble_partition_is_balanced_and_counted(k):
     Lmax, _ = O.bounds(int(g.node_w.sum()), int(g.node_w.max()), k, 0.03)
     assert np.bincount(r.block, minlength=k).max() <= Lmax
     assert r.cut == O.cut(g, r.block)
+
+
+# ------------------------------------------------------------- V-cycles
+# Iterated V-cycles (Sec. 4 "Iterated Multilevel Algorithms", App. A): later
+# cycles coarsen with clusterings inside the blocks of the current partition,
+# start from it on the coarsest graph and refine on the way back.
+
+def _restricted_clusters_ok(g, lab, blk):
+    """Every cluster lies inside one block."""
+    for c in np.unique(lab):
+        if len(np.unique(blk[lab == c])) != 1:
+            return False
+    return True
+
+
+@pytest.mark.parametrize("variant", [O.SYNC, O.SEQ])
+def test_vcycles_one_equals_plain(variant):
+    g = gg.rmat(12, 8, 3)
+    a = O.partition(g, 4, 0.03, seed=2, variant=variant, cfg=O.config(vcycles=1))
+    b = O.partition(g, 4, 0.03, seed=2, variant=variant)
+    assert a.cut == b.cut and np.array_equal(a.block, b.block)
+
+
+@pytest.mark.parametrize("variant", [O.SYNC, O.SEQ])
+def test_clustering_in_blocks(variant):
+    g = gg.rmat(12, 8, 4)
+    U = 50
+    blk = np.random.default_rng(1).integers(0, 3, g.n).astype(np.int32)
+    lab, _ = O.cluster_in_blocks(g, U, 5, blk, variant=variant)
+    assert _restricted_clusters_ok(g, lab, blk)
+    assert np.bincount(lab, weights=g.node_w, minlength=g.n).max() <= U
+    # one block for everybody: plain clustering
+    same, _ = O.cluster_in_blocks(g, U, 5, np.zeros(g.n, np.int32), variant=variant)
+    assert np.array_equal(same, O.cluster(g, U, 5, variant=variant)[0])
+    # a block per node: nothing can merge
+    alone, _ = O.cluster_in_blocks(g, U, 5, np.arange(g.n, dtype=np.int32), variant=variant)
+    assert np.array_equal(alone, np.arange(g.n))
+
+
+@pytest.mark.parametrize("variant", [O.SYNC, O.SEQ])
+@pytest.mark.parametrize("maker,k", [(lambda: gg.rmat(13, 8, 5), 2), (lambda: gg.rgg2d(8000, 3), 8),
+                                     (lambda: gg.random_weights(gg.rmat(12, 8, 1), 2), 4)])
+def test_vcycles_never_worsen_a_balanced_cut(variant, maker, k):
+    """A respecting clustering contracts no cut edge, so a cycle starts from
+    the previous cut; sequential refinement of a balanced partition makes
+    only positive-gain moves, so the cut can only drop (App. A).  In the
+    synchronous variant two adjacent nodes of one colour class may move
+    together, so there it is a property of these instances, not a theorem."""
+    g = maker()
+    Lmax, _ = O.bounds(int(g.node_w.sum()), int(g.node_w.max()), k, 0.03)
+    prev = None
+    for V in (1, 2, 3):
+        r = O.partition(g, k, 0.03, seed=7, variant=variant, cfg=O.config(vcycles=V))
+        assert r.cut == O.cut(g, r.block)
+        assert np.bincount(r.block, weights=g.node_w, minlength=k).max() <= Lmax
+        if prev is not None:
+            assert r.cut <= prev
+        prev = r.cut
