@@ -59,6 +59,10 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-single", action="store_true")
+    ap.add_argument("--workload", default="batched", choices=["batched", "large"],
+                    help="batched: the 512-graph batch (default); large: R-MAT scale 22 and "
+                         "RGG 2^22, one graph per call, both round drivers")
     ap.add_argument("--graph-rounds", action="store_true",
                     help="run each level's LP rounds as one CUDA graph (device-side loop)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -281,8 +285,84 @@ def serve_stream(P, graphs, lam, count, ref_cuts, seed=0):
             "equal_cut": bool(same)}
 
 
+def large_graphs():
+    """The large single graphs: R-MAT scale 22 (4,194,304 nodes, edge factor
+    16) and a 2D random geometric graph with 2^22 nodes, both seed 0."""
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(2) as pool:
+        a = pool.apply_async(gg.rmat, (22, 16, 0))
+        b = pool.apply_async(gg.rgg2d, (1 << 22, 0))
+        return [("rmat22-ef16", a.get()), ("rgg2d-2^22", b.get())]
+
+
+def large_workload(args):
+    """One big graph per call, k in {2, 8, 32, 64}, seeds 0..4, under the
+    host-driven and the CUDA-graph round drivers.  Every result is checked:
+    balance (every block <= Lmax), the cut recounted independently on the
+    device (sclap_cut), and equality between the two drivers."""
+    import torch
+    import paper_1402_3281_gb300 as P
+    P.load()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    sampler = ClockSampler(0)
+    runs = []
+    edges_total, ms_total = 0, {"host": 0.0, "graph": 0.0}
+    all_ok = True
+    for name, g in large_graphs():
+        rp, col = t(g.row_ptr), t(g.col)
+        for k in (2, 8, 32, 64):
+            for seed in range(5):
+                res = {}
+                for drv, gr in (("host", 0), ("graph", 1)):
+                    cfg = P.default_config(graph_rounds=gr)
+                    if seed == 0:      # warm-up for this shape
+                        P.sclap_partition_device(rp, col, k=k, eps=0.03, seed=seed, cfg=cfg)
+                    torch.cuda.synchronize()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    if drv == "host" and not runs:
+                        sampler.start()
+                    e0.record(stream)
+                    r = P.sclap_partition_device(rp, col, k=k, eps=0.03, seed=seed, cfg=cfg)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    res[drv] = (r, e0.elapsed_time(e1))
+                rh, mh = res["host"]
+                rg, mg = res["graph"]
+                Lmax = int(rh.stats["Lmax"])
+                bw = torch.bincount(rh.block.long(), minlength=k)
+                ok = (rh.status == 0 and int(bw.max()) <= Lmax
+                      and P.sclap_cut(rp, col, None, rh.block) == rh.cut
+                      and rg.cut == rh.cut and bool(torch.equal(rg.block, rh.block)))
+                all_ok &= ok
+                edges_total += g.edges
+                ms_total["host"] += mh
+                ms_total["graph"] += mg
+                runs.append({"graph": name, "k": k, "seed": seed, "cut": rh.cut,
+                             "ms_host": mh, "ms_graph": mg, "levels": rh.stats["levels"],
+                             "checked": ok})
+    clocks = sampler.stop()
+    line = {
+        "metric": "input edges/s", "value": edges_total / (ms_total["host"] / 1000.0),
+        "unit": "edges/s", "n_gpus": 1, "higher_is_better": True,
+        "data": "synthetic",
+        "config": {"workload": "large single graphs: R-MAT scale 22 ef 16 (a,b,c,d = "
+                               "0.57,0.19,0.19,0.05) and 2D RGG 2^22 nodes r=0.55*sqrt(ln n/n); "
+                               "k in {2,8,32,64}, eps 0.03, seeds 0-4, one graph per call"},
+        "graph_driver_value": edges_total / (ms_total["graph"] / 1000.0),
+        "all_checked": bool(all_ok), "runs": runs, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.workload == "large":
+        large_workload(args)
+        return
     if args.impl == "reference":
         reference_arm(args)
         return
@@ -437,6 +517,30 @@ def main():
         line["e2e"] = {"value": e2e_steps * len(graphs) * ws / et, "unit": "partitions/s",
                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                        "equal_cut": [r.cut for r in hres] == ref_cuts}
+
+    if rank == 0 and not args.no_single:
+        # one graph, one call: R-MAT scale 16 (65,536 nodes), edge factor 8,
+        # k = 2, eps = 0.03, seed 0 -- device-resident, latency per call
+        g1 = gg.rmat(16, 8, 0)
+        rp1, col1 = t(g1.row_ptr), t(g1.col)
+        for _ in range(3):
+            P.sclap_partition_device(rp1, col1, k=2, eps=0.03, seed=0)
+        torch.cuda.synchronize()
+        lat = []
+        for _ in range(10):
+            q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            q0.record(stream)
+            r1 = P.sclap_partition_device(rp1, col1, k=2, eps=0.03, seed=0)
+            q1.record(stream)
+            torch.cuda.synchronize()
+            lat.append(q0.elapsed_time(q1))
+        lat.sort()
+        line["single_graph"] = {
+            "workload": "R-MAT scale 16 ef 8 (65,536 nodes, %d undirected edges), k=2, eps=0.03, "
+                        "seed 0, device arrays, one call" % g1.edges,
+            "ms_median": lat[len(lat) // 2], "ms_min": lat[0],
+            "input_edges_per_s": g1.edges / (lat[len(lat) // 2] / 1000.0),
+            "cut": r1.cut, "levels": r1.stats["levels"]}
 
     if rank == 0 and not args.no_serve:
         runs = [serve_stream(P, graphs, lam, cnt, ref_cuts)

@@ -444,3 +444,18 @@ def test_full_batch_sampled_against_oracle():
         Lmax, _ = O.bounds(g.n, 1, k, eps)
         assert np.bincount(b, minlength=k).max() <= Lmax
         assert O.cut(g, b) == res[i].cut
+
+
+def test_scale19_rmat_bit_exact_both_drivers():
+    """A larger input (R-MAT scale 19, 524,288 nodes): the whole partition
+    bit-exact with the oracle under both round drivers; the reported cut
+    equals an independent recount on the device."""
+    g = gg.rmat(19, 8, 2)
+    ref = O.partition(g, 16, 0.03, seed=3)
+    rp, col = dt(g.row_ptr), dt(g.col)
+    for gr in (0, 1):
+        res = P.sclap_partition_device(rp, col, k=16, eps=0.03, seed=3,
+                                       cfg=P.default_config(graph_rounds=gr))
+        assert (res.status, res.cut) == (ref.status, ref.cut)
+        assert np.array_equal(res.block.cpu().numpy(), ref.block)
+        assert P.sclap_cut(rp, col, None, res.block) == res.cut
