@@ -75,6 +75,8 @@ __global__ void __launch_bounds__(GNT) k_ggg(GGGArgs a) {
   __shared__ int32_t shv[GNT / 32];
   __shared__ int64_t Wj_sh, accw_sh;
   __shared__ int32_t nstep_sh, seed_sh;
+  // a chunk of step nodes: row start, first and one-past-last arc offset
+  __shared__ int64_t st_rs[GNT], st_ex[GNT], st_in[GNT];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   for (int32_t s = blockIdx.x; s < a.nslots; s += gridDim.x) {
     const int64_t base = a.noff[s], n = a.noff[s + 1] - base;
@@ -125,16 +127,39 @@ __global__ void __launch_bounds__(GNT) k_ggg(GGGArgs a) {
       }
       __syncthreads();
       while (true) {
-        // connections of unassigned nodes to the block grow with each step
+        // connections of unassigned nodes to the block grow with each step;
+        // the arcs of up to GNT step nodes at a time are spread over all
+        // threads (a hub in the step does not hold back one warp)
         const int32_t nstep = nstep_sh;
-        for (int32_t q = wid; q < nstep; q += GNT / 32) {
-          const int32_t u = a.step[base + q];
-          for (int64_t e = a.row_ptr[u] + lane; e < a.row_ptr[u + 1]; e += 32) {
-            const int32_t x = a.col[e];
-            if (a.label[x] < 0) atomicAdd(ull(&a.conn[x]), (unsigned long long)a.ew[e]);
+        for (int32_t q0 = 0; q0 < nstep; q0 += GNT) {
+          const int32_t q = q0 + tid;
+          int64_t rs = 0, d = 0;
+          if (q < nstep) {
+            const int32_t u = a.step[base + q];
+            rs = a.row_ptr[u];
+            d = a.row_ptr[u + 1] - rs;
           }
+          int64_t tot;
+          const int64_t incl = block_incl_scan(d, sh, &tot);
+          st_rs[tid] = rs;
+          st_ex[tid] = incl - d;
+          st_in[tid] = incl;
+          __syncthreads();
+          const int cnt = min(GNT, nstep - q0);
+          for (int64_t x = tid; x < tot; x += GNT) {
+            // owner: the first step node whose arcs end after x (skips
+            // step nodes without arcs)
+            int lo = 0, hi = cnt - 1;
+            while (lo < hi) {
+              const int mid = (lo + hi) >> 1;
+              if (st_in[mid] > x) hi = mid; else lo = mid + 1;
+            }
+            const int64_t e = st_rs[lo] + (x - st_ex[lo]);
+            const int32_t y = a.col[e];
+            if (a.label[y] < 0) atomicAdd(ull(&a.conn[y]), (unsigned long long)a.ew[e]);
+          }
+          __syncthreads();
         }
-        __syncthreads();
         const int64_t Wj = Wj_sh;
         if (Wj >= avg) break;
         if (tid == 0) accw_sh = 0;

@@ -65,6 +65,9 @@ struct LPArgs {
   int32_t* ent_v;
   int32_t* ent_w;
   int32_t* ent_i;
+  uint64_t* sel_key[2];  // radix-select survivors (two copies used in turn)
+  int32_t* sel_v[2];
+  int32_t* sel_w[2];
   // bucketing
   int32_t* bcnt;
   int32_t* bfill;
@@ -429,22 +432,6 @@ __global__ void __launch_bounds__(256, 4) k_propose_small(LPArgs a, int32_t sub)
   else if (b < g[0] + g[1] + g[2]) propose_thread<16>(a, bo[2], c[2], b - g[0] - g[1], g[2]);
 }
 
-// Open-addressing accumulation (linear probing, bounded).
-__device__ __forceinline__ void table_add(int32_t* keys, unsigned long long* vals, int logcap,
-                                          int32_t C, int64_t w, int32_t* err) {
-  const uint32_t mask = (1u << logcap) - 1;
-  uint32_t s = table_slot(C, logcap);
-  for (uint32_t p = 0; p <= mask; ++p) {
-    const int32_t k = atomicCAS(&keys[s], -1, C);
-    if (k == -1 || k == C) {
-      atomicAdd(&vals[s], (unsigned long long)w);
-      return;
-    }
-    s = (s + 1) & mask;
-  }
-  atomicOr(err, DERR_HASH_FULL);
-}
-
 __device__ __forceinline__ int64_t table_get(const int32_t* keys, const unsigned long long* vals,
                                              int logcap, int32_t C) {
   const uint32_t mask = (1u << logcap) - 1;
@@ -456,42 +443,6 @@ __device__ __forceinline__ int64_t table_get(const int32_t* keys, const unsigned
     s = (s + 1) & mask;
   }
   return 0;
-}
-
-// Adds the arcs [rs, re) of a node into the table; the whole warp calls it
-// with the same range (lanes stride over the arcs, one atomic per arc).
-__device__ __forceinline__ void accumulate_arcs(const LPArgs& a, int64_t rs, int64_t re,
-                                                int first_lane, int lanes, int32_t* keys,
-                                                unsigned long long* vals, int logcap) {
-  const int lane = threadIdx.x & 31;
-  for (int64_t e0 = rs; e0 < re; e0 += lanes) {
-    const int64_t e = e0 + first_lane + lane;
-    const bool valid = e < re;
-    int32_t C = -1, w = 0;
-    if (valid) {
-      w = a.ew[e];
-      C = a.label[a.col[e]];
-    }
-    if (valid) table_add(keys, vals, logcap, C, w, a.err);
-  }
-}
-
-// Direct accumulation for local search: labels are block ids, so the
-// connection of block b (local id) sits at vals[b]; no probing.
-__device__ __forceinline__ void accumulate_direct(const LPArgs& a, int64_t rs, int64_t re,
-                                                  int first_lane, int lanes, int64_t loff,
-                                                  unsigned long long* vals) {
-  const int lane = threadIdx.x & 31;
-  for (int64_t e0 = rs; e0 < re; e0 += lanes) {
-    const int64_t e = e0 + first_lane + lane;
-    const bool valid = e < re;
-    int32_t b = -1, w = 0;
-    if (valid) {
-      w = a.ew[e];
-      b = (int32_t)(a.label[a.col[e]] - loff);
-    }
-    if (valid) atomicAdd(&vals[b], (unsigned long long)w);
-  }
 }
 
 template <int NT>
@@ -509,90 +460,6 @@ __device__ void block_reduce(long long& oc, Cand& cd, long long* sh_oc, Cand* sh
   }
 }
 
-// Degrees above 32 (and nodes of overloaded blocks): one CTA of NT threads
-// per node with a SLOTS-slot table in shared memory, or (GLOBAL, hubs) a
-// per-CTA region of global scratch.  Clustering keys the table by label
-// (open addressing); local search with k no larger than the table indexes
-// it by block id directly.
-template <int NT, int SLOTS, bool GLOBAL>
-__global__ void __launch_bounds__(NT) k_propose_cta(LPArgs a, int32_t sub, int32_t bucket,
-                                                    int32_t* gkeys, unsigned long long* gvals,
-                                                    int64_t gcap) {
-  int64_t lbeg, cnt;
-  sub_range(a, sub, bucket, bucket + 1, &lbeg, &cnt);
-  if (cnt == 0) return;
-  extern __shared__ unsigned long long smem_u64[];
-  __shared__ long long sh_oc[NT / 32];
-  __shared__ Cand sh_cd[NT / 32];
-  const int tid = threadIdx.x, wib = tid >> 5;
-  unsigned long long* vals;
-  int32_t* keys;
-  int64_t tcap;
-  if (GLOBAL) {
-    vals = gvals + (int64_t)blockIdx.x * gcap;
-    keys = gkeys + (int64_t)blockIdx.x * gcap;
-    tcap = gcap;
-  } else {
-    vals = smem_u64;
-    keys = reinterpret_cast<int32_t*>(smem_u64 + SLOTS);
-    tcap = SLOTS;
-    for (int j = tid; j < SLOTS; j += NT) { keys[j] = -1; vals[j] = 0; }
-    __syncthreads();
-  }
-  for (int64_t li = blockIdx.x; li < cnt; li += gridDim.x) {
-    const int64_t i = lbeg + li;
-    const NodeCtx c = load_node(a, i);
-    const bool ov = a.mode != MODE_CLUSTER && a.W[c.own] > c.bound;
-    long long oc = 0;
-    Cand cd{-1, 0, 0};
-    const int32_t nl = a.mode != MODE_CLUSTER ? a.nlab[c.slot] : 0;
-    if (a.mode != MODE_CLUSTER && nl <= tcap) {
-      accumulate_direct(a, c.rs, c.re, wib * 32, NT, c.loff, vals);
-      __syncthreads();
-      const int32_t own_l = (int32_t)(c.own - c.loff);
-      for (int32_t b = tid; b < nl; b += NT) {
-        const int64_t conn = (int64_t)vals[b];
-        if (b == own_l) { oc = conn; continue; }
-        if (conn == 0 && !ov) continue;
-        const int32_t C = (int32_t)(c.loff + b);
-        if ((int64_t)a.W[C] + c.cv > c.bound) continue;
-        Cand x = make_cand(c, C, conn);
-        if (cd.conn < 0 || cand_better(x, cd)) cd = x;
-      }
-      __syncthreads();
-      for (int32_t b = tid; b < nl; b += NT) vals[b] = 0;
-    } else {
-      const int64_t deg = c.re - c.rs;
-      const int logcap = ceil_log2(max64(2 * deg, 32));
-      const int64_t cap = (int64_t)1 << logcap;
-      accumulate_arcs(a, c.rs, c.re, wib * 32, NT, keys, vals, logcap);
-      __syncthreads();
-      for (int64_t j = tid; j < cap; j += NT) {
-        const int32_t K = keys[j];
-        if (K == -1) continue;
-        const int64_t conn = (int64_t)vals[j];
-        if (K == c.own) oc = conn;
-        else if (!ov && (int64_t)a.W[K] + c.cv <= c.bound && cand_block(a, c, true, K) == c.vb) {
-          Cand x = make_cand(c, K, conn);
-          if (cd.conn < 0 || cand_better(x, cd)) cd = x;
-        }
-      }
-      if (ov) {
-        for (int32_t b = tid; b < nl; b += NT) {
-          const int32_t C = (int32_t)(c.loff + b);
-          if (C == c.own || (int64_t)a.W[C] + c.cv > c.bound) continue;
-          Cand x = make_cand(c, C, table_get(keys, vals, logcap, C));
-          if (cd.conn < 0 || cand_better(x, cd)) cd = x;
-        }
-      }
-      __syncthreads();
-      for (int64_t j = tid; j < cap; j += NT) { keys[j] = -1; vals[j] = 0; }
-    }
-    block_reduce<NT>(oc, cd, sh_oc, sh_cd);
-    if (tid == 0) write_prop(a, i, c, cd, oc, ov);
-    __syncthreads();
-  }
-}
 
 // Degrees 17..128 (and nodes of overloaded blocks up to that degree): one
 // warp per node, eight warps per CTA, each with a private WCAP-slot table in
@@ -730,8 +597,13 @@ constexpr size_t blk_smem_bytes() {
          (size_t)(SLOTS / 2) * sizeof(int32_t);
 }
 
-template <int NT, int SLOTS>
-__global__ void __launch_bounds__(NT) k_propose_blk(LPArgs a, int32_t sub, int32_t bucket) {
+// GLOBAL (hubs, degree above 8192): the same per-node procedure, with each
+// CTA's table (gcap slots) and created list in a region of global memory
+// that stays clean between nodes (created slots are reset after each node).
+template <int NT, int SLOTS, bool GLOBAL>
+__global__ void __launch_bounds__(NT) k_propose_blk(LPArgs a, int32_t sub, int32_t bucket,
+                                                    int32_t* gkeys, unsigned long long* gvals,
+                                                    int32_t* glist, int64_t gcap) {
   int64_t lbeg, cnt;
   sub_range(a, sub, bucket, bucket + 1, &lbeg, &cnt);
   if (cnt == 0) return;
@@ -739,11 +611,23 @@ __global__ void __launch_bounds__(NT) k_propose_blk(LPArgs a, int32_t sub, int32
   __shared__ long long sh_oc[NT / 32];
   __shared__ Cand sh_cd[NT / 32];
   __shared__ int sh_nc;
-  unsigned long long* vals = smem_u64;
-  int32_t* keys = reinterpret_cast<int32_t*>(smem_u64 + SLOTS);
-  int32_t* clist = keys + SLOTS;
+  unsigned long long* vals;
+  int32_t* keys;
+  int32_t* clist;
+  int64_t tcap;
   const int tid = threadIdx.x, lane = tid & 31;
-  for (int j = tid; j < SLOTS; j += NT) { keys[j] = -1; vals[j] = 0; }
+  if (GLOBAL) {
+    vals = gvals + (int64_t)blockIdx.x * gcap;
+    keys = gkeys + (int64_t)blockIdx.x * gcap;
+    clist = glist + (int64_t)blockIdx.x * (gcap / 2);
+    tcap = gcap;
+  } else {
+    vals = smem_u64;
+    keys = reinterpret_cast<int32_t*>(smem_u64 + SLOTS);
+    clist = keys + SLOTS;
+    tcap = SLOTS;
+    for (int j = tid; j < SLOTS; j += NT) { keys[j] = -1; vals[j] = 0; }
+  }
   if (tid == 0) sh_nc = 0;
   __syncthreads();
   for (int64_t li = blockIdx.x; li < cnt; li += gridDim.x) {
@@ -751,7 +635,7 @@ __global__ void __launch_bounds__(NT) k_propose_blk(LPArgs a, int32_t sub, int32
     const NodeCtx c = load_node(a, i);
     const bool ov = a.mode != MODE_CLUSTER && a.W[c.own] > c.bound;
     const int32_t nl = a.mode != MODE_CLUSTER ? a.nlab[c.slot] : 0;
-    const bool direct = a.mode != MODE_CLUSTER && nl <= SLOTS;
+    const bool direct = a.mode != MODE_CLUSTER && nl <= tcap;
     const int64_t deg = c.re - c.rs;
     const int logcap = ceil_log2(max64(2 * deg, 32));
     const uint32_t mask = (1u << logcap) - 1;
@@ -948,14 +832,6 @@ __device__ __forceinline__ uint32_t digit_of(uint64_t k, int32_t v, int p) {
   return p < 8 ? (uint32_t)(k >> (56 - 8 * p)) & 0xffu
                : ((uint32_t)v >> (24 - 8 * (p - 8))) & 0xffu;
 }
-__device__ __forceinline__ bool prefix_match(uint64_t k, int32_t v, uint64_t PK, uint32_t PV,
-                                             int p) {
-  if (p == 0) return true;
-  if (p <= 8) return (k >> (64 - 8 * p)) == (PK >> (64 - 8 * p));
-  if (k != PK) return false;
-  const int b = 8 * (p - 8);
-  return ((uint32_t)v >> (32 - b)) == (PV >> (32 - b));
-}
 
 // Admission inside one overflowing group: entries ordered by (key, node);
 // target side admits while the inclusive prefix weight <= thr, source side
@@ -1001,7 +877,7 @@ __global__ void __launch_bounds__(SEL_NT) k_ovf_select(LPArgs a, int32_t source)
   __shared__ uint32_t PV;
   __shared__ int32_t vmin_sh, vmax_sh, BV;
   __shared__ long long acc_sh;
-  __shared__ int found_sh, ncand_sh, bfound_sh, done_sh;
+  __shared__ int found_sh, ncand_sh, bfound_sh, done_sh, x_sh, ncomp_sh;
   const int tid = threadIdx.x, lane = tid & 31;
   const int64_t nseg = a.ctr[1];
   // Phase 1: groups of <= 64 entries, one warp each (entries lane and
@@ -1090,19 +966,43 @@ __global__ void __launch_bounds__(SEL_NT) k_ovf_select(LPArgs a, int32_t source)
         bfound_sh = 0;
       }
       __syncthreads();
+      // Each pass histograms only the entries still sharing the chosen
+      // prefix: after the digit is picked, the entries of its bin are
+      // compacted into a scratch copy (two copies used in turn), so later
+      // passes read the survivors, not the whole group.
+      const uint64_t* ck = a.ent_key + base;
+      const int32_t* cv = a.ent_v + base;
+      const int32_t* cw = a.ent_w + base;
+      int64_t cn = n;
+      int buf = 0;
       int p = p0;
       for (; p < 12; ++p) {
         for (int j = tid; j < 256; j += SEL_NT) { hist[j] = 0; hcnt[j] = 0; }
         __syncthreads();
-        const uint64_t pk = PK;
-        const uint32_t pv = PV;
-        for (int64_t j = tid; j < n; j += SEL_NT) {
-          const uint64_t k = a.ent_key[base + j];
-          const int32_t v = a.ent_v[base + j];
-          if (prefix_match(k, v, pk, pv, p)) {
-            const uint32_t d = digit_of(k, v, p);
-            atomicAdd(&hist[d], (unsigned long long)a.ent_w[base + j]);
-            atomicAdd(&hcnt[d], 1u);
+        {
+          // runs of equal digits are summed in registers and added once: in
+          // a large group most entries share the leading digits, and one
+          // shared atomic per entry on the same bin would serialise
+          uint32_t dc = 0xffffffffu;
+          unsigned long long wacc = 0;
+          unsigned int cacc = 0;
+          for (int64_t j = tid; j < cn; j += SEL_NT) {
+            const uint32_t d = digit_of(ck[j], cv[j], p);
+            if (d != dc) {
+              if (cacc) {
+                atomicAdd(&hist[dc], wacc);
+                atomicAdd(&hcnt[dc], cacc);
+              }
+              dc = d;
+              wacc = 0;
+              cacc = 0;
+            }
+            wacc += (unsigned long long)cw[j];
+            cacc += 1;
+          }
+          if (cacc) {
+            atomicAdd(&hist[dc], wacc);
+            atomicAdd(&hcnt[dc], cacc);
           }
         }
         __syncthreads();
@@ -1136,25 +1036,44 @@ __global__ void __launch_bounds__(SEL_NT) k_ovf_select(LPArgs a, int32_t source)
             if (p < 8) PK |= (uint64_t)x << (56 - 8 * p);
             else PV |= (uint32_t)x << (24 - 8 * (p - 8));
             if (hcnt[x] <= SEL_SMALL) done_sh = 1;
+            x_sh = x;
+            ncomp_sh = 0;
           }
         }
         __syncthreads();
-        if (!found_sh || done_sh) break;
+        if (!found_sh) break;
+        {
+          const uint32_t x = (uint32_t)x_sh;
+          uint64_t* dk = a.sel_key[buf] + base;
+          int32_t* dv = a.sel_v[buf] + base;
+          int32_t* dw = a.sel_w[buf] + base;
+          for (int64_t j = tid; j < cn; j += SEL_NT) {
+            const uint64_t k = ck[j];
+            const int32_t v = cv[j];
+            if (digit_of(k, v, p) == x) {
+              const int q = atomicAdd(&ncomp_sh, 1);
+              dk[q] = k;
+              dv[q] = v;
+              dw[q] = cw[j];
+            }
+          }
+          __syncthreads();
+          ck = dk;
+          cv = dv;
+          cw = dw;
+          cn = ncomp_sh;
+          buf ^= 1;
+        }
+        if (done_sh) break;
       }
       if (found_sh && done_sh && p < 11) {
-        // stage the few candidates sharing the chosen prefix; rank them
-        const uint64_t pk = PK;
-        const uint32_t pv = PV;
-        for (int64_t j = tid; j < n; j += SEL_NT) {
-          const uint64_t k = a.ent_key[base + j];
-          const int32_t v = a.ent_v[base + j];
-          if (prefix_match(k, v, pk, pv, p + 1)) {
-            const int q = atomicAdd(&ncand_sh, 1);
-            sk[q] = k;
-            sv[q] = v;
-            sw[q] = a.ent_w[base + j];
-          }
+        // the few survivors are the candidates sharing the chosen prefix
+        for (int64_t j = tid; j < cn; j += SEL_NT) {
+          sk[j] = ck[j];
+          sv[j] = cv[j];
+          sw[j] = cw[j];
         }
+        if (tid == 0) ncand_sh = (int)cn;
         __syncthreads();
         select_rank_small(a, ncand_sh, thr, acc_sh, sk, sv, sw, si, false, source, &BK, &BV,
                           &bfound_sh);
@@ -1187,11 +1106,12 @@ __global__ void __launch_bounds__(SEL_NT) k_ovf_select(LPArgs a, int32_t source)
 // ------------------------------------------------------------- apply
 // Admitted moves update labels and weights; moved nodes activate their
 // neighbours (small rows by their own lane, larger rows by the whole warp).
-// Label-weight changes are first summed per CTA in a small shared hash
-// (label -> delta; a label that finds no slot within a few probes goes to
-// global memory directly), then flushed with one atomic per label: moves in
-// local search concentrate on a handful of blocks, whose global counters
-// would otherwise take one atomic per moved node each.
+// In local search, label-weight changes are first summed per CTA in a small
+// shared hash (label -> delta; a label that finds no slot within a few
+// probes goes to global memory directly), then flushed with one atomic per
+// label: moves concentrate on a handful of blocks, whose global counters
+// would otherwise take one atomic per moved node each.  Clustering moves
+// spread over many clusters and update the global weights directly.
 constexpr int APPLY_SLOTS = 1024;
 __device__ __forceinline__ void apply_delta(int32_t* hk, int32_t* hv, wgt_t* W, int32_t L,
                                             int32_t d) {
@@ -1214,8 +1134,11 @@ __global__ void __launch_bounds__(256) k_apply(LPArgs a, int32_t sub) {
   uint8_t* const an = act_next(a);
   __shared__ int32_t hk[APPLY_SLOTS];
   __shared__ int32_t hv[APPLY_SLOTS];
-  for (int j = threadIdx.x; j < APPLY_SLOTS; j += blockDim.x) { hk[j] = -1; hv[j] = 0; }
-  __syncthreads();
+  const bool agg = a.mode != MODE_CLUSTER;
+  if (agg) {
+    for (int j = threadIdx.x; j < APPLY_SLOTS; j += blockDim.x) { hk[j] = -1; hv[j] = 0; }
+    __syncthreads();
+  }
   const int lane = threadIdx.x & 31;
   const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -1241,8 +1164,13 @@ __global__ void __launch_bounds__(256) k_apply(LPArgs a, int32_t sub) {
             re = r2.x + r2.y;
           }
           a.label[v] = t;
-          apply_delta(hk, hv, a.W, t, cv);
-          apply_delta(hk, hv, a.W, own, -cv);
+          if (agg) {
+            apply_delta(hk, hv, a.W, t, cv);
+            apply_delta(hk, hv, a.W, own, -cv);
+          } else {
+            atomicAdd(&a.W[t], (wgt_t)cv);
+            atomicSub(&a.W[own], (wgt_t)cv);
+          }
           if (re - rs <= 8) {
             for (int64_t e = rs; e < re; ++e) an[a.col[e]] = 1;
             re = rs;
@@ -1270,9 +1198,11 @@ __global__ void __launch_bounds__(256) k_apply(LPArgs a, int32_t sub) {
     }
   }
   if (run_cnt) atomicAdd(ull(&a.moved[run_slot]), run_cnt);
-  __syncthreads();
-  for (int j = threadIdx.x; j < APPLY_SLOTS; j += blockDim.x)
-    if (hk[j] >= 0 && hv[j] != 0) atomicAdd(&a.W[hk[j]], (wgt_t)hv[j]);
+  if (agg) {
+    __syncthreads();
+    for (int j = threadIdx.x; j < APPLY_SLOTS; j += blockDim.x)
+      if (hk[j] >= 0 && hv[j] != 0) atomicAdd(&a.W[hk[j]], (wgt_t)hv[j]);
+  }
 }
 
 }  // namespace
@@ -1404,6 +1334,8 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, wgt_t*
   DevBuf<int8_t> adm(N, s), stage(N, s);
   DevBuf<int64_t> seg_base(N, s), seg_thr(N, s);
   DevBuf<int32_t> ent_v(N, s), ent_w(N, s), ent_i(N, s);
+  DevBuf<uint64_t> sel_k0(N, s), sel_k1(N, s);
+  DevBuf<int32_t> sel_v0(N, s), sel_v1(N, s), sel_w0(N, s), sel_w1(N, s);
   DevBuf<int64_t> ctr(2, s);
   DevBuf<int32_t> bcnt(nkeys, s), bfill(nkeys, s);
   DevBuf<int64_t> boff(nkeys + 1, s), arcs(1, s), karcs(nkeys, s);
@@ -1424,7 +1356,7 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, wgt_t*
   // Global hash scratch for hub nodes: one region per CTA, sized for the
   // largest degree of the level.
   int64_t gcap = 0;
-  DevBuf<int32_t> gkeys;
+  DevBuf<int32_t> gkeys, glist;
   DevBuf<unsigned long long> gvals;
   int gblocks = 0;
 
@@ -1437,7 +1369,10 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, wgt_t*
   a.grp = grp.p; a.ovf_cnt = ovf_cnt.p; a.ovf_fill = ovf_fill.p; a.ovf_base = ovf_base.p;
   a.ctr = ctr.p; a.seg_g = seg_g.p; a.seg_base = seg_base.p; a.seg_cnt = seg_cnt.p;
   a.seg_thr = seg_thr.p; a.ent_key = ent_key.p; a.ent_v = ent_v.p; a.ent_w = ent_w.p;
-  a.ent_i = ent_i.p; a.bcnt = bcnt.p; a.bfill = bfill.p; a.boff = boff.p; a.arcs = arcs.p;
+  a.ent_i = ent_i.p; a.bcnt = bcnt.p;
+  a.sel_key[0] = sel_k0.p; a.sel_key[1] = sel_k1.p;
+  a.sel_v[0] = sel_v0.p; a.sel_v[1] = sel_v1.p;
+  a.sel_w[0] = sel_w0.p; a.sel_w[1] = sel_w1.p; a.bfill = bfill.p; a.boff = boff.p; a.arcs = arcs.p;
   a.karcs = karcs.p;
   a.flags = flags.p;
   a.nkey = nkey.p;
@@ -1473,6 +1408,7 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, wgt_t*
     gblocks = (int)std::max<int64_t>(1, std::min<int64_t>(sms * 2, nhubs));
     gkeys.alloc((size_t)(gblocks * gcap), s);
     gvals.alloc((size_t)(gblocks * gcap), s);
+    glist.alloc((size_t)(gblocks * (gcap / 2)), s);
     gkeys.fill_bytes(0xff);
     gvals.zero();
   }
@@ -1481,9 +1417,9 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, wgt_t*
   constexpr size_t smem7 = blk_smem_bytes<B7_SLOTS>();
   static std::once_flag attrs_once;
   std::call_once(attrs_once, [&] {
-    SCLAP_CUDA(cudaFuncSetAttribute(k_propose_blk<256, B6_SLOTS>,
+    SCLAP_CUDA(cudaFuncSetAttribute(k_propose_blk<256, B6_SLOTS, false>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem6));
-    SCLAP_CUDA(cudaFuncSetAttribute(k_propose_blk<512, B7_SLOTS>,
+    SCLAP_CUDA(cudaFuncSetAttribute(k_propose_blk<512, B7_SLOTS, false>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem7));
   });
   // fixed launch shapes: kernels read their node ranges on the device and
@@ -1573,16 +1509,16 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, wgt_t*
       k_propose_warp<<<grid(3, 5, WPC, grid_warp), WPC * 32, 0, ls>>>(a, sub); SCLAP_NOTE_LAUNCH("k_propose_warp");
     });
     if (need[5]) launch(5, 6, 1, [&](cudaStream_t ls) {
-      k_propose_blk<128, B5_SLOTS><<<grid(5, 6, 1, grid_b5), 128, smem5, ls>>>(a, sub, 5); SCLAP_NOTE_LAUNCH("k_propose_blk128");
+      k_propose_blk<128, B5_SLOTS, false><<<grid(5, 6, 1, grid_b5), 128, smem5, ls>>>(a, sub, 5, nullptr, nullptr, nullptr, 0); SCLAP_NOTE_LAUNCH("k_propose_blk128");
     });
     if (need[6]) launch(6, 7, 2, [&](cudaStream_t ls) {
-      k_propose_blk<256, B6_SLOTS><<<grid(6, 7, 1, grid_b6), 256, smem6, ls>>>(a, sub, 6); SCLAP_NOTE_LAUNCH("k_propose_blk256");
+      k_propose_blk<256, B6_SLOTS, false><<<grid(6, 7, 1, grid_b6), 256, smem6, ls>>>(a, sub, 6, nullptr, nullptr, nullptr, 0); SCLAP_NOTE_LAUNCH("k_propose_blk256");
     });
     if (need[7]) launch(7, 8, 2, [&](cudaStream_t ls) {
-      k_propose_blk<512, B7_SLOTS><<<grid(7, 8, 1, grid_b7), 512, smem7, ls>>>(a, sub, 7); SCLAP_NOTE_LAUNCH("k_propose_blk512");
+      k_propose_blk<512, B7_SLOTS, false><<<grid(7, 8, 1, grid_b7), 512, smem7, ls>>>(a, sub, 7, nullptr, nullptr, nullptr, 0); SCLAP_NOTE_LAUNCH("k_propose_blk512");
     });
     if (need[8]) launch(8, 9, 3, [&](cudaStream_t ls) {
-      k_propose_cta<512, 1, true><<<(unsigned)gblocks, 512, 0, ls>>>(a, sub, 8, gkeys.p, gvals.p, gcap); SCLAP_NOTE_LAUNCH("k_propose_cta_global");
+      k_propose_blk<512, 1, true><<<(unsigned)gblocks, 512, 0, ls>>>(a, sub, 8, gkeys.p, gvals.p, glist.p, gcap); SCLAP_NOTE_LAUNCH("k_propose_hub");
     });
     if (fork) {
       for (int j = 0; j < nside; ++j) {
