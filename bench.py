@@ -65,6 +65,9 @@ def parse():
                          "RGG 2^22, one graph per call, both round drivers")
     ap.add_argument("--graph-rounds", action="store_true",
                     help="run each level's LP rounds as one CUDA graph (device-side loop)")
+    ap.add_argument("--autotune", action="store_true",
+                    help="before the warm-up, pick the launch tuning for this batch with "
+                         "sclap_autotune (results unchanged; the choice goes into config)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--phases", action="store_true",
                     help="print per-sub-round propose/admission times grouped by run kind "
@@ -390,6 +393,7 @@ def main():
     torch.cuda.synchronize()
 
     cfg = P.default_config(graph_rounds=1 if args.graph_rounds else 0)
+    tuning = P.autotune(items, cfg=cfg, reps=3) if args.autotune else P.get_tuning()
     ref = None
     for _ in range(args.warmup):
         ref = P.sclap_partition_batch(items, cfg=cfg, device=True)
@@ -478,6 +482,7 @@ def main():
 
     conf = config_dict(len(graphs), ws)
     conf["lp_rounds_driver"] = "cuda-graph (WHILE node per level)" if args.graph_rounds else "host"
+    conf["launch_tuning"] = dict(tuning.to_dict(), autotuned=bool(args.autotune))
     line = {
         "metric": "partitions/s", "value": value, "unit": "partitions/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,

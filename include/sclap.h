@@ -331,6 +331,37 @@ int sclap_cut_static(int64_t n, const int64_t* row_ptr, const int32_t* col,
                      const int32_t* node_w, const int32_t* edge_w, const int32_t* block,
                      int32_t k, int64_t* cut_out, int64_t* block_w_out, void* stream);
 
+/* ---- Launch tuning and autotuning (no counterpart in the paper).  Choices
+ * of the LP sweep that change scheduling, never results:
+ *   small_max_deg      rows of degree <= 8 or <= 16 get one thread per node
+ *                      (longer rows up to 128 get one warp per node)
+ *   small_ctas_per_sm  grid cap of the thread-per-node launch (1..32)
+ *   warp_ctas_per_sm   grid cap of the warp-per-node launch (1..32)
+ *   admit_ctas_per_sm  grid cap of the admission kernels (1..64)
+ *   concurrent         1: the propose launches of a colour class run
+ *                      concurrently on side streams; 0: one after another
+ * The setting is process-wide; defaults 16, 8, 8, 16, 1. ---- */
+typedef struct sclap_tuning {
+  int32_t small_max_deg;
+  int32_t small_ctas_per_sm;
+  int32_t warp_ctas_per_sm;
+  int32_t admit_ctas_per_sm;
+  int32_t concurrent;
+} sclap_tuning;
+void sclap_get_tuning(sclap_tuning* out);
+/* SCLAP_EINVAL for a value out of range (the setting is then unchanged). */
+int sclap_set_tuning(const sclap_tuning* t);
+/* Picks the tuning for a workload by coordinate descent: the batch (as for
+ * sclap_partition_batch) is partitioned `reps` times per candidate setting
+ * (each parameter in turn over a few values, the others fixed), the median
+ * wall time is compared, and a candidate replaces the current choice only if
+ * at least 2% faster.  Every run must give the same cut for every graph as
+ * the first (SCLAP_EINTERNAL otherwise).  The best setting is installed and
+ * written to *out (may be NULL).  The graphs' outputs hold the last run's
+ * (identical) results. */
+int sclap_autotune(int32_t count, sclap_graph* graphs, const sclap_config* cfg,
+                   int32_t device_ptrs, int32_t reps, sclap_tuning* out, void* stream);
+
 /* ---- Instrumentation (no counterpart in the paper).  Process-wide
  * counters read by the benchmark: every kernel launch is counted; with
  * profiling enabled, each launch of the LP propose sweep is bracketed by CUDA

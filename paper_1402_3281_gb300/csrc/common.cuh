@@ -63,6 +63,20 @@ inline void stream_sync(cudaStream_t s) {
 }
 cudaEvent_t event_from_pool();
 cudaStream_t side_stream(int i);
+
+// Launch choices of the LP sweep that change scheduling, never results
+// (sclap_tuning in sclap.h): rows of degree <= small_max_deg (8 or 16) get
+// one thread per node, longer rows up to 128 one warp; grid caps in CTAs per
+// SM; concurrent propose launches per colour class.
+struct Tuning {
+  int32_t small_max_deg = 16;
+  int32_t small_ctas_per_sm = 8;
+  int32_t warp_ctas_per_sm = 8;
+  int32_t admit_ctas_per_sm = 16;
+  int32_t concurrent = 1;
+};
+Tuning tuning_get();
+void tuning_set(const Tuning& t);
 void event_to_pool(cudaEvent_t e);
 #define SCLAP_NOTE_LAUNCH(name)                                               \
   do {                                                                        \

@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <chrono>
 #include <memory>
 
 #include "common.cuh"
@@ -1417,6 +1418,94 @@ int sclap_cut(int64_t n, const int64_t* row_ptr, const int32_t* col, const int32
     SCLAP_CUDA(cudaMemcpyAsync(&c2, cut2.p, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     stream_sync(s);
     if (cut_out) *cut_out = c2 / 2;
+  });
+}
+
+void sclap_get_tuning(sclap_tuning* out) {
+  if (!out) return;
+  const Tuning t = tuning_get();
+  out->small_max_deg = t.small_max_deg;
+  out->small_ctas_per_sm = t.small_ctas_per_sm;
+  out->warp_ctas_per_sm = t.warp_ctas_per_sm;
+  out->admit_ctas_per_sm = t.admit_ctas_per_sm;
+  out->concurrent = t.concurrent;
+}
+
+int sclap_set_tuning(const sclap_tuning* in) {
+  return guarded([&] {
+    if (!in) throw Error(SCLAP_EINVAL, "NULL tuning");
+    if ((in->small_max_deg != 8 && in->small_max_deg != 16) || in->small_ctas_per_sm < 1 ||
+        in->small_ctas_per_sm > 32 || in->warp_ctas_per_sm < 1 || in->warp_ctas_per_sm > 32 ||
+        in->admit_ctas_per_sm < 1 || in->admit_ctas_per_sm > 64 || in->concurrent < 0 ||
+        in->concurrent > 1)
+      throw Error(SCLAP_EINVAL, "tuning value out of range");
+    Tuning t;
+    t.small_max_deg = in->small_max_deg;
+    t.small_ctas_per_sm = in->small_ctas_per_sm;
+    t.warp_ctas_per_sm = in->warp_ctas_per_sm;
+    t.admit_ctas_per_sm = in->admit_ctas_per_sm;
+    t.concurrent = in->concurrent;
+    tuning_set(t);
+  });
+}
+
+int sclap_autotune(int32_t count, sclap_graph* graphs, const sclap_config* cfg,
+                   int32_t device_ptrs, int32_t reps, sclap_tuning* out, void* stream) {
+  return guarded([&] {
+    if (count < 1 || !graphs || reps < 1) throw Error(SCLAP_EINVAL, "bad argument");
+    const sclap_config c = resolve_cfg(cfg);
+    std::vector<int64_t> ref(count);
+    auto run_once = [&](const Tuning& t, bool record) -> double {
+      tuning_set(t);
+      const auto t0 = std::chrono::steady_clock::now();
+      const int rc = sclap_partition_batch(count, graphs, &c, device_ptrs, stream);
+      const double ms =
+          std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+      if (rc != SCLAP_OK && rc != SCLAP_EINFEASIBLE) throw Error(rc, "autotune: a run failed");
+      for (int32_t i = 0; i < count; ++i) {
+        if (record) ref[i] = graphs[i].cut;
+        else if (graphs[i].cut != ref[i])
+          throw Error(SCLAP_EINTERNAL, "autotune: a setting changed a result");
+      }
+      return ms;
+    };
+    auto measure = [&](const Tuning& t) {
+      std::vector<double> ms;
+      for (int32_t r = 0; r < reps; ++r) ms.push_back(run_once(t, false));
+      std::sort(ms.begin(), ms.end());
+      return ms[ms.size() / 2];
+    };
+    const Tuning start = tuning_get();
+    Tuning best = start;
+    try {
+      run_once(best, true);                       // warm-up, reference results
+      double best_ms = measure(best);
+      struct Param { int32_t Tuning::*f; std::vector<int32_t> vals; };
+      const Param params[] = {
+          {&Tuning::small_max_deg, {16, 8}},
+          {&Tuning::small_ctas_per_sm, {4, 8, 16}},
+          {&Tuning::warp_ctas_per_sm, {4, 8, 16}},
+          {&Tuning::admit_ctas_per_sm, {8, 16, 32}},
+          {&Tuning::concurrent, {1, 0}},
+      };
+      for (const Param& p : params) {
+        for (int32_t v : p.vals) {
+          if (best.*(p.f) == v) continue;
+          Tuning t = best;
+          t.*(p.f) = v;
+          const double ms = measure(t);
+          if (ms < 0.98 * best_ms) {
+            best = t;
+            best_ms = ms;
+          }
+        }
+      }
+    } catch (...) {
+      tuning_set(start);
+      throw;
+    }
+    tuning_set(best);
+    if (out) sclap_get_tuning(out);
   });
 }
 

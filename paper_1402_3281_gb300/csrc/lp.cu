@@ -400,12 +400,12 @@ __device__ __forceinline__ void propose_thread(const LPArgs& a, int64_t lbeg, in
 // The grid is split among the three buckets in proportion to the blocks each
 // needs (256 nodes per block), every non-empty bucket getting at least one;
 // every block computes the same split from the device offsets.
-__global__ void __launch_bounds__(256, 4) k_propose_small(LPArgs a, int32_t sub) {
+__global__ void __launch_bounds__(256, 4) k_propose_small(LPArgs a, int32_t sub, int32_t nb) {
   const int64_t* bo = a.boff + sub * NB;
   int64_t c[3], need[3], tot = 0;
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
-    c[j] = bo[j + 1] - bo[j];
+    c[j] = j < nb ? bo[j + 1] - bo[j] : 0;
     need[j] = (c[j] + 255) / 256;
     tot += need[j];
   }
@@ -476,9 +476,9 @@ constexpr int WLOG = 8;                      // log2(WCAP)
 constexpr int WPC = 8;                       // warps per CTA
 static_assert((1 << WLOG) == WCAP, "WCAP must be 2^WLOG");
 
-__global__ void __launch_bounds__(WPC * 32) k_propose_warp(LPArgs a, int32_t sub) {
+__global__ void __launch_bounds__(WPC * 32) k_propose_warp(LPArgs a, int32_t sub, int32_t b0) {
   int64_t lbeg, cnt;
-  sub_range(a, sub, 3, 5, &lbeg, &cnt);     // buckets 3 and 4 are adjacent
+  sub_range(a, sub, b0, 5, &lbeg, &cnt);    // buckets b0..4 are adjacent
   if (cnt == 0) return;
   __shared__ unsigned long long sh_vals[WPC][WCAP];
   __shared__ int32_t sh_keys[WPC][WCAP];
@@ -1207,6 +1207,18 @@ __global__ void __launch_bounds__(256) k_apply(LPArgs a, int32_t sub) {
 
 }  // namespace
 
+// Launch tuning, process-wide (see sclap_tuning in sclap.h).
+std::mutex g_tune_mu;
+Tuning g_tune;
+Tuning tuning_get() {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  return g_tune;
+}
+void tuning_set(const Tuning& t) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune = t;
+}
+
 // Stream on which this thread captures graphs (non-blocking, created once).
 cudaStream_t capture_stream() {
   thread_local cudaStream_t cs = nullptr;
@@ -1400,7 +1412,9 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, wgt_t*
   stream_sync(s);
   const int64_t maxdeg = hstat[0], nhubs = hstat[1];
   const bool refine = run.mode != MODE_CLUSTER;
-  const bool need[NB] = {true, true, true, refine || maxdeg > 16, false,
+  const Tuning tu = tuning_get();
+  const int nsb = tu.small_max_deg >= 16 ? 3 : 2;   // buckets of the thread-per-node launch
+  const bool need[NB] = {true, true, true, refine || maxdeg > (nsb == 3 ? 16 : 8), false,
                          maxdeg > B4_MAXDEG, maxdeg > B5_MAXDEG, maxdeg > B6_MAXDEG,
                          maxdeg > B7_MAXDEG};
   if (need[8]) {
@@ -1426,9 +1440,11 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, wgt_t*
   // grid-stride over them
   const unsigned nsl_grid = grid_for(sp.nslots, 128, 1024);
   const unsigned bgrid = (unsigned)((N + BK_TILE - 1) / BK_TILE);
-  const unsigned grid_small = (unsigned)(sms * 8), grid_warp = (unsigned)(sms * 8);
+  const unsigned grid_small = (unsigned)(sms * tu.small_ctas_per_sm);
+  const unsigned grid_warp = (unsigned)(sms * tu.warp_ctas_per_sm);
   const unsigned grid_b5 = (unsigned)(sms * 16), grid_b6 = (unsigned)(sms * 4);
-  const unsigned grid_b7 = (unsigned)sms, grid_adm_max = (unsigned)(sms * 16);
+  const unsigned grid_b7 = (unsigned)sms;
+  const unsigned grid_adm_max = (unsigned)(sms * tu.admit_ctas_per_sm);
   const unsigned grid_sel = (unsigned)(sms * 4);
   const int32_t raw = run.raw_key ? 1 : 0;
 
@@ -1496,17 +1512,17 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, wgt_t*
       if (!ho) return cap;
       if (b0 == 0) {                  // one block per 256 nodes of each bucket
         int64_t nb = 0;
-        for (int q = 0; q < 3; ++q) nb += (ho[sub * NB + q + 1] - ho[sub * NB + q] + 255) / 256;
+        for (int q = 0; q < b1; ++q) nb += (ho[sub * NB + q + 1] - ho[sub * NB + q] + 255) / 256;
         return (unsigned)std::max<int64_t>(1, std::min<int64_t>(nb, cap));
       }
       return grid_for(ho[sub * NB + b1] - ho[sub * NB + b0], per, cap);
     };
     // family 0 first: it holds most nodes, and the first launch gets the SMs
-    launch(0, 3, 0, [&](cudaStream_t ls) {
-      k_propose_small<<<grid(0, 3, 256, grid_small), 256, 0, ls>>>(a, sub); SCLAP_NOTE_LAUNCH("k_propose_small");
+    launch(0, nsb, 0, [&](cudaStream_t ls) {
+      k_propose_small<<<grid(0, nsb, 256, grid_small), 256, 0, ls>>>(a, sub, nsb); SCLAP_NOTE_LAUNCH("k_propose_small");
     });
-    if (need[3]) launch(3, 5, 1, [&](cudaStream_t ls) {
-      k_propose_warp<<<grid(3, 5, WPC, grid_warp), WPC * 32, 0, ls>>>(a, sub); SCLAP_NOTE_LAUNCH("k_propose_warp");
+    if (need[3]) launch(nsb, 5, 1, [&](cudaStream_t ls) {
+      k_propose_warp<<<grid(nsb, 5, WPC, grid_warp), WPC * 32, 0, ls>>>(a, sub, nsb); SCLAP_NOTE_LAUNCH("k_propose_warp");
     });
     if (need[5]) launch(5, 6, 1, [&](cudaStream_t ls) {
       k_propose_blk<128, B5_SLOTS, false><<<grid(5, 6, 1, grid_b5), 128, smem5, ls>>>(a, sub, 5, nullptr, nullptr, nullptr, 0); SCLAP_NOTE_LAUNCH("k_propose_blk128");
@@ -1598,7 +1614,7 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, wgt_t*
       try {
         head(cs);
         for (int sub = 0; sub < S; ++sub) {
-          propose(cs, sub, true, nullptr);
+          propose(cs, sub, tu.concurrent != 0, nullptr);
           admit(cs, sub, refine, -1);
         }
         tail(cs, h, true);
@@ -1650,7 +1666,7 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, wgt_t*
           phase.b = event_from_pool();
           SCLAP_CUDA(cudaEventRecord(phase.a, s));
         }
-        propose(s, sub, !timeline, hoff.data());
+        propose(s, sub, !timeline && tu.concurrent, hoff.data());
         if (prof) {
           SCLAP_CUDA(cudaEventRecord(phase.b, s));
           timed.push_back(phase);

@@ -27,7 +27,8 @@ SYMBOLS = (
     "sclap_partition_device", "sclap_partition_batch", "sclap_lp_round", "sclap_cluster",
     "sclap_contract", "sclap_cluster_hierarchy", "sclap_initial_partition", "sclap_refine", "sclap_cut",
     "sclap_cut_static", "sclap_server_create", "sclap_server_submit", "sclap_server_poll",
-    "sclap_server_destroy", "sclap_profile_enable", "sclap_profile_reset", "sclap_profile_read",
+    "sclap_server_destroy", "sclap_get_tuning", "sclap_set_tuning", "sclap_autotune",
+    "sclap_profile_enable", "sclap_profile_reset", "sclap_profile_read",
     "sclap_profile_timeline", "sclap_profile_dump", "sclap_profile_phases",
 )
 
@@ -81,6 +82,14 @@ class ServerOptions(C.Structure):
                 ("max_batch", C.c_int32), ("linger_us", C.c_int64)]
 
 
+class Tuning(C.Structure):
+    _fields_ = [(n, C.c_int32) for n in ("small_max_deg", "small_ctas_per_sm",
+                                         "warp_ctas_per_sm", "admit_ctas_per_sm", "concurrent")]
+
+    def to_dict(self) -> dict:
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
 class GraphDesc(C.Structure):
     _fields_ = [("n", C.c_int64), ("row_ptr", C.c_void_p), ("col", C.c_void_p),
                 ("node_w", C.c_void_p), ("edge_w", C.c_void_p), ("k", C.c_int32),
@@ -121,6 +130,9 @@ def _lib():
             "sclap_server_submit": (C.c_int, [p, i64, p, p, p, p, i32, dbl, u64, p]),
             "sclap_server_poll": (C.c_int, [p, i64, i32, p, p, p, p]),
             "sclap_server_destroy": (C.c_int, [p]),
+            "sclap_get_tuning": (None, [p]),
+            "sclap_set_tuning": (C.c_int, [p]),
+            "sclap_autotune": (C.c_int, [i32, p, p, i32, i32, p, p]),
             "sclap_profile_enable": (None, [C.c_int]),
             "sclap_profile_reset": (None, []),
             "sclap_profile_read": (None, [p]),
@@ -252,14 +264,9 @@ def sclap_partition_device(row_ptr, col, node_w=None, edge_w=None, k=2, eps=0.03
     return Result(block_out, cut.value, mb.value, rc, st.to_dict())
 
 
-def sclap_partition_batch(graphs: Sequence[dict], cfg: Optional[Config] = None,
-                          device: bool = False, stream=None):
-    """Partitions many graphs in one call (sclap_partition_batch).
-
-    Each entry: dict(row_ptr, col, node_w=None, edge_w=None, k, eps, seed); numpy
-    arrays when device=False, CUDA tensors when device=True.  Returns a list
-    of Result (block ids as numpy arrays or CUDA tensors).
-    """
+def _batch_descs(graphs: Sequence[dict], device: bool):
+    """sclap_graph descriptors for a batch, the output arrays, and the arrays
+    the descriptors point into (kept alive by the caller)."""
     descs = (GraphDesc * len(graphs))()
     keep = []
     outs = []
@@ -289,12 +296,25 @@ def sclap_partition_batch(graphs: Sequence[dict], cfg: Optional[Config] = None,
         d.eps = float(g.get("eps", 0.03))
         d.seed = int(g.get("seed", 0)) & (2**64 - 1)
         outs.append(out)
+    return descs, outs, keep
+
+
+def sclap_partition_batch(graphs: Sequence[dict], cfg: Optional[Config] = None,
+                          device: bool = False, stream=None):
+    """Partitions many graphs in one call (sclap_partition_batch).
+
+    Each entry: dict(row_ptr, col, node_w=None, edge_w=None, k, eps, seed); numpy
+    arrays when device=False, CUDA tensors when device=True.  Returns a list
+    of Result (block ids as numpy arrays or CUDA tensors).
+    """
+    descs, outs, keep = _batch_descs(graphs, device)
     rc = _lib().sclap_partition_batch(len(graphs), C.cast(descs, C.c_void_p),
                                       C.byref(cfg) if cfg else None, 1 if device else 0,
                                       _stream(stream) if device else None)
     res = [Result(outs[i], descs[i].cut, descs[i].max_block_weight, descs[i].status)
            for i in range(len(graphs))]
     _check(rc, "sclap_partition_batch", allow=(OK, EINFEASIBLE))
+    del keep
     return res
 
 
@@ -492,3 +512,32 @@ def sclap_profile_phases() -> np.ndarray:
     out = np.zeros((max(n, 1), 7), dtype=np.float64)
     m = _lib().sclap_profile_phases(out.ctypes.data_as(C.c_void_p), n)
     return out[:min(n, m)]
+
+
+def get_tuning() -> Tuning:
+    t = Tuning()
+    _lib().sclap_get_tuning(C.byref(t))
+    return t
+
+
+def set_tuning(**kw) -> Tuning:
+    """Changes some launch choices (sclap_set_tuning); returns the setting."""
+    t = get_tuning()
+    for k, v in kw.items():
+        setattr(t, k, int(v))
+    _check(_lib().sclap_set_tuning(C.byref(t)), "sclap_set_tuning")
+    return get_tuning()
+
+
+def autotune(graphs: Sequence[dict], cfg: Optional[Config] = None, device: bool = True,
+             reps: int = 3, stream=None) -> Tuning:
+    """Picks and installs the launch tuning for this batch (sclap_autotune)."""
+    descs, outs, keep = _batch_descs(graphs, device)
+    out = Tuning()
+    rc = _lib().sclap_autotune(len(graphs), C.cast(descs, C.c_void_p),
+                               C.byref(cfg) if cfg else None,
+                               1 if device else 0, int(reps), C.byref(out),
+                               _stream(stream) if device else None)
+    _check(rc, "sclap_autotune")
+    del keep, outs
+    return out
