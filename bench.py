@@ -24,6 +24,7 @@ Multi-GPU (torchrun): replicas only -- each rank partitions its own batch
 from __future__ import annotations
 
 import argparse
+import datetime
 import hashlib
 import json
 import os
@@ -52,7 +53,7 @@ FAMILIES = ["thread_deg_le16", "warp_deg_le128_cta128", "cta256_512", "cta_globa
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--count", type=int, default=512)
@@ -120,8 +121,13 @@ def config_dict(count, ws):
 
 
 class ClockSampler:
-    """nvidia-smi clocks/throttle reasons sampled every 200 ms."""
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi clocks/throttle reasons sampled every 200 ms.
+
+    Started before the warm-up (so nvidia-smi's own start-up, which takes
+    driver locks, falls outside the timed region); mark() and stop() bound the
+    timed window, and only samples stamped inside it are summarised (all of
+    them when fewer than two fall inside)."""
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -129,6 +135,8 @@ class ClockSampler:
         self.index = index
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         self.p = None
+        self.t0 = None
+        self.t1 = None
 
     def start(self):
         try:
@@ -138,7 +146,11 @@ class ClockSampler:
         except OSError:
             self.p = None
 
+    def mark(self):
+        self.t0 = datetime.datetime.now()
+
     def stop(self):
+        self.t1 = datetime.datetime.now()
         if self.p is None:
             return None
         self.p.terminate()
@@ -151,9 +163,18 @@ class ClockSampler:
         with open(self.f.name) as fh:
             for line in fh:
                 parts = [x.strip() for x in line.split(",")]
-                if len(parts) >= 9:
+                if len(parts) >= 10:
                     rows.append(parts)
         os.unlink(self.f.name)
+
+        def stamp(r):
+            try:
+                return datetime.datetime.strptime(r[0], "%Y/%m/%d %H:%M:%S.%f")
+            except ValueError:
+                return None
+        inside = [r for r in rows if self.t0 and stamp(r) and self.t0 <= stamp(r) <= self.t1]
+        window = "timed region" if len(inside) >= 2 else "warm-up and timed region"
+        rows = [r[1:] for r in (inside if len(inside) >= 2 else rows)]
         if not rows:
             return None
         sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
@@ -162,7 +183,7 @@ class ClockSampler:
         reasons = sorted({names[j] for r in rows for j in range(4) if r[5 + j] == "Active"})
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
-                "samples": len(rows)}
+                "samples": len(rows), "window": window}
 
 
 def traffic_for(kernel_src):
@@ -311,6 +332,7 @@ def large_workload(args):
     stream = torch.cuda.current_stream()
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     sampler = ClockSampler(0)
+    sampler.start()
     runs = []
     edges_total, ms_total = 0, {"host": 0.0, "graph": 0.0}
     all_ok = True
@@ -327,7 +349,7 @@ def large_workload(args):
                     e0 = torch.cuda.Event(enable_timing=True)
                     e1 = torch.cuda.Event(enable_timing=True)
                     if drv == "host" and not runs:
-                        sampler.start()
+                        sampler.mark()
                     e0.record(stream)
                     r = P.sclap_partition_device(rp, col, k=k, eps=0.03, seed=seed, cfg=cfg)
                     e1.record(stream)
@@ -394,6 +416,8 @@ def main():
 
     cfg = P.default_config(graph_rounds=1 if args.graph_rounds else 0)
     tuning = P.autotune(items, cfg=cfg, reps=3) if args.autotune else P.get_tuning()
+    sampler = ClockSampler(local)
+    sampler.start()
     ref = None
     for _ in range(args.warmup):
         ref = P.sclap_partition_batch(items, cfg=cfg, device=True)
@@ -401,14 +425,13 @@ def main():
     ref_cuts = [r.cut for r in ref]
 
     # timed steps: no event instrumentation inside (only the launch counter)
-    sampler = ClockSampler(local)
     P.sclap_profile_enable(False)
     P.sclap_profile_reset()
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
     torch.cuda.synchronize()
-    sampler.start()
+    sampler.mark()
     e0.record(stream)
     last = None
     for _ in range(args.steps):
