@@ -65,7 +65,8 @@ __global__ void __launch_bounds__(256) k_validate_level(
     const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
     const int32_t* __restrict__ ew, const int32_t* __restrict__ nw,
     const int64_t* __restrict__ noff, const int64_t* __restrict__ aoff, int32_t nslots,
-    int64_t N, int32_t* gerr, unsigned long long* cV, int32_t* maxc) {
+    int64_t N, int32_t* gerr, unsigned long long* cV, int32_t* maxc,
+    unsigned long long* arcw) {
   const int lane = threadIdx.x & 31;
   const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -106,6 +107,11 @@ __global__ void __launch_bounds__(256) k_validate_level(
     }
     const long long excl = incl - d;
     const long long total = __shfl_sync(0xffffffffu, incl, 31);
+    // total arc weight per slot: summed in registers when the warp's nodes
+    // all lie in one slot, else one atomic per arc
+    const int32_t s0 = __shfl_sync(0xffffffffu, s, 0);
+    const bool uni = __all_sync(0xffffffffu, s < 0 || s == s0);
+    unsigned long long acc = 0;
     for (long long x0 = 0; x0 < total; x0 += 32) {
       const long long x = x0 + lane;
       int L = 0;
@@ -120,8 +126,16 @@ __global__ void __launch_bounds__(256) k_validate_level(
         const int64_t e = rsL + (x - exL);
         const int64_t src = base + L;
         const int32_t c = col[e];
-        if (c < noff[sL] || c >= noff[sL + 1] || c == src || ew[e] <= 0) atomicOr(&gerr[sL], 1);
+        const int32_t we = ew[e];
+        if (c < noff[sL] || c >= noff[sL + 1] || c == src || we <= 0) atomicOr(&gerr[sL], 1);
+        const unsigned long long wp = we > 0 ? (unsigned long long)we : 0ull;
+        if (uni) acc += wp;
+        else if (wp) atomicAdd(&arcw[sL], wp);
       }
+    }
+    if (uni) {
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0 && acc) atomicAdd(&arcw[s0], acc);
     }
     if (bad && s >= 0) atomicOr(&gerr[s], 1);
   }
@@ -220,10 +234,12 @@ struct Level {
   DevBuf<int64_t> row_ptr, noff_d;
   DevBuf<int32_t> col, ew, nw, gid, cmap, blk;
   std::vector<int64_t> noff, aoff;
+  bool narrow = false;   // every arc-weight sum of every graph fits in 32 bits
   LevelView view() const {
     LevelView v;
     v.N = N; v.M = M; v.row_ptr = row_ptr.p; v.col = col.p; v.ew = ew.p; v.nw = nw.p;
     v.gid = gid.p;
+    v.narrow = narrow;
     return v;
   }
 };
@@ -281,49 +297,59 @@ void check_range(const int32_t* a, int64_t n, int64_t lo, int64_t hi, cudaStream
 void build_level0(const std::vector<GIn>& gs, struct Level& L, cudaStream_t s);
 
 // Validates the batched level L (built by build_level0 from `B` inputs):
-// per-graph status (SCLAP_OK, SCLAP_ECSR or SCLAP_EOVERFLOW), c(V), max c(v).
+// per-graph status (SCLAP_OK, SCLAP_ECSR or SCLAP_EOVERFLOW), c(V), max c(v)
+// and whether the graph's total arc weight fits in 32 bits (every sum of arc
+// weights met later, at any level of its hierarchy, is at most that total:
+// contraction only merges or drops arcs).
 void validate_level(const Level& L, int B, std::vector<int32_t>& status,
-                    std::vector<int64_t>& cV, std::vector<int64_t>& maxc, cudaStream_t s) {
+                    std::vector<int64_t>& cV, std::vector<int64_t>& maxc,
+                    std::vector<char>& narrow, cudaStream_t s) {
   DevBuf<int32_t> err(B, s), mx(B, s);
-  DevBuf<unsigned long long> sum(B, s);
+  DevBuf<unsigned long long> sum(B, s), arcw(B, s);
   DevBuf<int64_t> d_aoff(B + 1, s);
-  err.zero(); mx.zero(); sum.zero();
+  err.zero(); mx.zero(); sum.zero(); arcw.zero();
   d_aoff.upload(L.aoff);
   if (L.N > 0) {
     k_validate_level<<<grid_for(L.N, 256, (int64_t)num_sms() * 16), 256, 0, s>>>(
-        L.row_ptr.p, L.col.p, L.ew.p, L.nw.p, L.noff_d.p, d_aoff.p, B, L.N, err.p, sum.p, mx.p); SCLAP_NOTE_LAUNCH("k_validate_level");
+        L.row_ptr.p, L.col.p, L.ew.p, L.nw.p, L.noff_d.p, d_aoff.p, B, L.N, err.p, sum.p, mx.p,
+        arcw.p); SCLAP_NOTE_LAUNCH("k_validate_level");
     SCLAP_LAUNCH_CHECK();
   }
   std::vector<int32_t> e(B), m(B);
-  std::vector<unsigned long long> w(B);
+  std::vector<unsigned long long> w(B), aw(B);
   SCLAP_CUDA(cudaMemcpyAsync(e.data(), err.p, B * 4, cudaMemcpyDeviceToHost, s));
   SCLAP_CUDA(cudaMemcpyAsync(m.data(), mx.p, B * 4, cudaMemcpyDeviceToHost, s));
   SCLAP_CUDA(cudaMemcpyAsync(w.data(), sum.p, B * 8, cudaMemcpyDeviceToHost, s));
+  SCLAP_CUDA(cudaMemcpyAsync(aw.data(), arcw.p, B * 8, cudaMemcpyDeviceToHost, s));
   stream_sync(s);
   status.assign(B, SCLAP_OK);
   cV.assign(B, 0);
   maxc.assign(B, 0);
+  narrow.assign(B, 0);
   for (int g = 0; g < B; ++g) {
     if (e[g]) status[g] = SCLAP_ECSR;
     else if (w[g] >= (1ull << 31)) status[g] = SCLAP_EOVERFLOW;
     cV[g] = (int64_t)w[g];
     maxc[g] = m[g];
+    narrow[g] = aw[g] <= 0xffffffffull ? 1 : 0;
   }
 }
 
 // Validates one device-resident graph (step entry points); returns c(V) and
 // max c(v) or throws.
-void validate(const GIn& g, cudaStream_t s, int64_t* cV, int64_t* maxc) {
+void validate(const GIn& g, cudaStream_t s, int64_t* cV, int64_t* maxc, bool* narrow = nullptr) {
   Level L;
   build_level0({g}, L, s);
   std::vector<int32_t> st;
   std::vector<int64_t> a, b;
-  validate_level(L, 1, st, a, b, s);
+  std::vector<char> nar;
+  validate_level(L, 1, st, a, b, nar, s);
   if (st[0] == SCLAP_ECSR)
     throw Error(SCLAP_ECSR, "malformed CSR (row_ptr, column range, self-loop or weight)");
   if (st[0] == SCLAP_EOVERFLOW) throw Error(SCLAP_EOVERFLOW, "sum of node weights must be < 2^31");
   *cV = a[0];
   *maxc = b[0];
+  if (narrow) *narrow = nar[0] != 0;
 }
 
 // Builds the level holding the graphs `gs` back to back.
@@ -437,6 +463,8 @@ void run_ip(const std::vector<IPIn>& in, const sclap_config& cfg, wgt_t* Wg,
     }
   }
   Level ip;
+  ip.narrow = true;
+  for (const IPIn& x : in) ip.narrow = ip.narrow && x.Q->narrow;
   ip.N = noff[S];
   ip.M = aoff[S];
   if (ip.N >= ((int64_t)1 << 31)) throw Error(SCLAP_EINVAL, "trial batch too large");
@@ -543,13 +571,20 @@ void run_batch(const std::vector<GIn>& gs_in, const sclap_config& cfg,
   build_level0(gs_in, *L0, s);
   std::vector<int32_t> status;
   std::vector<int64_t> cV, maxc;
-  validate_level(*L0, B, status, cV, maxc, s);
+  std::vector<char> narrow;
+  validate_level(*L0, B, status, cV, maxc, narrow, s);
   std::vector<int> ok;
+  bool all_narrow = true;
   for (int g = 0; g < B; ++g) {
-    if (status[g] == SCLAP_OK) ok.push_back(g);
-    else res[g].status = status[g];
+    if (status[g] == SCLAP_OK) {
+      ok.push_back(g);
+      all_narrow = all_narrow && narrow[g];
+    } else {
+      res[g].status = status[g];
+    }
   }
   if ((int)ok.size() == B) {
+    L0->narrow = all_narrow;
     run_valid_batch(gs_in, cV, maxc, cfg, outs_in, res, std::move(L0), s);
     return;
   }
@@ -565,6 +600,7 @@ void run_batch(const std::vector<GIn>& gs_in, const sclap_config& cfg,
   }
   L0.reset(new Level());
   build_level0(gs, *L0, s);
+  L0->narrow = all_narrow;
   std::vector<GOut> r2;
   run_valid_batch(gs, c2, m2, cfg, outs, r2, std::move(L0), s);
   for (size_t j = 0; j < ok.size(); ++j) res[ok[j]] = r2[j];
@@ -691,6 +727,7 @@ void run_valid_batch(const std::vector<GIn>& gs, const std::vector<int64_t>& cV,
       CoarseLevel co;
       contract_build(v, cur.noff, label.p, cw, keep, cur.cmap.p, co, d_err.p, s);
       std::unique_ptr<Level> nx(new Level());
+      nx->narrow = cur.narrow;
       nx->N = co.N;
       nx->M = co.M;
       nx->row_ptr = std::move(co.row_ptr);
@@ -1162,11 +1199,13 @@ int sclap_lp_round(int32_t mode, int64_t n, const int64_t* row_ptr, const int32_
     g.ew = edge_w;
     check_col(g.col, g.m);
     int64_t cV, maxc;
-    validate(g, s, &cV, &maxc);
+    bool nar = false;
+    validate(g, s, &cV, &maxc, &nar);
     if (mode == 0 && nlabels < n) throw Error(SCLAP_EINVAL, "clustering needs nlabels >= n");
     check_range(label, n, 0, nlabels, s, "label");
     Level L;
     single_level(g, L, s);
+    L.narrow = nar;
     Slots sl(s, 1, L.noff_d.p, {0}, {bound}, {rkey}, {0}, {(int32_t)nlabels}, {0});
     LPRun run;
     run.mode = mode == 0 ? MODE_CLUSTER : MODE_REFINE;
@@ -1202,9 +1241,11 @@ int sclap_cluster(int64_t n, const int64_t* row_ptr, const int32_t* col, const i
     g.ew = edge_w;
     check_col(g.col, g.m);
     int64_t cV, maxc;
-    validate(g, s, &cV, &maxc);
+    bool nar = false;
+    validate(g, s, &cV, &maxc, &nar);
     Level L;
     single_level(g, L, s);
+    L.narrow = nar;
     Slots sl(s, 1, L.noff_d.p, {0}, {U}, {seed}, {level}, {0}, {0});
     DevBuf<wgt_t> W(n, s);
     k_iota<<<grid_for(n, 256, (int64_t)num_sms() * 16), 256, 0, s>>>(label_out, n); SCLAP_NOTE_LAUNCH("k_iota");
@@ -1239,10 +1280,12 @@ int sclap_cluster_hierarchy(int64_t n, const int64_t* row_ptr, const int32_t* co
     g.ew = edge_w;
     check_col(g.col, g.m);
     int64_t cV, maxc;
-    validate(g, s, &cV, &maxc);
+    bool nar = false;
+    validate(g, s, &cV, &maxc, &nar);
     const int sms = num_sms();
     std::unique_ptr<Level> cur(new Level());
     single_level(g, *cur, s);
+    cur->narrow = nar;
     k_iota<<<grid_for(n, 256, (int64_t)sms * 16), 256, 0, s>>>(comm_out, n); SCLAP_NOTE_LAUNCH("k_iota");
     int32_t levels = 0;
     if (level_n_out && cap > 0) level_n_out[0] = n;
@@ -1272,6 +1315,7 @@ int sclap_cluster_hierarchy(int64_t n, const int64_t* row_ptr, const int32_t* co
       contract_build(v, cur->noff, label.p, cw, {1}, cur->cmap.p, co, d_err.p, s);
       k_compose<<<grid_for(n, 256, (int64_t)sms * 16), 256, 0, s>>>(comm_out, cur->cmap.p, n); SCLAP_NOTE_LAUNCH("k_compose");
       std::unique_ptr<Level> nx(new Level());
+      nx->narrow = cur->narrow;
       nx->N = co.N;
       nx->M = co.M;
       nx->row_ptr = std::move(co.row_ptr);
@@ -1306,10 +1350,12 @@ int sclap_contract(int64_t n, const int64_t* row_ptr, const int32_t* col, const 
     g.ew = edge_w;
     check_col(g.col, g.m);
     int64_t cV, maxc;
-    validate(g, s, &cV, &maxc);
+    bool nar = false;
+    validate(g, s, &cV, &maxc, &nar);
     check_range(label, n, 0, n, s, "label");
     Level L;
     single_level(g, L, s);
+    L.narrow = nar;
     ContractWork w;
     std::vector<int64_t> nc;
     contract_rank(L.view(), L.noff, label, w, nc, s);
@@ -1346,9 +1392,11 @@ int sclap_initial_partition(int64_t n, const int64_t* row_ptr, const int32_t* co
     g.ew = edge_w;
     check_col(g.col, g.m);
     int64_t cV, maxc;
-    validate(g, s, &cV, &maxc);
+    bool nar = false;
+    validate(g, s, &cV, &maxc, &nar);
     Level L;
     single_level(g, L, s);
+    L.narrow = nar;
     DevBuf<wgt_t> Wg(k, s);
     DevBuf<int32_t> d_err(1, s);
     d_err.zero();
@@ -1376,10 +1424,12 @@ int sclap_refine(int64_t n, const int64_t* row_ptr, const int32_t* col, const in
     g.ew = edge_w;
     check_col(g.col, g.m);
     int64_t cV, maxc;
-    validate(g, s, &cV, &maxc);
+    bool nar = false;
+    validate(g, s, &cV, &maxc, &nar);
     check_range(block, n, 0, k, s, "block");
     Level L;
     single_level(g, L, s);
+    L.narrow = nar;
     DevBuf<wgt_t> W(k, s);
     W.zero();
     block_weights(block, L.nw.p, n, W.p, s);
@@ -1408,9 +1458,11 @@ int sclap_cut(int64_t n, const int64_t* row_ptr, const int32_t* col, const int32
     g.n = n; g.m = device_arcs(row_ptr, n, s); g.row_ptr = row_ptr; g.col = col; g.ew = edge_w;
     check_col(g.col, g.m);
     int64_t cV, maxc;
-    validate(g, s, &cV, &maxc);
+    bool nar = false;
+    validate(g, s, &cV, &maxc, &nar);
     Level L;
     single_level(g, L, s);
+    L.narrow = nar;
     DevBuf<int64_t> cut2(1, s);
     cut2.zero();
     slot_cut(L.view(), block, cut2.p, s);

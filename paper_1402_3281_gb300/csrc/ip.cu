@@ -276,7 +276,9 @@ __global__ void __launch_bounds__(GNT) k_ggg(GGGArgs a) {
 }
 
 // Twice the cut of every slot: 32 nodes per warp, their arcs spread over
-// the lanes; per-slot sums merged within the warp before the atomic.
+// the lanes.  When the warp's 32 nodes lie in one slot (all but the groups
+// that straddle a slot boundary) each lane sums in a register and the warp
+// merges once per group; otherwise every cut arc is added on its own.
 __global__ void __launch_bounds__(256) k_slot_cut(const int64_t* __restrict__ row_ptr,
                                                   const int32_t* __restrict__ col,
                                                   const int32_t* __restrict__ ew,
@@ -311,6 +313,9 @@ __global__ void __launch_bounds__(256) k_slot_cut(const int64_t* __restrict__ ro
     }
     const long long excl = incl - d;
     const long long total = __shfl_sync(0xffffffffu, incl, 31);
+    const int32_t s0 = __shfl_sync(0xffffffffu, s, 0);
+    const bool uni = __all_sync(0xffffffffu, s < 0 || s == s0);
+    unsigned long long acc = 0;
     for (long long x0 = 0; x0 < total; x0 += 32) {
       const long long x = x0 + lane;
       int L = 0;
@@ -322,17 +327,21 @@ __global__ void __launch_bounds__(256) k_slot_cut(const int64_t* __restrict__ ro
       const long long exL = __shfl_sync(0xffffffffu, excl, L);
       const int32_t lvL = __shfl_sync(0xffffffffu, lv, L);
       const int32_t sL = __shfl_sync(0xffffffffu, s, L);
-      int32_t w = 0;
       if (x < total) {
         const int64_t e = rsL + (x - exL);
-        if (label[col[e]] != lvL) w = ew[e];
+        if (label[col[e]] != lvL) {
+          const int32_t w = ew[e];
+          if (uni) acc += (unsigned long long)w;
+          else if (sL == sh_slot) atomicAdd(&sh_sum, (unsigned long long)w);
+          else atomicAdd(ull(&cut2[sL]), (unsigned long long)w);
+        }
       }
-      const int32_t key = w > 0 ? sL : -1;
-      const unsigned mm = __match_any_sync(0xffffffffu, key);
-      const int64_t sum = match_sum(mm, w);
-      if (key >= 0 && lane == __ffs(mm) - 1) {
-        if (sL == sh_slot) atomicAdd(&sh_sum, (unsigned long long)sum);
-        else atomicAdd(ull(&cut2[sL]), (unsigned long long)sum);
+    }
+    if (uni) {
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0 && acc) {
+        if (s0 == sh_slot) atomicAdd(&sh_sum, acc);
+        else atomicAdd(ull(&cut2[s0]), acc);
       }
     }
   }

@@ -28,6 +28,8 @@ struct LPArgs {
   const int32_t* ew;
   const int32_t* nw;
   const int32_t* gid;
+  int32_t narrow;          // 1: every connection sum is below 2^32
+  int32_t arcs32;          // 1: the level has fewer than 2^32 arcs
   // slots
   const int64_t* noff;
   const int64_t* loff;
@@ -230,6 +232,11 @@ __device__ __forceinline__ int node_key(const LPArgs& a, const uint8_t* ac, int6
   return sub * NB + bucket_of(deg, ov);
 }
 
+// Per-key node counts and arc sums, first per CTA in shared memory.  The arc
+// sums are 64-bit words, added with 32-bit atomics on the low word when the
+// level has fewer than 2^32 arcs (a CTA's sum is then below 2^32 too): the
+// lanes of a warp meet only a few keys, and contended 64-bit shared atomics
+// serialise.
 __global__ void __launch_bounds__(BK_NT) k_bucket_count(LPArgs a, int64_t N) {
   __shared__ int sh_cnt[MAX_KEYS];
   __shared__ unsigned long long sh_arcs[MAX_KEYS];
@@ -253,7 +260,8 @@ __global__ void __launch_bounds__(BK_NT) k_bucket_count(LPArgs a, int64_t N) {
     a.nkey[v] = (int16_t)key;
     if (key >= 0) {
       atomicAdd(&sh_cnt[key], 1);
-      atomicAdd(&sh_arcs[key], (unsigned long long)deg);
+      if (a.arcs32) atomicAdd(reinterpret_cast<unsigned int*>(&sh_arcs[key]), (unsigned int)deg);
+      else atomicAdd(&sh_arcs[key], (unsigned long long)deg);
       any_ov = any_ov || ov;
     }
   }
@@ -461,6 +469,17 @@ __device__ void block_reduce(long long& oc, Cand& cd, long long* sh_oc, Cand* sh
 }
 
 
+// Adds an arc weight to a connection sum held in 64 bits.  When every sum of
+// the level stays below 2^32 the add is a 32-bit atomic on the low word (the
+// high word stays zero): on sm_103a a 64-bit shared-memory atomic add costs
+// 6.7x a 32-bit one on distinct addresses and about 90x (16 addresses) to
+// 800x (2 addresses) under the contention of a high-degree row that meets
+// few labels (measured, 512 threads).
+__device__ __forceinline__ void conn_add(unsigned long long* p, int32_t w, int32_t narrow) {
+  if (narrow) atomicAdd(reinterpret_cast<unsigned int*>(p), (unsigned int)w);
+  else atomicAdd(p, (unsigned long long)w);
+}
+
 // Degrees 17..128 (and nodes of overloaded blocks up to that degree): one
 // warp per node, eight warps per CTA, each with a private WCAP-slot table in
 // shared memory, so no CTA barrier is needed between nodes.  The row (at most
@@ -515,14 +534,14 @@ __global__ void __launch_bounds__(WPC * 32) k_propose_warp(LPArgs a, int32_t sub
       const int32_t key = C[t] < 0 ? -1 : (direct ? (int32_t)(C[t] - c.loff) : C[t]);
       if (key < 0) continue;
       if (direct) {
-        atomicAdd(&vals[key], (unsigned long long)w[t]);
+        conn_add(&vals[key], w[t], a.narrow);
       } else {
         uint32_t s = table_slot(key, WLOG);
         for (int p = 0; p < WCAP; ++p) {
           const int32_t prev = atomicCAS(&keys[s], -1, key);
           if (prev == -1 || prev == key) {
             if (prev == -1) { created |= 1u << t; slot[t] = (int)s; }
-            atomicAdd(&vals[s], (unsigned long long)w[t]);
+            conn_add(&vals[s], w[t], a.narrow);
             break;
           }
           s = (s + 1) & (WCAP - 1);
@@ -655,19 +674,18 @@ __global__ void __launch_bounds__(NT) k_propose_blk(LPArgs a, int32_t sub, int32
       for (int u = 0; u < 4; ++u) {
         if (e0 + (int64_t)u * NT >= c.re) break;
         const int32_t key = C[u] < 0 ? -1 : (direct ? (int32_t)(C[u] - c.loff) : C[u]);
-        const int64_t sum = w[u];
         bool cr = false;
         uint32_t s = 0;
         if (key >= 0) {
           if (direct) {
-            atomicAdd(&vals[key], (unsigned long long)sum);
+            conn_add(&vals[key], w[u], a.narrow);
           } else {
             s = table_slot(key, logcap);
             for (uint32_t p = 0; p <= mask; ++p) {
               const int32_t prev = atomicCAS(&keys[s], -1, key);
               if (prev == -1 || prev == key) {
                 cr = prev == -1;
-                atomicAdd(&vals[s], (unsigned long long)sum);
+                conn_add(&vals[s], w[u], a.narrow);
                 break;
               }
               s = (s + 1) & mask;
@@ -1374,6 +1392,8 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, wgt_t*
 
   LPArgs a{};
   a.row_ptr = lv.row_ptr; a.col = lv.col; a.ew = lv.ew; a.nw = lv.nw; a.gid = lv.gid;
+  a.narrow = lv.narrow ? 1 : 0;
+  a.arcs32 = lv.M < ((int64_t)1 << 32) ? 1 : 0;
   a.noff = sp.noff; a.loff = sp.loff; a.bound = sp.bound; a.rkey = sp.rkey; a.nlab = sp.nlab;
   a.done = sp.done; a.moved = sp.moved; a.rounds = sp.rounds;
   a.label = label; a.W = W; a.in_w = in_w.p; a.mode = run.mode; a.S = S;

@@ -446,6 +446,50 @@ def test_full_batch_sampled_against_oracle():
         assert O.cut(g, b) == res[i].cut
 
 
+def _heavy(g, seed, bits=22):
+    """Edge weights up to 2^bits: the total arc weight is far above 2^32, so
+    the propose tables must accumulate in 64 bits (coarse edges stay below
+    2^31 for the inputs used here)."""
+    h = gg.random_weights(g, seed, max_node_w=3, max_edge_w=1 << bits)
+    assert int(h.edge_w.astype(np.int64).sum()) > (1 << 32)
+    return h
+
+
+@pytest.mark.parametrize("name,k", [("hub", 4), ("rmat12", 2), ("rmat16", 8)])
+def test_heavy_edge_weights_bit_exact(name, k):
+    g = _heavy(GRAPHS[name](), 17)
+    ref = O.partition(g, k, 0.03, seed=4)
+    res = P.sclap_partition_device(*dg(g), k=k, eps=0.03, seed=4)
+    assert (res.status, res.cut) == (ref.status, ref.cut)
+    assert np.array_equal(res.block.cpu().numpy(), ref.block)
+
+
+def test_batch_with_one_heavy_graph_equals_oracle():
+    """One heavy graph puts the whole batch on 64-bit sums; the light graphs'
+    results must not change."""
+    gs = [(gg.rmat(12, 8, 31), 4), (_heavy(hub_graph(5), 3, bits=20), 2), (gg.rgg2d(3000, 32), 8),
+          (gg.random_weights(gg.rmat(11, 8, 33), 34), 16)]
+    items = [dict(row_ptr=dt(g.row_ptr), col=dt(g.col), node_w=dt(g.node_w), edge_w=dt(g.edge_w),
+                  k=k, eps=0.03, seed=40 + i) for i, (g, k) in enumerate(gs)]
+    res = P.sclap_partition_batch(items, device=True)
+    for i, (g, k) in enumerate(gs):
+        ref = O.partition(g, k, 0.03, seed=40 + i)
+        assert (res[i].status, res[i].cut) == (ref.status, ref.cut), i
+        assert np.array_equal(res[i].block.cpu().numpy(), ref.block), i
+
+
+def test_coarse_edge_weight_overflow_reported_like_the_oracle():
+    """Edge weights up to 2^22 around a degree-9000 hub: merged coarse edges
+    pass 2^31.  The oracle stops with its overflow code; the device call
+    fails with SCLAP_EOVERFLOW."""
+    g = gg.random_weights(hub_graph(5), 3, max_node_w=3, max_edge_w=1 << 22)
+    with pytest.raises(RuntimeError, match="rc=-2"):
+        O.partition(g, 2, 0.03, seed=4)
+    with pytest.raises(P.SclapError) as e:
+        P.sclap_partition_device(*dg(g), k=2, eps=0.03, seed=4)
+    assert e.value.code == P.EOVERFLOW
+
+
 def test_scale19_rmat_bit_exact_both_drivers():
     """A larger input (R-MAT scale 19, 524,288 nodes): the whole partition
     bit-exact with the oracle under both round drivers; the reported cut
