@@ -433,6 +433,7 @@ struct GGGArgs {
   wgt_t* W;                // out: block weights
   int64_t* conn;           // scratch [N]
   int32_t* step;           // scratch [N]
+  int32_t* front;          // scratch [N]: newly reached nodes (step alternates with it)
   int64_t* wfA;            // scratch [sum k]
   int32_t* wforder;        // scratch [sum k]
   int32_t nslots;

@@ -105,11 +105,23 @@ __device__ __forceinline__ void for_inter_arcs(const CArgs& a, int64_t N, F f) {
   }
 }
 
+// Inter-cluster arcs per coarse node.  The lanes' arcs are in source order,
+// so lanes with the same coarse source form runs of consecutive lanes; two
+// ballots give each run's count and its last lane adds it (runs with equal
+// sources that are not adjacent simply add separately).
 __global__ void __launch_bounds__(256) k_count_inter(CArgs a, int64_t N) {
+  const int lane = threadIdx.x & 31;
   for_inter_arcs(a, N, [&](int32_t cv, int32_t cu, int32_t) {
-    const int32_t key = cu >= 0 ? cv : -1;
-    const unsigned mm = __match_any_sync(0xffffffffu, key);
-    if (key >= 0 && (threadIdx.x & 31) == __ffs(mm) - 1) atomicAdd(&a.inter[cv], __popc(mm));
+    const unsigned inter = __ballot_sync(0xffffffffu, cu >= 0);
+    const int32_t prev = __shfl_up_sync(0xffffffffu, cv, 1);
+    const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || prev != cv);
+    const bool last = lane == 31 || ((heads >> (lane + 1)) & 1u);
+    if (last) {
+      const unsigned upto = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);   // lanes 0..lane
+      const int first = 31 - __clz(heads & upto);                               // run start
+      const int c = __popc(inter & upto & ~((1u << first) - 1u));
+      if (c) atomicAdd(&a.inter[cv], c);
+    }
   });
 }
 

@@ -481,7 +481,8 @@ void run_ip(const std::vector<IPIn>& in, const sclap_config& cfg, wgt_t* Wg,
   fill_gid(ip.noff_d.p, S, ip.gid.p, ip.N, s);
 
   const int64_t K = boff[S];
-  DevBuf<int32_t> label(std::max<int64_t>(ip.N, 1), s), step(std::max<int64_t>(ip.N, 1), s);
+  DevBuf<int32_t> label(std::max<int64_t>(ip.N, 1), s), step(std::max<int64_t>(ip.N, 1), s),
+      front(std::max<int64_t>(ip.N, 1), s);
   DevBuf<wgt_t> W(std::max<int64_t>(K, 1), s);
   DevBuf<int64_t> conn(std::max<int64_t>(ip.N, 1), s);
   DevBuf<int64_t> wfA(std::max<int64_t>(K, 1), s), d_boff(S + 1, s), d_avg(S, s);
@@ -507,7 +508,7 @@ void run_ip(const std::vector<IPIn>& in, const sclap_config& cfg, wgt_t* Wg,
   ga.row_ptr = ip.row_ptr.p; ga.col = ip.col.p; ga.ew = ip.ew.p; ga.nw = ip.nw.p;
   ga.noff = ip.noff_d.p; ga.boff = d_boff.p; ga.nlab = sl.nlab.p; ga.avg = d_avg.p;
   ga.tkey = sl.seed.p; ga.level = sl.level.p; ga.label = label.p; ga.W = W.p;
-  ga.conn = conn.p; ga.step = step.p; ga.wfA = wfA.p; ga.wforder = wforder.p;
+  ga.conn = conn.p; ga.step = step.p; ga.front = front.p; ga.wfA = wfA.p; ga.wforder = wforder.p;
   ga.nslots = S;
   ggg_trials(ga, s);
 

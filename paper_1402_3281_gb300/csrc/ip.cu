@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(GNT) k_ggg(GGGArgs a) {
   __shared__ uint64_t shh[GNT / 32];
   __shared__ int32_t shv[GNT / 32];
   __shared__ int64_t Wj_sh, accw_sh;
-  __shared__ int32_t nstep_sh, seed_sh;
+  __shared__ int32_t nstep_sh, seed_sh, nfront_sh;
   // a chunk of step nodes: row start, first and one-past-last arc offset
   __shared__ int64_t st_rs[GNT], st_ex[GNT], st_in[GNT];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -118,11 +118,20 @@ __global__ void __launch_bounds__(GNT) k_ggg(GGGArgs a) {
       const int32_t seed = seed_sh;
       if (seed < 0) break;
       for (int64_t v = tid; v < n; v += GNT) a.conn[base + v] = 0;
+      // step nodes and newly reached nodes: two scratch lists that swap roles
+      int32_t* stp = a.step + base;
+      int32_t* frt = a.front + base;
+      // while every step has absorbed all its candidates, the candidates of
+      // the next step are exactly the nodes first reached by this one, listed
+      // as they are reached; the first step whose candidates do not all fit
+      // switches the block to the ordered scan over all nodes
+      bool ordered = false;
       __syncthreads();
       if (tid == 0) {
         a.label[base + seed] = (int32_t)(bo + j);
-        a.step[base] = (int32_t)(base + seed);
+        stp[0] = (int32_t)(base + seed);
         nstep_sh = 1;
+        nfront_sh = 0;
         Wj_sh = a.nw[base + seed];
       }
       __syncthreads();
@@ -131,11 +140,12 @@ __global__ void __launch_bounds__(GNT) k_ggg(GGGArgs a) {
         // the arcs of up to GNT step nodes at a time are spread over all
         // threads (a hub in the step does not hold back one warp)
         const int32_t nstep = nstep_sh;
+        int64_t fw = 0;   // weight of the nodes this thread listed
         for (int32_t q0 = 0; q0 < nstep; q0 += GNT) {
           const int32_t q = q0 + tid;
           int64_t rs = 0, d = 0;
           if (q < nstep) {
-            const int32_t u = a.step[base + q];
+            const int32_t u = stp[q];
             rs = a.row_ptr[u];
             d = a.row_ptr[u + 1] - rs;
           }
@@ -156,12 +166,38 @@ __global__ void __launch_bounds__(GNT) k_ggg(GGGArgs a) {
             }
             const int64_t e = st_rs[lo] + (x - st_ex[lo]);
             const int32_t y = a.col[e];
-            if (a.label[y] < 0) atomicAdd(ull(&a.conn[y]), (unsigned long long)a.ew[e]);
+            if (a.label[y] < 0) {
+              const unsigned long long old =
+                  atomicAdd(ull(&a.conn[y]), (unsigned long long)a.ew[e]);
+              if (!ordered && old == 0) {          // first arc into y (weights > 0)
+                frt[atomicAdd(&nfront_sh, 1)] = y;
+                fw += a.nw[y];
+              }
+            }
           }
           __syncthreads();
         }
         const int64_t Wj = Wj_sh;
         if (Wj >= avg) break;
+        if (!ordered) {
+          const int64_t fsum = block_sum(fw, sh);
+          const int32_t nf = nfront_sh;
+          if (Wj + fsum <= avg) {
+            // all of them fit: they are the next step, in any order
+            for (int32_t q = tid; q < nf; q += GNT) a.label[frt[q]] = (int32_t)(bo + j);
+            int32_t* t = stp; stp = frt; frt = t;
+            __syncthreads();
+            if (tid == 0) {
+              nstep_sh = nf;
+              nfront_sh = 0;
+              Wj_sh = Wj + fsum;
+            }
+            __syncthreads();
+            if (nf == 0) break;
+            continue;
+          }
+          ordered = true;
+        }
         if (tid == 0) accw_sh = 0;
         // connected unassigned nodes in id order, longest prefix that fits;
         // when all of them fit (the usual step) no ordered scan is needed
@@ -188,7 +224,7 @@ __global__ void __launch_bounds__(GNT) k_ggg(GGGArgs a) {
           int64_t tc;
           const int64_t ic = block_incl_scan(adm ? 1 : 0, sh, &tc);
           if (adm) {
-            a.step[base + carry_c + ic - 1] = (int32_t)(base + v);
+            stp[carry_c + ic - 1] = (int32_t)(base + v);
             atomicAdd(ull(&accw_sh), (unsigned long long)wt);
           }
           carry_w += tw;
@@ -203,7 +239,7 @@ __global__ void __launch_bounds__(GNT) k_ggg(GGGArgs a) {
         __syncthreads();
         const int32_t ns2 = nstep_sh;
         if (ns2 == 0) break;
-        for (int32_t q = tid; q < ns2; q += GNT) a.label[a.step[base + q]] = (int32_t)(bo + j);
+        for (int32_t q = tid; q < ns2; q += GNT) a.label[stp[q]] = (int32_t)(bo + j);
         __syncthreads();
       }
       if (tid == 0) a.W[bo + j] = (wgt_t)Wj_sh;
