@@ -115,10 +115,12 @@ enum Phase : int32_t {
 };
 enum Mode : int32_t { MODE_CLUSTER = 0, MODE_REFINE = 1, MODE_REPAIR = 2 };
 
-// Degree buckets of the LP sweep.  0..3: a group of 4/8/16/32 lanes per node,
-// labels aggregated with warp match; 4..7: one CTA of 64/128/256/512 threads
-// per node with a shared-memory table of 256/1024/4096/16384 slots; 8: one
-// CTA per node, table in global scratch (hubs).
+// Degree buckets of the LP sweep.  0..2 (degree <= 4 / 8 / 16): one thread
+// per node, the row sorted in registers; 3..4 (<= 32 / 128, and overloaded
+// nodes up to 128): one warp per node with a 256-slot shared table; 5..7
+// (<= 512 / 2048 / 8192): one CTA of 128/256/512 threads per node with a
+// shared table of 1024/4096/16384 slots; 8: one CTA per node, table in
+// global scratch (hubs).  Nodes of overloaded blocks skip buckets 0..3.
 constexpr int NB = 9;
 constexpr int B4_MAXDEG = 128, B4_SLOTS = 256;
 constexpr int B5_MAXDEG = 512, B5_SLOTS = 1024;
@@ -331,9 +333,6 @@ void scan_excl_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t s);
 void scan_excl_u8_to_i64(const uint8_t* in, int64_t* out, int64_t n, cudaStream_t s);
 // out[i] = number of keys[0..i) that are >= 0 (occupied hash slots).
 void scan_excl_occupied(const int32_t* keys, int64_t* out, int64_t n, cudaStream_t s);
-// out[i] = number of slots[0..i) that are not ~0 (occupied packed slots).
-void scan_excl_occupied_slots(const unsigned long long* slots, int64_t* out, int64_t n,
-                              cudaStream_t s);
 // largest row length (atomicMax into *out, which the caller zeroes)
 // out[0] = largest degree of the level, out[1] = nodes with degree > thr
 // (out zeroed by the caller).

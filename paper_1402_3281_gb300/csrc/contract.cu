@@ -42,6 +42,7 @@ struct CArgs {
   int32_t* inter;          // inter-cluster arcs per coarse node
   const int64_t* tbase;    // table region of each coarse node
   unsigned long long* tslot;   // (coarse neighbour << 32) | summed weight; ~0 = empty
+  int32_t* cdeg;           // distinct coarse neighbours per coarse node (slots claimed)
   int32_t* err;
 };
 
@@ -151,7 +152,10 @@ __global__ void __launch_bounds__(256) k_insert(CArgs a, int64_t N) {
       unsigned long long cur = *slot;
       if (cur == ~0ull) {
         cur = atomicCAS(slot, ~0ull, mine);
-        if (cur == ~0ull) return;
+        if (cur == ~0ull) {            // claimed: one more coarse arc of cv
+          atomicAdd(&a.cdeg[cv], 1);
+          return;
+        }
       }
       if ((uint32_t)(cur >> 32) == (uint32_t)cu) {
         const unsigned long long old = atomicAdd(slot, (unsigned long long)sum);
@@ -165,26 +169,34 @@ __global__ void __launch_bounds__(256) k_insert(CArgs a, int64_t N) {
   });
 }
 
-// Occupied slots land at their rank among all occupied slots: regions are
-// laid out in coarse-node order, so that rank is the CSR position directly.
-__global__ void k_emit(const unsigned long long* __restrict__ tslot,
-                       const int64_t* __restrict__ pos, int64_t T, int32_t* __restrict__ ccol,
-                       int32_t* __restrict__ cew) {
-  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < T;
-       j += (int64_t)gridDim.x * blockDim.x) {
-    const unsigned long long x = tslot[j];
-    if (x == ~0ull) continue;
-    ccol[pos[j]] = (int32_t)(x >> 32);
-    cew[pos[j]] = (int32_t)(x & 0xffffffffull);
+// Coarse rows: one warp per coarse node compacts the occupied slots of its
+// table region, in slot order, to the node's CSR positions (row offsets from
+// a scan of the claimed-slot counts), so no pass over all table slots is
+// needed to rank them.
+__global__ void __launch_bounds__(256) k_emit_rows(const unsigned long long* __restrict__ tslot,
+                                                   const int64_t* __restrict__ tbase,
+                                                   const int64_t* __restrict__ crow, int64_t Nc,
+                                                   int32_t* __restrict__ ccol,
+                                                   int32_t* __restrict__ cew) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t c = w0; c < Nc; c += nwarps) {
+    const int64_t b = tbase[c], e = tbase[c + 1];
+    int64_t out = crow[c];
+    for (int64_t j0 = b; j0 < e; j0 += 32) {
+      const int64_t j = j0 + lane;
+      const unsigned long long x = j < e ? tslot[j] : ~0ull;
+      const bool occ = x != ~0ull;
+      const unsigned bits = __ballot_sync(0xffffffffu, occ);
+      if (occ) {
+        const int64_t p = out + __popc(bits & ((1u << lane) - 1u));
+        ccol[p] = (int32_t)(x >> 32);
+        cew[p] = (int32_t)(x & 0xffffffffull);
+      }
+      out += __popc(bits);
+    }
   }
-}
-
-// crow[c] = occupied slots before region c; crow[Nc] = total.
-__global__ void k_rows(const int64_t* __restrict__ tbase, const int64_t* __restrict__ pos,
-                       int64_t Nc, int64_t* __restrict__ crow) {
-  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c <= Nc;
-       c += (int64_t)gridDim.x * blockDim.x)
-    crow[c] = pos[tbase[c]];
 }
 
 // Overlay (ensemble clusterings): the pair (O[v], C[v]) keys an open-
@@ -309,22 +321,25 @@ void contract_build(const LevelView& lv, const std::vector<int64_t>& noff, const
   SCLAP_CUDA(cudaMemcpyAsync(&T, tbase.p + Nc, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   stream_sync(s);
   DevBuf<unsigned long long> tslot(std::max<int64_t>(T, 1), s);
-  DevBuf<int64_t> pos(T + 1, s);
   tslot.fill_bytes(0xff);
   a.tslot = tslot.p;
+  // the inter-arc counts have served (table sizes); the array now counts
+  // claimed slots, i.e. the coarse degrees
+  a.cdeg = inter.p;
+  SCLAP_CUDA(cudaMemsetAsync(inter.p, 0, (size_t)std::max<int64_t>(Nc, 1) * sizeof(int32_t), s));
   if (N > 0 && T > 0) { k_insert<<<wg, 256, 0, s>>>(a, N); SCLAP_NOTE_LAUNCH("k_insert"); }
-  scan_excl_occupied_slots(tslot.p, pos.p, T, s);
   out.row_ptr.alloc(Nc + 1, s);
-  k_rows<<<grid_for(Nc + 1, 256, (int64_t)sms * 16), 256, 0, s>>>(tbase.p, pos.p, Nc, out.row_ptr.p); SCLAP_NOTE_LAUNCH("k_rows");
+  scan_excl_i32_to_i64(inter.p, out.row_ptr.p, Nc, s);
   int64_t Mc = 0;
-  SCLAP_CUDA(cudaMemcpyAsync(&Mc, pos.p + T, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  SCLAP_CUDA(cudaMemcpyAsync(&Mc, out.row_ptr.p + Nc, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   stream_sync(s);
   out.M = Mc;
   out.col.alloc(std::max<int64_t>(Mc, 1), s);
   out.ew.alloc(std::max<int64_t>(Mc, 1), s);
-  if (T > 0) {
-    k_emit<<<grid_for(T, 256, (int64_t)sms * 32), 256, 0, s>>>(tslot.p, pos.p, T, out.col.p,
-                                                               out.ew.p); SCLAP_NOTE_LAUNCH("k_emit");
+  if (Nc > 0 && T > 0) {
+    k_emit_rows<<<grid_for(Nc, 8, (int64_t)sms * 16), 256, 0, s>>>(tslot.p, tbase.p,
+                                                                   out.row_ptr.p, Nc, out.col.p,
+                                                                   out.ew.p); SCLAP_NOTE_LAUNCH("k_emit_rows");
   }
   SCLAP_LAUNCH_CHECK();
   out.gid.alloc(std::max<int64_t>(Nc, 1), s);

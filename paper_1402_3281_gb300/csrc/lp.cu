@@ -376,29 +376,75 @@ __device__ __forceinline__ void sorted_row_best(const LPArgs& a, const NodeCtx& 
   }
 }
 
+// One thread per node, 32 nodes per warp.  The warp first stages the rows of
+// its 32 nodes: their arcs are spread over the lanes in row order (owner
+// found from a prefix sum of the degrees), so consecutive lanes read
+// consecutive addresses of the same row, and each lane gathers the label at
+// the far end of its arc.  The (label, weight) pairs land in shared memory at
+// [j * 33 + node] (the skew keeps both the scattered writes of one row and
+// the reads of entry j by all 32 nodes free of bank conflicts); each thread
+// then reads its own row back into registers and sorts it.
+constexpr int STG_STRIDE = 33;
+
 template <int MAXD>
 __device__ __forceinline__ void propose_thread(const LPArgs& a, int64_t lbeg, int64_t cnt,
-                                               int64_t blk, int64_t nblk) {
-  for (int64_t li = blk * blockDim.x + threadIdx.x; li < cnt; li += nblk * blockDim.x) {
-    const int64_t i = lbeg + li;
-    const NodeCtx c = load_node(a, i);
-    const int deg = (int)(c.re - c.rs);
-    int32_t C[MAXD], w[MAXD];
-    int64_t total = 0;
-#pragma unroll
-    for (int j = 0; j < MAXD; ++j) {
-      const bool in = j < deg;
-      w[j] = in ? a.ew[c.rs + j] : 0;
-      C[j] = in ? a.col[c.rs + j] : -1;
-      total += w[j];
+                                               int64_t blk, int64_t nblk, int32_t* stC,
+                                               int32_t* stW) {
+  const int lane = threadIdx.x & 31;
+  const int64_t step = nblk * blockDim.x;
+  for (int64_t wb = blk * blockDim.x + (threadIdx.x & ~31); wb < cnt; wb += step) {
+    const int64_t li = wb + lane;
+    const bool act = li < cnt;
+    NodeCtx c{};
+    int deg = 0;
+    if (act) {
+      c = load_node(a, lbeg + li);
+      deg = (int)(c.re - c.rs);
     }
+    int incl = deg;
 #pragma unroll
-    for (int j = 0; j < MAXD; ++j) C[j] = C[j] >= 0 ? a.label[C[j]] : INT32_MAX;
-    long long oc = 0;
-    Cand best{-1, 0, 0};
-    if (total <= INT32_MAX) sorted_row_best<MAXD, int32_t>(a, c, C, w, oc, best);
-    else sorted_row_best<MAXD, int64_t>(a, c, C, w, oc, best);
-    write_prop(a, i, c, best, oc, false);
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const int excl = incl - deg;
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    for (int x0 = 0; x0 < total; x0 += 32) {
+      const int x = x0 + lane;
+      int L = 0;                       // first lane whose inclusive prefix exceeds x
+#pragma unroll
+      for (int st = 16; st > 0; st >>= 1) {
+        const int y = __shfl_sync(0xffffffffu, incl, L + st - 1);
+        if (y <= x) L += st;
+      }
+      const long long rsL = __shfl_sync(0xffffffffu, (long long)c.rs, L);
+      const int exL = __shfl_sync(0xffffffffu, excl, L);
+      if (x < total) {
+        const int j = x - exL;
+        const int64_t e = rsL + j;
+        const int32_t u = a.col[e];
+        stW[j * STG_STRIDE + L] = a.ew[e];
+        stC[j * STG_STRIDE + L] = a.label[u];
+      }
+    }
+    __syncwarp();
+    if (act) {
+      int32_t C[MAXD], w[MAXD];
+      int64_t tw = 0;
+#pragma unroll
+      for (int j = 0; j < MAXD; ++j) {
+        const bool in = j < deg;
+        C[j] = in ? stC[j * STG_STRIDE + lane] : INT32_MAX;
+        w[j] = in ? stW[j * STG_STRIDE + lane] : 0;
+        tw += w[j];
+      }
+      long long oc = 0;
+      Cand best{-1, 0, 0};
+      if (tw <= INT32_MAX) sorted_row_best<MAXD, int32_t>(a, c, C, w, oc, best);
+      else sorted_row_best<MAXD, int64_t>(a, c, C, w, oc, best);
+      write_prop(a, lbeg + li, c, best, oc, false);
+    }
+    __syncwarp();                      // the staging area is reused
   }
 }
 
@@ -409,6 +455,10 @@ __device__ __forceinline__ void propose_thread(const LPArgs& a, int64_t lbeg, in
 // needs (256 nodes per block), every non-empty bucket getting at least one;
 // every block computes the same split from the device offsets.
 __global__ void __launch_bounds__(256, 4) k_propose_small(LPArgs a, int32_t sub, int32_t nb) {
+  __shared__ int32_t stg_c[8][16 * STG_STRIDE];
+  __shared__ int32_t stg_w[8][16 * STG_STRIDE];
+  int32_t* stC = stg_c[threadIdx.x >> 5];
+  int32_t* stW = stg_w[threadIdx.x >> 5];
   const int64_t* bo = a.boff + sub * NB;
   int64_t c[3], need[3], tot = 0;
 #pragma unroll
@@ -435,9 +485,10 @@ __global__ void __launch_bounds__(256, 4) k_propose_small(LPArgs a, int32_t sub,
     g[last] += G - used;
   }
   const int64_t b = blockIdx.x;
-  if (b < g[0]) propose_thread<4>(a, bo[0], c[0], b, g[0]);
-  else if (b < g[0] + g[1]) propose_thread<8>(a, bo[1], c[1], b - g[0], g[1]);
-  else if (b < g[0] + g[1] + g[2]) propose_thread<16>(a, bo[2], c[2], b - g[0] - g[1], g[2]);
+  if (b < g[0]) propose_thread<4>(a, bo[0], c[0], b, g[0], stC, stW);
+  else if (b < g[0] + g[1]) propose_thread<8>(a, bo[1], c[1], b - g[0], g[1], stC, stW);
+  else if (b < g[0] + g[1] + g[2])
+    propose_thread<16>(a, bo[2], c[2], b - g[0] - g[1], g[2], stC, stW);
 }
 
 __device__ __forceinline__ int64_t table_get(const int32_t* keys, const unsigned long long* vals,

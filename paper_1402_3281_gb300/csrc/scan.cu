@@ -45,11 +45,6 @@ struct Plain {
 struct Occupied {
   __device__ __forceinline__ int64_t operator()(int32_t x) const { return x >= 0 ? 1 : 0; }
 };
-struct OccupiedSlot {
-  __device__ __forceinline__ int64_t operator()(unsigned long long x) const {
-    return x != ~0ull ? 1 : 0;
-  }
-};
 
 template <class Tin, class Tout, class F = Plain>
 __global__ void __launch_bounds__(SB) k_reduce(const Tin* __restrict__ in, int64_t n,
@@ -176,10 +171,6 @@ void scan_excl_u8_to_i64(const uint8_t* in, int64_t* out, int64_t n, cudaStream_
 }
 void scan_excl_occupied(const int32_t* keys, int64_t* out, int64_t n, cudaStream_t s) {
   scan_excl<int32_t, int64_t, Occupied>(keys, out, n, s);
-}
-void scan_excl_occupied_slots(const unsigned long long* slots, int64_t* out, int64_t n,
-                              cudaStream_t s) {
-  scan_excl<unsigned long long, int64_t, OccupiedSlot>(slots, out, n, s);
 }
 
 void fill_gid(const int64_t* noff, int32_t nslots, int32_t* gid, int64_t N, cudaStream_t s) {
