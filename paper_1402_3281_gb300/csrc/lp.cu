@@ -28,7 +28,7 @@ struct LPArgs {
   const int32_t* ew;
   const int32_t* nw;
   const int32_t* gid;
-  int32_t narrow;          // 1: every connection sum is below 2^32
+  int32_t narrow;          // 1: every connection sum is below 2^32 - 1
   int32_t arcs32;          // 1: the level has fewer than 2^32 arcs
   // slots
   const int64_t* noff;
@@ -376,75 +376,29 @@ __device__ __forceinline__ void sorted_row_best(const LPArgs& a, const NodeCtx& 
   }
 }
 
-// One thread per node, 32 nodes per warp.  The warp first stages the rows of
-// its 32 nodes: their arcs are spread over the lanes in row order (owner
-// found from a prefix sum of the degrees), so consecutive lanes read
-// consecutive addresses of the same row, and each lane gathers the label at
-// the far end of its arc.  The (label, weight) pairs land in shared memory at
-// [j * 33 + node] (the skew keeps both the scattered writes of one row and
-// the reads of entry j by all 32 nodes free of bank conflicts); each thread
-// then reads its own row back into registers and sorts it.
-constexpr int STG_STRIDE = 33;
-
 template <int MAXD>
 __device__ __forceinline__ void propose_thread(const LPArgs& a, int64_t lbeg, int64_t cnt,
-                                               int64_t blk, int64_t nblk, int32_t* stC,
-                                               int32_t* stW) {
-  const int lane = threadIdx.x & 31;
-  const int64_t step = nblk * blockDim.x;
-  for (int64_t wb = blk * blockDim.x + (threadIdx.x & ~31); wb < cnt; wb += step) {
-    const int64_t li = wb + lane;
-    const bool act = li < cnt;
-    NodeCtx c{};
-    int deg = 0;
-    if (act) {
-      c = load_node(a, lbeg + li);
-      deg = (int)(c.re - c.rs);
-    }
-    int incl = deg;
+                                               int64_t blk, int64_t nblk) {
+  for (int64_t li = blk * blockDim.x + threadIdx.x; li < cnt; li += nblk * blockDim.x) {
+    const int64_t i = lbeg + li;
+    const NodeCtx c = load_node(a, i);
+    const int deg = (int)(c.re - c.rs);
+    int32_t C[MAXD], w[MAXD];
+    int64_t total = 0;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += y;
+    for (int j = 0; j < MAXD; ++j) {
+      const bool in = j < deg;
+      w[j] = in ? a.ew[c.rs + j] : 0;
+      C[j] = in ? a.col[c.rs + j] : -1;
+      total += w[j];
     }
-    const int excl = incl - deg;
-    const int total = __shfl_sync(0xffffffffu, incl, 31);
-    for (int x0 = 0; x0 < total; x0 += 32) {
-      const int x = x0 + lane;
-      int L = 0;                       // first lane whose inclusive prefix exceeds x
 #pragma unroll
-      for (int st = 16; st > 0; st >>= 1) {
-        const int y = __shfl_sync(0xffffffffu, incl, L + st - 1);
-        if (y <= x) L += st;
-      }
-      const long long rsL = __shfl_sync(0xffffffffu, (long long)c.rs, L);
-      const int exL = __shfl_sync(0xffffffffu, excl, L);
-      if (x < total) {
-        const int j = x - exL;
-        const int64_t e = rsL + j;
-        const int32_t u = a.col[e];
-        stW[j * STG_STRIDE + L] = a.ew[e];
-        stC[j * STG_STRIDE + L] = a.label[u];
-      }
-    }
-    __syncwarp();
-    if (act) {
-      int32_t C[MAXD], w[MAXD];
-      int64_t tw = 0;
-#pragma unroll
-      for (int j = 0; j < MAXD; ++j) {
-        const bool in = j < deg;
-        C[j] = in ? stC[j * STG_STRIDE + lane] : INT32_MAX;
-        w[j] = in ? stW[j * STG_STRIDE + lane] : 0;
-        tw += w[j];
-      }
-      long long oc = 0;
-      Cand best{-1, 0, 0};
-      if (tw <= INT32_MAX) sorted_row_best<MAXD, int32_t>(a, c, C, w, oc, best);
-      else sorted_row_best<MAXD, int64_t>(a, c, C, w, oc, best);
-      write_prop(a, lbeg + li, c, best, oc, false);
-    }
-    __syncwarp();                      // the staging area is reused
+    for (int j = 0; j < MAXD; ++j) C[j] = C[j] >= 0 ? a.label[C[j]] : INT32_MAX;
+    long long oc = 0;
+    Cand best{-1, 0, 0};
+    if (total <= INT32_MAX) sorted_row_best<MAXD, int32_t>(a, c, C, w, oc, best);
+    else sorted_row_best<MAXD, int64_t>(a, c, C, w, oc, best);
+    write_prop(a, i, c, best, oc, false);
   }
 }
 
@@ -455,10 +409,6 @@ __device__ __forceinline__ void propose_thread(const LPArgs& a, int64_t lbeg, in
 // needs (256 nodes per block), every non-empty bucket getting at least one;
 // every block computes the same split from the device offsets.
 __global__ void __launch_bounds__(256, 4) k_propose_small(LPArgs a, int32_t sub, int32_t nb) {
-  __shared__ int32_t stg_c[8][16 * STG_STRIDE];
-  __shared__ int32_t stg_w[8][16 * STG_STRIDE];
-  int32_t* stC = stg_c[threadIdx.x >> 5];
-  int32_t* stW = stg_w[threadIdx.x >> 5];
   const int64_t* bo = a.boff + sub * NB;
   int64_t c[3], need[3], tot = 0;
 #pragma unroll
@@ -485,10 +435,9 @@ __global__ void __launch_bounds__(256, 4) k_propose_small(LPArgs a, int32_t sub,
     g[last] += G - used;
   }
   const int64_t b = blockIdx.x;
-  if (b < g[0]) propose_thread<4>(a, bo[0], c[0], b, g[0], stC, stW);
-  else if (b < g[0] + g[1]) propose_thread<8>(a, bo[1], c[1], b - g[0], g[1], stC, stW);
-  else if (b < g[0] + g[1] + g[2])
-    propose_thread<16>(a, bo[2], c[2], b - g[0] - g[1], g[2], stC, stW);
+  if (b < g[0]) propose_thread<4>(a, bo[0], c[0], b, g[0]);
+  else if (b < g[0] + g[1]) propose_thread<8>(a, bo[1], c[1], b - g[0], g[1]);
+  else if (b < g[0] + g[1] + g[2]) propose_thread<16>(a, bo[2], c[2], b - g[0] - g[1], g[2]);
 }
 
 __device__ __forceinline__ int64_t table_get(const int32_t* keys, const unsigned long long* vals,
@@ -519,6 +468,26 @@ __device__ void block_reduce(long long& oc, Cand& cd, long long* sh_oc, Cand* sh
   }
 }
 
+
+// Warp-wide strongest candidate in two phases, for connections below
+// 2^32 - 1: the largest eligible connection M by one 32-bit reduction of
+// connection + 1 (0: none), then, among the candidates with connection M
+// only, the smallest tie-break hash by two 32-bit reductions (high word,
+// then low word among the lanes holding that high word).  The hash is a
+// bijection of the label, so the winner is unique.  Each lane passes its own
+// best hash among its candidates with connection M (has = false if none).
+__device__ __forceinline__ unsigned warp_max_conn32(int64_t lmax) {
+  return __reduce_max_sync(0xffffffffu, (unsigned)(lmax + 1));
+}
+__device__ __forceinline__ int warp_min_hash_lane(bool has, uint64_t h) {
+  const unsigned hi = has ? (unsigned)(h >> 32) : 0xffffffffu;
+  const unsigned mhi = __reduce_min_sync(0xffffffffu, hi);
+  const bool in = has && hi == mhi;
+  const unsigned lo = in ? (unsigned)h : 0xffffffffu;
+  const unsigned mlo = __reduce_min_sync(0xffffffffu, lo);
+  const unsigned win = __ballot_sync(0xffffffffu, in && (unsigned)h == mlo);
+  return __ffs(win) - 1;
+}
 
 // Adds an arc weight to a connection sum held in 64 bits.  When every sum of
 // the level stays below 2^32 the add is a 32-bit atomic on the low word (the
@@ -604,7 +573,40 @@ __global__ void __launch_bounds__(WPC * 32) k_propose_warp(LPArgs a, int32_t sub
     long long oc = 0;
     bool has_oc = false;
     Cand cd{-1, 0, 0};
-    if (direct) {
+    // two-phase argmax (hash only the candidates at the largest connection)
+    // unless the node is overloaded (every fitting block is a candidate) or
+    // connections may not fit the 32-bit reductions
+    const bool fast = a.narrow && !ov;
+    bool reduced = false;
+    if (direct && fast) {
+      const int32_t own_l = (int32_t)(c.own - c.loff);
+      int64_t lmax = -1;
+      uint32_t elig = 0;                 // bit q: block lane + 32 q is a candidate
+      for (int32_t b = lane, q = 0; b < nl; b += 32, ++q) {
+        const int64_t conn = (int64_t)vals[b];
+        if (b == own_l) { oc = conn; has_oc = true; continue; }
+        if (conn == 0) continue;
+        if ((int64_t)a.W[c.loff + b] + c.cv > c.bound) continue;
+        elig |= 1u << q;
+        lmax = conn > lmax ? conn : lmax;
+      }
+      const int64_t M = (int64_t)warp_max_conn32(lmax) - 1;
+      if (M >= 0) {
+        bool has = false;
+        uint64_t hb = ~0ull;
+        int32_t Cb = -1;
+        for (int32_t b = lane, q = 0; b < nl; b += 32, ++q) {
+          if (!((elig >> q) & 1u) || (int64_t)vals[b] != M) continue;
+          const uint64_t h = mix64(c.hv ^ (uint64_t)(uint32_t)b);
+          if (!has || h < hb) { hb = h; Cb = b; has = true; }
+        }
+        const int wl = warp_min_hash_lane(has, hb);
+        cd = Cand{M, 0, __shfl_sync(0xffffffffu, Cb, wl)};
+      }
+      reduced = true;
+      __syncwarp();
+      for (int32_t b = lane; b < nl; b += 32) vals[b] = 0;
+    } else if (direct) {
       const int32_t own_l = (int32_t)(c.own - c.loff);
       for (int32_t b = lane; b < nl; b += 32) {
         const int64_t conn = (int64_t)vals[b];
@@ -617,6 +619,48 @@ __global__ void __launch_bounds__(WPC * 32) k_propose_warp(LPArgs a, int32_t sub
       }
       __syncwarp();
       for (int32_t b = lane; b < nl; b += 32) vals[b] = 0;
+    } else if (fast) {
+      int32_t Wk[4], Bk[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const bool q = ((created >> t) & 1u) && C[t] != c.own;
+        Wk[t] = q ? a.W[C[t]] : 0;
+        Bk[t] = cand_block(a, c, q, C[t]);
+      }
+      int64_t cn[4];
+      uint32_t elig = 0;
+      int64_t lmax = -1;
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        cn[t] = -1;
+        if (!((created >> t) & 1u)) continue;
+        const int64_t conn = (int64_t)vals[slot[t]];
+        if (C[t] == c.own) { oc = conn; has_oc = true; continue; }
+        if ((int64_t)Wk[t] + c.cv > c.bound || Bk[t] != c.vb) continue;
+        cn[t] = conn;
+        elig |= 1u << t;
+        lmax = conn > lmax ? conn : lmax;
+      }
+      const int64_t M = (int64_t)warp_max_conn32(lmax) - 1;
+      if (M >= 0) {
+        bool has = false;
+        uint64_t hb = ~0ull;
+        int32_t Cb = -1;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          if (!((elig >> t) & 1u) || cn[t] != M) continue;
+          const int32_t Cl = (int32_t)(C[t] - c.loff);
+          const uint64_t h = mix64(c.hv ^ (uint64_t)(uint32_t)Cl);
+          if (!has || h < hb) { hb = h; Cb = Cl; has = true; }
+        }
+        const int wl = warp_min_hash_lane(has, hb);
+        cd = Cand{M, 0, __shfl_sync(0xffffffffu, Cb, wl)};
+      }
+      reduced = true;
+      __syncwarp();
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+        if ((created >> t) & 1u) { keys[slot[t]] = -1; vals[slot[t]] = 0; }
     } else {
       int32_t Wk[4], Bk[4];
 #pragma unroll
@@ -650,7 +694,7 @@ __global__ void __launch_bounds__(WPC * 32) k_propose_warp(LPArgs a, int32_t sub
     }
     const unsigned om = __ballot_sync(0xffffffffu, has_oc);
     oc = om ? __shfl_sync(0xffffffffu, oc, __ffs(om) - 1) : 0;
-    cd = warp_best(cd);
+    if (!reduced) cd = warp_best(cd);
     if (lane == 0) write_prop(a, i, c, cd, oc, ov);
     __syncwarp();
   }
