@@ -157,9 +157,8 @@ struct LevelView {
   const int32_t* ew = nullptr;
   const int32_t* nw = nullptr;
   const int32_t* gid = nullptr;   // slot of each node
-  // every sum of arc weights over a row (so every connection) is below
-  // 2^32 - 1: the propose tables may accumulate with 32-bit atomics and a
-  // warp may reduce connection + 1 as a 32-bit value
+  // every sum of arc weights over a row (so every connection) is below 2^32:
+  // the propose tables may accumulate with 32-bit atomics
   bool narrow = false;
 };
 

@@ -43,6 +43,7 @@ struct CArgs {
   const int64_t* tbase;    // table region of each coarse node
   unsigned long long* tslot;   // (coarse neighbour << 32) | summed weight; ~0 = empty
   int32_t* cdeg;           // distinct coarse neighbours per coarse node (slots claimed)
+  int32_t* towner;         // coarse node owning each claimed slot
   int32_t* err;
 };
 
@@ -153,6 +154,7 @@ __global__ void __launch_bounds__(256) k_insert(CArgs a, int64_t N) {
       if (cur == ~0ull) {
         cur = atomicCAS(slot, ~0ull, mine);
         if (cur == ~0ull) {            // claimed: one more coarse arc of cv
+          a.towner[base + sl] = cv;
           atomicAdd(&a.cdeg[cv], 1);
           return;
         }
@@ -169,33 +171,23 @@ __global__ void __launch_bounds__(256) k_insert(CArgs a, int64_t N) {
   });
 }
 
-// Coarse rows: one warp per coarse node compacts the occupied slots of its
-// table region, in slot order, to the node's CSR positions (row offsets from
-// a scan of the claimed-slot counts), so no pass over all table slots is
-// needed to rank them.
-__global__ void __launch_bounds__(256) k_emit_rows(const unsigned long long* __restrict__ tslot,
-                                                   const int64_t* __restrict__ tbase,
-                                                   const int64_t* __restrict__ crow, int64_t Nc,
-                                                   int32_t* __restrict__ ccol,
-                                                   int32_t* __restrict__ cew) {
-  const int lane = threadIdx.x & 31;
-  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t c = w0; c < Nc; c += nwarps) {
-    const int64_t b = tbase[c], e = tbase[c + 1];
-    int64_t out = crow[c];
-    for (int64_t j0 = b; j0 < e; j0 += 32) {
-      const int64_t j = j0 + lane;
-      const unsigned long long x = j < e ? tslot[j] : ~0ull;
-      const bool occ = x != ~0ull;
-      const unsigned bits = __ballot_sync(0xffffffffu, occ);
-      if (occ) {
-        const int64_t p = out + __popc(bits & ((1u << lane) - 1u));
-        ccol[p] = (int32_t)(x >> 32);
-        cew[p] = (int32_t)(x & 0xffffffffull);
-      }
-      out += __popc(bits);
-    }
+// Coarse rows: one thread per table slot; an occupied slot goes to its
+// owner's row (offsets from a scan of the claimed-slot counts) at a position
+// taken from a per-row counter.  The order of a row's arcs is therefore not
+// fixed, as the slot order already was not (concurrent claims in one region
+// race); nothing computed from a coarse graph depends on that order.
+__global__ void k_emit(const unsigned long long* __restrict__ tslot,
+                       const int32_t* __restrict__ towner, const int64_t* __restrict__ crow,
+                       int32_t* __restrict__ fill, int64_t T, int32_t* __restrict__ ccol,
+                       int32_t* __restrict__ cew) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < T;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long x = tslot[j];
+    if (x == ~0ull) continue;
+    const int32_t c = towner[j];
+    const int64_t p = crow[c] + atomicAdd(&fill[c], 1);
+    ccol[p] = (int32_t)(x >> 32);
+    cew[p] = (int32_t)(x & 0xffffffffull);
   }
 }
 
@@ -321,8 +313,10 @@ void contract_build(const LevelView& lv, const std::vector<int64_t>& noff, const
   SCLAP_CUDA(cudaMemcpyAsync(&T, tbase.p + Nc, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   stream_sync(s);
   DevBuf<unsigned long long> tslot(std::max<int64_t>(T, 1), s);
+  DevBuf<int32_t> towner(std::max<int64_t>(T, 1), s);
   tslot.fill_bytes(0xff);
   a.tslot = tslot.p;
+  a.towner = towner.p;
   // the inter-arc counts have served (table sizes); the array now counts
   // claimed slots, i.e. the coarse degrees
   a.cdeg = inter.p;
@@ -337,9 +331,9 @@ void contract_build(const LevelView& lv, const std::vector<int64_t>& noff, const
   out.col.alloc(std::max<int64_t>(Mc, 1), s);
   out.ew.alloc(std::max<int64_t>(Mc, 1), s);
   if (Nc > 0 && T > 0) {
-    k_emit_rows<<<grid_for(Nc, 8, (int64_t)sms * 16), 256, 0, s>>>(tslot.p, tbase.p,
-                                                                   out.row_ptr.p, Nc, out.col.p,
-                                                                   out.ew.p); SCLAP_NOTE_LAUNCH("k_emit_rows");
+    SCLAP_CUDA(cudaMemsetAsync(inter.p, 0, (size_t)Nc * sizeof(int32_t), s));   // row fill
+    k_emit<<<grid_for(T, 256, (int64_t)sms * 32), 256, 0, s>>>(tslot.p, towner.p, out.row_ptr.p,
+                                                               inter.p, T, out.col.p, out.ew.p); SCLAP_NOTE_LAUNCH("k_emit");
   }
   SCLAP_LAUNCH_CHECK();
   out.gid.alloc(std::max<int64_t>(Nc, 1), s);

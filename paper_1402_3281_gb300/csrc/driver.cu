@@ -298,7 +298,7 @@ void build_level0(const std::vector<GIn>& gs, struct Level& L, cudaStream_t s);
 
 // Validates the batched level L (built by build_level0 from `B` inputs):
 // per-graph status (SCLAP_OK, SCLAP_ECSR or SCLAP_EOVERFLOW), c(V), max c(v)
-// and whether the graph's total arc weight is below 2^32 - 1 (every sum of arc
+// and whether the graph's total arc weight fits in 32 bits (every sum of arc
 // weights met later, at any level of its hierarchy, is at most that total:
 // contraction only merges or drops arcs).
 void validate_level(const Level& L, int B, std::vector<int32_t>& status,
@@ -331,7 +331,7 @@ void validate_level(const Level& L, int B, std::vector<int32_t>& status,
     else if (w[g] >= (1ull << 31)) status[g] = SCLAP_EOVERFLOW;
     cV[g] = (int64_t)w[g];
     maxc[g] = m[g];
-    narrow[g] = aw[g] < 0xffffffffull ? 1 : 0;   // sums and sums + 1 fit in 32 bits
+    narrow[g] = aw[g] <= 0xffffffffull ? 1 : 0;
   }
 }
 

@@ -28,7 +28,7 @@ struct LPArgs {
   const int32_t* ew;
   const int32_t* nw;
   const int32_t* gid;
-  int32_t narrow;          // 1: every connection sum is below 2^32 - 1
+  int32_t narrow;          // 1: every connection sum is below 2^32
   int32_t arcs32;          // 1: the level has fewer than 2^32 arcs
   // slots
   const int64_t* noff;
@@ -469,26 +469,6 @@ __device__ void block_reduce(long long& oc, Cand& cd, long long* sh_oc, Cand* sh
 }
 
 
-// Warp-wide strongest candidate in two phases, for connections below
-// 2^32 - 1: the largest eligible connection M by one 32-bit reduction of
-// connection + 1 (0: none), then, among the candidates with connection M
-// only, the smallest tie-break hash by two 32-bit reductions (high word,
-// then low word among the lanes holding that high word).  The hash is a
-// bijection of the label, so the winner is unique.  Each lane passes its own
-// best hash among its candidates with connection M (has = false if none).
-__device__ __forceinline__ unsigned warp_max_conn32(int64_t lmax) {
-  return __reduce_max_sync(0xffffffffu, (unsigned)(lmax + 1));
-}
-__device__ __forceinline__ int warp_min_hash_lane(bool has, uint64_t h) {
-  const unsigned hi = has ? (unsigned)(h >> 32) : 0xffffffffu;
-  const unsigned mhi = __reduce_min_sync(0xffffffffu, hi);
-  const bool in = has && hi == mhi;
-  const unsigned lo = in ? (unsigned)h : 0xffffffffu;
-  const unsigned mlo = __reduce_min_sync(0xffffffffu, lo);
-  const unsigned win = __ballot_sync(0xffffffffu, in && (unsigned)h == mlo);
-  return __ffs(win) - 1;
-}
-
 // Adds an arc weight to a connection sum held in 64 bits.  When every sum of
 // the level stays below 2^32 the add is a 32-bit atomic on the low word (the
 // high word stays zero): on sm_103a a 64-bit shared-memory atomic add costs
@@ -573,40 +553,7 @@ __global__ void __launch_bounds__(WPC * 32) k_propose_warp(LPArgs a, int32_t sub
     long long oc = 0;
     bool has_oc = false;
     Cand cd{-1, 0, 0};
-    // two-phase argmax (hash only the candidates at the largest connection)
-    // unless the node is overloaded (every fitting block is a candidate) or
-    // connections may not fit the 32-bit reductions
-    const bool fast = a.narrow && !ov;
-    bool reduced = false;
-    if (direct && fast) {
-      const int32_t own_l = (int32_t)(c.own - c.loff);
-      int64_t lmax = -1;
-      uint32_t elig = 0;                 // bit q: block lane + 32 q is a candidate
-      for (int32_t b = lane, q = 0; b < nl; b += 32, ++q) {
-        const int64_t conn = (int64_t)vals[b];
-        if (b == own_l) { oc = conn; has_oc = true; continue; }
-        if (conn == 0) continue;
-        if ((int64_t)a.W[c.loff + b] + c.cv > c.bound) continue;
-        elig |= 1u << q;
-        lmax = conn > lmax ? conn : lmax;
-      }
-      const int64_t M = (int64_t)warp_max_conn32(lmax) - 1;
-      if (M >= 0) {
-        bool has = false;
-        uint64_t hb = ~0ull;
-        int32_t Cb = -1;
-        for (int32_t b = lane, q = 0; b < nl; b += 32, ++q) {
-          if (!((elig >> q) & 1u) || (int64_t)vals[b] != M) continue;
-          const uint64_t h = mix64(c.hv ^ (uint64_t)(uint32_t)b);
-          if (!has || h < hb) { hb = h; Cb = b; has = true; }
-        }
-        const int wl = warp_min_hash_lane(has, hb);
-        cd = Cand{M, 0, __shfl_sync(0xffffffffu, Cb, wl)};
-      }
-      reduced = true;
-      __syncwarp();
-      for (int32_t b = lane; b < nl; b += 32) vals[b] = 0;
-    } else if (direct) {
+    if (direct) {
       const int32_t own_l = (int32_t)(c.own - c.loff);
       for (int32_t b = lane; b < nl; b += 32) {
         const int64_t conn = (int64_t)vals[b];
@@ -619,48 +566,6 @@ __global__ void __launch_bounds__(WPC * 32) k_propose_warp(LPArgs a, int32_t sub
       }
       __syncwarp();
       for (int32_t b = lane; b < nl; b += 32) vals[b] = 0;
-    } else if (fast) {
-      int32_t Wk[4], Bk[4];
-#pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        const bool q = ((created >> t) & 1u) && C[t] != c.own;
-        Wk[t] = q ? a.W[C[t]] : 0;
-        Bk[t] = cand_block(a, c, q, C[t]);
-      }
-      int64_t cn[4];
-      uint32_t elig = 0;
-      int64_t lmax = -1;
-#pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        cn[t] = -1;
-        if (!((created >> t) & 1u)) continue;
-        const int64_t conn = (int64_t)vals[slot[t]];
-        if (C[t] == c.own) { oc = conn; has_oc = true; continue; }
-        if ((int64_t)Wk[t] + c.cv > c.bound || Bk[t] != c.vb) continue;
-        cn[t] = conn;
-        elig |= 1u << t;
-        lmax = conn > lmax ? conn : lmax;
-      }
-      const int64_t M = (int64_t)warp_max_conn32(lmax) - 1;
-      if (M >= 0) {
-        bool has = false;
-        uint64_t hb = ~0ull;
-        int32_t Cb = -1;
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          if (!((elig >> t) & 1u) || cn[t] != M) continue;
-          const int32_t Cl = (int32_t)(C[t] - c.loff);
-          const uint64_t h = mix64(c.hv ^ (uint64_t)(uint32_t)Cl);
-          if (!has || h < hb) { hb = h; Cb = Cl; has = true; }
-        }
-        const int wl = warp_min_hash_lane(has, hb);
-        cd = Cand{M, 0, __shfl_sync(0xffffffffu, Cb, wl)};
-      }
-      reduced = true;
-      __syncwarp();
-#pragma unroll
-      for (int t = 0; t < 4; ++t)
-        if ((created >> t) & 1u) { keys[slot[t]] = -1; vals[slot[t]] = 0; }
     } else {
       int32_t Wk[4], Bk[4];
 #pragma unroll
@@ -694,7 +599,7 @@ __global__ void __launch_bounds__(WPC * 32) k_propose_warp(LPArgs a, int32_t sub
     }
     const unsigned om = __ballot_sync(0xffffffffu, has_oc);
     oc = om ? __shfl_sync(0xffffffffu, oc, __ffs(om) - 1) : 0;
-    if (!reduced) cd = warp_best(cd);
+    cd = warp_best(cd);
     if (lane == 0) write_prop(a, i, c, cd, oc, ov);
     __syncwarp();
   }
