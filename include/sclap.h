@@ -340,13 +340,17 @@ int sclap_cut_static(int64_t n, const int64_t* row_ptr, const int32_t* col,
  *   admit_ctas_per_sm  grid cap of the admission kernels (1..64)
  *   concurrent         1: the propose launches of a colour class run
  *                      concurrently on side streams; 0: one after another
- * The setting is process-wide; defaults 16, 8, 8, 16, 1. ---- */
+ *   pdl                1: kernels that follow a kernel of the same stream in
+ *                      the host-driven round loop are launched as
+ *                      programmatic dependent launches; 0: plain launches
+ * The setting is process-wide; defaults 16, 8, 8, 16, 1, 1. ---- */
 typedef struct sclap_tuning {
   int32_t small_max_deg;
   int32_t small_ctas_per_sm;
   int32_t warp_ctas_per_sm;
   int32_t admit_ctas_per_sm;
   int32_t concurrent;
+  int32_t pdl;
 } sclap_tuning;
 void sclap_get_tuning(sclap_tuning* out);
 /* SCLAP_EINVAL for a value out of range (the setting is then unchanged). */

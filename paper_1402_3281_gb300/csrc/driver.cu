@@ -1482,6 +1482,7 @@ void sclap_get_tuning(sclap_tuning* out) {
   out->warp_ctas_per_sm = t.warp_ctas_per_sm;
   out->admit_ctas_per_sm = t.admit_ctas_per_sm;
   out->concurrent = t.concurrent;
+  out->pdl = t.pdl;
 }
 
 int sclap_set_tuning(const sclap_tuning* in) {
@@ -1490,7 +1491,7 @@ int sclap_set_tuning(const sclap_tuning* in) {
     if ((in->small_max_deg != 8 && in->small_max_deg != 16) || in->small_ctas_per_sm < 1 ||
         in->small_ctas_per_sm > 32 || in->warp_ctas_per_sm < 1 || in->warp_ctas_per_sm > 32 ||
         in->admit_ctas_per_sm < 1 || in->admit_ctas_per_sm > 64 || in->concurrent < 0 ||
-        in->concurrent > 1)
+        in->concurrent > 1 || in->pdl < 0 || in->pdl > 1)
       throw Error(SCLAP_EINVAL, "tuning value out of range");
     Tuning t;
     t.small_max_deg = in->small_max_deg;
@@ -1498,6 +1499,7 @@ int sclap_set_tuning(const sclap_tuning* in) {
     t.warp_ctas_per_sm = in->warp_ctas_per_sm;
     t.admit_ctas_per_sm = in->admit_ctas_per_sm;
     t.concurrent = in->concurrent;
+    t.pdl = in->pdl;
     tuning_set(t);
   });
 }
@@ -1540,6 +1542,7 @@ int sclap_autotune(int32_t count, sclap_graph* graphs, const sclap_config* cfg,
           {&Tuning::warp_ctas_per_sm, {4, 8, 16}},
           {&Tuning::admit_ctas_per_sm, {8, 16, 32}},
           {&Tuning::concurrent, {1, 0}},
+          {&Tuning::pdl, {1, 0}},
       };
       for (const Param& p : params) {
         for (int32_t v : p.vals) {

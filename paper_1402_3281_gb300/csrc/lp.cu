@@ -160,8 +160,18 @@ __device__ __forceinline__ void write_prop(const LPArgs& a, int64_t i, const Nod
 // ------------------------------------------------------------- round control
 __global__ void k_round_begin(LPArgs a, int32_t nslots, int32_t phase,
                               const uint64_t* seed, const int32_t* level, int32_t raw_key) {
+  griddep_wait();
   const int32_t r = a.rnd[0];
-  if (blockIdx.x == 0 && threadIdx.x == 0) a.live[0] = 0;
+  if (blockIdx.x == 0) {                 // per-round counters of the bucketing
+    for (int j = threadIdx.x; j < a.S * NB; j += blockDim.x) {
+      a.bcnt[j] = 0;
+      a.karcs[j] = 0;
+    }
+    if (threadIdx.x == 0) {
+      a.live[0] = 0;
+      a.flags[0] = 0;
+    }
+  }
   for (int32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < nslots;
        s += gridDim.x * blockDim.x) {
     if (a.done[s]) continue;
@@ -177,6 +187,7 @@ __global__ void k_round_begin(LPArgs a, int32_t nslots, int32_t phase,
 }
 
 __global__ void k_round_end(LPArgs a, int32_t nslots) {
+  griddep_wait();
   int live = 0;
   for (int32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < nslots;
        s += gridDim.x * blockDim.x) {
@@ -194,6 +205,7 @@ __global__ void k_round_end(LPArgs a, int32_t nslots) {
 // round index and, inside a graph, sets the loop's condition.
 __global__ void k_round_cond(LPArgs a, int32_t nkeys, cudaGraphConditionalHandle h,
                              int32_t use_handle, int32_t* cont) {
+  griddep_wait();
   const int32_t r = a.rnd[0];
   const bool more = r + 1 < a.rounds_max && a.boff[nkeys] > 0 && a.live[0] > 0;
   a.rnd[0] = r + 1;
@@ -238,6 +250,7 @@ __device__ __forceinline__ int node_key(const LPArgs& a, const uint8_t* ac, int6
 // lanes of a warp meet only a few keys, and contended 64-bit shared atomics
 // serialise.
 __global__ void __launch_bounds__(BK_NT) k_bucket_count(LPArgs a, int64_t N) {
+  griddep_wait();
   __shared__ int sh_cnt[MAX_KEYS];
   __shared__ unsigned long long sh_arcs[MAX_KEYS];
   __shared__ int sh_ov;
@@ -277,6 +290,7 @@ __global__ void __launch_bounds__(BK_NT) k_bucket_count(LPArgs a, int64_t N) {
 }
 
 __global__ void __launch_bounds__(BK_NT) k_bucket_scatter(LPArgs a, int64_t N) {
+  griddep_wait();
   __shared__ int sh_cnt[MAX_KEYS];
   __shared__ int sh_base[MAX_KEYS];
   const int nkeys = a.S * NB;
@@ -306,6 +320,7 @@ __global__ void __launch_bounds__(BK_NT) k_bucket_scatter(LPArgs a, int64_t N) {
 }
 
 __global__ void k_bucket_offsets(LPArgs a, int nkeys) {
+  griddep_wait();
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     int64_t s = 0, arcs = 0;
     for (int j = 0; j < nkeys; ++j) {
@@ -409,6 +424,7 @@ __device__ __forceinline__ void propose_thread(const LPArgs& a, int64_t lbeg, in
 // needs (256 nodes per block), every non-empty bucket getting at least one;
 // every block computes the same split from the device offsets.
 __global__ void __launch_bounds__(256, 4) k_propose_small(LPArgs a, int32_t sub, int32_t nb) {
+  griddep_wait();
   const int64_t* bo = a.boff + sub * NB;
   int64_t c[3], need[3], tot = 0;
 #pragma unroll
@@ -496,6 +512,7 @@ constexpr int WPC = 8;                       // warps per CTA
 static_assert((1 << WLOG) == WCAP, "WCAP must be 2^WLOG");
 
 __global__ void __launch_bounds__(WPC * 32) k_propose_warp(LPArgs a, int32_t sub, int32_t b0) {
+  griddep_wait();
   int64_t lbeg, cnt;
   sub_range(a, sub, b0, 5, &lbeg, &cnt);    // buckets b0..4 are adjacent
   if (cnt == 0) return;
@@ -623,6 +640,7 @@ template <int NT, int SLOTS, bool GLOBAL>
 __global__ void __launch_bounds__(NT) k_propose_blk(LPArgs a, int32_t sub, int32_t bucket,
                                                     int32_t* gkeys, unsigned long long* gvals,
                                                     int32_t* glist, int64_t gcap) {
+  griddep_wait();
   int64_t lbeg, cnt;
   sub_range(a, sub, bucket, bucket + 1, &lbeg, &cnt);
   if (cnt == 0) return;
@@ -758,6 +776,11 @@ __global__ void __launch_bounds__(NT) k_propose_blk(LPArgs a, int32_t sub, int32
 
 // ------------------------------------------------------------- admission
 __global__ void k_resolve(LPArgs a, int32_t sub) {
+  griddep_wait();
+  if (blockIdx.x == 0 && threadIdx.x == 0) {   // segment counters of the target side
+    a.ctr[0] = 0;
+    a.ctr[1] = 0;
+  }
   int64_t lbeg, cnt;
   sub_range(a, sub, 0, NB, &lbeg, &cnt);
   for (int64_t li = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; li < cnt;
@@ -780,6 +803,11 @@ __global__ void k_resolve(LPArgs a, int32_t sub) {
 
 // Forced moves out of overloaded blocks (local search), grouped by source.
 __global__ void k_forced(LPArgs a, int32_t sub) {
+  griddep_wait();
+  if (blockIdx.x == 0 && threadIdx.x == 0) {   // segment counters of the source side
+    a.ctr[0] = 0;
+    a.ctr[1] = 0;
+  }
   if (a.flags[0] == 0) return;              // no listed node in an overloaded block
   int64_t lbeg, cnt;
   sub_range(a, sub, 0, NB, &lbeg, &cnt);
@@ -802,6 +830,7 @@ __global__ void k_forced(LPArgs a, int32_t sub) {
 // admit while the inclusive prefix <= bound - W[t]; source side, admit while
 // the exclusive prefix <= W[src] - bound - 1.
 __global__ void k_ovf_alloc(LPArgs a, int32_t sub, int32_t source) {
+  griddep_wait();
   if (source && a.flags[0] == 0) return;    // source side idle this round
   int64_t lbeg, cnt;
   sub_range(a, sub, 0, NB, &lbeg, &cnt);
@@ -823,6 +852,7 @@ __global__ void k_ovf_alloc(LPArgs a, int32_t sub, int32_t source) {
 }
 
 __global__ void k_ovf_scatter(LPArgs a, int32_t sub, int32_t source) {
+  griddep_wait();
   if (source && a.flags[0] == 0) return;
   int64_t lbeg, cnt;
   sub_range(a, sub, 0, NB, &lbeg, &cnt);
@@ -885,6 +915,7 @@ __device__ __forceinline__ void select_rank_small(const LPArgs& a, int n, int64_
 }
 
 __global__ void __launch_bounds__(SEL_NT) k_ovf_select(LPArgs a, int32_t source) {
+  griddep_wait();
   __shared__ uint64_t sk[SEL_SMALL];
   __shared__ int32_t sv[SEL_SMALL];
   __shared__ int32_t sw[SEL_SMALL];
@@ -1147,6 +1178,7 @@ __device__ __forceinline__ void apply_delta(int32_t* hk, int32_t* hv, wgt_t* W, 
 }
 
 __global__ void __launch_bounds__(256) k_apply(LPArgs a, int32_t sub) {
+  griddep_wait();
   int64_t lbeg, cnt;
   sub_range(a, sub, 0, NB, &lbeg, &cnt);
   uint8_t* const an = act_next(a);
@@ -1471,14 +1503,14 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, wgt_t*
   // ---- one round, as launches on s (shared by both drivers) ----------------
   // (every operation of a round goes to the stream passed in: the caller's
   // stream when driven directly, the capture stream when building the graph)
-  auto head = [&](cudaStream_t s) {
-    k_round_begin<<<nsl_grid, 128, 0, s>>>(a, sp.nslots, run.phase, sp.seed, sp.level, raw); SCLAP_NOTE_LAUNCH("k_round_begin");
-    SCLAP_CUDA(cudaMemsetAsync(bcnt.p, 0, nkeys * sizeof(int32_t), s));
-    SCLAP_CUDA(cudaMemsetAsync(karcs.p, 0, nkeys * sizeof(int64_t), s));
-    SCLAP_CUDA(cudaMemsetAsync(flags.p, 0, sizeof(int32_t), s));
-    k_bucket_count<<<bgrid, BK_NT, 0, s>>>(a, N); SCLAP_NOTE_LAUNCH("k_bucket_count");
-    k_bucket_offsets<<<1, 32, 0, s>>>(a, nkeys); SCLAP_NOTE_LAUNCH("k_bucket_offsets");
-    k_bucket_scatter<<<bgrid, BK_NT, 0, s>>>(a, N); SCLAP_NOTE_LAUNCH("k_bucket_scatter");
+  // pdl: programmatic launches for kernels that follow a kernel of the same
+  // stream (never for the first kernel after an event, a copy or a wait)
+  auto head = [&](cudaStream_t s, bool pdl) {
+    launch_k(false, k_round_begin, nsl_grid, 128, 0, s, a, sp.nslots, run.phase, sp.seed,
+             sp.level, raw); SCLAP_NOTE_LAUNCH("k_round_begin");
+    launch_k(pdl, k_bucket_count, bgrid, BK_NT, 0, s, a, N); SCLAP_NOTE_LAUNCH("k_bucket_count");
+    launch_k(pdl, k_bucket_offsets, 1, 32, 0, s, a, nkeys); SCLAP_NOTE_LAUNCH("k_bucket_offsets");
+    launch_k(pdl, k_bucket_scatter, bgrid, BK_NT, 0, s, a, N); SCLAP_NOTE_LAUNCH("k_bucket_scatter");
     SCLAP_LAUNCH_CHECK();
   };
   // Per-launch profiling of the direct driver (host offsets known).
@@ -1493,7 +1525,7 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, wgt_t*
   // launches overlap (serial when the timeline profiler is on).  With host
   // offsets (direct driver) empty launches are skipped and, when profiling,
   // each launch is timed and its nodes and arcs tallied by family.
-  auto propose = [&](cudaStream_t s, int sub, bool fork, const int64_t* ho) {
+  auto propose = [&](cudaStream_t s, int sub, bool fork, const int64_t* ho, bool pdl) {
     cudaEvent_t ev_fork = nullptr;
     if (fork) {
       ev_fork = sync_event_get();
@@ -1508,19 +1540,24 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, wgt_t*
       joined[nside++] = ss;
       return ss;
     };
-    // buckets [b0, b1) of this colour class in one launch of family fam
+    // buckets [b0, b1) of this colour class in one launch of family fam; a
+    // launch follows a kernel of its stream only when the launches are
+    // serial, it is not the first, and no per-launch events are recorded
+    int nlaunched = 0;
     auto launch = [&](int b0, int b1, int fam, auto&& fn) {
       if (ho && ho[sub * NB + b1] == ho[sub * NB + b0]) return;
       cudaStream_t ls = lane();
       Timed tm{fam, nullptr, nullptr};
-      if (prof && ho) {
+      const bool timed_launch = prof && ho;
+      if (timed_launch) {
         tm.a = event_from_pool();
         tm.b = event_from_pool();
         SCLAP_CUDA(cudaEventRecord(tm.a, ls));
         pn[fam] += ho[sub * NB + b1] - ho[sub * NB + b0];
         for (int q = b0; q < b1; ++q) pa[fam] += hkarcs[sub * NB + q];
       }
-      fn(ls);
+      fn(ls, pdl && !fork && !timed_launch && nlaunched > 0);
+      ++nlaunched;
       if (prof && ho) {
         SCLAP_CUDA(cudaEventRecord(tm.b, ls));
         timed.push_back(tm);
@@ -1538,23 +1575,25 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, wgt_t*
       return grid_for(ho[sub * NB + b1] - ho[sub * NB + b0], per, cap);
     };
     // family 0 first: it holds most nodes, and the first launch gets the SMs
-    launch(0, nsb, 0, [&](cudaStream_t ls) {
-      k_propose_small<<<grid(0, nsb, 256, grid_small), 256, 0, ls>>>(a, sub, nsb); SCLAP_NOTE_LAUNCH("k_propose_small");
+    int32_t* const no_i = nullptr;
+    unsigned long long* const no_u = nullptr;
+    launch(0, nsb, 0, [&](cudaStream_t ls, bool p) {
+      launch_k(p, k_propose_small, grid(0, nsb, 256, grid_small), 256, 0, ls, a, sub, nsb); SCLAP_NOTE_LAUNCH("k_propose_small");
     });
-    if (need[3]) launch(nsb, 5, 1, [&](cudaStream_t ls) {
-      k_propose_warp<<<grid(nsb, 5, WPC, grid_warp), WPC * 32, 0, ls>>>(a, sub, nsb); SCLAP_NOTE_LAUNCH("k_propose_warp");
+    if (need[3]) launch(nsb, 5, 1, [&](cudaStream_t ls, bool p) {
+      launch_k(p, k_propose_warp, grid(nsb, 5, WPC, grid_warp), WPC * 32, 0, ls, a, sub, nsb); SCLAP_NOTE_LAUNCH("k_propose_warp");
     });
-    if (need[5]) launch(5, 6, 1, [&](cudaStream_t ls) {
-      k_propose_blk<128, B5_SLOTS, false><<<grid(5, 6, 1, grid_b5), 128, smem5, ls>>>(a, sub, 5, nullptr, nullptr, nullptr, 0); SCLAP_NOTE_LAUNCH("k_propose_blk128");
+    if (need[5]) launch(5, 6, 1, [&](cudaStream_t ls, bool p) {
+      launch_k(p, k_propose_blk<128, B5_SLOTS, false>, grid(5, 6, 1, grid_b5), 128, smem5, ls, a, sub, 5, no_i, no_u, no_i, (int64_t)0); SCLAP_NOTE_LAUNCH("k_propose_blk128");
     });
-    if (need[6]) launch(6, 7, 2, [&](cudaStream_t ls) {
-      k_propose_blk<256, B6_SLOTS, false><<<grid(6, 7, 1, grid_b6), 256, smem6, ls>>>(a, sub, 6, nullptr, nullptr, nullptr, 0); SCLAP_NOTE_LAUNCH("k_propose_blk256");
+    if (need[6]) launch(6, 7, 2, [&](cudaStream_t ls, bool p) {
+      launch_k(p, k_propose_blk<256, B6_SLOTS, false>, grid(6, 7, 1, grid_b6), 256, smem6, ls, a, sub, 6, no_i, no_u, no_i, (int64_t)0); SCLAP_NOTE_LAUNCH("k_propose_blk256");
     });
-    if (need[7]) launch(7, 8, 2, [&](cudaStream_t ls) {
-      k_propose_blk<512, B7_SLOTS, false><<<grid(7, 8, 1, grid_b7), 512, smem7, ls>>>(a, sub, 7, nullptr, nullptr, nullptr, 0); SCLAP_NOTE_LAUNCH("k_propose_blk512");
+    if (need[7]) launch(7, 8, 2, [&](cudaStream_t ls, bool p) {
+      launch_k(p, k_propose_blk<512, B7_SLOTS, false>, grid(7, 8, 1, grid_b7), 512, smem7, ls, a, sub, 7, no_i, no_u, no_i, (int64_t)0); SCLAP_NOTE_LAUNCH("k_propose_blk512");
     });
-    if (need[8]) launch(8, 9, 3, [&](cudaStream_t ls) {
-      k_propose_blk<512, 1, true><<<(unsigned)gblocks, 512, 0, ls>>>(a, sub, 8, gkeys.p, gvals.p, glist.p, gcap); SCLAP_NOTE_LAUNCH("k_propose_hub");
+    if (need[8]) launch(8, 9, 3, [&](cudaStream_t ls, bool p) {
+      launch_k(p, k_propose_blk<512, 1, true>, (unsigned)gblocks, 512, 0, ls, a, sub, 8, gkeys.p, gvals.p, glist.p, gcap); SCLAP_NOTE_LAUNCH("k_propose_hub");
     });
     if (fork) {
       for (int j = 0; j < nside; ++j) {
@@ -1570,26 +1609,26 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, wgt_t*
   // Admission and application of colour class `sub`; the source-side chain
   // (local search) is skipped by the host when it knows no listed node sits
   // in an overloaded block, else its kernels check that on the device.
-  auto admit = [&](cudaStream_t s, int sub, bool source_chain, int64_t cnt) {
+  // admission: the segment counters are cleared by k_resolve (target side)
+  // and k_forced (source side), so the chain is kernels only
+  auto admit = [&](cudaStream_t s, int sub, bool source_chain, int64_t cnt, bool pdl) {
     const unsigned grid_adm = cnt < 0 ? grid_adm_max : grid_for(cnt, 256, grid_adm_max);
-    k_resolve<<<grid_adm, 256, 0, s>>>(a, sub); SCLAP_NOTE_LAUNCH("k_resolve");
-    SCLAP_CUDA(cudaMemsetAsync(ctr.p, 0, 2 * sizeof(int64_t), s));
-    k_ovf_alloc<<<grid_adm, 256, 0, s>>>(a, sub, 0); SCLAP_NOTE_LAUNCH("k_ovf_alloc");
-    k_ovf_scatter<<<grid_adm, 256, 0, s>>>(a, sub, 0); SCLAP_NOTE_LAUNCH("k_ovf_scatter");
-    k_ovf_select<<<grid_sel, SEL_NT, 0, s>>>(a, 0); SCLAP_NOTE_LAUNCH("k_ovf_select");
+    launch_k(false, k_resolve, grid_adm, 256, 0, s, a, sub); SCLAP_NOTE_LAUNCH("k_resolve");
+    launch_k(pdl, k_ovf_alloc, grid_adm, 256, 0, s, a, sub, 0); SCLAP_NOTE_LAUNCH("k_ovf_alloc");
+    launch_k(pdl, k_ovf_scatter, grid_adm, 256, 0, s, a, sub, 0); SCLAP_NOTE_LAUNCH("k_ovf_scatter");
+    launch_k(pdl, k_ovf_select, grid_sel, SEL_NT, 0, s, a, 0); SCLAP_NOTE_LAUNCH("k_ovf_select");
     if (source_chain) {
-      k_forced<<<grid_adm, 256, 0, s>>>(a, sub); SCLAP_NOTE_LAUNCH("k_forced");
-      SCLAP_CUDA(cudaMemsetAsync(ctr.p, 0, 2 * sizeof(int64_t), s));
-      k_ovf_alloc<<<grid_adm, 256, 0, s>>>(a, sub, 1); SCLAP_NOTE_LAUNCH("k_ovf_alloc");
-      k_ovf_scatter<<<grid_adm, 256, 0, s>>>(a, sub, 1); SCLAP_NOTE_LAUNCH("k_ovf_scatter");
-      k_ovf_select<<<grid_sel, SEL_NT, 0, s>>>(a, 1); SCLAP_NOTE_LAUNCH("k_ovf_select");
+      launch_k(pdl, k_forced, grid_adm, 256, 0, s, a, sub); SCLAP_NOTE_LAUNCH("k_forced");
+      launch_k(pdl, k_ovf_alloc, grid_adm, 256, 0, s, a, sub, 1); SCLAP_NOTE_LAUNCH("k_ovf_alloc");
+      launch_k(pdl, k_ovf_scatter, grid_adm, 256, 0, s, a, sub, 1); SCLAP_NOTE_LAUNCH("k_ovf_scatter");
+      launch_k(pdl, k_ovf_select, grid_sel, SEL_NT, 0, s, a, 1); SCLAP_NOTE_LAUNCH("k_ovf_select");
     }
-    k_apply<<<grid_adm, 256, 0, s>>>(a, sub); SCLAP_NOTE_LAUNCH("k_apply");
+    launch_k(pdl, k_apply, grid_adm, 256, 0, s, a, sub); SCLAP_NOTE_LAUNCH("k_apply");
     SCLAP_LAUNCH_CHECK();
   };
-  auto tail = [&](cudaStream_t s, cudaGraphConditionalHandle h, bool in_graph) {
-    k_round_end<<<nsl_grid, 128, 0, s>>>(a, sp.nslots); SCLAP_NOTE_LAUNCH("k_round_end");
-    k_round_cond<<<1, 1, 0, s>>>(a, nkeys, h, in_graph ? 1 : 0, d_cont); SCLAP_NOTE_LAUNCH("k_round_cond");
+  auto tail = [&](cudaStream_t s, cudaGraphConditionalHandle h, bool in_graph, bool pdl) {
+    launch_k(false, k_round_end, nsl_grid, 128, 0, s, a, sp.nslots); SCLAP_NOTE_LAUNCH("k_round_end");
+    launch_k(pdl, k_round_cond, 1, 1, 0, s, a, nkeys, h, in_graph ? 1 : 0, d_cont); SCLAP_NOTE_LAUNCH("k_round_cond");
     SCLAP_LAUNCH_CHECK();
   };
 
@@ -1632,12 +1671,12 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, wgt_t*
       SCLAP_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0,
                                                cudaStreamCaptureModeThreadLocal));
       try {
-        head(cs);
+        head(cs, false);
         for (int sub = 0; sub < S; ++sub) {
-          propose(cs, sub, tu.concurrent != 0, nullptr);
-          admit(cs, sub, refine, -1);
+          propose(cs, sub, tu.concurrent != 0, nullptr, false);
+          admit(cs, sub, refine, -1, false);
         }
-        tail(cs, h, true);
+        tail(cs, h, true, false);
       } catch (...) {
         cudaGraph_t junk = nullptr;
         cudaStreamEndCapture(cs, &junk);
@@ -1664,8 +1703,10 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, wgt_t*
     // ---- direct driver: one round at a time; the host reads the bucket
     // offsets after bucketing (one wait per round), skips empty launches and
     // colour classes, and stops at the first round that lists no node
+    // the per-kernel timeline records an event after every launch
+    const bool pdl = tu.pdl != 0 && !timeline;
     for (int r = 0; r < run.rounds; ++r) {
-      head(s);
+      head(s, pdl);
       int32_t hflags = 0;
       SCLAP_CUDA(cudaMemcpyAsync(hoff.data(), boff.p, (nkeys + 1) * sizeof(int64_t),
                                  cudaMemcpyDeviceToHost, s));
@@ -1674,7 +1715,7 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, wgt_t*
       SCLAP_CUDA(cudaMemcpyAsync(&hflags, flags.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
       stream_sync(s);
       if (hoff[nkeys] == 0) {
-        tail(s, 0, false);
+        tail(s, 0, false, pdl);
         break;
       }
       for (int sub = 0; sub < S; ++sub) {
@@ -1686,7 +1727,7 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, wgt_t*
           phase.b = event_from_pool();
           SCLAP_CUDA(cudaEventRecord(phase.a, s));
         }
-        propose(s, sub, !timeline && tu.concurrent, hoff.data());
+        propose(s, sub, !timeline && tu.concurrent, hoff.data(), pdl);
         if (prof) {
           SCLAP_CUDA(cudaEventRecord(phase.b, s));
           timed.push_back(phase);
@@ -1695,10 +1736,10 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, wgt_t*
           precs.push_back(PhaseRec{run.phase, r, sub, cnt, sub_arcs, phase.a, phase.b,
                                    event_from_pool()});
         }
-        admit(s, sub, refine && hflags != 0, cnt);
+        admit(s, sub, refine && hflags != 0, cnt, pdl);
         if (prof) SCLAP_CUDA(cudaEventRecord(precs.back().c, s));
       }
-      tail(s, 0, false);
+      tail(s, 0, false, pdl);
     }
   }
   int32_t hr = 0;

@@ -13,7 +13,7 @@ import oracle as O
 import paper_1402_3281_gb300 as P
 
 DEFAULT = dict(small_max_deg=16, small_ctas_per_sm=8, warp_ctas_per_sm=8, admit_ctas_per_sm=16,
-               concurrent=1)
+               concurrent=1, pdl=1)
 
 
 @pytest.fixture
@@ -31,7 +31,7 @@ def test_default_tuning(restore_tuning):
 @pytest.mark.parametrize("field,bad", [("small_max_deg", 12), ("small_max_deg", 32),
                                        ("small_ctas_per_sm", 0), ("warp_ctas_per_sm", 33),
                                        ("admit_ctas_per_sm", 65), ("concurrent", 2),
-                                       ("concurrent", -1)])
+                                       ("concurrent", -1), ("pdl", 2)])
 def test_out_of_range_values_are_rejected_and_leave_the_setting(restore_tuning, field, bad):
     P.set_tuning(**DEFAULT)
     with pytest.raises(P.SclapError) as e:
@@ -42,9 +42,9 @@ def test_out_of_range_values_are_rejected_and_leave_the_setting(restore_tuning, 
 
 def test_set_tuning_round_trip(restore_tuning):
     t = P.set_tuning(small_max_deg=8, small_ctas_per_sm=3, warp_ctas_per_sm=32,
-                     admit_ctas_per_sm=1, concurrent=0)
+                     admit_ctas_per_sm=1, concurrent=0, pdl=0)
     assert t.to_dict() == dict(small_max_deg=8, small_ctas_per_sm=3, warp_ctas_per_sm=32,
-                               admit_ctas_per_sm=1, concurrent=0)
+                               admit_ctas_per_sm=1, concurrent=0, pdl=0)
 
 
 # ------------------------------------------------------------------ GPU
@@ -63,6 +63,8 @@ SETTINGS = [
     dict(small_ctas_per_sm=1, warp_ctas_per_sm=1, admit_ctas_per_sm=1),
     dict(small_ctas_per_sm=32, warp_ctas_per_sm=32, admit_ctas_per_sm=64),
     dict(concurrent=0),
+    dict(pdl=0),
+    dict(concurrent=0, pdl=0),
     dict(small_max_deg=8, small_ctas_per_sm=2, warp_ctas_per_sm=3, admit_ctas_per_sm=5,
          concurrent=0),
 ]
