@@ -467,8 +467,11 @@ struct GGGArgs {
   int64_t* wfA;            // scratch [sum k]
   int32_t* wforder;        // scratch [sum k]
   int32_t nslots;
+  const int32_t* order;    // trial slots in the order they are taken (set by ggg_trials)
+  int32_t* next;           // queue position (set by ggg_trials)
 };
-void ggg_trials(const GGGArgs& a, cudaStream_t s);
+// noff: host copy of the trial slot node offsets [nslots + 1].
+void ggg_trials(const GGGArgs& a, const std::vector<int64_t>& noff, cudaStream_t s);
 // cut2[slot] += twice the cut of each slot (arcs counted from both ends).
 void slot_cut(const LevelView& lv, const int32_t* label, int64_t* cut2, cudaStream_t s);
 struct SelectTask {            // choose the best trial of one graph, copy it out

@@ -7,6 +7,8 @@
 // nodes connected to it, in node-id order, while it stays <= ceil(c(V)/k)),
 // water-filling of the leftovers, then LP local search (the lp.cu kernels on
 // the whole trial batch).  The best trial by (overload, cut, trial) is kept.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace sclap {
@@ -77,8 +79,17 @@ __global__ void __launch_bounds__(GNT) k_ggg(GGGArgs a) {
   __shared__ int32_t nstep_sh, seed_sh, nfront_sh;
   // a chunk of step nodes: row start, first and one-past-last arc offset
   __shared__ int64_t st_rs[GNT], st_ex[GNT], st_in[GNT];
+  __shared__ int32_t next_sh;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  for (int32_t s = blockIdx.x; s < a.nslots; s += gridDim.x) {
+  // trials are taken from a queue ordered by size, largest first, so the
+  // long trials of the batch start first and on different CTAs
+  for (;;) {
+    if (tid == 0) next_sh = atomicAdd(a.next, 1);
+    __syncthreads();
+    const int32_t qi = next_sh;
+    __syncthreads();
+    if (qi >= a.nslots) break;
+    const int32_t s = a.order[qi];
     const int64_t base = a.noff[s], n = a.noff[s + 1] - base;
     const int32_t k = a.nlab[s];
     const int64_t bo = a.boff[s], avg = a.avg[s];
@@ -565,9 +576,25 @@ void ip_replicate(const std::vector<CopyTask>& tasks, int64_t* row_ptr, int32_t*
   SCLAP_LAUNCH_CHECK();
 }
 
-void ggg_trials(const GGGArgs& a, cudaStream_t s) {
-  if (a.nslots <= 0) return;
-  k_ggg<<<(unsigned)std::min<int64_t>(a.nslots, (int64_t)num_sms() * 8), GNT, 0, s>>>(a); SCLAP_NOTE_LAUNCH("k_ggg");
+void ggg_trials(const GGGArgs& a_in, const std::vector<int64_t>& noff, cudaStream_t s) {
+  if (a_in.nslots <= 0) return;
+  const int32_t S = a_in.nslots;
+  // longest processing time first: trial slots by node count, descending
+  std::vector<int32_t> order(S);
+  for (int32_t i = 0; i < S; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
+    return noff[x + 1] - noff[x] > noff[y + 1] - noff[y];
+  });
+  DevBuf<int32_t> d_order(S, s), d_next(1, s);
+  d_order.upload(order);
+  d_next.zero();
+  GGGArgs a = a_in;
+  a.order = d_order.p;
+  a.next = d_next.p;
+  int per_sm = 0;
+  SCLAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ggg, GNT, 0));
+  const int64_t resident = (int64_t)num_sms() * std::max(per_sm, 1);
+  k_ggg<<<(unsigned)std::min<int64_t>(S, resident), GNT, 0, s>>>(a); SCLAP_NOTE_LAUNCH("k_ggg");
   SCLAP_LAUNCH_CHECK();
 }
 
