@@ -14,7 +14,9 @@
 namespace sclap {
 namespace {
 
-constexpr int GNT = 512;
+// CTA sizes of the greedy-growing kernel: 128 threads when a batch has many
+// trials (more trials in flight), 512 when it has few (wider steps).
+constexpr int GNT_MANY = 128, GNT_FEW = 512;
 
 __global__ void k_replicate(const CopyTask* __restrict__ tasks, int64_t* __restrict__ row_ptr,
                             int32_t* __restrict__ col, int32_t* __restrict__ ew,
@@ -40,6 +42,7 @@ __global__ void k_replicate(const CopyTask* __restrict__ tasks, int64_t* __restr
 }
 
 // Block-wide inclusive scan of an int64 (all GNT threads call it).
+template <int GNT>
 __device__ int64_t block_incl_scan(int64_t x, int64_t* sh, int64_t* total) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int o = 1; o < 32; o <<= 1) {
@@ -65,12 +68,14 @@ __device__ int64_t block_incl_scan(int64_t x, int64_t* sh, int64_t* total) {
   return x;
 }
 
+template <int GNT>
 __device__ int64_t block_sum(int64_t x, int64_t* sh) {
   int64_t tot;
-  block_incl_scan(x, sh, &tot);
+  block_incl_scan<GNT>(x, sh, &tot);
   return tot;
 }
 
+template <int GNT>
 __global__ void __launch_bounds__(GNT) k_ggg(GGGArgs a) {
   __shared__ int64_t sh[33];
   __shared__ uint64_t shh[GNT / 32];
@@ -161,7 +166,7 @@ __global__ void __launch_bounds__(GNT) k_ggg(GGGArgs a) {
             d = a.row_ptr[u + 1] - rs;
           }
           int64_t tot;
-          const int64_t incl = block_incl_scan(d, sh, &tot);
+          const int64_t incl = block_incl_scan<GNT>(d, sh, &tot);
           st_rs[tid] = rs;
           st_ex[tid] = incl - d;
           st_in[tid] = incl;
@@ -191,7 +196,7 @@ __global__ void __launch_bounds__(GNT) k_ggg(GGGArgs a) {
         const int64_t Wj = Wj_sh;
         if (Wj >= avg) break;
         if (!ordered) {
-          const int64_t fsum = block_sum(fw, sh);
+          const int64_t fsum = block_sum<GNT>(fw, sh);
           const int32_t nf = nfront_sh;
           if (Wj + fsum <= avg) {
             // all of them fit: they are the next step, in any order
@@ -217,7 +222,7 @@ __global__ void __launch_bounds__(GNT) k_ggg(GGGArgs a) {
           const int64_t gv = base + v;
           if (a.label[gv] < 0 && a.conn[gv] > 0) cw_all += a.nw[gv];
         }
-        const bool all_fit = Wj + block_sum(cw_all, sh) <= avg;
+        const bool all_fit = Wj + block_sum<GNT>(cw_all, sh) <= avg;
         int64_t carry_w = 0;
         int32_t carry_c = 0;
         for (int64_t v0 = 0; v0 < n; v0 += GNT) {
@@ -230,10 +235,10 @@ __global__ void __launch_bounds__(GNT) k_ggg(GGGArgs a) {
             wt = cand ? a.nw[gv] : 0;
           }
           int64_t tw = 0, iw = wt;
-          if (!all_fit) iw = block_incl_scan(wt, sh, &tw);
+          if (!all_fit) iw = block_incl_scan<GNT>(wt, sh, &tw);
           const bool adm = cand && (all_fit || Wj + carry_w + iw <= avg);
           int64_t tc;
-          const int64_t ic = block_incl_scan(adm ? 1 : 0, sh, &tc);
+          const int64_t ic = block_incl_scan<GNT>(adm ? 1 : 0, sh, &tc);
           if (adm) {
             stp[carry_c + ic - 1] = (int32_t)(base + v);
             atomicAdd(ull(&accw_sh), (unsigned long long)wt);
@@ -260,7 +265,7 @@ __global__ void __launch_bounds__(GNT) k_ggg(GGGArgs a) {
     int64_t r = 0;
     for (int64_t v = tid; v < n; v += GNT)
       if (a.label[base + v] < 0) r += a.nw[base + v];
-    const int64_t R = block_sum(r, sh);
+    const int64_t R = block_sum<GNT>(r, sh);
     if (R > 0) {
       if (tid == 0) {
         int64_t lo = a.W[bo], hi = a.W[bo];
@@ -303,7 +308,7 @@ __global__ void __launch_bounds__(GNT) k_ggg(GGGArgs a) {
         const bool left = v < n && a.label[base + v] < 0;
         const int64_t wt = left ? a.nw[base + v] : 0;
         int64_t tw;
-        const int64_t iw = block_incl_scan(wt, sh, &tw);
+        const int64_t iw = block_incl_scan<GNT>(wt, sh, &tw);
         if (left) {
           const int64_t p = carry + iw - wt;
           int32_t lo = 0, hi = k - 1;               // last j with A[j] <= p
@@ -591,10 +596,19 @@ void ggg_trials(const GGGArgs& a_in, const std::vector<int64_t>& noff, cudaStrea
   GGGArgs a = a_in;
   a.order = d_order.p;
   a.next = d_next.p;
-  int per_sm = 0;
-  SCLAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ggg, GNT, 0));
-  const int64_t resident = (int64_t)num_sms() * std::max(per_sm, 1);
-  k_ggg<<<(unsigned)std::min<int64_t>(S, resident), GNT, 0, s>>>(a); SCLAP_NOTE_LAUNCH("k_ggg");
+  // a trial is a chain of small steps, so the kernel is bound by how many
+  // trials are in flight: small CTAs when the trials outnumber the resident
+  // 512-thread CTAs
+  int few_per_sm = 0, many_per_sm = 0;
+  SCLAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&few_per_sm, k_ggg<GNT_FEW>, GNT_FEW, 0));
+  SCLAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&many_per_sm, k_ggg<GNT_MANY>, GNT_MANY, 0));
+  const int64_t few_resident = (int64_t)num_sms() * std::max(few_per_sm, 1);
+  const int64_t many_resident = (int64_t)num_sms() * std::max(many_per_sm, 1);
+  if (S > few_resident) {
+    k_ggg<GNT_MANY><<<(unsigned)std::min<int64_t>(S, many_resident), GNT_MANY, 0, s>>>(a); SCLAP_NOTE_LAUNCH("k_ggg");
+  } else {
+    k_ggg<GNT_FEW><<<(unsigned)std::min<int64_t>(S, few_resident), GNT_FEW, 0, s>>>(a); SCLAP_NOTE_LAUNCH("k_ggg");
+  }
   SCLAP_LAUNCH_CHECK();
 }
 
