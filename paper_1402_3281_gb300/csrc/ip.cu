@@ -108,8 +108,10 @@ __global__ void __launch_bounds__(GNT) k_ggg(GGGArgs a) {
       const uint64_t skey = hkey(tkey, PH_GGG, (uint64_t)lvl, (uint64_t)j);
       uint64_t bh = ~0ull;
       int32_t bv = -1;
+      // (the same pass clears the connections left by the previous block)
       for (int64_t v = tid; v < n; v += GNT) {
         const int64_t gv = base + v;
+        a.conn[gv] = 0;
         if (a.label[gv] >= 0 || a.row_ptr[gv + 1] == a.row_ptr[gv]) continue;
         const uint64_t h = mix64(skey ^ (uint64_t)v);
         if (bv < 0 || h < bh) { bh = h; bv = (int32_t)v; }
@@ -133,7 +135,6 @@ __global__ void __launch_bounds__(GNT) k_ggg(GGGArgs a) {
       __syncthreads();
       const int32_t seed = seed_sh;
       if (seed < 0) break;
-      for (int64_t v = tid; v < n; v += GNT) a.conn[base + v] = 0;
       // step nodes and newly reached nodes: two scratch lists that swap roles
       int32_t* stp = a.step + base;
       int32_t* frt = a.front + base;
