@@ -92,7 +92,7 @@ void event_to_pool(cudaEvent_t e);
 // with); its first statement is griddep_wait(), which returns once that
 // kernel has completed and its writes are visible (and at once for a normal
 // launch).  Only for a kernel whose preceding operation in the stream is a
-// kernel launch, outside graph capture.
+// kernel launch (under stream capture it becomes a programmatic edge).
 __device__ __forceinline__ void griddep_wait() {
   asm volatile("griddepcontrol.wait;" ::: "memory");
 }

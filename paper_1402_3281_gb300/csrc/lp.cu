@@ -1671,12 +1671,14 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, wgt_t*
       SCLAP_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0,
                                                cudaStreamCaptureModeThreadLocal));
       try {
-        head(cs, false);
+        // programmatic launches are captured as programmatic edges
+        const bool pdl = tu.pdl != 0;
+        head(cs, pdl);
         for (int sub = 0; sub < S; ++sub) {
-          propose(cs, sub, tu.concurrent != 0, nullptr, false);
-          admit(cs, sub, refine, -1, false);
+          propose(cs, sub, tu.concurrent != 0, nullptr, pdl);
+          admit(cs, sub, refine, -1, pdl);
         }
-        tail(cs, h, true, false);
+        tail(cs, h, true, pdl);
       } catch (...) {
         cudaGraph_t junk = nullptr;
         cudaStreamEndCapture(cs, &junk);
