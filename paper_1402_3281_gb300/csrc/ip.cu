@@ -17,6 +17,7 @@ namespace {
 // CTA sizes of the greedy-growing kernel: 128 threads when a batch has many
 // trials (more trials in flight), 512 when it has few (wider steps).
 constexpr int GNT_MANY = 128, GNT_FEW = 512;
+constexpr int GPER = 8;   // consecutive nodes per thread in the greedy-growing scans
 
 __global__ void k_replicate(const CopyTask* __restrict__ tasks, int64_t* __restrict__ row_ptr,
                             int32_t* __restrict__ col, int32_t* __restrict__ ew,
@@ -109,12 +110,17 @@ __global__ void __launch_bounds__(GNT) k_ggg(GGGArgs a) {
       uint64_t bh = ~0ull;
       int32_t bv = -1;
       // (the same pass clears the connections left by the previous block)
-      for (int64_t v = tid; v < n; v += GNT) {
-        const int64_t gv = base + v;
-        a.conn[gv] = 0;
-        if (a.label[gv] >= 0 || a.row_ptr[gv + 1] == a.row_ptr[gv]) continue;
-        const uint64_t h = mix64(skey ^ (uint64_t)v);
-        if (bv < 0 || h < bh) { bh = h; bv = (int32_t)v; }
+      for (int64_t v0 = (int64_t)tid * GPER; v0 < n; v0 += (int64_t)GNT * GPER) {
+#pragma unroll
+        for (int i = 0; i < GPER; ++i) {
+          const int64_t v = v0 + i;
+          if (v >= n) break;
+          const int64_t gv = base + v;
+          a.conn[gv] = 0;
+          if (a.label[gv] >= 0 || a.row_ptr[gv + 1] == a.row_ptr[gv]) continue;
+          const uint64_t h = mix64(skey ^ (uint64_t)v);
+          if (bv < 0 || h < bh) { bh = h; bv = (int32_t)v; }
+        }
       }
       for (int o = 16; o > 0; o >>= 1) {
         uint64_t oh = __shfl_xor_sync(0xffffffffu, (unsigned long long)bh, o);
@@ -217,37 +223,58 @@ __global__ void __launch_bounds__(GNT) k_ggg(GGGArgs a) {
         }
         if (tid == 0) accw_sh = 0;
         // connected unassigned nodes in id order, longest prefix that fits;
-        // when all of them fit (the usual step) no ordered scan is needed
+        // each thread takes GPER consecutive nodes per pass (its prefix is
+        // serial, the block scans give its offsets), so one pair of block
+        // scans covers GPER * GNT nodes
         int64_t cw_all = 0;
-        for (int64_t v = tid; v < n; v += GNT) {
-          const int64_t gv = base + v;
-          if (a.label[gv] < 0 && a.conn[gv] > 0) cw_all += a.nw[gv];
+        for (int64_t v0 = (int64_t)tid * GPER; v0 < n; v0 += (int64_t)GNT * GPER) {
+#pragma unroll
+          for (int i = 0; i < GPER; ++i) {
+            const int64_t v = v0 + i;
+            if (v < n && a.label[base + v] < 0 && a.conn[base + v] > 0) cw_all += a.nw[base + v];
+          }
         }
         const bool all_fit = Wj + block_sum<GNT>(cw_all, sh) <= avg;
         int64_t carry_w = 0;
         int32_t carry_c = 0;
-        for (int64_t v0 = 0; v0 < n; v0 += GNT) {
-          const int64_t v = v0 + tid;
-          bool cand = false;
-          int64_t wt = 0;
-          if (v < n) {
-            const int64_t gv = base + v;
-            cand = a.label[gv] < 0 && a.conn[gv] > 0;
-            wt = cand ? a.nw[gv] : 0;
+        int64_t acc_w = 0;
+        for (int64_t c0 = 0; c0 < n; c0 += (int64_t)GNT * GPER) {
+          const int64_t vb = c0 + (int64_t)tid * GPER;
+          int32_t wt[GPER];                        // node weight, -1: not a candidate
+          int64_t tsum = 0;
+#pragma unroll
+          for (int i = 0; i < GPER; ++i) {
+            const int64_t v = vb + i;
+            const bool cand = v < n && a.label[base + v] < 0 && a.conn[base + v] > 0;
+            wt[i] = cand ? a.nw[base + v] : -1;
+            tsum += cand ? wt[i] : 0;
           }
-          int64_t tw = 0, iw = wt;
-          if (!all_fit) iw = block_incl_scan<GNT>(wt, sh, &tw);
-          const bool adm = cand && (all_fit || Wj + carry_w + iw <= avg);
+          int64_t tw = 0, pre = 0;
+          if (!all_fit) pre = block_incl_scan<GNT>(tsum, sh, &tw) - tsum;
+          int64_t run = pre, na = 0;
+          uint32_t adm = 0;
+#pragma unroll
+          for (int i = 0; i < GPER; ++i) {
+            if (wt[i] < 0) continue;
+            run += wt[i];
+            if (all_fit || Wj + carry_w + run <= avg) {
+              adm |= 1u << i;
+              ++na;
+            }
+          }
           int64_t tc;
-          const int64_t ic = block_incl_scan<GNT>(adm ? 1 : 0, sh, &tc);
-          if (adm) {
-            stp[carry_c + ic - 1] = (int32_t)(base + v);
-            atomicAdd(ull(&accw_sh), (unsigned long long)wt);
+          int64_t pos = block_incl_scan<GNT>(na, sh, &tc) - na + carry_c;
+#pragma unroll
+          for (int i = 0; i < GPER; ++i) {
+            if (!((adm >> i) & 1u)) continue;
+            stp[pos++] = (int32_t)(base + vb + i);
+            acc_w += wt[i];
           }
           carry_w += tw;
           carry_c += (int32_t)tc;
           if (!all_fit && Wj + carry_w > avg) break;   // no later candidate can fit
         }
+        if (acc_w) atomicAdd(ull(&accw_sh), (unsigned long long)acc_w);
         __syncthreads();
         if (tid == 0) {
           nstep_sh = carry_c;
