@@ -18,6 +18,7 @@ namespace {
 // trials (more trials in flight), 512 when it has few (wider steps).
 constexpr int GNT_MANY = 128, GNT_FEW = 512;
 constexpr int GPER = 8;   // consecutive nodes per thread in the greedy-growing scans
+constexpr int GARC = 4;   // arcs per thread per pass in the greedy-growing accumulation
 
 __global__ void k_replicate(const CopyTask* __restrict__ tasks, int64_t* __restrict__ row_ptr,
                             int32_t* __restrict__ col, int32_t* __restrict__ ew,
@@ -179,22 +180,40 @@ __global__ void __launch_bounds__(GNT) k_ggg(GGGArgs a) {
           st_in[tid] = incl;
           __syncthreads();
           const int cnt = min(GNT, nstep - q0);
-          for (int64_t x = tid; x < tot; x += GNT) {
-            // owner: the first step node whose arcs end after x (skips
-            // step nodes without arcs)
-            int lo = 0, hi = cnt - 1;
-            while (lo < hi) {
-              const int mid = (lo + hi) >> 1;
-              if (st_in[mid] > x) hi = mid; else lo = mid + 1;
+          // GARC arcs per thread per pass, their chains (owner search, arc,
+          // label, connection add) interleaved so the loads overlap
+          for (int64_t x0 = tid; x0 < tot; x0 += (int64_t)GNT * GARC) {
+            int32_t y[GARC], w[GARC], lab[GARC];
+#pragma unroll
+            for (int u = 0; u < GARC; ++u) {
+              const int64_t x = x0 + (int64_t)u * GNT;
+              y[u] = -1;
+              w[u] = 0;
+              if (x >= tot) continue;
+              // owner: the first step node whose arcs end after x (skips
+              // step nodes without arcs)
+              int lo = 0, hi = cnt - 1;
+              while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (st_in[mid] > x) hi = mid; else lo = mid + 1;
+              }
+              const int64_t e = st_rs[lo] + (x - st_ex[lo]);
+              y[u] = a.col[e];
+              w[u] = a.ew[e];
             }
-            const int64_t e = st_rs[lo] + (x - st_ex[lo]);
-            const int32_t y = a.col[e];
-            if (a.label[y] < 0) {
-              const unsigned long long old =
-                  atomicAdd(ull(&a.conn[y]), (unsigned long long)a.ew[e]);
-              if (!ordered && old == 0) {          // first arc into y (weights > 0)
-                frt[atomicAdd(&nfront_sh, 1)] = y;
-                fw += a.nw[y];
+#pragma unroll
+            for (int u = 0; u < GARC; ++u) lab[u] = y[u] >= 0 ? a.label[y[u]] : 0;
+            unsigned long long old[GARC];
+#pragma unroll
+            for (int u = 0; u < GARC; ++u)
+              old[u] = (y[u] >= 0 && lab[u] < 0)
+                           ? atomicAdd(ull(&a.conn[y[u]]), (unsigned long long)w[u])
+                           : 1ull;
+#pragma unroll
+            for (int u = 0; u < GARC; ++u) {
+              if (!ordered && old[u] == 0) {       // first arc into y (weights > 0)
+                frt[atomicAdd(&nfront_sh, 1)] = y[u];
+                fw += a.nw[y[u]];
               }
             }
           }
