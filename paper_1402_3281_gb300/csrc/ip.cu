@@ -16,9 +16,11 @@ namespace {
 
 // CTA sizes of the greedy-growing kernel: 128 threads when a batch has many
 // trials (more trials in flight), 512 when it has few (wider steps).
-constexpr int GNT_MANY = 128, GNT_FEW = 512;
+constexpr int GNT_MANY = 128, GNT_FEW = 1024;
 constexpr int GPER = 8;   // consecutive nodes per thread in the greedy-growing scans
-constexpr int GARC = 4;   // arcs per thread per pass in the greedy-growing accumulation
+// arcs per thread per pass in the greedy-growing accumulation (more in the
+// wide CTAs, which have the registers and run on few trials)
+template <int GNT> struct Garc { static constexpr int value = GNT >= 512 ? 8 : 4; };
 
 __global__ void k_replicate(const CopyTask* __restrict__ tasks, int64_t* __restrict__ row_ptr,
                             int32_t* __restrict__ col, int32_t* __restrict__ ew,
@@ -79,6 +81,7 @@ __device__ int64_t block_sum(int64_t x, int64_t* sh) {
 
 template <int GNT>
 __global__ void __launch_bounds__(GNT) k_ggg(GGGArgs a) {
+  constexpr int GARC = Garc<GNT>::value;
   __shared__ int64_t sh[33];
   __shared__ uint64_t shh[GNT / 32];
   __shared__ int32_t shv[GNT / 32];
