@@ -47,7 +47,7 @@ import graphgen as gg  # noqa: E402
 # admission key (8) written.
 ARC_BYTES = 12
 NODE_BYTES = 44
-FAMILIES = ["thread_deg_le16", "warp_deg_le128_cta128", "cta256_512", "cta_global"]
+FAMILIES = ["thread_deg_le16", "warp_deg_le128_cta128", "cta256_512", "hub_global_table"]
 
 
 def parse():
