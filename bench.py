@@ -61,9 +61,12 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-single", action="store_true")
-    ap.add_argument("--workload", default="batched", choices=["batched", "large"],
+    ap.add_argument("--workload", default="batched", choices=["batched", "large", "huge"],
                     help="batched: the 512-graph batch (default); large: R-MAT scale 22 and "
-                         "RGG 2^22, one graph per call, both round drivers")
+                         "RGG 2^22, one graph per call, both round drivers; huge: one R-MAT "
+                         "graph of --scale (default 27, edge factor 24) generated on the "
+                         "device, k = 16")
+    ap.add_argument("--scale", type=int, default=27, help="R-MAT scale of --workload huge")
     ap.add_argument("--graph-rounds", action="store_true",
                     help="run each level's LP rounds as one CUDA graph (device-side loop)")
     ap.add_argument("--autotune", action="store_true",
@@ -383,10 +386,62 @@ def large_workload(args):
     print(json.dumps(line), flush=True)
 
 
+def huge_workload(args):
+    """One R-MAT graph of 2^scale nodes and edge factor 24, generated on the
+    device (graphgen.device: same model as the host generator, counter-based
+    draws), partitioned with k = 16 after a warm-up on a scale-16 graph.  The
+    result is checked (balance, a device recount of the cut); a run that does
+    not fit in device memory reports the library's out-of-memory error."""
+    import torch
+    import paper_1402_3281_gb300 as P
+    from graphgen.device import rmat_torch
+    P.load()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    rp_w, col_w = rmat_torch(16, 24, 1, device=dev)
+    P.sclap_partition_device(rp_w, col_w, k=16, eps=0.03, seed=0)
+    t0 = time.perf_counter()
+    rp, col = rmat_torch(args.scale, 24, 0, device=dev)
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    n, arcs = rp.numel() - 1, col.numel()
+    del rp_w, col_w
+    torch.cuda.empty_cache()
+    sampler = ClockSampler(0)
+    sampler.start()
+    torch.cuda.synchronize()
+    sampler.mark()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    line = {"metric": "input edges/s", "unit": "edges/s", "n_gpus": 1, "higher_is_better": True,
+            "data": "synthetic",
+            "config": {"workload": f"R-MAT scale {args.scale} ef 24 (a,b,c,d = 0.57,0.19,0.19,0.05), "
+                                   "generated on the device, k = 16, eps 0.03, seed 0, one call",
+                       "n": n, "arcs": arcs, "generation_s": gen_s}}
+    try:
+        e0.record(stream)
+        res = P.sclap_partition_device(rp, col, k=16, eps=0.03, seed=0)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        bw = torch.bincount(res.block.long(), minlength=16)
+        ok = (res.status == 0 and int(bw.max()) <= int(res.stats["Lmax"])
+              and P.sclap_cut(rp, col, None, res.block) == res.cut)
+        line.update(value=(arcs // 2) / (ms / 1000.0), ms=ms, cut=res.cut,
+                    levels=res.stats["levels"], checked=bool(ok))
+    except P.SclapError as e:
+        line.update(value=None, error=str(e))
+    line["clocks"] = sampler.stop()
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.workload == "large":
         large_workload(args)
+        return
+    if args.workload == "huge":
+        huge_workload(args)
         return
     if args.impl == "reference":
         reference_arm(args)
