@@ -5,12 +5,16 @@
 // A round splits the participating nodes into S colour classes by a per-node
 // hash; each class is a sub-round:
 //   propose  every node computes its connection to each neighbouring label
-//            (degree-bucketed: lane groups + warp match for small degrees,
-//            shared-memory hashes per warp or CTA, a global-memory hash for
-//            hubs) and proposes the strongest eligible label;
+//            (degree-bucketed: one thread per node with its row sorted in
+//            registers up to degree 16, one warp per node with a shared-
+//            memory table up to 128, one CTA per node with a shared-memory
+//            table up to 8192, a global-memory table for hubs) and proposes
+//            the strongest eligible label;
 //   resolve  a target whose proposals all fit admits them all; otherwise the
-//            proposals into it form a segment and one CTA admits the longest
-//            prefix in (gain desc, priority asc, node asc) order that fits;
+//            proposals into it form a segment, and the longest prefix in
+//            (gain desc, priority asc, node asc) order that fits is admitted
+//            (one warp ranks all pairs of a segment of <= 64 entries, one CTA
+//            locates the boundary of a larger one by radix select);
 //   source   (local search) forced moves out of an overloaded block are capped
 //            at the block's excess the same way;
 //   apply    labels and label weights are updated with integer atomics
