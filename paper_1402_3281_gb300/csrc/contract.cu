@@ -7,9 +7,11 @@
 // node order (warp per 32 nodes, arcs flattened across lanes) once to count
 // each coarse node's inter-cluster arcs, size one open-addressing region per
 // coarse node from that count, stream the arcs again inserting (coarse
-// neighbour, weight) with warp pre-aggregation and global atomics, then emit
-// every region compactly.  Rows come out in table order, which no later
-// step depends on; all sums are integer, hence deterministic.
+// neighbour, weight) with one 64-bit CAS or atomic add each (a claim also
+// records the slot's owner and counts its degree), scan the degrees into row
+// offsets, and place every occupied slot in its owner's row.  The order of a
+// row's arcs is not fixed, which no later step depends on; all sums are
+// integer, hence deterministic.
 #include "common.cuh"
 
 namespace sclap {
