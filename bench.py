@@ -402,7 +402,15 @@ def huge_workload(args):
     rp_w, col_w = rmat_torch(16, 24, 1, device=dev)
     P.sclap_partition_device(rp_w, col_w, k=16, eps=0.03, seed=0)
     t0 = time.perf_counter()
-    rp, col = rmat_torch(args.scale, 24, 0, device=dev)
+    try:
+        rp, col = rmat_torch(args.scale, 24, 0, device=dev)
+    except torch.cuda.OutOfMemoryError as e:
+        print(json.dumps({"metric": "input edges/s", "unit": "edges/s", "n_gpus": 1,
+                          "higher_is_better": True, "data": "synthetic", "value": None,
+                          "config": {"workload": f"R-MAT scale {args.scale} ef 24, generated on "
+                                                 "the device, k = 16"},
+                          "error": "generation: " + str(e).splitlines()[0]}), flush=True)
+        return
     torch.cuda.synchronize()
     gen_s = time.perf_counter() - t0
     n, arcs = rp.numel() - 1, col.numel()
