@@ -624,3 +624,191 @@ def test_vcycles_never_worsen_a_balanced_cut(variant, maker, k):
         if prev is not None:
             assert r.cut <= prev
         prev = r.cut
+
+
+# ------------------------------------------- admission order (hand-computed)
+# One synchronous sub-round (S = 1), target side: when the proposals into a
+# cluster do not all fit, the longest prefix in (larger gain, smaller
+# priority hash, smaller node id) order whose weight fits is admitted, and
+# admission stops at the first proposal that does not fit (Sec. 3.1 "will
+# not become overloaded", read for simultaneous moves).  The expected sets
+# below are worked out by hand; the comments name the plausible mistakes
+# each case rejects.
+
+def _admission_graph(room):
+    """Target cluster 0 = {t=0, a=1} (edge t-a of weight 100 keeps both at
+    home).  Proposers p = 2..6, each with a partner q = p + 5 in its own
+    cluster (label p); edge p-t of weight w, edge p-q of weight o.  Gains
+    w - o and node weights c(p):
+        p : 2  3  4  5  6
+        w : 10 12  8  6  3     (connection to cluster 0)
+        o :  1  8  1  1  1     (connection to its own cluster)
+      gain:  9  4  7  5  2
+      c(p):  2  1  3  1  1
+    Cluster 0 weighs 2; U = 2 + room."""
+    w = {2: 10, 3: 12, 4: 8, 5: 6, 6: 3}
+    o = {2: 1, 3: 8, 4: 1, 5: 1, 6: 1}
+    cp = {2: 2, 3: 1, 4: 3, 5: 1, 6: 1}
+    s, d, ww = [0], [1], [100]
+    for p in range(2, 7):
+        s += [p, p]
+        d += [0, p + 5]
+        ww += [w[p], o[p]]
+    g = gg.from_edges(12, s, d, w=ww)
+    for p in range(2, 7):
+        g.node_w[p] = cp[p]
+    label = np.array([0, 0, 2, 3, 4, 5, 6, 2, 3, 4, 5, 6], np.int32)
+    W = np.bincount(label, weights=g.node_w, minlength=12).astype(np.int64)
+    return g, label, W, int(W[0]) + room
+
+
+@pytest.mark.parametrize("room,admitted", [
+    # gain order 2 (c 2), 4 (c 3), 5, 3, 6 (c 1 each):
+    (4, {2}),          # 2 fits (2), 4 does not (5 > 4): stop.  Skipping instead
+                       # would also admit 5 and 3; ordering by connection (3, 2, 4)
+                       # admits {3, 2}; ascending gain admits {6, 3, 5}
+    (5, {2, 4}),       # 2 + 3 = 5 fits, then 5 would make 6
+    (7, {2, 4, 5, 3}),  # 6 would make 8
+    (8, {2, 3, 4, 5, 6}),  # everything fits: all admitted
+    (1, {5}),          # a move that would overload cluster 0 by itself is not
+                       # eligible (2 and 4 do not propose); of 5, 3, 6 (c 1 each)
+                       # the largest gain, 5, takes the one unit
+])
+def test_admission_admits_the_longest_prefix_in_gain_order(room, admitted):
+    g, label, W, U = _admission_graph(room)
+    lab2, W2, moved, _ = O.lp_round(g, O.MODE_CLUSTER, label, W, U, rkey=12345, sub_rounds=1)
+    got = {int(v) for v in np.nonzero(lab2 != label)[0]}
+    # every proposer that does not fit in cluster 0 stays (its only other
+    # option, staying, is what a rejected proposal means)
+    assert got == admitted
+    assert all(lab2[v] == 0 for v in got)
+    assert moved == len(admitted) and W2[0] == W[0] + sum(int(g.node_w[v]) for v in admitted)
+    assert W2[0] <= U
+
+
+def test_admission_ties_in_gain_go_to_the_smaller_priority_hash():
+    """Two proposers (nodes 2, 3) of equal gain and weight into cluster 0,
+    room for one.  The priority is the low 32 bits of the node's round hash
+    mix64(rkey ^ v) (mix64 is pinned to the published SplitMix64 outputs);
+    the smaller one wins.  Round keys are chosen so that each node wins in
+    one of them: ordering by node id, by descending hash or by the high hash
+    bits fails one of the two."""
+    s, d, ww = [0, 2, 3], [1, 0, 0], [100, 5, 5]
+    g = gg.from_edges(4, s, d, w=ww)
+    label = np.array([0, 0, 2, 3], np.int32)
+    W = np.bincount(label, weights=g.node_w, minlength=4).astype(np.int64)
+    U = int(W[0]) + 1
+
+    def prio(rkey, v):
+        return O.mix64(rkey ^ v) & 0xFFFFFFFF
+
+    def hi(rkey, v):
+        return O.mix64(rkey ^ v) >> 32
+
+    seen = set()
+    for rkey in range(1, 400):
+        win = 2 if prio(rkey, 2) < prio(rkey, 3) else 3
+        # keep only keys where the high half would pick the other node, so a
+        # high-bits mistake is caught as well
+        if (hi(rkey, 2) < hi(rkey, 3)) == (win == 2):
+            continue
+        if win in seen:
+            continue
+        seen.add(win)
+        lab2, _, moved, _ = O.lp_round(g, O.MODE_CLUSTER, label, W, U, rkey=rkey, sub_rounds=1)
+        assert moved == 1 and lab2[win] == 0 and lab2[5 - win] == 5 - win, rkey
+        if seen == {2, 3}:
+            break
+    assert seen == {2, 3}
+
+
+# ------------------------------------------------- greedy growing (by hand)
+# Greedy graph growing as the initial partitioning reads it (the paper
+# leaves KaHIP's initial partitioner unspecified): block j starts at the
+# unassigned node with neighbours of smallest seed hash; every step absorbs,
+# in increasing id order, the unassigned nodes adjacent to the block while
+# its weight stays <= ceil(c(V)/k), stopping at the first that would
+# overflow; leftovers are water-filled into the lightest blocks.
+
+def _ggg_tkey(g, k, want, level=0):
+    """A trial key whose block seeds are the nodes `want` (block j grows from
+    want[j]); seeds are the smallest mix64(hkey(tkey, GGG, level, j) ^ v)
+    over the nodes not yet taken.  Searched, not assumed."""
+    nonisolated = [v for v in range(g.n) if g.row_ptr[v + 1] > g.row_ptr[v]]
+    for tkey in range(1, 20000):
+        taken = set()
+        ok = True
+        for j, seed in enumerate(want):
+            skey = O.hkey(tkey, O.PH_GGG, level, j)
+            cand = [v for v in nonisolated if v not in taken]
+            best = min(cand, key=lambda v: O.mix64(skey ^ v))
+            if best != seed:
+                ok = False
+                break
+            # the rest of block j is not known here; it is enough that the
+            # seed of block j+1 lies outside block j (true for the cases below)
+            taken.add(best)
+        if ok:
+            return tkey
+    raise AssertionError("no trial key found")
+
+
+def test_ggg_grows_by_adjacency_steps_in_id_order():
+    """Path 0-1-...-10, unit weights, k = 2, avg = ceil(11/2) = 6.
+    Block 0 from node 5: step 1 takes {4, 6} (weight 3), step 2 {3, 7} (5),
+    step 3 meets candidates 2 and 8 in id order: 2 fits (6), 8 does not
+    -> block 0 = {2..7}.  Block 1 from node 10: {9}, then {8}, then no
+    unassigned neighbour -> {8, 9, 10} (weight 3).  Leftovers 0 and 1
+    (weight 2) are water-filled: level 5 frees 2 units in block 1 only.
+    Absorbing in descending id order would take 8 instead of 2; growing
+    without adjacency would start with 0, 1, 2."""
+    g = gg.path(11)
+    tkey = _ggg_tkey(g, 2, [5, 10])
+    blk, W = O.ggg(g, 2, 6, tkey)
+    assert blk.tolist() == [1, 1, 0, 0, 0, 0, 0, 0, 1, 1, 1]
+    assert W.tolist() == [6, 5]
+
+
+def test_ggg_stops_at_the_first_node_that_would_overflow():
+    """Paths 0-1-2-3 and 4-5-6-7-8 joined by the edge 2-5; c(3) = 6, every
+    other node weighs 1: c(V) = 14, k = 2, avg = 7.
+    Block 0 from node 2: candidates 1, 3, 5 in id order; 1 fits (2), 3 would
+    make 8 -> stop (5 is not taken although it would fit).  Step 2: 0 fits
+    (3), 3 would overflow -> stop.  Step 3: only 3 is adjacent and does not
+    fit -> block 0 = {0, 1, 2} (weight 3).
+    Block 1 from node 8 walks 7, 6, 5, 4 (weight 5); 3 is not adjacent.
+    Leftover 3 (weight 6) goes to the lightest block, 0: W = [9, 5].
+    Skipping the overflowing node instead of stopping would give block 0
+    = {0, 1, 2, 4, 5, 6, 7}."""
+    s = [0, 1, 2, 4, 5, 6, 7, 2]
+    d = [1, 2, 3, 5, 6, 7, 8, 5]
+    g = gg.from_edges(9, s, d)
+    g.node_w[3] = 6
+    tkey = _ggg_tkey(g, 2, [2, 8])
+    blk, W = O.ggg(g, 2, 7, tkey)
+    assert blk.tolist() == [0, 0, 0, 0, 1, 1, 1, 1, 1]
+    assert W.tolist() == [9, 5]
+
+
+# ------------------------------------------- sequential node order (by hand)
+def test_sequential_round_visits_nodes_in_increasing_degree_order():
+    """Sec. 4 "Node Ordering": the sequential algorithm visits nodes in
+    increasing degree (equal degrees in the round's hash order, ascending).
+    Path 0-1-2 with w(0,1) = 5, w(1,2) = 3, unit node weights, U = 2, one
+    round.  Degrees 1, 2, 1: node 1 comes last, 0 and 2 in hash order.
+      2 first: 2 joins 1's cluster (full now); 0 cannot; 1 then prefers
+               cluster 0 (5 > 3) and moves there -> [0, 0, 1].
+      0 first: 0 joins 1's cluster; 2 cannot; 1 stays (5 > 3) -> [1, 1, 2].
+    Id order (0, 1, 2) gives [1, 1, 2] for every seed; decreasing degree
+    (1 first) gives [0, 0, 2]."""
+    g = gg.from_edges(3, [0, 1], [1, 2], w=[5, 3])
+    cfg = O.config(lp_rounds_coarse=1)
+    outcomes = set()
+    for seed in range(64):
+        rk = O.hkey(seed, O.PH_CLUSTER, 0, 0)
+        two_first = O.mix64(rk ^ 2) < O.mix64(rk ^ 0)
+        lab, rounds = O.cluster(g, 2, seed, variant=O.SEQ, cfg=cfg)
+        assert rounds == 1
+        assert lab.tolist() == ([0, 0, 1] if two_first else [1, 1, 2]), seed
+        outcomes.add(two_first)
+    assert outcomes == {True, False}
