@@ -427,6 +427,25 @@ __device__ __forceinline__ void propose_thread(const LPArgs& a, int64_t lbeg, in
 // The grid is split among the three buckets in proportion to the blocks each
 // needs (256 nodes per block), every non-empty bucket getting at least one;
 // every block computes the same split from the device offsets.
+// Split of a grid of G blocks among three buckets needing need[j] blocks
+// (tot = sum > G): floor of the proportional share, raised to one for every
+// non-empty bucket, and the difference to G (at most two blocks too many,
+// or some too few) settled on the bucket with the largest share, which
+// holds at least G / 3 blocks, so every non-empty bucket keeps >= 1 when
+// G >= 3 (the host never launches fewer than the SM count).
+__host__ __device__ __forceinline__ void split_small_grid(int64_t G, const int64_t (&need)[3],
+                                                          int64_t tot, int64_t (&g)[3]) {
+  int64_t used = 0;
+  int big = 0;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    g[j] = need[j] ? max64(1, G * need[j] / tot) : 0;
+    used += g[j];
+    if (g[j] > g[big]) big = j;
+  }
+  g[big] += G - used;
+}
+
 __global__ void __launch_bounds__(256, 4) k_propose_small(LPArgs a, int32_t sub, int32_t nb) {
   griddep_wait();
   const int64_t* bo = a.boff + sub * NB;
@@ -444,15 +463,11 @@ __global__ void __launch_bounds__(256, 4) k_propose_small(LPArgs a, int32_t sub,
 #pragma unroll
     for (int j = 0; j < 3; ++j) g[j] = need[j];
   } else {
-    int64_t used = 0;
-    int last = 0;
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      g[j] = c[j] ? max64(1, G * need[j] / tot) : 0;
-      used += g[j];
-      if (c[j]) last = j;
-    }
-    g[last] += G - used;
+    split_small_grid(G, need, tot, g);
+    // a non-empty bucket without a block would leave its nodes unproposed
+    if (blockIdx.x == 0 && threadIdx.x == 0 &&
+        ((need[0] && g[0] < 1) || (need[1] && g[1] < 1) || (need[2] && g[2] < 1)))
+      atomicOr(a.err, DERR_INTERNAL);
   }
   const int64_t b = blockIdx.x;
   if (b < g[0]) propose_thread<4>(a, bo[0], c[0], b, g[0]);

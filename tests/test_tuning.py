@@ -109,3 +109,49 @@ def test_autotune_installs_a_valid_setting_with_unchanged_results(restore_tuning
     for x, y in zip(before, after):
         assert (x.status, x.cut) == (y.status, y.cut)
         assert np.array_equal(x.block.cpu().numpy(), y.block.cpu().numpy())
+
+
+def _bucket_mix_graph():
+    """A path of 110,000 nodes (degree 2: the degree <= 4 bucket needs 430
+    blocks of 256 nodes), one node of degree 6 and one of degree 12 (one
+    node each in the degree 5..8 and 9..16 buckets)."""
+    n_path = 110_000
+    s = [np.arange(n_path - 1)]
+    d = [np.arange(1, n_path)]
+    c6, c12 = n_path, n_path + 7
+    s += [np.full(6, c6), np.full(12, c12)]
+    d += [np.arange(c6 + 1, c6 + 7), np.arange(c12 + 1, c12 + 13)]
+    return gg.from_edges(c12 + 13, np.concatenate(s), np.concatenate(d), name="bucket-mix")
+
+
+@pytest.mark.gpu
+def test_thread_launch_split_serves_every_small_bucket(restore_tuning):
+    """With one CTA per SM the thread-per-node launch has fewer blocks than
+    the three small buckets need; the split must still give the two
+    single-node buckets a block each (rounding both up to one once took the
+    last bucket's block away, so its node never proposed)."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    dev = torch.device("cuda:0")
+    g = _bucket_mix_graph()
+    deg = g.degrees()
+    assert (deg <= 4).sum() > 2 * 152 * 256 and ((deg > 4) & (deg <= 8)).sum() == 1
+    assert ((deg > 8) & (deg <= 16)).sum() == 1
+    P.set_tuning(**{**DEFAULT, "small_ctas_per_sm": 1})
+    label = np.arange(g.n, dtype=np.int32)
+    W = np.ones(g.n, np.int64)
+    for U, rkey in ((3, 5), (20, 99)):
+        ol, oW, om, on = O.lp_round(g, O.MODE_CLUSTER, label, W, U, rkey, 1, want_next=True)
+        t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+        tl, tW = t(label), t(W)
+        an = torch.zeros(g.n, dtype=torch.uint8, device=dev)
+        moved = P.sclap_lp_round(0, t(g.row_ptr), t(g.col), t(g.node_w), t(g.edge_w), tl, tW, U,
+                                 rkey, 1, active_next=an)
+        assert moved == om
+        assert np.array_equal(tl.cpu().numpy(), ol)
+        assert np.array_equal(tW.cpu().numpy(), oW)
+        assert np.array_equal(an.cpu().numpy(), on)
+        # both centres move in the oracle (each joins a singleton leaf), so a
+        # centre left without a proposal would show as a difference above
+        assert ol[110_000] != 110_000 and ol[110_007] != 110_007
