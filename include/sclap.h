@@ -294,9 +294,9 @@ int sclap_server_poll(sclap_server* srv, int64_t request_id, int32_t timeout_ms,
  * frees the server. */
 int sclap_server_destroy(sclap_server* srv);
 
-/* ---- Cut and block weights without device allocation (the paper has no
- * counterpart: it is a deployment variant of sclap_cut plus the block
- * weights c(V_i) of Sec. 2.1).
+/* ---- Cut and block weights without device allocation.  The paper has no
+ * counterpart: this is a deployment variant of sclap_cut that also returns
+ * the weight of every block.
  *
  * Every other entry point takes working memory from the CUDA allocator.
  * This one does not: its working memory is one fixed array in device global
@@ -321,11 +321,16 @@ int sclap_server_destroy(sclap_server* srv);
  * self-loop or a non-positive weight -> SCLAP_ECSR.  Symmetry is not
  * checked.
  *
+ * Synchronisation: every call reads row_ptr[n] back to the host and waits
+ * for `stream` twice (before its kernels and before returning), so it
+ * cannot be called while `stream` is being captured into a CUDA graph.
+ *
  * Set-up: the first call on a device looks up the array's device address
- * (once per device, with that device current); make that first call before
- * any stream capture starts.  The array is shared by all callers on a
- * device: calls that overlap in time (from two host threads, or on two
- * streams) race on it and must be serialised by the caller. */
+ * (once per device, with that device current), so that first call must come
+ * before any stream capture starts.  The array is shared by all callers on
+ * a device and keeps the last call's contents (each call clears the words
+ * it uses first): calls that overlap in time (from two host threads, or on
+ * two streams) race on it and must be serialised by the caller. */
 #define SCLAP_CUT_STATIC_MAX_K 4096
 int sclap_cut_static(int64_t n, const int64_t* row_ptr, const int32_t* col,
                      const int32_t* node_w, const int32_t* edge_w, const int32_t* block,
