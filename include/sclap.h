@@ -34,8 +34,11 @@
  * from the CUDA stream-ordered allocator of the current device.
  *
  * Errors: every function returns SCLAP_OK (0) or a negative SCLAP_E* code;
- * sclap_error_string() describes it.  No exception crosses the ABI.  Device
- * waits are bounded; a bounded wait that runs out reports SCLAP_ETIMEOUT.
+ * sclap_error_string() describes it.  No exception crosses the ABI.  The only
+ * device-side waits are the grid barriers of the cooperative admission kernel
+ * (tuning field fused_admission); they are bounded, and one that runs out
+ * ends the call with SCLAP_ETIMEOUT.  Every other device loop is bounded by
+ * its data size.
  */
 #ifndef SCLAP_H
 #define SCLAP_H
@@ -336,6 +339,24 @@ int sclap_cut_static(int64_t n, const int64_t* row_ptr, const int32_t* col,
                      const int32_t* node_w, const int32_t* edge_w, const int32_t* block,
                      int32_t k, int64_t* cut_out, int64_t* block_w_out, void* stream);
 
+/* ---- Host-side fault injection for tests (no counterpart in the paper).
+ * Makes the library's own failure paths run without faulting the GPU:
+ *   wait_limit   iteration limit of every bounded device-side wait (the grid
+ *                barriers of the admission kernel, ~0.5 us per iteration);
+ *                0 restores the default (2^22, about two seconds).  A small
+ *                value makes the waits run out: the call returns
+ *                SCLAP_ETIMEOUT, and the library stays usable.
+ *   probe_limit  probes allowed per insertion into the LP sweep's open-
+ *                addressing tables; 0 restores the default (the table size,
+ *                which never runs out).  A small value makes insertions
+ *                fail: the call returns SCLAP_EINTERNAL.
+ *   fail_allocs  the fail_allocs-th device allocation of the library from
+ *                now on fails once, as if the device were out of memory (the
+ *                call making it returns SCLAP_ENOMEM); 0 clears.
+ * The setting is process-wide and stays until changed.  SCLAP_EINVAL for a
+ * negative value or a limit above 2^32 - 1. ---- */
+int sclap_debug_inject(int64_t wait_limit, int64_t probe_limit, int32_t fail_allocs);
+
 /* ---- Launch tuning and autotuning (no counterpart in the paper).  Choices
  * of the LP sweep that change scheduling, never results:
  *   small_max_deg      rows of degree <= 8 or <= 16 get one thread per node
@@ -348,7 +369,16 @@ int sclap_cut_static(int64_t n, const int64_t* row_ptr, const int32_t* col,
  *   pdl                1: kernels that follow a kernel of the same stream in
  *                      the host-driven round loop are launched as
  *                      programmatic dependent launches; 0: plain launches
- * The setting is process-wide; defaults 16, 8, 8, 16, 1, 1. ---- */
+ *   fused_admission    1: the admission and application of a colour class
+ *                      run as one cooperative launch whose phases are
+ *                      separated by bounded grid-wide barriers (a barrier
+ *                      that waits too long ends the call with
+ *                      SCLAP_ETIMEOUT); 0: a chain of six launches
+ *   contract_table_slots  slots of the contraction table per pass: a level
+ *                      whose table is larger is contracted in passes over
+ *                      ranges of coarse nodes (same result); 0: automatic,
+ *                      half of the device memory still obtainable
+ * The setting is process-wide; defaults 16, 8, 8, 16, 1, 1, 0, 0. ---- */
 typedef struct sclap_tuning {
   int32_t small_max_deg;
   int32_t small_ctas_per_sm;
@@ -356,6 +386,8 @@ typedef struct sclap_tuning {
   int32_t admit_ctas_per_sm;
   int32_t concurrent;
   int32_t pdl;
+  int32_t fused_admission;
+  int32_t contract_table_slots;
 } sclap_tuning;
 void sclap_get_tuning(sclap_tuning* out);
 /* SCLAP_EINVAL for a value out of range (the setting is then unchanged). */

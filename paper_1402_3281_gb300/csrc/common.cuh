@@ -75,7 +75,13 @@ struct Tuning {
   int32_t admit_ctas_per_sm = 16;
   int32_t concurrent = 1;
   int32_t pdl = 1;
+  int32_t fused_admission = 0;   // 1: admission as one cooperative launch
+  int32_t contract_table_slots = 0;   // slots per contraction pass (0: automatic)
 };
+// Slots of the contraction table one pass may use: the tuning value, or
+// (automatic) half of the device memory still obtainable (free memory plus
+// what the allocator pool holds unused) at 12 bytes per slot.
+int64_t table_pass_slots();
 Tuning tuning_get();
 void tuning_set(const Tuning& t);
 void event_to_pool(cudaEvent_t e);
@@ -122,7 +128,88 @@ enum : int32_t {
   DERR_W_OVERFLOW = 2,    // coarse edge weight above INT32_MAX
   DERR_BAD_CSR = 4,       // validation
   DERR_INTERNAL = 8,
+  DERR_TIMEOUT = 16,      // a bounded device-side wait ran out of iterations
 };
+
+// ---------------------------------------------------------------------------
+// Grid-wide barrier of a cooperative launch (every CTA resident at once),
+// with a bounded wait.  Thread 0 of each CTA reads the generation, arrives
+// on the counter (release), and the last arriver resets the counter and
+// advances the generation; the others poll the generation (acquire) at most
+// `limit` times, ~0.5 us apart.  A wait that runs out sets DERR_TIMEOUT in
+// the error word and the CTA is told to leave (returns false); the
+// remaining CTAs then run out at their next barrier, so no CTA waits
+// forever.  The state (two words, zeroed once) is left ready for the next
+// barrier after every completed one.
+// ---------------------------------------------------------------------------
+struct GridSync {
+  unsigned int arrive;
+  unsigned int gen;
+};
+__device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ bool grid_sync(GridSync* gs, int32_t* err, uint32_t limit) {
+  __shared__ int sh_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned int g = ld_acquire_gpu(&gs->gen);
+    __threadfence();
+    const unsigned int prev = atomicAdd(&gs->arrive, 1u);
+    if (prev == gridDim.x - 1) {
+      gs->arrive = 0;
+      __threadfence();
+      atomicAdd(&gs->gen, 1u);
+    } else {
+      uint32_t it = 0;
+      while (ld_acquire_gpu(&gs->gen) == g) {
+        if (++it > limit) {
+          atomicOr(err, DERR_TIMEOUT);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    sh_ok = ok;
+  }
+  __syncthreads();
+  return sh_ok != 0;
+}
+
+// Iteration limit of every bounded device-side wait (about 2 s at the
+// default); a host-side fault-injection setting (sclap_debug_inject) may
+// lower it to make waits run out on purpose.
+uint32_t wait_limit();
+// Probe limit of the open-addressing tables of the LP sweep (default: the
+// table size, i.e. no limit); lowered only by sclap_debug_inject.
+uint32_t probe_limit();
+// Sets the three fault-injection values (see sclap_debug_inject).
+void debug_inject(uint32_t wait, uint32_t probe, int32_t fail_allocs);
+// Called by every device allocation: true for the allocation chosen to fail
+// by sclap_debug_inject (the fail_allocs-th from the call on).
+bool take_injected_alloc_failure();
+
+// Cooperative launch (all CTAs co-resident; required by grid_sync).
+template <typename... KArgs, typename... Args>
+inline void launch_coop(void (*k)(KArgs...), unsigned grid, unsigned block, size_t smem,
+                        cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  SCLAP_CUDA(cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...));
+}
 
 // ---------------------------------------------------------------------------
 // SplitMix64 output function (Steele, Lea, Flood, OOPSLA 2014) and the keyed
@@ -172,6 +259,16 @@ __host__ __device__ __forceinline__ int bucket_of(int64_t deg, bool overloaded) 
   return 8;
 }
 
+// Node and edge weight arrays of a level may be NULL: every weight is then 1
+// (the input level of unit-weight graphs keeps no array of ones).  The slot
+// array may be NULL when a level holds one graph (every node in slot 0).
+__device__ __forceinline__ int32_t wat(const int32_t* __restrict__ w, int64_t i) {
+  return w ? w[i] : 1;
+}
+__device__ __forceinline__ int32_t slot_at(const int32_t* __restrict__ gid, int64_t v) {
+  return gid ? gid[v] : 0;
+}
+
 // Weight of a cluster or block.  Node weights are validated to sum below
 // 2^31, so every label weight fits in 32 bits; sums with a node weight are
 // formed in 64 bits.
@@ -185,9 +282,9 @@ struct LevelView {
   int64_t N = 0, M = 0;
   const int64_t* row_ptr = nullptr;
   const int32_t* col = nullptr;
-  const int32_t* ew = nullptr;
-  const int32_t* nw = nullptr;
-  const int32_t* gid = nullptr;   // slot of each node
+  const int32_t* ew = nullptr;    // NULL: unit edge weights
+  const int32_t* nw = nullptr;    // NULL: unit node weights
+  const int32_t* gid = nullptr;   // slot of each node (NULL: one slot)
   // every sum of arc weights over a row (so every connection) is below 2^32:
   // the propose tables may accumulate with 32-bit atomics
   bool narrow = false;
@@ -323,6 +420,8 @@ struct DevBuf {
   void alloc(size_t count, cudaStream_t st) {
     release();
     s = st;
+    if (count && take_injected_alloc_failure())
+      throw Error(SCLAP_ENOMEM, "device allocation failed (injected)");
     n = count;
     if (count) SCLAP_CUDA(cudaMallocAsync((void**)&p, count * sizeof(T), st));
   }
@@ -444,7 +543,8 @@ struct CopyTask {              // copy one graph segment (NULL weights -> unit)
   int64_t rbase;
 };
 // Copies graph segments; row_ptr[N_total] = M_total.  N_total_override < 0:
-// the end of the last plain task.
+// the end of the last plain task.  ew / nw may be NULL: the destination
+// level keeps no weight array (unit weights).
 void ip_replicate(const std::vector<CopyTask>& tasks, int64_t* row_ptr, int32_t* col,
                   int32_t* ew, int32_t* nw, int64_t M_total, cudaStream_t s,
                   int64_t N_total_override = -1);

@@ -12,6 +12,8 @@
 // offsets, and place every occupied slot in its owner's row.  The order of a
 // row's arcs is not fixed, which no later step depends on; all sums are
 // integer, hence deterministic.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace sclap {
@@ -47,16 +49,20 @@ struct CArgs {
   int32_t* cdeg;           // distinct coarse neighbours per coarse node (slots claimed)
   int32_t* towner;         // coarse node owning each claimed slot
   int32_t* err;
+  // pass of the table build: only sources with coarse id in [c_lo, c_hi)
+  // insert, into the table regions of that range, which start at toff
+  int32_t c_lo, c_hi;
+  int64_t toff;
 };
 
 __global__ void k_map(CArgs a, int64_t N) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N;
        v += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t s = a.gid[v];
+    const int32_t s = slot_at(a.gid, v);
     if (!a.keep[s]) { a.cmap[v] = -1; continue; }
     const int32_t c = (int32_t)(a.cid[a.label[v]] + a.delta[s]);
     a.cmap[v] = c;
-    atomicAdd(&a.cnw[c], a.nw[v]);
+    atomicAdd(&a.cnw[c], wat(a.nw, v));
   }
 }
 
@@ -75,7 +81,7 @@ __device__ __forceinline__ void for_inter_arcs(const CArgs& a, int64_t N, F f) {
     int32_t cv = -1;
     if (v < N) {
       cv = a.cmap[v];
-      if (cv >= 0) {
+      if (cv >= a.c_lo && cv < a.c_hi) {
         rs = a.row_ptr[v];
         d = a.row_ptr[v + 1] - rs;
       }
@@ -102,7 +108,7 @@ __device__ __forceinline__ void for_inter_arcs(const CArgs& a, int64_t N, F f) {
         const int64_t e = rsL + (x - exL);
         cu = a.cmap[a.col[e]];
         if (cu == cvL) cu = -1;
-        else w = a.ew[e];
+        else w = wat(a.ew, e);
       }
       f(cvL, cu, w);
     }
@@ -145,8 +151,8 @@ __global__ void __launch_bounds__(256) k_insert(CArgs a, int64_t N) {
   for_inter_arcs(a, N, [&](int32_t cv, int32_t cu, int32_t w) {
     if (cu < 0) return;
     const int64_t sum = w;
-    const int64_t base = a.tbase[cv];
-    const int logcap = ceil_log2(a.tbase[cv + 1] - base);
+    const int64_t base = a.tbase[cv] - a.toff;
+    const int logcap = ceil_log2(a.tbase[cv + 1] - a.tbase[cv]);
     const uint32_t mask = (1u << logcap) - 1;
     uint32_t sl = table_slot(cu, logcap);
     const unsigned long long mine = ((unsigned long long)(uint32_t)cu << 32) | (uint64_t)sum;
@@ -193,6 +199,15 @@ __global__ void k_emit(const unsigned long long* __restrict__ tslot,
   }
 }
 
+// row_ptr[c_lo + j] = base + part[j] for j in [0, n]: the row offsets of
+// one pass's coarse nodes, placed after the rows of the earlier passes.
+__global__ void k_rows_from_part(const int64_t* __restrict__ part, int64_t n, int64_t base,
+                                 int64_t* __restrict__ row_ptr) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j <= n;
+       j += (int64_t)gridDim.x * blockDim.x)
+    row_ptr[j] = base + part[j];
+}
+
 // Overlay (ensemble clusterings): the pair (O[v], C[v]) keys an open-
 // addressing table whose entry keeps the smallest node id with that pair.
 // Labels are node ids < 2^31, so a key never equals the empty marker ~0.
@@ -207,7 +222,7 @@ __global__ void k_overlay_insert(const int32_t* __restrict__ gid, const int32_t*
   const uint64_t mask = ((uint64_t)1 << logcap) - 1;
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N;
        v += (int64_t)gridDim.x * blockDim.x) {
-    if (!part[gid[v]]) continue;
+    if (!part[slot_at(gid, v)]) continue;
     const unsigned long long key = pair_key(O[v], C[v]);
     uint64_t s = mix64(key) & mask;
     bool placed = false;
@@ -232,7 +247,7 @@ __global__ void k_overlay_apply(const int32_t* __restrict__ gid, const int32_t* 
   const uint64_t mask = ((uint64_t)1 << logcap) - 1;
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N;
        v += (int64_t)gridDim.x * blockDim.x) {
-    if (!part[gid[v]]) continue;
+    if (!part[slot_at(gid, v)]) continue;
     const unsigned long long key = pair_key(O[v], C[v]);
     uint64_t s = mix64(key) & mask;
     for (uint64_t p = 0; p <= mask; ++p) {
@@ -300,6 +315,7 @@ void contract_build(const LevelView& lv, const std::vector<int64_t>& noff, const
   a.row_ptr = lv.row_ptr; a.col = lv.col; a.ew = lv.ew; a.nw = lv.nw; a.gid = lv.gid;
   a.label = label; a.cid = w.cid.p; a.delta = d_delta.p; a.keep = d_keep.p; a.cmap = cmap;
   a.cnw = out.nw.p; a.inter = inter.p; a.tbase = tbase.p; a.err = d_err;
+  a.c_lo = 0; a.c_hi = INT32_MAX; a.toff = 0;
 
   const unsigned ng = grid_for(N, 256, (int64_t)sms * 16);
   const unsigned wg = grid_for(N, 256, (int64_t)sms * 16);   // 8 warps x 32 nodes per block
@@ -314,28 +330,82 @@ void contract_build(const LevelView& lv, const std::vector<int64_t>& noff, const
   int64_t T = 0;
   SCLAP_CUDA(cudaMemcpyAsync(&T, tbase.p + Nc, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   stream_sync(s);
-  DevBuf<unsigned long long> tslot(std::max<int64_t>(T, 1), s);
-  DevBuf<int32_t> towner(std::max<int64_t>(T, 1), s);
-  tslot.fill_bytes(0xff);
-  a.tslot = tslot.p;
-  a.towner = towner.p;
   // the inter-arc counts have served (table sizes); the array now counts
   // claimed slots, i.e. the coarse degrees
   a.cdeg = inter.p;
   SCLAP_CUDA(cudaMemsetAsync(inter.p, 0, (size_t)std::max<int64_t>(Nc, 1) * sizeof(int32_t), s));
-  if (N > 0 && T > 0) { k_insert<<<wg, 256, 0, s>>>(a, N); SCLAP_NOTE_LAUNCH("k_insert"); }
   out.row_ptr.alloc(Nc + 1, s);
-  scan_excl_i32_to_i64(inter.p, out.row_ptr.p, Nc, s);
-  int64_t Mc = 0;
-  SCLAP_CUDA(cudaMemcpyAsync(&Mc, out.row_ptr.p + Nc, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-  stream_sync(s);
-  out.M = Mc;
-  out.col.alloc(std::max<int64_t>(Mc, 1), s);
-  out.ew.alloc(std::max<int64_t>(Mc, 1), s);
-  if (Nc > 0 && T > 0) {
+  const int64_t Tcap = table_pass_slots();
+  if (T <= Tcap) {
+    // one pass: the whole table at once
+    DevBuf<unsigned long long> tslot(std::max<int64_t>(T, 1), s);
+    DevBuf<int32_t> towner(std::max<int64_t>(T, 1), s);
+    tslot.fill_bytes(0xff);
+    a.tslot = tslot.p;
+    a.towner = towner.p;
+    if (N > 0 && T > 0) { k_insert<<<wg, 256, 0, s>>>(a, N); SCLAP_NOTE_LAUNCH("k_insert"); }
+    scan_excl_i32_to_i64(inter.p, out.row_ptr.p, Nc, s);
+    int64_t Mc = 0;
+    SCLAP_CUDA(cudaMemcpyAsync(&Mc, out.row_ptr.p + Nc, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    stream_sync(s);
+    out.M = Mc;
+    out.col.alloc(std::max<int64_t>(Mc, 1), s);
+    out.ew.alloc(std::max<int64_t>(Mc, 1), s);
+    if (Nc > 0 && T > 0) {
+      SCLAP_CUDA(cudaMemsetAsync(inter.p, 0, (size_t)Nc * sizeof(int32_t), s));   // row fill
+      k_emit<<<grid_for(T, 256, (int64_t)sms * 32), 256, 0, s>>>(tslot.p, towner.p, out.row_ptr.p,
+                                                                 inter.p, T, out.col.p, out.ew.p); SCLAP_NOTE_LAUNCH("k_emit");
+    }
+  } else {
+    // Passes over ranges of coarse nodes whose table regions fit in Tcap
+    // slots (a region larger than that gets a pass of its own).  Each pass
+    // streams every fine node but inserts only the arcs of sources in its
+    // range.  Sweep 1 counts the coarse degrees, which give the row offsets
+    // and the exact size of the coarse arrays; sweep 2 inserts again and
+    // emits every pass's rows in place.  Identical result to one pass.
+    std::vector<int64_t> htb(Nc + 1);
+    SCLAP_CUDA(cudaMemcpyAsync(htb.data(), tbase.p, (Nc + 1) * sizeof(int64_t),
+                               cudaMemcpyDeviceToHost, s));
+    stream_sync(s);
+    std::vector<int32_t> cut_at{0};
+    while (cut_at.back() < Nc) {
+      const int64_t lo = cut_at.back();
+      int64_t hi = std::upper_bound(htb.begin() + lo + 1, htb.end(), htb[lo] + Tcap) -
+                   htb.begin() - 1;
+      if (hi <= lo) hi = lo + 1;
+      cut_at.push_back((int32_t)hi);
+    }
+    int64_t Tmax = 1;
+    for (size_t q = 0; q + 1 < cut_at.size(); ++q)
+      Tmax = std::max<int64_t>(Tmax, htb[cut_at[q + 1]] - htb[cut_at[q]]);
+    DevBuf<unsigned long long> tslot(Tmax, s);
+    DevBuf<int32_t> towner(Tmax, s), claims(std::max<int64_t>(Nc, 1), s);
+    a.tslot = tslot.p;
+    a.towner = towner.p;
+    auto pass = [&](size_t q) {
+      a.c_lo = cut_at[q];
+      a.c_hi = cut_at[q + 1];
+      a.toff = htb[a.c_lo];
+      SCLAP_CUDA(cudaMemsetAsync(tslot.p, 0xff, (size_t)(htb[a.c_hi] - a.toff) * 8, s));
+      if (N > 0) { k_insert<<<wg, 256, 0, s>>>(a, N); SCLAP_NOTE_LAUNCH("k_insert"); }
+      return htb[a.c_hi] - a.toff;
+    };
+    for (size_t q = 0; q + 1 < cut_at.size(); ++q) pass(q);            // sweep 1: degrees
+    scan_excl_i32_to_i64(inter.p, out.row_ptr.p, Nc, s);
+    int64_t Mc = 0;
+    SCLAP_CUDA(cudaMemcpyAsync(&Mc, out.row_ptr.p + Nc, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    stream_sync(s);
+    out.M = Mc;
+    out.col.alloc(std::max<int64_t>(Mc, 1), s);
+    out.ew.alloc(std::max<int64_t>(Mc, 1), s);
+    a.cdeg = claims.p;                   // sweep 2 counts claims apart from the row fill
     SCLAP_CUDA(cudaMemsetAsync(inter.p, 0, (size_t)Nc * sizeof(int32_t), s));   // row fill
-    k_emit<<<grid_for(T, 256, (int64_t)sms * 32), 256, 0, s>>>(tslot.p, towner.p, out.row_ptr.p,
-                                                               inter.p, T, out.col.p, out.ew.p); SCLAP_NOTE_LAUNCH("k_emit");
+    for (size_t q = 0; q + 1 < cut_at.size(); ++q) {                    // sweep 2: emit
+      const int64_t Tp = pass(q);
+      k_emit<<<grid_for(Tp, 256, (int64_t)sms * 32), 256, 0, s>>>(tslot.p, towner.p,
+                                                                  out.row_ptr.p, inter.p, Tp,
+                                                                  out.col.p, out.ew.p); SCLAP_NOTE_LAUNCH("k_emit");
+    }
   }
   SCLAP_LAUNCH_CHECK();
   out.gid.alloc(std::max<int64_t>(Nc, 1), s);

@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(256) k_validate_level(
       if (rs > re || rs < aoff[s] || re > aoff[s + 1]) bad = true;
       if (v == noff[s] && rs != aoff[s]) bad = true;
       if (v == noff[s + 1] - 1 && re != aoff[s + 1]) bad = true;
-      w = nw[v];
+      w = wat(nw, v);
       if (w <= 0) bad = true;
       d = bad ? 0 : re - rs;
     }
@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(256) k_validate_level(
         const int64_t e = rsL + (x - exL);
         const int64_t src = base + L;
         const int32_t c = col[e];
-        const int32_t we = ew[e];
+        const int32_t we = wat(ew, e);
         if (c < noff[sL] || c >= noff[sL + 1] || c == src || we <= 0) atomicOr(&gerr[sL], 1);
         const unsigned long long wp = we > 0 ? (unsigned long long)we : 0ull;
         if (uni) acc += wp;
@@ -159,7 +159,7 @@ __global__ void k_compose(int32_t* __restrict__ comm, const int32_t* __restrict_
 __global__ void k_w_from_nw(const int32_t* nw, int64_t N, wgt_t* W) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N;
        v += (int64_t)gridDim.x * blockDim.x)
-    W[v] = nw[v];
+    W[v] = wat(nw, v);
 }
 
 __global__ void k_check_range(const int32_t* __restrict__ a, int64_t n, int64_t lo, int64_t hi,
@@ -228,16 +228,33 @@ struct Slots {
   }
 };
 
-// A batched level with owned storage.
+// A batched level.  Its graph arrays are owned, or (the input level of a
+// single device-resident graph) borrowed from the caller, read in place and
+// never written.  Weight arrays are NULL for unit weights, the slot array
+// NULL for a level holding one graph.
 struct Level {
   int64_t N = 0, M = 0;
   DevBuf<int64_t> row_ptr, noff_d;
   DevBuf<int32_t> col, ew, nw, gid, cmap, blk;
+  const int64_t* rp_in = nullptr;          // borrowed arrays (input level)
+  const int32_t* col_in = nullptr;
+  const int32_t* ew_in = nullptr;
+  const int32_t* nw_in = nullptr;
+  bool borrowed = false;
   std::vector<int64_t> noff, aoff;
-  bool narrow = false;   // every arc-weight sum of every graph fits in 32 bits
+  // every sum of arc weights over a row of this level fits in 32 bits: true
+  // when every graph's total arc weight does (which then holds on every
+  // level of its hierarchy: contraction only merges or drops arcs), and on
+  // an input level of unit weights (a row's sum is its degree, < 2^31)
+  bool narrow = false;
+  bool narrow_total = false;   // the total-weight rule alone (inherited by coarse levels)
+  const int64_t* rp() const { return borrowed ? rp_in : row_ptr.p; }
+  const int32_t* colp() const { return borrowed ? col_in : col.p; }
+  const int32_t* ewp() const { return borrowed ? ew_in : ew.p; }
+  const int32_t* nwp() const { return borrowed ? nw_in : nw.p; }
   LevelView view() const {
     LevelView v;
-    v.N = N; v.M = M; v.row_ptr = row_ptr.p; v.col = col.p; v.ew = ew.p; v.nw = nw.p;
+    v.N = N; v.M = M; v.row_ptr = rp(); v.col = colp(); v.ew = ewp(); v.nw = nwp();
     v.gid = gid.p;
     v.narrow = narrow;
     return v;
@@ -275,6 +292,7 @@ void check_err(int32_t* d_err, cudaStream_t s) {
   int32_t e = 0;
   SCLAP_CUDA(cudaMemcpyAsync(&e, d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   stream_sync(s);
+  if (e & DERR_TIMEOUT) throw Error(SCLAP_ETIMEOUT, "a bounded device-side wait ran out");
   if (e & DERR_W_OVERFLOW) throw Error(SCLAP_EOVERFLOW, "coarse edge weight above INT32_MAX");
   if (e & DERR_HASH_FULL) throw Error(SCLAP_EINTERNAL, "hash table full");
   if (e & DERR_BAD_CSR) throw Error(SCLAP_ECSR, "malformed CSR");
@@ -311,7 +329,7 @@ void validate_level(const Level& L, int B, std::vector<int32_t>& status,
   d_aoff.upload(L.aoff);
   if (L.N > 0) {
     k_validate_level<<<grid_for(L.N, 256, (int64_t)num_sms() * 16), 256, 0, s>>>(
-        L.row_ptr.p, L.col.p, L.ew.p, L.nw.p, L.noff_d.p, d_aoff.p, B, L.N, err.p, sum.p, mx.p,
+        L.rp(), L.colp(), L.ewp(), L.nwp(), L.noff_d.p, d_aoff.p, B, L.N, err.p, sum.p, mx.p,
         arcw.p); SCLAP_NOTE_LAUNCH("k_validate_level");
     SCLAP_LAUNCH_CHECK();
   }
@@ -352,7 +370,10 @@ void validate(const GIn& g, cudaStream_t s, int64_t* cV, int64_t* maxc, bool* na
   if (narrow) *narrow = nar[0] != 0;
 }
 
-// Builds the level holding the graphs `gs` back to back.
+// Builds the level holding the graphs `gs` back to back.  One graph is used
+// in place (its device arrays are only read; no copy, no slot array); a
+// batch is copied into one segmented CSR.  Weight arrays are kept only when
+// some graph has weights: a batch of unit-weight graphs keeps none.
 void build_level0(const std::vector<GIn>& gs, Level& L, cudaStream_t s) {
   const int B = (int)gs.size();
   L.noff.assign(B + 1, 0);
@@ -364,17 +385,30 @@ void build_level0(const std::vector<GIn>& gs, Level& L, cudaStream_t s) {
   L.N = L.noff[B];
   L.M = L.aoff[B];
   if (L.N >= ((int64_t)1 << 31)) throw Error(SCLAP_EINVAL, "total node count must be < 2^31");
+  L.noff_d.alloc(B + 1, s);
+  L.noff_d.upload(L.noff);
+  if (B == 1) {
+    L.borrowed = true;
+    L.rp_in = gs[0].row_ptr;
+    L.col_in = gs[0].col;
+    L.ew_in = gs[0].ew;
+    L.nw_in = gs[0].nw;
+    return;
+  }
+  bool any_ew = false, any_nw = false;
+  for (const GIn& g : gs) {
+    any_ew = any_ew || g.ew != nullptr;
+    any_nw = any_nw || g.nw != nullptr;
+  }
   L.row_ptr.alloc(L.N + 1, s);
   L.col.alloc(std::max<int64_t>(L.M, 1), s);
-  L.ew.alloc(std::max<int64_t>(L.M, 1), s);
-  L.nw.alloc(std::max<int64_t>(L.N, 1), s);
+  if (any_ew) L.ew.alloc(std::max<int64_t>(L.M, 1), s);
+  if (any_nw) L.nw.alloc(std::max<int64_t>(L.N, 1), s);
   std::vector<CopyTask> tasks(B);
   for (int i = 0; i < B; ++i)
     tasks[i] = CopyTask{gs[i].row_ptr, gs[i].col, gs[i].ew, gs[i].nw, 0, 0, gs[i].n, gs[i].m,
                         L.noff[i], L.aoff[i], nullptr, 0};
   ip_replicate(tasks, L.row_ptr.p, L.col.p, L.ew.p, L.nw.p, L.M, s);
-  L.noff_d.alloc(B + 1, s);
-  L.noff_d.upload(L.noff);
   L.gid.alloc(std::max<int64_t>(L.N, 1), s);
   fill_gid(L.noff_d.p, B, L.gid.p, L.N, s);
 }
@@ -429,7 +463,7 @@ void run_ip(const std::vector<IPIn>& in, const sclap_config& cfg, wgt_t* Wg,
     const int ns = (int)Q->noff.size() - 1;
     DevBuf<uint8_t> flags(std::max<int64_t>(Q->N, 1), s);
     DevBuf<int32_t> iso(std::max<int64_t>(Q->N, 1), s);
-    isolated_flags(Q->row_ptr.p, Q->nw.p, Q->N, flags.p, iso.p, s);
+    isolated_flags(Q->rp(), Q->nwp(), Q->N, flags.p, iso.p, s);
     x->rank.alloc(Q->N + 1, s);
     x->iso_prefix.alloc(Q->N + 1, s);
     scan_excl_u8_to_i64(flags.p, x->rank.p, Q->N, s);
@@ -458,7 +492,7 @@ void run_ip(const std::vector<IPIn>& in, const sclap_config& cfg, wgt_t* Wg,
       noff[i + 1] = noff[i] + nA;
       aoff[i + 1] = aoff[i] + m;
       boff[i + 1] = boff[i] + in[g].k;
-      tasks.push_back(CopyTask{Q.row_ptr.p, Q.col.p, Q.ew.p, Q.nw.p, Q.noff[x], Q.aoff[x], n, m,
+      tasks.push_back(CopyTask{Q.rp(), Q.colp(), Q.ewp(), Q.nwp(), Q.noff[x], Q.aoff[x], n, m,
                                noff[i], aoff[i], X.rank.p, X.rank_at[x]});
     }
   }
@@ -541,7 +575,7 @@ void run_ip(const std::vector<IPIn>& in, const sclap_config& cfg, wgt_t* Wg,
     const Level& Q = *in[g].Q;
     LevelAux& X = aux_of(&Q);
     const int x = in[g].g;
-    fill[g] = FillTask{in[g].dst_blk, Q.nw.p, X.iso_prefix.p, Q.noff[x], Q.noff[x + 1] - Q.noff[x],
+    fill[g] = FillTask{in[g].dst_blk, Q.nwp(), X.iso_prefix.p, Q.noff[x], Q.noff[x + 1] - Q.noff[x],
                        in[g].boff, in[g].k};
     Kmax = std::max(Kmax, in[g].boff + in[g].k);
   }
@@ -585,7 +619,8 @@ void run_batch(const std::vector<GIn>& gs_in, const sclap_config& cfg,
     }
   }
   if ((int)ok.size() == B) {
-    L0->narrow = all_narrow;
+    L0->narrow_total = all_narrow;
+    L0->narrow = all_narrow || L0->ewp() == nullptr;
     run_valid_batch(gs_in, cV, maxc, cfg, outs_in, res, std::move(L0), s);
     return;
   }
@@ -601,7 +636,8 @@ void run_batch(const std::vector<GIn>& gs_in, const sclap_config& cfg,
   }
   L0.reset(new Level());
   build_level0(gs, *L0, s);
-  L0->narrow = all_narrow;
+  L0->narrow_total = all_narrow;
+  L0->narrow = all_narrow || L0->ewp() == nullptr;
   std::vector<GOut> r2;
   run_valid_batch(gs, c2, m2, cfg, outs, r2, std::move(L0), s);
   for (size_t j = 0; j < ok.size(); ++j) res[ok[j]] = r2[j];
@@ -728,7 +764,8 @@ void run_valid_batch(const std::vector<GIn>& gs, const std::vector<int64_t>& cV,
       CoarseLevel co;
       contract_build(v, cur.noff, label.p, cw, keep, cur.cmap.p, co, d_err.p, s);
       std::unique_ptr<Level> nx(new Level());
-      nx->narrow = cur.narrow;
+      nx->narrow = cur.narrow_total;
+      nx->narrow_total = cur.narrow_total;
       nx->N = co.N;
       nx->M = co.M;
       nx->row_ptr = std::move(co.row_ptr);
@@ -1250,7 +1287,7 @@ int sclap_cluster(int64_t n, const int64_t* row_ptr, const int32_t* col, const i
     Slots sl(s, 1, L.noff_d.p, {0}, {U}, {seed}, {level}, {0}, {0});
     DevBuf<wgt_t> W(n, s);
     k_iota<<<grid_for(n, 256, (int64_t)num_sms() * 16), 256, 0, s>>>(label_out, n); SCLAP_NOTE_LAUNCH("k_iota");
-    k_w_from_nw<<<grid_for(n, 256, (int64_t)num_sms() * 16), 256, 0, s>>>(L.nw.p, n, W.p); SCLAP_NOTE_LAUNCH("k_w_from_nw");
+    k_w_from_nw<<<grid_for(n, 256, (int64_t)num_sms() * 16), 256, 0, s>>>(L.nwp(), n, W.p); SCLAP_NOTE_LAUNCH("k_w_from_nw");
     LPRun run;
     run.mode = MODE_CLUSTER;
     run.phase = PH_CLUSTER;
@@ -1433,7 +1470,7 @@ int sclap_refine(int64_t n, const int64_t* row_ptr, const int32_t* col, const in
     L.narrow = nar;
     DevBuf<wgt_t> W(k, s);
     W.zero();
-    block_weights(block, L.nw.p, n, W.p, s);
+    block_weights(block, L.nwp(), n, W.p, s);
     Slots sl(s, 1, L.noff_d.p, {0}, {Lmax}, {seed}, {level}, {k}, {0});
     LPRun run;
     run.mode = MODE_REFINE;
@@ -1474,6 +1511,15 @@ int sclap_cut(int64_t n, const int64_t* row_ptr, const int32_t* col, const int32
   });
 }
 
+int sclap_debug_inject(int64_t wait, int64_t probe, int32_t fail_allocs) {
+  return guarded([&] {
+    if (wait < 0 || probe < 0 || fail_allocs < 0 || wait > 0xffffffffll || probe > 0xffffffffll)
+      throw Error(SCLAP_EINVAL, "fault-injection value out of range");
+    debug_inject(wait == 0 ? (1u << 22) : (uint32_t)wait,
+                 probe == 0 ? 0xffffffffu : (uint32_t)probe, fail_allocs);
+  });
+}
+
 void sclap_get_tuning(sclap_tuning* out) {
   if (!out) return;
   const Tuning t = tuning_get();
@@ -1483,6 +1529,8 @@ void sclap_get_tuning(sclap_tuning* out) {
   out->admit_ctas_per_sm = t.admit_ctas_per_sm;
   out->concurrent = t.concurrent;
   out->pdl = t.pdl;
+  out->fused_admission = t.fused_admission;
+  out->contract_table_slots = t.contract_table_slots;
 }
 
 int sclap_set_tuning(const sclap_tuning* in) {
@@ -1491,7 +1539,8 @@ int sclap_set_tuning(const sclap_tuning* in) {
     if ((in->small_max_deg != 8 && in->small_max_deg != 16) || in->small_ctas_per_sm < 1 ||
         in->small_ctas_per_sm > 32 || in->warp_ctas_per_sm < 1 || in->warp_ctas_per_sm > 32 ||
         in->admit_ctas_per_sm < 1 || in->admit_ctas_per_sm > 64 || in->concurrent < 0 ||
-        in->concurrent > 1 || in->pdl < 0 || in->pdl > 1)
+        in->concurrent > 1 || in->pdl < 0 || in->pdl > 1 || in->fused_admission < 0 ||
+        in->fused_admission > 1 || in->contract_table_slots < 0)
       throw Error(SCLAP_EINVAL, "tuning value out of range");
     Tuning t;
     t.small_max_deg = in->small_max_deg;
@@ -1500,6 +1549,8 @@ int sclap_set_tuning(const sclap_tuning* in) {
     t.admit_ctas_per_sm = in->admit_ctas_per_sm;
     t.concurrent = in->concurrent;
     t.pdl = in->pdl;
+    t.fused_admission = in->fused_admission;
+    t.contract_table_slots = in->contract_table_slots;
     tuning_set(t);
   });
 }
@@ -1543,6 +1594,7 @@ int sclap_autotune(int32_t count, sclap_graph* graphs, const sclap_config* cfg,
           {&Tuning::admit_ctas_per_sm, {8, 16, 32}},
           {&Tuning::concurrent, {1, 0}},
           {&Tuning::pdl, {1, 0}},
+          {&Tuning::fused_admission, {0, 1}},
       };
       for (const Param& p : params) {
         for (int32_t v : p.vals) {

@@ -35,13 +35,13 @@ __global__ void k_replicate(const CopyTask* __restrict__ tasks, int64_t* __restr
       d = r0 - t.rbase;
     }
     row_ptr[t.dst_n0 + d] = t.dst_a0 + (t.row_ptr[t.src_n0 + v] - t.src_a0);
-    nw[t.dst_n0 + d] = t.nw ? t.nw[t.src_n0 + v] : 1;
+    if (nw) nw[t.dst_n0 + d] = wat(t.nw, t.src_n0 + v);
   }
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < t.m; e += stride) {
     const int64_t u = t.col[t.src_a0 + e];
     const int64_t du = t.rank ? t.rank[u] - t.rbase : u - t.src_n0;
     col[t.dst_a0 + e] = (int32_t)(du + t.dst_n0);
-    ew[t.dst_a0 + e] = t.ew ? t.ew[t.src_a0 + e] : 1;
+    if (ew) ew[t.dst_a0 + e] = wat(t.ew, t.src_a0 + e);
   }
 }
 
@@ -394,7 +394,7 @@ __global__ void __launch_bounds__(256) k_slot_cut(const int64_t* __restrict__ ro
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   if (threadIdx.x == 0) {
     const int64_t v0 = (int64_t)blockIdx.x * blockDim.x;
-    sh_slot = v0 < N ? gid[v0] : -1;
+    sh_slot = v0 < N ? slot_at(gid, v0) : -1;
     sh_sum = 0;
   }
   __syncthreads();
@@ -406,7 +406,7 @@ __global__ void __launch_bounds__(256) k_slot_cut(const int64_t* __restrict__ ro
       rs = row_ptr[v];
       d = row_ptr[v + 1] - rs;
       lv = label[v];
-      s = gid[v];
+      s = slot_at(gid, v);
     }
     long long incl = d;
     for (int o = 1; o < 32; o <<= 1) {
@@ -432,7 +432,7 @@ __global__ void __launch_bounds__(256) k_slot_cut(const int64_t* __restrict__ ro
       if (x < total) {
         const int64_t e = rsL + (x - exL);
         if (label[col[e]] != lvL) {
-          const int32_t w = ew[e];
+          const int32_t w = wat(ew, e);
           if (uni) acc += (unsigned long long)w;
           else if (sL == sh_slot) atomicAdd(&sh_sum, (unsigned long long)w);
           else atomicAdd(ull(&cut2[sL]), (unsigned long long)w);
@@ -510,7 +510,7 @@ __global__ void k_block_weights(const int32_t* __restrict__ label, const int32_t
                                 int64_t N, wgt_t* __restrict__ W) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N;
        v += (int64_t)gridDim.x * blockDim.x)
-    atomicAdd(&W[label[v]], (wgt_t)nw[v]);
+    atomicAdd(&W[label[v]], (wgt_t)wat(nw, v));
 }
 
 __global__ void k_isolated(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ nw,
@@ -519,7 +519,7 @@ __global__ void k_isolated(const int64_t* __restrict__ row_ptr, const int32_t* _
        v += (int64_t)gridDim.x * blockDim.x) {
     const bool has = row_ptr[v + 1] > row_ptr[v];
     flags[v] = has ? 1 : 0;
-    iso_w[v] = has ? 0 : nw[v];
+    iso_w[v] = has ? 0 : wat(nw, v);
   }
 }
 
@@ -574,7 +574,7 @@ __global__ void k_wf_assign(const FillTask* __restrict__ tasks, wgt_t* Wg,
     }
     const int32_t b = order[t.g_boff + lo];
     t.blk[t.n0 + v] = (int32_t)(t.g_boff + b);
-    atomicAdd(&Wg[t.g_boff + b], (wgt_t)t.nw[t.n0 + v]);
+    atomicAdd(&Wg[t.g_boff + b], (wgt_t)wat(t.nw, t.n0 + v));
   }
 }
 

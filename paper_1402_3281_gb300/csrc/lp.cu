@@ -62,7 +62,7 @@ struct LPArgs {
   int32_t* ovf_cnt;
   int32_t* ovf_fill;
   int64_t* ovf_base;
-  int64_t* ctr;          // [0] entry cursor, [1] segment count
+  int64_t* ctr;          // admission segment counters (8 words, see adm_ctr)
   int32_t* seg_g;
   int64_t* seg_base;
   int32_t* seg_cnt;
@@ -96,6 +96,8 @@ struct LPArgs {
   // (a node joins only clusters of its own block), or NULL
   const int32_t* rblk;
   int32_t* err;
+  uint32_t wait_limit;    // iterations of a bounded grid-barrier wait
+  uint32_t probe_limit;   // probes of an open-addressing table (sclap_debug_inject)
 };
 
 __device__ __forceinline__ const uint8_t* act_cur(const LPArgs& a) {
@@ -175,6 +177,7 @@ __global__ void k_round_begin(LPArgs a, int32_t nslots, int32_t phase,
       a.live[0] = 0;
       a.flags[0] = 0;
     }
+    if (threadIdx.x < 8) a.ctr[threadIdx.x] = 0;   // admission segment counters
   }
   for (int32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < nslots;
        s += gridDim.x * blockDim.x) {
@@ -229,7 +232,7 @@ constexpr int MAX_KEYS = 64 * NB;
 
 __device__ __forceinline__ int node_key(const LPArgs& a, const uint8_t* ac, int64_t v,
                                         int64_t* deg_out, bool* ov_out) {
-  const int32_t s = a.gid[v];
+  const int32_t s = slot_at(a.gid, v);
   if (a.done[s]) return -1;
   const int64_t deg = a.row_ptr[v + 1] - a.row_ptr[v];
   bool take, ov = false;
@@ -318,7 +321,7 @@ __global__ void __launch_bounds__(BK_NT) k_bucket_scatter(LPArgs a, int64_t N) {
     const int64_t v = base + (int64_t)j * BK_NT + threadIdx.x;
     const int64_t pos = a.boff[key[j]] + sh_base[key[j]] + rank[j];
     const int64_t rs = a.row_ptr[v];
-    a.rec[pos] = make_int4((int32_t)v, a.label[v], a.nw[v], a.gid[v]);
+    a.rec[pos] = make_int4((int32_t)v, a.label[v], wat(a.nw, v), slot_at(a.gid, v));
     a.rec2[pos] = make_longlong2(rs, a.row_ptr[v + 1] - rs);
   }
 }
@@ -407,7 +410,7 @@ __device__ __forceinline__ void propose_thread(const LPArgs& a, int64_t lbeg, in
 #pragma unroll
     for (int j = 0; j < MAXD; ++j) {
       const bool in = j < deg;
-      w[j] = in ? a.ew[c.rs + j] : 0;
+      w[j] = in ? wat(a.ew, c.rs + j) : 0;
       C[j] = in ? a.col[c.rs + j] : -1;
       total += w[j];
     }
@@ -555,7 +558,7 @@ __global__ void __launch_bounds__(WPC * 32) k_propose_warp(LPArgs a, int32_t sub
     for (int t = 0; t < 4; ++t) {
       const bool in = t * 32 + lane < deg;
       const int64_t e = c.rs + t * 32 + lane;
-      w[t] = in ? a.ew[e] : 0;
+      w[t] = in ? wat(a.ew, e) : 0;
       C[t] = in ? a.col[e] : -1;
     }
 #pragma unroll
@@ -573,16 +576,19 @@ __global__ void __launch_bounds__(WPC * 32) k_propose_warp(LPArgs a, int32_t sub
         conn_add(&vals[key], w[t], a.narrow);
       } else {
         uint32_t s = table_slot(key, WLOG);
-        for (int p = 0; p < WCAP; ++p) {
+        const uint32_t pmax = a.probe_limit < (uint32_t)WCAP ? a.probe_limit : (uint32_t)WCAP;
+        bool placed = false;
+        for (uint32_t p = 0; p < pmax; ++p) {
           const int32_t prev = atomicCAS(&keys[s], -1, key);
           if (prev == -1 || prev == key) {
             if (prev == -1) { created |= 1u << t; slot[t] = (int)s; }
             conn_add(&vals[s], w[t], a.narrow);
+            placed = true;
             break;
           }
           s = (s + 1) & (WCAP - 1);
-          if (p == WCAP - 1) atomicOr(a.err, DERR_HASH_FULL);
         }
+        if (!placed) atomicOr(a.err, DERR_HASH_FULL);
       }
     }
     __syncwarp();
@@ -701,7 +707,7 @@ __global__ void __launch_bounds__(NT) k_propose_blk(LPArgs a, int32_t sub, int32
       for (int u = 0; u < 4; ++u) {
         const int64_t e = e0 + (int64_t)u * NT + tid;
         const bool in = e < c.re;
-        w[u] = in ? a.ew[e] : 0;
+        w[u] = in ? wat(a.ew, e) : 0;
         C[u] = in ? a.col[e] : -1;
       }
 #pragma unroll
@@ -718,16 +724,19 @@ __global__ void __launch_bounds__(NT) k_propose_blk(LPArgs a, int32_t sub, int32
             conn_add(&vals[key], w[u], a.narrow);
           } else {
             s = table_slot(key, logcap);
-            for (uint32_t p = 0; p <= mask; ++p) {
+            const uint32_t pmax = a.probe_limit <= mask ? a.probe_limit : mask + 1;
+            bool placed = false;
+            for (uint32_t p = 0; p < pmax; ++p) {
               const int32_t prev = atomicCAS(&keys[s], -1, key);
               if (prev == -1 || prev == key) {
                 cr = prev == -1;
                 conn_add(&vals[s], w[u], a.narrow);
+                placed = true;
                 break;
               }
               s = (s + 1) & mask;
-              if (p == mask) atomicOr(a.err, DERR_HASH_FULL);
             }
+            if (!placed) atomicOr(a.err, DERR_HASH_FULL);
           }
         }
         // one list reservation per warp for the slots it created
@@ -794,42 +803,56 @@ __global__ void __launch_bounds__(NT) k_propose_blk(LPArgs a, int32_t sub, int32
 }
 
 // ------------------------------------------------------------- admission
-__global__ void k_resolve(LPArgs a, int32_t sub) {
-  griddep_wait();
-  if (blockIdx.x == 0 && threadIdx.x == 0) {   // segment counters of the target side
-    a.ctr[0] = 0;
-    a.ctr[1] = 0;
-  }
-  int64_t lbeg, cnt;
-  sub_range(a, sub, 0, NB, &lbeg, &cnt);
+// Admission and application of one colour class run as ONE cooperative
+// launch (k_admit below), its phases separated by bounded grid barriers:
+//   resolve   every proposal into a target whose proposals all fit is
+//             admitted; the others are counted per target, and the first
+//             proposal into an overflowing target registers the target as a
+//             segment (with its admission threshold);
+//   alloc     each segment takes its range of the entry arrays;
+//   scatter   the overflowing proposals are written into their segments;
+//   select    each segment admits its longest fitting prefix;
+//   (source side, local search with overloaded blocks: forced moves out of
+//   an overloaded block are grouped by source the same way)
+//   apply     labels and label weights are updated.
+// When no target overflows (known to every CTA after the first barrier) the
+// kernel goes from resolve straight to apply: one barrier per colour class.
+//
+// Segment counters: ctr[set * 4 + side * 2 + {0: entry cursor, 1: segments}],
+// set = colour class & 1; a launch clears the other set for the next class
+// (k_round_begin clears both at the start of a round).
+__device__ __forceinline__ int64_t* adm_ctr(const LPArgs& a, int sub, int side) {
+  return a.ctr + (sub & 1) * 4 + side * 2;
+}
+
+__device__ void adm_resolve(const LPArgs& a, int64_t lbeg, int64_t cnt, int64_t* ct) {
   for (int64_t li = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; li < cnt;
        li += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = lbeg + li;
     const int32_t t = a.prop_t[i];
     a.stage[i] = 0;
     if (t < 0) { a.adm[i] = 0; continue; }
-    const int32_t s = a.rec[i].w;
-    if ((int64_t)a.W[t] + a.in_w[t] <= a.bound[s]) {
+    const int64_t bound = a.bound[a.rec[i].w];
+    const int64_t Wt = a.W[t];
+    if (Wt + a.in_w[t] <= bound) {
       a.adm[i] = 1;
     } else {
       a.adm[i] = 0;
       a.grp[i] = t;
       const int c = atomicAdd(&a.ovf_cnt[t], 1);
       a.stage[i] = c == 0 ? 2 : 1;
+      if (c == 0) {                     // admit while the inclusive prefix <= bound - W[t]
+        const int64_t seg = (int64_t)atomicAdd(ull(&ct[1]), 1ull);
+        a.seg_g[seg] = t;
+        a.seg_thr[seg] = bound - Wt;
+      }
     }
   }
 }
 
-// Forced moves out of overloaded blocks (local search), grouped by source.
-__global__ void k_forced(LPArgs a, int32_t sub) {
-  griddep_wait();
-  if (blockIdx.x == 0 && threadIdx.x == 0) {   // segment counters of the source side
-    a.ctr[0] = 0;
-    a.ctr[1] = 0;
-  }
-  if (a.flags[0] == 0) return;              // no listed node in an overloaded block
-  int64_t lbeg, cnt;
-  sub_range(a, sub, 0, NB, &lbeg, &cnt);
+// Forced moves out of overloaded blocks (local search), grouped by source;
+// admit while the exclusive prefix <= W[src] - bound - 1.
+__device__ void adm_forced(const LPArgs& a, int64_t lbeg, int64_t cnt, int64_t* ct) {
   for (int64_t li = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; li < cnt;
        li += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = lbeg + li;
@@ -837,44 +860,35 @@ __global__ void k_forced(LPArgs a, int32_t sub) {
     if (a.adm[i] != 1) continue;
     const int4 r = a.rec[i];
     const int32_t own = r.y;
-    if (a.W[own] > a.bound[r.w]) {
+    const int64_t bound = a.bound[r.w];
+    const int64_t Wo = a.W[own];
+    if (Wo > bound) {
       a.grp[i] = own;
       const int c = atomicAdd(&a.ovf_cnt[own], 1);
       a.stage[i] = c == 0 ? 2 : 1;
+      if (c == 0) {
+        const int64_t seg = (int64_t)atomicAdd(ull(&ct[1]), 1ull);
+        a.seg_g[seg] = own;
+        a.seg_thr[seg] = Wo - bound - 1;
+      }
     }
   }
 }
 
-// One leader per group allocates the group's segment.  thr: target side,
-// admit while the inclusive prefix <= bound - W[t]; source side, admit while
-// the exclusive prefix <= W[src] - bound - 1.
-__global__ void k_ovf_alloc(LPArgs a, int32_t sub, int32_t source) {
-  griddep_wait();
-  if (source && a.flags[0] == 0) return;    // source side idle this round
-  int64_t lbeg, cnt;
-  sub_range(a, sub, 0, NB, &lbeg, &cnt);
-  for (int64_t li = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; li < cnt;
-       li += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = lbeg + li;
-    if (a.stage[i] != 2) continue;
-    const int32_t g = a.grp[i];
+// Each segment takes the range of its entries (order of segments is free).
+__device__ void adm_alloc(const LPArgs& a, int64_t nseg, int64_t* ct) {
+  for (int64_t sg = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; sg < nseg;
+       sg += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t g = a.seg_g[sg];
     const int32_t n = a.ovf_cnt[g];
-    const int64_t base = (int64_t)atomicAdd(ull(&a.ctr[0]), (unsigned long long)n);
+    const int64_t base = (int64_t)atomicAdd(ull(&ct[0]), (unsigned long long)n);
     a.ovf_base[g] = base;
-    const int64_t seg = (int64_t)atomicAdd(ull(&a.ctr[1]), 1ull);
-    const int64_t bound = a.bound[a.rec[i].w];
-    a.seg_g[seg] = g;
-    a.seg_base[seg] = base;
-    a.seg_cnt[seg] = n;
-    a.seg_thr[seg] = source ? ((int64_t)a.W[g] - bound - 1) : (bound - (int64_t)a.W[g]);
+    a.seg_base[sg] = base;
+    a.seg_cnt[sg] = n;
   }
 }
 
-__global__ void k_ovf_scatter(LPArgs a, int32_t sub, int32_t source) {
-  griddep_wait();
-  if (source && a.flags[0] == 0) return;
-  int64_t lbeg, cnt;
-  sub_range(a, sub, 0, NB, &lbeg, &cnt);
+__device__ void adm_scatter(const LPArgs& a, int64_t lbeg, int64_t cnt) {
   for (int64_t li = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; li < cnt;
        li += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = lbeg + li;
@@ -933,8 +947,7 @@ __device__ __forceinline__ void select_rank_small(const LPArgs& a, int n, int64_
   }
 }
 
-__global__ void __launch_bounds__(SEL_NT) k_ovf_select(LPArgs a, int32_t source) {
-  griddep_wait();
+__device__ void adm_select(const LPArgs& a, int64_t nseg, int32_t source) {
   __shared__ uint64_t sk[SEL_SMALL];
   __shared__ int32_t sv[SEL_SMALL];
   __shared__ int32_t sw[SEL_SMALL];
@@ -947,7 +960,6 @@ __global__ void __launch_bounds__(SEL_NT) k_ovf_select(LPArgs a, int32_t source)
   __shared__ long long acc_sh;
   __shared__ int found_sh, ncand_sh, bfound_sh, done_sh, x_sh, ncomp_sh;
   const int tid = threadIdx.x, lane = tid & 31;
-  const int64_t nseg = a.ctr[1];
   // Phase 1: groups of <= 64 entries, one warp each (entries lane and
   // lane + 32 in registers, every pair ranked through shuffles).
   {
@@ -1196,10 +1208,7 @@ __device__ __forceinline__ void apply_delta(int32_t* hk, int32_t* hv, wgt_t* W, 
   atomicAdd(&W[L], (wgt_t)d);
 }
 
-__global__ void __launch_bounds__(256) k_apply(LPArgs a, int32_t sub) {
-  griddep_wait();
-  int64_t lbeg, cnt;
-  sub_range(a, sub, 0, NB, &lbeg, &cnt);
+__device__ void adm_apply(const LPArgs& a, int64_t lbeg, int64_t cnt) {
   uint8_t* const an = act_next(a);
   __shared__ int32_t hk[APPLY_SLOTS];
   __shared__ int32_t hv[APPLY_SLOTS];
@@ -1274,7 +1283,116 @@ __global__ void __launch_bounds__(256) k_apply(LPArgs a, int32_t sub) {
   }
 }
 
+constexpr int ADM_NT = 256;
+
+// The admission and application of colour class `sub` (see "admission"
+// above).  source_chain: local search, forced moves out of overloaded
+// blocks are possible this round.
+__global__ void __launch_bounds__(ADM_NT) k_admit(LPArgs a, int32_t sub, int32_t source_chain,
+                                                  GridSync* gs) {
+  if (blockIdx.x == 0 && threadIdx.x < 4) a.ctr[((sub + 1) & 1) * 4 + threadIdx.x] = 0;
+  // a bounded wait of an earlier launch ran out: the run is abandoned
+  if (*(volatile int32_t*)a.err & DERR_TIMEOUT) return;
+  int64_t lbeg, cnt;
+  sub_range(a, sub, 0, NB, &lbeg, &cnt);
+  const uint32_t lim = a.wait_limit;
+  int64_t* ct = adm_ctr(a, sub, 0);
+  adm_resolve(a, lbeg, cnt, ct);
+  if (!grid_sync(gs, a.err, lim)) return;
+  const int64_t nseg = *(volatile int64_t*)&ct[1];
+  if (nseg > 0) {
+    adm_alloc(a, nseg, ct);
+    if (!grid_sync(gs, a.err, lim)) return;
+    adm_scatter(a, lbeg, cnt);
+    if (!grid_sync(gs, a.err, lim)) return;
+    adm_select(a, nseg, 0);
+    if (!grid_sync(gs, a.err, lim)) return;
+  }
+  if (source_chain && *(volatile int32_t*)a.flags != 0) {
+    int64_t* cs = adm_ctr(a, sub, 1);
+    adm_forced(a, lbeg, cnt, cs);
+    if (!grid_sync(gs, a.err, lim)) return;
+    const int64_t nsrc = *(volatile int64_t*)&cs[1];
+    if (nsrc > 0) {
+      adm_alloc(a, nsrc, cs);
+      if (!grid_sync(gs, a.err, lim)) return;
+      adm_scatter(a, lbeg, cnt);
+      if (!grid_sync(gs, a.err, lim)) return;
+      adm_select(a, nsrc, 1);
+      if (!grid_sync(gs, a.err, lim)) return;
+    }
+  }
+  adm_apply(a, lbeg, cnt);
+}
+
+// The same phases as separate launches, chained on one stream with
+// programmatic dependent launches (the default: on the 512-graph batch the
+// chain measured faster than the cooperative kernel, whose launches also
+// slowed the propose launches that follow them).  Every kernel waits for
+// its predecessor first; the later phases read the segment counters on the
+// device and return at once when there is nothing to do.
+__global__ void __launch_bounds__(ADM_NT) k_resolve(LPArgs a, int32_t sub) {
+  griddep_wait();
+  if (blockIdx.x == 0 && threadIdx.x < 4) a.ctr[((sub + 1) & 1) * 4 + threadIdx.x] = 0;
+  int64_t lbeg, cnt;
+  sub_range(a, sub, 0, NB, &lbeg, &cnt);
+  adm_resolve(a, lbeg, cnt, adm_ctr(a, sub, 0));
+}
+__global__ void __launch_bounds__(ADM_NT) k_forced(LPArgs a, int32_t sub) {
+  griddep_wait();
+  if (*(volatile int32_t*)a.flags == 0) return;   // no listed node in an overloaded block
+  int64_t lbeg, cnt;
+  sub_range(a, sub, 0, NB, &lbeg, &cnt);
+  adm_forced(a, lbeg, cnt, adm_ctr(a, sub, 1));
+}
+__global__ void __launch_bounds__(ADM_NT) k_ovf_alloc(LPArgs a, int32_t sub, int32_t side) {
+  griddep_wait();
+  int64_t* ct = adm_ctr(a, sub, side);
+  const int64_t nseg = *(volatile int64_t*)&ct[1];
+  if (nseg > 0) adm_alloc(a, nseg, ct);
+}
+__global__ void __launch_bounds__(ADM_NT) k_ovf_scatter(LPArgs a, int32_t sub, int32_t side) {
+  griddep_wait();
+  if (*(volatile int64_t*)&adm_ctr(a, sub, side)[1] == 0) return;
+  int64_t lbeg, cnt;
+  sub_range(a, sub, 0, NB, &lbeg, &cnt);
+  adm_scatter(a, lbeg, cnt);
+}
+__global__ void __launch_bounds__(SEL_NT) k_ovf_select(LPArgs a, int32_t sub, int32_t side) {
+  griddep_wait();
+  const int64_t nseg = *(volatile int64_t*)&adm_ctr(a, sub, side)[1];
+  if (nseg > 0) adm_select(a, nseg, side);
+}
+__global__ void __launch_bounds__(ADM_NT) k_apply(LPArgs a, int32_t sub) {
+  griddep_wait();
+  int64_t lbeg, cnt;
+  sub_range(a, sub, 0, NB, &lbeg, &cnt);
+  adm_apply(a, lbeg, cnt);
+}
+
 }  // namespace
+
+// Limits of the bounded device-side loops, process-wide; changed only by the
+// host-side fault injection of sclap_debug_inject (tests).
+std::atomic<uint32_t> g_wait_limit{1u << 22};
+std::atomic<uint32_t> g_probe_limit{0xffffffffu};
+std::atomic<int32_t> g_fail_allocs{0};
+uint32_t wait_limit() { return g_wait_limit.load(); }
+uint32_t probe_limit() { return g_probe_limit.load(); }
+void debug_inject(uint32_t wait, uint32_t probe, int32_t fail_allocs) {
+  g_wait_limit.store(wait);
+  g_probe_limit.store(probe);
+  g_fail_allocs.store(fail_allocs);
+}
+// Counts down the allocations to the injected failure; true for the one
+// that fails (the count then stays at zero).
+bool take_injected_alloc_failure() {
+  int32_t n = g_fail_allocs.load();
+  while (n > 0) {
+    if (g_fail_allocs.compare_exchange_weak(n, n - 1)) return n == 1;
+  }
+  return false;
+}
 
 // Launch tuning, process-wide (see sclap_tuning in sclap.h).
 std::mutex g_tune_mu;
@@ -1286,6 +1404,23 @@ Tuning tuning_get() {
 void tuning_set(const Tuning& t) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune = t;
+}
+
+int64_t table_pass_slots() {
+  const Tuning t = tuning_get();
+  if (t.contract_table_slots > 0) return t.contract_table_slots;
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return (int64_t)1 << 30;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaMemPool_t pool;
+  uint64_t reserved = 0, used = 0;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved);
+    cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used);
+  }
+  const int64_t avail = (int64_t)fr + (int64_t)(reserved > used ? reserved - used : 0);
+  return std::max<int64_t>((int64_t)1 << 20, avail / 2 / 12);
 }
 
 // Stream on which this thread captures graphs (non-blocking, created once).
@@ -1417,7 +1552,10 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, wgt_t*
   DevBuf<int32_t> ent_v(N, s), ent_w(N, s), ent_i(N, s);
   DevBuf<uint64_t> sel_k0(N, s), sel_k1(N, s);
   DevBuf<int32_t> sel_v0(N, s), sel_v1(N, s), sel_w0(N, s), sel_w1(N, s);
-  DevBuf<int64_t> ctr(2, s);
+  DevBuf<int64_t> ctr(8, s);
+  ctr.zero();
+  DevBuf<GridSync> gsync(1, s);
+  gsync.zero();
   DevBuf<int32_t> bcnt(nkeys, s), bfill(nkeys, s);
   DevBuf<int64_t> boff(nkeys + 1, s), arcs(1, s), karcs(nkeys, s);
   DevBuf<int32_t> flags(1, s);
@@ -1460,6 +1598,8 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, wgt_t*
   a.flags = flags.p;
   a.nkey = nkey.p;
   a.err = d_err;
+  a.wait_limit = wait_limit();
+  a.probe_limit = probe_limit();
 
   // ---- round-invariant setup ---------------------------------------------
   DevBuf<int32_t> rstate(3, s);        // round index, live slots, continue flag
@@ -1515,8 +1655,6 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, wgt_t*
   const unsigned grid_warp = (unsigned)(sms * tu.warp_ctas_per_sm);
   const unsigned grid_b5 = (unsigned)(sms * 16), grid_b6 = (unsigned)(sms * 4);
   const unsigned grid_b7 = (unsigned)sms;
-  const unsigned grid_adm_max = (unsigned)(sms * tu.admit_ctas_per_sm);
-  const unsigned grid_sel = (unsigned)(sms * 4);
   const int32_t raw = run.raw_key ? 1 : 0;
 
   // ---- one round, as launches on s (shared by both drivers) ----------------
@@ -1625,24 +1763,43 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, wgt_t*
     }
     SCLAP_LAUNCH_CHECK();
   };
-  // Admission and application of colour class `sub`; the source-side chain
-  // (local search) is skipped by the host when it knows no listed node sits
-  // in an overloaded block, else its kernels check that on the device.
-  // admission: the segment counters are cleared by k_resolve (target side)
-  // and k_forced (source side), so the chain is kernels only
+  // Admission and application of colour class `sub`: one cooperative launch
+  // (k_admit).  The source-side phases (local search) are skipped by the
+  // host when it knows no listed node sits in an overloaded block, else the
+  // kernel checks that on the device.  The grid is sized from the host's
+  // proposal count when known (fewer CTAs make the barriers cheaper), else
+  // the largest co-resident grid.
+  static int adm_occ = 0;
+  static std::once_flag adm_once;
+  std::call_once(adm_once, [&] {
+    SCLAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&adm_occ, k_admit, ADM_NT, 0));
+    if (adm_occ < 1) adm_occ = 1;
+  });
+  const unsigned grid_adm_coop =
+      (unsigned)std::max(1, sms * std::min<int>(adm_occ, tu.admit_ctas_per_sm));
+  const unsigned grid_adm_max = (unsigned)(sms * tu.admit_ctas_per_sm);
+  const unsigned grid_sel = (unsigned)(sms * 4);
   auto admit = [&](cudaStream_t s, int sub, bool source_chain, int64_t cnt, bool pdl) {
-    const unsigned grid_adm = cnt < 0 ? grid_adm_max : grid_for(cnt, 256, grid_adm_max);
-    launch_k(false, k_resolve, grid_adm, 256, 0, s, a, sub); SCLAP_NOTE_LAUNCH("k_resolve");
-    launch_k(pdl, k_ovf_alloc, grid_adm, 256, 0, s, a, sub, 0); SCLAP_NOTE_LAUNCH("k_ovf_alloc");
-    launch_k(pdl, k_ovf_scatter, grid_adm, 256, 0, s, a, sub, 0); SCLAP_NOTE_LAUNCH("k_ovf_scatter");
-    launch_k(pdl, k_ovf_select, grid_sel, SEL_NT, 0, s, a, 0); SCLAP_NOTE_LAUNCH("k_ovf_select");
-    if (source_chain) {
-      launch_k(pdl, k_forced, grid_adm, 256, 0, s, a, sub); SCLAP_NOTE_LAUNCH("k_forced");
-      launch_k(pdl, k_ovf_alloc, grid_adm, 256, 0, s, a, sub, 1); SCLAP_NOTE_LAUNCH("k_ovf_alloc");
-      launch_k(pdl, k_ovf_scatter, grid_adm, 256, 0, s, a, sub, 1); SCLAP_NOTE_LAUNCH("k_ovf_scatter");
-      launch_k(pdl, k_ovf_select, grid_sel, SEL_NT, 0, s, a, 1); SCLAP_NOTE_LAUNCH("k_ovf_select");
+    if (tu.fused_admission) {
+      // one cooperative launch; it follows the propose join: plain launch
+      const unsigned grid = cnt < 0 ? grid_adm_coop : grid_for(cnt, ADM_NT, grid_adm_coop);
+      launch_coop(k_admit, grid, ADM_NT, 0, s, a, sub, source_chain ? 1 : 0, gsync.p);
+      SCLAP_NOTE_LAUNCH("k_admit");
+      SCLAP_LAUNCH_CHECK();
+      return;
     }
-    launch_k(pdl, k_apply, grid_adm, 256, 0, s, a, sub); SCLAP_NOTE_LAUNCH("k_apply");
+    const unsigned grid_adm = cnt < 0 ? grid_adm_max : grid_for(cnt, ADM_NT, grid_adm_max);
+    launch_k(false, k_resolve, grid_adm, ADM_NT, 0, s, a, sub); SCLAP_NOTE_LAUNCH("k_resolve");
+    launch_k(pdl, k_ovf_alloc, grid_sel, ADM_NT, 0, s, a, sub, 0); SCLAP_NOTE_LAUNCH("k_ovf_alloc");
+    launch_k(pdl, k_ovf_scatter, grid_adm, ADM_NT, 0, s, a, sub, 0); SCLAP_NOTE_LAUNCH("k_ovf_scatter");
+    launch_k(pdl, k_ovf_select, grid_sel, SEL_NT, 0, s, a, sub, 0); SCLAP_NOTE_LAUNCH("k_ovf_select");
+    if (source_chain) {
+      launch_k(pdl, k_forced, grid_adm, ADM_NT, 0, s, a, sub); SCLAP_NOTE_LAUNCH("k_forced");
+      launch_k(pdl, k_ovf_alloc, grid_sel, ADM_NT, 0, s, a, sub, 1); SCLAP_NOTE_LAUNCH("k_ovf_alloc");
+      launch_k(pdl, k_ovf_scatter, grid_adm, ADM_NT, 0, s, a, sub, 1); SCLAP_NOTE_LAUNCH("k_ovf_scatter");
+      launch_k(pdl, k_ovf_select, grid_sel, SEL_NT, 0, s, a, sub, 1); SCLAP_NOTE_LAUNCH("k_ovf_select");
+    }
+    launch_k(pdl, k_apply, grid_adm, ADM_NT, 0, s, a, sub); SCLAP_NOTE_LAUNCH("k_apply");
     SCLAP_LAUNCH_CHECK();
   };
   auto tail = [&](cudaStream_t s, cudaGraphConditionalHandle h, bool in_graph, bool pdl) {

@@ -30,6 +30,7 @@ SYMBOLS = (
     "sclap_server_destroy", "sclap_get_tuning", "sclap_set_tuning", "sclap_autotune",
     "sclap_profile_enable", "sclap_profile_reset", "sclap_profile_read",
     "sclap_profile_timeline", "sclap_profile_dump", "sclap_profile_phases",
+    "sclap_debug_inject",
 )
 
 
@@ -85,7 +86,7 @@ class ServerOptions(C.Structure):
 class Tuning(C.Structure):
     _fields_ = [(n, C.c_int32) for n in ("small_max_deg", "small_ctas_per_sm",
                                          "warp_ctas_per_sm", "admit_ctas_per_sm", "concurrent",
-                                         "pdl")]
+                                         "pdl", "fused_admission", "contract_table_slots")]
 
     def to_dict(self) -> dict:
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -131,6 +132,7 @@ def _lib():
             "sclap_server_submit": (C.c_int, [p, i64, p, p, p, p, i32, dbl, u64, p]),
             "sclap_server_poll": (C.c_int, [p, i64, i32, p, p, p, p]),
             "sclap_server_destroy": (C.c_int, [p]),
+            "sclap_debug_inject": (C.c_int, [i64, i64, i32]),
             "sclap_get_tuning": (None, [p]),
             "sclap_set_tuning": (C.c_int, [p]),
             "sclap_autotune": (C.c_int, [i32, p, p, i32, i32, p, p]),
@@ -513,6 +515,13 @@ def sclap_profile_phases() -> np.ndarray:
     out = np.zeros((max(n, 1), 7), dtype=np.float64)
     m = _lib().sclap_profile_phases(out.ctypes.data_as(C.c_void_p), n)
     return out[:min(n, m)]
+
+
+def debug_inject(wait_limit: int = 0, probe_limit: int = 0, fail_allocs: int = 0) -> None:
+    """Host-side fault injection (sclap_debug_inject); all zeros restores
+    the defaults."""
+    _check(_lib().sclap_debug_inject(int(wait_limit), int(probe_limit), int(fail_allocs)),
+           "sclap_debug_inject")
 
 
 def get_tuning() -> Tuning:

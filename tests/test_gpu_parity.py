@@ -503,3 +503,37 @@ def test_scale19_rmat_bit_exact_both_drivers():
         assert (res.status, res.cut) == (ref.status, ref.cut)
         assert np.array_equal(res.block.cpu().numpy(), ref.block)
         assert P.sclap_cut(rp, col, None, res.block) == res.cut
+
+
+def test_large_single_graphs_bit_exact():
+    """The large single-graph workload at full size, one graph per call as
+    the benchmark runs it: R-MAT scale 22, edge factor 16 (4,194,304 nodes,
+    ~128M arcs; generated on the device by graphgen.device), k = 8, seed 0;
+    and a 2D RGG with 2^22 nodes, k = 64.  Blocks, cut and level sizes are
+    bit-exact with the oracle (run in spawn-started worker processes), and
+    the cut equals a device recount."""
+    import multiprocessing as mp
+    import _oracle_jobs as J
+    from graphgen.device import rmat_torch
+
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(2) as pool:
+        rgg_job = pool.apply_async(J.rgg_and_partition, (1 << 22, 0, 64, 0.03, 0))
+        rp, col = rmat_torch(22, 16, 0, device=DEV)
+        hrp, hcol = rp.cpu().numpy(), col.cpu().numpy()
+        assert hrp.size - 1 == 1 << 22 and hcol.size > 100_000_000
+        rmat_job = pool.apply_async(J.partition, (hrp, hcol, 8, 0.03, 0))
+        res = P.sclap_partition_device(rp, col, k=8, eps=0.03, seed=0)
+        blk, cut, status, level_n = rmat_job.get()
+        assert (res.status, res.cut) == (status, cut)
+        assert np.array_equal(res.block.cpu().numpy(), blk)
+        assert res.stats["level_n"] == level_n
+        assert P.sclap_cut(rp, col, None, res.block) == res.cut
+        del rp, col
+        grp, gcol, blk, cut, status, level_n = rgg_job.get()
+        trp, tcol = dt(grp), dt(gcol)
+        res = P.sclap_partition_device(trp, tcol, k=64, eps=0.03, seed=0)
+        assert (res.status, res.cut) == (status, cut)
+        assert np.array_equal(res.block.cpu().numpy(), blk)
+        assert res.stats["level_n"] == level_n
+        assert P.sclap_cut(trp, tcol, None, res.block) == res.cut

@@ -42,7 +42,45 @@ def test_some_kernels_are_launched_programmatically():
     launched = set()
     for src in _sources().values():
         launched |= _pdl_launched(src)
-    assert {"k_ovf_alloc", "k_apply", "k_bucket_count"} <= launched
+    assert {"k_bucket_count", "k_bucket_scatter", "k_round_cond"} <= launched
+
+
+def _kernels_calling(src, callee):
+    """__global__ functions whose body calls `callee` (directly)."""
+    out = set()
+    for m in re.finditer(r"__global__\s+void[^{;]*?\b(k_[A-Za-z_0-9]+)\s*\(", src):
+        start = src.index("{", m.end())
+        depth, i = 0, start
+        while True:
+            if src[i] == "{":
+                depth += 1
+            elif src[i] == "}":
+                depth -= 1
+                if depth == 0:
+                    break
+            i += 1
+        if re.search(r"\b" + callee + r"\s*\(", src[start:i]):
+            out.add(m.group(1))
+    return out
+
+
+def test_grid_barriers_only_in_cooperative_launches():
+    """A grid-wide barrier needs every CTA resident at once: a kernel that
+    calls grid_sync must be launched with launch_coop and never with a plain
+    or programmatic launch."""
+    srcs = _sources()
+    users = set()
+    for src in srcs.values():
+        users |= _kernels_calling(src, "grid_sync")
+    assert "k_admit" in users
+    coop = set()
+    for src in srcs.values():
+        coop |= set(re.findall(r"launch_coop\(\s*([A-Za-z_][A-Za-z_0-9]*)", src))
+        plain = set(re.findall(r"\b(k_[A-Za-z_0-9]+)\s*<<<", src)) | _pdl_launched(src)
+        plain |= {m.group(1) for m in re.finditer(
+            r"launch_k\(\s*false\s*,\s*([A-Za-z_][A-Za-z_0-9]*)", src)}
+        assert not (users & plain), users & plain
+    assert users <= coop, users - coop
 
 
 @pytest.mark.parametrize("fname", sorted(_sources()))

@@ -13,7 +13,7 @@ import oracle as O
 import paper_1402_3281_gb300 as P
 
 DEFAULT = dict(small_max_deg=16, small_ctas_per_sm=8, warp_ctas_per_sm=8, admit_ctas_per_sm=16,
-               concurrent=1, pdl=1)
+               concurrent=1, pdl=1, fused_admission=0, contract_table_slots=0)
 
 
 @pytest.fixture
@@ -31,7 +31,9 @@ def test_default_tuning(restore_tuning):
 @pytest.mark.parametrize("field,bad", [("small_max_deg", 12), ("small_max_deg", 32),
                                        ("small_ctas_per_sm", 0), ("warp_ctas_per_sm", 33),
                                        ("admit_ctas_per_sm", 65), ("concurrent", 2),
-                                       ("concurrent", -1), ("pdl", 2)])
+                                       ("concurrent", -1), ("pdl", 2),
+                                       ("fused_admission", 2), ("fused_admission", -1),
+                                       ("contract_table_slots", -5)])
 def test_out_of_range_values_are_rejected_and_leave_the_setting(restore_tuning, field, bad):
     P.set_tuning(**DEFAULT)
     with pytest.raises(P.SclapError) as e:
@@ -42,9 +44,11 @@ def test_out_of_range_values_are_rejected_and_leave_the_setting(restore_tuning, 
 
 def test_set_tuning_round_trip(restore_tuning):
     t = P.set_tuning(small_max_deg=8, small_ctas_per_sm=3, warp_ctas_per_sm=32,
-                     admit_ctas_per_sm=1, concurrent=0, pdl=0)
+                     admit_ctas_per_sm=1, concurrent=0, pdl=0, fused_admission=1,
+                     contract_table_slots=4096)
     assert t.to_dict() == dict(small_max_deg=8, small_ctas_per_sm=3, warp_ctas_per_sm=32,
-                               admit_ctas_per_sm=1, concurrent=0, pdl=0)
+                               admit_ctas_per_sm=1, concurrent=0, pdl=0, fused_admission=1,
+                               contract_table_slots=4096)
 
 
 # ------------------------------------------------------------------ GPU
@@ -67,6 +71,10 @@ SETTINGS = [
     dict(concurrent=0, pdl=0),
     dict(small_max_deg=8, small_ctas_per_sm=2, warp_ctas_per_sm=3, admit_ctas_per_sm=5,
          concurrent=0),
+    dict(fused_admission=1),
+    dict(fused_admission=1, admit_ctas_per_sm=1, concurrent=0),
+    dict(contract_table_slots=4096),      # contraction in passes of 4096 slots
+    dict(contract_table_slots=1),         # a pass per coarse node
 ]
 
 
@@ -155,3 +163,37 @@ def test_thread_launch_split_serves_every_small_bucket(restore_tuning):
         # both centres move in the oracle (each joins a singleton leaf), so a
         # centre left without a proposal would show as a difference above
         assert ol[110_000] != 110_000 and ol[110_007] != 110_007
+
+
+def _canon(rp, col, w):
+    n = rp.size - 1
+    src = np.repeat(np.arange(n), np.diff(rp))
+    o = np.lexsort((col, src))
+    return src[o], col[o], w[o]
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("slots", [1, 64, 4096])
+def test_contraction_in_passes_equals_the_oracle(restore_tuning, slots):
+    """A contraction table capped at `slots` slots per pass (1: a pass per
+    coarse node) builds the same coarse graph as the oracle: map, node
+    weights, row offsets, and the arcs of every row."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    dev = torch.device("cuda:0")
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    g = gg.random_weights(gg.rmat(13, 8, 3), 5)
+    P.set_tuning(**{**DEFAULT, "contract_table_slots": slots})
+    for label in (O.cluster(g, 40, seed=2)[0],
+                  np.random.default_rng(4).integers(0, g.n // 30, g.n).astype(np.int32)):
+        c = O.contract(g, label)
+        cmap, crp, ccol, cnw, cew = P.sclap_contract(t(g.row_ptr), t(g.col), t(g.node_w),
+                                                     t(g.edge_w), t(label))
+        assert np.array_equal(cmap.cpu().numpy(), c.cmap)
+        assert np.array_equal(cnw.cpu().numpy(), c.node_w)
+        assert np.array_equal(crp.cpu().numpy(), c.row_ptr)
+        a = _canon(crp.cpu().numpy(), ccol.cpu().numpy(), cew.cpu().numpy())
+        b = _canon(c.row_ptr, c.col, c.edge_w)
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
