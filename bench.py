@@ -435,10 +435,14 @@ def huge_workload(args):
         bw = torch.bincount(res.block.long(), minlength=16)
         ok = (res.status == 0 and int(bw.max()) <= int(res.stats["Lmax"])
               and P.sclap_cut(rp, col, None, res.block) == res.cut)
+        st = res.stats
         line.update(value=(arcs // 2) / (ms / 1000.0), ms=ms, cut=res.cut,
-                    levels=res.stats["levels"], checked=bool(ok))
+                    levels=st["levels"], level_n=st["level_n"], level_m=st["level_m"],
+                    cluster_rounds=st.get("cluster_rounds"), ip_cut=st.get("ip_cut"),
+                    checked=bool(ok))
     except P.SclapError as e:
-        line.update(value=None, error=str(e))
+        line.update(value=None, error=str(e),
+                    torch_reserved_gb=torch.cuda.memory_reserved() / 1e9)
     line["clocks"] = sampler.stop()
     print(json.dumps(line), flush=True)
 

@@ -378,7 +378,11 @@ int sclap_debug_inject(int64_t wait_limit, int64_t probe_limit, int32_t fail_all
  *                      whose table is larger is contracted in passes over
  *                      ranges of coarse nodes (same result); 0: automatic,
  *                      half of the device memory still obtainable
- * The setting is process-wide; defaults 16, 8, 8, 16, 1, 1, 0, 0. ---- */
+ *   ip_trial_group     initial-partitioning trials whose graph copies exist
+ *                      at once (the trials run group after group; same
+ *                      result); 0: automatic, as many as fit in half of the
+ *                      device memory still obtainable
+ * The setting is process-wide; defaults 16, 8, 8, 16, 1, 1, 0, 0, 0. ---- */
 typedef struct sclap_tuning {
   int32_t small_max_deg;
   int32_t small_ctas_per_sm;
@@ -388,6 +392,7 @@ typedef struct sclap_tuning {
   int32_t pdl;
   int32_t fused_admission;
   int32_t contract_table_slots;
+  int32_t ip_trial_group;
 } sclap_tuning;
 void sclap_get_tuning(sclap_tuning* out);
 /* SCLAP_EINVAL for a value out of range (the setting is then unchanged). */

@@ -77,10 +77,13 @@ struct Tuning {
   int32_t pdl = 1;
   int32_t fused_admission = 0;   // 1: admission as one cooperative launch
   int32_t contract_table_slots = 0;   // slots per contraction pass (0: automatic)
+  int32_t ip_trial_group = 0;         // trials replicated at once (0: automatic)
 };
+// Device memory still obtainable: free memory plus what the allocator pool
+// holds unused.
+int64_t obtainable_device_bytes();
 // Slots of the contraction table one pass may use: the tuning value, or
-// (automatic) half of the device memory still obtainable (free memory plus
-// what the allocator pool holds unused) at 12 bytes per slot.
+// (automatic) half of the obtainable memory at 12 bytes per slot.
 int64_t table_pass_slots();
 Tuning tuning_get();
 void tuning_set(const Tuning& t);
@@ -245,6 +248,13 @@ constexpr int B5_MAXDEG = 512, B5_SLOTS = 1024;
 constexpr int B6_MAXDEG = 2048, B6_SLOTS = 4096;
 constexpr int B7_MAXDEG = 8192, B7_SLOTS = 16384;
 
+// Slots of the global-memory table of a hub of degree d: at most half full.
+__host__ __device__ __forceinline__ int64_t hub_table_slots(int64_t d) {
+  int64_t c = 32;
+  while (c < 2 * d) c <<= 1;
+  return c;
+}
+
 __host__ __device__ __forceinline__ int bucket_of(int64_t deg, bool overloaded) {
   if (!overloaded) {
     if (deg <= 4) return 0;
@@ -407,6 +417,10 @@ __device__ __forceinline__ uint32_t table_slot(int32_t C, int logcap) {
   return logcap == 0 ? 0u : (((uint32_t)C * 0x9E3779B1u) >> (32 - logcap));
 }
 
+// Message of a failed device allocation: the request, the device's free and
+// total memory, and what the allocator pool holds and uses.
+std::string alloc_failure_message(size_t bytes, cudaError_t e);
+
 // ---------------------------------------------------------------------------
 // Device buffers from the stream-ordered allocator.
 // ---------------------------------------------------------------------------
@@ -423,7 +437,16 @@ struct DevBuf {
     if (count && take_injected_alloc_failure())
       throw Error(SCLAP_ENOMEM, "device allocation failed (injected)");
     n = count;
-    if (count) SCLAP_CUDA(cudaMallocAsync((void**)&p, count * sizeof(T), st));
+    if (count) {
+      const cudaError_t e = cudaMallocAsync((void**)&p, count * sizeof(T), st);
+      if (e != cudaSuccess) {
+        p = nullptr;
+        n = 0;
+        cudaGetLastError();
+        throw Error(e == cudaErrorMemoryAllocation ? SCLAP_ENOMEM : SCLAP_ECUDA,
+                    alloc_failure_message(count * sizeof(T), e));
+      }
+    }
   }
   void release() {
     if (p) cudaFreeAsync(p, s);
@@ -464,8 +487,8 @@ void scan_excl_u8_to_i64(const uint8_t* in, int64_t* out, int64_t n, cudaStream_
 // out[i] = number of keys[0..i) that are >= 0 (occupied hash slots).
 void scan_excl_occupied(const int32_t* keys, int64_t* out, int64_t n, cudaStream_t s);
 // largest row length (atomicMax into *out, which the caller zeroes)
-// out[0] = largest degree of the level, out[1] = nodes with degree > thr
-// (out zeroed by the caller).
+// out[0] = largest degree of the level, out[1] = nodes with degree > thr,
+// out[2] = the table slots of those nodes together (out zeroed by the caller).
 void level_degree_stats(const int64_t* row_ptr, int64_t N, int64_t thr, int64_t* out,
                         cudaStream_t s);
 // slot id of every node from node offsets
@@ -579,6 +602,7 @@ struct SelectTask {            // choose the best trial of one graph, copy it ou
   int64_t dst_n0, n;
   int64_t slot0;               // first trial slot of the graph
   int32_t trials, k;
+  int32_t trial0;              // index of the first of these trials among all
   int64_t Lmax, g_boff;        // graph's block offset in the refinement block space
   int32_t g;
   const int64_t* rank;         // renumbering of the trial graphs (see CopyTask)
@@ -600,10 +624,15 @@ void waterfill_isolated(const std::vector<FillTask>& tasks, wgt_t* Wg, int64_t K
 void isolated_flags(const int64_t* row_ptr, const int32_t* nw, int64_t N, uint8_t* flags,
                     int32_t* iso_w, cudaStream_t s);
 // best[g], ipcut[g] on the device; block weights copied to Wg[g_boff..].
+// Trials may come in groups (one call per group, in increasing trial
+// order): best[g] < 0 means no trial yet; a group's best trial replaces the
+// kept one only if strictly better by (overload, cut), so the earliest of
+// equal trials wins, as with all trials at once.  rb_ov: overload of the
+// kept trial per graph.
 void ip_select_copy(const std::vector<SelectTask>& tasks, const int64_t* cut2,
                     const wgt_t* ip_W, const int64_t* ip_noff, const int64_t* ip_boff,
                     const int32_t* ip_label, wgt_t* Wg, int32_t* best, int64_t* ipcut,
-                    cudaStream_t s);
+                    int64_t* rb_ov, cudaStream_t s);
 // fine_blk[v] = coarse_blk[cmap[v]] where cmap[v] >= 0.
 // V-cycles: coarse_blk[cmap[v]] = fine_blk[v] for every fine node with
 // cmap[v] >= 0 (all members of a coarse node share one block).

@@ -447,7 +447,6 @@ void run_ip(const std::vector<IPIn>& in, const sclap_config& cfg, wgt_t* Wg,
             int32_t* d_err, cudaStream_t s) {
   const int B = (int)in.size();
   const int T = cfg.ip_trials;
-  const int S = B * T;
   // Trials run on the nodes that have neighbours: per level holding coarsest
   // graphs, rank them (scan of "has neighbours") and keep the isolated
   // nodes' weight prefix for the water-filling afterwards.
@@ -478,6 +477,31 @@ void run_ip(const std::vector<IPIn>& in, const sclap_config& cfg, wgt_t* Wg,
     aux.emplace_back(Q, std::move(x));
     return *aux.back().second;
   };
+  // Trials run in groups whose replicated graphs fit in memory (all of them
+  // at once unless the coarsest graphs are very large): about 200 bytes per
+  // node and 8 per arc of each trial copy (graph, growing and LP state),
+  // against half of the device memory still obtainable, or the tuning's
+  // group size.  Results do not depend on the grouping: a trial's
+  // arithmetic is independent of the others, and the best trial is kept
+  // across groups in trial order.
+  int64_t per_trial = 0;
+  for (int g = 0; g < B; ++g) {
+    const Level& Q = *in[g].Q;
+    LevelAux& X = aux_of(&Q);
+    const int x = in[g].g;
+    per_trial += 200 * (X.rank_at[x + 1] - X.rank_at[x]) + 8 * (Q.aoff[x + 1] - Q.aoff[x]) + 64;
+  }
+  const Tuning tu = tuning_get();
+  const int64_t fit = tu.ip_trial_group > 0
+                          ? tu.ip_trial_group
+                          : obtainable_device_bytes() / 2 / std::max<int64_t>(per_trial, 1);
+  const int TG = (int)std::max<int64_t>(1, std::min<int64_t>(T, fit));
+  DevBuf<int32_t> d_best(B, s);
+  DevBuf<int64_t> d_cut(B, s), d_ov(B, s);
+  d_best.fill_bytes(0xff);
+  for (int t0 = 0; t0 < T; t0 += TG) {
+  const int T = std::min(TG, cfg.ip_trials - t0);   // trials of this group
+  const int S = B * T;
   std::vector<int64_t> noff(S + 1, 0), aoff(S + 1, 0), boff(S + 1, 0);
   std::vector<CopyTask> tasks;
   tasks.reserve(S);
@@ -529,7 +553,7 @@ void run_ip(const std::vector<IPIn>& in, const sclap_config& cfg, wgt_t* Wg,
       const int i = g * T + t;
       h_avg[i] = in[g].avg;
       h_bound[i] = in[g].Lmax;
-      h_tkey[i] = hkey(in[g].seed, PH_TRIAL, (uint64_t)in[g].q, (uint64_t)t);
+      h_tkey[i] = hkey(in[g].seed, PH_TRIAL, (uint64_t)in[g].q, (uint64_t)(t0 + t));
       h_level[i] = in[g].q;
       h_nlab[i] = in[g].k;
     }
@@ -564,11 +588,11 @@ void run_ip(const std::vector<IPIn>& in, const sclap_config& cfg, wgt_t* Wg,
     const int x = in[g].g;
     LevelAux& X = aux_of(&Q);
     sel[g] = SelectTask{in[g].dst_blk, Q.noff[x], Q.noff[x + 1] - Q.noff[x], (int64_t)g * T, T,
-                        in[g].k, in[g].Lmax, in[g].boff, g, X.rank.p, X.rank_at[x]};
+                        in[g].k, t0, in[g].Lmax, in[g].boff, g, X.rank.p, X.rank_at[x]};
   }
-  DevBuf<int32_t> d_best(B, s);
-  DevBuf<int64_t> d_cut(B, s);
-  ip_select_copy(sel, cut2.p, W.p, ip.noff_d.p, d_boff.p, label.p, Wg, d_best.p, d_cut.p, s);
+  ip_select_copy(sel, cut2.p, W.p, ip.noff_d.p, d_boff.p, label.p, Wg, d_best.p, d_cut.p,
+                 d_ov.p, s);
+  }
   std::vector<FillTask> fill(B);
   int64_t Kmax = 0;
   for (int g = 0; g < B; ++g) {
@@ -1531,6 +1555,7 @@ void sclap_get_tuning(sclap_tuning* out) {
   out->pdl = t.pdl;
   out->fused_admission = t.fused_admission;
   out->contract_table_slots = t.contract_table_slots;
+  out->ip_trial_group = t.ip_trial_group;
 }
 
 int sclap_set_tuning(const sclap_tuning* in) {
@@ -1540,7 +1565,7 @@ int sclap_set_tuning(const sclap_tuning* in) {
         in->small_ctas_per_sm > 32 || in->warp_ctas_per_sm < 1 || in->warp_ctas_per_sm > 32 ||
         in->admit_ctas_per_sm < 1 || in->admit_ctas_per_sm > 64 || in->concurrent < 0 ||
         in->concurrent > 1 || in->pdl < 0 || in->pdl > 1 || in->fused_admission < 0 ||
-        in->fused_admission > 1 || in->contract_table_slots < 0)
+        in->fused_admission > 1 || in->contract_table_slots < 0 || in->ip_trial_group < 0)
       throw Error(SCLAP_EINVAL, "tuning value out of range");
     Tuning t;
     t.small_max_deg = in->small_max_deg;
@@ -1551,6 +1576,7 @@ int sclap_set_tuning(const sclap_tuning* in) {
     t.pdl = in->pdl;
     t.fused_admission = in->fused_admission;
     t.contract_table_slots = in->contract_table_slots;
+    t.ip_trial_group = in->ip_trial_group;
     tuning_set(t);
   });
 }

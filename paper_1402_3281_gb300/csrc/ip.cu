@@ -455,7 +455,8 @@ __global__ void k_select_copy(const SelectTask* __restrict__ tasks, const int64_
                               const wgt_t* __restrict__ ip_W, const int64_t* __restrict__ ip_noff,
                               const int64_t* __restrict__ ip_boff,
                               const int32_t* __restrict__ ip_label, wgt_t* __restrict__ Wg,
-                              int32_t* __restrict__ best, int64_t* __restrict__ ipcut) {
+                              int32_t* __restrict__ best, int64_t* __restrict__ ipcut,
+                              int64_t* __restrict__ rb_ov) {
   const SelectTask t = tasks[blockIdx.x];
   __shared__ int32_t bt_sh;
   if (threadIdx.x == 0) {
@@ -469,11 +470,16 @@ __global__ void k_select_copy(const SelectTask* __restrict__ tasks, const int64_
       const int64_t c = cut2[slot] / 2;
       if (bt < 0 || ov < bo || (ov == bo && c < bc)) { bo = ov; bc = c; bt = tr; }
     }
-    bt_sh = bt;
-    best[t.g] = bt;
-    ipcut[t.g] = bc;
+    const bool take = best[t.g] < 0 || bo < rb_ov[t.g] || (bo == rb_ov[t.g] && bc < ipcut[t.g]);
+    if (take) {
+      best[t.g] = t.trial0 + bt;
+      ipcut[t.g] = bc;
+      rb_ov[t.g] = bo;
+    }
+    bt_sh = take ? bt : -1;
   }
   __syncthreads();
+  if (bt_sh < 0) return;
   const int64_t slot = t.slot0 + bt_sh;
   const int64_t src = ip_noff[slot], sbo = ip_boff[slot];
   for (int64_t v = threadIdx.x; v < t.n; v += blockDim.x) {
@@ -672,12 +678,12 @@ void slot_cut(const LevelView& lv, const int32_t* label, int64_t* cut2, cudaStre
 void ip_select_copy(const std::vector<SelectTask>& tasks, const int64_t* cut2,
                     const wgt_t* ip_W, const int64_t* ip_noff, const int64_t* ip_boff,
                     const int32_t* ip_label, wgt_t* Wg, int32_t* best, int64_t* ipcut,
-                    cudaStream_t s) {
+                    int64_t* rb_ov, cudaStream_t s) {
   if (tasks.empty()) return;
   DevBuf<SelectTask> d(tasks.size(), s);
   d.upload(tasks);
   k_select_copy<<<(unsigned)tasks.size(), 256, 0, s>>>(d.p, cut2, ip_W, ip_noff, ip_boff,
-                                                       ip_label, Wg, best, ipcut); SCLAP_NOTE_LAUNCH("k_select_copy");
+                                                       ip_label, Wg, best, ipcut, rb_ov); SCLAP_NOTE_LAUNCH("k_select_copy");
   SCLAP_LAUNCH_CHECK();
   stream_sync(s);   // the task array is freed on return
 }

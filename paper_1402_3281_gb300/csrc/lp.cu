@@ -658,13 +658,14 @@ constexpr size_t blk_smem_bytes() {
          (size_t)(SLOTS / 2) * sizeof(int32_t);
 }
 
-// GLOBAL (hubs, degree above 8192): the same per-node procedure, with each
-// CTA's table (gcap slots) and created list in a region of global memory
-// that stays clean between nodes (created slots are reset after each node).
+// GLOBAL (hubs, degree above 8192): the same per-node procedure, with the
+// node's table (hub_table_slots(degree) slots) and created list in its own
+// region of global memory, at hoff[li] (list at hoff[li] / 2); the CTA
+// clears the region before using it.
 template <int NT, int SLOTS, bool GLOBAL>
 __global__ void __launch_bounds__(NT) k_propose_blk(LPArgs a, int32_t sub, int32_t bucket,
                                                     int32_t* gkeys, unsigned long long* gvals,
-                                                    int32_t* glist, int64_t gcap) {
+                                                    int32_t* glist, const int64_t* hoff) {
   griddep_wait();
   int64_t lbeg, cnt;
   sub_range(a, sub, bucket, bucket + 1, &lbeg, &cnt);
@@ -679,10 +680,10 @@ __global__ void __launch_bounds__(NT) k_propose_blk(LPArgs a, int32_t sub, int32
   int64_t tcap;
   const int tid = threadIdx.x, lane = tid & 31;
   if (GLOBAL) {
-    vals = gvals + (int64_t)blockIdx.x * gcap;
-    keys = gkeys + (int64_t)blockIdx.x * gcap;
-    clist = glist + (int64_t)blockIdx.x * (gcap / 2);
-    tcap = gcap;
+    vals = gvals;
+    keys = gkeys;
+    clist = glist;
+    tcap = 0;
   } else {
     vals = smem_u64;
     keys = reinterpret_cast<int32_t*>(smem_u64 + SLOTS);
@@ -695,6 +696,15 @@ __global__ void __launch_bounds__(NT) k_propose_blk(LPArgs a, int32_t sub, int32
   for (int64_t li = blockIdx.x; li < cnt; li += gridDim.x) {
     const int64_t i = lbeg + li;
     const NodeCtx c = load_node(a, i);
+    if (GLOBAL) {
+      const int64_t off = hoff[li];
+      tcap = hub_table_slots(c.re - c.rs);
+      vals = gvals + off;
+      keys = gkeys + off;
+      clist = glist + off / 2;
+      for (int64_t j = tid; j < tcap; j += NT) { keys[j] = -1; vals[j] = 0; }
+      __syncthreads();
+    }
     const bool ov = a.mode != MODE_CLUSTER && a.W[c.own] > c.bound;
     const int32_t nl = a.mode != MODE_CLUSTER ? a.nlab[c.slot] : 0;
     const bool direct = a.mode != MODE_CLUSTER && nl <= tcap;
@@ -800,6 +810,47 @@ __global__ void __launch_bounds__(NT) k_propose_blk(LPArgs a, int32_t sub, int32
     }
     __syncthreads();
   }
+}
+
+// Table regions of the hubs of colour class `sub`: hoff[li] = exclusive
+// prefix of hub_table_slots(degree) over the class's hub list (one CTA,
+// chunks of its size with a running carry); hoff[cnt] = the total.
+constexpr int HO_NT = 1024;
+__global__ void __launch_bounds__(HO_NT) k_hub_offsets(LPArgs a, int32_t sub, int64_t* hoff) {
+  griddep_wait();
+  __shared__ int64_t sh[HO_NT / 32];
+  __shared__ int64_t carry;
+  int64_t lbeg, cnt;
+  sub_range(a, sub, NB - 1, NB, &lbeg, &cnt);
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  for (int64_t b0 = 0; b0 < cnt; b0 += HO_NT) {
+    const int64_t li = b0 + threadIdx.x;
+    const int64_t x = li < cnt ? hub_table_slots(a.rec2[lbeg + li].y) : 0;
+    int64_t incl = x;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) sh[wib] = incl;
+    __syncthreads();
+    if (wib == 0) {
+      int64_t t = sh[lane];
+      for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, t, o);
+        if (lane >= o) t += y;
+      }
+      sh[lane] = t;                       // inclusive over warps
+    }
+    __syncthreads();
+    const int64_t before = carry + (wib ? sh[wib - 1] : 0);
+    if (li < cnt) hoff[li] = before + incl - x;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += sh[HO_NT / 32 - 1];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) hoff[cnt] = carry;
 }
 
 // ------------------------------------------------------------- admission
@@ -1406,11 +1457,9 @@ void tuning_set(const Tuning& t) {
   g_tune = t;
 }
 
-int64_t table_pass_slots() {
-  const Tuning t = tuning_get();
-  if (t.contract_table_slots > 0) return t.contract_table_slots;
+std::string alloc_failure_message(size_t bytes, cudaError_t e) {
   size_t fr = 0, tot = 0;
-  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return (int64_t)1 << 30;
+  cudaMemGetInfo(&fr, &tot);
   int dev = 0;
   cudaGetDevice(&dev);
   cudaMemPool_t pool;
@@ -1419,8 +1468,37 @@ int64_t table_pass_slots() {
     cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved);
     cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used);
   }
-  const int64_t avail = (int64_t)fr + (int64_t)(reserved > used ? reserved - used : 0);
-  return std::max<int64_t>((int64_t)1 << 20, avail / 2 / 12);
+  cudaGetLastError();
+  char buf[320];
+  snprintf(buf, sizeof(buf),
+           "device allocation of %.3f GB failed (%s); device free %.3f of %.3f GB, "
+           "pool reserved %.3f GB, in use %.3f GB",
+           bytes / 1e9, cudaGetErrorString(e), fr / 1e9, tot / 1e9, reserved / 1e9, used / 1e9);
+  return buf;
+}
+
+int64_t table_pass_slots() {
+  const Tuning t = tuning_get();
+  if (t.contract_table_slots > 0) return t.contract_table_slots;
+  return std::max<int64_t>((int64_t)1 << 20, obtainable_device_bytes() / 2 / 12);
+}
+
+int64_t obtainable_device_bytes() {
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+    cudaGetLastError();
+    return (int64_t)1 << 32;
+  }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaMemPool_t pool;
+  uint64_t reserved = 0, used = 0;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved);
+    cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used);
+  }
+  cudaGetLastError();
+  return (int64_t)fr + (int64_t)(reserved > used ? reserved - used : 0);
 }
 
 // Stream on which this thread captures graphs (non-blocking, created once).
@@ -1572,12 +1650,24 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, wgt_t*
     act_b.zero();
   }
 
-  // Global hash scratch for hub nodes: one region per CTA, sized for the
-  // largest degree of the level.
-  int64_t gcap = 0;
+  // Global hash tables of hub nodes: a region per hub of a colour class,
+  // sized to its degree (hub_table_slots), in a pool sized for the class's
+  // hubs (host-driven rounds: 4 slots per arc + 32 per hub of the class, a
+  // bound of the sum; CUDA-graph rounds: the sum over all hubs of the
+  // level).
+  int64_t pool_slots = 0;
   DevBuf<int32_t> gkeys, glist;
   DevBuf<unsigned long long> gvals;
+  DevBuf<int64_t> hub_off;
   int gblocks = 0;
+  auto ensure_pool = [&](int64_t slots) {
+    if (slots <= pool_slots) return;
+    slots = std::max<int64_t>(slots, 1024);
+    gkeys.alloc((size_t)slots, s);
+    gvals.alloc((size_t)slots, s);
+    glist.alloc((size_t)(slots / 2), s);
+    pool_slots = slots;
+  };
 
   LPArgs a{};
   a.row_ptr = lv.row_ptr; a.col = lv.col; a.ew = lv.ew; a.nw = lv.nw; a.gid = lv.gid;
@@ -1615,13 +1705,13 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, wgt_t*
 
   // The level's degrees decide which propose launches can ever have work
   // (and size the hub tables): one read-back per run, none per round.
-  DevBuf<int64_t> dstat(2, s);
+  DevBuf<int64_t> dstat(3, s);
   dstat.zero();
   level_degree_stats(lv.row_ptr, N, B7_MAXDEG, dstat.p, s);
-  int64_t hstat[2] = {0, 0};
+  int64_t hstat[3] = {0, 0, 0};
   SCLAP_CUDA(cudaMemcpyAsync(hstat, dstat.p, sizeof(hstat), cudaMemcpyDeviceToHost, s));
   stream_sync(s);
-  const int64_t maxdeg = hstat[0], nhubs = hstat[1];
+  const int64_t maxdeg = hstat[0], nhubs = hstat[1], hub_slots = hstat[2];
   const bool refine = run.mode != MODE_CLUSTER;
   const Tuning tu = tuning_get();
   const int nsb = tu.small_max_deg >= 16 ? 3 : 2;   // buckets of the thread-per-node launch
@@ -1629,13 +1719,9 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, wgt_t*
                          maxdeg > B4_MAXDEG, maxdeg > B5_MAXDEG, maxdeg > B6_MAXDEG,
                          maxdeg > B7_MAXDEG};
   if (need[8]) {
-    gcap = (int64_t)1 << ceil_log2(std::max<int64_t>(2 * maxdeg, 32));
     gblocks = (int)std::max<int64_t>(1, std::min<int64_t>(sms * 2, nhubs));
-    gkeys.alloc((size_t)(gblocks * gcap), s);
-    gvals.alloc((size_t)(gblocks * gcap), s);
-    glist.alloc((size_t)(gblocks * (gcap / 2)), s);
-    gkeys.fill_bytes(0xff);
-    gvals.zero();
+    hub_off.alloc((size_t)(nhubs + 1), s);
+    if (run.graph) ensure_pool(hub_slots);
   }
   constexpr size_t smem5 = blk_smem_bytes<B5_SLOTS>();
   constexpr size_t smem6 = blk_smem_bytes<B6_SLOTS>();
@@ -1683,6 +1769,12 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, wgt_t*
   // offsets (direct driver) empty launches are skipped and, when profiling,
   // each launch is timed and its nodes and arcs tallied by family.
   auto propose = [&](cudaStream_t s, int sub, bool fork, const int64_t* ho, bool pdl) {
+    // the hub pool grows on the round's stream before the fork, so the side
+    // streams see the allocation
+    if (need[8] && ho) {
+      const int64_t nh = ho[sub * NB + 9] - ho[sub * NB + 8];
+      if (nh > 0) ensure_pool(4 * hkarcs[sub * NB + 8] + 32 * nh);
+    }
     cudaEvent_t ev_fork = nullptr;
     if (fork) {
       ev_fork = sync_event_get();
@@ -1741,16 +1833,17 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, wgt_t*
       launch_k(p, k_propose_warp, grid(nsb, 5, WPC, grid_warp), WPC * 32, 0, ls, a, sub, nsb); SCLAP_NOTE_LAUNCH("k_propose_warp");
     });
     if (need[5]) launch(5, 6, 1, [&](cudaStream_t ls, bool p) {
-      launch_k(p, k_propose_blk<128, B5_SLOTS, false>, grid(5, 6, 1, grid_b5), 128, smem5, ls, a, sub, 5, no_i, no_u, no_i, (int64_t)0); SCLAP_NOTE_LAUNCH("k_propose_blk128");
+      launch_k(p, k_propose_blk<128, B5_SLOTS, false>, grid(5, 6, 1, grid_b5), 128, smem5, ls, a, sub, 5, no_i, no_u, no_i, (const int64_t*)nullptr); SCLAP_NOTE_LAUNCH("k_propose_blk128");
     });
     if (need[6]) launch(6, 7, 2, [&](cudaStream_t ls, bool p) {
-      launch_k(p, k_propose_blk<256, B6_SLOTS, false>, grid(6, 7, 1, grid_b6), 256, smem6, ls, a, sub, 6, no_i, no_u, no_i, (int64_t)0); SCLAP_NOTE_LAUNCH("k_propose_blk256");
+      launch_k(p, k_propose_blk<256, B6_SLOTS, false>, grid(6, 7, 1, grid_b6), 256, smem6, ls, a, sub, 6, no_i, no_u, no_i, (const int64_t*)nullptr); SCLAP_NOTE_LAUNCH("k_propose_blk256");
     });
     if (need[7]) launch(7, 8, 2, [&](cudaStream_t ls, bool p) {
-      launch_k(p, k_propose_blk<512, B7_SLOTS, false>, grid(7, 8, 1, grid_b7), 512, smem7, ls, a, sub, 7, no_i, no_u, no_i, (int64_t)0); SCLAP_NOTE_LAUNCH("k_propose_blk512");
+      launch_k(p, k_propose_blk<512, B7_SLOTS, false>, grid(7, 8, 1, grid_b7), 512, smem7, ls, a, sub, 7, no_i, no_u, no_i, (const int64_t*)nullptr); SCLAP_NOTE_LAUNCH("k_propose_blk512");
     });
     if (need[8]) launch(8, 9, 3, [&](cudaStream_t ls, bool p) {
-      launch_k(p, k_propose_blk<512, 1, true>, (unsigned)gblocks, 512, 0, ls, a, sub, 8, gkeys.p, gvals.p, glist.p, gcap); SCLAP_NOTE_LAUNCH("k_propose_hub");
+      launch_k(p, k_hub_offsets, 1, HO_NT, 0, ls, a, sub, hub_off.p); SCLAP_NOTE_LAUNCH("k_hub_offsets");
+      launch_k(tu.pdl != 0, k_propose_blk<512, 1, true>, (unsigned)gblocks, 512, 0, ls, a, sub, 8, gkeys.p, gvals.p, glist.p, (const int64_t*)hub_off.p); SCLAP_NOTE_LAUNCH("k_propose_hub");
     });
     if (fork) {
       for (int j = 0; j < nside; ++j) {

@@ -128,25 +128,31 @@ __global__ void k_fill_gid(const int64_t* __restrict__ noff, int32_t nslots,
   }
 }
 
-// Largest degree of a level (out[0]) and the number of nodes whose degree
-// exceeds thr (out[1]).
+// Largest degree of a level (out[0]), the number of nodes whose degree
+// exceeds thr (out[1]), and the table slots those nodes need together
+// (out[2]: the sum of hub_table_slots over them).
 __global__ void k_degree_stats(const int64_t* __restrict__ row_ptr, int64_t N, int64_t thr,
                                unsigned long long* out) {
-  unsigned long long m = 0, c = 0;
+  unsigned long long m = 0, c = 0, t = 0;
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N;
        v += (int64_t)gridDim.x * blockDim.x) {
     const int64_t d = row_ptr[v + 1] - row_ptr[v];
     m = (unsigned long long)d > m ? (unsigned long long)d : m;
-    c += d > thr ? 1ull : 0ull;
+    if (d > thr) {
+      c += 1;
+      t += (unsigned long long)hub_table_slots(d);
+    }
   }
   for (int o = 16; o > 0; o >>= 1) {
     const unsigned long long y = __shfl_xor_sync(0xffffffffu, m, o);
     m = y > m ? y : m;
     c += __shfl_xor_sync(0xffffffffu, c, o);
+    t += __shfl_xor_sync(0xffffffffu, t, o);
   }
   if ((threadIdx.x & 31) == 0) {
     if (m) atomicMax(&out[0], m);
     if (c) atomicAdd(&out[1], c);
+    if (t) atomicAdd(&out[2], t);
   }
 }
 

@@ -13,7 +13,7 @@ import oracle as O
 import paper_1402_3281_gb300 as P
 
 DEFAULT = dict(small_max_deg=16, small_ctas_per_sm=8, warp_ctas_per_sm=8, admit_ctas_per_sm=16,
-               concurrent=1, pdl=1, fused_admission=0, contract_table_slots=0)
+               concurrent=1, pdl=1, fused_admission=0, contract_table_slots=0, ip_trial_group=0)
 
 
 @pytest.fixture
@@ -33,7 +33,7 @@ def test_default_tuning(restore_tuning):
                                        ("admit_ctas_per_sm", 65), ("concurrent", 2),
                                        ("concurrent", -1), ("pdl", 2),
                                        ("fused_admission", 2), ("fused_admission", -1),
-                                       ("contract_table_slots", -5)])
+                                       ("contract_table_slots", -5), ("ip_trial_group", -1)])
 def test_out_of_range_values_are_rejected_and_leave_the_setting(restore_tuning, field, bad):
     P.set_tuning(**DEFAULT)
     with pytest.raises(P.SclapError) as e:
@@ -45,10 +45,10 @@ def test_out_of_range_values_are_rejected_and_leave_the_setting(restore_tuning, 
 def test_set_tuning_round_trip(restore_tuning):
     t = P.set_tuning(small_max_deg=8, small_ctas_per_sm=3, warp_ctas_per_sm=32,
                      admit_ctas_per_sm=1, concurrent=0, pdl=0, fused_admission=1,
-                     contract_table_slots=4096)
+                     contract_table_slots=4096, ip_trial_group=3)
     assert t.to_dict() == dict(small_max_deg=8, small_ctas_per_sm=3, warp_ctas_per_sm=32,
                                admit_ctas_per_sm=1, concurrent=0, pdl=0, fused_admission=1,
-                               contract_table_slots=4096)
+                               contract_table_slots=4096, ip_trial_group=3)
 
 
 # ------------------------------------------------------------------ GPU
@@ -75,6 +75,8 @@ SETTINGS = [
     dict(fused_admission=1, admit_ctas_per_sm=1, concurrent=0),
     dict(contract_table_slots=4096),      # contraction in passes of 4096 slots
     dict(contract_table_slots=1),         # a pass per coarse node
+    dict(ip_trial_group=1),               # initial-partitioning trials one at a time
+    dict(ip_trial_group=5),               # groups of 5, 5, 5 and 1 of the 16 trials
 ]
 
 
