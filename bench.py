@@ -61,11 +61,14 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-single", action="store_true")
-    ap.add_argument("--workload", default="batched", choices=["batched", "large", "huge"],
+    ap.add_argument("--workload", default="batched",
+                    choices=["batched", "large", "huge", "serve", "cpu"],
                     help="batched: the 512-graph batch (default); large: R-MAT scale 22 and "
                          "RGG 2^22, one graph per call, both round drivers; huge: one R-MAT "
                          "graph of --scale (default 27, edge factor 24) generated on the "
-                         "device, k = 16")
+                         "device, k = 16; serve: Poisson request streams of mixed R-MAT and "
+                         "RGG graphs through the server; cpu: the CPU oracles (sequential "
+                         "and round-synchronous) on one host core")
     ap.add_argument("--scale", type=int, default=27, help="R-MAT scale of --workload huge")
     ap.add_argument("--graph-rounds", action="store_true",
                     help="run each level's LP rounds as one CUDA graph (device-side loop)")
@@ -242,12 +245,75 @@ def reference_arm(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": config_dict(args.count, 1),
+        "config": dict(config_dict(args.count, 1),
+                       sample="each step partitions the first 16 graphs of the batch (a "
+                              "bounded sample: the whole batch takes the oracle ~12 s); "
+                              "value = partitions/s over the sample"),
         "cpu_baseline": {"value": value, "unit": "partitions/s", "cores": 1, "kind": "oracle",
                          "sample": f"first {len(sample)} graphs of the batch per step, "
                                    "round-synchronous oracle, single thread"},
         "e2e": {"value": value, "unit": "partitions/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_model():
+    """The host's CPU model and core count, as the OS reports them."""
+    model = ""
+    try:
+        for line in open("/proc/cpuinfo"):
+            key = line.split(":")[0].strip().lower()
+            if key in ("model name", "cpu model", "hardware") and not model:
+                model = line.split(":", 1)[1].strip()
+            if key == "cpu part" and not model:
+                model = "ARM part " + line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return {"model": model or platform.processor() or platform.machine(),
+            "machine": platform.machine(), "nproc": os.cpu_count()}
+
+
+def cpu_workload(args):
+    """CPU baseline of the plan: the paper's sequential SCLaP (increasing-
+    degree order, immediate moves, FIFO active-node queues) and the
+    round-synchronous variant the GPU follows, both single-threaded oracles,
+    on the single-graph workload (R-MAT scale 16, edge factor 8, k = 2,
+    eps = 0.03), seeds 0-4: wall time best and median, mean cut; and
+    partitions/s of both over a bounded sample of the 512-graph batch."""
+    import oracle as O
+    O.build()
+    g = gg.rmat(16, 8, 0)
+    out = {}
+    for name, var in (("sequential", O.SEQ), ("synchronous", O.SYNC)):
+        ts, cuts = [], []
+        for seed in range(5):
+            t0 = time.perf_counter()
+            r = O.partition(g, 2, 0.03, seed=seed, variant=var)
+            ts.append(time.perf_counter() - t0)
+            cuts.append(r.cut)
+        ts.sort()
+        out[name] = {"best_s": ts[0], "median_s": ts[2], "mean_cut": float(np.mean(cuts)),
+                     "cuts": cuts}
+    batch = workload(512, 0)
+    sample = batch[::16][:32]            # 32 graphs spread over the batch
+    rates = {}
+    for name, var in (("sequential", O.SEQ), ("synchronous", O.SYNC)):
+        t0 = time.perf_counter()
+        for bg, k, eps in sample:
+            O.partition(bg, k, eps, seed=0, variant=var)
+        rates[name] = len(sample) / (time.perf_counter() - t0)
+    line = {
+        "metric": "seconds per partition (CPU oracle, 1 thread)", "unit": "s",
+        "higher_is_better": False, "data": "synthetic",
+        "config": {"workload": "R-MAT scale 16 ef 8 (65,536 nodes), k = 2, eps 0.03, seeds 0-4; "
+                               "and every 16th graph of the 512-graph batch (32 graphs)",
+                   "threads": 1},
+        "host": cpu_model(),
+        "single_graph": out,
+        "batch_sample_partitions_per_s": rates,
+        "sync_over_seq_mean_cut": out["synchronous"]["mean_cut"] / out["sequential"]["mean_cut"],
     }
     print(json.dumps(line), flush=True)
 
@@ -310,6 +376,106 @@ def serve_stream(P, graphs, lam, count, ref_cuts, seed=0):
     return {"lambda_per_s": lam, "requests": count, "p50_ms": q(0.50), "p99_ms": q(0.99),
             "partitions_per_s": count / (t1 - t0), "offered_per_s": count / float(gaps.sum()),
             "equal_cut": bool(same)}
+
+
+def serve_request(i, seed=0):
+    """Request i of the serving mix: even i an R-MAT graph with scale
+    uniform in 12..20 (edge factor 8), odd i a 2D RGG with 2^u nodes, u
+    uniform in [12, 20]; k uniform in {2, 4, 8, 16, 32, 64}; eps uniform in
+    {0.01, 0.03, 0.05}; a partition seed of its own.  (Graph, k, eps, seed)."""
+    rng = np.random.default_rng(np.random.SeedSequence([0x53455256, seed, i]))
+    k = int(rng.choice([2, 4, 8, 16, 32, 64]))
+    eps = float(rng.choice([0.01, 0.03, 0.05]))
+    pseed = int(rng.integers(0, 2**31))
+    if i % 2 == 0:
+        g = gg.rmat(int(rng.integers(12, 21)), 8, seed=7000 + i)
+    else:
+        g = gg.rgg2d(int(round(2.0 ** rng.uniform(12, 20))), seed=7000 + i)
+    return g, k, eps, pseed
+
+
+def serve_workload(args):
+    """C5-style serving: a pool of 96 requests of the serving mix, submitted
+    as open-loop Poisson streams at 50 to 2000 requests/s through the server
+    (host arrays, default options: 2 workers, 120 GiB admission budget); each
+    result must equal the same request partitioned alone.  Reported per
+    rate: p50/p99 latency from submit to completion and completed
+    partitions/s; and the one-at-a-time rate of the same requests."""
+    import threading
+    import multiprocessing as mp
+    import torch
+    import paper_1402_3281_gb300 as P
+    P.load()
+    torch.cuda.set_device(0)
+    pool_n = 96
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        reqs = pool.starmap(serve_request, [(i, 0) for i in range(pool_n)])
+    sampler = ClockSampler(0)
+    sampler.start()
+    for g, k, eps, sd in reqs[:8]:                       # warm-up
+        P.sclap_partition(g.row_ptr, g.col, k=k, eps=eps, seed=sd)
+    torch.cuda.synchronize()
+    sampler.mark()
+    t0 = time.perf_counter()
+    alone = [P.sclap_partition(g.row_ptr, g.col, k=k, eps=eps, seed=sd) for g, k, eps, sd in reqs]
+    plain_s = time.perf_counter() - t0
+    ref = [(r.cut, r.block) for r in alone]
+    runs = []
+    for lam in (50, 200, 500, 1000, 2000):
+        count = int(min(384, max(96, 2 * lam)))
+        rng = np.random.default_rng(np.random.SeedSequence([0x50535452, lam, count]))
+        gaps = rng.exponential(1.0 / lam, size=count)
+        ids = [None] * count
+        ready = [threading.Event() for _ in range(count)]
+        with P.Server() as srv:
+            def feeder():
+                t_next = time.perf_counter()
+                for i in range(count):
+                    t_next += gaps[i]
+                    d = t_next - time.perf_counter()
+                    if d > 0:
+                        time.sleep(d)
+                    g, k, eps, sd = reqs[i % pool_n]
+                    ids[i] = srv.submit(g.row_ptr, g.col, None, None, k, eps, sd)
+                    ready[i].set()
+            th = threading.Thread(target=feeder)
+            s0 = time.perf_counter()
+            th.start()
+            lat, same = [], True
+            for i in range(count):
+                ready[i].wait()
+                r = srv.poll(ids[i], -1)
+                lat.append(r.latency_ms)
+                c, b = ref[i % pool_n]
+                same &= r.cut == c and bool(np.array_equal(r.block, b))
+            s1 = time.perf_counter()
+            th.join()
+        lat.sort()
+        q = lambda f: lat[min(len(lat) - 1, int(f * len(lat)))]
+        runs.append({"lambda_per_s": lam, "requests": count, "p50_ms": q(0.50),
+                     "p99_ms": q(0.99), "partitions_per_s": count / (s1 - s0),
+                     "offered_per_s": count / float(gaps.sum()), "equal_to_alone": bool(same)})
+    clocks = sampler.stop()
+    best = max(r["partitions_per_s"] for r in runs)
+    h2d = sum(g.row_ptr.nbytes + g.col.nbytes for g, _, _, _ in reqs) / pool_n
+    line = {
+        "metric": "partitions/s", "value": best, "unit": "partitions/s", "n_gpus": 1,
+        "higher_is_better": True, "data": "synthetic", "dtype": "int32",
+        "config": {"workload": "serving: open-loop Poisson streams at 50/200/500/1000/2000 "
+                               "req/s over a pool of 96 requests (even: R-MAT scale U[12,20] ef 8, "
+                               "odd: 2D RGG 2^U[12,20] nodes; k U{2,4,8,16,32,64}; eps "
+                               "U{0.01,0.03,0.05}); host arrays through sclap_server_* (2 workers, "
+                               "120 GiB admission budget)",
+                   "pool_nodes": int(sum(g.n for g, _, _, _ in reqs)),
+                   "pool_arcs": int(sum(g.arcs for g, _, _, _ in reqs))},
+        "plain_partitions_per_s": pool_n / plain_s,
+        "served_vs_plain": best / (pool_n / plain_s),
+        "runs": runs,
+        "e2e": {"value": best, "unit": "partitions/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(sum(4 * g.n for g, _, _, _ in reqs) / pool_n)},
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
 
 
 def large_graphs():
@@ -454,6 +620,12 @@ def main():
         return
     if args.workload == "huge":
         huge_workload(args)
+        return
+    if args.workload == "serve":
+        serve_workload(args)
+        return
+    if args.workload == "cpu":
+        cpu_workload(args)
         return
     if args.impl == "reference":
         reference_arm(args)
