@@ -610,6 +610,18 @@ def huge_workload(args):
         line.update(value=None, error=str(e),
                     torch_reserved_gb=torch.cuda.memory_reserved() / 1e9)
     line["clocks"] = sampler.stop()
+    if args.timeline and line.get("value"):
+        # one more call with an event after every launch: time per kernel
+        P.sclap_profile_dump()
+        P.sclap_profile_timeline(True)
+        P.sclap_partition_device(rp, col, k=16, eps=0.03, seed=0)
+        torch.cuda.synchronize()
+        P.sclap_profile_timeline(False)
+        tl = P.sclap_profile_dump()
+        tot = sum(v[1] for v in tl.values())
+        print(f"timeline of one call: {tot:.2f} ms", file=sys.stderr)
+        for name, (cnt, ms) in sorted(tl.items(), key=lambda x: -x[1][1]):
+            print(f"  {name:28s} {cnt:7d} {ms:10.3f} ms {100 * ms / tot:6.1f}%", file=sys.stderr)
     print(json.dumps(line), flush=True)
 
 

@@ -154,7 +154,10 @@ __device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int* p) {
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
-__device__ __forceinline__ bool grid_sync(GridSync* gs, int32_t* err, uint32_t limit) {
+// Barrier of the `nblocks` CTAs that share `gs` (a group of CTAs of a
+// cooperative launch, or the whole grid: grid_sync).
+__device__ __forceinline__ bool group_sync(GridSync* gs, unsigned int nblocks, int32_t* err,
+                                           uint32_t limit) {
   __shared__ int sh_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -162,7 +165,7 @@ __device__ __forceinline__ bool grid_sync(GridSync* gs, int32_t* err, uint32_t l
     const unsigned int g = ld_acquire_gpu(&gs->gen);
     __threadfence();
     const unsigned int prev = atomicAdd(&gs->arrive, 1u);
-    if (prev == gridDim.x - 1) {
+    if (prev == nblocks - 1) {
       gs->arrive = 0;
       __threadfence();
       atomicAdd(&gs->gen, 1u);
@@ -182,6 +185,9 @@ __device__ __forceinline__ bool grid_sync(GridSync* gs, int32_t* err, uint32_t l
   }
   __syncthreads();
   return sh_ok != 0;
+}
+__device__ __forceinline__ bool grid_sync(GridSync* gs, int32_t* err, uint32_t limit) {
+  return group_sync(gs, gridDim.x, err, limit);
 }
 
 // Iteration limit of every bounded device-side wait (about 2 s at the
@@ -592,6 +598,7 @@ struct GGGArgs {
   int32_t nslots;
   const int32_t* order;    // trial slots in the order they are taken (set by ggg_trials)
   int32_t* next;           // queue position (set by ggg_trials)
+  int32_t* err;            // device error word (bounded waits of the grouped kernel)
 };
 // noff: host copy of the trial slot node offsets [nslots + 1].
 void ggg_trials(const GGGArgs& a, const std::vector<int64_t>& noff, cudaStream_t s);

@@ -568,6 +568,7 @@ void run_ip(const std::vector<IPIn>& in, const sclap_config& cfg, wgt_t* Wg,
   ga.tkey = sl.seed.p; ga.level = sl.level.p; ga.label = label.p; ga.W = W.p;
   ga.conn = conn.p; ga.step = step.p; ga.front = front.p; ga.wfA = wfA.p; ga.wforder = wforder.p;
   ga.nslots = S;
+  ga.err = d_err;
   ggg_trials(ga, noff, s);
 
   LPRun run;

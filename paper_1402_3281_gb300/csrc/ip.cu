@@ -377,6 +377,297 @@ __global__ void __launch_bounds__(GNT) k_ggg(GGGArgs a) {
   }
 }
 
+// ------------------------------------------------------------------------
+// Greedy growing of few, large trials: each trial is grown by a group of cpt
+// CTAs of one cooperative launch (CTAs g * cpt .. g * cpt + cpt - 1 grow
+// trial slot g), with the same rules as k_ggg.  The group shares the
+// trial's step and front lists and a few counters in global memory and
+// meets at a barrier of its own (bounded wait: a wait that runs out sets
+// DERR_TIMEOUT and the group leaves).  Each CTA owns a contiguous range of
+// the trial's nodes for the scans (seed search, ordered candidates,
+// water-filling); id-ordered prefixes over the whole trial are the CTAs'
+// partial sums in rank order plus the CTA's own scan.  The step nodes'
+// arcs are shared out by step node in chunks of GG_NT per CTA.  Every
+// decision is a set or an id-ordered prefix, so the result equals k_ggg's.
+struct GroupState {
+  GridSync bar;
+  int32_t nstep, nfront, nnext, seed;
+  int64_t Wj, fsum, accw;
+};
+constexpr int GG_NT = 512;
+
+__global__ void __launch_bounds__(GG_NT) k_ggg_group(GGGArgs a, int32_t cpt, GroupState* gst,
+                                                     uint64_t* ph, int32_t* pv, int64_t* pw,
+                                                     uint32_t lim) {
+  __shared__ int64_t sh[33];
+  __shared__ uint64_t shh[GG_NT / 32];
+  __shared__ int32_t shv[GG_NT / 32];
+  __shared__ int64_t st_rs[GG_NT], st_ex[GG_NT], st_in[GG_NT];
+  __shared__ int64_t pre_sh, tot_sh;
+  __shared__ int32_t seed_sh;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int32_t s = (int32_t)(blockIdx.x / cpt);
+  const int r = (int)(blockIdx.x % cpt);
+  GroupState* st = gst + s;
+  uint64_t* gph = ph + (int64_t)s * cpt;
+  int32_t* gpv = pv + (int64_t)s * cpt;
+  int64_t* gpw = pw + (int64_t)s * cpt;
+  const int64_t base = a.noff[s], n = a.noff[s + 1] - base;
+  const int32_t k = a.nlab[s];
+  const int64_t bo = a.boff[s], avg = a.avg[s];
+  const uint64_t tkey = a.tkey[s];
+  const int32_t lvl = a.level[s];
+  const int64_t r0 = n * r / cpt, r1 = n * (r + 1) / cpt;   // this CTA's node range
+  const int64_t qstride = (int64_t)GG_NT * cpt;            // step-list share-out
+  auto sync = [&]() { return group_sync(&st->bar, (unsigned)cpt, a.err, lim); };
+  // exclusive prefix and total over the CTAs of the group of the values
+  // they left in gpw (after a barrier)
+  auto group_prefix = [&]() {
+    if (tid == 0) {
+      int64_t p = 0, t = 0;
+      for (int q = 0; q < cpt; ++q) {
+        const int64_t x = *(volatile int64_t*)&gpw[q];
+        if (q < r) p += x;
+        t += x;
+      }
+      pre_sh = p;
+      tot_sh = t;
+    }
+    __syncthreads();
+  };
+  for (int64_t v = r0 + tid; v < r1; v += GG_NT) a.label[base + v] = -1;
+  if (r == 0)
+    for (int32_t b = tid; b < k; b += GG_NT) a.W[bo + b] = 0;
+  if (!sync()) return;
+  int32_t* stp = a.step + base;
+  int32_t* frt = a.front + base;
+  for (int32_t j = 0; j < k; ++j) {
+    // seed: unassigned non-isolated node with the smallest hash (the same
+    // pass clears the connections of the previous block)
+    const uint64_t skey = hkey(tkey, PH_GGG, (uint64_t)lvl, (uint64_t)j);
+    uint64_t bh = ~0ull;
+    int32_t bv = -1;
+    for (int64_t v = r0 + tid; v < r1; v += GG_NT) {
+      const int64_t gv = base + v;
+      a.conn[gv] = 0;
+      if (a.label[gv] >= 0 || a.row_ptr[gv + 1] == a.row_ptr[gv]) continue;
+      const uint64_t h = mix64(skey ^ (uint64_t)v);
+      if (bv < 0 || h < bh) { bh = h; bv = (int32_t)v; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const uint64_t oh = __shfl_xor_sync(0xffffffffu, (unsigned long long)bh, o);
+      const int32_t ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      if (ov >= 0 && (bv < 0 || oh < bh || (oh == bh && ov < bv))) { bh = oh; bv = ov; }
+    }
+    if (lane == 0) { shh[wid] = bh; shv[wid] = bv; }
+    __syncthreads();
+    if (tid == 0) {
+      uint64_t h = ~0ull;
+      int32_t v = -1;
+      for (int w = 0; w < GG_NT / 32; ++w)
+        if (shv[w] >= 0 && (v < 0 || shh[w] < h || (shh[w] == h && shv[w] < v))) {
+          h = shh[w]; v = shv[w];
+        }
+      gph[r] = h;
+      gpv[r] = v;
+    }
+    if (!sync()) return;
+    if (tid == 0) {
+      uint64_t h = ~0ull;
+      int32_t v = -1;
+      for (int q = 0; q < cpt; ++q) {
+        const uint64_t qh = *(volatile uint64_t*)&gph[q];
+        const int32_t qv = *(volatile int32_t*)&gpv[q];
+        if (qv >= 0 && (v < 0 || qh < h || (qh == h && qv < v))) { h = qh; v = qv; }
+      }
+      seed_sh = v;
+    }
+    __syncthreads();
+    const int32_t seed = seed_sh;
+    if (seed < 0) break;
+    if (r == 0 && tid == 0) {
+      a.label[base + seed] = (int32_t)(bo + j);
+      stp[0] = (int32_t)(base + seed);
+      st->nstep = 1;
+      st->nfront = 0;
+      st->nnext = 0;
+      st->fsum = 0;
+      st->accw = 0;
+      st->Wj = a.nw[base + seed];
+    }
+    bool ordered = false;
+    if (!sync()) return;
+    while (true) {
+      const int32_t nstep = *(volatile int32_t*)&st->nstep;
+      int64_t fw = 0;
+      for (int64_t q0 = (int64_t)r * GG_NT; q0 < nstep; q0 += qstride) {
+        const int64_t q = q0 + tid;
+        int64_t rs = 0, d = 0;
+        if (q < nstep) {
+          const int32_t u = stp[q];
+          rs = a.row_ptr[u];
+          d = a.row_ptr[u + 1] - rs;
+        }
+        int64_t tot;
+        const int64_t incl = block_incl_scan<GG_NT>(d, sh, &tot);
+        st_rs[tid] = rs;
+        st_ex[tid] = incl - d;
+        st_in[tid] = incl;
+        __syncthreads();
+        const int cnt = (int)min64(GG_NT, nstep - q0);
+        for (int64_t x = tid; x < tot; x += GG_NT) {
+          int lo = 0, hi = cnt - 1;
+          while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (st_in[mid] > x) hi = mid; else lo = mid + 1;
+          }
+          const int64_t e = st_rs[lo] + (x - st_ex[lo]);
+          const int32_t y = a.col[e];
+          if (a.label[y] >= 0) continue;
+          const unsigned long long old = atomicAdd(ull(&a.conn[y]), (unsigned long long)a.ew[e]);
+          if (!ordered && old == 0) {          // first arc into y (weights > 0)
+            frt[atomicAdd(&st->nfront, 1)] = y;
+            fw += a.nw[y];
+          }
+        }
+        __syncthreads();
+      }
+      const int64_t fwb = block_sum<GG_NT>(fw, sh);
+      if (tid == 0 && fwb) atomicAdd(ull(&st->fsum), (unsigned long long)fwb);
+      if (!sync()) return;
+      const int64_t Wj = *(volatile int64_t*)&st->Wj;
+      if (Wj >= avg) break;
+      if (!ordered) {
+        const int64_t fsum = *(volatile int64_t*)&st->fsum;
+        const int32_t nf = *(volatile int32_t*)&st->nfront;
+        if (Wj + fsum <= avg) {
+          // all of them fit: they are the next step, in any order
+          for (int64_t q = (int64_t)r * GG_NT + tid; q < nf; q += qstride)
+            a.label[frt[q]] = (int32_t)(bo + j);
+          int32_t* t = stp; stp = frt; frt = t;
+          if (!sync()) return;
+          if (r == 0 && tid == 0) {
+            st->nstep = nf;
+            st->nfront = 0;
+            st->fsum = 0;
+            st->Wj = Wj + fsum;
+          }
+          if (!sync()) return;
+          if (nf == 0) break;
+          continue;
+        }
+        ordered = true;
+      }
+      // connected unassigned nodes in id order, longest prefix that fits:
+      // this CTA's range starts after the candidate weight of the ranks below
+      int64_t cw = 0;
+      for (int64_t v = r0 + tid; v < r1; v += GG_NT)
+        if (a.label[base + v] < 0 && a.conn[base + v] > 0) cw += a.nw[base + v];
+      const int64_t cwb = block_sum<GG_NT>(cw, sh);
+      if (tid == 0) gpw[r] = cwb;
+      if (!sync()) return;
+      group_prefix();
+      const bool all_fit = Wj + tot_sh <= avg;
+      int64_t carry_w = pre_sh, acc_w = 0;
+      for (int64_t c0 = r0; c0 < r1; c0 += GG_NT) {
+        if (!all_fit && Wj + carry_w > avg) break;          // no later candidate fits
+        const int64_t v = c0 + tid;
+        const bool cand = v < r1 && a.label[base + v] < 0 && a.conn[base + v] > 0;
+        const int64_t wt = cand ? a.nw[base + v] : 0;
+        int64_t tw;
+        const int64_t iw = block_incl_scan<GG_NT>(wt, sh, &tw);
+        if (cand && (all_fit || Wj + carry_w + iw <= avg)) {
+          stp[atomicAdd(&st->nnext, 1)] = (int32_t)(base + v);
+          acc_w += wt;
+        }
+        carry_w += tw;
+      }
+      const int64_t accb = block_sum<GG_NT>(acc_w, sh);
+      if (tid == 0 && accb) atomicAdd(ull(&st->accw), (unsigned long long)accb);
+      if (!sync()) return;
+      const int32_t ns2 = *(volatile int32_t*)&st->nnext;
+      const int64_t newW = Wj + *(volatile int64_t*)&st->accw;
+      for (int64_t q = (int64_t)r * GG_NT + tid; q < ns2; q += qstride)
+        a.label[stp[q]] = (int32_t)(bo + j);
+      if (!sync()) return;
+      if (r == 0 && tid == 0) {
+        st->nstep = ns2;
+        st->Wj = newW;
+        st->nnext = 0;
+        st->accw = 0;
+      }
+      if (!sync()) return;
+      if (ns2 == 0) break;
+    }
+    if (r == 0 && tid == 0) a.W[bo + j] = (wgt_t)*(volatile int64_t*)&st->Wj;
+    if (!sync()) return;
+  }
+  // water-filling of the nodes left unassigned, in id order over the trial
+  int64_t rw = 0;
+  for (int64_t v = r0 + tid; v < r1; v += GG_NT)
+    if (a.label[base + v] < 0) rw += a.nw[base + v];
+  const int64_t rwb = block_sum<GG_NT>(rw, sh);
+  if (tid == 0) gpw[r] = rwb;
+  if (!sync()) return;
+  group_prefix();
+  const int64_t R = tot_sh;
+  if (R == 0) return;
+  if (r == 0 && tid == 0) {
+    int64_t lo = a.W[bo], hi = a.W[bo];
+    for (int32_t b = 1; b < k; ++b) {
+      lo = min64(lo, (int64_t)a.W[bo + b]);
+      hi = max64(hi, (int64_t)a.W[bo + b]);
+    }
+    hi += R;
+    while (lo < hi) {
+      const int64_t mid = lo + (hi - lo) / 2;
+      int64_t f = 0;
+      for (int32_t b = 0; b < k; ++b) f += max64(0, mid - (int64_t)a.W[bo + b]);
+      if (f >= R) hi = mid; else lo = mid + 1;
+    }
+    const int64_t L = lo;
+    for (int32_t jj = 0; jj < k; ++jj) {       // insertion sort by (W, id)
+      int32_t p = jj;
+      while (p > 0) {
+        const int32_t q = a.wforder[bo + p - 1];
+        if (a.W[bo + q] > a.W[bo + jj] || (a.W[bo + q] == a.W[bo + jj] && q > jj)) {
+          a.wforder[bo + p] = q;
+          --p;
+        } else {
+          break;
+        }
+      }
+      a.wforder[bo + p] = jj;
+    }
+    int64_t acc = 0;
+    for (int32_t jj = 0; jj < k; ++jj) {
+      a.wfA[bo + jj] = acc;
+      acc += max64(0, L - (int64_t)a.W[bo + a.wforder[bo + jj]]);
+    }
+  }
+  if (!sync()) return;
+  int64_t carry = pre_sh;
+  for (int64_t v0 = r0; v0 < r1; v0 += GG_NT) {
+    const int64_t v = v0 + tid;
+    const bool left = v < r1 && a.label[base + v] < 0;
+    const int64_t wt = left ? a.nw[base + v] : 0;
+    int64_t tw;
+    const int64_t iw = block_incl_scan<GG_NT>(wt, sh, &tw);
+    if (left) {
+      const int64_t p = carry + iw - wt;
+      int32_t lo = 0, hi = k - 1;               // last j with A[j] <= p
+      while (lo < hi) {
+        const int32_t mid = (lo + hi + 1) >> 1;
+        if (a.wfA[bo + mid] <= p) lo = mid; else hi = mid - 1;
+      }
+      const int32_t b = a.wforder[bo + lo];
+      a.label[base + v] = (int32_t)(bo + b);
+      atomicAdd(&a.W[bo + b], (wgt_t)wt);
+    }
+    carry += tw;
+  }
+}
+
 // Twice the cut of every slot: 32 nodes per warp, their arcs spread over
 // the lanes.  When the warp's 32 nodes lie in one slot (all but the groups
 // that straddle a slot boundary) each lane sums in a register and the warp
@@ -660,6 +951,25 @@ void ggg_trials(const GGGArgs& a_in, const std::vector<int64_t>& noff, cudaStrea
   SCLAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&many_per_sm, k_ggg<GNT_MANY>, GNT_MANY, 0));
   const int64_t few_resident = (int64_t)num_sms() * std::max(few_per_sm, 1);
   const int64_t many_resident = (int64_t)num_sms() * std::max(many_per_sm, 1);
+  // few trials: a group of CTAs per trial, sized to the largest trial
+  // (at most 64 CTAs per trial, and only when every trial gets at least 4)
+  int group_per_sm = 0;
+  SCLAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&group_per_sm, k_ggg_group, GG_NT, 0));
+  const int64_t group_resident = (int64_t)num_sms() * std::max(group_per_sm, 1);
+  const int64_t cpt = std::min<int64_t>(64, group_resident / S);
+  int64_t largest = 0;
+  for (int32_t i = 0; i < S; ++i) largest = std::max(largest, noff[i + 1] - noff[i]);
+  if (cpt >= 4 && largest >= 4096) {
+    DevBuf<GroupState> gs(S, s);
+    DevBuf<uint64_t> ph(S * cpt, s);
+    DevBuf<int32_t> pv(S * cpt, s);
+    DevBuf<int64_t> pw(S * cpt, s);
+    gs.zero();
+    launch_coop(k_ggg_group, (unsigned)(S * cpt), GG_NT, 0, s, a, (int32_t)cpt, gs.p, ph.p, pv.p,
+                pw.p, wait_limit()); SCLAP_NOTE_LAUNCH("k_ggg_group");
+    SCLAP_LAUNCH_CHECK();
+    return;
+  }
   if (S > few_resident) {
     k_ggg<GNT_MANY><<<(unsigned)std::min<int64_t>(S, many_resident), GNT_MANY, 0, s>>>(a); SCLAP_NOTE_LAUNCH("k_ggg");
   } else {

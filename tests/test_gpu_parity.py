@@ -537,3 +537,25 @@ def test_large_single_graphs_bit_exact():
         assert np.array_equal(res.block.cpu().numpy(), blk)
         assert res.stats["level_n"] == level_n
         assert P.sclap_cut(trp, tcol, None, res.block) == res.cut
+
+
+@pytest.mark.parametrize("maker,k,trials,rounds", [
+    (lambda: gg.rgg2d(20000, 6), 4, 1, 0),           # growing + water-filling alone
+    (lambda: gg.rmat(14, 8, 7), 16, 3, 0),
+    (lambda: gg.random_weights(gg.rmat(13, 8, 8), 9), 8, 2, 10),
+    (lambda: gg.rgg2d(60000, 10), 64, 4, 10),
+])
+def test_initial_partition_of_few_large_trials_bit_exact(maker, k, trials, rounds):
+    """Few trials on graphs of thousands of nodes: the trials are grown by
+    groups of CTAs (one cooperative launch) instead of one CTA each; blocks,
+    cut and best trial equal the oracle's."""
+    g = maker()
+    cV = int(g.node_w.sum())
+    Lmax, _ = O.bounds(cV, int(g.node_w.max()), k, 0.03)
+    avg = -(-cV // k)
+    cfg_o = O.config(ip_trials=trials, lp_rounds_refine=rounds)
+    ob, ocut, obest = O.initial_partition(g, k, Lmax, avg, seed=12, level=1, cfg=cfg_o)
+    tb, cut, best = P.sclap_initial_partition(
+        *dg(g), k, Lmax, avg, 12, 1, cfg=P.default_config(ip_trials=trials, lp_rounds_refine=rounds))
+    assert (cut, best) == (ocut, obest)
+    assert np.array_equal(tb.cpu().numpy(), ob)
