@@ -42,10 +42,12 @@ sys.path.insert(0, ROOT)
 import graphgen as gg  # noqa: E402
 
 # Algorithmic bytes of the LP propose sweep.  Per arc: col (4) + edge weight
-# (4) + label gather (4).  Per node: sub-round list entry (4), row_ptr pair
-# (16), slot id (4), own label (4), node weight (4), proposal target (4) and
-# admission key (8) written.
+# (4) + label gather (4); on a level of unit edge weights no weight is read
+# (8).  Per node: sub-round list entry (4), row_ptr pair (16), slot id (4),
+# own label (4), node weight (4), proposal target (4) and admission key (8)
+# written.
 ARC_BYTES = 12
+ARC_BYTES_UNIT = 8
 NODE_BYTES = 44
 FAMILIES = ["thread_deg_le16", "warp_deg_le128_cta128", "cta256_512", "hub_global_table"]
 
@@ -325,7 +327,8 @@ def print_phases(ph, steps):
     """Per-step totals of the sub-round records, by run kind and round."""
     if ph.size == 0:
         return
-    print(f"sub-rounds per step: {len(ph) / steps:.0f}", file=sys.stderr)
+    print(f"sub-rounds per step: {len(ph) / steps:.0f} (GB/s at 12 B per arc, an upper "
+          "bound on levels of unit edge weights)", file=sys.stderr)
     print(f"{'kind':10s} {'round':>5s} {'subs':>5s} {'nodes':>11s} {'arcs':>12s} "
           f"{'sweep_ms':>9s} {'adm_ms':>8s} {'GB/s':>7s}", file=sys.stderr)
     keys = sorted({(int(r[0]), int(r[1])) for r in ph})
@@ -726,8 +729,10 @@ def main():
     parts = args.steps * len(graphs) * ws
     value = parts / (elapsed_ms / 1000.0)
     swept = sum(prof["propose_arcs"])
+    unit_arcs = prof["propose_arcs_unit"]
     prop_ms = prof["sweep_ms"]
-    prop_bytes = ARC_BYTES * swept + NODE_BYTES * sum(prof["propose_nodes"])
+    prop_bytes = (ARC_BYTES * (swept - unit_arcs) + ARC_BYTES_UNIT * unit_arcs
+                  + NODE_BYTES * sum(prof["propose_nodes"]))
     peaks = {}
     pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(pk):
@@ -742,6 +747,9 @@ def main():
                   "concurrently); one 'launch' = one such phase, timed fork to join with "
                   "CUDA events",
         "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+        "bytes_model": "12 B per scanned arc (8 on levels of unit edge weights) + 44 B per "
+                       "listed node",
+        "arcs_unit_weight": unit_arcs,
         "frac": achieved / peak, "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
         "traffic": (tr[0] * swept / nl if tr and tr[0] else None) if nl else None,
         "bytes_per_launch": prop_bytes / nl if nl else None,

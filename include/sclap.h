@@ -425,6 +425,8 @@ typedef struct sclap_profile {
   double sweep_ms;             /* propose phases: the families of a sub-round
                                   run concurrently; first launch to last     */
   int64_t sweeps;
+  int64_t propose_arcs_unit;   /* of all propose arcs, those on levels with
+                                  unit edge weights (no weight array read)   */
 } sclap_profile;
 void sclap_profile_enable(int on);
 void sclap_profile_reset(void);

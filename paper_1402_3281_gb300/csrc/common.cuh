@@ -42,6 +42,7 @@ struct ProfileState {
   std::mutex mu;
   double ms[4] = {};
   int64_t nlaunch[4] = {}, nodes[4] = {}, arcs[4] = {};
+  int64_t arcs_unit = 0;     // arcs of propose launches on levels without edge weights
   double sweep_ms = 0;       // propose phases, fork to join (concurrent launches)
   int64_t sweeps = 0;
   // per sub-round: run kind, round, colour class, nodes, arcs, propose ms,

@@ -1663,6 +1663,7 @@ void sclap_profile_reset(void) {
   std::lock_guard<std::mutex> lk(P.mu);
   P.launches.store(0);
   for (int b = 0; b < 4; ++b) { P.ms[b] = 0; P.nlaunch[b] = 0; P.nodes[b] = 0; P.arcs[b] = 0; }
+  P.arcs_unit = 0;
   P.sweep_ms = 0;
   P.sweeps = 0;
   P.phases.clear();
@@ -1692,6 +1693,7 @@ void sclap_profile_read(sclap_profile* out) {
   }
   out->sweep_ms = P.sweep_ms;
   out->sweeps = P.sweeps;
+  out->propose_arcs_unit = P.arcs_unit;
 }
 
 }  // extern "C"

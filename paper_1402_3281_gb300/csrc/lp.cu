@@ -2035,6 +2035,7 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, wgt_t*
       P.nlaunch[t.family] += 1;
     }
     for (int b = 0; b < 4; ++b) { P.nodes[b] += pn[b]; P.arcs[b] += pa[b]; }
+    if (!lv.ew) for (int b = 0; b < 4; ++b) P.arcs_unit += pa[b];
     for (const PhaseRec& q : precs) {
       float sw = 0.f, ad = 0.f;
       SCLAP_CUDA(cudaEventElapsedTime(&sw, q.a, q.b));

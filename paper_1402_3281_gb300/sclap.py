@@ -68,14 +68,14 @@ class Profile(C.Structure):
     _fields_ = [("kernel_launches", C.c_int64), ("propose_launches", C.c_int64 * 4),
                 ("propose_ms", C.c_double * 4), ("propose_nodes", C.c_int64 * 4),
                 ("propose_arcs", C.c_int64 * 4), ("sweep_ms", C.c_double),
-                ("sweeps", C.c_int64)]
+                ("sweeps", C.c_int64), ("propose_arcs_unit", C.c_int64)]
 
     def to_dict(self) -> dict:
         return dict(kernel_launches=self.kernel_launches,
                     propose_launches=list(self.propose_launches),
                     propose_ms=list(self.propose_ms), propose_nodes=list(self.propose_nodes),
                     propose_arcs=list(self.propose_arcs), sweep_ms=self.sweep_ms,
-                    sweeps=self.sweeps)
+                    sweeps=self.sweeps, propose_arcs_unit=self.propose_arcs_unit)
 
 
 class ServerOptions(C.Structure):
