@@ -601,8 +601,10 @@ struct GGGArgs {
   int32_t* next;           // queue position (set by ggg_trials)
   int32_t* err;            // device error word (bounded waits of the grouped kernel)
 };
-// noff: host copy of the trial slot node offsets [nslots + 1].
-void ggg_trials(const GGGArgs& a, const std::vector<int64_t>& noff, cudaStream_t s);
+// noff: host copy of the trial slot node offsets [nslots + 1]; nlab: host
+// copy of k per trial slot.
+void ggg_trials(const GGGArgs& a, const std::vector<int64_t>& noff,
+                const std::vector<int32_t>& nlab, cudaStream_t s);
 // cut2[slot] += twice the cut of each slot (arcs counted from both ends).
 void slot_cut(const LevelView& lv, const int32_t* label, int64_t* cut2, cudaStream_t s);
 struct SelectTask {            // choose the best trial of one graph, copy it out

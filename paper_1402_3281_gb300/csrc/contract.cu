@@ -6,7 +6,8 @@
 // between them.  GPU plan: rank the labels by a scan; stream the fine arcs in
 // node order (warp per 32 nodes, arcs flattened across lanes) once to count
 // each coarse node's inter-cluster arcs, size one open-addressing region per
-// coarse node from that count, stream the arcs again inserting (coarse
+// coarse node from that count (next_pow2 of it: the distinct coarse
+// neighbours never outnumber the arcs, and are usually far fewer), stream the arcs again inserting (coarse
 // neighbour, weight) with one 64-bit CAS or atomic add each (a claim also
 // records the slot's owner and counts its degree), scan the degrees into row
 // offsets, and place every occupied slot in its owner's row.  The order of a
@@ -139,7 +140,7 @@ __global__ void k_table_caps(const int32_t* __restrict__ inter, int64_t Nc, int6
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < Nc;
        c += (int64_t)gridDim.x * blockDim.x) {
     const int32_t x = inter[c];
-    cap[c] = x > 0 ? ((int64_t)1 << ceil_log2(2 * (int64_t)x)) : 0;
+    cap[c] = x > 0 ? ((int64_t)1 << ceil_log2((int64_t)x)) : 0;
   }
 }
 

@@ -569,7 +569,7 @@ void run_ip(const std::vector<IPIn>& in, const sclap_config& cfg, wgt_t* Wg,
   ga.conn = conn.p; ga.step = step.p; ga.front = front.p; ga.wfA = wfA.p; ga.wforder = wforder.p;
   ga.nslots = S;
   ga.err = d_err;
-  ggg_trials(ga, noff, s);
+  ggg_trials(ga, noff, h_nlab, s);
 
   LPRun run;
   run.mode = MODE_REFINE;

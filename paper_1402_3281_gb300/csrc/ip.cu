@@ -928,7 +928,8 @@ void ip_replicate(const std::vector<CopyTask>& tasks, int64_t* row_ptr, int32_t*
   SCLAP_LAUNCH_CHECK();
 }
 
-void ggg_trials(const GGGArgs& a_in, const std::vector<int64_t>& noff, cudaStream_t s) {
+void ggg_trials(const GGGArgs& a_in, const std::vector<int64_t>& noff,
+                const std::vector<int32_t>& nlab, cudaStream_t s) {
   if (a_in.nslots <= 0) return;
   const int32_t S = a_in.nslots;
   // longest processing time first: trial slots by node count, descending
@@ -951,15 +952,22 @@ void ggg_trials(const GGGArgs& a_in, const std::vector<int64_t>& noff, cudaStrea
   SCLAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&many_per_sm, k_ggg<GNT_MANY>, GNT_MANY, 0));
   const int64_t few_resident = (int64_t)num_sms() * std::max(few_per_sm, 1);
   const int64_t many_resident = (int64_t)num_sms() * std::max(many_per_sm, 1);
-  // few trials: a group of CTAs per trial, sized to the largest trial
-  // (at most 64 CTAs per trial, and only when every trial gets at least 4)
+  // few trials of large blocks: a group of CTAs per trial (at most 64 CTAs
+  // per trial, and only when every trial gets at least 4).  A growth step
+  // costs the group a few barriers, so the groups pay off only when the
+  // blocks are large: measured faster on R-MAT scale 22 at k = 2 and 8 and
+  // on scale 25 at k = 16 (1149 -> 369 ms), slower on scale 22 at k = 32
+  // and 64, and the same gate cannot separate them at 2^16 or 2^17 nodes per
+  // block (scale 22, k = 8 fell below 2^15 as well); the gate is 2^14
+  // nodes per block on average in some trial.
   int group_per_sm = 0;
   SCLAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&group_per_sm, k_ggg_group, GG_NT, 0));
   const int64_t group_resident = (int64_t)num_sms() * std::max(group_per_sm, 1);
   const int64_t cpt = std::min<int64_t>(64, group_resident / S);
-  int64_t largest = 0;
-  for (int32_t i = 0; i < S; ++i) largest = std::max(largest, noff[i + 1] - noff[i]);
-  if (cpt >= 4 && largest >= 4096) {
+  int64_t per_block = 0;
+  for (int32_t i = 0; i < S; ++i)
+    per_block = std::max(per_block, (noff[i + 1] - noff[i]) / std::max<int32_t>(1, nlab[i]));
+  if (cpt >= 4 && per_block >= ((int64_t)1 << 14)) {
     DevBuf<GroupState> gs(S, s);
     DevBuf<uint64_t> ph(S * cpt, s);
     DevBuf<int32_t> pv(S * cpt, s);

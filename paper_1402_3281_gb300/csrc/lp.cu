@@ -34,6 +34,7 @@ struct LPArgs {
   const int32_t* gid;
   int32_t narrow;          // 1: every connection sum is below 2^32
   int32_t arcs32;          // 1: the level has fewer than 2^32 arcs
+  int64_t M;               // arcs of the level (length of col / ew)
   // slots
   const int64_t* noff;
   const int64_t* loff;
@@ -652,6 +653,76 @@ __global__ void __launch_bounds__(WPC * 32) k_propose_warp(LPArgs a, int32_t sub
 // slots created for the current node.  The row is read four strides at a
 // time (loads first, then label gathers, then inserts), candidates are the
 // created slots only, and only those slots are cleared afterwards.
+// ---------------------------------------------------------------- bulk copies
+// Hub rows are staged in shared memory by the bulk-copy engine: one thread
+// issues a cp.async.bulk of a chunk of the row (col, and the weights when
+// the level has them) completing on an mbarrier with the byte count, and
+// every thread waits on the barrier's phase (bounded) before reading the
+// chunk.  Source addresses and sizes are multiples of 16 bytes: the chunk
+// is widened to 16-byte boundaries, and entries past the last full 16-byte
+// word of the array are read from global memory directly.
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}" : "=r"(ok) : "r"(smem_addr(bar)), "r"(parity) : "memory");
+  return ok != 0;
+}
+// Waits until phase `parity` of the barrier completes, at most `limit` polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit) {
+  for (uint32_t it = 0; it <= limit; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+constexpr int HUB_NT = 512;
+constexpr int HUB_CH = 4 * HUB_NT;           // arcs per staged chunk
+constexpr int HUB_BUF = HUB_CH + 8;          // entries per buffer (16-byte widening)
+constexpr size_t hub_smem_bytes() { return (size_t)2 * 2 * HUB_BUF * sizeof(int32_t); }
+
+// The 16-byte-aligned window [a0, a1) of the chunk [e0, end) that is copied
+// (a1 <= M rounded down to 16 bytes; entries at or past a1 are read from
+// global memory), and the bulk copies of it into buffer b.
+__device__ __forceinline__ void hub_window(int64_t e0, int64_t end, int64_t M, int64_t* a0,
+                                           int64_t* a1) {
+  *a0 = e0 & ~(int64_t)3;
+  int64_t x = (end + 3) & ~(int64_t)3;
+  const int64_t mlim = M & ~(int64_t)3;
+  *a1 = x < mlim ? x : mlim;
+  if (*a1 < *a0) *a1 = *a0;
+}
+__device__ __forceinline__ void hub_issue(const LPArgs& a, int64_t e0, int64_t end, int32_t* scol,
+                                          int32_t* sew, uint64_t* bar) {
+  int64_t a0, a1;
+  hub_window(e0, end, a.M, &a0, &a1);
+  const uint32_t bytes = (uint32_t)((a1 - a0) * 4);
+  mbar_expect_tx(bar, a.ew ? 2 * bytes : bytes);
+  if (bytes) {
+    bulk_g2s(scol, a.col + a0, bytes, bar);
+    if (a.ew) bulk_g2s(sew, a.ew + a0, bytes, bar);
+  }
+}
+
 template <int SLOTS>
 constexpr size_t blk_smem_bytes() {
   return (size_t)SLOTS * (sizeof(unsigned long long) + sizeof(int32_t)) +
@@ -679,11 +750,27 @@ __global__ void __launch_bounds__(NT) k_propose_blk(LPArgs a, int32_t sub, int32
   int32_t* clist;
   int64_t tcap;
   const int tid = threadIdx.x, lane = tid & 31;
+  // hubs: rows staged chunk by chunk in two shared-memory buffers by bulk
+  // copies (when col and the weights start on 16-byte boundaries); the next
+  // chunk is copied while the CTA works on the current one
+  __shared__ uint64_t hub_bar[2];
+  int32_t* scol[2] = {nullptr, nullptr};
+  int32_t* sew[2] = {nullptr, nullptr};
+  const bool staged = GLOBAL && NT == HUB_NT &&
+      ((reinterpret_cast<uintptr_t>(a.col) | reinterpret_cast<uintptr_t>(a.ew)) & 15) == 0;
+  uint32_t kchunk = 0, phs[2] = {0, 0};
   if (GLOBAL) {
     vals = gvals;
     keys = gkeys;
     clist = glist;
     tcap = 0;
+    int32_t* sb = reinterpret_cast<int32_t*>(smem_u64);
+    scol[0] = sb; scol[1] = sb + HUB_BUF; sew[0] = sb + 2 * HUB_BUF; sew[1] = sb + 3 * HUB_BUF;
+    if (tid == 0) {
+      mbar_init(&hub_bar[0], 1);
+      mbar_init(&hub_bar[1], 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
   } else {
     vals = smem_u64;
     keys = reinterpret_cast<int32_t*>(smem_u64 + SLOTS);
@@ -711,14 +798,58 @@ __global__ void __launch_bounds__(NT) k_propose_blk(LPArgs a, int32_t sub, int32
     const int64_t deg = c.re - c.rs;
     const int logcap = ceil_log2(max64(2 * deg, 32));
     const uint32_t mask = (1u << logcap) - 1;
+    if (staged && tid == 0) {
+      // the buffer was last read two chunks ago, before a CTA barrier
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      hub_issue(a, c.rs, min64(c.rs + HUB_CH, c.re), scol[kchunk & 1], sew[kchunk & 1],
+                &hub_bar[kchunk & 1]);
+    }
     for (int64_t e0 = c.rs; e0 < c.re; e0 += 4 * NT) {
       int32_t C[4], w[4];
+      if (staged) {
+        const int b = (int)(kchunk & 1);
+        const int64_t nx = e0 + HUB_CH;
+        if (tid == 0 && nx < c.re) {
+          // buffer b ^ 1 was last read before the barrier that ended the
+          // previous chunk; order those reads before the copy's writes
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          hub_issue(a, nx, min64(nx + HUB_CH, c.re), scol[b ^ 1], sew[b ^ 1], &hub_bar[b ^ 1]);
+        }
+        const bool ok = mbar_wait(&hub_bar[b], phs[b], a.wait_limit);
+        if (__syncthreads_or(!ok)) {
+          // the copy did not complete in time: report, let the copies in
+          // flight land (bounded), leave
+          if (tid == 0) atomicOr(a.err, DERR_TIMEOUT);
+          mbar_wait(&hub_bar[b], phs[b], a.wait_limit);
+          if (nx < c.re) mbar_wait(&hub_bar[b ^ 1], phs[b ^ 1], a.wait_limit);
+          return;
+        }
+        phs[b] ^= 1u;
+        int64_t w0, w1;
+        hub_window(e0, min64(e0 + HUB_CH, c.re), a.M, &w0, &w1);
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int64_t e = e0 + (int64_t)u * NT + tid;
-        const bool in = e < c.re;
-        w[u] = in ? wat(a.ew, e) : 0;
-        C[u] = in ? a.col[e] : -1;
+        for (int u = 0; u < 4; ++u) {
+          const int64_t e = e0 + (int64_t)u * NT + tid;
+          C[u] = -1;
+          w[u] = 0;
+          if (e < c.re) {
+            if (e < w1) {
+              C[u] = scol[b][e - w0];
+              w[u] = a.ew ? sew[b][e - w0] : 1;
+            } else {
+              C[u] = a.col[e];
+              w[u] = wat(a.ew, e);
+            }
+          }
+        }
+      } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int64_t e = e0 + (int64_t)u * NT + tid;
+          const bool in = e < c.re;
+          w[u] = in ? wat(a.ew, e) : 0;
+          C[u] = in ? a.col[e] : -1;
+        }
       }
 #pragma unroll
       for (int u = 0; u < 4; ++u)
@@ -758,6 +889,10 @@ __global__ void __launch_bounds__(NT) k_propose_blk(LPArgs a, int32_t sub, int32
           base = __shfl_sync(0xffffffffu, base, first);
           if (cr) clist[base + __popc(cm & ((1u << lane) - 1))] = (int32_t)s;
         }
+      }
+      if (staged) {          // every thread is done with this chunk's buffer
+        ++kchunk;
+        __syncthreads();
       }
     }
     __syncthreads();
@@ -1673,6 +1808,7 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, wgt_t*
   a.row_ptr = lv.row_ptr; a.col = lv.col; a.ew = lv.ew; a.nw = lv.nw; a.gid = lv.gid;
   a.narrow = lv.narrow ? 1 : 0;
   a.arcs32 = lv.M < ((int64_t)1 << 32) ? 1 : 0;
+  a.M = lv.M;
   a.noff = sp.noff; a.loff = sp.loff; a.bound = sp.bound; a.rkey = sp.rkey; a.nlab = sp.nlab;
   a.done = sp.done; a.moved = sp.moved; a.rounds = sp.rounds;
   a.label = label; a.W = W; a.in_w = in_w.p; a.mode = run.mode; a.S = S;
@@ -1843,7 +1979,7 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, wgt_t*
     });
     if (need[8]) launch(8, 9, 3, [&](cudaStream_t ls, bool p) {
       launch_k(p, k_hub_offsets, 1, HO_NT, 0, ls, a, sub, hub_off.p); SCLAP_NOTE_LAUNCH("k_hub_offsets");
-      launch_k(tu.pdl != 0, k_propose_blk<512, 1, true>, (unsigned)gblocks, 512, 0, ls, a, sub, 8, gkeys.p, gvals.p, glist.p, (const int64_t*)hub_off.p); SCLAP_NOTE_LAUNCH("k_propose_hub");
+      launch_k(tu.pdl != 0, k_propose_blk<HUB_NT, 1, true>, (unsigned)gblocks, HUB_NT, hub_smem_bytes(), ls, a, sub, 8, gkeys.p, gvals.p, glist.p, (const int64_t*)hub_off.p); SCLAP_NOTE_LAUNCH("k_propose_hub");
     });
     if (fork) {
       for (int j = 0; j < nside; ++j) {

@@ -540,15 +540,17 @@ def test_large_single_graphs_bit_exact():
 
 
 @pytest.mark.parametrize("maker,k,trials,rounds", [
-    (lambda: gg.rgg2d(20000, 6), 4, 1, 0),           # growing + water-filling alone
-    (lambda: gg.rmat(14, 8, 7), 16, 3, 0),
-    (lambda: gg.random_weights(gg.rmat(13, 8, 8), 9), 8, 2, 10),
-    (lambda: gg.rgg2d(60000, 10), 64, 4, 10),
+    (lambda: gg.rgg2d(300000, 6), 2, 1, 0),          # growing + water-filling alone
+    (lambda: gg.rmat(19, 8, 7), 2, 2, 0),            # ~300k nodes with neighbours
+    (lambda: gg.random_weights(gg.rgg2d(280000, 8), 9), 2, 2, 10),
+    (lambda: gg.rgg2d(20000, 10), 16, 4, 10),        # small blocks: one CTA per trial
+    (lambda: gg.rgg2d(60000, 11), 2, 3, 10),         # 30k nodes per block: groups
 ])
 def test_initial_partition_of_few_large_trials_bit_exact(maker, k, trials, rounds):
-    """Few trials on graphs of thousands of nodes: the trials are grown by
-    groups of CTAs (one cooperative launch) instead of one CTA each; blocks,
-    cut and best trial equal the oracle's."""
+    """Few trials with blocks of more than 2^14 nodes on average: each trial
+    is grown by a group of CTAs (one cooperative launch) instead of one CTA;
+    blocks, cut and best trial equal the oracle's (the last case stays on
+    the one-CTA kernel)."""
     g = maker()
     cV = int(g.node_w.sum())
     Lmax, _ = O.bounds(cV, int(g.node_w.max()), k, 0.03)
