@@ -77,6 +77,10 @@ def parse():
     ap.add_argument("--autotune", action="store_true",
                     help="before the warm-up, pick the launch tuning for this batch with "
                          "sclap_autotune (results unchanged; the choice goes into config)")
+    ap.add_argument("--tuning", default="",
+                    help="comma-separated field=value launch-tuning settings applied with "
+                         "sclap_set_tuning before the run, e.g. contract_merge=0 (results "
+                         "unchanged; the setting goes into config)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--phases", action="store_true",
                     help="print per-sub-round propose/admission times grouped by run kind "
@@ -628,8 +632,18 @@ def huge_workload(args):
     print(json.dumps(line), flush=True)
 
 
+def apply_tuning(args):
+    if not args.tuning or args.impl == "reference" or args.workload == "cpu":
+        return
+    import paper_1402_3281_gb300 as P
+    P.load()
+    kv = dict(item.split("=", 1) for item in args.tuning.split(",") if item)
+    P.set_tuning(**{k.strip(): int(v) for k, v in kv.items()})
+
+
 def main():
     args = parse()
+    apply_tuning(args)
     if args.workload == "large":
         large_workload(args)
         return

@@ -382,7 +382,13 @@ int sclap_debug_inject(int64_t wait_limit, int64_t probe_limit, int32_t fail_all
  *                      at once (the trials run group after group; same
  *                      result); 0: automatic, as many as fit in half of the
  *                      device memory still obtainable
- * The setting is process-wide; defaults 16, 8, 8, 16, 1, 1, 0, 0, 0. ---- */
+ *   contract_merge     1: contraction sorts the fine nodes by coarse node
+ *                      and merges each coarse node's arcs in shared memory
+ *                      (a level whose merge regions do not fit in the
+ *                      memory of one contraction pass falls back to the
+ *                      hash tables); 0: hash tables (same result up to the
+ *                      order of each coarse row's arcs)
+ * The setting is process-wide; defaults 16, 8, 8, 16, 1, 1, 0, 0, 0, 0. ---- */
 typedef struct sclap_tuning {
   int32_t small_max_deg;
   int32_t small_ctas_per_sm;
@@ -393,6 +399,7 @@ typedef struct sclap_tuning {
   int32_t fused_admission;
   int32_t contract_table_slots;
   int32_t ip_trial_group;
+  int32_t contract_merge;
 } sclap_tuning;
 void sclap_get_tuning(sclap_tuning* out);
 /* SCLAP_EINVAL for a value out of range (the setting is then unchanged). */

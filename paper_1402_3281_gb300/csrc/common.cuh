@@ -79,6 +79,7 @@ struct Tuning {
   int32_t fused_admission = 0;   // 1: admission as one cooperative launch
   int32_t contract_table_slots = 0;   // slots per contraction pass (0: automatic)
   int32_t ip_trial_group = 0;         // trials replicated at once (0: automatic)
+  int32_t contract_merge = 0;         // 1: contraction by member lists and merges
 };
 // Device memory still obtainable: free memory plus what the allocator pool
 // holds unused.
@@ -305,6 +306,9 @@ struct LevelView {
   // every sum of arc weights over a row (so every connection) is below 2^32:
   // the propose tables may accumulate with 32-bit atomics
   bool narrow = false;
+  // every graph's total arc weight is at most INT32_MAX, so no sum of arc
+  // weights (a coarse arc's weight in particular) can overflow int32
+  bool sums31 = false;
 };
 
 // Per-slot parameters of an LP run (device arrays of `nslots` entries).

@@ -248,6 +248,7 @@ struct Level {
   // an input level of unit weights (a row's sum is its degree, < 2^31)
   bool narrow = false;
   bool narrow_total = false;   // the total-weight rule alone (inherited by coarse levels)
+  bool sums31 = false;         // every graph's total arc weight <= INT32_MAX (inherited)
   const int64_t* rp() const { return borrowed ? rp_in : row_ptr.p; }
   const int32_t* colp() const { return borrowed ? col_in : col.p; }
   const int32_t* ewp() const { return borrowed ? ew_in : ew.p; }
@@ -257,6 +258,7 @@ struct Level {
     v.N = N; v.M = M; v.row_ptr = rp(); v.col = colp(); v.ew = ewp(); v.nw = nwp();
     v.gid = gid.p;
     v.narrow = narrow;
+    v.sums31 = sums31;
     return v;
   }
 };
@@ -321,7 +323,8 @@ void build_level0(const std::vector<GIn>& gs, struct Level& L, cudaStream_t s);
 // contraction only merges or drops arcs).
 void validate_level(const Level& L, int B, std::vector<int32_t>& status,
                     std::vector<int64_t>& cV, std::vector<int64_t>& maxc,
-                    std::vector<char>& narrow, cudaStream_t s) {
+                    std::vector<char>& narrow, cudaStream_t s,
+                    std::vector<char>* sums31 = nullptr) {
   DevBuf<int32_t> err(B, s), mx(B, s);
   DevBuf<unsigned long long> sum(B, s), arcw(B, s);
   DevBuf<int64_t> d_aoff(B + 1, s);
@@ -344,12 +347,14 @@ void validate_level(const Level& L, int B, std::vector<int32_t>& status,
   cV.assign(B, 0);
   maxc.assign(B, 0);
   narrow.assign(B, 0);
+  if (sums31) sums31->assign(B, 0);
   for (int g = 0; g < B; ++g) {
     if (e[g]) status[g] = SCLAP_ECSR;
     else if (w[g] >= (1ull << 31)) status[g] = SCLAP_EOVERFLOW;
     cV[g] = (int64_t)w[g];
     maxc[g] = m[g];
     narrow[g] = aw[g] <= 0xffffffffull ? 1 : 0;
+    if (sums31) (*sums31)[g] = aw[g] <= (unsigned long long)INT32_MAX ? 1 : 0;
   }
 }
 
@@ -631,14 +636,15 @@ void run_batch(const std::vector<GIn>& gs_in, const sclap_config& cfg,
   build_level0(gs_in, *L0, s);
   std::vector<int32_t> status;
   std::vector<int64_t> cV, maxc;
-  std::vector<char> narrow;
-  validate_level(*L0, B, status, cV, maxc, narrow, s);
+  std::vector<char> narrow, small;
+  validate_level(*L0, B, status, cV, maxc, narrow, s, &small);
   std::vector<int> ok;
-  bool all_narrow = true;
+  bool all_narrow = true, all_small = true;
   for (int g = 0; g < B; ++g) {
     if (status[g] == SCLAP_OK) {
       ok.push_back(g);
       all_narrow = all_narrow && narrow[g];
+      all_small = all_small && small[g];
     } else {
       res[g].status = status[g];
     }
@@ -646,6 +652,7 @@ void run_batch(const std::vector<GIn>& gs_in, const sclap_config& cfg,
   if ((int)ok.size() == B) {
     L0->narrow_total = all_narrow;
     L0->narrow = all_narrow || L0->ewp() == nullptr;
+    L0->sums31 = all_small;
     run_valid_batch(gs_in, cV, maxc, cfg, outs_in, res, std::move(L0), s);
     return;
   }
@@ -663,6 +670,7 @@ void run_batch(const std::vector<GIn>& gs_in, const sclap_config& cfg,
   build_level0(gs, *L0, s);
   L0->narrow_total = all_narrow;
   L0->narrow = all_narrow || L0->ewp() == nullptr;
+  L0->sums31 = all_small;
   std::vector<GOut> r2;
   run_valid_batch(gs, c2, m2, cfg, outs, r2, std::move(L0), s);
   for (size_t j = 0; j < ok.size(); ++j) res[ok[j]] = r2[j];
@@ -791,6 +799,7 @@ void run_valid_batch(const std::vector<GIn>& gs, const std::vector<int64_t>& cV,
       std::unique_ptr<Level> nx(new Level());
       nx->narrow = cur.narrow_total;
       nx->narrow_total = cur.narrow_total;
+      nx->sums31 = cur.sums31;
       nx->N = co.N;
       nx->M = co.M;
       nx->row_ptr = std::move(co.row_ptr);
@@ -1557,6 +1566,7 @@ void sclap_get_tuning(sclap_tuning* out) {
   out->fused_admission = t.fused_admission;
   out->contract_table_slots = t.contract_table_slots;
   out->ip_trial_group = t.ip_trial_group;
+  out->contract_merge = t.contract_merge;
 }
 
 int sclap_set_tuning(const sclap_tuning* in) {
@@ -1566,7 +1576,8 @@ int sclap_set_tuning(const sclap_tuning* in) {
         in->small_ctas_per_sm > 32 || in->warp_ctas_per_sm < 1 || in->warp_ctas_per_sm > 32 ||
         in->admit_ctas_per_sm < 1 || in->admit_ctas_per_sm > 64 || in->concurrent < 0 ||
         in->concurrent > 1 || in->pdl < 0 || in->pdl > 1 || in->fused_admission < 0 ||
-        in->fused_admission > 1 || in->contract_table_slots < 0 || in->ip_trial_group < 0)
+        in->fused_admission > 1 || in->contract_table_slots < 0 || in->ip_trial_group < 0 ||
+        in->contract_merge < 0 || in->contract_merge > 1)
       throw Error(SCLAP_EINVAL, "tuning value out of range");
     Tuning t;
     t.small_max_deg = in->small_max_deg;
@@ -1578,6 +1589,7 @@ int sclap_set_tuning(const sclap_tuning* in) {
     t.fused_admission = in->fused_admission;
     t.contract_table_slots = in->contract_table_slots;
     t.ip_trial_group = in->ip_trial_group;
+    t.contract_merge = in->contract_merge;
     tuning_set(t);
   });
 }
@@ -1622,6 +1634,7 @@ int sclap_autotune(int32_t count, sclap_graph* graphs, const sclap_config* cfg,
           {&Tuning::concurrent, {1, 0}},
           {&Tuning::pdl, {1, 0}},
           {&Tuning::fused_admission, {0, 1}},
+          {&Tuning::contract_merge, {0, 1}},
       };
       for (const Param& p : params) {
         for (int32_t v : p.vals) {

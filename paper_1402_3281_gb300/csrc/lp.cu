@@ -648,11 +648,6 @@ __global__ void __launch_bounds__(WPC * 32) k_propose_warp(LPArgs a, int32_t sub
   }
 }
 
-// Degrees 129..8192 (buckets 5-7): one CTA of NT threads per node, a
-// SLOTS-slot table in dynamic shared memory (keys, sums) plus a list of the
-// slots created for the current node.  The row is read four strides at a
-// time (loads first, then label gathers, then inserts), candidates are the
-// created slots only, and only those slots are cleared afterwards.
 // ---------------------------------------------------------------- bulk copies
 // Hub rows are staged in shared memory by the bulk-copy engine: one thread
 // issues a cp.async.bulk of a chunk of the row (col, and the weights when
@@ -729,14 +724,13 @@ constexpr size_t blk_smem_bytes() {
          (size_t)(SLOTS / 2) * sizeof(int32_t);
 }
 
-// GLOBAL (hubs, degree above 8192): the same per-node procedure, with the
-// node's table (hub_table_slots(degree) slots) and created list in its own
-// region of global memory, at hoff[li] (list at hoff[li] / 2); the CTA
-// clears the region before using it.
-template <int NT, int SLOTS, bool GLOBAL>
-__global__ void __launch_bounds__(NT) k_propose_blk(LPArgs a, int32_t sub, int32_t bucket,
-                                                    int32_t* gkeys, unsigned long long* gvals,
-                                                    int32_t* glist, const int64_t* hoff) {
+// Degrees 129..8192 (buckets 5-7): one CTA of NT threads per node, a
+// SLOTS-slot table in dynamic shared memory (keys, sums) plus a list of the
+// slots created for the current node.  The row is read four strides at a
+// time (loads first, then label gathers, then inserts), candidates are the
+// created slots only, and only those slots are cleared afterwards.
+template <int NT, int SLOTS>
+__global__ void __launch_bounds__(NT) k_propose_blk(LPArgs a, int32_t sub, int32_t bucket) {
   griddep_wait();
   int64_t lbeg, cnt;
   sub_range(a, sub, bucket, bucket + 1, &lbeg, &cnt);
@@ -745,111 +739,31 @@ __global__ void __launch_bounds__(NT) k_propose_blk(LPArgs a, int32_t sub, int32
   __shared__ long long sh_oc[NT / 32];
   __shared__ Cand sh_cd[NT / 32];
   __shared__ int sh_nc;
-  unsigned long long* vals;
-  int32_t* keys;
-  int32_t* clist;
-  int64_t tcap;
+  unsigned long long* vals = smem_u64;
+  int32_t* keys = reinterpret_cast<int32_t*>(smem_u64 + SLOTS);
+  int32_t* clist = keys + SLOTS;
+  constexpr int64_t tcap = SLOTS;
   const int tid = threadIdx.x, lane = tid & 31;
-  // hubs: rows staged chunk by chunk in two shared-memory buffers by bulk
-  // copies (when col and the weights start on 16-byte boundaries); the next
-  // chunk is copied while the CTA works on the current one
-  __shared__ uint64_t hub_bar[2];
-  int32_t* scol[2] = {nullptr, nullptr};
-  int32_t* sew[2] = {nullptr, nullptr};
-  const bool staged = GLOBAL && NT == HUB_NT &&
-      ((reinterpret_cast<uintptr_t>(a.col) | reinterpret_cast<uintptr_t>(a.ew)) & 15) == 0;
-  uint32_t kchunk = 0, phs[2] = {0, 0};
-  if (GLOBAL) {
-    vals = gvals;
-    keys = gkeys;
-    clist = glist;
-    tcap = 0;
-    int32_t* sb = reinterpret_cast<int32_t*>(smem_u64);
-    scol[0] = sb; scol[1] = sb + HUB_BUF; sew[0] = sb + 2 * HUB_BUF; sew[1] = sb + 3 * HUB_BUF;
-    if (tid == 0) {
-      mbar_init(&hub_bar[0], 1);
-      mbar_init(&hub_bar[1], 1);
-      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-  } else {
-    vals = smem_u64;
-    keys = reinterpret_cast<int32_t*>(smem_u64 + SLOTS);
-    clist = keys + SLOTS;
-    tcap = SLOTS;
-    for (int j = tid; j < SLOTS; j += NT) { keys[j] = -1; vals[j] = 0; }
-  }
+  for (int j = tid; j < SLOTS; j += NT) { keys[j] = -1; vals[j] = 0; }
   if (tid == 0) sh_nc = 0;
   __syncthreads();
   for (int64_t li = blockIdx.x; li < cnt; li += gridDim.x) {
     const int64_t i = lbeg + li;
     const NodeCtx c = load_node(a, i);
-    if (GLOBAL) {
-      const int64_t off = hoff[li];
-      tcap = hub_table_slots(c.re - c.rs);
-      vals = gvals + off;
-      keys = gkeys + off;
-      clist = glist + off / 2;
-      for (int64_t j = tid; j < tcap; j += NT) { keys[j] = -1; vals[j] = 0; }
-      __syncthreads();
-    }
     const bool ov = a.mode != MODE_CLUSTER && a.W[c.own] > c.bound;
     const int32_t nl = a.mode != MODE_CLUSTER ? a.nlab[c.slot] : 0;
     const bool direct = a.mode != MODE_CLUSTER && nl <= tcap;
     const int64_t deg = c.re - c.rs;
     const int logcap = ceil_log2(max64(2 * deg, 32));
     const uint32_t mask = (1u << logcap) - 1;
-    if (staged && tid == 0) {
-      // the buffer was last read two chunks ago, before a CTA barrier
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      hub_issue(a, c.rs, min64(c.rs + HUB_CH, c.re), scol[kchunk & 1], sew[kchunk & 1],
-                &hub_bar[kchunk & 1]);
-    }
     for (int64_t e0 = c.rs; e0 < c.re; e0 += 4 * NT) {
       int32_t C[4], w[4];
-      if (staged) {
-        const int b = (int)(kchunk & 1);
-        const int64_t nx = e0 + HUB_CH;
-        if (tid == 0 && nx < c.re) {
-          // buffer b ^ 1 was last read before the barrier that ended the
-          // previous chunk; order those reads before the copy's writes
-          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          hub_issue(a, nx, min64(nx + HUB_CH, c.re), scol[b ^ 1], sew[b ^ 1], &hub_bar[b ^ 1]);
-        }
-        const bool ok = mbar_wait(&hub_bar[b], phs[b], a.wait_limit);
-        if (__syncthreads_or(!ok)) {
-          // the copy did not complete in time: report, let the copies in
-          // flight land (bounded), leave
-          if (tid == 0) atomicOr(a.err, DERR_TIMEOUT);
-          mbar_wait(&hub_bar[b], phs[b], a.wait_limit);
-          if (nx < c.re) mbar_wait(&hub_bar[b ^ 1], phs[b ^ 1], a.wait_limit);
-          return;
-        }
-        phs[b] ^= 1u;
-        int64_t w0, w1;
-        hub_window(e0, min64(e0 + HUB_CH, c.re), a.M, &w0, &w1);
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int64_t e = e0 + (int64_t)u * NT + tid;
-          C[u] = -1;
-          w[u] = 0;
-          if (e < c.re) {
-            if (e < w1) {
-              C[u] = scol[b][e - w0];
-              w[u] = a.ew ? sew[b][e - w0] : 1;
-            } else {
-              C[u] = a.col[e];
-              w[u] = wat(a.ew, e);
-            }
-          }
-        }
-      } else {
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int64_t e = e0 + (int64_t)u * NT + tid;
-          const bool in = e < c.re;
-          w[u] = in ? wat(a.ew, e) : 0;
-          C[u] = in ? a.col[e] : -1;
-        }
+      for (int u = 0; u < 4; ++u) {
+        const int64_t e = e0 + (int64_t)u * NT + tid;
+        const bool in = e < c.re;
+        w[u] = in ? wat(a.ew, e) : 0;
+        C[u] = in ? a.col[e] : -1;
       }
 #pragma unroll
       for (int u = 0; u < 4; ++u)
@@ -889,10 +803,6 @@ __global__ void __launch_bounds__(NT) k_propose_blk(LPArgs a, int32_t sub, int32
           base = __shfl_sync(0xffffffffu, base, first);
           if (cr) clist[base + __popc(cm & ((1u << lane) - 1))] = (int32_t)s;
         }
-      }
-      if (staged) {          // every thread is done with this chunk's buffer
-        ++kchunk;
-        __syncthreads();
       }
     }
     __syncthreads();
@@ -947,45 +857,367 @@ __global__ void __launch_bounds__(NT) k_propose_blk(LPArgs a, int32_t sub, int32
   }
 }
 
-// Table regions of the hubs of colour class `sub`: hoff[li] = exclusive
-// prefix of hub_table_slots(degree) over the class's hub list (one CTA,
-// chunks of its size with a running carry); hoff[cnt] = the total.
+// ------------------------------------------------------------------ hubs
+// Hubs (degree above 8192) are split over the grid in two launches.
+//   k_hub_accum   the row of each hub is cut into parts of HUB_PART arcs;
+//                 CTAs take parts in turn and add every arc's weight into
+//                 the hub's table in global memory (its own region of
+//                 hub_table_slots(degree) entries; in local search with few
+//                 labels, direct-indexed by label and pre-summed per part in
+//                 shared memory);
+//   k_hub_select  the table (or the nl label entries) is cut into chunks of
+//                 HUB_SC entries; CTAs take chunks in turn, evaluate the
+//                 candidates of their chunk, reset the entries they read,
+//                 and leave the chunk's best; the CTA that completes a
+//                 hub's last chunk (a per-hub counter, no waiting) reduces
+//                 the chunks' bests and writes the hub's proposal.
+// The table pool is clean (keys -1, sums 0) before the first launch and
+// after every selection.  Results equal the per-node procedure's: the same
+// sums, the same candidates, the same order-free best.
+constexpr int64_t HUB_PART = 16384;
+constexpr int HUB_SC = 8192;
+constexpr int HUB_DACC = 1024;
+
+struct HubSel {
+  int64_t* hoff;      // [cnt + 1] table regions (exclusive scan of table slots)
+  int64_t* hpa;       // [cnt + 1] accumulation parts
+  int64_t* hpb;       // [cnt + 1] selection chunks
+  int32_t* hdone;     // [cnt] chunks selected so far
+  Cand* pcd;          // best candidate of each selection chunk
+  long long* poc;     // the node's own connection seen by each chunk
+};
+
+__device__ __forceinline__ bool hub_direct(const LPArgs& a, int32_t nl, int64_t tcap) {
+  return a.mode != MODE_CLUSTER && nl <= tcap;
+}
+
+// Offsets of colour class `sub`'s hubs (one CTA, chunks of its size with a
+// running carry): hoff / hpa / hpb = exclusive prefixes of table slots,
+// parts and selection chunks over the class's hub list, with the totals at
+// [cnt]; the done counters are cleared.
 constexpr int HO_NT = 1024;
-__global__ void __launch_bounds__(HO_NT) k_hub_offsets(LPArgs a, int32_t sub, int64_t* hoff) {
+__global__ void __launch_bounds__(HO_NT) k_hub_offsets(LPArgs a, int32_t sub, HubSel h) {
   griddep_wait();
-  __shared__ int64_t sh[HO_NT / 32];
-  __shared__ int64_t carry;
+  __shared__ int64_t sh[3][HO_NT / 32];
+  __shared__ int64_t carry[3];
   int64_t lbeg, cnt;
   sub_range(a, sub, NB - 1, NB, &lbeg, &cnt);
-  if (threadIdx.x == 0) carry = 0;
+  if (threadIdx.x < 3) carry[threadIdx.x] = 0;
   __syncthreads();
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  int64_t* const out[3] = {h.hoff, h.hpa, h.hpb};
   for (int64_t b0 = 0; b0 < cnt; b0 += HO_NT) {
     const int64_t li = b0 + threadIdx.x;
-    const int64_t x = li < cnt ? hub_table_slots(a.rec2[lbeg + li].y) : 0;
-    int64_t incl = x;
-    for (int o = 1; o < 32; o <<= 1) {
-      const int64_t y = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += y;
+    int64_t x[3] = {0, 0, 0};
+    if (li < cnt) {
+      const int64_t deg = a.rec2[lbeg + li].y;
+      const int32_t slot = a.rec[lbeg + li].w;
+      const int64_t tcap = hub_table_slots(deg);
+      const int32_t nl = a.mode != MODE_CLUSTER ? a.nlab[slot] : 0;
+      const int64_t range = hub_direct(a, nl, tcap) ? nl : tcap;
+      x[0] = tcap;
+      x[1] = (deg + HUB_PART - 1) / HUB_PART;
+      x[2] = max64((range + HUB_SC - 1) / HUB_SC, 1);
+      h.hdone[li] = 0;
     }
-    if (lane == 31) sh[wib] = incl;
+    int64_t incl[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      incl[k] = x[k];
+      for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, incl[k], o);
+        if (lane >= o) incl[k] += y;
+      }
+      if (lane == 31) sh[k][wib] = incl[k];
+    }
     __syncthreads();
     if (wib == 0) {
-      int64_t t = sh[lane];
-      for (int o = 1; o < 32; o <<= 1) {
-        const int64_t y = __shfl_up_sync(0xffffffffu, t, o);
-        if (lane >= o) t += y;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        int64_t t = sh[k][lane];
+        for (int o = 1; o < 32; o <<= 1) {
+          const int64_t y = __shfl_up_sync(0xffffffffu, t, o);
+          if (lane >= o) t += y;
+        }
+        sh[k][lane] = t;                  // inclusive over warps
       }
-      sh[lane] = t;                       // inclusive over warps
     }
     __syncthreads();
-    const int64_t before = carry + (wib ? sh[wib - 1] : 0);
-    if (li < cnt) hoff[li] = before + incl - x;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int64_t before = carry[k] + (wib ? sh[k][wib - 1] : 0);
+      if (li < cnt) out[k][li] = before + incl[k] - x[k];
+    }
     __syncthreads();
-    if (threadIdx.x == 0) carry += sh[HO_NT / 32 - 1];
+    if (threadIdx.x < 3) carry[threadIdx.x] += sh[threadIdx.x][HO_NT / 32 - 1];
     __syncthreads();
   }
-  if (threadIdx.x == 0) hoff[cnt] = carry;
+  if (threadIdx.x < 3) out[threadIdx.x][cnt] = carry[threadIdx.x];
+}
+
+// Last hub position li with off[li] <= q (off nondecreasing, off[0] = 0).
+__device__ __forceinline__ int64_t hub_owner(const int64_t* off, int64_t cnt, int64_t q) {
+  int64_t lo = 0, hi = cnt - 1;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= q) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+constexpr size_t hub_accum_smem() {
+  return hub_smem_bytes() + (size_t)HUB_DACC * sizeof(unsigned long long);
+}
+
+__global__ void __launch_bounds__(HUB_NT) k_hub_accum(LPArgs a, int32_t sub, int32_t* gkeys,
+                                                      unsigned long long* gvals, HubSel h) {
+  griddep_wait();
+  int64_t lbeg, cnt;
+  sub_range(a, sub, NB - 1, NB, &lbeg, &cnt);
+  if (cnt == 0) return;
+  extern __shared__ unsigned long long smem_u64[];
+  __shared__ uint64_t hub_bar[2];
+  const int tid = threadIdx.x;
+  // rows staged chunk by chunk in two shared-memory buffers by bulk copies
+  // (when col and the weights start on 16-byte boundaries); the next chunk
+  // is copied while the CTA works on the current one
+  int32_t* sb = reinterpret_cast<int32_t*>(smem_u64);
+  int32_t* scol[2] = {sb, sb + HUB_BUF};
+  int32_t* sew[2] = {sb + 2 * HUB_BUF, sb + 3 * HUB_BUF};
+  unsigned long long* sacc = smem_u64 + (2 * 2 * HUB_BUF) / 2;   // after the staging buffers
+  const bool staged =
+      ((reinterpret_cast<uintptr_t>(a.col) | reinterpret_cast<uintptr_t>(a.ew)) & 15) == 0;
+  uint32_t kchunk = 0, phs[2] = {0, 0};
+  if (tid == 0) {
+    mbar_init(&hub_bar[0], 1);
+    mbar_init(&hub_bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  for (int j = tid; j < HUB_DACC; j += HUB_NT) sacc[j] = 0;
+  __syncthreads();
+  const int64_t total = h.hpa[cnt];
+  for (int64_t q = blockIdx.x; q < total; q += gridDim.x) {
+    const int64_t li = hub_owner(h.hpa, cnt, q);
+    const NodeCtx c = load_node(a, lbeg + li);
+    const int64_t p0 = c.rs + (q - h.hpa[li]) * HUB_PART;
+    const int64_t p1 = min64(p0 + HUB_PART, c.re);
+    const int64_t deg = c.re - c.rs;
+    const int64_t tcap = hub_table_slots(deg);
+    int32_t* keys = gkeys + h.hoff[li];
+    unsigned long long* vals = gvals + h.hoff[li];
+    const int32_t nl = a.mode != MODE_CLUSTER ? a.nlab[c.slot] : 0;
+    const bool direct = hub_direct(a, nl, tcap);
+    const bool pre = direct && nl <= HUB_DACC;
+    const int logcap = ceil_log2(tcap);
+    const uint32_t mask = (1u << logcap) - 1;
+    if (staged && tid == 0) {
+      // the buffer was last read two chunks ago, before a CTA barrier
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      hub_issue(a, p0, min64(p0 + HUB_CH, p1), scol[kchunk & 1], sew[kchunk & 1],
+                &hub_bar[kchunk & 1]);
+    }
+    for (int64_t e0 = p0; e0 < p1; e0 += HUB_CH) {
+      int32_t C[4], w[4];
+      if (staged) {
+        const int b = (int)(kchunk & 1);
+        const int64_t nx = e0 + HUB_CH;
+        if (tid == 0 && nx < p1) {
+          // buffer b ^ 1 was last read before the barrier that ended the
+          // previous chunk; order those reads before the copy's writes
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          hub_issue(a, nx, min64(nx + HUB_CH, p1), scol[b ^ 1], sew[b ^ 1], &hub_bar[b ^ 1]);
+        }
+        const bool ok = mbar_wait(&hub_bar[b], phs[b], a.wait_limit);
+        if (__syncthreads_or(!ok)) {
+          // the copy did not complete in time: report, let the copies in
+          // flight land (bounded), leave
+          if (tid == 0) atomicOr(a.err, DERR_TIMEOUT);
+          mbar_wait(&hub_bar[b], phs[b], a.wait_limit);
+          if (nx < p1) mbar_wait(&hub_bar[b ^ 1], phs[b ^ 1], a.wait_limit);
+          return;
+        }
+        phs[b] ^= 1u;
+        int64_t w0, w1;
+        hub_window(e0, min64(e0 + HUB_CH, p1), a.M, &w0, &w1);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int64_t e = e0 + (int64_t)u * HUB_NT + tid;
+          C[u] = -1;
+          w[u] = 0;
+          if (e < p1) {
+            if (e < w1) {
+              C[u] = scol[b][e - w0];
+              w[u] = a.ew ? sew[b][e - w0] : 1;
+            } else {
+              C[u] = a.col[e];
+              w[u] = wat(a.ew, e);
+            }
+          }
+        }
+      } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int64_t e = e0 + (int64_t)u * HUB_NT + tid;
+          const bool in = e < p1;
+          w[u] = in ? wat(a.ew, e) : 0;
+          C[u] = in ? a.col[e] : -1;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (C[u] >= 0) C[u] = a.label[C[u]];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (C[u] < 0) continue;
+        if (direct) {
+          const int32_t key = (int32_t)(C[u] - c.loff);
+          conn_add(pre ? &sacc[key] : &vals[key], w[u], a.narrow);
+          continue;
+        }
+        const int32_t key = C[u];
+        uint32_t s = table_slot(key, logcap);
+        const uint32_t pmax = a.probe_limit <= mask ? a.probe_limit : mask + 1;
+        bool placed = false;
+        for (uint32_t p = 0; p < pmax; ++p) {
+          const int32_t prev = atomicCAS(&keys[s], -1, key);
+          if (prev == -1 || prev == key) {
+            conn_add(&vals[s], w[u], a.narrow);
+            placed = true;
+            break;
+          }
+          s = (s + 1) & mask;
+        }
+        if (!placed) atomicOr(a.err, DERR_HASH_FULL);
+      }
+      if (staged) {          // every thread is done with this chunk's buffer
+        ++kchunk;
+        __syncthreads();
+      }
+    }
+    if (pre) {
+      // the part's per-label sums into the hub's entries (a part's sum of a
+      // label is at most its row's, so the narrow rule still holds)
+      __syncthreads();
+      for (int32_t b = tid; b < nl; b += HUB_NT) {
+        const unsigned long long x = sacc[b];
+        if (!x) continue;
+        sacc[b] = 0;
+        if (a.narrow) atomicAdd(reinterpret_cast<unsigned int*>(&vals[b]), (unsigned int)x);
+        else atomicAdd(&vals[b], x);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ Cand ld_cand_cg(const Cand* p) {
+  Cand c;
+  c.conn = __ldcg(&p->conn);
+  c.h = __ldcg(reinterpret_cast<const unsigned long long*>(&p->h));
+  c.C = __ldcg(&p->C);
+  return c;
+}
+
+__global__ void __launch_bounds__(HUB_NT) k_hub_select(LPArgs a, int32_t sub, int32_t* gkeys,
+                                                       unsigned long long* gvals, HubSel h) {
+  griddep_wait();
+  int64_t lbeg, cnt;
+  sub_range(a, sub, NB - 1, NB, &lbeg, &cnt);
+  if (cnt == 0) return;
+  __shared__ long long sh_oc[HUB_NT / 32];
+  __shared__ Cand sh_cd[HUB_NT / 32];
+  __shared__ int sh_last;
+  const int tid = threadIdx.x;
+  const int64_t total = h.hpb[cnt];
+  for (int64_t q = blockIdx.x; q < total; q += gridDim.x) {
+    const int64_t li = hub_owner(h.hpb, cnt, q);
+    const int64_t i = lbeg + li;
+    const NodeCtx c = load_node(a, i);
+    const int64_t q0 = h.hpb[li], nchunks = h.hpb[li + 1] - q0;
+    const int64_t tcap = hub_table_slots(c.re - c.rs);
+    int32_t* keys = gkeys + h.hoff[li];
+    unsigned long long* vals = gvals + h.hoff[li];
+    const int32_t nl = a.mode != MODE_CLUSTER ? a.nlab[c.slot] : 0;
+    const bool direct = hub_direct(a, nl, tcap);
+    const bool ov = a.mode != MODE_CLUSTER && a.W[c.own] > c.bound;
+    long long oc = 0;
+    Cand cd{-1, 0, 0};
+    const int64_t j0 = (q - q0) * HUB_SC;
+    if (direct) {
+      const int32_t own_l = (int32_t)(c.own - c.loff);
+      const int64_t j1 = min64(j0 + HUB_SC, (int64_t)nl);
+      for (int64_t b = j0 + tid; b < j1; b += HUB_NT) {
+        const int64_t conn = (int64_t)vals[b];
+        if (conn) vals[b] = 0;
+        if (b == own_l) { oc = conn; continue; }
+        if (conn == 0 && !ov) continue;
+        const int32_t Cb = (int32_t)(c.loff + b);
+        if ((int64_t)a.W[Cb] + c.cv > c.bound) continue;
+        Cand x = make_cand(c, Cb, conn);
+        if (cd.conn < 0 || cand_better(x, cd)) cd = x;
+      }
+    } else if (!ov) {
+      const int64_t j1 = min64(j0 + HUB_SC, tcap);
+      for (int64_t s = j0 + tid; s < j1; s += HUB_NT) {
+        const int32_t K = keys[s];
+        if (K < 0) continue;
+        const int64_t conn = (int64_t)vals[s];
+        keys[s] = -1;
+        vals[s] = 0;
+        if (K == c.own) { oc = conn; continue; }
+        if ((int64_t)a.W[K] + c.cv > c.bound) continue;
+        if (cand_block(a, c, true, K) != c.vb) continue;
+        Cand x = make_cand(c, K, conn);
+        if (cd.conn < 0 || cand_better(x, cd)) cd = x;
+      }
+    }
+    block_reduce<HUB_NT>(oc, cd, sh_oc, sh_cd);
+    if (tid == 0) {
+      h.pcd[q] = cd;
+      h.poc[q] = oc;
+      __threadfence();
+      sh_last = atomicAdd(&h.hdone[li], 1) == (int32_t)(nchunks - 1);
+    }
+    __syncthreads();
+    if (sh_last) {
+      __threadfence();
+      oc = 0;
+      cd = Cand{-1, 0, 0};
+      if (!direct && ov) {
+        // an overloaded node whose labels outnumber its table (local search
+        // with more blocks than table entries): every label is a candidate,
+        // its connection looked up; the chunks left the table to this CTA
+        const int logcap = ceil_log2(tcap);
+        oc = table_get(keys, vals, logcap, c.own);
+        for (int32_t b = tid; b < nl; b += HUB_NT) {
+          const int32_t Cb = (int32_t)(c.loff + b);
+          if (Cb == c.own || (int64_t)a.W[Cb] + c.cv > c.bound) continue;
+          Cand x = make_cand(c, Cb, table_get(keys, vals, logcap, Cb));
+          if (cd.conn < 0 || cand_better(x, cd)) cd = x;
+        }
+        __syncthreads();
+        for (int64_t s = tid; s < tcap; s += HUB_NT) {
+          keys[s] = -1;
+          vals[s] = 0;
+        }
+      } else {
+        for (int64_t k = tid; k < nchunks; k += HUB_NT) {
+          const long long o = __ldcg(&h.poc[q0 + k]);
+          if (o > oc) oc = o;
+          const Cand x = ld_cand_cg(&h.pcd[q0 + k]);
+          if (x.conn >= 0 && (cd.conn < 0 || cand_better(x, cd))) cd = x;
+        }
+      }
+      __syncthreads();                   // sh_oc / sh_cd reused
+      block_reduce<HUB_NT>(oc, cd, sh_oc, sh_cd);
+      if (tid == 0) {
+        write_prop(a, i, c, cd, oc, ov);
+        h.hdone[li] = 0;
+      }
+    }
+    __syncthreads();
+  }
 }
 
 // ------------------------------------------------------------- admission
@@ -1791,16 +2023,21 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, wgt_t*
   // bound of the sum; CUDA-graph rounds: the sum over all hubs of the
   // level).
   int64_t pool_slots = 0;
-  DevBuf<int32_t> gkeys, glist;
+  DevBuf<int32_t> gkeys, hub_done;
   DevBuf<unsigned long long> gvals;
   DevBuf<int64_t> hub_off;
+  DevBuf<Cand> hub_pcd;
+  DevBuf<long long> hub_poc;
+  HubSel hs{};
   int gblocks = 0;
+  // the pool starts clean (keys -1, sums 0); every selection leaves it so
   auto ensure_pool = [&](int64_t slots) {
     if (slots <= pool_slots) return;
     slots = std::max<int64_t>(slots, 1024);
     gkeys.alloc((size_t)slots, s);
     gvals.alloc((size_t)slots, s);
-    glist.alloc((size_t)(slots / 2), s);
+    gkeys.fill_bytes(0xff);
+    gvals.zero();
     pool_slots = slots;
   };
 
@@ -1855,8 +2092,21 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, wgt_t*
                          maxdeg > B4_MAXDEG, maxdeg > B5_MAXDEG, maxdeg > B6_MAXDEG,
                          maxdeg > B7_MAXDEG};
   if (need[8]) {
-    gblocks = (int)std::max<int64_t>(1, std::min<int64_t>(sms * 2, nhubs));
-    hub_off.alloc((size_t)(nhubs + 1), s);
+    gblocks = sms * 2;
+    // per hub of a class: offsets of its table, parts and selection chunks
+    // (three arrays), its done counter; per selection chunk (at most one per
+    // HUB_SC table slots of the level's hubs, plus one per hub): its best
+    hub_off.alloc((size_t)(3 * (nhubs + 1)), s);
+    hub_done.alloc((size_t)nhubs, s);
+    const int64_t nchunk = hub_slots / HUB_SC + nhubs + 1;
+    hub_pcd.alloc((size_t)nchunk, s);
+    hub_poc.alloc((size_t)nchunk, s);
+    hs.hoff = hub_off.p;
+    hs.hpa = hub_off.p + (nhubs + 1);
+    hs.hpb = hub_off.p + 2 * (nhubs + 1);
+    hs.hdone = hub_done.p;
+    hs.pcd = hub_pcd.p;
+    hs.poc = hub_poc.p;
     if (run.graph) ensure_pool(hub_slots);
   }
   constexpr size_t smem5 = blk_smem_bytes<B5_SLOTS>();
@@ -1864,9 +2114,9 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, wgt_t*
   constexpr size_t smem7 = blk_smem_bytes<B7_SLOTS>();
   static std::once_flag attrs_once;
   std::call_once(attrs_once, [&] {
-    SCLAP_CUDA(cudaFuncSetAttribute(k_propose_blk<256, B6_SLOTS, false>,
+    SCLAP_CUDA(cudaFuncSetAttribute(k_propose_blk<256, B6_SLOTS>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem6));
-    SCLAP_CUDA(cudaFuncSetAttribute(k_propose_blk<512, B7_SLOTS, false>,
+    SCLAP_CUDA(cudaFuncSetAttribute(k_propose_blk<512, B7_SLOTS>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem7));
   });
   // fixed launch shapes: kernels read their node ranges on the device and
@@ -1960,8 +2210,6 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, wgt_t*
       return grid_for(ho[sub * NB + b1] - ho[sub * NB + b0], per, cap);
     };
     // family 0 first: it holds most nodes, and the first launch gets the SMs
-    int32_t* const no_i = nullptr;
-    unsigned long long* const no_u = nullptr;
     launch(0, nsb, 0, [&](cudaStream_t ls, bool p) {
       launch_k(p, k_propose_small, grid(0, nsb, 256, grid_small), 256, 0, ls, a, sub, nsb); SCLAP_NOTE_LAUNCH("k_propose_small");
     });
@@ -1969,17 +2217,18 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, wgt_t*
       launch_k(p, k_propose_warp, grid(nsb, 5, WPC, grid_warp), WPC * 32, 0, ls, a, sub, nsb); SCLAP_NOTE_LAUNCH("k_propose_warp");
     });
     if (need[5]) launch(5, 6, 1, [&](cudaStream_t ls, bool p) {
-      launch_k(p, k_propose_blk<128, B5_SLOTS, false>, grid(5, 6, 1, grid_b5), 128, smem5, ls, a, sub, 5, no_i, no_u, no_i, (const int64_t*)nullptr); SCLAP_NOTE_LAUNCH("k_propose_blk128");
+      launch_k(p, k_propose_blk<128, B5_SLOTS>, grid(5, 6, 1, grid_b5), 128, smem5, ls, a, sub, 5); SCLAP_NOTE_LAUNCH("k_propose_blk128");
     });
     if (need[6]) launch(6, 7, 2, [&](cudaStream_t ls, bool p) {
-      launch_k(p, k_propose_blk<256, B6_SLOTS, false>, grid(6, 7, 1, grid_b6), 256, smem6, ls, a, sub, 6, no_i, no_u, no_i, (const int64_t*)nullptr); SCLAP_NOTE_LAUNCH("k_propose_blk256");
+      launch_k(p, k_propose_blk<256, B6_SLOTS>, grid(6, 7, 1, grid_b6), 256, smem6, ls, a, sub, 6); SCLAP_NOTE_LAUNCH("k_propose_blk256");
     });
     if (need[7]) launch(7, 8, 2, [&](cudaStream_t ls, bool p) {
-      launch_k(p, k_propose_blk<512, B7_SLOTS, false>, grid(7, 8, 1, grid_b7), 512, smem7, ls, a, sub, 7, no_i, no_u, no_i, (const int64_t*)nullptr); SCLAP_NOTE_LAUNCH("k_propose_blk512");
+      launch_k(p, k_propose_blk<512, B7_SLOTS>, grid(7, 8, 1, grid_b7), 512, smem7, ls, a, sub, 7); SCLAP_NOTE_LAUNCH("k_propose_blk512");
     });
     if (need[8]) launch(8, 9, 3, [&](cudaStream_t ls, bool p) {
-      launch_k(p, k_hub_offsets, 1, HO_NT, 0, ls, a, sub, hub_off.p); SCLAP_NOTE_LAUNCH("k_hub_offsets");
-      launch_k(tu.pdl != 0, k_propose_blk<HUB_NT, 1, true>, (unsigned)gblocks, HUB_NT, hub_smem_bytes(), ls, a, sub, 8, gkeys.p, gvals.p, glist.p, (const int64_t*)hub_off.p); SCLAP_NOTE_LAUNCH("k_propose_hub");
+      launch_k(p, k_hub_offsets, 1, HO_NT, 0, ls, a, sub, hs); SCLAP_NOTE_LAUNCH("k_hub_offsets");
+      launch_k(tu.pdl != 0, k_hub_accum, (unsigned)gblocks, HUB_NT, hub_accum_smem(), ls, a, sub, gkeys.p, gvals.p, hs); SCLAP_NOTE_LAUNCH("k_hub_accum");
+      launch_k(tu.pdl != 0, k_hub_select, (unsigned)gblocks, HUB_NT, 0, ls, a, sub, gkeys.p, gvals.p, hs); SCLAP_NOTE_LAUNCH("k_hub_select");
     });
     if (fork) {
       for (int j = 0; j < nside; ++j) {

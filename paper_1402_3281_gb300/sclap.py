@@ -87,7 +87,7 @@ class Tuning(C.Structure):
     _fields_ = [(n, C.c_int32) for n in ("small_max_deg", "small_ctas_per_sm",
                                          "warp_ctas_per_sm", "admit_ctas_per_sm", "concurrent",
                                          "pdl", "fused_admission", "contract_table_slots",
-                                         "ip_trial_group")]
+                                         "ip_trial_group", "contract_merge")]
 
     def to_dict(self) -> dict:
         return {n: getattr(self, n) for n, _ in self._fields_}

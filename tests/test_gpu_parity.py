@@ -44,6 +44,22 @@ def hub_graph(seed=0):
     return gg.from_edges(n + 9000, s, d, name="hub")
 
 
+def split_hub_graph(seed=0):
+    """R-MAT with two hubs whose rows span several accumulation parts
+    (16,384 arcs each): node 0 joined to 40,000 new leaves, node 1 to the
+    last 20,000 of them; every leaf also meets one of nodes 2..200.  Random
+    node and edge weights."""
+    base = gg.rmat(12, 8, seed)
+    n, L = base.n, 40000
+    src = np.repeat(np.arange(n), np.diff(base.row_ptr))
+    keep = src < base.col
+    leaves = np.arange(n, n + L)
+    s = np.concatenate([src[keep], np.zeros(L, np.int64), np.ones(L // 2, np.int64), leaves])
+    d = np.concatenate([base.col[keep], leaves, leaves[L // 2:], 2 + np.arange(L) % 199])
+    g = gg.from_edges(n + L, s, d, name="split-hub")
+    return gg.random_weights(g, seed + 5, max_node_w=3, max_edge_w=5)
+
+
 GRAPHS = {
     "rmat12": lambda: gg.rmat(12, 8, 1),
     "rmat16": lambda: gg.rmat(16, 8, 0),
@@ -51,6 +67,7 @@ GRAPHS = {
     "weighted": lambda: gg.random_weights(gg.rmat(11, 8, 4), 7, max_node_w=5, max_edge_w=9),
     "star": lambda: gg.star(3000),
     "hub": lambda: hub_graph(2),
+    "split_hub": lambda: split_hub_graph(3),
 }
 
 
@@ -244,7 +261,7 @@ def test_cut_matches_oracle(graph):
 # ------------------------------------------------------------------ end to end
 E2E = [
     ("rmat16", 2), ("rmat16", 8), ("rmat12", 4), ("rgg", 2), ("rgg", 16), ("weighted", 3),
-    ("star", 2), ("hub", 4),
+    ("star", 2), ("hub", 4), ("split_hub", 8), ("split_hub", 64),
 ]
 
 
@@ -273,7 +290,8 @@ def test_partition_active_coarsening_bit_exact(name):
     assert res.stats["level_n"] == list(ref.stats.level_n[:ref.stats.levels])
 
 
-@pytest.mark.parametrize("name,k", [("rmat16", 2), ("rgg", 8), ("weighted", 5), ("hub", 4)])
+@pytest.mark.parametrize("name,k", [("rmat16", 2), ("rgg", 8), ("weighted", 5), ("hub", 4),
+                                    ("split_hub", 3)])
 def test_partition_graph_driver_bit_exact(name, k):
     """The rounds run as one CUDA graph (device-side loop condition) give the
     same partition as the host-driven rounds and the oracle."""

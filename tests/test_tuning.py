@@ -13,7 +13,8 @@ import oracle as O
 import paper_1402_3281_gb300 as P
 
 DEFAULT = dict(small_max_deg=16, small_ctas_per_sm=8, warp_ctas_per_sm=8, admit_ctas_per_sm=16,
-               concurrent=1, pdl=1, fused_admission=0, contract_table_slots=0, ip_trial_group=0)
+               concurrent=1, pdl=1, fused_admission=0, contract_table_slots=0, ip_trial_group=0,
+               contract_merge=0)
 
 
 @pytest.fixture
@@ -33,7 +34,8 @@ def test_default_tuning(restore_tuning):
                                        ("admit_ctas_per_sm", 65), ("concurrent", 2),
                                        ("concurrent", -1), ("pdl", 2),
                                        ("fused_admission", 2), ("fused_admission", -1),
-                                       ("contract_table_slots", -5), ("ip_trial_group", -1)])
+                                       ("contract_table_slots", -5), ("ip_trial_group", -1),
+                                       ("contract_merge", 2), ("contract_merge", -1)])
 def test_out_of_range_values_are_rejected_and_leave_the_setting(restore_tuning, field, bad):
     P.set_tuning(**DEFAULT)
     with pytest.raises(P.SclapError) as e:
@@ -45,10 +47,10 @@ def test_out_of_range_values_are_rejected_and_leave_the_setting(restore_tuning, 
 def test_set_tuning_round_trip(restore_tuning):
     t = P.set_tuning(small_max_deg=8, small_ctas_per_sm=3, warp_ctas_per_sm=32,
                      admit_ctas_per_sm=1, concurrent=0, pdl=0, fused_admission=1,
-                     contract_table_slots=4096, ip_trial_group=3)
+                     contract_table_slots=4096, ip_trial_group=3, contract_merge=1)
     assert t.to_dict() == dict(small_max_deg=8, small_ctas_per_sm=3, warp_ctas_per_sm=32,
                                admit_ctas_per_sm=1, concurrent=0, pdl=0, fused_admission=1,
-                               contract_table_slots=4096, ip_trial_group=3)
+                               contract_table_slots=4096, ip_trial_group=3, contract_merge=1)
 
 
 # ------------------------------------------------------------------ GPU
@@ -73,6 +75,8 @@ SETTINGS = [
          concurrent=0),
     dict(fused_admission=1),
     dict(fused_admission=1, admit_ctas_per_sm=1, concurrent=0),
+    dict(contract_merge=1),               # contraction by member lists and merges
+    dict(contract_merge=1, contract_table_slots=4096),   # merges where they fit, else passes
     dict(contract_table_slots=4096),      # contraction in passes of 4096 slots
     dict(contract_table_slots=1),         # a pass per coarse node
     dict(ip_trial_group=1),               # initial-partitioning trials one at a time
@@ -189,6 +193,45 @@ def test_contraction_in_passes_equals_the_oracle(restore_tuning, slots):
     P.set_tuning(**{**DEFAULT, "contract_table_slots": slots})
     for label in (O.cluster(g, 40, seed=2)[0],
                   np.random.default_rng(4).integers(0, g.n // 30, g.n).astype(np.int32)):
+        c = O.contract(g, label)
+        cmap, crp, ccol, cnw, cew = P.sclap_contract(t(g.row_ptr), t(g.col), t(g.node_w),
+                                                     t(g.edge_w), t(label))
+        assert np.array_equal(cmap.cpu().numpy(), c.cmap)
+        assert np.array_equal(cnw.cpu().numpy(), c.node_w)
+        assert np.array_equal(crp.cpu().numpy(), c.row_ptr)
+        a = _canon(crp.cpu().numpy(), ccol.cpu().numpy(), cew.cpu().numpy())
+        b = _canon(c.row_ptr, c.col, c.edge_w)
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
+
+
+def _grid_blocks(rows, cols, bh, bw):
+    r, c = np.divmod(np.arange(rows * cols), cols)
+    return ((r // bh) * -(-cols // bw) + c // bw).astype(np.int32)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("merge", [1, 0])
+def test_contraction_by_merges_covers_every_class(restore_tuning, merge):
+    """Grid blocks give coarse nodes of each merge class: 10x10 blocks (40
+    inter-cluster arcs, 400 member arcs: a warp each), 40x40 (160 and 6,400:
+    a CTA each), 50-row strips (400 inter-cluster arcs but 40,000 member
+    arcs: large), and a star whose centre is a cluster of its own (4,999
+    inter-cluster arcs: large).  Same coarse graph as the oracle with merges
+    on or off."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    dev = torch.device("cuda:0")
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    P.set_tuning(**{**DEFAULT, "contract_merge": merge})
+    grid = gg.random_weights(gg.grid(200, 200), 8)
+    star = gg.random_weights(gg.star(4999), 9)
+    cases = [(grid, _grid_blocks(200, 200, 10, 10)), (grid, _grid_blocks(200, 200, 40, 40)),
+             (grid, _grid_blocks(200, 200, 50, 200)),
+             (grid, np.where(np.arange(40000) < 36000, 0, np.arange(40000)).astype(np.int32)),
+             (star, np.where(np.arange(5000) == 0, 0, 1 + np.arange(5000) % 7).astype(np.int32))]
+    for g, label in cases:
         c = O.contract(g, label)
         cmap, crp, ccol, cnw, cew = P.sclap_contract(t(g.row_ptr), t(g.col), t(g.node_w),
                                                      t(g.edge_w), t(label))
