@@ -598,6 +598,7 @@ struct GGGArgs {
   int64_t* conn;           // scratch [N]
   int32_t* step;           // scratch [N]
   int32_t* front;          // scratch [N]: newly reached nodes (step alternates with it)
+  int32_t* heavy;          // scratch [N]: a step's long rows (grouped growing)
   int64_t* wfA;            // scratch [sum k]
   int32_t* wforder;        // scratch [sum k]
   int32_t nslots;

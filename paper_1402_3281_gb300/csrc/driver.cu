@@ -483,7 +483,7 @@ void run_ip(const std::vector<IPIn>& in, const sclap_config& cfg, wgt_t* Wg,
     return *aux.back().second;
   };
   // Trials run in groups whose replicated graphs fit in memory (all of them
-  // at once unless the coarsest graphs are very large): about 200 bytes per
+  // at once unless the coarsest graphs are very large): about 204 bytes per
   // node and 8 per arc of each trial copy (graph, growing and LP state),
   // against half of the device memory still obtainable, or the tuning's
   // group size.  Results do not depend on the grouping: a trial's
@@ -494,7 +494,7 @@ void run_ip(const std::vector<IPIn>& in, const sclap_config& cfg, wgt_t* Wg,
     const Level& Q = *in[g].Q;
     LevelAux& X = aux_of(&Q);
     const int x = in[g].g;
-    per_trial += 200 * (X.rank_at[x + 1] - X.rank_at[x]) + 8 * (Q.aoff[x + 1] - Q.aoff[x]) + 64;
+    per_trial += 204 * (X.rank_at[x + 1] - X.rank_at[x]) + 8 * (Q.aoff[x + 1] - Q.aoff[x]) + 64;
   }
   const Tuning tu = tuning_get();
   const int64_t fit = tu.ip_trial_group > 0
@@ -545,7 +545,7 @@ void run_ip(const std::vector<IPIn>& in, const sclap_config& cfg, wgt_t* Wg,
 
   const int64_t K = boff[S];
   DevBuf<int32_t> label(std::max<int64_t>(ip.N, 1), s), step(std::max<int64_t>(ip.N, 1), s),
-      front(std::max<int64_t>(ip.N, 1), s);
+      front(std::max<int64_t>(ip.N, 1), s), heavy(std::max<int64_t>(ip.N, 1), s);
   DevBuf<wgt_t> W(std::max<int64_t>(K, 1), s);
   DevBuf<int64_t> conn(std::max<int64_t>(ip.N, 1), s);
   DevBuf<int64_t> wfA(std::max<int64_t>(K, 1), s), d_boff(S + 1, s), d_avg(S, s);
@@ -571,7 +571,8 @@ void run_ip(const std::vector<IPIn>& in, const sclap_config& cfg, wgt_t* Wg,
   ga.row_ptr = ip.row_ptr.p; ga.col = ip.col.p; ga.ew = ip.ew.p; ga.nw = ip.nw.p;
   ga.noff = ip.noff_d.p; ga.boff = d_boff.p; ga.nlab = sl.nlab.p; ga.avg = d_avg.p;
   ga.tkey = sl.seed.p; ga.level = sl.level.p; ga.label = label.p; ga.W = W.p;
-  ga.conn = conn.p; ga.step = step.p; ga.front = front.p; ga.wfA = wfA.p; ga.wforder = wforder.p;
+  ga.conn = conn.p; ga.step = step.p; ga.front = front.p; ga.heavy = heavy.p;
+  ga.wfA = wfA.p; ga.wforder = wforder.p;
   ga.nslots = S;
   ga.err = d_err;
   ggg_trials(ga, noff, h_nlab, s);

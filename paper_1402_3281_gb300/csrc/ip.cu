@@ -387,14 +387,23 @@ __global__ void __launch_bounds__(GNT) k_ggg(GGGArgs a) {
 // the trial's nodes for the scans (seed search, ordered candidates,
 // water-filling); id-ordered prefixes over the whole trial are the CTAs'
 // partial sums in rank order plus the CTA's own scan.  The step nodes'
-// arcs are shared out by step node in chunks of GG_NT per CTA.  Every
-// decision is a set or an id-ordered prefix, so the result equals k_ggg's.
+// arcs are shared out by step node in chunks of GG_NT per CTA; a step node
+// with more than GG_HEAVY arcs (known in advance: the step that builds the
+// next step records whether it took one) is listed instead, and after a
+// group barrier the listed rows are read by all CTAs of the group together.
+// Every decision is a set or an id-ordered prefix, so the result equals
+// k_ggg's.
 struct GroupState {
   GridSync bar;
   int32_t nstep, nfront, nnext, seed;
   int64_t Wj, fsum, accw;
+  // heavy step nodes (more than GG_HEAVY arcs): whether the current step
+  // has any, whether the frontier / the ordered selection being built took
+  // one, and the current step's list length
+  int32_t step_heavy, front_heavy, next_heavy, nheavy;
 };
 constexpr int GG_NT = 512;
+constexpr int64_t GG_HEAVY = 8 * GG_NT;
 
 __global__ void __launch_bounds__(GG_NT) k_ggg_group(GGGArgs a, int32_t cpt, GroupState* gst,
                                                      uint64_t* ph, int32_t* pv, int64_t* pw,
@@ -441,6 +450,7 @@ __global__ void __launch_bounds__(GG_NT) k_ggg_group(GGGArgs a, int32_t cpt, Gro
   if (!sync()) return;
   int32_t* stp = a.step + base;
   int32_t* frt = a.front + base;
+  int32_t* hvl = a.heavy + base;
   for (int32_t j = 0; j < k; ++j) {
     // seed: unassigned non-isolated node with the smallest hash (the same
     // pass clears the connections of the previous block)
@@ -494,12 +504,30 @@ __global__ void __launch_bounds__(GG_NT) k_ggg_group(GGGArgs a, int32_t cpt, Gro
       st->fsum = 0;
       st->accw = 0;
       st->Wj = a.nw[base + seed];
+      st->step_heavy = a.row_ptr[base + seed + 1] - a.row_ptr[base + seed] > GG_HEAVY;
+      st->front_heavy = 0;
+      st->next_heavy = 0;
+      st->nheavy = 0;
     }
     bool ordered = false;
     if (!sync()) return;
     while (true) {
       const int32_t nstep = *(volatile int32_t*)&st->nstep;
+      const bool hv_step = *(volatile int32_t*)&st->step_heavy != 0;
       int64_t fw = 0;
+      // an arc out of the step: connection of an unassigned head; its first
+      // arc lists it as reached (weights > 0)
+      auto visit = [&](int64_t e) {
+        const int32_t y = a.col[e];
+        if (a.label[y] >= 0) return;
+        const unsigned long long old = atomicAdd(ull(&a.conn[y]), (unsigned long long)a.ew[e]);
+        if (!ordered && old == 0) {
+          frt[atomicAdd(&st->nfront, 1)] = y;
+          fw += a.nw[y];
+          if (a.row_ptr[y + 1] - a.row_ptr[y] > GG_HEAVY)
+            *(volatile int32_t*)&st->front_heavy = 1;
+        }
+      };
       for (int64_t q0 = (int64_t)r * GG_NT; q0 < nstep; q0 += qstride) {
         const int64_t q = q0 + tid;
         int64_t rs = 0, d = 0;
@@ -507,6 +535,10 @@ __global__ void __launch_bounds__(GG_NT) k_ggg_group(GGGArgs a, int32_t cpt, Gro
           const int32_t u = stp[q];
           rs = a.row_ptr[u];
           d = a.row_ptr[u + 1] - rs;
+          if (hv_step && d > GG_HEAVY) {          // read by the whole group below
+            hvl[atomicAdd(&st->nheavy, 1)] = u;
+            d = 0;
+          }
         }
         int64_t tot;
         const int64_t incl = block_incl_scan<GG_NT>(d, sh, &tot);
@@ -521,16 +553,19 @@ __global__ void __launch_bounds__(GG_NT) k_ggg_group(GGGArgs a, int32_t cpt, Gro
             const int mid = (lo + hi) >> 1;
             if (st_in[mid] > x) hi = mid; else lo = mid + 1;
           }
-          const int64_t e = st_rs[lo] + (x - st_ex[lo]);
-          const int32_t y = a.col[e];
-          if (a.label[y] >= 0) continue;
-          const unsigned long long old = atomicAdd(ull(&a.conn[y]), (unsigned long long)a.ew[e]);
-          if (!ordered && old == 0) {          // first arc into y (weights > 0)
-            frt[atomicAdd(&st->nfront, 1)] = y;
-            fw += a.nw[y];
-          }
+          visit(st_rs[lo] + (x - st_ex[lo]));
         }
         __syncthreads();
+      }
+      if (hv_step) {
+        if (!sync()) return;                     // the heavy list is complete
+        const int32_t nh = *(volatile int32_t*)&st->nheavy;
+        for (int32_t hq = 0; hq < nh; ++hq) {
+          const int32_t u = hvl[hq];
+          const int64_t re = a.row_ptr[u + 1];
+          for (int64_t e = a.row_ptr[u] + (int64_t)r * GG_NT + tid; e < re; e += qstride)
+            visit(e);
+        }
       }
       const int64_t fwb = block_sum<GG_NT>(fw, sh);
       if (tid == 0 && fwb) atomicAdd(ull(&st->fsum), (unsigned long long)fwb);
@@ -551,6 +586,9 @@ __global__ void __launch_bounds__(GG_NT) k_ggg_group(GGGArgs a, int32_t cpt, Gro
             st->nfront = 0;
             st->fsum = 0;
             st->Wj = Wj + fsum;
+            st->step_heavy = st->front_heavy;
+            st->front_heavy = 0;
+            st->nheavy = 0;
           }
           if (!sync()) return;
           if (nf == 0) break;
@@ -579,6 +617,8 @@ __global__ void __launch_bounds__(GG_NT) k_ggg_group(GGGArgs a, int32_t cpt, Gro
         if (cand && (all_fit || Wj + carry_w + iw <= avg)) {
           stp[atomicAdd(&st->nnext, 1)] = (int32_t)(base + v);
           acc_w += wt;
+          if (a.row_ptr[base + v + 1] - a.row_ptr[base + v] > GG_HEAVY)
+            *(volatile int32_t*)&st->next_heavy = 1;
         }
         carry_w += tw;
       }
@@ -595,6 +635,10 @@ __global__ void __launch_bounds__(GG_NT) k_ggg_group(GGGArgs a, int32_t cpt, Gro
         st->Wj = newW;
         st->nnext = 0;
         st->accw = 0;
+        st->step_heavy = st->next_heavy;
+        st->next_heavy = 0;
+        st->front_heavy = 0;
+        st->nheavy = 0;
       }
       if (!sync()) return;
       if (ns2 == 0) break;

@@ -1604,12 +1604,14 @@ __device__ void adm_select(const LPArgs& a, int64_t nseg, int32_t source) {
 // ------------------------------------------------------------- apply
 // Admitted moves update labels and weights; moved nodes activate their
 // neighbours (small rows by their own lane, larger rows by the whole warp).
-// In local search, label-weight changes are first summed per CTA in a small
-// shared hash (label -> delta; a label that finds no slot within a few
-// probes goes to global memory directly), then flushed with one atomic per
-// label: moves concentrate on a handful of blocks, whose global counters
-// would otherwise take one atomic per moved node each.  Clustering moves
-// spread over many clusters and update the global weights directly.
+// Label-weight changes are first summed per CTA in a small shared hash
+// (label -> delta; a label that finds no slot within a few probes goes to
+// global memory directly), then flushed with one atomic per label: in local
+// search moves concentrate on a handful of blocks, and in clustering many
+// nodes can join one cluster in a colour class (the leaves of a hub), whose
+// global counters would otherwise take one atomic per moved node each.  The
+// clusters that clustering moves leave are spread out and are updated
+// directly.
 constexpr int APPLY_SLOTS = 1024;
 __device__ __forceinline__ void apply_delta(int32_t* hk, int32_t* hv, wgt_t* W, int32_t L,
                                             int32_t d) {
@@ -1630,11 +1632,9 @@ __device__ void adm_apply(const LPArgs& a, int64_t lbeg, int64_t cnt) {
   uint8_t* const an = act_next(a);
   __shared__ int32_t hk[APPLY_SLOTS];
   __shared__ int32_t hv[APPLY_SLOTS];
-  const bool agg = a.mode != MODE_CLUSTER;
-  if (agg) {
-    for (int j = threadIdx.x; j < APPLY_SLOTS; j += blockDim.x) { hk[j] = -1; hv[j] = 0; }
-    __syncthreads();
-  }
+  const bool agg_src = a.mode != MODE_CLUSTER;
+  for (int j = threadIdx.x; j < APPLY_SLOTS; j += blockDim.x) { hk[j] = -1; hv[j] = 0; }
+  __syncthreads();
   const int lane = threadIdx.x & 31;
   const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -1660,13 +1660,9 @@ __device__ void adm_apply(const LPArgs& a, int64_t lbeg, int64_t cnt) {
             re = r2.x + r2.y;
           }
           a.label[v] = t;
-          if (agg) {
-            apply_delta(hk, hv, a.W, t, cv);
-            apply_delta(hk, hv, a.W, own, -cv);
-          } else {
-            atomicAdd(&a.W[t], (wgt_t)cv);
-            atomicSub(&a.W[own], (wgt_t)cv);
-          }
+          apply_delta(hk, hv, a.W, t, cv);
+          if (agg_src) apply_delta(hk, hv, a.W, own, -cv);
+          else atomicSub(&a.W[own], (wgt_t)cv);
           if (re - rs <= 8) {
             for (int64_t e = rs; e < re; ++e) an[a.col[e]] = 1;
             re = rs;
@@ -1694,11 +1690,9 @@ __device__ void adm_apply(const LPArgs& a, int64_t lbeg, int64_t cnt) {
     }
   }
   if (run_cnt) atomicAdd(ull(&a.moved[run_slot]), run_cnt);
-  if (agg) {
-    __syncthreads();
-    for (int j = threadIdx.x; j < APPLY_SLOTS; j += blockDim.x)
-      if (hk[j] >= 0 && hv[j] != 0) atomicAdd(&a.W[hk[j]], (wgt_t)hv[j]);
-  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < APPLY_SLOTS; j += blockDim.x)
+    if (hk[j] >= 0 && hv[j] != 0) atomicAdd(&a.W[hk[j]], (wgt_t)hv[j]);
 }
 
 constexpr int ADM_NT = 256;
