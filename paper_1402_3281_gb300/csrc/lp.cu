@@ -86,6 +86,12 @@ struct LPArgs {
   // active nodes: act[r & 1] holds round r's flags, act[(r + 1) & 1] the
   // next round's (both NULL when all nodes are always active)
   uint8_t* act[2];
+  // moved rows longer than mark_big arcs (0: none on the level) activate
+  // their neighbours through a queue of arc chunks, per colour class
+  // mqn[sub] entries, read by a launch of their own
+  int64_t mark_big;
+  longlong2* mq;
+  int32_t* mqn;
   // round state on the device, so that a level's rounds need no host
   // decision: the round index, slots still running after k_round_end, and
   // the limits of the run
@@ -179,6 +185,8 @@ __global__ void k_round_begin(LPArgs a, int32_t nslots, int32_t phase,
       a.flags[0] = 0;
     }
     if (threadIdx.x < 8) a.ctr[threadIdx.x] = 0;   // admission segment counters
+    if (a.mqn)
+      for (int j = threadIdx.x; j < a.S; j += blockDim.x) a.mqn[j] = 0;
   }
   for (int32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < nslots;
        s += gridDim.x * blockDim.x) {
@@ -1067,28 +1075,37 @@ __global__ void __launch_bounds__(HUB_NT) k_hub_accum(LPArgs a, int32_t sub, int
 #pragma unroll
       for (int u = 0; u < 4; ++u)
         if (C[u] >= 0) C[u] = a.label[C[u]];
+      if (direct) {
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        if (C[u] < 0) continue;
-        if (direct) {
+        for (int u = 0; u < 4; ++u) {
+          if (C[u] < 0) continue;
           const int32_t key = (int32_t)(C[u] - c.loff);
           conn_add(pre ? &sacc[key] : &vals[key], w[u], a.narrow);
-          continue;
         }
-        const int32_t key = C[u];
-        uint32_t s = table_slot(key, logcap);
+      } else {
+        // the four arcs' first probes are independent: issue them together
         const uint32_t pmax = a.probe_limit <= mask ? a.probe_limit : mask + 1;
-        bool placed = false;
-        for (uint32_t p = 0; p < pmax; ++p) {
-          const int32_t prev = atomicCAS(&keys[s], -1, key);
-          if (prev == -1 || prev == key) {
-            conn_add(&vals[s], w[u], a.narrow);
-            placed = true;
-            break;
-          }
-          s = (s + 1) & mask;
+        uint32_t sl[4];
+        int32_t prev[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          sl[u] = C[u] >= 0 ? table_slot(C[u], logcap) : 0;
+          prev[u] = C[u] >= 0 && pmax > 0 ? atomicCAS(&keys[sl[u]], -1, C[u]) : -2;
         }
-        if (!placed) atomicOr(a.err, DERR_HASH_FULL);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (C[u] < 0) continue;
+          const int32_t key = C[u];
+          uint32_t s = sl[u];
+          bool placed = prev[u] == -1 || prev[u] == key;
+          for (uint32_t p = 1; !placed && p < pmax; ++p) {
+            s = (s + 1) & mask;
+            const int32_t pv = atomicCAS(&keys[s], -1, key);
+            placed = pv == -1 || pv == key;
+          }
+          if (placed) conn_add(&vals[s], w[u], a.narrow);
+          else atomicOr(a.err, DERR_HASH_FULL);
+        }
       }
       if (staged) {          // every thread is done with this chunk's buffer
         ++kchunk;
@@ -1158,18 +1175,36 @@ __global__ void __launch_bounds__(HUB_NT) k_hub_select(LPArgs a, int32_t sub, in
         if (cd.conn < 0 || cand_better(x, cd)) cd = x;
       }
     } else if (!ov) {
+      // four entries per thread at a time: their loads, then their label
+      // weight gathers, are in flight together
       const int64_t j1 = min64(j0 + HUB_SC, tcap);
-      for (int64_t s = j0 + tid; s < j1; s += HUB_NT) {
-        const int32_t K = keys[s];
-        if (K < 0) continue;
-        const int64_t conn = (int64_t)vals[s];
-        keys[s] = -1;
-        vals[s] = 0;
-        if (K == c.own) { oc = conn; continue; }
-        if ((int64_t)a.W[K] + c.cv > c.bound) continue;
-        if (cand_block(a, c, true, K) != c.vb) continue;
-        Cand x = make_cand(c, K, conn);
-        if (cd.conn < 0 || cand_better(x, cd)) cd = x;
+      for (int64_t s0 = j0; s0 < j1; s0 += 4 * HUB_NT) {
+        int32_t K[4];
+        int64_t conn[4];
+        wgt_t WK[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int64_t sx = s0 + (int64_t)u * HUB_NT + tid;
+          K[u] = sx < j1 ? keys[sx] : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int64_t sx = s0 + (int64_t)u * HUB_NT + tid;
+          conn[u] = K[u] >= 0 ? (int64_t)vals[sx] : 0;
+          WK[u] = K[u] >= 0 && K[u] != c.own ? a.W[K[u]] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (K[u] < 0) continue;
+          const int64_t sx = s0 + (int64_t)u * HUB_NT + tid;
+          keys[sx] = -1;
+          vals[sx] = 0;
+          if (K[u] == c.own) { oc = conn[u]; continue; }
+          if ((int64_t)WK[u] + c.cv > c.bound) continue;
+          if (cand_block(a, c, true, K[u]) != c.vb) continue;
+          Cand x = make_cand(c, K[u], conn[u]);
+          if (cd.conn < 0 || cand_better(x, cd)) cd = x;
+        }
       }
     }
     block_reduce<HUB_NT>(oc, cd, sh_oc, sh_cd);
@@ -1628,7 +1663,9 @@ __device__ __forceinline__ void apply_delta(int32_t* hk, int32_t* hv, wgt_t* W, 
   atomicAdd(&W[L], (wgt_t)d);
 }
 
-__device__ void adm_apply(const LPArgs& a, int64_t lbeg, int64_t cnt) {
+constexpr int64_t MARK_CH = 4096;     // arcs per queued chunk of a moved long row
+
+__device__ void adm_apply(const LPArgs& a, int64_t lbeg, int64_t cnt, int32_t sub) {
   uint8_t* const an = act_next(a);
   __shared__ int32_t hk[APPLY_SLOTS];
   __shared__ int32_t hv[APPLY_SLOTS];
@@ -1665,6 +1702,12 @@ __device__ void adm_apply(const LPArgs& a, int64_t lbeg, int64_t cnt) {
           else atomicSub(&a.W[own], (wgt_t)cv);
           if (re - rs <= 8) {
             for (int64_t e = rs; e < re; ++e) an[a.col[e]] = 1;
+            re = rs;
+          } else if (a.mark_big > 0 && re - rs > a.mark_big) {
+            const int32_t nch = (int32_t)((re - rs + MARK_CH - 1) / MARK_CH);
+            const int32_t q0 = atomicAdd(&a.mqn[sub], nch);
+            for (int32_t c = 0; c < nch; ++c)
+              a.mq[q0 + c] = make_longlong2(rs + c * MARK_CH, min64(rs + (c + 1) * MARK_CH, re));
             re = rs;
           }
         }
@@ -1734,7 +1777,7 @@ __global__ void __launch_bounds__(ADM_NT) k_admit(LPArgs a, int32_t sub, int32_t
       if (!grid_sync(gs, a.err, lim)) return;
     }
   }
-  adm_apply(a, lbeg, cnt);
+  adm_apply(a, lbeg, cnt, sub);
 }
 
 // The same phases as separate launches, chained on one stream with
@@ -1779,7 +1822,19 @@ __global__ void __launch_bounds__(ADM_NT) k_apply(LPArgs a, int32_t sub) {
   griddep_wait();
   int64_t lbeg, cnt;
   sub_range(a, sub, 0, NB, &lbeg, &cnt);
-  adm_apply(a, lbeg, cnt);
+  adm_apply(a, lbeg, cnt, sub);
+}
+
+// The queued chunks of moved long rows of colour class `sub`: one CTA per
+// chunk marks its heads active for the next round.
+__global__ void __launch_bounds__(256) k_mark_rows(LPArgs a, int32_t sub) {
+  griddep_wait();
+  uint8_t* const an = act_next(a);
+  const int32_t n = a.mqn[sub];
+  for (int32_t q = blockIdx.x; q < n; q += gridDim.x) {
+    const longlong2 c = a.mq[q];
+    for (int64_t e = c.x + threadIdx.x; e < c.y; e += blockDim.x) an[a.col[e]] = 1;
+  }
 }
 
 }  // namespace
@@ -2103,6 +2158,19 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, wgt_t*
     hs.poc = hub_poc.p;
     if (run.graph) ensure_pool(hub_slots);
   }
+  // moved rows above 4096 arcs activate their neighbours through the chunk
+  // queue (at most arcs / 4096 chunks plus one per such row, per class)
+  DevBuf<longlong2> mark_q;
+  DevBuf<int32_t> mark_n;
+  if (track_active && maxdeg > MARK_CH) {
+    mark_q.alloc((size_t)(2 * (lv.M / MARK_CH) + 2), s);
+    mark_n.alloc((size_t)S, s);
+    mark_n.zero();
+    a.mark_big = MARK_CH;
+    a.mq = mark_q.p;
+    a.mqn = mark_n.p;
+  }
+  const unsigned grid_mark = (unsigned)(sms * 8);
   constexpr size_t smem5 = blk_smem_bytes<B5_SLOTS>();
   constexpr size_t smem6 = blk_smem_bytes<B6_SLOTS>();
   constexpr size_t smem7 = blk_smem_bytes<B7_SLOTS>();
@@ -2257,6 +2325,7 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, wgt_t*
       const unsigned grid = cnt < 0 ? grid_adm_coop : grid_for(cnt, ADM_NT, grid_adm_coop);
       launch_coop(k_admit, grid, ADM_NT, 0, s, a, sub, source_chain ? 1 : 0, gsync.p);
       SCLAP_NOTE_LAUNCH("k_admit");
+      if (a.mark_big) { launch_k(false, k_mark_rows, grid_mark, 256, 0, s, a, sub); SCLAP_NOTE_LAUNCH("k_mark_rows"); }
       SCLAP_LAUNCH_CHECK();
       return;
     }
@@ -2272,6 +2341,7 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, wgt_t*
       launch_k(pdl, k_ovf_select, grid_sel, SEL_NT, 0, s, a, sub, 1); SCLAP_NOTE_LAUNCH("k_ovf_select");
     }
     launch_k(pdl, k_apply, grid_adm, ADM_NT, 0, s, a, sub); SCLAP_NOTE_LAUNCH("k_apply");
+    if (a.mark_big) { launch_k(pdl, k_mark_rows, grid_mark, 256, 0, s, a, sub); SCLAP_NOTE_LAUNCH("k_mark_rows"); }
     SCLAP_LAUNCH_CHECK();
   };
   auto tail = [&](cudaStream_t s, cudaGraphConditionalHandle h, bool in_graph, bool pdl) {
