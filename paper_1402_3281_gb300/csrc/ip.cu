@@ -715,13 +715,21 @@ __global__ void __launch_bounds__(GG_NT) k_ggg_group(GGGArgs a, int32_t cpt, Gro
 // Twice the cut of every slot: 32 nodes per warp, their arcs spread over
 // the lanes.  When the warp's 32 nodes lie in one slot (all but the groups
 // that straddle a slot boundary) each lane sums in a register and the warp
-// merges once per group; otherwise every cut arc is added on its own.
+// merges once per group; otherwise every cut arc is added on its own.  Rows
+// longer than CUT_CH arcs are queued in chunks of CUT_CH arcs for
+// k_slot_cut_long instead (at most 2 * arcs / CUT_CH chunks).
+constexpr int64_t CUT_CH = 4096;
+struct CutChunk {
+  int64_t lo, hi;
+  int32_t v, pad;
+};
 __global__ void __launch_bounds__(256) k_slot_cut(const int64_t* __restrict__ row_ptr,
                                                   const int32_t* __restrict__ col,
                                                   const int32_t* __restrict__ ew,
                                                   const int32_t* __restrict__ gid,
                                                   const int32_t* __restrict__ label, int64_t N,
-                                                  int64_t* __restrict__ cut2) {
+                                                  int64_t* __restrict__ cut2,
+                                                  CutChunk* __restrict__ q, int32_t* qn) {
   __shared__ int sh_slot;
   __shared__ unsigned long long sh_sum;
   const int lane = threadIdx.x & 31;
@@ -742,6 +750,13 @@ __global__ void __launch_bounds__(256) k_slot_cut(const int64_t* __restrict__ ro
       d = row_ptr[v + 1] - rs;
       lv = label[v];
       s = slot_at(gid, v);
+      if (d > CUT_CH) {
+        const int32_t nch = (int32_t)((d + CUT_CH - 1) / CUT_CH);
+        const int32_t q0 = atomicAdd(qn, nch);
+        for (int32_t c = 0; c < nch; ++c)
+          q[q0 + c] = CutChunk{rs + c * CUT_CH, min64(rs + (c + 1) * CUT_CH, rs + d), (int32_t)v, 0};
+        d = 0;
+      }
     }
     long long incl = d;
     for (int o = 1; o < 32; o <<= 1) {
@@ -786,38 +801,80 @@ __global__ void __launch_bounds__(256) k_slot_cut(const int64_t* __restrict__ ro
   if (threadIdx.x == 0 && sh_sum) atomicAdd(ull(&cut2[sh_slot]), sh_sum);
 }
 
-__global__ void k_select_copy(const SelectTask* __restrict__ tasks, const int64_t* __restrict__ cut2,
-                              const wgt_t* __restrict__ ip_W, const int64_t* __restrict__ ip_noff,
-                              const int64_t* __restrict__ ip_boff,
-                              const int32_t* __restrict__ ip_label, wgt_t* __restrict__ Wg,
-                              int32_t* __restrict__ best, int64_t* __restrict__ ipcut,
-                              int64_t* __restrict__ rb_ov) {
-  const SelectTask t = tasks[blockIdx.x];
-  __shared__ int32_t bt_sh;
-  if (threadIdx.x == 0) {
-    int64_t bo = -1, bc = -1;
-    int32_t bt = -1;
-    for (int32_t tr = 0; tr < t.trials; ++tr) {
-      const int64_t slot = t.slot0 + tr;
-      int64_t mx = 0;
-      for (int32_t b = 0; b < t.k; ++b) mx = max64(mx, (int64_t)ip_W[ip_boff[slot] + b]);
-      const int64_t ov = max64(0, mx - t.Lmax);
-      const int64_t c = cut2[slot] / 2;
-      if (bt < 0 || ov < bo || (ov == bo && c < bc)) { bo = ov; bc = c; bt = tr; }
+// The queued chunks of long rows: one CTA per chunk, one atomic per chunk.
+__global__ void __launch_bounds__(256) k_slot_cut_long(const int32_t* __restrict__ col,
+                                                       const int32_t* __restrict__ ew,
+                                                       const int32_t* __restrict__ gid,
+                                                       const int32_t* __restrict__ label,
+                                                       const CutChunk* __restrict__ q,
+                                                       const int32_t* qn,
+                                                       int64_t* __restrict__ cut2) {
+  __shared__ unsigned long long sh[8];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int32_t n = *qn;
+  for (int32_t i = blockIdx.x; i < n; i += gridDim.x) {
+    const CutChunk c = q[i];
+    const int32_t lv = label[c.v];
+    unsigned long long acc = 0;
+    for (int64_t e = c.lo + threadIdx.x; e < c.hi; e += blockDim.x)
+      if (label[col[e]] != lv) acc += (unsigned long long)wat(ew, e);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) sh[wid] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned long long t = 0;
+      for (int w = 0; w < 8; ++w) t += sh[w];
+      if (t) atomicAdd(ull(&cut2[slot_at(gid, c.v)]), t);
     }
-    const bool take = best[t.g] < 0 || bo < rb_ov[t.g] || (bo == rb_ov[t.g] && bc < ipcut[t.g]);
-    if (take) {
-      best[t.g] = t.trial0 + bt;
-      ipcut[t.g] = bc;
-      rb_ov[t.g] = bo;
-    }
-    bt_sh = take ? bt : -1;
+    __syncthreads();
   }
-  __syncthreads();
-  if (bt_sh < 0) return;
-  const int64_t slot = t.slot0 + bt_sh;
+}
+
+// Best trial of each task (a graph's trials of one group): least overload,
+// then least cut; it replaces the graph's best so far only if better (the
+// groups run in trial order, so the first best trial wins ties).  take[i] =
+// the task's trial to copy out, or -1.
+__global__ void k_select_best(const SelectTask* __restrict__ tasks, int32_t ntasks,
+                              const int64_t* __restrict__ cut2, const wgt_t* __restrict__ ip_W,
+                              const int64_t* __restrict__ ip_boff, int32_t* __restrict__ best,
+                              int64_t* __restrict__ ipcut, int64_t* __restrict__ rb_ov,
+                              int32_t* __restrict__ take) {
+  const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ntasks) return;
+  const SelectTask t = tasks[i];
+  int64_t bo = -1, bc = -1;
+  int32_t bt = -1;
+  for (int32_t tr = 0; tr < t.trials; ++tr) {
+    const int64_t slot = t.slot0 + tr;
+    int64_t mx = 0;
+    for (int32_t b = 0; b < t.k; ++b) mx = max64(mx, (int64_t)ip_W[ip_boff[slot] + b]);
+    const int64_t ov = max64(0, mx - t.Lmax);
+    const int64_t c = cut2[slot] / 2;
+    if (bt < 0 || ov < bo || (ov == bo && c < bc)) { bo = ov; bc = c; bt = tr; }
+  }
+  const bool tk = best[t.g] < 0 || bo < rb_ov[t.g] || (bo == rb_ov[t.g] && bc < ipcut[t.g]);
+  if (tk) {
+    best[t.g] = t.trial0 + bt;
+    ipcut[t.g] = bc;
+    rb_ov[t.g] = bo;
+  }
+  take[i] = tk ? bt : -1;
+}
+
+// Copies the taken trial's blocks out: tasks along y, chunks of SC_CH nodes
+// along x.
+constexpr int64_t SC_CH = 65536;
+__global__ void k_copy_best(const SelectTask* __restrict__ tasks, const int32_t* __restrict__ take,
+                            const int64_t* __restrict__ ip_noff, const int64_t* __restrict__ ip_boff,
+                            const int32_t* __restrict__ ip_label, const wgt_t* __restrict__ ip_W,
+                            wgt_t* __restrict__ Wg) {
+  const int32_t bt = take[blockIdx.y];
+  if (bt < 0) return;
+  const SelectTask t = tasks[blockIdx.y];
+  const int64_t slot = t.slot0 + bt;
   const int64_t src = ip_noff[slot], sbo = ip_boff[slot];
-  for (int64_t v = threadIdx.x; v < t.n; v += blockDim.x) {
+  const int64_t v1 = min64(((int64_t)blockIdx.x + 1) * SC_CH, t.n);
+  for (int64_t v = (int64_t)blockIdx.x * SC_CH + threadIdx.x; v < v1; v += blockDim.x) {
     int64_t d = v;
     if (t.rank) {
       const int64_t r0 = t.rank[t.dst_n0 + v];
@@ -826,7 +883,8 @@ __global__ void k_select_copy(const SelectTask* __restrict__ tasks, const int64_
     }
     t.dst_blk[t.dst_n0 + v] = (int32_t)(t.g_boff + (ip_label[src + d] - sbo));
   }
-  for (int32_t b = threadIdx.x; b < t.k; b += blockDim.x) Wg[t.g_boff + b] = ip_W[sbo + b];
+  if (blockIdx.x == 0)
+    for (int32_t b = threadIdx.x; b < t.k; b += blockDim.x) Wg[t.g_boff + b] = ip_W[sbo + b];
 }
 
 __global__ void k_project(const int32_t* __restrict__ cmap, const int32_t* __restrict__ cblk,
@@ -939,8 +997,9 @@ void waterfill_isolated(const std::vector<FillTask>& tasks, wgt_t* Wg, int64_t K
   k_wf_setup<<<(nt + 127) / 128, 128, 0, s>>>(d.p, nt, Wg, order.p, A.p); SCLAP_NOTE_LAUNCH("k_wf_setup");
   int64_t mx = 1;
   for (const auto& t : tasks) mx = std::max(mx, t.n);
+  const int64_t per_task = std::max<int64_t>(64, (int64_t)num_sms() * 8 / nt);
   for (int t0 = 0; t0 < nt; t0 += 65535) {
-    dim3 grid(grid_for(mx, 256, 64), (unsigned)std::min(65535, nt - t0));
+    dim3 grid(grid_for(mx, 256, per_task), (unsigned)std::min(65535, nt - t0));
     k_wf_assign<<<grid, 256, 0, s>>>(d.p + t0, Wg, order.p, A.p); SCLAP_NOTE_LAUNCH("k_wf_assign");
   }
   SCLAP_LAUNCH_CHECK();
@@ -955,9 +1014,11 @@ void ip_replicate(const std::vector<CopyTask>& tasks, int64_t* row_ptr, int32_t*
   d.upload(tasks);
   int64_t mx = 1;
   for (const auto& t : tasks) mx = std::max(mx, std::max(t.n, t.m));
+  // at least 64 CTAs per task, more when few tasks would leave SMs idle
+  const int64_t per_task = std::max<int64_t>(64, (int64_t)num_sms() * 8 / (int64_t)tasks.size());
   for (size_t t0 = 0; t0 < tasks.size(); t0 += 65535) {
     const unsigned ny = (unsigned)std::min<size_t>(65535, tasks.size() - t0);
-    dim3 grid(grid_for(mx, 256, 64), ny);
+    dim3 grid(grid_for(mx, 256, per_task), ny);
     k_replicate<<<grid, 256, 0, s>>>(d.p + t0, row_ptr, col, ew, nw); SCLAP_NOTE_LAUNCH("k_replicate");
   }
   int64_t endv = M_total;
@@ -996,8 +1057,9 @@ void ggg_trials(const GGGArgs& a_in, const std::vector<int64_t>& noff,
   SCLAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&many_per_sm, k_ggg<GNT_MANY>, GNT_MANY, 0));
   const int64_t few_resident = (int64_t)num_sms() * std::max(few_per_sm, 1);
   const int64_t many_resident = (int64_t)num_sms() * std::max(many_per_sm, 1);
-  // few trials of large blocks: a group of CTAs per trial (at most 64 CTAs
-  // per trial, and only when every trial gets at least 4).  A growth step
+  // few trials of large blocks: a group of CTAs per trial (the resident
+  // CTAs shared out, at most 256 per trial, and only when every trial gets
+  // at least 4).  A growth step
   // costs the group a few barriers, so the groups pay off only when the
   // blocks are large: measured faster on R-MAT scale 22 at k = 2 and 8 and
   // on scale 25 at k = 16 (1149 -> 369 ms), slower on scale 22 at k = 32
@@ -1007,7 +1069,7 @@ void ggg_trials(const GGGArgs& a_in, const std::vector<int64_t>& noff,
   int group_per_sm = 0;
   SCLAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&group_per_sm, k_ggg_group, GG_NT, 0));
   const int64_t group_resident = (int64_t)num_sms() * std::max(group_per_sm, 1);
-  const int64_t cpt = std::min<int64_t>(64, group_resident / S);
+  const int64_t cpt = std::min<int64_t>(256, group_resident / S);
   int64_t per_block = 0;
   for (int32_t i = 0; i < S; ++i)
     per_block = std::max(per_block, (noff[i + 1] - noff[i]) / std::max<int32_t>(1, nlab[i]));
@@ -1032,8 +1094,13 @@ void ggg_trials(const GGGArgs& a_in, const std::vector<int64_t>& noff,
 
 void slot_cut(const LevelView& lv, const int32_t* label, int64_t* cut2, cudaStream_t s) {
   if (lv.N <= 0) return;
+  DevBuf<CutChunk> q((size_t)(2 * (lv.M / CUT_CH) + 2), s);
+  DevBuf<int32_t> qn(1, s);
+  qn.zero();
   k_slot_cut<<<grid_for(lv.N, 256, (int64_t)num_sms() * 16), 256, 0, s>>>(
-      lv.row_ptr, lv.col, lv.ew, lv.gid, label, lv.N, cut2); SCLAP_NOTE_LAUNCH("k_slot_cut");
+      lv.row_ptr, lv.col, lv.ew, lv.gid, label, lv.N, cut2, q.p, qn.p); SCLAP_NOTE_LAUNCH("k_slot_cut");
+  k_slot_cut_long<<<(unsigned)num_sms() * 8, 256, 0, s>>>(lv.col, lv.ew, lv.gid, label, q.p, qn.p,
+                                                          cut2); SCLAP_NOTE_LAUNCH("k_slot_cut_long");
   SCLAP_LAUNCH_CHECK();
 }
 
@@ -1042,10 +1109,18 @@ void ip_select_copy(const std::vector<SelectTask>& tasks, const int64_t* cut2,
                     const int32_t* ip_label, wgt_t* Wg, int32_t* best, int64_t* ipcut,
                     int64_t* rb_ov, cudaStream_t s) {
   if (tasks.empty()) return;
-  DevBuf<SelectTask> d(tasks.size(), s);
+  const int32_t nt = (int32_t)tasks.size();
+  DevBuf<SelectTask> d(nt, s);
+  DevBuf<int32_t> take(nt, s);
   d.upload(tasks);
-  k_select_copy<<<(unsigned)tasks.size(), 256, 0, s>>>(d.p, cut2, ip_W, ip_noff, ip_boff,
-                                                       ip_label, Wg, best, ipcut, rb_ov); SCLAP_NOTE_LAUNCH("k_select_copy");
+  k_select_best<<<(nt + 127) / 128, 128, 0, s>>>(d.p, nt, cut2, ip_W, ip_boff, best, ipcut, rb_ov,
+                                                 take.p); SCLAP_NOTE_LAUNCH("k_select_best");
+  int64_t mx = 1;
+  for (const auto& t : tasks) mx = std::max(mx, t.n);
+  for (int32_t t0 = 0; t0 < nt; t0 += 65535) {
+    dim3 grid((unsigned)((mx + SC_CH - 1) / SC_CH), (unsigned)std::min(65535, nt - t0));
+    k_copy_best<<<grid, 256, 0, s>>>(d.p + t0, take.p + t0, ip_noff, ip_boff, ip_label, ip_W, Wg); SCLAP_NOTE_LAUNCH("k_copy_best");
+  }
   SCLAP_LAUNCH_CHECK();
   stream_sync(s);   // the task array is freed on return
 }
