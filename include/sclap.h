@@ -357,6 +357,22 @@ int sclap_cut_static(int64_t n, const int64_t* row_ptr, const int32_t* col,
  * negative value or a limit above 2^32 - 1. ---- */
 int sclap_debug_inject(int64_t wait_limit, int64_t probe_limit, int32_t fail_allocs);
 
+/* ---- Bounds-check build (no counterpart in the paper).  The library
+ * compiled with -DSCLAP_CHECK=1 (python -m paper_1402_3281_gb300.build
+ * --check writes libsclap_check.so) checks the data-dependent indices of its
+ * kernels (neighbours, labels, coarse ids, table slots) against their
+ * arrays' lengths; an index out of range is not used, and the call returns
+ * SCLAP_EINTERNAL ("bounds check failed").  It stands in for a memory
+ * checker where none can be run.
+ *   sclap_check_build()     1 in the bounds-check build, 0 otherwise.
+ *   sclap_check_selftest()  bounds-check build only: a kernel checks one
+ *                           index inside and one just past a 4-element device
+ *                           array (the second access is intercepted, never
+ *                           made); SCLAP_OK when exactly the second was
+ *                           caught.  SCLAP_EINVAL in the normal build. ---- */
+int sclap_check_build(void);
+int sclap_check_selftest(void* stream);
+
 /* ---- Launch tuning and autotuning (no counterpart in the paper).  Choices
  * of the LP sweep that change scheduling, never results:
  *   small_max_deg      rows of degree <= 8 or <= 16 get one thread per node

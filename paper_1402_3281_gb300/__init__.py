@@ -5,7 +5,8 @@ include/sclap.h); `sclap` is its ctypes binding.
 """
 from .sclap import (  # noqa: F401
     CUT_STATIC_MAX_K, PENDING, ECSR, ECUDA, EINFEASIBLE, EINTERNAL, EINVAL, ENOMEM, EOVERFLOW, ETIMEOUT, OK,
-    Config, Result, SclapError, Server, Served, Tuning, autotune, debug_inject, default_config, get_tuning, load,
+    Config, Result, SclapError, Server, Served, Tuning, autotune, check_build, check_selftest, debug_inject,
+    default_config, get_tuning, load,
     set_tuning, sclap_cluster,
     sclap_cluster_hierarchy, sclap_contract, sclap_cut,
     sclap_cut_static,

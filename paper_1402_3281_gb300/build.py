@@ -1,7 +1,9 @@
 """Builds libsclap.so (all CUDA sources, sm_103a) in place, with nvcc only.
 
 Objects go to _build/ next to this file; sources compile in parallel and the
-library is relinked only when a source or header is newer than it.
+library is relinked only when a source or header is newer than it.  With
+check=True (--check) it builds the bounds-check variant instead:
+-DSCLAP_CHECK=1, objects in _build_check/, libsclap_check.so.
 """
 from __future__ import annotations
 
@@ -15,6 +17,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 SO = os.path.join(HERE, "libsclap.so")
+BUILD_CHECK = os.path.join(HERE, "_build_check")
+SO_CHECK = os.path.join(HERE, "libsclap_check.so")
 SOURCES = ["scan.cu", "lp.cu", "contract.cu", "ip.cu", "driver.cu", "noalloc.cu", "server.cu"]
 HEADERS = [os.path.join(CSRC, "common.cuh"), os.path.join(ROOT, "include", "sclap.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -35,17 +39,19 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, check: bool = False) -> str:
+    bdir, so = (BUILD_CHECK, SO_CHECK) if check else (BUILD, SO)
+    flags = FLAGS + (["-DSCLAP_CHECK=1"] if check else [])
+    os.makedirs(bdir, exist_ok=True)
     nvcc = _nvcc()
     jobs = []
     objs = []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
-        o = os.path.join(BUILD, src.replace(".cu", ".o"))
+        o = os.path.join(bdir, src.replace(".cu", ".o"))
         objs.append(o)
         if force or _stale(o, [s] + HEADERS):
-            jobs.append([nvcc] + FLAGS + ARCH + ["-c", s, "-o", o])
+            jobs.append([nvcc] + flags + ARCH + ["-c", s, "-o", o])
 
     def run(cmd):
         if verbose:
@@ -58,12 +64,12 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if jobs:
         with cf.ThreadPoolExecutor(max_workers=len(jobs)) as ex:
             list(ex.map(run, jobs))
-    if force or jobs or _stale(SO, objs):
-        tmp = SO + f".tmp{os.getpid()}"
+    if force or jobs or _stale(so, objs):
+        tmp = so + f".tmp{os.getpid()}"
         run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs)
-        os.replace(tmp, SO)
-    return SO
+        os.replace(tmp, so)
+    return so
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True))
+    print(build(force="--force" in sys.argv, verbose=True, check="--check" in sys.argv))

@@ -134,7 +134,32 @@ enum : int32_t {
   DERR_BAD_CSR = 4,       // validation
   DERR_INTERNAL = 8,
   DERR_TIMEOUT = 16,      // a bounded device-side wait ran out of iterations
+  DERR_BOUNDS = 32,       // SCLAP_CHECK builds: a checked index was out of range
 };
+
+// Bounds checks of the SCLAP_CHECK build (compiled with -DSCLAP_CHECK=1):
+// data-dependent indices (a neighbour, a label, a coarse id, a table slot)
+// are checked against their array's length before the access; an index out
+// of range sets DERR_BOUNDS in the kernel's error word and the access is
+// skipped (a load yields zero), so the kernel never touches memory outside
+// its arrays and the call ends with SCLAP_EINTERNAL.  In the normal build
+// both macros are the plain access / `true`.
+#if defined(SCLAP_CHECK) && SCLAP_CHECK
+__device__ __forceinline__ bool sclap_chk(int64_t i, int64_t n, int32_t* err) {
+  if (i >= 0 && i < n) return true;
+  atomicOr(err, DERR_BOUNDS);
+  return false;
+}
+template <class T>
+__device__ __forceinline__ T sclap_chk_ld(const T* p, int64_t i, int64_t n, int32_t* err) {
+  return sclap_chk(i, n, err) ? p[i] : T();
+}
+#define SCLAP_OK(i, n, err) sclap_chk((int64_t)(i), (int64_t)(n), (err))
+#define SCLAP_LD(p, i, n, err) sclap_chk_ld((p), (int64_t)(i), (int64_t)(n), (err))
+#else
+#define SCLAP_OK(i, n, err) true
+#define SCLAP_LD(p, i, n, err) ((p)[i])
+#endif
 
 // ---------------------------------------------------------------------------
 // Grid-wide barrier of a cooperative launch (every CTA resident at once),
@@ -599,12 +624,13 @@ struct GGGArgs {
   int32_t* step;           // scratch [N]
   int32_t* front;          // scratch [N]: newly reached nodes (step alternates with it)
   int32_t* heavy;          // scratch [N]: a step's long rows (grouped growing)
+  int64_t N;               // nodes of all trial slots (array lengths for bounds checks)
   int64_t* wfA;            // scratch [sum k]
   int32_t* wforder;        // scratch [sum k]
   int32_t nslots;
   const int32_t* order;    // trial slots in the order they are taken (set by ggg_trials)
   int32_t* next;           // queue position (set by ggg_trials)
-  int32_t* err;            // device error word (bounded waits of the grouped kernel)
+  int32_t* err;            // device error word (bounded waits, bounds-check builds)
 };
 // noff: host copy of the trial slot node offsets [nslots + 1]; nlab: host
 // copy of k per trial slot.

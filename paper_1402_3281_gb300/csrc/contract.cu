@@ -65,6 +65,7 @@ struct CArgs {
   // rows longer than `heavy` arcs are left to the heavy-row kernels (split
   // into chunks over many CTAs); 0: no split
   int64_t heavy;
+  int64_t N, Nc;     // fine and coarse nodes (array lengths for bounds checks)
 };
 
 __global__ void k_map(CArgs a, int64_t N) {
@@ -72,9 +73,9 @@ __global__ void k_map(CArgs a, int64_t N) {
        v += (int64_t)gridDim.x * blockDim.x) {
     const int32_t s = slot_at(a.gid, v);
     if (!a.keep[s]) { a.cmap[v] = -1; continue; }
-    const int32_t c = (int32_t)(a.cid[a.label[v]] + a.delta[s]);
+    const int32_t c = (int32_t)(SCLAP_LD(a.cid, a.label[v], a.N + 1, a.err) + a.delta[s]);
     a.cmap[v] = c;
-    atomicAdd(&a.cnw[c], wat(a.nw, v));
+    if (SCLAP_OK(c, a.Nc, a.err)) atomicAdd(&a.cnw[c], wat(a.nw, v));
   }
 }
 
@@ -119,7 +120,7 @@ __device__ __forceinline__ void for_inter_arcs(const CArgs& a, int64_t N, F f) {
       int32_t cu = -1, w = 0;
       if (x < total) {
         const int64_t e = rsL + (x - exL);
-        cu = a.cmap[a.col[e]];
+        cu = SCLAP_LD(a.cmap, a.col[e], a.N, a.err);
         if (cu == cvL) cu = -1;
         else w = wat(a.ew, e);
       }
@@ -143,7 +144,7 @@ __global__ void __launch_bounds__(256) k_count_inter(CArgs a, int64_t N) {
       const unsigned upto = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);   // lanes 0..lane
       const int first = 31 - __clz(heads & upto);                               // run start
       const int c = __popc(inter & upto & ~((1u << first) - 1u));
-      if (c) atomicAdd(&a.inter[cv], c);
+      if (c && SCLAP_OK(cv, a.Nc, a.err)) atomicAdd(&a.inter[cv], c);
     }
   });
 }
@@ -161,6 +162,7 @@ __global__ void k_table_caps(const int32_t* __restrict__ inter, int64_t Nc, int6
 // add to the low half with one atomicAdd.  A coarse edge weight must fit in
 // int32, so a sum reaching 2^31 is reported (and cannot carry into the key).
 __device__ __forceinline__ void insert_arc(const CArgs& a, int32_t cv, int32_t cu, int32_t w) {
+  if (!SCLAP_OK(cv, a.Nc, a.err) || !SCLAP_OK(cu, a.Nc, a.err)) return;
   const int64_t sum = w;
   const int64_t base = a.tbase[cv] - a.toff;
   const int logcap = ceil_log2(a.tbase[cv + 1] - a.tbase[cv]);
@@ -246,7 +248,7 @@ __device__ __forceinline__ void for_heavy_arcs(const CArgs& a, const int32_t* __
     const int64_t e0 = a.row_ptr[v] + (q - hoff[lo]) * HV_CH;
     const int64_t e1 = min(e0 + HV_CH, a.row_ptr[v + 1]);
     for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-      int32_t cu = a.cmap[a.col[e]];
+      int32_t cu = SCLAP_LD(a.cmap, a.col[e], a.N, a.err);
       int32_t w = 0;
       if (cu == cv) cu = -1;
       else w = wat(a.ew, e);
@@ -273,9 +275,10 @@ __global__ void __launch_bounds__(256) k_count_heavy(CArgs a, const int32_t* __r
     const int64_t e0 = a.row_ptr[v] + (q - hoff[lo]) * HV_CH;
     const int64_t e1 = min(e0 + HV_CH, a.row_ptr[v + 1]);
     int c = 0;
-    for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) c += a.cmap[a.col[e]] != cv;
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x)
+      c += SCLAP_LD(a.cmap, a.col[e], a.N, a.err) != cv;
     for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-    if (lane == 0 && c) atomicAdd(&a.inter[cv], c);
+    if (lane == 0 && c && SCLAP_OK(cv, a.Nc, a.err)) atomicAdd(&a.inter[cv], c);
   }
 }
 
@@ -968,6 +971,7 @@ void contract_build(const LevelView& lv, const std::vector<int64_t>& noff, const
   a.label = label; a.cid = w.cid.p; a.delta = d_delta.p; a.keep = d_keep.p; a.cmap = cmap;
   a.cnw = out.nw.p; a.inter = inter.p; a.tbase = tbase.p; a.err = d_err;
   a.c_lo = 0; a.c_hi = INT32_MAX; a.toff = 0; a.sums31 = lv.sums31;
+  a.N = N; a.Nc = Nc;
 
   const unsigned ng = grid_for(N, 256, (int64_t)sms * 16);
   const unsigned wg = grid_for(N, 256, (int64_t)sms * 16);   // 8 warps x 32 nodes per block

@@ -162,6 +162,15 @@ __global__ void k_w_from_nw(const int32_t* nw, int64_t N, wgt_t* W) {
     W[v] = wat(nw, v);
 }
 
+#if defined(SCLAP_CHECK) && SCLAP_CHECK
+// Bounds-check self test: index n - 1 of buf is read; index n is checked
+// and refused (never read).  err[0] / err[1]: the error word of each.
+__global__ void k_check_selftest(const int32_t* buf, int64_t n, int32_t* out, int32_t* err) {
+  out[0] = SCLAP_LD(buf, n - 1, n, &err[0]);
+  out[1] = SCLAP_LD(buf, n, n, &err[1]);
+}
+#endif
+
 __global__ void k_check_range(const int32_t* __restrict__ a, int64_t n, int64_t lo, int64_t hi,
                               int32_t* err) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
@@ -298,6 +307,7 @@ void check_err(int32_t* d_err, cudaStream_t s) {
   if (e & DERR_W_OVERFLOW) throw Error(SCLAP_EOVERFLOW, "coarse edge weight above INT32_MAX");
   if (e & DERR_HASH_FULL) throw Error(SCLAP_EINTERNAL, "hash table full");
   if (e & DERR_BAD_CSR) throw Error(SCLAP_ECSR, "malformed CSR");
+  if (e & DERR_BOUNDS) throw Error(SCLAP_EINTERNAL, "bounds check failed (SCLAP_CHECK build)");
   if (e) throw Error(SCLAP_EINTERNAL, "device error word set");
 }
 
@@ -574,6 +584,7 @@ void run_ip(const std::vector<IPIn>& in, const sclap_config& cfg, wgt_t* Wg,
   ga.conn = conn.p; ga.step = step.p; ga.front = front.p; ga.heavy = heavy.p;
   ga.wfA = wfA.p; ga.wforder = wforder.p;
   ga.nslots = S;
+  ga.N = ip.N;
   ga.err = d_err;
   ggg_trials(ga, noff, h_nlab, s);
 
@@ -1543,6 +1554,37 @@ int sclap_cut(int64_t n, const int64_t* row_ptr, const int32_t* col, const int32
     SCLAP_CUDA(cudaMemcpyAsync(&c2, cut2.p, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     stream_sync(s);
     if (cut_out) *cut_out = c2 / 2;
+  });
+}
+
+int sclap_check_build(void) {
+#if defined(SCLAP_CHECK) && SCLAP_CHECK
+  return 1;
+#else
+  return 0;
+#endif
+}
+
+int sclap_check_selftest(void* stream) {
+  return guarded([&] {
+#if defined(SCLAP_CHECK) && SCLAP_CHECK
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    DevBuf<int32_t> buf(4, s), out(2, s), err(2, s);
+    const std::vector<int32_t> init{10, 11, 12, 13};
+    buf.upload(init);
+    err.zero();
+    k_check_selftest<<<1, 1, 0, s>>>(buf.p, 4, out.p, err.p); SCLAP_NOTE_LAUNCH("k_check_selftest");
+    SCLAP_LAUNCH_CHECK();
+    int32_t h[4] = {0, 0, 0, 0};
+    SCLAP_CUDA(cudaMemcpyAsync(h, out.p, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    SCLAP_CUDA(cudaMemcpyAsync(h + 2, err.p, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    stream_sync(s);
+    if (h[0] != 13 || h[1] != 0 || h[2] != 0 || h[3] != DERR_BOUNDS)
+      throw Error(SCLAP_EINTERNAL, "bounds-check self test failed");
+#else
+    (void)stream;
+    throw Error(SCLAP_EINVAL, "not a bounds-check build");
+#endif
   });
 }
 

@@ -203,6 +203,7 @@ __global__ void __launch_bounds__(GNT) k_ggg(GGGArgs a) {
               const int64_t e = st_rs[lo] + (x - st_ex[lo]);
               y[u] = a.col[e];
               w[u] = a.ew[e];
+              if (!SCLAP_OK(y[u], a.N, a.err)) y[u] = -1;
             }
 #pragma unroll
             for (int u = 0; u < GARC; ++u) lab[u] = y[u] >= 0 ? a.label[y[u]] : 0;
@@ -519,7 +520,7 @@ __global__ void __launch_bounds__(GG_NT) k_ggg_group(GGGArgs a, int32_t cpt, Gro
       // arc lists it as reached (weights > 0)
       auto visit = [&](int64_t e) {
         const int32_t y = a.col[e];
-        if (a.label[y] >= 0) return;
+        if (!SCLAP_OK(y, a.N, a.err) || a.label[y] >= 0) return;
         const unsigned long long old = atomicAdd(ull(&a.conn[y]), (unsigned long long)a.ew[e]);
         if (!ordered && old == 0) {
           frt[atomicAdd(&st->nfront, 1)] = y;

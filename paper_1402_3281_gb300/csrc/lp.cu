@@ -35,6 +35,8 @@ struct LPArgs {
   int32_t narrow;          // 1: every connection sum is below 2^32
   int32_t arcs32;          // 1: the level has fewer than 2^32 arcs
   int64_t M;               // arcs of the level (length of col / ew)
+  int64_t N;               // nodes of the level (length of label, col's range)
+  int64_t nlabels;         // length of W and in_w
   // slots
   const int64_t* noff;
   const int64_t* loff;
@@ -164,7 +166,7 @@ __device__ __forceinline__ void write_prop(const LPArgs& a, int64_t i, const Nod
     const int32_t t = (int32_t)(c.loff + best.C);
     a.prop_t[i] = t;
     a.prop_key[i] = admission_key(best.conn - own_conn, (uint32_t)c.hv);
-    atomicAdd(ull(&a.in_w[t]), (unsigned long long)c.cv);
+    if (SCLAP_OK(t, a.nlabels, a.err)) atomicAdd(ull(&a.in_w[t]), (unsigned long long)c.cv);
   } else {
     a.prop_t[i] = -1;
   }
@@ -392,7 +394,7 @@ __device__ __forceinline__ void sorted_row_best(const LPArgs& a, const NodeCtx& 
 #pragma unroll
   for (int j = 0; j < MAXD; ++j) {
     const bool q = end[j] & (C[j] != c.own);
-    Wl[j] = q ? a.W[C[j]] : 0;
+    Wl[j] = q ? SCLAP_LD(a.W, C[j], a.nlabels, a.err) : 0;
     Bl[j] = cand_block(a, c, q, C[j]);
   }
 #pragma unroll
@@ -424,7 +426,7 @@ __device__ __forceinline__ void propose_thread(const LPArgs& a, int64_t lbeg, in
       total += w[j];
     }
 #pragma unroll
-    for (int j = 0; j < MAXD; ++j) C[j] = C[j] >= 0 ? a.label[C[j]] : INT32_MAX;
+    for (int j = 0; j < MAXD; ++j) C[j] = C[j] >= 0 ? SCLAP_LD(a.label, C[j], a.N, a.err) : INT32_MAX;
     long long oc = 0;
     Cand best{-1, 0, 0};
     if (total <= INT32_MAX) sorted_row_best<MAXD, int32_t>(a, c, C, w, oc, best);
@@ -572,7 +574,7 @@ __global__ void __launch_bounds__(WPC * 32) k_propose_warp(LPArgs a, int32_t sub
     }
 #pragma unroll
     for (int t = 0; t < 4; ++t)
-      if (C[t] >= 0) C[t] = a.label[C[t]];
+      if (C[t] >= 0) C[t] = SCLAP_LD(a.label, C[t], a.N, a.err);
     // keys: local block id (direct) or label (hashed)
     int slot[4] = {0, 0, 0, 0};
     unsigned created = 0;
@@ -622,7 +624,7 @@ __global__ void __launch_bounds__(WPC * 32) k_propose_warp(LPArgs a, int32_t sub
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
         const bool q = ((created >> t) & 1u) && C[t] != c.own && !ov;
-        Wk[t] = q ? a.W[C[t]] : 0;
+        Wk[t] = q ? SCLAP_LD(a.W, C[t], a.nlabels, a.err) : 0;
         Bk[t] = cand_block(a, c, q, C[t]);
       }
 #pragma unroll
@@ -775,7 +777,7 @@ __global__ void __launch_bounds__(NT) k_propose_blk(LPArgs a, int32_t sub, int32
       }
 #pragma unroll
       for (int u = 0; u < 4; ++u)
-        if (C[u] >= 0) C[u] = a.label[C[u]];
+        if (C[u] >= 0) C[u] = SCLAP_LD(a.label, C[u], a.N, a.err);
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         if (e0 + (int64_t)u * NT >= c.re) break;
@@ -1074,13 +1076,14 @@ __global__ void __launch_bounds__(HUB_NT) k_hub_accum(LPArgs a, int32_t sub, int
       }
 #pragma unroll
       for (int u = 0; u < 4; ++u)
-        if (C[u] >= 0) C[u] = a.label[C[u]];
+        if (C[u] >= 0) C[u] = SCLAP_LD(a.label, C[u], a.N, a.err);
       if (direct) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           if (C[u] < 0) continue;
           const int32_t key = (int32_t)(C[u] - c.loff);
-          conn_add(pre ? &sacc[key] : &vals[key], w[u], a.narrow);
+          if (SCLAP_OK(key, pre ? (int64_t)HUB_DACC : tcap, a.err))
+            conn_add(pre ? &sacc[key] : &vals[key], w[u], a.narrow);
         }
       } else {
         // the four arcs' first probes are independent: issue them together
@@ -1191,7 +1194,7 @@ __global__ void __launch_bounds__(HUB_NT) k_hub_select(LPArgs a, int32_t sub, in
         for (int u = 0; u < 4; ++u) {
           const int64_t sx = s0 + (int64_t)u * HUB_NT + tid;
           conn[u] = K[u] >= 0 ? (int64_t)vals[sx] : 0;
-          WK[u] = K[u] >= 0 && K[u] != c.own ? a.W[K[u]] : 0;
+          WK[u] = K[u] >= 0 && K[u] != c.own ? SCLAP_LD(a.W, K[u], a.nlabels, a.err) : 0;
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -1286,8 +1289,8 @@ __device__ void adm_resolve(const LPArgs& a, int64_t lbeg, int64_t cnt, int64_t*
     a.stage[i] = 0;
     if (t < 0) { a.adm[i] = 0; continue; }
     const int64_t bound = a.bound[a.rec[i].w];
-    const int64_t Wt = a.W[t];
-    if (Wt + a.in_w[t] <= bound) {
+    const int64_t Wt = SCLAP_LD(a.W, t, a.nlabels, a.err);
+    if (Wt + SCLAP_LD(a.in_w, t, a.nlabels, a.err) <= bound) {
       a.adm[i] = 1;
     } else {
       a.adm[i] = 0;
@@ -1314,7 +1317,7 @@ __device__ void adm_forced(const LPArgs& a, int64_t lbeg, int64_t cnt, int64_t* 
     const int4 r = a.rec[i];
     const int32_t own = r.y;
     const int64_t bound = a.bound[r.w];
-    const int64_t Wo = a.W[own];
+    const int64_t Wo = SCLAP_LD(a.W, own, a.nlabels, a.err);
     if (Wo > bound) {
       a.grp[i] = own;
       const int c = atomicAdd(&a.ovf_cnt[own], 1);
@@ -1649,7 +1652,7 @@ __device__ void adm_select(const LPArgs& a, int64_t nseg, int32_t source) {
 // directly.
 constexpr int APPLY_SLOTS = 1024;
 __device__ __forceinline__ void apply_delta(int32_t* hk, int32_t* hv, wgt_t* W, int32_t L,
-                                            int32_t d) {
+                                            int32_t d, int64_t nW, int32_t* err) {
   uint32_t s = table_slot(L, 10);
 #pragma unroll 1
   for (int p = 0; p < 8; ++p) {
@@ -1660,7 +1663,7 @@ __device__ __forceinline__ void apply_delta(int32_t* hk, int32_t* hv, wgt_t* W, 
     }
     s = (s + 1) & (APPLY_SLOTS - 1);
   }
-  atomicAdd(&W[L], (wgt_t)d);
+  if (SCLAP_OK(L, nW, err)) atomicAdd(&W[L], (wgt_t)d);
 }
 
 constexpr int64_t MARK_CH = 4096;     // arcs per queued chunk of a moved long row
@@ -1685,7 +1688,7 @@ __device__ void adm_apply(const LPArgs& a, int64_t lbeg, int64_t cnt, int32_t su
       const int64_t i = lbeg + li;
       const int32_t t = a.prop_t[i];
       const int8_t ad = a.adm[i];
-      if (t >= 0) {
+      if (t >= 0 && SCLAP_OK(t, a.nlabels, a.err)) {
         a.in_w[t] = 0;
         if (ad) {
           const int4 r = a.rec[i];
@@ -1696,12 +1699,13 @@ __device__ void adm_apply(const LPArgs& a, int64_t lbeg, int64_t cnt, int32_t su
             rs = r2.x;
             re = r2.x + r2.y;
           }
-          a.label[v] = t;
-          apply_delta(hk, hv, a.W, t, cv);
-          if (agg_src) apply_delta(hk, hv, a.W, own, -cv);
-          else atomicSub(&a.W[own], (wgt_t)cv);
+          if (SCLAP_OK(v, a.N, a.err)) a.label[v] = t;
+          apply_delta(hk, hv, a.W, t, cv, a.nlabels, a.err);
+          if (agg_src) apply_delta(hk, hv, a.W, own, -cv, a.nlabels, a.err);
+          else if (SCLAP_OK(own, a.nlabels, a.err)) atomicSub(&a.W[own], (wgt_t)cv);
           if (re - rs <= 8) {
-            for (int64_t e = rs; e < re; ++e) an[a.col[e]] = 1;
+            for (int64_t e = rs; e < re; ++e)
+              if (SCLAP_OK(a.col[e], a.N, a.err)) an[a.col[e]] = 1;
             re = rs;
           } else if (a.mark_big > 0 && re - rs > a.mark_big) {
             const int32_t nch = (int32_t)((re - rs + MARK_CH - 1) / MARK_CH);
@@ -1719,7 +1723,8 @@ __device__ void adm_apply(const LPArgs& a, int64_t lbeg, int64_t cnt, int32_t su
       big &= big - 1;
       const int64_t s0 = __shfl_sync(0xffffffffu, (long long)rs, src);
       const int64_t s1 = __shfl_sync(0xffffffffu, (long long)re, src);
-      for (int64_t e = s0 + lane; e < s1; e += 32) an[a.col[e]] = 1;
+      for (int64_t e = s0 + lane; e < s1; e += 32)
+        if (SCLAP_OK(a.col[e], a.N, a.err)) an[a.col[e]] = 1;
     }
     const unsigned mm = __match_any_sync(0xffffffffu, slot);
     if (slot >= 0 && lane == __ffs(mm) - 1) {
@@ -1735,7 +1740,8 @@ __device__ void adm_apply(const LPArgs& a, int64_t lbeg, int64_t cnt, int32_t su
   if (run_cnt) atomicAdd(ull(&a.moved[run_slot]), run_cnt);
   __syncthreads();
   for (int j = threadIdx.x; j < APPLY_SLOTS; j += blockDim.x)
-    if (hk[j] >= 0 && hv[j] != 0) atomicAdd(&a.W[hk[j]], (wgt_t)hv[j]);
+    if (hk[j] >= 0 && hv[j] != 0 && SCLAP_OK(hk[j], a.nlabels, a.err))
+      atomicAdd(&a.W[hk[j]], (wgt_t)hv[j]);
 }
 
 constexpr int ADM_NT = 256;
@@ -1833,7 +1839,8 @@ __global__ void __launch_bounds__(256) k_mark_rows(LPArgs a, int32_t sub) {
   const int32_t n = a.mqn[sub];
   for (int32_t q = blockIdx.x; q < n; q += gridDim.x) {
     const longlong2 c = a.mq[q];
-    for (int64_t e = c.x + threadIdx.x; e < c.y; e += blockDim.x) an[a.col[e]] = 1;
+    for (int64_t e = c.x + threadIdx.x; e < c.y; e += blockDim.x)
+      if (SCLAP_OK(a.col[e], a.N, a.err)) an[a.col[e]] = 1;
   }
 }
 
@@ -2095,6 +2102,8 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, wgt_t*
   a.narrow = lv.narrow ? 1 : 0;
   a.arcs32 = lv.M < ((int64_t)1 << 32) ? 1 : 0;
   a.M = lv.M;
+  a.N = lv.N;
+  a.nlabels = Wsize;
   a.noff = sp.noff; a.loff = sp.loff; a.bound = sp.bound; a.rkey = sp.rkey; a.nlab = sp.nlab;
   a.done = sp.done; a.moved = sp.moved; a.rounds = sp.rounds;
   a.label = label; a.W = W; a.in_w = in_w.p; a.mode = run.mode; a.S = S;

@@ -14,7 +14,9 @@ from typing import Optional, Sequence
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libsclap.so")
+# SCLAP_LIBRARY selects another build of the same ABI (the bounds-check
+# build, libsclap_check.so); the default is the in-tree libsclap.so
+LIB_PATH = os.environ.get("SCLAP_LIBRARY") or os.path.join(_HERE, "libsclap.so")
 
 OK, EINVAL, ECSR, ENOMEM, ECUDA, EOVERFLOW, EINFEASIBLE, ETIMEOUT, EINTERNAL = (
     0, -1, -2, -3, -4, -5, -6, -7, -8)
@@ -30,7 +32,7 @@ SYMBOLS = (
     "sclap_server_destroy", "sclap_get_tuning", "sclap_set_tuning", "sclap_autotune",
     "sclap_profile_enable", "sclap_profile_reset", "sclap_profile_read",
     "sclap_profile_timeline", "sclap_profile_dump", "sclap_profile_phases",
-    "sclap_debug_inject",
+    "sclap_debug_inject", "sclap_check_build", "sclap_check_selftest",
 )
 
 
@@ -134,6 +136,8 @@ def _lib():
             "sclap_server_poll": (C.c_int, [p, i64, i32, p, p, p, p]),
             "sclap_server_destroy": (C.c_int, [p]),
             "sclap_debug_inject": (C.c_int, [i64, i64, i32]),
+            "sclap_check_build": (C.c_int, []),
+            "sclap_check_selftest": (C.c_int, [p]),
             "sclap_get_tuning": (None, [p]),
             "sclap_set_tuning": (C.c_int, [p]),
             "sclap_autotune": (C.c_int, [i32, p, p, i32, i32, p, p]),
@@ -155,6 +159,19 @@ def _lib():
 def load():
     """Loads libsclap.so (raises if it is missing)."""
     return _lib()
+
+
+def check_build() -> bool:
+    """True when the loaded library is the bounds-check build."""
+    return _lib().sclap_check_build() == 1
+
+
+def check_selftest(stream=None) -> None:
+    """Bounds-check build only: one checked index in range, one refused
+    (sclap_check_selftest, on `stream` or the default stream); raises
+    SclapError otherwise."""
+    _check(_lib().sclap_check_selftest(None if stream is None else _stream(stream)),
+           "sclap_check_selftest")
 
 
 def sclap_profile_enable(on: bool = True) -> None:
