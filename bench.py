@@ -75,8 +75,9 @@ def parse():
     ap.add_argument("--graph-rounds", action="store_true",
                     help="run each level's LP rounds as one CUDA graph (device-side loop)")
     ap.add_argument("--autotune", action="store_true",
-                    help="before the warm-up, pick the launch tuning for this batch with "
-                         "sclap_autotune (results unchanged; the choice goes into config)")
+                    help="batched: before the warm-up, pick the launch tuning for this batch "
+                         "with sclap_autotune (results unchanged; the choice goes into "
+                         "config); large: pick it per graph at k = 8 and report its gain")
     ap.add_argument("--tuning", default="",
                     help="comma-separated field=value launch-tuning settings applied with "
                          "sclap_set_tuning before the run, e.g. contract_merge=0 (results "
@@ -512,8 +513,32 @@ def large_workload(args):
     runs = []
     edges_total, ms_total = 0, {"host": 0.0, "graph": 0.0}
     all_ok = True
+    rooflines, tuned = {}, {}
+    default_tuning = P.get_tuning().to_dict()
+
+    def median_ms(rp, col, k, reps=3):
+        ms = []
+        for _ in range(reps):
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            P.sclap_partition_device(rp, col, k=k, eps=0.03, seed=0)
+            a1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a0.elapsed_time(a1))
+        return sorted(ms)[len(ms) // 2]
+
     for name, g in large_graphs():
         rp, col = t(g.row_ptr), t(g.col)
+        if args.autotune:
+            # sclap_autotune on this graph at k = 8; its choice is used for
+            # every run of the graph, and its gain reported
+            P.set_tuning(**default_tuning)
+            P.sclap_partition_device(rp, col, k=8, eps=0.03, seed=0)
+            before = median_ms(rp, col, 8)
+            tu = P.autotune([dict(row_ptr=rp, col=col, k=8, eps=0.03, seed=0)], reps=3)
+            after = median_ms(rp, col, 8)
+            tuned[name] = {"tuning": tu.to_dict(), "ms_default": before, "ms_tuned": after,
+                           "gain": before / after if after > 0 else None}
         for k in (2, 8, 32, 64):
             for seed in range(5):
                 res = {}
@@ -545,6 +570,20 @@ def large_workload(args):
                 runs.append({"graph": name, "k": k, "seed": seed, "cut": rh.cut,
                              "ms_host": mh, "ms_graph": mg, "levels": rh.stats["levels"],
                              "checked": ok})
+        # the propose sweep's roofline on this graph: one more call (k = 8,
+        # seed 0, host driver) with CUDA events around every propose phase
+        P.sclap_profile_reset()
+        P.sclap_profile_enable(True)
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        P.sclap_partition_device(rp, col, k=8, eps=0.03, seed=0)
+        p1.record(stream)
+        torch.cuda.synchronize()
+        P.sclap_profile_enable(False)
+        rf = propose_roofline(P.sclap_profile_read(), p0.elapsed_time(p1), 1)
+        rooflines[name] = {x: rf[x] for x in ("achieved", "peak", "unit", "frac",
+                                              "avg_launch_ms", "launches", "share_of_step")}
+    P.set_tuning(**default_tuning)
     clocks = sampler.stop()
     line = {
         "metric": "input edges/s", "value": edges_total / (ms_total["host"] / 1000.0),
@@ -555,8 +594,50 @@ def large_workload(args):
                                "k in {2,8,32,64}, eps 0.03, seeds 0-4, one graph per call"},
         "graph_driver_value": edges_total / (ms_total["graph"] / 1000.0),
         "all_checked": bool(all_ok), "runs": runs, "clocks": clocks,
+        "propose_roofline_k8": rooflines,
     }
+    if args.autotune:
+        line["autotuned"] = tuned
     print(json.dumps(line), flush=True)
+
+
+def propose_roofline(prof, prof_ms, steps):
+    """Roofline of the LP propose sweep from the library's profile of `steps`
+    profiled calls taking prof_ms in all: algorithmic bytes of every propose
+    phase over their fork-to-join time, against the measured HBM peak."""
+    swept = sum(prof["propose_arcs"])
+    unit_arcs = prof["propose_arcs_unit"]
+    prop_ms = prof["sweep_ms"]
+    prop_bytes = (ARC_BYTES * (swept - unit_arcs) + ARC_BYTES_UNIT * unit_arcs
+                  + NODE_BYTES * sum(prof["propose_nodes"]))
+    peaks = {}
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        peaks = json.load(open(pk))
+    peak = peaks.get("hbm_gbs", 6800.0)
+    achieved = prop_bytes / (prop_ms / 1000.0) / 1e9 if prop_ms > 0 else 0.0
+    tr = traffic_for(os.path.join(ROOT, "paper_1402_3281_gb300", "csrc", "lp.cu"))
+    nl = prof["sweeps"]
+    return {
+        "kernel": "LP propose sweep of a sub-round (k_propose_small, k_propose_warp, "
+                  "k_propose_blk*: the degree-bucket launches of one colour class, run "
+                  "concurrently); one 'launch' = one such phase, timed fork to join with "
+                  "CUDA events",
+        "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+        "bytes_model": "12 B per scanned arc (8 on levels of unit edge weights) + 44 B per "
+                       "listed node",
+        "arcs_unit_weight": unit_arcs,
+        "frac": achieved / peak, "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+        "traffic": (tr[0] * swept / nl if tr and tr[0] else None) if nl else None,
+        "bytes_per_launch": prop_bytes / nl if nl else None,
+        "avg_launch_ms": prop_ms / nl if nl else None,
+        "launches": nl,
+        "share_of_step": prop_ms / prof_ms if prof_ms else None,
+        "profiled_ms_per_step": prof_ms / steps,
+        "per_family": {FAMILIES[b]: {"ms": prof["propose_ms"][b], "launches": prof["propose_launches"][b],
+                                     "nodes": prof["propose_nodes"][b], "arcs": prof["propose_arcs"][b]}
+                       for b in range(4)},
+    }
 
 
 def huge_workload(args):
@@ -617,6 +698,18 @@ def huge_workload(args):
         line.update(value=None, error=str(e),
                     torch_reserved_gb=torch.cuda.memory_reserved() / 1e9)
     line["clocks"] = sampler.stop()
+    if line.get("value"):
+        # one more call with CUDA events around every propose phase: the
+        # sweep's roofline at this size
+        P.sclap_profile_reset()
+        P.sclap_profile_enable(True)
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        P.sclap_partition_device(rp, col, k=16, eps=0.03, seed=0)
+        p1.record(stream)
+        torch.cuda.synchronize()
+        P.sclap_profile_enable(False)
+        line["roofline"] = propose_roofline(P.sclap_profile_read(), p0.elapsed_time(p1), 1)
     if args.timeline and line.get("value"):
         # one more call with an event after every launch: time per kernel
         P.sclap_profile_dump()
@@ -743,38 +836,7 @@ def main():
     parts = args.steps * len(graphs) * ws
     value = parts / (elapsed_ms / 1000.0)
     swept = sum(prof["propose_arcs"])
-    unit_arcs = prof["propose_arcs_unit"]
-    prop_ms = prof["sweep_ms"]
-    prop_bytes = (ARC_BYTES * (swept - unit_arcs) + ARC_BYTES_UNIT * unit_arcs
-                  + NODE_BYTES * sum(prof["propose_nodes"]))
-    peaks = {}
-    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(pk):
-        peaks = json.load(open(pk))
-    peak = peaks.get("hbm_gbs", 6800.0)
-    achieved = prop_bytes / (prop_ms / 1000.0) / 1e9 if prop_ms > 0 else 0.0
-    tr = traffic_for(os.path.join(ROOT, "paper_1402_3281_gb300", "csrc", "lp.cu"))
-    nl = prof["sweeps"]
-    roofline = {
-        "kernel": "LP propose sweep of a sub-round (k_propose_small, k_propose_warp, "
-                  "k_propose_blk*: the degree-bucket launches of one colour class, run "
-                  "concurrently); one 'launch' = one such phase, timed fork to join with "
-                  "CUDA events",
-        "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-        "bytes_model": "12 B per scanned arc (8 on levels of unit edge weights) + 44 B per "
-                       "listed node",
-        "arcs_unit_weight": unit_arcs,
-        "frac": achieved / peak, "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
-        "traffic": (tr[0] * swept / nl if tr and tr[0] else None) if nl else None,
-        "bytes_per_launch": prop_bytes / nl if nl else None,
-        "avg_launch_ms": prop_ms / nl if nl else None,
-        "launches": nl,
-        "share_of_step": prop_ms / prof_ms if prof_ms else None,
-        "profiled_ms_per_step": prof_ms / args.steps,
-        "per_family": {FAMILIES[b]: {"ms": prof["propose_ms"][b], "launches": prof["propose_launches"][b],
-                                     "nodes": prof["propose_nodes"][b], "arcs": prof["propose_arcs"][b]}
-                       for b in range(4)},
-    }
+    roofline = propose_roofline(prof, prof_ms, args.steps)
 
     conf = config_dict(len(graphs), ws)
     conf["lp_rounds_driver"] = "cuda-graph (WHILE node per level)" if args.graph_rounds else "host"
