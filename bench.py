@@ -48,6 +48,7 @@ import graphgen as gg  # noqa: E402
 # written.
 ARC_BYTES = 12
 ARC_BYTES_UNIT = 8
+SECTOR_BYTES = 32     # one DRAM sector: the cost of a label gather that misses L2
 NODE_BYTES = 44
 FAMILIES = ["thread_deg_le16", "warp_deg_le128_cta128", "cta256_512", "hub_global_table"]
 
@@ -616,6 +617,10 @@ def propose_roofline(prof, prof_ms, steps):
         peaks = json.load(open(pk))
     peak = peaks.get("hbm_gbs", 6800.0)
     achieved = prop_bytes / (prop_ms / 1000.0) / 1e9 if prop_ms > 0 else 0.0
+    # the same phases with every label gather counted as the 32-byte sector
+    # it touches (what it costs once the label array no longer fits in L2)
+    sec_bytes = prop_bytes + (SECTOR_BYTES - 4) * swept
+    achieved_sec = sec_bytes / (prop_ms / 1000.0) / 1e9 if prop_ms > 0 else 0.0
     tr = traffic_for(os.path.join(ROOT, "paper_1402_3281_gb300", "csrc", "lp.cu"))
     nl = prof["sweeps"]
     return {
@@ -628,6 +633,8 @@ def propose_roofline(prof, prof_ms, steps):
                        "listed node",
         "arcs_unit_weight": unit_arcs,
         "frac": achieved / peak, "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+        "sector_model": {"achieved": achieved_sec, "frac": achieved_sec / peak,
+                         "bytes": "as above with each label gather at 32 B (one sector)"},
         "traffic": (tr[0] * swept / nl if tr and tr[0] else None) if nl else None,
         "bytes_per_launch": prop_bytes / nl if nl else None,
         "avg_launch_ms": prop_ms / nl if nl else None,

@@ -600,8 +600,12 @@ struct CopyTask {              // copy one graph segment (NULL weights -> unit)
   // are dropped.  NULL: plain copy.
   const int64_t* rank;
   int64_t rbase;
+  int64_t nd;                  // nodes written (renumbered tasks; 0: n)
 };
-// Copies graph segments; row_ptr[N_total] = M_total.  N_total_override < 0:
+// Copies graph segments; row_ptr[N_total] = M_total.  Tasks with the same
+// source segment (the trials of one graph) are copied once from the source
+// and then from that first copy, with the node and arc offsets shifted (a
+// streaming copy instead of one renumbering gather per arc).  N_total_override < 0:
 // the end of the last plain task.  ew / nw may be NULL: the destination
 // level keeps no weight array (unit weights).
 void ip_replicate(const std::vector<CopyTask>& tasks, int64_t* row_ptr, int32_t* col,

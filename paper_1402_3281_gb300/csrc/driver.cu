@@ -422,7 +422,7 @@ void build_level0(const std::vector<GIn>& gs, Level& L, cudaStream_t s) {
   std::vector<CopyTask> tasks(B);
   for (int i = 0; i < B; ++i)
     tasks[i] = CopyTask{gs[i].row_ptr, gs[i].col, gs[i].ew, gs[i].nw, 0, 0, gs[i].n, gs[i].m,
-                        L.noff[i], L.aoff[i], nullptr, 0};
+                        L.noff[i], L.aoff[i], nullptr, 0, gs[i].n};
   ip_replicate(tasks, L.row_ptr.p, L.col.p, L.ew.p, L.nw.p, L.M, s);
   L.gid.alloc(std::max<int64_t>(L.N, 1), s);
   fill_gid(L.noff_d.p, B, L.gid.p, L.N, s);
@@ -532,7 +532,7 @@ void run_ip(const std::vector<IPIn>& in, const sclap_config& cfg, wgt_t* Wg,
       aoff[i + 1] = aoff[i] + m;
       boff[i + 1] = boff[i] + in[g].k;
       tasks.push_back(CopyTask{Q.rp(), Q.colp(), Q.ewp(), Q.nwp(), Q.noff[x], Q.aoff[x], n, m,
-                               noff[i], aoff[i], X.rank.p, X.rank_at[x]});
+                               noff[i], aoff[i], X.rank.p, X.rank_at[x], nA});
     }
   }
   Level ip;

@@ -9,6 +9,9 @@
 // the whole trial batch).  The best trial by (overload, cut, trial) is kept.
 #include <algorithm>
 
+#include <map>
+#include <tuple>
+
 #include "common.cuh"
 
 namespace sclap {
@@ -42,6 +45,30 @@ __global__ void k_replicate(const CopyTask* __restrict__ tasks, int64_t* __restr
     const int64_t du = t.rank ? t.rank[u] - t.rbase : u - t.src_n0;
     col[t.dst_a0 + e] = (int32_t)(du + t.dst_n0);
     if (ew) ew[t.dst_a0 + e] = wat(t.ew, t.src_a0 + e);
+  }
+}
+
+// A later copy of an already copied segment: nodes [0, nd) and arcs
+// [0, m) of the first copy (at tn0 / ta0) to dn0 / da0, row offsets shifted
+// by the arc offset difference and neighbour ids by the node offset
+// difference.
+struct CopyFrom {
+  int64_t dn0, da0, tn0, ta0, nd, m;
+};
+__global__ void k_replicate_from(const CopyFrom* __restrict__ tasks, int64_t* __restrict__ row_ptr,
+                                 int32_t* __restrict__ col, int32_t* __restrict__ ew,
+                                 int32_t* __restrict__ nw) {
+  const CopyFrom t = tasks[blockIdx.y];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t da = t.da0 - t.ta0;
+  const int32_t dn = (int32_t)(t.dn0 - t.tn0);
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < t.nd; v += stride) {
+    row_ptr[t.dn0 + v] = row_ptr[t.tn0 + v] + da;
+    if (nw) nw[t.dn0 + v] = nw[t.tn0 + v];
+  }
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < t.m; e += stride) {
+    col[t.da0 + e] = col[t.ta0 + e] + dn;
+    if (ew) ew[t.da0 + e] = ew[t.ta0 + e];
   }
 }
 
@@ -1011,16 +1038,45 @@ void ip_replicate(const std::vector<CopyTask>& tasks, int64_t* row_ptr, int32_t*
                   int32_t* ew, int32_t* nw, int64_t M_total, cudaStream_t s,
                   int64_t N_total_override) {
   if (tasks.empty()) return;
-  DevBuf<CopyTask> d(tasks.size(), s);
-  d.upload(tasks);
+  // the first task of each source segment copies from the source, the
+  // others from that copy
+  std::vector<CopyTask> first;
+  std::vector<CopyFrom> later;
+  std::map<std::tuple<const void*, int64_t, int64_t, int64_t, const void*, int64_t>, size_t> seen;
+  for (const auto& t : tasks) {
+    const auto key = std::make_tuple((const void*)t.col, t.src_n0, t.src_a0, t.m,
+                                     (const void*)t.rank, t.rbase);
+    const auto it = seen.find(key);
+    if (it == seen.end()) {
+      seen.emplace(key, first.size());
+      first.push_back(t);
+    } else {
+      const CopyTask& f = first[it->second];
+      later.push_back(CopyFrom{t.dst_n0, t.dst_a0, f.dst_n0, f.dst_a0, t.nd ? t.nd : t.n, t.m});
+    }
+  }
+  DevBuf<CopyTask> d(first.size(), s);
+  d.upload(first);
   int64_t mx = 1;
-  for (const auto& t : tasks) mx = std::max(mx, std::max(t.n, t.m));
+  for (const auto& t : first) mx = std::max(mx, std::max(t.n, t.m));
   // at least 64 CTAs per task, more when few tasks would leave SMs idle
-  const int64_t per_task = std::max<int64_t>(64, (int64_t)num_sms() * 8 / (int64_t)tasks.size());
-  for (size_t t0 = 0; t0 < tasks.size(); t0 += 65535) {
-    const unsigned ny = (unsigned)std::min<size_t>(65535, tasks.size() - t0);
+  const int64_t per_task = std::max<int64_t>(64, (int64_t)num_sms() * 8 / (int64_t)first.size());
+  for (size_t t0 = 0; t0 < first.size(); t0 += 65535) {
+    const unsigned ny = (unsigned)std::min<size_t>(65535, first.size() - t0);
     dim3 grid(grid_for(mx, 256, per_task), ny);
     k_replicate<<<grid, 256, 0, s>>>(d.p + t0, row_ptr, col, ew, nw); SCLAP_NOTE_LAUNCH("k_replicate");
+  }
+  DevBuf<CopyFrom> dl(std::max<size_t>(later.size(), 1), s);
+  if (!later.empty()) {
+    dl.upload(later);
+    int64_t ml = 1;
+    for (const auto& t : later) ml = std::max(ml, std::max(t.nd, t.m));
+    const int64_t per_l = std::max<int64_t>(64, (int64_t)num_sms() * 8 / (int64_t)later.size());
+    for (size_t t0 = 0; t0 < later.size(); t0 += 65535) {
+      const unsigned ny = (unsigned)std::min<size_t>(65535, later.size() - t0);
+      dim3 grid(grid_for(ml, 256, per_l), ny);
+      k_replicate_from<<<grid, 256, 0, s>>>(dl.p + t0, row_ptr, col, ew, nw); SCLAP_NOTE_LAUNCH("k_replicate_from");
+    }
   }
   int64_t endv = M_total;
   int64_t Ntot = 0;
