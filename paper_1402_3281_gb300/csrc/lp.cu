@@ -766,6 +766,15 @@ __global__ void __launch_bounds__(NT) k_propose_blk(LPArgs a, int32_t sub, int32
     const int64_t deg = c.re - c.rs;
     const int logcap = ceil_log2(max64(2 * deg, 32));
     const uint32_t mask = (1u << logcap) - 1;
+    if (!direct && ((int64_t)1 << logcap) > tcap) {
+      // a launch with a smaller table than this node's hashing needs (the
+      // host only does this when every node indexes its block directly)
+      if (tid == 0) {
+        atomicOr(a.err, DERR_INTERNAL);
+        a.prop_t[i] = -1;
+      }
+      continue;
+    }
     for (int64_t e0 = c.rs; e0 < c.re; e0 += 4 * NT) {
       int32_t C[4], w[4];
 #pragma unroll
@@ -1831,6 +1840,16 @@ __global__ void __launch_bounds__(ADM_NT) k_apply(LPArgs a, int32_t sub) {
   adm_apply(a, lbeg, cnt, sub);
 }
 
+// Largest label count over the slots (local search: the largest k).
+__global__ void k_max_labels(const int32_t* __restrict__ nlab, int32_t nslots, int64_t* out) {
+  int32_t m = 0;
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nslots; i += gridDim.x * blockDim.x)
+    m = max(m, nlab[i]);
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m) atomicMax(reinterpret_cast<unsigned long long*>(out),
+                                             (unsigned long long)m);
+}
+
 // The queued chunks of moved long rows of colour class `sub`: one CTA per
 // chunk marks its heads active for the next round.
 __global__ void __launch_bounds__(256) k_mark_rows(LPArgs a, int32_t sub) {
@@ -2136,13 +2155,21 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, wgt_t*
 
   // The level's degrees decide which propose launches can ever have work
   // (and size the hub tables): one read-back per run, none per round.
-  DevBuf<int64_t> dstat(3, s);
+  DevBuf<int64_t> dstat(4, s);
   dstat.zero();
   level_degree_stats(lv.row_ptr, N, B7_MAXDEG, dstat.p, s);
-  int64_t hstat[3] = {0, 0, 0};
+  if (run.mode != MODE_CLUSTER && sp.nslots > 0) {
+    k_max_labels<<<grid_for(sp.nslots, 256, 64), 256, 0, s>>>(sp.nlab, sp.nslots, dstat.p + 3); SCLAP_NOTE_LAUNCH("k_max_labels");
+  }
+  int64_t hstat[4] = {0, 0, 0, 0};
   SCLAP_CUDA(cudaMemcpyAsync(hstat, dstat.p, sizeof(hstat), cudaMemcpyDeviceToHost, s));
   stream_sync(s);
   const int64_t maxdeg = hstat[0], nhubs = hstat[1], hub_slots = hstat[2];
+  // local search where every slot has at most B5_SLOTS labels: every node of
+  // the CTA buckets indexes its block directly, so buckets 6 and 7 need only
+  // a B5_SLOTS-entry shared table (more CTAs per SM) instead of one sized
+  // for hashing 2 x degree labels
+  const bool compact_blk = run.mode != MODE_CLUSTER && hstat[3] > 0 && hstat[3] <= B5_SLOTS;
   const bool refine = run.mode != MODE_CLUSTER;
   const Tuning tu = tuning_get();
   const int nsb = tu.small_max_deg >= 16 ? 3 : 2;   // buckets of the thread-per-node launch
@@ -2291,10 +2318,18 @@ int64_t lp_run(const LevelView& lv, const SlotParams& sp, int32_t* label, wgt_t*
       launch_k(p, k_propose_blk<128, B5_SLOTS>, grid(5, 6, 1, grid_b5), 128, smem5, ls, a, sub, 5); SCLAP_NOTE_LAUNCH("k_propose_blk128");
     });
     if (need[6]) launch(6, 7, 2, [&](cudaStream_t ls, bool p) {
-      launch_k(p, k_propose_blk<256, B6_SLOTS>, grid(6, 7, 1, grid_b6), 256, smem6, ls, a, sub, 6); SCLAP_NOTE_LAUNCH("k_propose_blk256");
+      if (compact_blk)
+        launch_k(p, k_propose_blk<256, B5_SLOTS>, grid(6, 7, 1, grid_b5), 256, smem5, ls, a, sub, 6);
+      else
+        launch_k(p, k_propose_blk<256, B6_SLOTS>, grid(6, 7, 1, grid_b6), 256, smem6, ls, a, sub, 6);
+      SCLAP_NOTE_LAUNCH("k_propose_blk256");
     });
     if (need[7]) launch(7, 8, 2, [&](cudaStream_t ls, bool p) {
-      launch_k(p, k_propose_blk<512, B7_SLOTS>, grid(7, 8, 1, grid_b7), 512, smem7, ls, a, sub, 7); SCLAP_NOTE_LAUNCH("k_propose_blk512");
+      if (compact_blk)
+        launch_k(p, k_propose_blk<512, B5_SLOTS>, grid(7, 8, 1, grid_b6), 512, smem5, ls, a, sub, 7);
+      else
+        launch_k(p, k_propose_blk<512, B7_SLOTS>, grid(7, 8, 1, grid_b7), 512, smem7, ls, a, sub, 7);
+      SCLAP_NOTE_LAUNCH("k_propose_blk512");
     });
     if (need[8]) launch(8, 9, 3, [&](cudaStream_t ls, bool p) {
       launch_k(p, k_hub_offsets, 1, HO_NT, 0, ls, a, sub, hs); SCLAP_NOTE_LAUNCH("k_hub_offsets");
