@@ -290,6 +290,19 @@ def test_partition_active_coarsening_bit_exact(name):
     assert res.stats["level_n"] == list(ref.stats.level_n[:ref.stats.levels])
 
 
+@pytest.mark.parametrize("gname,k", [("split_hub", 1500), ("rmat14", 1100)])
+def test_partition_with_more_than_1024_blocks_bit_exact(gname, k):
+    """Local search with more blocks than the compact CTA tables hold (1,024):
+    the degree 513..8192 buckets use their full hashing-sized tables, and
+    the split hubs accumulate by block without the per-part shared-memory
+    pre-sum (more than 1,024 blocks)."""
+    g = split_hub_graph(3) if gname == "split_hub" else gg.rmat(14, 8, 5)
+    ref = O.partition(g, k, 0.03, seed=0)
+    res = P.sclap_partition_device(*dg(g), k=k, eps=0.03, seed=0)
+    assert (res.status, res.cut) == (ref.status, ref.cut)
+    assert np.array_equal(res.block.cpu().numpy(), ref.block)
+
+
 @pytest.mark.parametrize("name,k", [("rmat16", 2), ("rgg", 8), ("weighted", 5), ("hub", 4),
                                     ("split_hub", 3)])
 def test_partition_graph_driver_bit_exact(name, k):
