@@ -877,6 +877,9 @@ def main():
                       for g, k, eps in graphs]
         h2d = sum(g.row_ptr.nbytes + g.col.nbytes for g, _, _ in graphs)
         d2h = sum(4 * g.n for g, _, _ in graphs)
+        # one untimed call first, as for the device-resident steps (the
+        # library's host staging buffer is allocated on first use)
+        P.sclap_partition_batch(host_items, device=False)
         barrier()
         t0 = time.perf_counter()
         e2e_steps = max(1, min(2, args.steps))

@@ -14,6 +14,7 @@
 #include <cstring>
 #include <chrono>
 #include <memory>
+#include <thread>
 
 #include "common.cuh"
 
@@ -1085,6 +1086,73 @@ struct HostUpload {
   }
 };
 
+// Host arrays of a batch go through one pinned staging buffer per calling
+// thread, kept and grown across calls: host threads pack every graph's
+// arrays into it, one copy moves them to one device buffer, and the block
+// arrays come back the same way.  (One pageable copy per array costs a
+// driver-staged transfer each: about a thousand per 512-graph batch.)
+struct PinnedStage {
+  void* p = nullptr;
+  size_t cap = 0;
+  PinnedStage() = default;
+  PinnedStage(const PinnedStage&) = delete;
+  PinnedStage& operator=(const PinnedStage&) = delete;
+  ~PinnedStage() {
+    if (p) cudaFreeHost(p);
+  }
+  // NULL when pinned memory cannot be had (the caller copies array by array)
+  char* get(size_t bytes) {
+    if (bytes > cap) {
+      if (p) cudaFreeHost(p);
+      p = nullptr;
+      cap = 0;
+      const size_t want = std::max<size_t>(bytes + bytes / 4, (size_t)1 << 20);
+      if (cudaHostAlloc(&p, want, cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+        return nullptr;
+      }
+      cap = want;
+    }
+    return static_cast<char*>(p);
+  }
+};
+thread_local PinnedStage t_stage;
+
+struct Piece {
+  void* dst;
+  const void* src;
+  size_t bytes;
+};
+// The pieces' memcpys on up to 8 host threads, split into runs of about
+// equal bytes.
+void parallel_copy(const std::vector<Piece>& pieces) {
+  size_t total = 0;
+  for (const Piece& x : pieces) total += x.bytes;
+  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  const int nt = (int)std::min<size_t>(std::min(8u, hw), std::max<size_t>(1, total >> 24));
+  if (nt <= 1) {
+    for (const Piece& x : pieces) std::memcpy(x.dst, x.src, x.bytes);
+    return;
+  }
+  // cut the byte stream into nt ranges; a piece may be split between threads
+  auto run = [&](size_t lo, size_t hi) {
+    size_t at = 0;
+    for (const Piece& x : pieces) {
+      const size_t a = std::max(lo, at), b = std::min(hi, at + x.bytes);
+      if (a < b)
+        std::memcpy(static_cast<char*>(x.dst) + (a - at),
+                    static_cast<const char*>(x.src) + (a - at), b - a);
+      at += x.bytes;
+      if (at >= hi) break;
+    }
+  };
+  std::vector<std::thread> th;
+  for (int t = 1; t < nt; ++t) th.emplace_back(run, total * t / nt, total * (t + 1) / nt);
+  run(0, total / nt);
+  for (auto& x : th) x.join();
+}
+
 // A one-slot level holding a copy of a device graph (step entry points).
 void single_level(const GIn& g, Level& L, cudaStream_t s) {
   std::vector<GIn> v{g};
@@ -1223,6 +1291,53 @@ int sclap_partition_batch(int32_t count, sclap_graph* graphs, const sclap_config
       const std::vector<int64_t> m = device_arcs_many(ends, s);
       for (size_t j = 0; j < who.size(); ++j) dev_m[who[j]] = m[j];
     }
+    // host arrays: sizes and packed offsets (16-byte aligned) of every valid
+    // graph, so that one pinned buffer and one copy carry them all
+    struct Pack { int64_t m; size_t rp, col, nw, ew; };
+    std::vector<Pack> pk(count);
+    size_t in_bytes = 0, out_bytes = 0;
+    auto take = [&](size_t bytes) {
+      const size_t at = in_bytes;
+      in_bytes += (bytes + 15) & ~(size_t)15;
+      return at;
+    };
+    char* stage = nullptr;
+    DevBuf<char> din;
+    DevBuf<int32_t> dout;
+    if (!device_ptrs) {
+      for (int i = 0; i < count; ++i) {
+        const sclap_graph& G = graphs[i];
+        pk[i].m = -1;
+        if (G.row_ptr && G.n >= 1 && G.n < ((int64_t)1 << 31)) {
+          const int64_t m = G.row_ptr[G.n];
+          if (m < 0) continue;
+          pk[i].m = m;
+          pk[i].rp = take((G.n + 1) * sizeof(int64_t));
+          pk[i].col = take(m * sizeof(int32_t));
+          pk[i].nw = G.node_w ? take(G.n * sizeof(int32_t)) : 0;
+          pk[i].ew = G.edge_w ? take(m * sizeof(int32_t)) : 0;
+          out_bytes += G.n * sizeof(int32_t);
+        }
+      }
+      if (in_bytes > 0) stage = t_stage.get(std::max(in_bytes, out_bytes));
+      if (stage) {
+        std::vector<Piece> pieces;
+        for (int i = 0; i < count; ++i) {
+          const sclap_graph& G = graphs[i];
+          if (pk[i].m < 0 || (pk[i].m > 0 && !G.col)) continue;
+          pieces.push_back({stage + pk[i].rp, G.row_ptr, (G.n + 1) * sizeof(int64_t)});
+          pieces.push_back({stage + pk[i].col, G.col, pk[i].m * sizeof(int32_t)});
+          if (G.node_w) pieces.push_back({stage + pk[i].nw, G.node_w, G.n * sizeof(int32_t)});
+          if (G.edge_w) pieces.push_back({stage + pk[i].ew, G.edge_w, pk[i].m * sizeof(int32_t)});
+        }
+        parallel_copy(pieces);
+        din.alloc(in_bytes, s);
+        SCLAP_CUDA(cudaMemcpyAsync(din.p, stage, in_bytes, cudaMemcpyHostToDevice, s));
+        dout.alloc(std::max<size_t>(out_bytes / sizeof(int32_t), 1), s);
+        stream_sync(s);   // the stage is free again (it carries the blocks back)
+      }
+    }
+    int64_t out_at = 0;
     for (int i = 0; i < count; ++i) {
       sclap_graph& G = graphs[i];
       G.status = guarded([&] {
@@ -1231,6 +1346,15 @@ int sclap_partition_batch(int32_t count, sclap_graph* graphs, const sclap_config
         if (device_ptrs) {
           g.n = G.n; g.m = dev_m[i]; g.row_ptr = G.row_ptr;
           g.col = G.col; g.nw = G.node_w; g.ew = G.edge_w;
+        } else if (stage) {
+          if (pk[i].m < 0) throw Error(SCLAP_ECSR, "row_ptr[n] < 0");
+          g.n = G.n;
+          g.m = pk[i].m;
+          g.row_ptr = reinterpret_cast<const int64_t*>(din.p + pk[i].rp);
+          g.col = reinterpret_cast<const int32_t*>(din.p + pk[i].col);
+          g.nw = G.node_w ? reinterpret_cast<const int32_t*>(din.p + pk[i].nw) : nullptr;
+          g.ew = G.edge_w ? reinterpret_cast<const int32_t*>(din.p + pk[i].ew) : nullptr;
+          check_col(G.col, g.m);
         } else {
           ups.emplace_back(new HostUpload(G.n, G.row_ptr, G.col, G.node_w, G.edge_w, s));
           g = ups.back()->g;
@@ -1241,6 +1365,9 @@ int sclap_partition_batch(int32_t count, sclap_graph* graphs, const sclap_config
         idx.push_back(i);
         if (device_ptrs) {
           outs.push_back(G.block_out);
+        } else if (stage) {
+          outs.push_back(dout.p + out_at);
+          out_at += G.n;
         } else {
           outbufs.emplace_back(new DevBuf<int32_t>(G.n, s));
           outs.push_back(outbufs.back()->p);
@@ -1251,9 +1378,22 @@ int sclap_partition_batch(int32_t count, sclap_graph* graphs, const sclap_config
     if (gs.empty()) return;
     std::vector<GOut> res;
     run_batch(gs, c, outs, res, s);
+    if (!device_ptrs && stage) {
+      // every block array back in one copy, then out to the callers' arrays
+      SCLAP_CUDA(cudaMemcpyAsync(stage, dout.p, out_at * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                 s));
+      stream_sync(s);
+      std::vector<Piece> pieces;
+      for (size_t j = 0; j < gs.size(); ++j) {
+        const sclap_graph& G = graphs[idx[j]];
+        pieces.push_back({G.block_out, stage + (outs[j] - dout.p) * sizeof(int32_t),
+                          G.n * sizeof(int32_t)});
+      }
+      parallel_copy(pieces);
+    }
     for (size_t j = 0; j < gs.size(); ++j) {
       sclap_graph& G = graphs[idx[j]];
-      if (!device_ptrs)
+      if (!device_ptrs && !stage)
         SCLAP_CUDA(cudaMemcpyAsync(G.block_out, outs[j], G.n * sizeof(int32_t),
                                    cudaMemcpyDeviceToHost, s));
       G.cut = res[j].cut;
