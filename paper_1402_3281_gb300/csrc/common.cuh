@@ -629,6 +629,7 @@ struct GGGArgs {
   int32_t* front;          // scratch [N]: newly reached nodes (step alternates with it)
   int32_t* heavy;          // scratch [N]: a step's long rows (grouped growing)
   int64_t N;               // nodes of all trial slots (array lengths for bounds checks)
+  uint32_t* asg;           // scratch [N / 32 + 1]: assigned-node bitmap (grouped growing)
   int64_t* wfA;            // scratch [sum k]
   int32_t* wforder;        // scratch [sum k]
   int32_t nslots;

@@ -433,6 +433,17 @@ struct GroupState {
 constexpr int GG_NT = 512;
 constexpr int64_t GG_HEAVY = 8 * GG_NT;
 
+// Assigned-node bitmap of the grouped growing (one bit per node of the
+// trial level, set when a growth step assigns the node): the arc passes ask
+// it whether a head is still free, a read that stays in L2 where the label
+// array (32 bits per node, one trial copy per slot) does not.
+__device__ __forceinline__ bool is_assigned(const uint32_t* asg, int64_t y) {
+  return (asg[y >> 5] >> (y & 31)) & 1u;
+}
+__device__ __forceinline__ void mark_assigned(uint32_t* asg, int64_t y) {
+  atomicOr(&asg[y >> 5], 1u << (y & 31));
+}
+
 __global__ void __launch_bounds__(GG_NT) k_ggg_group(GGGArgs a, int32_t cpt, GroupState* gst,
                                                      uint64_t* ph, int32_t* pv, int64_t* pw,
                                                      uint32_t lim) {
@@ -525,6 +536,7 @@ __global__ void __launch_bounds__(GG_NT) k_ggg_group(GGGArgs a, int32_t cpt, Gro
     if (seed < 0) break;
     if (r == 0 && tid == 0) {
       a.label[base + seed] = (int32_t)(bo + j);
+      mark_assigned(a.asg, base + seed);
       stp[0] = (int32_t)(base + seed);
       st->nstep = 1;
       st->nfront = 0;
@@ -547,7 +559,7 @@ __global__ void __launch_bounds__(GG_NT) k_ggg_group(GGGArgs a, int32_t cpt, Gro
       // arc lists it as reached (weights > 0)
       auto visit = [&](int64_t e) {
         const int32_t y = a.col[e];
-        if (!SCLAP_OK(y, a.N, a.err) || a.label[y] >= 0) return;
+        if (!SCLAP_OK(y, a.N, a.err) || is_assigned(a.asg, y)) return;
         const unsigned long long old = atomicAdd(ull(&a.conn[y]), (unsigned long long)a.ew[e]);
         if (!ordered && old == 0) {
           frt[atomicAdd(&st->nfront, 1)] = y;
@@ -605,8 +617,10 @@ __global__ void __launch_bounds__(GG_NT) k_ggg_group(GGGArgs a, int32_t cpt, Gro
         const int32_t nf = *(volatile int32_t*)&st->nfront;
         if (Wj + fsum <= avg) {
           // all of them fit: they are the next step, in any order
-          for (int64_t q = (int64_t)r * GG_NT + tid; q < nf; q += qstride)
+          for (int64_t q = (int64_t)r * GG_NT + tid; q < nf; q += qstride) {
             a.label[frt[q]] = (int32_t)(bo + j);
+            mark_assigned(a.asg, frt[q]);
+          }
           int32_t* t = stp; stp = frt; frt = t;
           if (!sync()) return;
           if (r == 0 && tid == 0) {
@@ -655,8 +669,10 @@ __global__ void __launch_bounds__(GG_NT) k_ggg_group(GGGArgs a, int32_t cpt, Gro
       if (!sync()) return;
       const int32_t ns2 = *(volatile int32_t*)&st->nnext;
       const int64_t newW = Wj + *(volatile int64_t*)&st->accw;
-      for (int64_t q = (int64_t)r * GG_NT + tid; q < ns2; q += qstride)
+      for (int64_t q = (int64_t)r * GG_NT + tid; q < ns2; q += qstride) {
         a.label[stp[q]] = (int32_t)(bo + j);
+        mark_assigned(a.asg, stp[q]);
+      }
       if (!sync()) return;
       if (r == 0 && tid == 0) {
         st->nstep = ns2;
@@ -1132,6 +1148,9 @@ void ggg_trials(const GGGArgs& a_in, const std::vector<int64_t>& noff,
     per_block = std::max(per_block, (noff[i + 1] - noff[i]) / std::max<int32_t>(1, nlab[i]));
   if (cpt >= 4 && per_block >= ((int64_t)1 << 14)) {
     DevBuf<GroupState> gs(S, s);
+    DevBuf<uint32_t> asg((size_t)((a.N + 31) / 32 + 1), s);
+    asg.zero();
+    a.asg = asg.p;
     DevBuf<uint64_t> ph(S * cpt, s);
     DevBuf<int32_t> pv(S * cpt, s);
     DevBuf<int64_t> pw(S * cpt, s);
