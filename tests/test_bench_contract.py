@@ -36,3 +36,29 @@ def test_reference_line():
 
 def test_other_ranks_print_nothing():
     assert _run({"RANK": "1", "LOCAL_RANK": "1", "WORLD_SIZE": "2"}) == []
+
+
+def test_propose_roofline_arithmetic():
+    """The sweep's roofline from a library profile: 12 B per weighted arc, 8
+    per unit-weight arc, 44 per listed node, over the phases' time; the
+    sector reading adds 28 B per arc (a 4-byte label gather read as a 32-byte
+    sector); traffic scales the committed bytes per arc to the average
+    phase when the capture matches the current kernel source."""
+    sys.path.insert(0, ROOT)
+    import bench
+    prof = {"propose_arcs": [600, 300, 100, 0], "propose_arcs_unit": 400,
+            "propose_nodes": [50, 30, 20, 0], "sweep_ms": 2.0, "sweeps": 4,
+            "propose_ms": [1.0, 0.5, 0.5, 0.0], "propose_launches": [4, 4, 4, 0]}
+    r = bench.propose_roofline(prof, prof_ms=8.0, steps=2)
+    alg = 12 * 600 + 8 * 400 + 44 * 100
+    assert abs(r["achieved"] - alg / 2e-3 / 1e9) < 1e-12
+    assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-15
+    assert abs(r["sector_model"]["achieved"] - (alg + 28 * 1000) / 2e-3 / 1e9) < 1e-12
+    assert r["launches"] == 4 and abs(r["avg_launch_ms"] - 0.5) < 1e-15
+    assert abs(r["bytes_per_launch"] - alg / 4) < 1e-9
+    assert abs(r["share_of_step"] - 0.25) < 1e-15 and abs(r["profiled_ms_per_step"] - 4.0) < 1e-15
+    tr = bench.traffic_for(os.path.join(ROOT, "paper_1402_3281_gb300", "csrc", "lp.cu"))
+    if tr is not None and tr[0]:
+        assert abs(r["traffic"] - tr[0] * 1000 / 4) < 1e-6
+    else:
+        assert r["traffic"] is None
