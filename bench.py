@@ -348,6 +348,25 @@ def print_phases(ph, steps):
               f"{nodes:11.0f} {arcs:12.0f} {sw:9.3f} {ad:8.3f} {gbs:7.0f}", file=sys.stderr)
 
 
+def sweep_by_kind(ph, steps=1):
+    """Per run kind (clustering, local search, initial partitioning, ...)
+    from the library's sub-round records: nodes and arcs swept, propose time,
+    SCLaP edges/s (arcs / propose time) and algorithmic GB/s at 12 B per arc
+    (an upper bound on levels of unit edge weights) + 44 B per node."""
+    out = {}
+    if ph.size == 0:
+        return out
+    for kind in sorted({int(r[0]) for r in ph}):
+        q = ph[ph[:, 0] == kind]
+        nodes, arcs = q[:, 3].sum() / steps, q[:, 4].sum() / steps
+        sw = q[:, 5].sum() / steps
+        out[KINDS.get(kind, str(kind))] = {
+            "sub_rounds": len(q) / steps, "nodes": nodes, "arcs": arcs, "sweep_ms": sw,
+            "edges_per_s": arcs / (sw / 1e3) if sw else None,
+            "gbs": (ARC_BYTES * arcs + NODE_BYTES * nodes) / (sw / 1e3) / 1e9 if sw else None}
+    return out
+
+
 def serve_stream(P, graphs, lam, count, ref_cuts, seed=0):
     """Open-loop Poisson stream through the server: ``count`` requests (the
     batch's graphs in order, cycling) with exponential gaps of mean 1/lam s,
@@ -717,6 +736,7 @@ def huge_workload(args):
         torch.cuda.synchronize()
         P.sclap_profile_enable(False)
         line["roofline"] = propose_roofline(P.sclap_profile_read(), p0.elapsed_time(p1), 1)
+        line["sweep_by_kind"] = sweep_by_kind(P.sclap_profile_phases())
     if args.timeline and line.get("value"):
         # one more call with an event after every launch: time per kernel
         P.sclap_profile_dump()

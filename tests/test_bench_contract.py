@@ -62,3 +62,19 @@ def test_propose_roofline_arithmetic():
         assert abs(r["traffic"] - tr[0] * 1000 / 4) < 1e-6
     else:
         assert r["traffic"] is None
+
+
+def test_sweep_by_kind_groups_the_sub_round_records():
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import bench
+    # (kind, round, class, nodes, arcs, propose ms, admission ms)
+    ph = np.array([[0, 0, 0, 10, 100, 1.0, 0.5], [0, 0, 1, 20, 300, 1.0, 0.5],
+                   [1, 0, 0, 5, 50, 0.5, 0.1]], dtype=np.float64)
+    out = bench.sweep_by_kind(ph, steps=1)
+    assert set(out) == {bench.KINDS.get(0, "0"), bench.KINDS.get(1, "1")}
+    c = out[bench.KINDS.get(0, "0")]
+    assert c["sub_rounds"] == 2 and c["nodes"] == 30 and c["arcs"] == 400 and c["sweep_ms"] == 2.0
+    assert abs(c["edges_per_s"] - 400 / 2e-3) < 1e-6
+    assert abs(c["gbs"] - (12 * 400 + 44 * 30) / 2e-3 / 1e9) < 1e-12
+    assert bench.sweep_by_kind(np.zeros((0, 7))) == {}
